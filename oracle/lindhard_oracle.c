@@ -1,0 +1,260 @@
+/*
+ * Lindhard susceptibility oracle: plain FP64 CPU code.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the
+ * CPU-baseline leg of the benchmark load this library.  The GPU library never
+ * links, includes or calls it, and it shares no code with the GPU library.
+ *
+ * What it computes (Wang et al., "Lindhard and RPA susceptibility
+ * computations in extended momentum space in electron doped cuprates"):
+ *
+ *   Sec. 2, Eq. 9:  Im chi(q,w) = - Int_{-w}^{0} de/(2 pi) Int d^dp/(2 pi)^d
+ *                                   A(p,e) A(p+q, e+w)
+ *   Sec. 3 (2D reduction, k_z dispersion neglected): d = 2.
+ *   Sec. 2, Eqs. 4-5: A(p,e) = |M(p)|^2 * gamma / (pi [(e - xi_p)^2 + gamma^2]),
+ *                     a Lorentzian of unit weight centred on the band energy.
+ *   Sec. 3 (rigid band): mu shifted to hold the requested electron count.
+ *
+ * Discretisation (each choice is a reading of the paper, listed in the design doc):
+ *   lattice constant 1, zone width 2 pi, N = zones * npz points per axis,
+ *   p_i = (i - N/2) * dp, dp = 2 pi / npz;
+ *   cell-centred energies e_j = -E + (j + 1/2) de, de = 2E / n_eps;
+ *   the T = 0 occupation split of Sec. 3 / Appendix A (Eq. A3): the integral
+ *   over e in [-w, 0] becomes the sum over cells j with e_j < 0 and
+ *   e_{j+m} >= 0, i.e. 2j+1 < n_eps <= 2(j+m)+1;
+ *   w_m = m de; lags q_l = (l - Q/2) dp;
+ *   d^2p/(2 pi)^2 -> dp^2/(2 pi)^2 = 1/npz^2 per grid point;
+ *   zones == 1: the grid is one period and p+q wraps (reduced zone);
+ *   zones  > 1: A = 0 outside the grid (extended zone, truncation).
+ *
+ * Everything is a plain loop in the order the formula is written.  OpenMP
+ * splits independent outputs across threads; no sum is reordered within one
+ * output.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+static const double LO_PI = 3.14159265358979323846264338327950288;
+
+/* Single-band dispersion eps0(p) in eV.
+ * kind 0: square-lattice tight binding with hoppings t, t', t'' (the band
+ *         that stands in for the paper's KKR CuO2 band of Sec. 3):
+ *         -2t (cos px + cos py) - 4t' cos px cos py - 2t'' (cos 2px + cos 2py)
+ * kind 1: free electrons, |p|^2 / 2 (the "free fermion form" of Sec. 2). */
+double lo_band(int kind, double t, double tp, double tpp, double px, double py)
+{
+    if (kind == 1)
+        return 0.5 * (px * px + py * py);
+    return -2.0 * t * (cos(px) + cos(py)) - 4.0 * tp * cos(px) * cos(py)
+           - 2.0 * tpp * (cos(2.0 * px) + cos(2.0 * py));
+}
+
+/* Electron count per site including spin at chemical potential mu
+ * (rigid band, Sec. 3).  Each first-zone state carries the weight of its
+ * Lorentzian (Eq. 5) below the Fermi level:
+ *   Int_{-inf}^{0} gamma / (pi [(e - xi)^2 + gamma^2]) de = 1/2 - atan(xi/gamma)/pi,
+ * summed over the npz x npz first-zone grid with measure 2/npz^2. */
+double lo_filling(int kind, double t, double tp, double tpp, double gamma,
+                  int npz, double mu)
+{
+    double dp = 2.0 * LO_PI / npz, sum = 0.0;
+    for (int ix = 0; ix < npz; ++ix)
+        for (int iy = 0; iy < npz; ++iy) {
+            double px = (ix - npz / 2) * dp, py = (iy - npz / 2) * dp;
+            double xi = lo_band(kind, t, tp, tpp, px, py) - mu;
+            sum += 0.5 - atan(xi / gamma) / LO_PI;
+        }
+    return 2.0 * sum / ((double)npz * (double)npz);
+}
+
+/* mu such that lo_filling(mu) == filling, by bisection on [-20, 20] eV.
+ * lo_filling is strictly increasing in mu, so the root is unique.
+ * Returns 0 on success, 1 if the filling lies outside (0, 2). */
+int lo_mu(int kind, double t, double tp, double tpp, double gamma, int npz,
+          double filling, double *mu_out)
+{
+    double lo = -20.0, hi = 20.0;
+    if (!(filling > lo_filling(kind, t, tp, tpp, gamma, npz, lo)) ||
+        !(filling < lo_filling(kind, t, tp, tpp, gamma, npz, hi)))
+        return 1;
+    for (int it = 0; it < 200 && hi - lo > 1e-14; ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (lo_filling(kind, t, tp, tpp, gamma, npz, mid) < filling)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    *mu_out = 0.5 * (lo + hi);
+    return 0;
+}
+
+/* Spectral function A(p_i, e_j) on the grid (Eqs. 4-5), layout [N][N][n_eps]
+ * with the energy index fastest.  |M(p)|^2 = exp(-|p|^2 ff_a^2 / 8) stands in
+ * for the Bloch momentum density of Eq. 7; ff_a == 0 means |M|^2 = 1. */
+void lo_spectral(int kind, double t, double tp, double tpp, double mu,
+                 double gamma, double ff_a, int zones, int npz, int n_eps,
+                 double e_max, double *A)
+{
+    int N = zones * npz;
+    double dp = 2.0 * LO_PI / npz, de = 2.0 * e_max / n_eps;
+#pragma omp parallel for schedule(static)
+    for (int ix = 0; ix < N; ++ix)
+        for (int iy = 0; iy < N; ++iy) {
+            double px = (ix - N / 2) * dp, py = (iy - N / 2) * dp;
+            double xi = lo_band(kind, t, tp, tpp, px, py) - mu;
+            double m2 = (ff_a == 0.0) ? 1.0
+                        : exp(-(px * px + py * py) * ff_a * ff_a / 8.0);
+            for (int j = 0; j < n_eps; ++j) {
+                double e = -e_max + (j + 0.5) * de;
+                A[((size_t)ix * N + iy) * n_eps + j] =
+                    m2 * gamma / (LO_PI * ((e - xi) * (e - xi) + gamma * gamma));
+            }
+        }
+}
+
+/* Index of momentum i + s on the grid, or -1 if it falls outside
+ * (extended zone).  In the reduced zone (zones == 1) it wraps. */
+static long lo_shift(long i, long s, long N, int periodic)
+{
+    long k = i + s;
+    if (periodic) {
+        k %= N;
+        if (k < 0) k += N;
+        return k;
+    }
+    return (k >= 0 && k < N) ? k : -1;
+}
+
+/* The discrete Eq. 9 at n sample outputs (lx[k], ly[k], m[k]):
+ *   out[k] = -(de / 2 pi) (1 / npz^2) *
+ *            sum_{j: e_j < 0 <= e_{j+m}} sum_{p, p+q on grid} A(p, e_j) A(p+q, e_{j+m})
+ * with q = ((lx - Q/2) dp, (ly - Q/2) dp), Q = q_extent, w = m de. */
+void lo_imchi_samples(int zones, int npz, int n_eps, double e_max,
+                      const double *A, int q_extent, long n, const int *lx,
+                      const int *ly, const int *m, double *out)
+{
+    long N = (long)zones * npz;
+    int periodic = (zones == 1);
+    double de = 2.0 * e_max / n_eps;
+    double c = de / (2.0 * LO_PI) / ((double)npz * (double)npz);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (long k = 0; k < n; ++k) {
+        long sx = lx[k] - q_extent / 2, sy = ly[k] - q_extent / 2;
+        int mm = m[k];
+        double sum = 0.0;
+        for (long ix = 0; ix < N; ++ix) {
+            long jx = lo_shift(ix, sx, N, periodic);
+            if (jx < 0) continue;
+            for (long iy = 0; iy < N; ++iy) {
+                long jy = lo_shift(iy, sy, N, periodic);
+                if (jy < 0) continue;
+                const double *a = A + ((size_t)ix * N + iy) * n_eps;
+                const double *b = A + ((size_t)jx * N + jy) * n_eps;
+                for (int j = 0; j + mm < n_eps; ++j) {
+                    /* occupied at e_j (e_j < 0), empty at e_{j+m} (>= 0) */
+                    if (2 * j + 1 < n_eps && 2 * (j + mm) + 1 >= n_eps)
+                        sum += a[j] * b[j + mm];
+                }
+            }
+        }
+        out[k] = -c * sum;
+    }
+}
+
+/* Gradient of L = sum_{l,m} w[l_x][l_y][m] Im chi(q_l, w_m) with respect to
+ * A(p_i, e_j), at n sample points (ix[k], iy[k], j[k]).  Eq. 9 is bilinear in
+ * the occupied part a = A [e < 0] and the empty part b = A [e >= 0]:
+ *   dL/da(p, e_j)   = -c sum_{l,m} w(l,m) b(p + q_l, e_{j+m})
+ *   dL/db(p', e_j') = -c sum_{l,m} w(l,m) a(p' - q_l, e_{j'-m})
+ * w has layout [Q][Q][n_omega]. */
+void lo_grad_A_samples(int zones, int npz, int n_eps, double e_max,
+                       const double *A, int q_extent, int n_omega,
+                       const double *w, long n, const int *ix, const int *iy,
+                       const int *jj, double *out)
+{
+    long N = (long)zones * npz;
+    int periodic = (zones == 1), Q = q_extent;
+    double de = 2.0 * e_max / n_eps;
+    double c = de / (2.0 * LO_PI) / ((double)npz * (double)npz);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (long k = 0; k < n; ++k) {
+        int j = jj[k];
+        int occupied = (2 * j + 1 < n_eps);
+        double sum = 0.0;
+        for (int lx = 0; lx < Q; ++lx) {
+            long sx = lx - Q / 2;
+            long kx = lo_shift(ix[k], occupied ? sx : -sx, N, periodic);
+            if (kx < 0) continue;
+            for (int ly = 0; ly < Q; ++ly) {
+                long sy = ly - Q / 2;
+                long ky = lo_shift(iy[k], occupied ? sy : -sy, N, periodic);
+                if (ky < 0) continue;
+                const double *row = A + ((size_t)kx * N + ky) * n_eps;
+                const double *wr = w + ((size_t)lx * Q + ly) * n_omega;
+                for (int mm = 0; mm < n_omega; ++mm) {
+                    if (occupied) {
+                        /* partner e_{j+m} must be on the grid and empty */
+                        int jp = j + mm;
+                        if (jp < n_eps && 2 * jp + 1 >= n_eps)
+                            sum += wr[mm] * row[jp];
+                    } else {
+                        /* partner e_{j-m} must be on the grid and occupied */
+                        int jp = j - mm;
+                        if (jp >= 0 && 2 * jp + 1 < n_eps)
+                            sum += wr[mm] * row[jp];
+                    }
+                }
+            }
+        }
+        out[k] = -c * sum;
+    }
+}
+
+/* Derivatives of A(p, e) (Eqs. 4-5 with the band above) with respect to the
+ * five band parameters theta = (t, t', t'', mu, gamma), written into
+ * dA[5][N][N][n_eps].  With D = (e - xi)^2 + gamma^2:
+ *   dA/dxi    = |M|^2 (gamma/pi) 2 (e - xi) / D^2
+ *   dA/dgamma = |M|^2 ((e - xi)^2 - gamma^2) / (pi D^2)
+ *   dxi/d(t, t', t'', mu) = (-2(cx+cy), -4 cx cy, -2(c2x+c2y), -1). */
+void lo_spectral_dtheta(double t, double tp, double tpp, double mu,
+                        double gamma, double ff_a, int zones, int npz,
+                        int n_eps, double e_max, double *dA)
+{
+    long N = (long)zones * npz;
+    size_t plane = (size_t)N * N * n_eps;
+    double dp = 2.0 * LO_PI / npz, de = 2.0 * e_max / n_eps;
+#pragma omp parallel for schedule(static)
+    for (long ix = 0; ix < N; ++ix)
+        for (long iy = 0; iy < N; ++iy) {
+            double px = (ix - N / 2) * dp, py = (iy - N / 2) * dp;
+            double xi = lo_band(0, t, tp, tpp, px, py) - mu;
+            double m2 = (ff_a == 0.0) ? 1.0
+                        : exp(-(px * px + py * py) * ff_a * ff_a / 8.0);
+            double dxi[4] = {-2.0 * (cos(px) + cos(py)),
+                             -4.0 * cos(px) * cos(py),
+                             -2.0 * (cos(2.0 * px) + cos(2.0 * py)), -1.0};
+            for (int j = 0; j < n_eps; ++j) {
+                double e = -e_max + (j + 0.5) * de;
+                double d = (e - xi) * (e - xi) + gamma * gamma;
+                double dA_dxi = m2 * (gamma / LO_PI) * 2.0 * (e - xi) / (d * d);
+                double dA_dg = m2 * ((e - xi) * (e - xi) - gamma * gamma) / (LO_PI * d * d);
+                size_t at = ((size_t)ix * N + iy) * n_eps + j;
+                for (int r = 0; r < 4; ++r)
+                    dA[r * plane + at] = dA_dxi * dxi[r];
+                dA[4 * plane + at] = dA_dg;
+            }
+        }
+}
+
+int lo_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

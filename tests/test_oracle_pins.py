@@ -1,0 +1,309 @@
+"""Pins of the FP64 oracle to facts fixed by the paper and by mathematics.
+
+Each test checks the oracle against something other than itself: a closed
+form worked out by hand, an exact identity of Eq. 9, a different algorithm
+(the convolution theorem that the paper's method relies on, Sec. 3), a
+symmetry of the lattice, or a continuum limit (Appendix A, the free-fermion
+form of Sec. 2).  Together they are chosen so that a dropped term, a wrong
+sign or index, a transposed operand or a wrong prefactor fails at least one.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1208_3210_gb300 import workloads as wl
+
+T, TP, TPP = 0.42, -0.10, 0.065
+
+
+def _grid(zones, npz, n_eps, e_max):
+    return dict(zones=zones, npz=npz, n_eps=n_eps, e_max=e_max)
+
+
+def _band(mu, gamma, ff_a=0.0, kind=0):
+    return dict(kind=kind, t=T, tp=TP, tpp=TPP, mu=mu, gamma=gamma, ff_a=ff_a)
+
+
+def _fft_correlation(A, grid, Q, n_omega):
+    """Im chi through the convolution theorem (Sec. 3, the B(r, w) product):
+    zero-padded FP64 numpy FFTs, a conjugate product and an inverse FFT.
+    An algorithm independent of the oracle's direct double sum."""
+    N, _, n_eps = A.shape
+    j = np.arange(n_eps)
+    occ = (2 * j + 1 < n_eps)
+    a = A * occ[None, None, :]
+    b = A * (~occ)[None, None, :]
+    periodic = grid["zones"] == 1
+    P = N if periodic else 2 * N
+    PE = 2 * n_eps
+    fa = np.fft.fftn(a, s=(P, P, PE), axes=(0, 1, 2))
+    fb = np.fft.fftn(b, s=(P, P, PE), axes=(0, 1, 2))
+    corr = np.fft.ifftn(np.conj(fa) * fb).real
+    s = (np.arange(Q) - Q // 2) % P
+    _, _, _, c = oracle.grid_sizes(grid["zones"], grid["npz"], n_eps, grid["e_max"])
+    return -c * corr[np.ix_(s, s, np.arange(n_omega))]
+
+
+# --- the band and the rigid-band chemical potential -------------------------
+
+def test_band_high_symmetry_points():
+    # Substituting Gamma = (0,0), X = (pi,0), M = (pi,pi) into the band by hand.
+    assert oracle.band(0, T, TP, TPP, 0.0, 0.0) == pytest.approx(-4 * T - 4 * TP - 4 * TPP, abs=1e-14)
+    assert oracle.band(0, T, TP, TPP, math.pi, 0.0) == pytest.approx(4 * TP - 4 * TPP, abs=1e-14)
+    assert oracle.band(0, T, TP, TPP, math.pi, math.pi) == pytest.approx(4 * T - 4 * TP - 4 * TPP, abs=1e-14)
+    assert oracle.band(1, 0, 0, 0, 0.3, -0.4) == pytest.approx(0.125, abs=1e-15)
+
+
+def test_mu_half_filling_particle_hole():
+    # Nearest-neighbour band: eps(k + (pi,pi)) = -eps(k), so one electron per
+    # site puts mu at exactly 0 for any broadening (rigid band, Sec. 3).
+    for npz in (16, 32):
+        assert abs(oracle.solve_mu(0, T, 0.0, 0.0, 0.05, npz, 1.0)) < 1e-12
+
+
+def test_filling_measure_free_electrons():
+    # n = 2 Int d^2p/(2pi)^2 Theta(mu - p^2/2) = mu/pi in the gamma -> 0 limit:
+    # pins the 2/npz^2 measure of d^2p/(2 pi)^2.
+    n = oracle.filling(1, 0, 0, 0, 1e-3, 256, 1.0)
+    assert n == pytest.approx(1.0 / math.pi, rel=2e-3)
+
+
+def test_filling_monotone_and_solved():
+    fills = [oracle.filling(0, T, TP, TPP, 0.05, 32, mu) for mu in np.linspace(-2, 2, 41)]
+    assert all(b > a for a, b in zip(fills, fills[1:]))
+    mu = oracle.solve_mu(0, T, TP, TPP, 0.05, 32, 1.15)
+    assert oracle.filling(0, T, TP, TPP, 0.05, 32, mu) == pytest.approx(1.15, abs=1e-12)
+    with pytest.raises(ValueError):
+        oracle.solve_mu(0, T, TP, TPP, 0.05, 32, 2.5)
+
+
+# --- the spectral function (Eqs. 4-5) -------------------------------------------
+
+def test_lorentzian_weight_and_form_factor():
+    # Midpoint sum of A over the window -> |M|^2 [atan((E-xi)/g) + atan((E+xi)/g)]/pi.
+    grid = _grid(2, 8, 4000, 1.0)
+    mu, gamma, ff = 0.05, 0.05, 1.0
+    A = oracle.spectral(_band(mu, gamma, ff), grid)
+    N, dp, de, _ = oracle.grid_sizes(2, 8, 4000, 1.0)
+    for ix, iy in [(8, 8), (3, 11), (15, 0)]:
+        px, py = (ix - N // 2) * dp, (iy - N // 2) * dp
+        xi = oracle.band(0, T, TP, TPP, px, py) - mu
+        m2 = math.exp(-(px * px + py * py) * ff * ff / 8)
+        exact = m2 * (math.atan((1 - xi) / gamma) + math.atan((1 + xi) / gamma)) / math.pi
+        assert A[ix, iy].sum() * de == pytest.approx(exact, rel=1e-5)
+
+
+# --- Eq. 9 itself -----------------------------------------------------------------
+
+@pytest.mark.parametrize("zones,npz,n_eps", [(1, 8, 12), (2, 4, 10), (2, 4, 9), (3, 4, 8)])
+def test_direct_sum_equals_fft_correlation(zones, npz, n_eps):
+    # P1: the direct double sum and the convolution-theorem route agree to
+    # rounding, for the reduced (wrapping) and extended (truncating) zones and
+    # for an odd energy count (e = 0 on the grid goes to the empty part).
+    grid = _grid(zones, npz, n_eps, 1.0)
+    mu = oracle.solve_mu(0, T, TP, TPP, 0.1, npz, 1.15)
+    A = oracle.spectral(_band(mu, 0.1, 0.7), grid)
+    N = zones * npz
+    for Q, n_omega in [(N, n_eps // 2), (N if zones == 1 else 2 * N, n_eps)]:
+        direct = oracle.imchi_full(A, grid, Q, n_omega)
+        ref = _fft_correlation(A, grid, Q, n_omega)
+        scale = np.abs(ref).max()
+        assert scale > 0
+        np.testing.assert_allclose(direct, ref, rtol=0, atol=1e-12 * scale)
+
+
+def test_random_spectral_function_matches_shift_and_multiply():
+    # A with no symmetry (the caller-supplied-A path): explicit array shifts.
+    grid = _grid(2, 3, 7, 1.0)
+    A = wl.random_spectral(grid, seed=3).astype(np.float64)
+    N, n_eps = 6, 7
+    _, _, _, c = oracle.grid_sizes(2, 3, 7, 1.0)
+    Q, n_omega = 2 * N, n_eps
+    direct = oracle.imchi_full(A, grid, Q, n_omega)
+    j = np.arange(n_eps)
+    a = A * (2 * j + 1 < n_eps)
+    b = A * (2 * j + 1 >= n_eps)
+    for l in [(0, 0), (1, 11), (6, 6), (9, 2), (11, 11)]:
+        sx, sy = l[0] - Q // 2, l[1] - Q // 2
+        for m in range(n_omega):
+            acc = 0.0
+            for ix in range(N):
+                for iy in range(N):
+                    if 0 <= ix + sx < N and 0 <= iy + sy < N:
+                        acc += float(np.dot(a[ix, iy, : n_eps - m], b[ix + sx, iy + sy, m:]))
+            assert direct[l[0], l[1], m] == pytest.approx(-c * acc, rel=1e-12, abs=1e-300)
+
+
+@pytest.mark.parametrize("zones,npz,n_eps", [(1, 8, 16), (2, 6, 12), (2, 6, 11)])
+def test_sum_rule(zones, npz, n_eps):
+    # P2: summing Eq. 9 over all q factorises into the energy correlation of
+    # the occupied and empty densities of states:
+    #   sum_q Im chi(q, w_m) = -c sum_j D_a(e_j) D_b(e_{j+m}).
+    grid = _grid(zones, npz, n_eps, 1.5)
+    A = oracle.spectral(_band(0.05, 0.08, 1.0), grid)
+    N, _, _, c = oracle.grid_sizes(zones, npz, n_eps, 1.5)
+    Q = N if zones == 1 else 2 * N
+    chi = oracle.imchi_full(A, grid, Q, n_eps)
+    j = np.arange(n_eps)
+    D = A.sum(axis=(0, 1))
+    Da = D * (2 * j + 1 < n_eps)
+    Db = D * (2 * j + 1 >= n_eps)
+    for m in range(n_eps):
+        rhs = -c * float(np.dot(Da[: n_eps - m], Db[m:]))
+        assert chi[:, :, m].sum() == pytest.approx(rhs, rel=1e-12, abs=1e-15)
+
+
+def test_square_lattice_symmetry():
+    # P3: the band and |M|^2 are invariant under the square group, so is Im chi.
+    # Reduced zone: exact.  Extended zone: exact under x <-> y; reflections hold
+    # up to the unpaired edge row of the even grid (|M|^2 there ~ 1e-3 here).
+    grid = _grid(1, 12, 16, 1.0)
+    mu = oracle.solve_mu(0, T, TP, TPP, 0.05, 12, 1.15)
+    A = oracle.spectral(_band(mu, 0.05), grid)
+    chi = oracle.imchi_full(A, grid, 12, 8)
+    scale = np.abs(chi).max()
+    np.testing.assert_allclose(chi, chi.transpose(1, 0, 2), atol=1e-13 * scale)
+    refl = np.roll(chi[::-1], 1, axis=0)  # l -> -l (mod 12) about l = Q/2
+    np.testing.assert_allclose(chi, refl, atol=1e-13 * scale)
+    grid = _grid(3, 6, 12, 1.5)
+    A = oracle.spectral(_band(mu, 0.05, ff_a=1.0), grid)
+    chi = oracle.imchi_full(A, grid, 18, 6)
+    scale = np.abs(chi).max()
+    np.testing.assert_allclose(chi, chi.transpose(1, 0, 2), atol=1e-13 * scale)
+    inner = chi[1:, 1:]
+    np.testing.assert_allclose(inner, inner[::-1, ::-1], atol=2e-3 * scale)
+
+
+def test_zero_energy_transfer_and_sign():
+    # P4: with the T = 0 split the occupied and empty supports are disjoint, so
+    # Im chi(q, 0) = 0 exactly; every term is >= 0, so Im chi <= 0.
+    grid = _grid(2, 6, 14, 1.0)
+    A = oracle.spectral(_band(0.0, 0.1, 1.0), grid)
+    chi = oracle.imchi_full(A, grid, 12, 14)
+    assert np.all(chi[:, :, 0] == 0.0)
+    assert np.all(chi <= 0.0)
+    assert chi.min() < 0.0
+
+
+def test_two_level_appendix_a():
+    # P5: one occupied momentum p1 and one empty momentum p2 (a caller-supplied
+    # A).  Im chi is nonzero only at q in {0, p2 - p1, p1 - p2}; at q = p2 - p1
+    # it is -(1/(2 pi npz^2)) times the midpoint sum of L(e - xi1) L(e + w - xi2)
+    # over [-w, 0], which converges to the integral of Eq. A3 as de^2.
+    from scipy.integrate import quad
+
+    zones, npz, e_max, gamma = 2, 4, 1.0, 0.05
+    xi1, xi2 = -0.2, 0.25
+    p1, p2 = (2, 5), (6, 3)
+
+    def lor(e, xi):
+        return gamma / (math.pi * ((e - xi) ** 2 + gamma ** 2))
+
+    errs = []
+    for n_eps in (200, 400, 800):
+        grid = _grid(zones, npz, n_eps, e_max)
+        N, dp, de, _ = oracle.grid_sizes(zones, npz, n_eps, e_max)
+        e = -e_max + (np.arange(n_eps) + 0.5) * de
+        A = np.zeros((N, N, n_eps))
+        A[p1] = lor(e, xi1)
+        A[p2] = lor(e, xi2)
+        Q = 2 * N
+        m = n_eps // 4                      # w = e_max / 2
+        w = m * de
+        lq = (p2[0] - p1[0] + Q // 2, p2[1] - p1[1] + Q // 2)
+        val = oracle.imchi_samples(A, grid, Q, [lq[0]], [lq[1]], [m])[0]
+        integral = quad(lambda x: lor(x, xi1) * lor(x + w, xi2), -w, 0.0, points=[xi1, xi2 - w], limit=200)[0]
+        errs.append(abs(val / (-integral / (2 * math.pi * npz * npz)) - 1.0))
+        full = oracle.imchi_full(A, grid, Q, m + 1)
+        nz = {tuple(x) for x in np.argwhere(np.abs(full[:, :, m]) > 0)}
+        assert nz == {(Q // 2, Q // 2), lq, (p1[0] - p2[0] + Q // 2, p1[1] - p2[1] + Q // 2)}
+    assert errs[-1] < 2e-4
+    assert errs[0] / errs[1] > 3.5 and errs[1] / errs[2] > 3.5
+
+
+def test_free_electron_lindhard_limit():
+    # P6: for xi = p^2/2 - mu and gamma -> 0, Eq. 9 in 2D becomes
+    #   Im chi = -2/((2 pi)^3 q) [sqrt((kF^2 - p0^2)_+) - sqrt((kF^2 - (p0+q)^2)_+)],
+    # p0 = w/q - q/2, kF^2 = 2 mu (delta(w - q(p_par + q/2)) fixes p_par, and
+    # the p_perp measure is the difference of two chords).  Pins the absolute
+    # scale de/(2 pi) * 1/npz^2 and the occupation split; the error falls as
+    # gamma shrinks.
+    mu = 1.0
+
+    def closed(q, w):
+        p0 = w / q - q / 2
+        return -(2 / q) * (math.sqrt(max(2 * mu - p0 * p0, 0)) - math.sqrt(max(2 * mu - (p0 + q) ** 2, 0))) \
+            / (2 * math.pi) ** 3
+
+    errs = []
+    for gamma, n_eps in ((0.1, 160), (0.05, 320)):
+        grid = _grid(2, 192, n_eps, 0.8)
+        N, dp, de, _ = oracle.grid_sizes(2, 192, n_eps, 0.8)
+        A = oracle.spectral(dict(kind=1, t=0, tp=0, tpp=0, mu=mu, gamma=gamma, ff_a=0.0), grid)
+        lq, m = int(round(1.0 / dp)), int(round(0.5 / de))
+        val = oracle.imchi_samples(A, grid, N, [N // 2 + lq], [N // 2], [m])[0]
+        errs.append(abs(val / closed(lq * dp, m * de) - 1.0))
+        del A
+    assert errs[1] < 0.015
+    assert errs[0] / errs[1] > 2.5
+
+
+# --- the adjoint --------------------------------------------------------------------
+
+def _small_case(zones=2, npz=4, n_eps=10, seed=1):
+    grid = _grid(zones, npz, n_eps, 1.0)
+    mu = oracle.solve_mu(0, T, TP, TPP, 0.1, npz, 1.15)
+    band = _band(mu, 0.1, 0.8)
+    A = oracle.spectral(band, grid)
+    N = zones * npz
+    Q, n_omega = N, n_eps // 2
+    w = np.random.default_rng(seed).uniform(0, 1, (Q, Q, n_omega))
+    return grid, band, A, Q, w
+
+
+@pytest.mark.parametrize("zones", [1, 2])
+def test_grad_A_central_difference_is_exact(zones):
+    # L is a quadratic form in A, so a central difference in A is exact up to
+    # rounding: (L(A + hE) - L(A - hE)) / 2h = dL/dA . E.
+    grid, band, A, Q, w = _small_case(zones=zones, npz=6 if zones == 1 else 4)
+    g = oracle.grad_A_full(A, grid, Q, w)
+    rng = np.random.default_rng(7)
+    h = 0.05
+    for _ in range(6):
+        ix, iy, j = (int(rng.integers(0, A.shape[0])), int(rng.integers(0, A.shape[1])),
+                     int(rng.integers(0, A.shape[2])))
+        Ap, Am = A.copy(), A.copy()
+        Ap[ix, iy, j] += h
+        Am[ix, iy, j] -= h
+        fd = (oracle.loss(Ap, grid, Q, w) - oracle.loss(Am, grid, Q, w)) / (2 * h)
+        assert g[ix, iy, j] == pytest.approx(fd, rel=1e-9, abs=1e-13)
+
+
+def test_grad_A_bilinear_identity():
+    # L = a^T K b with a, b the occupied and empty parts of A, so
+    # <dL/da, a> = <dL/db, b> = L.
+    grid, band, A, Q, w = _small_case()
+    g = oracle.grad_A_full(A, grid, Q, w)
+    L = oracle.loss(A, grid, Q, w)
+    j = np.arange(A.shape[2])
+    occ = (2 * j + 1 < A.shape[2])
+    assert float(np.sum((g * A)[:, :, occ])) == pytest.approx(L, rel=1e-12)
+    assert float(np.sum((g * A)[:, :, ~occ])) == pytest.approx(L, rel=1e-12)
+
+
+def test_grad_params_central_difference():
+    # dL/d(t, t', t'', mu, gamma) through Eqs. 4-5 against central differences
+    # of the oracle loss with h = 1e-4 eV (truncation ~ h^2/gamma^2 ~ 1e-6).
+    grid, band, A, Q, w = _small_case()
+    g = oracle.grad_params(A, band, grid, Q, w)
+    names = ["t", "tp", "tpp", "mu", "gamma"]
+    h = 1e-4
+    for r, name in enumerate(names):
+        bp, bm = dict(band), dict(band)
+        bp[name] += h
+        bm[name] -= h
+        fd = (oracle.loss(oracle.spectral(bp, grid), grid, Q, w)
+              - oracle.loss(oracle.spectral(bm, grid), grid, Q, w)) / (2 * h)
+        assert g[r] == pytest.approx(fd, rel=2e-5, abs=1e-9 * abs(fd) + 1e-12)
