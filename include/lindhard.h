@@ -1,0 +1,178 @@
+/*
+ * lindhard.h -- C ABI of the GB300 FFT Lindhard susceptibility library.
+ *
+ * Computes, on one GPU, the Lindhard approximation of Wang et al.
+ * ("Lindhard and RPA susceptibility computations in extended momentum space
+ * in electron doped cuprates"):
+ *
+ *   Sec. 2, Eq. 9:  Im chi(q, w) = - Int_{-w}^{0} de/(2 pi) Int d^2p/(2 pi)^2
+ *                                     A(p, e) A(p + q, e + w)
+ *
+ * in two dimensions (Sec. 3: k_z dispersion neglected), with the spectral
+ * function of Sec. 2, Eqs. 4-5,
+ *
+ *   A(p, e) = |M(p)|^2 gamma / (pi [(e - xi_p)^2 + gamma^2]),
+ *
+ * and obtains it as the paper's method does (Sec. 3: the momentum
+ * convolution replaced by products of Fourier transforms): a forward FFT of
+ * the occupied and empty parts of A, their conjugate product, and an inverse
+ * FFT.  The FFT also runs along the energy axis, so the whole (p, e)
+ * correlation is one 3D transform.
+ *
+ * Grid conventions (shared by every entry point):
+ *   lattice constant 1, zone width 2 pi; N = zones * pts_per_zone points per
+ *   axis at p_i = (i - N/2) dp, dp = 2 pi / pts_per_zone, i in [0, N);
+ *   n_eps cell-centred energies e_j = -e_max + (j + 1/2) de, de = 2 e_max / n_eps;
+ *   the T = 0 occupation split (Sec. 3; Appendix A, Eq. A3): A at e_j < 0 is
+ *   occupied, A at e_j >= 0 is empty (with odd n_eps, e = 0 is empty);
+ *   outputs at w_m = m de, m in [0, n_omega), and q_l = (l - Q/2) dp,
+ *   l in [0, Q), Q = q_extent, for both axes;
+ *   measure d^2p/(2 pi)^2 -> 1/pts_per_zone^2 per grid point;
+ *   zones == 1: reduced zone, p + q wraps (the band is periodic);
+ *   zones  > 1: extended zone, A = 0 outside the grid.
+ *
+ * Memory: every pointer argument named "device" must point to memory of the
+ * current CUDA device, owned by the caller, not aliased by any other argument.
+ * Work is enqueued on `stream` (a cudaStream_t; NULL = the legacy default
+ * stream) and is asynchronous: the call returns once the work is enqueued.
+ * Host-side argument errors are returned before anything is enqueued.
+ * Errors found on the device (no chemical potential for the filling, a
+ * bounded wait that timed out) are recorded in the plan and returned by
+ * lindhard_plan_status(), which synchronises the stream.
+ * A plan is not thread-safe: use one plan per stream.
+ */
+#ifndef LINDHARD_H
+#define LINDHARD_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LINDHARD_OK = 0,
+    LINDHARD_EINVAL = 1,        /* an argument is out of range or NULL       */
+    LINDHARD_ENOMEM = 2,        /* device or host allocation failed          */
+    LINDHARD_ECUDA = 3,         /* a CUDA runtime call failed                */
+    LINDHARD_ETIMEOUT = 4,      /* a bounded device wait gave up             */
+    LINDHARD_ENOCONV = 5,       /* no chemical potential for the filling     */
+    LINDHARD_EUNSUPPORTED = 6   /* grid size or precision not built          */
+} lindhard_status;
+
+typedef enum {
+    LINDHARD_FP32 = 0,          /* FP32 SIMT FFT, FP32 intermediates          */
+    LINDHARD_FP64 = 2           /* FP64 everywhere; FFT lengths <= 256 only   */
+} lindhard_precision;
+
+/* One instance's physics, eV, lattice constant 1 (Sec. 2 Eqs. 4-5, Sec. 3). */
+typedef struct {
+    double t, tp, tpp;  /* tight-binding hoppings: xi_p = -2t (cos px + cos py)
+                           - 4t' cos px cos py - 2t'' (cos 2px + cos 2py) - mu */
+    double mu;          /* chemical potential; used as given iff filling is NaN */
+    double filling;     /* electrons per site incl. spin (rigid band, Sec. 3);
+                           mu is then solved in FP64 so that
+                           (2/npz^2) sum_k [1/2 - atan(xi_k/gamma)/pi] = filling
+                           over the first-zone grid                          */
+    double gamma;       /* Lorentzian half-width (Eq. 5), > 0                 */
+    double ff_a;        /* |M(p)|^2 = exp(-|p|^2 ff_a^2 / 8); 0 => |M|^2 = 1   */
+    int band_kind;      /* 0 tight binding; 1 free electrons, xi = |p|^2/2 - mu */
+    int reserved;       /* must be 0                                          */
+} lindhard_band;
+
+/* One instance's grid. */
+typedef struct {
+    int zones;          /* Brillouin zones per axis, >= 1                     */
+    int pts_per_zone;   /* points per zone per axis, even, >= 2               */
+    int n_eps;          /* energies on [-e_max, e_max], >= 2                  */
+    double e_max;       /* energy half-window, eV, > 0                        */
+    int n_omega;        /* energy transfers w_m = m de kept; 0 => n_eps / 2   */
+    int q_extent;       /* lags kept per axis, even; 0 => N; <= 2N (zones > 1),
+                           <= N (zones == 1)                                 */
+    int precision;      /* lindhard_precision                                 */
+    int reserved;       /* must be 0                                          */
+} lindhard_grid;
+
+typedef struct lindhard_plan lindhard_plan;
+
+/* Sizes the library derives for one grid (for callers sizing buffers). */
+typedef struct {
+    long long N;            /* momentum points per axis                       */
+    long long n_eps;        /* energies                                       */
+    long long n_omega;      /* energy transfers kept                          */
+    long long q_extent;     /* lags kept per axis                             */
+    long long fft_p;        /* FFT length along each momentum axis            */
+    long long fft_e;        /* FFT length along the energy axis               */
+    long long out_elems;    /* q_extent^2 * n_omega                           */
+    long long a_elems;      /* N^2 * n_eps (layout of A_in and dA)           */
+    long long hbm_bytes_forward;  /* algorithmic HBM bytes of one forward call */
+    long long kernels_forward;    /* kernel launches of one forward call       */
+} lindhard_sizes;
+
+/* Builds a plan for `batch` instances with the given grids (host array).
+ * Validates the grids, picks FFT lengths (the smallest supported length that
+ * keeps the circular correlation free of wrap-around: >= N + Q/2 per momentum
+ * axis in the extended zone, N in the reduced zone, >= n_eps in energy), and
+ * allocates the device workspace and twiddle tables on the current device.
+ * Instances are computed one after another and share one workspace sized for
+ * the largest.  flags must be 0.  On success *out receives the plan. */
+lindhard_status lindhard_plan_create(const lindhard_grid *grids, int batch,
+                                     unsigned flags, lindhard_plan **out);
+
+/* Sizes for instance `index` of the plan. */
+lindhard_status lindhard_plan_sizes(const lindhard_plan *plan, int index,
+                                    lindhard_sizes *out);
+
+/* Bytes of device workspace the plan owns. */
+lindhard_status lindhard_plan_workspace_bytes(const lindhard_plan *plan,
+                                              size_t *out);
+
+/* Forward: Im chi(q_l, w_m) for every instance (Eq. 9).
+ *   bands : host [batch]; read before return.
+ *   A_in  : device, optional.  NULL => A is generated from bands (Eqs. 4-5).
+ *           Otherwise the batch-concatenated caller A(p_i, e_j), float32,
+ *           layout [N][N][n_eps] per instance (e fastest), and bands are
+ *           ignored (may be NULL).
+ *   out   : device, float32, batch-concatenated, layout [Q][Q][n_omega] per
+ *           instance (w fastest).
+ * Every grid of the plan must use LINDHARD_FP32 (see lindhard_imchi_f64).
+ *   mu_out: device, optional, double [batch]: the chemical potential used.
+ * Returns before the work completes (stream-ordered). */
+lindhard_status lindhard_imchi(lindhard_plan *plan, const lindhard_band *bands,
+                               const float *A_in, float *out, double *mu_out,
+                               void *stream);
+
+/* As lindhard_imchi, for plans whose grids all use LINDHARD_FP64: A_in is
+ * double [N][N][n_eps] per instance and out is double [Q][Q][n_omega]. */
+lindhard_status lindhard_imchi_f64(lindhard_plan *plan, const lindhard_band *bands,
+                                   const double *A_in, double *out, double *mu_out,
+                                   void *stream);
+
+/* Adjoint of lindhard_imchi for L = sum_{l,m} w[l_x][l_y][m] Im chi(q_l, w_m):
+ *   w       : device, float32, layout of `out` above.
+ *   A_in    : as in lindhard_imchi (NULL => generated from bands).
+ *   dA      : device, optional, float32, layout of A_in: dL/dA(p_i, e_j).
+ *   dparams : device, optional, double [batch][5]:
+ *             dL/d(t, t', t'', mu, gamma) through Eqs. 4-5 (A_in must be NULL),
+ *             with mu held as an independent parameter.
+ * Each gradient is itself a correlation (with w) computed by FFT. */
+lindhard_status lindhard_imchi_backward(lindhard_plan *plan,
+                                        const lindhard_band *bands,
+                                        const float *A_in, const float *w,
+                                        float *dA, double *dparams, void *stream);
+
+/* Synchronises `stream` and returns the first device-side error recorded by
+ * the plan since the last call (LINDHARD_OK if none), then clears it. */
+lindhard_status lindhard_plan_status(lindhard_plan *plan, void *stream);
+
+/* Releases the plan's device memory.  Synchronises the device first. */
+void lindhard_plan_destroy(lindhard_plan *plan);
+
+/* Human-readable text of the last host-side error in this thread. */
+const char *lindhard_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LINDHARD_H */

@@ -1,0 +1,255 @@
+// Register-resident Stockham FFT engine for one CTA (sm_103a).
+//
+// A CTA transforms C independent lines of power-of-two length L (16..4096).
+// Each stage is a radix-R butterfly held in registers; between stages the
+// values go through shared memory once (the Stockham exchange), so an L-point
+// transform with S stages touches shared memory 2(S-1) times per point and
+// global memory only in the caller's load (first stage) and store (last
+// stage).  Two thread mappings:
+//   MAP_COL  : lanes run across the C lines first.  Used when the lines are
+//              the strided axis of a row-major array (C neighbouring columns
+//              form contiguous segments), so loads/stores of one warp cover
+//              C*sizeof(complex) contiguous bytes per row.
+//   MAP_LINE : lanes run along a line.  Used when each line is contiguous.
+// Shared memory layouts keep each exchange free of bank conflicts for
+// 8-byte elements: [L][C] for MAP_COL, [C][L + L/16] with one pad element per
+// 16 for MAP_LINE (the stride-R writes of the first exchange then spread over
+// all banks).
+//
+// Conventions: forward = sum_n x_n exp(-2 pi i n k / L), inverse uses the
+// opposite sign, neither is scaled.  The inverse runs the forward radix
+// schedule in reverse order, so that the last forward stage and the first
+// inverse stage have the same radix and the same element-to-thread
+// assignment: a pointwise operation between them (the conjugate product of
+// the correlation) needs no data exchange.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace lh {
+
+template <typename R> struct cpx_of;
+template <> struct cpx_of<float> { using type = float2; };
+template <> struct cpx_of<double> { using type = double2; };
+template <typename R> using cx = typename cpx_of<R>::type;
+
+template <typename C> __device__ __forceinline__ C mk(decltype(C::x) a, decltype(C::x) b) { C r; r.x = a; r.y = b; return r; }
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return mk<C>(a.x + b.x, a.y + b.y); }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { return mk<C>(a.x - b.x, a.y - b.y); }
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) { return mk<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+template <typename C> __device__ __forceinline__ C cmulc(C a, C b) { return mk<C>(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y); } // a * conj(b)
+template <typename C> __device__ __forceinline__ C cconj(C a) { return mk<C>(a.x, -a.y); }
+template <typename C> __device__ __forceinline__ C mul_i(C a) { return mk<C>(-a.y, a.x); }   //  i * a
+template <typename C> __device__ __forceinline__ C mul_mi(C a) { return mk<C>(a.y, -a.x); }  // -i * a
+
+// ---------------------------------------------------------------------------
+// Radix schedules (forward order).  L = prod radix(L, s).
+__host__ __device__ constexpr int fft_nstages(int L) { return L <= 16 ? 1 : (L <= 256 ? 2 : 3); }
+__host__ __device__ constexpr int fft_fwd_radix(int L, int s)
+{
+    return L == 16 ? 16
+         : L == 32 ? (s == 0 ? 8 : 4)
+         : L == 64 ? 8
+         : L == 128 ? (s == 0 ? 16 : 8)
+         : L == 256 ? 16
+         : L == 512 ? 8
+         : L == 1024 ? (s == 0 ? 16 : 8)
+         : L == 2048 ? (s < 2 ? 16 : 8)
+         : 16; /* 4096 */
+}
+__host__ __device__ constexpr int fft_radix(int L, int s, bool inv)
+{
+    return inv ? fft_fwd_radix(L, fft_nstages(L) - 1 - s) : fft_fwd_radix(L, s);
+}
+__host__ __device__ constexpr int fft_ns_before(int L, int s, bool inv)
+{
+    return s == 0 ? 1 : fft_ns_before(L, s - 1, inv) * fft_radix(L, s - 1, inv);
+}
+
+// ---------------------------------------------------------------------------
+// Exact small DFTs in registers.  cos / sin of 2 pi k / 16, k = 0..4.
+__host__ __device__ constexpr double cos16_q(int k)
+{
+    return k == 0 ? 1.0 : k == 1 ? 0.92387953251128675613 : k == 2 ? 0.70710678118654752440
+         : k == 3 ? 0.38268343236508977173 : 0.0;
+}
+__host__ __device__ constexpr double cos16(int k)
+{
+    // cos(2 pi k / 16) for any k >= 0, from the first-quadrant values
+    return (k % 16) <= 4 ? cos16_q(k % 16)
+         : (k % 16) <= 8 ? -cos16_q(8 - k % 16)
+         : (k % 16) <= 12 ? -cos16_q(k % 16 - 8)
+         : cos16_q(16 - k % 16);
+}
+__host__ __device__ constexpr double sin16(int k) { return cos16(k + 12); }  // sin x = cos(x - pi/2)
+
+// x * exp(-+ 2 pi i K / R) with compile-time R | 16 (INV flips the sign).
+template <int R, int K, bool INV, typename C>
+__device__ __forceinline__ C twc(C x)
+{
+    constexpr int k = ((K % R) + R) % R;
+    constexpr int k16 = k * (16 / R);
+    using T = decltype(C::x);
+    if constexpr (k16 == 0) return x;
+    else if constexpr (k16 == 8) return mk<C>(-x.x, -x.y);
+    else if constexpr (k16 == 4) return INV ? mul_i(x) : mul_mi(x);
+    else if constexpr (k16 == 12) return INV ? mul_mi(x) : mul_i(x);
+    else {
+        constexpr T cr = (T)cos16(k16);
+        constexpr T ci = INV ? (T)sin16(k16) : (T)-sin16(k16);
+        return mk<C>(x.x * cr - x.y * ci, x.x * ci + x.y * cr);
+    }
+}
+
+template <int R, bool INV, typename C> struct Dft;
+
+template <bool INV, typename C> struct Dft<1, INV, C> {
+    __device__ __forceinline__ static void run(C *) {}
+};
+template <bool INV, typename C> struct Dft<2, INV, C> {
+    __device__ __forceinline__ static void run(C *v)
+    {
+        C a = v[0], b = v[1];
+        v[0] = cadd(a, b);
+        v[1] = csub(a, b);
+    }
+};
+template <bool INV, typename C> struct Dft<4, INV, C> {
+    __device__ __forceinline__ static void run(C *v)
+    {
+        C t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+        C t2 = cadd(v[1], v[3]), t3 = csub(v[1], v[3]);
+        t3 = INV ? mul_i(t3) : mul_mi(t3);
+        v[0] = cadd(t0, t2);
+        v[2] = csub(t0, t2);
+        v[1] = cadd(t1, t3);
+        v[3] = csub(t1, t3);
+    }
+};
+// Radix 8 and 16: decimation in time into two halves of radix R/2.
+template <int R, bool INV, typename C, int K>
+__device__ __forceinline__ void dit_combine(C *v, const C *e, const C *o)
+{
+    if constexpr (K < R / 2) {
+        C t = twc<R, K, INV>(o[K]);
+        v[K] = cadd(e[K], t);
+        v[K + R / 2] = csub(e[K], t);
+        dit_combine<R, INV, C, K + 1>(v, e, o);
+    }
+}
+template <bool INV, typename C> struct Dft<8, INV, C> {
+    __device__ __forceinline__ static void run(C *v)
+    {
+        C e[4] = {v[0], v[2], v[4], v[6]}, o[4] = {v[1], v[3], v[5], v[7]};
+        Dft<4, INV, C>::run(e);
+        Dft<4, INV, C>::run(o);
+        dit_combine<8, INV, C, 0>(v, e, o);
+    }
+};
+template <bool INV, typename C> struct Dft<16, INV, C> {
+    __device__ __forceinline__ static void run(C *v)
+    {
+        C e[8], o[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) { e[i] = v[2 * i]; o[i] = v[2 * i + 1]; }
+        Dft<8, INV, C>::run(e);
+        Dft<8, INV, C>::run(o);
+        dit_combine<16, INV, C, 0>(v, e, o);
+    }
+};
+
+enum { MAP_COL = 0, MAP_LINE = 1 };
+
+// ---------------------------------------------------------------------------
+// The engine.  VPT = C*L/T values per thread, stored as v[b*R + r] for the
+// b-th butterfly of the current stage.
+template <typename Real, int L, int C, int T, int MAP, bool INV>
+struct Fft {
+    using Cx = cx<Real>;
+    static constexpr int NS = fft_nstages(L);
+    static constexpr int VPT = C * L / T;
+    static constexpr int LP = L + L / 16;                    // padded line (MAP_LINE)
+    static constexpr int SMEM_ELEMS = (MAP == MAP_COL) ? L * C : C * LP;
+    static constexpr int R0 = fft_radix(L, 0, INV);
+    static constexpr int RL = fft_radix(L, NS - 1, INV);
+    static_assert((C * L) % T == 0, "tile must split evenly over threads");
+    static_assert(VPT % R0 == 0 && VPT % RL == 0 && VPT % fft_radix(L, NS > 2 ? 1 : 0, INV) == 0,
+                  "values per thread must be a multiple of every radix");
+    static_assert(MAP == MAP_LINE || T % C == 0, "column map needs T % C == 0");
+
+    __device__ __forceinline__ static int saddr(int col, int n)
+    {
+        return MAP == MAP_COL ? n * C + col : col * LP + n + (n >> 4);
+    }
+    // butterfly index -> (line, j) for a stage of radix Rs
+    template <int Rs>
+    __device__ __forceinline__ static void map(int beta, int &col, int &j)
+    {
+        if constexpr (MAP == MAP_COL) { col = beta % C; j = beta / C; }
+        else { col = beta / (L / Rs); j = beta % (L / Rs); }
+    }
+    // element held in v[b*R0 + r] before the first stage
+    __device__ __forceinline__ static void first_elem(int b, int r, int &col, int &n)
+    {
+        int j;
+        map<R0>(threadIdx.x + b * T, col, j);
+        n = j + r * (L / R0);
+    }
+    // element held in v[b*RL + r] after the last stage
+    __device__ __forceinline__ static void last_elem(int b, int r, int &col, int &n)
+    {
+        int j;
+        map<RL>(threadIdx.x + b * T, col, j);
+        n = j + r * (L / RL);
+    }
+
+    template <int S>
+    __device__ __forceinline__ static void stage_rest(Cx *v, Cx *sm, const Cx *__restrict__ tw, int tw_stride)
+    {
+        if constexpr (S < NS) {
+            constexpr int Rp = fft_radix(L, S - 1, INV);
+            constexpr int Nsp = fft_ns_before(L, S - 1, INV);
+            constexpr int Rs = fft_radix(L, S, INV);
+            constexpr int Ns = Nsp * Rp;
+            // write the previous stage's outputs (Stockham order)
+#pragma unroll
+            for (int b = 0; b < VPT / Rp; ++b) {
+                int col, j;
+                map<Rp>(threadIdx.x + b * T, col, j);
+                int idxD = (j / Nsp) * Nsp * Rp + (j % Nsp);
+#pragma unroll
+                for (int r = 0; r < Rp; ++r) sm[saddr(col, idxD + r * Nsp)] = v[b * Rp + r];
+            }
+            __syncthreads();
+#pragma unroll
+            for (int b = 0; b < VPT / Rs; ++b) {
+                int col, j;
+                map<Rs>(threadIdx.x + b * T, col, j);
+#pragma unroll
+                for (int r = 0; r < Rs; ++r) v[b * Rs + r] = sm[saddr(col, j + r * (L / Rs))];
+                int k = j % Ns;
+                // twiddle exp(-+ 2 pi i k r / (Ns Rs)) from the table of exp(-2 pi i n / (L tw_stride))
+#pragma unroll
+                for (int r = 1; r < Rs; ++r) {
+                    Cx w = __ldg(&tw[(size_t)(k * r * (L / (Ns * Rs))) * tw_stride]);
+                    v[b * Rs + r] = INV ? cmulc(v[b * Rs + r], w) : cmul(v[b * Rs + r], w);
+                }
+                Dft<Rs, INV, Cx>::run(v + b * Rs);
+            }
+            __syncthreads();
+            stage_rest<S + 1>(v, sm, tw, tw_stride);
+        }
+    }
+
+    // Transform the tile in place: v holds the first-stage inputs (see
+    // first_elem) on entry and the outputs (see last_elem) on exit.  sm must
+    // hold SMEM_ELEMS elements; the call ends with a __syncthreads().
+    __device__ __forceinline__ static void run(Cx *v, Cx *sm, const Cx *__restrict__ tw, int tw_stride)
+    {
+#pragma unroll
+        for (int b = 0; b < VPT / R0; ++b) Dft<R0, INV, Cx>::run(v + b * R0);
+        stage_rest<1>(v, sm, tw, tw_stride);
+    }
+};
+
+}  // namespace lh

@@ -1,0 +1,220 @@
+// Forward passes of the correlation (Sec. 3: Fourier transforms of the
+// occupied and empty parts of A).
+//
+//   k_fwd_energy : generates A(p, e) for a tile of momentum points (Eqs. 4-5),
+//                  splits it at e = 0 into the occupied part a and the empty
+//                  part b (T = 0 split, Appendix A Eq. A3), transforms
+//                  z = a + i b along energy, and separates the two transforms
+//                  a^(k) = (Z(k) + conj Z(-k)) / 2, b^(k) = (Z(k) - conj Z(-k)) / 2i
+//                  for the non-redundant frequencies k in [0, PE/2].
+//   k_fwd_y      : transforms both half spectra along p_y, zero-padded from N
+//                  to P points.
+#include "kernels.cuh"
+
+namespace lh {
+
+// ---------------------------------------------------------------------------
+// Energy pass.  One CTA = C momentum points (lines), output U1 layout
+// [N*N lines][2][SP] complex: row 0 = a^, row 1 = b^.
+template <typename Real, int L>
+__global__ void __launch_bounds__(LineCfg<L>::T)
+k_fwd_energy(Geom g, Band band, const AxisTab *__restrict__ axis,
+             const typename EpsEntry<Real>::type *__restrict__ eps,
+             const InstState *__restrict__ st, const Real *__restrict__ A_in,
+             cx<Real> *__restrict__ U1, const cx<Real> *__restrict__ tw, int tw_stride)
+{
+    constexpr int C = LineCfg<L>::C, T = LineCfg<L>::T;
+    using E = Fft<Real, L, C, T, MAP_LINE, false>;
+    using Cx = cx<Real>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Cx *sm = reinterpret_cast<Cx *>(smem_raw);
+    __shared__ Real s_xhi[C], s_xlo[C], s_amp[C];
+
+    const long long nlines = (long long)g.N * g.N;
+    const long long line0 = (long long)blockIdx.x * C;
+
+    if (A_in == nullptr && threadIdx.x < C) {
+        // band energy and |M|^2 of this line's momentum point, in FP64
+        long long line = line0 + threadIdx.x;
+        if (line < nlines) {
+            int ix = (int)(line / g.N), iy = (int)(line % g.N);
+            AxisTab ax = axis[ix], ay = axis[iy];
+            double e0;
+            if (band.band_kind == 1)
+                e0 = 0.5 * (ax.p2 + ay.p2);
+            else
+                e0 = -2.0 * band.t * (ax.c1 + ay.c1) - 4.0 * band.tp * ax.c1 * ay.c1
+                     - 2.0 * band.tpp * (ax.c2 + ay.c2);
+            double xi = e0 - st->mu;
+            double amp = ax.g * ay.g * band.gamma / 3.14159265358979323846;  // |M|^2 gamma / pi
+            s_xhi[threadIdx.x] = (Real)xi;
+            s_xlo[threadIdx.x] = (Real)(xi - (double)(Real)xi);
+            s_amp[threadIdx.x] = (Real)amp;
+        }
+    }
+    __syncthreads();
+
+    const Real g2 = (Real)(band.gamma * band.gamma);
+    Cx v[E::VPT];
+#pragma unroll
+    for (int b = 0; b < E::VPT / E::R0; ++b) {
+#pragma unroll
+        for (int r = 0; r < E::R0; ++r) {
+            int col, n;
+            E::first_elem(b, r, col, n);
+            long long line = line0 + col;
+            Real A = 0;
+            if (n < g.n_eps && line < nlines) {
+                if (A_in != nullptr) {
+                    A = A_in[line * g.n_eps + n];
+                } else {
+                    Real e;
+                    if constexpr (sizeof(Real) == 4) {
+                        float2 ej = eps[n];
+                        e = (ej.x - s_xhi[col]) + (ej.y - s_xlo[col]);
+                    } else {
+                        e = eps[n] - s_xhi[col];
+                    }
+                    Real d = e * e + g2;
+                    if constexpr (sizeof(Real) == 4) A = s_amp[col] * __frcp_rn(d);
+                    else A = s_amp[col] / d;
+                }
+            }
+            // occupied (e_n < 0) -> real part, empty -> imaginary part
+            v[b * E::R0 + r] = (n < g.J0) ? mk<Cx>(A, (Real)0) : mk<Cx>((Real)0, A);
+        }
+    }
+
+    E::run(v, sm, tw, tw_stride);
+
+    // natural-order spectrum to shared memory, then separate a^ and b^
+#pragma unroll
+    for (int b = 0; b < E::VPT / E::RL; ++b) {
+#pragma unroll
+        for (int r = 0; r < E::RL; ++r) {
+            int col, n;
+            E::last_elem(b, r, col, n);
+            sm[E::saddr(col, n)] = v[b * E::RL + r];
+        }
+    }
+    __syncthreads();
+    const Real half = (Real)0.5;
+    for (int idx = threadIdx.x; idx < C * g.H; idx += T) {
+        int col = idx / g.H, k = idx % g.H;
+        long long line = line0 + col;
+        if (line >= nlines) continue;
+        Cx zk = sm[E::saddr(col, k)];
+        Cx zm = sm[E::saddr(col, (L - k) & (L - 1))];
+        // a^ = (Z(k) + conj Z(-k)) / 2 ; b^ = (Z(k) - conj Z(-k)) / 2i
+        Cx ah = mk<Cx>(half * (zk.x + zm.x), half * (zk.y - zm.y));
+        Cx dd = mk<Cx>(zk.x - zm.x, zk.y + zm.y);
+        Cx bh = mk<Cx>(half * dd.y, -half * dd.x);
+        Cx *row = U1 + line * (2LL * g.SP);
+        row[k] = ah;
+        row[g.SP + k] = bh;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// p_y pass.  CTA = (column tile, ix).  U1 [N][N][2 SP] -> U2 [N][P][2 SP].
+template <typename Real, int L>
+__global__ void __launch_bounds__(ColCfg<L>::T)
+k_fwd_y(Geom g, const cx<Real> *__restrict__ U1, cx<Real> *__restrict__ U2,
+        const cx<Real> *__restrict__ tw, int tw_stride)
+{
+    constexpr int C = ColCfg<L>::C, T = ColCfg<L>::T;
+    using E = Fft<Real, L, C, T, MAP_COL, false>;
+    using Cx = cx<Real>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Cx *sm = reinterpret_cast<Cx *>(smem_raw);
+
+    const int W = 2 * g.SP;                       // row width (a^ and b^)
+    const int ix = blockIdx.y;
+    const int c = blockIdx.x * C + (int)(threadIdx.x % C);
+    const bool valid = c < W && (c % g.SP) < g.H;
+    const Cx *src = U1 + (long long)ix * g.N * W + c;
+    Cx *dst = U2 + (long long)ix * g.P * W + c;
+
+    Cx v[E::VPT];
+#pragma unroll
+    for (int b = 0; b < E::VPT / E::R0; ++b)
+#pragma unroll
+        for (int r = 0; r < E::R0; ++r) {
+            int col, n;
+            E::first_elem(b, r, col, n);
+            v[b * E::R0 + r] = (valid && n < g.N) ? src[(long long)n * W] : mk<Cx>((Real)0, (Real)0);
+        }
+    E::run(v, sm, tw, tw_stride);
+    if (valid) {
+#pragma unroll
+        for (int b = 0; b < E::VPT / E::RL; ++b)
+#pragma unroll
+            for (int r = 0; r < E::RL; ++r) {
+                int col, n;
+                E::last_elem(b, r, col, n);
+                dst[(long long)n * W] = v[b * E::RL + r];
+            }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Launchers.
+template <typename Real, int L>
+cudaError_t launch_fwd_energy_t(const Geom &g, const Band &band, const Work<Real> &w,
+                                const Real *A_in, cudaStream_t s)
+{
+    constexpr int C = LineCfg<L>::C, T = LineCfg<L>::T;
+    using E = Fft<Real, L, C, T, MAP_LINE, false>;
+    size_t smem = sizeof(cx<Real>) * E::SMEM_ELEMS;
+    auto k = k_fwd_energy<Real, L>;
+    static const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    long long nlines = (long long)g.N * g.N;
+    unsigned grid = (unsigned)((nlines + C - 1) / C);
+    k<<<grid, T, smem, s>>>(g, band, w.axis, (const typename EpsEntry<Real>::type *)w.eps, w.state, A_in,
+                            (cx<Real> *)w.X, (const cx<Real> *)w.tw, w.tw_len / L);
+    return cudaGetLastError();
+}
+
+template <typename Real, int L>
+cudaError_t launch_fwd_y_t(const Geom &g, const Work<Real> &w, cudaStream_t s)
+{
+    constexpr int C = ColCfg<L>::C, T = ColCfg<L>::T;
+    using E = Fft<Real, L, C, T, MAP_COL, false>;
+    size_t smem = sizeof(cx<Real>) * E::SMEM_ELEMS;
+    auto k = k_fwd_y<Real, L>;
+    static const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((2 * g.SP + C - 1) / C, g.N);
+    k<<<grid, T, smem, s>>>(g, (const cx<Real> *)w.X, (cx<Real> *)w.Y, (const cx<Real> *)w.tw, w.tw_len / L);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fwd_energy(const Geom &g, const Band &band, const Work<float> &w, const float *A_in,
+                              cudaStream_t s)
+{
+#define CALL(L) launch_fwd_energy_t<float, L>(g, band, w, A_in, s)
+    LH_LEN_SWITCH(g.PE, CALL)
+#undef CALL
+}
+cudaError_t launch_fwd_energy(const Geom &g, const Band &band, const Work<double> &w, const double *A_in,
+                              cudaStream_t s)
+{
+#define CALL(L) launch_fwd_energy_t<double, L>(g, band, w, A_in, s)
+    LH_LEN_SWITCH_SMALL(g.PE, CALL)
+#undef CALL
+}
+cudaError_t launch_fwd_y(const Geom &g, const Work<float> &w, cudaStream_t s)
+{
+#define CALL(L) launch_fwd_y_t<float, L>(g, w, s)
+    LH_LEN_SWITCH(g.P, CALL)
+#undef CALL
+}
+cudaError_t launch_fwd_y(const Geom &g, const Work<double> &w, cudaStream_t s)
+{
+#define CALL(L) launch_fwd_y_t<double, L>(g, w, s)
+    LH_LEN_SWITCH_SMALL(g.P, CALL)
+#undef CALL
+}
+
+}  // namespace lh

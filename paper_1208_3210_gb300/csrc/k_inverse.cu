@@ -1,0 +1,161 @@
+// Inverse passes of the correlation.
+//
+//   k_inv_y      : inverse transform along p_y of the product spectrum, keeping
+//                  the Q lags q_y.  U3 [Q][P][SP] -> U4 [Q][Q][SP].
+//   k_inv_energy : inverse real transform along energy.  For fixed (q_x, q_y)
+//                  the product spectrum is Hermitian in the energy frequency
+//                  (the correlation is real), so two output lines share one
+//                  complex inverse FFT: W(k) = X1(k) + i X2(k), with X(k) for
+//                  k > PE/2 rebuilt as conj X(PE - k); Re w = line 1, Im w =
+//                  line 2.  Keeps w_m = m de for m < n_omega and applies the
+//                  prefactor of Eq. 9, -(de / 2 pi)(1 / npz^2), with the FFT
+//                  normalisation 1 / (P P PE).  Writes out [Q][Q][n_omega].
+#include "kernels.cuh"
+
+namespace lh {
+
+template <typename Real, int L>
+__global__ void __launch_bounds__(ColCfg<L>::T)
+k_inv_y(Geom g, const cx<Real> *__restrict__ U3, cx<Real> *__restrict__ U4,
+        const cx<Real> *__restrict__ tw, int tw_stride)
+{
+    constexpr int C = ColCfg<L>::C, T = ColCfg<L>::T;
+    using E = Fft<Real, L, C, T, MAP_COL, true>;
+    using Cx = cx<Real>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Cx *sm = reinterpret_cast<Cx *>(smem_raw);
+
+    const int lx = blockIdx.y;
+    const int c = blockIdx.x * C + (int)(threadIdx.x % C);
+    const bool valid = c < g.H;
+    const Cx *src = U3 + (long long)lx * g.P * g.SP + c;
+    Cx *dst = U4 + (long long)lx * g.Q * g.SP + c;
+
+    Cx v[E::VPT];
+#pragma unroll
+    for (int b = 0; b < E::VPT / E::R0; ++b)
+#pragma unroll
+        for (int r = 0; r < E::R0; ++r) {
+            int col, n;
+            E::first_elem(b, r, col, n);
+            v[b * E::R0 + r] = valid ? src[(long long)n * g.SP] : mk<Cx>((Real)0, (Real)0);
+        }
+    E::run(v, sm, tw, tw_stride);
+    if (valid) {
+#pragma unroll
+        for (int b = 0; b < E::VPT / E::RL; ++b)
+#pragma unroll
+            for (int r = 0; r < E::RL; ++r) {
+                int col, n;
+                E::last_elem(b, r, col, n);
+                int l = lag_index(n, g.P, g.Q);
+                if (l >= 0) dst[(long long)l * g.SP] = v[b * E::RL + r];
+            }
+    }
+}
+
+template <typename Real, typename OutT, int L>
+__global__ void __launch_bounds__(LineCfg<L>::T)
+k_inv_energy(Geom g, const cx<Real> *__restrict__ U4, OutT *__restrict__ out,
+             const cx<Real> *__restrict__ tw, int tw_stride)
+{
+    constexpr int C = LineCfg<L>::C, T = LineCfg<L>::T;
+    using E = Fft<Real, L, C, T, MAP_LINE, true>;
+    using Cx = cx<Real>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Cx *sm = reinterpret_cast<Cx *>(smem_raw);
+
+    const long long npairs = (long long)g.Q * g.Q / 2;
+    const long long f0 = (long long)blockIdx.x * C;
+
+    Cx v[E::VPT];
+#pragma unroll
+    for (int b = 0; b < E::VPT / E::R0; ++b)
+#pragma unroll
+        for (int r = 0; r < E::R0; ++r) {
+            int col, n;
+            E::first_elem(b, r, col, n);
+            long long f = f0 + col;
+            Cx w = mk<Cx>((Real)0, (Real)0);
+            if (f < npairs) {
+                const Cx *row1 = U4 + (2 * f) * g.SP;
+                const Cx *row2 = row1 + g.SP;
+                Cx x1, x2;
+                if (n < g.H) { x1 = row1[n]; x2 = row2[n]; }
+                else { x1 = cconj(row1[L - n]); x2 = cconj(row2[L - n]); }
+                w = mk<Cx>(x1.x - x2.y, x1.y + x2.x);   // X1 + i X2
+            }
+            v[b * E::R0 + r] = w;
+        }
+    E::run(v, sm, tw, tw_stride);
+    const Real sc = (Real)g.scale;
+#pragma unroll
+    for (int b = 0; b < E::VPT / E::RL; ++b)
+#pragma unroll
+        for (int r = 0; r < E::RL; ++r) {
+            int col, n;
+            E::last_elem(b, r, col, n);
+            long long f = f0 + col;
+            if (f < npairs && n < g.n_omega) {
+                Cx w = v[b * E::RL + r];
+                out[(2 * f) * g.n_omega + n] = (OutT)(sc * w.x);
+                out[(2 * f + 1) * g.n_omega + n] = (OutT)(sc * w.y);
+            }
+        }
+}
+
+template <typename Real, int L>
+cudaError_t launch_inv_y_t(const Geom &g, const Work<Real> &w, cudaStream_t s)
+{
+    constexpr int C = ColCfg<L>::C, T = ColCfg<L>::T;
+    using E = Fft<Real, L, C, T, MAP_COL, true>;
+    size_t smem = sizeof(cx<Real>) * E::SMEM_ELEMS;
+    auto k = k_inv_y<Real, L>;
+    static const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((g.H + C - 1) / C, g.Q);
+    k<<<grid, T, smem, s>>>(g, (const cx<Real> *)w.X, (cx<Real> *)w.Y, (const cx<Real> *)w.tw, w.tw_len / L);
+    return cudaGetLastError();
+}
+
+template <typename Real, typename OutT, int L>
+cudaError_t launch_inv_energy_t(const Geom &g, const Work<Real> &w, OutT *out, cudaStream_t s)
+{
+    constexpr int C = LineCfg<L>::C, T = LineCfg<L>::T;
+    using E = Fft<Real, L, C, T, MAP_LINE, true>;
+    size_t smem = sizeof(cx<Real>) * E::SMEM_ELEMS;
+    auto k = k_inv_energy<Real, OutT, L>;
+    static const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    long long npairs = (long long)g.Q * g.Q / 2;
+    unsigned grid = (unsigned)((npairs + C - 1) / C);
+    k<<<grid, T, smem, s>>>(g, (const cx<Real> *)w.Y, out, (const cx<Real> *)w.tw, w.tw_len / L);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_inv_y(const Geom &g, const Work<float> &w, cudaStream_t s)
+{
+#define CALL(L) launch_inv_y_t<float, L>(g, w, s)
+    LH_LEN_SWITCH(g.P, CALL)
+#undef CALL
+}
+cudaError_t launch_inv_y(const Geom &g, const Work<double> &w, cudaStream_t s)
+{
+#define CALL(L) launch_inv_y_t<double, L>(g, w, s)
+    LH_LEN_SWITCH_SMALL(g.P, CALL)
+#undef CALL
+}
+cudaError_t launch_inv_energy(const Geom &g, const Work<float> &w, float *out, cudaStream_t s)
+{
+#define CALL(L) launch_inv_energy_t<float, float, L>(g, w, out, s)
+    LH_LEN_SWITCH(g.PE, CALL)
+#undef CALL
+}
+cudaError_t launch_inv_energy(const Geom &g, const Work<double> &w, double *out, cudaStream_t s)
+{
+#define CALL(L) launch_inv_energy_t<double, double, L>(g, w, out, s)
+    LH_LEN_SWITCH_SMALL(g.PE, CALL)
+#undef CALL
+}
+
+}  // namespace lh

@@ -1,0 +1,96 @@
+// The p_x pass: forward transform of both half spectra along p_x, their
+// conjugate product (the convolution theorem of Sec. 3 turns the momentum and
+// energy correlation of Eq. 9 into a pointwise product of transforms), and the
+// inverse transform along p_x, keeping the Q lags q_x of the output.
+//
+// CTA = (column tile of energy frequencies, k_y).  Reads U2 [N][P][2 SP]
+// (rows i_x < N; rows N..P-1 are the zero padding and are not stored), writes
+// U3 [Q][P][SP].  The forward and inverse transforms share the thread
+// assignment of the last forward / first inverse stage, so the product
+// conj(a^) b^ is formed in registers.
+#include "kernels.cuh"
+
+namespace lh {
+
+template <typename Real, int L>
+__global__ void __launch_bounds__(ColCfg<L>::T)
+k_x_product(Geom g, const cx<Real> *__restrict__ U2, cx<Real> *__restrict__ U3,
+            const cx<Real> *__restrict__ tw, int tw_stride)
+{
+    constexpr int C = ColCfg<L>::C, T = ColCfg<L>::T;
+    using EF = Fft<Real, L, C, T, MAP_COL, false>;
+    using EI = Fft<Real, L, C, T, MAP_COL, true>;
+    static_assert(EF::RL == EI::R0, "last forward radix must equal first inverse radix");
+    using Cx = cx<Real>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Cx *sm = reinterpret_cast<Cx *>(smem_raw);
+
+    const int W = 2 * g.SP;
+    const int ky = blockIdx.y;
+    const int c = blockIdx.x * C + (int)(threadIdx.x % C);
+    const bool valid = c < g.H;
+    const long long rstride = (long long)g.P * W;     // U2 stride between i_x rows
+    const Cx *srcA = U2 + (long long)ky * W + c;      // a^ column
+    const Cx *srcB = srcA + g.SP;                     // b^ column
+    const Cx zero = mk<Cx>((Real)0, (Real)0);
+
+    Cx va[EF::VPT], vb[EF::VPT];
+#pragma unroll
+    for (int b = 0; b < EF::VPT / EF::R0; ++b)
+#pragma unroll
+        for (int r = 0; r < EF::R0; ++r) {
+            int col, n;
+            EF::first_elem(b, r, col, n);
+            bool ld = valid && n < g.N;
+            va[b * EF::R0 + r] = ld ? srcA[(long long)n * rstride] : zero;
+            vb[b * EF::R0 + r] = ld ? srcB[(long long)n * rstride] : zero;
+        }
+    EF::run(va, sm, tw, tw_stride);
+    EF::run(vb, sm, tw, tw_stride);
+    // conj(a^) * b^ : transform of the correlation sum_p a(p) b(p + q)
+#pragma unroll
+    for (int i = 0; i < EF::VPT; ++i) va[i] = cmulc(vb[i], va[i]);
+    EI::run(va, sm, tw, tw_stride);
+    if (valid) {
+        Cx *dst = U3 + (long long)ky * g.SP + c;
+        const long long ostride = (long long)g.P * g.SP;
+#pragma unroll
+        for (int b = 0; b < EI::VPT / EI::RL; ++b)
+#pragma unroll
+            for (int r = 0; r < EI::RL; ++r) {
+                int col, n;
+                EI::last_elem(b, r, col, n);
+                int l = lag_index(n, g.P, g.Q);
+                if (l >= 0) dst[(long long)l * ostride] = va[b * EI::RL + r];
+            }
+    }
+}
+
+template <typename Real, int L>
+cudaError_t launch_x_product_t(const Geom &g, const Work<Real> &w, cudaStream_t s)
+{
+    constexpr int C = ColCfg<L>::C, T = ColCfg<L>::T;
+    using E = Fft<Real, L, C, T, MAP_COL, false>;
+    size_t smem = sizeof(cx<Real>) * E::SMEM_ELEMS;
+    auto k = k_x_product<Real, L>;
+    static const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((g.H + C - 1) / C, g.P);
+    k<<<grid, T, smem, s>>>(g, (const cx<Real> *)w.Y, (cx<Real> *)w.X, (const cx<Real> *)w.tw, w.tw_len / L);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_x_product(const Geom &g, const Work<float> &w, cudaStream_t s)
+{
+#define CALL(L) launch_x_product_t<float, L>(g, w, s)
+    LH_LEN_SWITCH(g.P, CALL)
+#undef CALL
+}
+cudaError_t launch_x_product(const Geom &g, const Work<double> &w, cudaStream_t s)
+{
+#define CALL(L) launch_x_product_t<double, L>(g, w, s)
+    LH_LEN_SWITCH_SMALL(g.P, CALL)
+#undef CALL
+}
+
+}  // namespace lh

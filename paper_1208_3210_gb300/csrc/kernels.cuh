@@ -1,0 +1,73 @@
+// Tile configurations and device helpers shared by the pass kernels.
+#pragma once
+
+#include "fft_engine.cuh"
+#include "lindhard_internal.h"
+
+namespace lh {
+
+// Strided-axis passes (momentum axes): C columns x L rows per CTA, T threads.
+// Values per thread VPT = C L / T is 16 up to L = 256 and 32 above.
+template <int L> struct ColCfg;
+template <> struct ColCfg<16>   { static constexpr int C = 32, T = 32; };
+template <> struct ColCfg<32>   { static constexpr int C = 32, T = 64; };
+template <> struct ColCfg<64>   { static constexpr int C = 16, T = 64; };
+template <> struct ColCfg<128>  { static constexpr int C = 16, T = 128; };
+template <> struct ColCfg<256>  { static constexpr int C = 16, T = 256; };
+template <> struct ColCfg<512>  { static constexpr int C = 16, T = 256; };
+template <> struct ColCfg<1024> { static constexpr int C = 8, T = 256; };
+template <> struct ColCfg<2048> { static constexpr int C = 8, T = 512; };
+template <> struct ColCfg<4096> { static constexpr int C = 4, T = 512; };
+
+// Contiguous-axis passes (energy axis): C lines of length L per CTA.
+template <int L> struct LineCfg;
+template <> struct LineCfg<16>   { static constexpr int C = 64, T = 64; };
+template <> struct LineCfg<32>   { static constexpr int C = 32, T = 64; };
+template <> struct LineCfg<64>   { static constexpr int C = 16, T = 64; };
+template <> struct LineCfg<128>  { static constexpr int C = 16, T = 128; };
+template <> struct LineCfg<256>  { static constexpr int C = 16, T = 256; };
+template <> struct LineCfg<512>  { static constexpr int C = 16, T = 256; };
+template <> struct LineCfg<1024> { static constexpr int C = 8, T = 256; };
+template <> struct LineCfg<2048> { static constexpr int C = 4, T = 256; };
+template <> struct LineCfg<4096> { static constexpr int C = 2, T = 256; };
+
+// Energy table entry: FP32 path stores e_j as an unevaluated sum hi + lo.
+template <typename Real> struct EpsEntry;
+template <> struct EpsEntry<float> { using type = float2; };
+template <> struct EpsEntry<double> { using type = double; };
+
+// Circular index n of an inverse transform of length P -> output lag index
+// l in [0, Q), or -1 when the lag is not kept.
+__device__ __forceinline__ int lag_index(int n, int P, int Q)
+{
+    int s = (n < P / 2) ? n : n - P;
+    int l = s + Q / 2;
+    return (l >= 0 && l < Q) ? l : -1;
+}
+
+}  // namespace lh
+
+// Dispatch on a runtime FFT length to the compiled template instance.
+#define LH_LEN_SWITCH(L_, CALL)                                   \
+    switch (L_) {                                                 \
+    case 16: return CALL(16);                                     \
+    case 32: return CALL(32);                                     \
+    case 64: return CALL(64);                                     \
+    case 128: return CALL(128);                                   \
+    case 256: return CALL(256);                                   \
+    case 512: return CALL(512);                                   \
+    case 1024: return CALL(1024);                                 \
+    case 2048: return CALL(2048);                                 \
+    case 4096: return CALL(4096);                                 \
+    default: return cudaErrorInvalidValue;                        \
+    }
+#define LH_LEN_SWITCH_SMALL(L_, CALL)                             \
+    switch (L_) {                                                 \
+    case 16: return CALL(16);                                     \
+    case 32: return CALL(32);                                     \
+    case 64: return CALL(64);                                     \
+    case 128: return CALL(128);                                   \
+    case 256: return CALL(256);                                   \
+    default: return cudaErrorInvalidValue;                        \
+    }
+

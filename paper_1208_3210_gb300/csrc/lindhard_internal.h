@@ -1,0 +1,68 @@
+// Internal types shared by the kernels and the host plan code.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/lindhard.h"
+
+namespace lh {
+
+// Geometry of one instance, derived on the host from lindhard_grid.
+struct Geom {
+    int N;          // momentum points per axis (zones * npz)
+    int npz;        // points per zone per axis
+    int periodic;   // 1: reduced zone, p + q wraps
+    int n_eps;      // energies
+    int J0;         // e_j < 0 (occupied) iff j < J0 (= n_eps / 2)
+    int P;          // FFT length per momentum axis
+    int PE;         // FFT length along energy
+    int H;          // PE / 2 + 1 non-redundant energy frequencies
+    int SP;         // row stride of half spectra (H rounded up to 8)
+    int Q;          // lags kept per momentum axis
+    int n_omega;    // energy transfers kept
+    int band_kind;  // 0 tight binding, 1 free electrons
+    double e_max, de, dp;
+    double scale;   // -(de / 2 pi) / npz^2 / (P * P * PE): Eq. 9 prefactor and FFT norm
+};
+
+// Per-call physics of one instance, passed by value to the kernels.
+struct Band {
+    double t, tp, tpp, mu, filling, gamma, ff_a;
+    int band_kind;
+    int solve_mu;   // 1: mu from filling
+};
+
+// Device-side per-instance state written by the set-up kernels.
+struct InstState {
+    double mu;          // chemical potential used
+    double last_step;   // size of the last Newton correction (convergence check)
+};
+
+// Status word codes recorded on the device.
+enum { DEV_OK = 0, DEV_ENOCONV = 1, DEV_ETIMEOUT = 2 };
+
+// Per-axis FP64 tables for one instance (N entries each).
+struct AxisTab {
+    double c1;   // cos(p_i)
+    double c2;   // cos(2 p_i)
+    double g;    // exp(-p_i^2 ff_a^2 / 8), so |M(p)|^2 = g(px) g(py)
+    double p2;   // p_i^2
+};
+
+// Workspace of one instance (device pointers into the plan's allocation).
+template <typename Real>
+struct Work {
+    void *X;               // half spectra: forward energy pass output, later x-product output
+    void *Y;               // y pass output, later inverse-y output
+    AxisTab *axis;         // [N]
+    void *eps;             // energy table: float2 (hi, lo) or double, [n_eps]
+    const void *tw;        // twiddles exp(-2 pi i n / TWL): float2 or double2
+    int tw_len;            // TWL
+    InstState *state;      // [1]
+    unsigned *status;      // plan-wide device status word
+    double *mu_acc;        // scratch for the chemical potential solve
+    unsigned *barrier;     // [3] grid barrier: counter, generation, failure flag
+};
+
+}  // namespace lh

@@ -1,0 +1,362 @@
+// Host implementation of the C ABI declared in include/lindhard.h: grid
+// validation, FFT length selection, workspace layout and the launch sequence
+// of one forward call.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+
+namespace lh {
+// launchers (k_*.cu)
+cudaError_t launch_twiddles(int len, float2 *tw32, double2 *tw64, cudaStream_t s);
+cudaError_t launch_tables(const Geom &g, const Band &band, AxisTab *axis, float2 *eps32, double *eps64,
+                          cudaStream_t s);
+size_t mu_acc_doubles(int G);
+int mu_grid_size(int num_sms, int npts);
+cudaError_t launch_solve_mu(const Geom &g, const Band &band, const AxisTab *axis, InstState *st, double *acc,
+                            unsigned *bar, unsigned *status, double *mu_out, int G, cudaStream_t s);
+cudaError_t launch_fwd_energy(const Geom &g, const Band &band, const Work<float> &w, const float *A_in,
+                              cudaStream_t s);
+cudaError_t launch_fwd_energy(const Geom &g, const Band &band, const Work<double> &w, const double *A_in,
+                              cudaStream_t s);
+cudaError_t launch_fwd_y(const Geom &g, const Work<float> &w, cudaStream_t s);
+cudaError_t launch_fwd_y(const Geom &g, const Work<double> &w, cudaStream_t s);
+cudaError_t launch_x_product(const Geom &g, const Work<float> &w, cudaStream_t s);
+cudaError_t launch_x_product(const Geom &g, const Work<double> &w, cudaStream_t s);
+cudaError_t launch_inv_y(const Geom &g, const Work<float> &w, cudaStream_t s);
+cudaError_t launch_inv_y(const Geom &g, const Work<double> &w, cudaStream_t s);
+cudaError_t launch_inv_energy(const Geom &g, const Work<float> &w, float *out, cudaStream_t s);
+cudaError_t launch_inv_energy(const Geom &g, const Work<double> &w, double *out, cudaStream_t s);
+}  // namespace lh
+
+using namespace lh;
+
+static thread_local std::string g_last_error;
+
+static lindhard_status fail(lindhard_status st, const std::string &msg)
+{
+    g_last_error = msg;
+    return st;
+}
+
+static lindhard_status cuda_fail(cudaError_t e, const char *what)
+{
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return LINDHARD_ECUDA;
+}
+
+static const int kMinLen = 16, kMaxLen = 4096, kMaxLen64 = 256;
+
+static bool is_pow2(long long x) { return x > 0 && (x & (x - 1)) == 0; }
+
+static long long next_len(long long x)
+{
+    long long L = kMinLen;
+    while (L < x) L <<= 1;
+    return L;
+}
+
+struct lindhard_plan {
+    int batch = 0;
+    std::vector<Geom> geoms;
+    std::vector<int> precision;
+    int device = 0, num_sms = 0, mu_G = 1;
+    unsigned char *ws = nullptr;
+    size_t ws_bytes = 0;
+    size_t off_X = 0, off_Y = 0, off_axis = 0, off_eps32 = 0, off_eps64 = 0, off_tw32 = 0, off_tw64 = 0,
+           off_state = 0, off_status = 0, off_acc = 0, off_bar = 0;
+    int tw_len = 0;
+};
+
+// Bytes of one complex element for a precision.
+static size_t cx_bytes(int prec) { return prec == LINDHARD_FP64 ? 16 : 8; }
+
+static lindhard_status make_geom(const lindhard_grid &gr, Geom &g, int &prec)
+{
+    if (gr.reserved != 0) return fail(LINDHARD_EINVAL, "grid.reserved must be 0");
+    if (gr.zones < 1) return fail(LINDHARD_EINVAL, "zones must be >= 1");
+    if (gr.pts_per_zone < 2 || gr.pts_per_zone % 2) return fail(LINDHARD_EINVAL, "pts_per_zone must be even and >= 2");
+    if (gr.n_eps < 2) return fail(LINDHARD_EINVAL, "n_eps must be >= 2");
+    if (!(gr.e_max > 0) || !isfinite(gr.e_max)) return fail(LINDHARD_EINVAL, "e_max must be finite and > 0");
+    if (gr.precision != LINDHARD_FP32 && gr.precision != LINDHARD_FP64)
+        return fail(LINDHARD_EUNSUPPORTED, "precision must be LINDHARD_FP32 or LINDHARD_FP64");
+    long long N = (long long)gr.zones * gr.pts_per_zone;
+    if (N > kMaxLen) return fail(LINDHARD_EUNSUPPORTED, "zones * pts_per_zone exceeds 4096");
+    long long n_omega = gr.n_omega ? gr.n_omega : gr.n_eps / 2;
+    if (n_omega < 1 || n_omega > gr.n_eps) return fail(LINDHARD_EINVAL, "n_omega must be in [1, n_eps]");
+    long long Q = gr.q_extent ? gr.q_extent : N;
+    if (Q < 2 || Q % 2) return fail(LINDHARD_EINVAL, "q_extent must be even and >= 2");
+    bool periodic = gr.zones == 1;
+    if (Q > (periodic ? N : 2 * N)) return fail(LINDHARD_EINVAL, "q_extent too large");
+    long long P;
+    if (periodic) {
+        // the reduced zone is one period: the circular correlation is the exact one
+        if (!is_pow2(N) || N < kMinLen)
+            return fail(LINDHARD_EUNSUPPORTED, "reduced zone needs pts_per_zone a power of two >= 16");
+        P = N;
+    } else {
+        // lags |s| <= Q/2 of a length-N sequence: no wrap-around when P >= N + Q/2
+        P = next_len(N + Q / 2);
+    }
+    // energy: with the occupied/empty split every lag m in [0, PE) is alias-free
+    // once PE >= n_eps (the occupied part sits below the empty part).
+    long long PE = next_len(gr.n_eps);
+    long long maxlen = gr.precision == LINDHARD_FP64 ? kMaxLen64 : kMaxLen;
+    if (P > maxlen || PE > maxlen) return fail(LINDHARD_EUNSUPPORTED, "FFT length beyond the compiled range");
+    g.N = (int)N;
+    g.npz = gr.pts_per_zone;
+    g.periodic = periodic;
+    g.n_eps = gr.n_eps;
+    g.J0 = gr.n_eps / 2;
+    g.P = (int)P;
+    g.PE = (int)PE;
+    g.H = (int)(PE / 2 + 1);
+    g.SP = (g.H + 7) / 8 * 8;
+    g.Q = (int)Q;
+    g.n_omega = (int)n_omega;
+    g.band_kind = 0;
+    g.e_max = gr.e_max;
+    g.de = 2.0 * gr.e_max / gr.n_eps;
+    g.dp = 2.0 * M_PI / gr.pts_per_zone;
+    g.scale = -(g.de / (2.0 * M_PI)) / ((double)g.npz * g.npz) / ((double)P * P * PE);
+    prec = gr.precision;
+    return LINDHARD_OK;
+}
+
+static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+extern "C" lindhard_status lindhard_plan_create(const lindhard_grid *grids, int batch, unsigned flags,
+                                                lindhard_plan **out)
+{
+    if (!grids || !out || batch < 1) return fail(LINDHARD_EINVAL, "grids/out must be non-NULL and batch >= 1");
+    if (flags != 0) return fail(LINDHARD_EINVAL, "flags must be 0");
+    *out = nullptr;
+    lindhard_plan *p = new (std::nothrow) lindhard_plan;
+    if (!p) return fail(LINDHARD_ENOMEM, "host allocation failed");
+    p->batch = batch;
+    p->geoms.resize(batch);
+    p->precision.resize(batch);
+    size_t maxX = 0, maxY = 0, maxN = 0, maxE = 0;
+    int maxLen = kMinLen, maxNpts = 1;
+    for (int i = 0; i < batch; ++i) {
+        lindhard_status st = make_geom(grids[i], p->geoms[i], p->precision[i]);
+        if (st != LINDHARD_OK) {
+            delete p;
+            return st;
+        }
+        const Geom &g = p->geoms[i];
+        size_t cb = cx_bytes(p->precision[i]);
+        size_t X = std::max((size_t)g.N * g.N * 2 * g.SP, (size_t)g.Q * g.P * g.SP) * cb;
+        size_t Y = std::max((size_t)g.N * g.P * 2 * g.SP, (size_t)g.Q * g.Q * g.SP) * cb;
+        maxX = std::max(maxX, X);
+        maxY = std::max(maxY, Y);
+        maxN = std::max(maxN, (size_t)g.N);
+        maxE = std::max(maxE, (size_t)g.n_eps);
+        maxLen = std::max(maxLen, std::max(g.P, g.PE));
+        maxNpts = std::max(maxNpts, g.npz * g.npz);
+    }
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
+    if (e != cudaSuccess) {
+        delete p;
+        return cuda_fail(e, "device query");
+    }
+    p->mu_G = mu_grid_size(p->num_sms, maxNpts);
+    p->tw_len = maxLen;
+    size_t o = 0;
+    p->off_X = o; o = align_up(o + maxX);
+    p->off_Y = o; o = align_up(o + maxY);
+    p->off_axis = o; o = align_up(o + maxN * sizeof(AxisTab));
+    p->off_eps32 = o; o = align_up(o + maxE * sizeof(float2));
+    p->off_eps64 = o; o = align_up(o + maxE * sizeof(double));
+    p->off_tw32 = o; o = align_up(o + (size_t)maxLen * sizeof(float2));
+    p->off_tw64 = o; o = align_up(o + (size_t)maxLen * sizeof(double2));
+    p->off_state = o; o = align_up(o + sizeof(InstState));
+    p->off_status = o; o = align_up(o + sizeof(unsigned));
+    p->off_acc = o; o = align_up(o + mu_acc_doubles(p->mu_G) * sizeof(double));
+    p->off_bar = o; o = align_up(o + 3 * sizeof(unsigned));
+    p->ws_bytes = o;
+    e = cudaMalloc(&p->ws, p->ws_bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete p;
+        return fail(LINDHARD_ENOMEM, std::string("workspace cudaMalloc failed: ") + cudaGetErrorString(e));
+    }
+    e = cudaMemset(p->ws + p->off_status, 0, sizeof(unsigned));
+    if (e == cudaSuccess)
+        e = launch_twiddles(p->tw_len, (float2 *)(p->ws + p->off_tw32), (double2 *)(p->ws + p->off_tw64), 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        cudaFree(p->ws);
+        delete p;
+        return cuda_fail(e, "plan set-up");
+    }
+    *out = p;
+    return LINDHARD_OK;
+}
+
+extern "C" lindhard_status lindhard_plan_sizes(const lindhard_plan *p, int index, lindhard_sizes *out)
+{
+    if (!p || !out || index < 0 || index >= p->batch) return fail(LINDHARD_EINVAL, "bad plan/index/out");
+    const Geom &g = p->geoms[index];
+    long long cb = (long long)cx_bytes(p->precision[index]);
+    long long rb = cb / 2;
+    out->N = g.N;
+    out->n_eps = g.n_eps;
+    out->n_omega = g.n_omega;
+    out->q_extent = g.Q;
+    out->fft_p = g.P;
+    out->fft_e = g.PE;
+    out->out_elems = (long long)g.Q * g.Q * g.n_omega;
+    out->a_elems = (long long)g.N * g.N * g.n_eps;
+    // each intermediate written once and read once; only its non-redundant
+    // (valid) entries count
+    long long W1 = (long long)g.N * g.N * 2 * g.H;
+    long long W2 = (long long)g.N * g.P * 2 * g.H;
+    long long W3 = (long long)g.Q * g.P * g.H;
+    long long W4 = (long long)g.Q * g.Q * g.H;
+    out->hbm_bytes_forward = 2 * (W1 + W2 + W3 + W4) * cb + out->out_elems * rb;
+    out->kernels_forward = 7;
+    return LINDHARD_OK;
+}
+
+extern "C" lindhard_status lindhard_plan_workspace_bytes(const lindhard_plan *p, size_t *out)
+{
+    if (!p || !out) return fail(LINDHARD_EINVAL, "bad plan/out");
+    *out = p->ws_bytes;
+    return LINDHARD_OK;
+}
+
+static lindhard_status make_band(const lindhard_band *b, Band &o)
+{
+    if (!b) return fail(LINDHARD_EINVAL, "bands must be non-NULL when A is generated");
+    if (b->reserved != 0) return fail(LINDHARD_EINVAL, "band.reserved must be 0");
+    if (b->band_kind != 0 && b->band_kind != 1) return fail(LINDHARD_EINVAL, "band_kind must be 0 or 1");
+    if (!(b->gamma > 0) || !isfinite(b->gamma)) return fail(LINDHARD_EINVAL, "gamma must be finite and > 0");
+    if (!(b->ff_a >= 0) || !isfinite(b->ff_a)) return fail(LINDHARD_EINVAL, "ff_a must be finite and >= 0");
+    if (!isfinite(b->t) || !isfinite(b->tp) || !isfinite(b->tpp))
+        return fail(LINDHARD_EINVAL, "hoppings must be finite");
+    o.t = b->t;
+    o.tp = b->tp;
+    o.tpp = b->tpp;
+    o.mu = b->mu;
+    o.filling = b->filling;
+    o.gamma = b->gamma;
+    o.ff_a = b->ff_a;
+    o.band_kind = b->band_kind;
+    o.solve_mu = isnan(b->filling) ? 0 : 1;
+    if (o.solve_mu) {
+        if (!(b->filling > 0 && b->filling < 2)) return fail(LINDHARD_EINVAL, "filling must be in (0, 2) or NaN");
+    } else if (!isfinite(b->mu)) {
+        return fail(LINDHARD_EINVAL, "mu must be finite when filling is NaN");
+    }
+    return LINDHARD_OK;
+}
+
+template <typename Real>
+static Work<Real> work_of(lindhard_plan *p)
+{
+    Work<Real> w;
+    w.X = p->ws + p->off_X;
+    w.Y = p->ws + p->off_Y;
+    w.axis = (AxisTab *)(p->ws + p->off_axis);
+    w.eps = sizeof(Real) == 4 ? (void *)(p->ws + p->off_eps32) : (void *)(p->ws + p->off_eps64);
+    w.tw = sizeof(Real) == 4 ? (const void *)(p->ws + p->off_tw32) : (const void *)(p->ws + p->off_tw64);
+    w.tw_len = p->tw_len;
+    w.state = (InstState *)(p->ws + p->off_state);
+    w.status = (unsigned *)(p->ws + p->off_status);
+    w.mu_acc = (double *)(p->ws + p->off_acc);
+    w.barrier = (unsigned *)(p->ws + p->off_bar);
+    return w;
+}
+
+template <typename Real>
+static lindhard_status forward_impl(lindhard_plan *p, const lindhard_band *bands, const Real *A_in, Real *out,
+                                    double *mu_out, void *stream, int want_prec)
+{
+    if (!p || !out) return fail(LINDHARD_EINVAL, "plan and out must be non-NULL");
+    for (int i = 0; i < p->batch; ++i)
+        if (p->precision[i] != want_prec)
+            return fail(LINDHARD_EINVAL, "plan precision does not match the entry point");
+    std::vector<Band> bs(p->batch);
+    if (A_in == nullptr) {
+        for (int i = 0; i < p->batch; ++i) {
+            lindhard_status st = make_band(bands ? bands + i : nullptr, bs[i]);
+            if (st != LINDHARD_OK) return st;
+            if (bs[i].band_kind == 1 && p->geoms[i].periodic)
+                return fail(LINDHARD_EINVAL, "free electrons need zones > 1 (the band is not periodic)");
+        }
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    Work<Real> w = work_of<Real>(p);
+    size_t a_off = 0, o_off = 0;
+    for (int i = 0; i < p->batch; ++i) {
+        const Geom &g = p->geoms[i];
+        cudaError_t e = cudaSuccess;
+        if (A_in == nullptr) {
+            e = launch_tables(g, bs[i], w.axis, sizeof(Real) == 4 ? (float2 *)w.eps : nullptr,
+                              sizeof(Real) == 8 ? (double *)w.eps : nullptr, s);
+            if (e == cudaSuccess)
+                e = launch_solve_mu(g, bs[i], w.axis, w.state, w.mu_acc, w.barrier, w.status,
+                                    mu_out ? mu_out + i : nullptr, p->mu_G, s);
+        }
+        if (e == cudaSuccess) e = launch_fwd_energy(g, bs[i], w, A_in ? A_in + a_off : nullptr, s);
+        if (e == cudaSuccess) e = launch_fwd_y(g, w, s);
+        if (e == cudaSuccess) e = launch_x_product(g, w, s);
+        if (e == cudaSuccess) e = launch_inv_y(g, w, s);
+        if (e == cudaSuccess) e = launch_inv_energy(g, w, out + o_off, s);
+        if (e != cudaSuccess) return cuda_fail(e, "forward launch");
+        a_off += (size_t)g.N * g.N * g.n_eps;
+        o_off += (size_t)g.Q * g.Q * g.n_omega;
+    }
+    return LINDHARD_OK;
+}
+
+extern "C" lindhard_status lindhard_imchi(lindhard_plan *p, const lindhard_band *bands, const float *A_in,
+                                          float *out, double *mu_out, void *stream)
+{
+    return forward_impl<float>(p, bands, A_in, out, mu_out, stream, LINDHARD_FP32);
+}
+
+extern "C" lindhard_status lindhard_imchi_f64(lindhard_plan *p, const lindhard_band *bands, const double *A_in,
+                                              double *out, double *mu_out, void *stream)
+{
+    return forward_impl<double>(p, bands, A_in, out, mu_out, stream, LINDHARD_FP64);
+}
+
+extern "C" lindhard_status lindhard_imchi_backward(lindhard_plan *p, const lindhard_band *bands, const float *A_in,
+                                                   const float *w, float *dA, double *dparams, void *stream)
+{
+    (void)p; (void)bands; (void)A_in; (void)w; (void)dA; (void)dparams; (void)stream;
+    return fail(LINDHARD_EUNSUPPORTED, "backward is not built yet");
+}
+
+extern "C" lindhard_status lindhard_plan_status(lindhard_plan *p, void *stream)
+{
+    if (!p) return fail(LINDHARD_EINVAL, "plan must be non-NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned h = 0;
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaMemcpy(&h, p->ws + p->off_status, sizeof(unsigned), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(p->ws + p->off_status, 0, sizeof(unsigned));
+    if (e != cudaSuccess) return cuda_fail(e, "status read");
+    if (h == DEV_ENOCONV) return fail(LINDHARD_ENOCONV, "no chemical potential for the filling");
+    if (h == DEV_ETIMEOUT) return fail(LINDHARD_ETIMEOUT, "a bounded device wait timed out");
+    return LINDHARD_OK;
+}
+
+extern "C" void lindhard_plan_destroy(lindhard_plan *p)
+{
+    if (!p) return;
+    cudaDeviceSynchronize();
+    cudaFree(p->ws);
+    delete p;
+}
+
+extern "C" const char *lindhard_last_error(void) { return g_last_error.c_str(); }

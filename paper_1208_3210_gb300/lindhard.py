@@ -1,0 +1,183 @@
+"""Python binding of liblindhard.so (include/lindhard.h): argument marshalling only.
+
+Every computation runs in the library's CUDA kernels; this module converts
+Python parameters to the C structs, passes torch tensors' device pointers and
+the current CUDA stream, and maps status codes to exceptions.  There is no
+fallback: if the library cannot be loaded the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from typing import Optional, Sequence
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "liblindhard.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOCONV, EUNSUPPORTED = range(7)
+FP32, FP64 = 0, 2
+_STATUS_NAMES = {OK: "OK", EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", ETIMEOUT: "ETIMEOUT",
+                 ENOCONV: "ENOCONV", EUNSUPPORTED: "EUNSUPPORTED"}
+
+# Exported symbols, in the order include/lindhard.h declares them.
+SYMBOLS = ("lindhard_plan_create", "lindhard_plan_sizes", "lindhard_plan_workspace_bytes", "lindhard_imchi",
+           "lindhard_imchi_f64", "lindhard_imchi_backward", "lindhard_plan_status", "lindhard_plan_destroy",
+           "lindhard_last_error")
+
+
+class LindhardError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Band(ctypes.Structure):
+    _fields_ = [("t", ctypes.c_double), ("tp", ctypes.c_double), ("tpp", ctypes.c_double),
+                ("mu", ctypes.c_double), ("filling", ctypes.c_double), ("gamma", ctypes.c_double),
+                ("ff_a", ctypes.c_double), ("band_kind", ctypes.c_int), ("reserved", ctypes.c_int)]
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("zones", ctypes.c_int), ("pts_per_zone", ctypes.c_int), ("n_eps", ctypes.c_int),
+                ("e_max", ctypes.c_double), ("n_omega", ctypes.c_int), ("q_extent", ctypes.c_int),
+                ("precision", ctypes.c_int), ("reserved", ctypes.c_int)]
+
+
+class Sizes(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_longlong) for n in ("N", "n_eps", "n_omega", "q_extent", "fft_p", "fft_e",
+                                                 "out_elems", "a_elems", "hbm_bytes_forward",
+                                                 "kernels_forward")]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load liblindhard.so (build it first with paper_1208_3210_gb300.build)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: run paper_1208_3210_gb300.build.build() "
+                               "(there is no CPU fallback)")
+        lib = ctypes.CDLL(path)
+        vp = ctypes.c_void_p
+        lib.lindhard_plan_create.argtypes = [ctypes.POINTER(Grid), ctypes.c_int, ctypes.c_uint, ctypes.POINTER(vp)]
+        lib.lindhard_plan_sizes.argtypes = [vp, ctypes.c_int, ctypes.POINTER(Sizes)]
+        lib.lindhard_plan_workspace_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
+        lib.lindhard_imchi.argtypes = [vp, ctypes.POINTER(Band), vp, vp, vp, vp]
+        lib.lindhard_imchi_f64.argtypes = [vp, ctypes.POINTER(Band), vp, vp, vp, vp]
+        lib.lindhard_imchi_backward.argtypes = [vp, ctypes.POINTER(Band), vp, vp, vp, vp, vp]
+        lib.lindhard_plan_status.argtypes = [vp, vp]
+        lib.lindhard_plan_destroy.argtypes = [vp]
+        lib.lindhard_plan_destroy.restype = None
+        lib.lindhard_last_error.restype = ctypes.c_char_p
+        for name in ("lindhard_plan_create", "lindhard_plan_sizes", "lindhard_plan_workspace_bytes",
+                     "lindhard_imchi", "lindhard_imchi_f64", "lindhard_imchi_backward", "lindhard_plan_status"):
+            getattr(lib, name).restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def _check(status: int):
+    if status != OK:
+        raise LindhardError(status, load().lindhard_last_error().decode())
+
+
+def make_grid(zones, npz, n_eps, e_max, n_omega=0, q_extent=0, precision=FP32) -> Grid:
+    return Grid(int(zones), int(npz), int(n_eps), float(e_max), int(n_omega), int(q_extent), int(precision), 0)
+
+
+def make_band(t=0.42, tp=-0.10, tpp=0.065, mu=float("nan"), filling=1.15, gamma=0.05, ff_a=0.0,
+              kind=0, **_ignored) -> Band:
+    return Band(float(t), float(tp), float(tpp), float(mu), float(filling), float(gamma), float(ff_a), int(kind), 0)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Plan:
+    """A lindhard_plan for one or more instance grids (dicts with zones, npz,
+    n_eps, e_max and optional n_omega, q_extent, precision)."""
+
+    def __init__(self, grids: Sequence[dict], precision: int = FP32):
+        lib = load()
+        self.grids = [make_grid(g["zones"], g["npz"], g["n_eps"], g["e_max"], g.get("n_omega", 0),
+                                g.get("q_extent", 0), g.get("precision", precision)) for g in grids]
+        self.batch = len(self.grids)
+        arr = (Grid * self.batch)(*self.grids)
+        h = ctypes.c_void_p()
+        _check(lib.lindhard_plan_create(arr, self.batch, 0, ctypes.byref(h)))
+        self._h = h
+        self.sizes = []
+        for i in range(self.batch):
+            s = Sizes()
+            _check(lib.lindhard_plan_sizes(h, i, ctypes.byref(s)))
+            self.sizes.append(s)
+        self.precision = self.grids[0].precision
+
+    @property
+    def handle(self):
+        return self._h
+
+    def workspace_bytes(self) -> int:
+        n = ctypes.c_size_t()
+        _check(load().lindhard_plan_workspace_bytes(self._h, ctypes.byref(n)))
+        return n.value
+
+    def out_elems(self) -> int:
+        return sum(s.out_elems for s in self.sizes)
+
+    def a_elems(self) -> int:
+        return sum(s.a_elems for s in self.sizes)
+
+    def _bands(self, bands):
+        if bands is None:
+            return None
+        if isinstance(bands, dict):
+            bands = [bands]
+        assert len(bands) == self.batch
+        return (Band * self.batch)(*[b if isinstance(b, Band) else make_band(**b) for b in bands])
+
+    def imchi(self, bands=None, out=None, A_in=None, mu_out=None, stream=None):
+        """Im chi for every instance into `out` (device tensor, concatenated
+        [Q][Q][n_omega] blocks).  Allocates `out` when it is None."""
+        import torch
+        f64 = self.precision == FP64
+        dt = torch.float64 if f64 else torch.float32
+        if out is None:
+            out = torch.empty(self.out_elems(), dtype=dt, device="cuda")
+        assert out.dtype == dt and out.is_cuda and out.is_contiguous() and out.numel() == self.out_elems()
+        if A_in is not None:
+            assert A_in.dtype == dt and A_in.is_cuda and A_in.is_contiguous() and A_in.numel() == self.a_elems()
+        if mu_out is not None:
+            assert mu_out.dtype == torch.float64 and mu_out.is_cuda and mu_out.numel() >= self.batch
+        fn = load().lindhard_imchi_f64 if f64 else load().lindhard_imchi
+        _check(fn(self._h, self._bands(bands), _ptr(A_in), _ptr(out), _ptr(mu_out), _stream(stream)))
+        return out
+
+    def backward(self, w, bands=None, A_in=None, dA=None, dparams=None, stream=None):
+        _check(load().lindhard_imchi_backward(self._h, self._bands(bands), _ptr(A_in), _ptr(w), _ptr(dA),
+                                              _ptr(dparams), _stream(stream)))
+        return dA, dparams
+
+    def status(self, stream=None):
+        _check(load().lindhard_plan_status(self._h, _stream(stream)))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().lindhard_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

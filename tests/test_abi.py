@@ -1,0 +1,79 @@
+"""The C ABI library: it loads, exports every function include/*.h declares,
+and rejects bad arguments on the host before touching the GPU (no GPU needed)."""
+import ctypes
+import glob
+import math
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        for m in re.finditer(r"\b(lindhard_[a-z0-9_]+)\s*\(", src):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1208_3210_gb300 import build, lindhard
+    build.build()
+    return lindhard.load()
+
+
+def test_library_exports_every_declared_function(lib):
+    from paper_1208_3210_gb300 import lindhard
+    declared = _declared_functions()
+    assert declared, "no functions found in include/*.h"
+    assert declared == set(lindhard.SYMBOLS)
+    for name in declared:
+        assert hasattr(lib, name), name
+
+
+def _create(lib, grid):
+    from paper_1208_3210_gb300 import lindhard as lh
+    h = ctypes.c_void_p()
+    st = lib.lindhard_plan_create(ctypes.byref(grid), 1, 0, ctypes.byref(h))
+    return st, h
+
+
+@pytest.mark.parametrize("kw,expect", [
+    (dict(zones=0, npz=32, n_eps=48, e_max=1.0), 1),
+    (dict(zones=1, npz=31, n_eps=48, e_max=1.0), 1),          # odd points per zone
+    (dict(zones=1, npz=24, n_eps=48, e_max=1.0), 6),          # reduced zone not a power of two
+    (dict(zones=1, npz=8, n_eps=48, e_max=1.0), 6),           # below the smallest FFT
+    (dict(zones=2, npz=32, n_eps=1, e_max=1.0), 1),
+    (dict(zones=2, npz=32, n_eps=48, e_max=0.0), 1),
+    (dict(zones=2, npz=32, n_eps=48, e_max=float("nan")), 1),
+    (dict(zones=2, npz=32, n_eps=48, e_max=1.0, n_omega=49), 1),
+    (dict(zones=2, npz=32, n_eps=48, e_max=1.0, q_extent=7), 1),
+    (dict(zones=2, npz=32, n_eps=48, e_max=1.0, q_extent=130), 1),
+    (dict(zones=1, npz=32, n_eps=48, e_max=1.0, q_extent=34), 1),
+    (dict(zones=64, npz=128, n_eps=48, e_max=1.0), 6),        # N beyond the compiled FFT range
+    (dict(zones=2, npz=96, n_eps=48, e_max=1.0, precision=2), 6),  # FP64 only up to length 256
+    (dict(zones=2, npz=32, n_eps=48, e_max=1.0, precision=1), 6),
+])
+def test_plan_rejects_bad_grids_on_host(lib, kw, expect):
+    from paper_1208_3210_gb300 import lindhard as lh
+    g = lh.make_grid(kw["zones"], kw["npz"], kw["n_eps"], kw["e_max"], kw.get("n_omega", 0),
+                     kw.get("q_extent", 0), kw.get("precision", 0))
+    st, h = _create(lib, g)
+    assert st == expect, lib.lindhard_last_error().decode()
+    assert not h.value
+    assert lib.lindhard_last_error().decode()
+
+
+def test_null_arguments(lib):
+    h = ctypes.c_void_p()
+    assert lib.lindhard_plan_create(None, 1, 0, ctypes.byref(h)) == 1
+    assert lib.lindhard_imchi(None, None, None, None, None, None) == 1
+    assert lib.lindhard_plan_status(None, None) == 1
+    lib.lindhard_plan_destroy(None)

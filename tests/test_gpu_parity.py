@@ -1,0 +1,186 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerance: |Im chi_gpu - Im chi_oracle| <= 2e-5 max|Im chi_oracle| per
+instance for the FP32 path (the bar the problem statement sets for FP32),
+1e-12 max|Im chi_oracle| for the FP64 instantiation (which separates algorithm
+errors from rounding).  Small grids are compared element by element over the
+whole output; the full-size workloads on seeded samples of outputs that the
+oracle computes one by one, plus properties that hold at any size.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1208_3210_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+TOL32 = 2e-5
+TOL64 = 1e-12
+
+
+@pytest.fixture(scope="module")
+def lh():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1208_3210_gb300 import build, lindhard
+    build.build()
+    return lindhard
+
+
+def _oracle_band(band, grid):
+    b = dict(band)
+    if math.isnan(b.get("mu", float("nan"))):
+        b["mu"] = oracle.solve_mu(b.get("kind", 0), b["t"], b["tp"], b["tpp"], b["gamma"], grid["npz"],
+                                  b["filling"])
+    return b
+
+
+def _run_gpu(lh, grid, band=None, A=None, precision=0):
+    import torch
+    plan = lh.Plan([grid], precision=precision)
+    mu = torch.full((1,), float("nan"), dtype=torch.float64, device="cuda")
+    dt = torch.float64 if precision == lh.FP64 else torch.float32
+    A_t = None if A is None else torch.from_numpy(np.ascontiguousarray(A)).to(dt).cuda().reshape(-1)
+    out = plan.imchi(None if band is None else [band], A_in=A_t, mu_out=mu)
+    plan.status()
+    s = plan.sizes[0]
+    res = out.cpu().numpy().astype(np.float64).reshape(s.q_extent, s.q_extent, s.n_omega)
+    plan.close()
+    return res, mu.item()
+
+
+def _full_grid(**kw):
+    g = dict(zones=kw["zones"], npz=kw["npz"], n_eps=kw["n_eps"], e_max=kw.get("e_max", 1.0))
+    N = g["zones"] * g["npz"]
+    g["n_omega"] = kw.get("n_omega", g["n_eps"] // 2)
+    g["q_extent"] = kw.get("q_extent", N)
+    return g
+
+
+def _compare(got, ref, tol):
+    scale = np.abs(ref).max()
+    assert scale > 0
+    err = np.abs(got - ref).max() / scale
+    assert err <= tol, f"max err {err:.3e} of max|ref| > {tol:.1e}"
+    return err
+
+
+# --- small grids, every output ---------------------------------------------------
+
+def test_reduced_zone_workload_fp32(lh):
+    w = wl.WORKLOADS["reduced_32x32x48"]
+    got, mu = _run_gpu(lh, w["grid"], w["band"])
+    import os
+    ref = np.load(os.path.join(os.path.dirname(__file__), "golden", "reduced_32x32x48.npz"))
+    assert abs(mu - float(ref["mu"])) < 1e-10
+    _compare(got, ref["imchi"], TOL32)
+
+
+@pytest.mark.parametrize("prec", [0, 2])
+@pytest.mark.parametrize("cfg", [
+    dict(zones=1, npz=16, n_eps=24),                                # reduced zone, ragged energy tail
+    dict(zones=2, npz=24, n_eps=40, e_max=1.2),                     # extended, P = 128 > N + Q/2
+    dict(zones=3, npz=10, n_eps=33, e_max=1.5, q_extent=60, n_omega=33),  # all lags, odd n_eps
+    dict(zones=2, npz=8, n_eps=64, e_max=2.0, q_extent=10, n_omega=7),    # few lags kept
+])
+def test_small_grids_match_oracle(lh, prec, cfg):
+    grid = _full_grid(**cfg)
+    band = wl.band_params(filling=1.1, gamma=0.08, ff_a=0.9)
+    got, mu = _run_gpu(lh, grid, band, precision=prec)
+    b = _oracle_band(band, grid)
+    assert abs(mu - b["mu"]) < 1e-10
+    ref = oracle.imchi_full(oracle.spectral(b, grid), grid, grid["q_extent"], grid["n_omega"])
+    _compare(got, ref, TOL64 if prec == 2 else TOL32)
+
+
+@pytest.mark.parametrize("prec", [0, 2])
+def test_caller_supplied_spectral_function(lh, prec):
+    # A with no lattice symmetry exercises every index of the correlation
+    grid = _full_grid(zones=2, npz=12, n_eps=20, q_extent=48, n_omega=20)
+    A = wl.random_spectral(grid, seed=5)
+    got, _ = _run_gpu(lh, grid, A=A, precision=prec)
+    ref = oracle.imchi_full(A.astype(np.float64), grid, grid["q_extent"], grid["n_omega"])
+    _compare(got, ref, TOL64 if prec == 2 else TOL32)
+
+
+def test_free_electron_band(lh):
+    grid = _full_grid(zones=2, npz=16, n_eps=32, e_max=1.5)
+    band = dict(kind=1, t=0.0, tp=0.0, tpp=0.0, mu=0.6, filling=float("nan"), gamma=0.1, ff_a=0.0)
+    got, mu = _run_gpu(lh, grid, band)
+    assert mu == 0.6
+    ref = oracle.imchi_full(oracle.spectral(band, grid), grid, grid["q_extent"], grid["n_omega"])
+    _compare(got, ref, TOL32)
+
+
+def test_batch_of_mixed_instances(lh):
+    import torch
+    grids = [_full_grid(zones=2, npz=8, n_eps=24), _full_grid(zones=1, npz=16, n_eps=16),
+             _full_grid(zones=4, npz=6, n_eps=20, e_max=2.0)]
+    bands = [wl.band_params(filling=1.05, gamma=0.1, ff_a=1.0), wl.band_params(filling=1.15, gamma=0.05),
+             wl.band_params(filling=1.17, gamma=0.15, ff_a=1.0)]
+    plan = lh.Plan(grids)
+    mu = torch.zeros(3, dtype=torch.float64, device="cuda")
+    out = plan.imchi(bands, mu_out=mu).cpu().numpy().astype(np.float64)
+    plan.status()
+    off = 0
+    for i, (g, b) in enumerate(zip(grids, bands)):
+        s = plan.sizes[i]
+        got = out[off:off + s.out_elems].reshape(s.q_extent, s.q_extent, s.n_omega)
+        off += s.out_elems
+        bo = _oracle_band(b, g)
+        assert abs(mu[i].item() - bo["mu"]) < 1e-10
+        ref = oracle.imchi_full(oracle.spectral(bo, g), g, g["q_extent"], g["n_omega"])
+        _compare(got, ref, TOL32)
+    plan.close()
+
+
+def test_two_calls_identical_and_no_state(lh):
+    # a second call on the same plan gives the same bits (no state carried over)
+    grid = _full_grid(zones=2, npz=16, n_eps=32)
+    band = wl.band_params(filling=1.15, gamma=0.05, ff_a=1.0)
+    plan = lh.Plan([grid])
+    a = plan.imchi([band]).cpu().numpy()
+    b = plan.imchi([band]).cpu().numpy()
+    plan.status()
+    plan.close()
+    assert np.array_equal(a, b)
+
+
+# --- full-size workloads, sampled outputs -------------------------------------------
+
+@pytest.mark.parametrize("name,count", [("extended_256x256x256", 1500), ("large_1024x1024x512", 200)])
+def test_full_size_workload_samples(lh, name, count):
+    import torch
+    w = wl.WORKLOADS[name]
+    grid, band = w["grid"], w["band"]
+    plan = lh.Plan([grid])
+    mu = torch.zeros(1, dtype=torch.float64, device="cuda")
+    out = plan.imchi([band], mu_out=mu)
+    plan.status()
+    s = plan.sizes[0]
+    Q, n_omega = s.q_extent, s.n_omega
+    out = out.reshape(Q, Q, n_omega)
+    # properties over the whole output: Im chi <= 0 and Im chi(q, 0) = 0 (P4)
+    mx = float(out.abs().max())
+    assert float(out.max()) <= TOL32 * mx
+    assert float(out[:, :, 0].abs().max()) <= TOL32 * mx
+    got_all = out.cpu()
+    plan.close()
+    del out
+    torch.cuda.empty_cache()
+    b = _oracle_band(band, grid)
+    assert abs(mu.item() - b["mu"]) < 1e-10
+    lx, ly, m = wl.output_samples(grid, count, seed=1)
+    A = oracle.spectral(b, grid)
+    ref = oracle.imchi_samples(A, grid, Q, lx, ly, m)
+    del A
+    got = got_all.numpy()[lx, ly, m].astype(np.float64)
+    scale = np.abs(ref).max()
+    # the sample includes the block around q = 0 where |Im chi| peaks
+    assert scale >= 0.9 * mx
+    err = np.abs(got - ref).max() / scale
+    assert err <= TOL32, f"{name}: max err {err:.3e}"
