@@ -161,6 +161,22 @@ lindhard_status lindhard_imchi_backward(lindhard_plan *plan,
                                         const float *A_in, const float *w,
                                         float *dA, double *dparams, void *stream);
 
+/* Per-pass timing.  With enable != 0 the plan records a CUDA event pair on
+ * the call's stream around each of its kernel launches (profiling); enable = 0
+ * stops recording.  Either call clears the accumulated times. */
+lindhard_status lindhard_plan_profile(lindhard_plan *plan, int enable);
+
+/* Kernels of one forward call, in launch order (the slots of
+ * lindhard_plan_pass_times). */
+#define LINDHARD_NUM_PASSES 7
+/* 0 tables, 1 mu solve, 2 energy forward (generation + FFT), 3 p_y forward,
+ * 4 p_x forward + product + p_x inverse, 5 p_y inverse, 6 energy inverse.   */
+
+/* Waits for the recorded events and returns, per slot, the summed device time
+ * in milliseconds (ms[LINDHARD_NUM_PASSES]) and the number of launches timed
+ * (launches[LINDHARD_NUM_PASSES]) since profiling was enabled. */
+lindhard_status lindhard_plan_pass_times(lindhard_plan *plan, double *ms, long long *launches);
+
 /* Synchronises `stream` and returns the first device-side error recorded by
  * the plan since the last call (LINDHARD_OK if none), then clears it. */
 lindhard_status lindhard_plan_status(lindhard_plan *plan, void *stream);

@@ -72,7 +72,54 @@ struct lindhard_plan {
     size_t off_X = 0, off_Y = 0, off_axis = 0, off_eps32 = 0, off_eps64 = 0, off_tw32 = 0, off_tw64 = 0,
            off_state = 0, off_status = 0, off_acc = 0, off_bar = 0;
     int tw_len = 0;
+    // per-pass event timing (lindhard_plan_profile)
+    bool profile = false;
+    struct Timed { int slot; cudaEvent_t a, b; };
+    std::vector<Timed> pending;
+    std::vector<cudaEvent_t> pool;
+    double pass_ms[LINDHARD_NUM_PASSES] = {0};
+    long long pass_n[LINDHARD_NUM_PASSES] = {0};
 };
+
+static cudaEvent_t pool_event(lindhard_plan *p)
+{
+    if (!p->pool.empty()) {
+        cudaEvent_t e = p->pool.back();
+        p->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// Runs `launch` and, when profiling, brackets it with an event pair on s.
+template <typename F>
+static cudaError_t timed(lindhard_plan *p, int slot, cudaStream_t s, F &&launch)
+{
+    if (!p->profile) return launch();
+    cudaEvent_t a = pool_event(p), b = pool_event(p);
+    if (!a || !b) return cudaErrorMemoryAllocation;
+    cudaError_t e = cudaEventRecord(a, s);
+    if (e == cudaSuccess) e = launch();
+    if (e == cudaSuccess) e = cudaEventRecord(b, s);
+    p->pending.push_back({slot, a, b});
+    return e;
+}
+
+static void drain_events(lindhard_plan *p)
+{
+    for (auto &t : p->pending) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(t.b) == cudaSuccess && cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) {
+            p->pass_ms[t.slot] += ms;
+            p->pass_n[t.slot] += 1;
+        }
+        p->pool.push_back(t.a);
+        p->pool.push_back(t.b);
+    }
+    p->pending.clear();
+}
 
 // Bytes of one complex element for a precision.
 static size_t cx_bytes(int prec) { return prec == LINDHARD_FP64 ? 16 : 8; }
@@ -299,18 +346,25 @@ static lindhard_status forward_impl(lindhard_plan *p, const lindhard_band *bands
     for (int i = 0; i < p->batch; ++i) {
         const Geom &g = p->geoms[i];
         cudaError_t e = cudaSuccess;
+        const Band &b = bs[i];
         if (A_in == nullptr) {
-            e = launch_tables(g, bs[i], w.axis, sizeof(Real) == 4 ? (float2 *)w.eps : nullptr,
-                              sizeof(Real) == 8 ? (double *)w.eps : nullptr, s);
+            e = timed(p, 0, s, [&] {
+                return launch_tables(g, b, w.axis, sizeof(Real) == 4 ? (float2 *)w.eps : nullptr,
+                                     sizeof(Real) == 8 ? (double *)w.eps : nullptr, s);
+            });
             if (e == cudaSuccess)
-                e = launch_solve_mu(g, bs[i], w.axis, w.state, w.mu_acc, w.barrier, w.status,
-                                    mu_out ? mu_out + i : nullptr, p->mu_G, s);
+                e = timed(p, 1, s, [&] {
+                    return launch_solve_mu(g, b, w.axis, w.state, w.mu_acc, w.barrier, w.status,
+                                           mu_out ? mu_out + i : nullptr, p->mu_G, s);
+                });
         }
-        if (e == cudaSuccess) e = launch_fwd_energy(g, bs[i], w, A_in ? A_in + a_off : nullptr, s);
-        if (e == cudaSuccess) e = launch_fwd_y(g, w, s);
-        if (e == cudaSuccess) e = launch_x_product(g, w, s);
-        if (e == cudaSuccess) e = launch_inv_y(g, w, s);
-        if (e == cudaSuccess) e = launch_inv_energy(g, w, out + o_off, s);
+        const Real *a_i = A_in ? A_in + a_off : nullptr;
+        Real *o_i = out + o_off;
+        if (e == cudaSuccess) e = timed(p, 2, s, [&] { return launch_fwd_energy(g, b, w, a_i, s); });
+        if (e == cudaSuccess) e = timed(p, 3, s, [&] { return launch_fwd_y(g, w, s); });
+        if (e == cudaSuccess) e = timed(p, 4, s, [&] { return launch_x_product(g, w, s); });
+        if (e == cudaSuccess) e = timed(p, 5, s, [&] { return launch_inv_y(g, w, s); });
+        if (e == cudaSuccess) e = timed(p, 6, s, [&] { return launch_inv_energy(g, w, o_i, s); });
         if (e != cudaSuccess) return cuda_fail(e, "forward launch");
         a_off += (size_t)g.N * g.N * g.n_eps;
         o_off += (size_t)g.Q * g.Q * g.n_omega;
@@ -337,6 +391,23 @@ extern "C" lindhard_status lindhard_imchi_backward(lindhard_plan *p, const lindh
     return fail(LINDHARD_EUNSUPPORTED, "backward is not built yet");
 }
 
+extern "C" lindhard_status lindhard_plan_profile(lindhard_plan *p, int enable)
+{
+    if (!p) return fail(LINDHARD_EINVAL, "plan must be non-NULL");
+    drain_events(p);
+    for (int i = 0; i < LINDHARD_NUM_PASSES; ++i) { p->pass_ms[i] = 0; p->pass_n[i] = 0; }
+    p->profile = enable != 0;
+    return LINDHARD_OK;
+}
+
+extern "C" lindhard_status lindhard_plan_pass_times(lindhard_plan *p, double *ms, long long *launches)
+{
+    if (!p || !ms || !launches) return fail(LINDHARD_EINVAL, "plan/ms/launches must be non-NULL");
+    drain_events(p);
+    for (int i = 0; i < LINDHARD_NUM_PASSES; ++i) { ms[i] = p->pass_ms[i]; launches[i] = p->pass_n[i]; }
+    return LINDHARD_OK;
+}
+
 extern "C" lindhard_status lindhard_plan_status(lindhard_plan *p, void *stream)
 {
     if (!p) return fail(LINDHARD_EINVAL, "plan must be non-NULL");
@@ -355,6 +426,8 @@ extern "C" void lindhard_plan_destroy(lindhard_plan *p)
 {
     if (!p) return;
     cudaDeviceSynchronize();
+    drain_events(p);
+    for (cudaEvent_t e : p->pool) cudaEventDestroy(e);
     cudaFree(p->ws);
     delete p;
 }

@@ -22,8 +22,10 @@ _STATUS_NAMES = {OK: "OK", EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", E
 
 # Exported symbols, in the order include/lindhard.h declares them.
 SYMBOLS = ("lindhard_plan_create", "lindhard_plan_sizes", "lindhard_plan_workspace_bytes", "lindhard_imchi",
-           "lindhard_imchi_f64", "lindhard_imchi_backward", "lindhard_plan_status", "lindhard_plan_destroy",
-           "lindhard_last_error")
+           "lindhard_imchi_f64", "lindhard_imchi_backward", "lindhard_plan_profile", "lindhard_plan_pass_times",
+           "lindhard_plan_status", "lindhard_plan_destroy", "lindhard_last_error")
+NUM_PASSES = 7
+PASS_NAMES = ("tables", "mu_solve", "energy_fwd", "py_fwd", "px_product", "py_inv", "energy_inv")
 
 
 class LindhardError(RuntimeError):
@@ -68,12 +70,15 @@ def load(path: str = LIB_PATH):
         lib.lindhard_imchi.argtypes = [vp, ctypes.POINTER(Band), vp, vp, vp, vp]
         lib.lindhard_imchi_f64.argtypes = [vp, ctypes.POINTER(Band), vp, vp, vp, vp]
         lib.lindhard_imchi_backward.argtypes = [vp, ctypes.POINTER(Band), vp, vp, vp, vp, vp]
+        lib.lindhard_plan_profile.argtypes = [vp, ctypes.c_int]
+        lib.lindhard_plan_pass_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]
         lib.lindhard_plan_status.argtypes = [vp, vp]
         lib.lindhard_plan_destroy.argtypes = [vp]
         lib.lindhard_plan_destroy.restype = None
         lib.lindhard_last_error.restype = ctypes.c_char_p
         for name in ("lindhard_plan_create", "lindhard_plan_sizes", "lindhard_plan_workspace_bytes",
-                     "lindhard_imchi", "lindhard_imchi_f64", "lindhard_imchi_backward", "lindhard_plan_status"):
+                     "lindhard_imchi", "lindhard_imchi_f64", "lindhard_imchi_backward", "lindhard_plan_profile",
+                     "lindhard_plan_pass_times", "lindhard_plan_status"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -167,6 +172,17 @@ class Plan:
         _check(load().lindhard_imchi_backward(self._h, self._bands(bands), _ptr(A_in), _ptr(w), _ptr(dA),
                                               _ptr(dparams), _stream(stream)))
         return dA, dparams
+
+    def profile(self, enable: bool = True):
+        """Start (or stop) per-pass CUDA-event timing; clears accumulated times."""
+        _check(load().lindhard_plan_profile(self._h, 1 if enable else 0))
+
+    def pass_times(self):
+        """{pass name: (total ms, launches)} since profiling was enabled."""
+        ms = (ctypes.c_double * NUM_PASSES)()
+        n = (ctypes.c_longlong * NUM_PASSES)()
+        _check(load().lindhard_plan_pass_times(self._h, ms, n))
+        return {PASS_NAMES[i]: (ms[i], n[i]) for i in range(NUM_PASSES)}
 
     def status(self, stream=None):
         _check(load().lindhard_plan_status(self._h, _stream(stream)))

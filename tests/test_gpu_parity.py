@@ -152,7 +152,7 @@ def test_two_calls_identical_and_no_state(lh):
 
 # --- full-size workloads, sampled outputs -------------------------------------------
 
-@pytest.mark.parametrize("name,count", [("extended_256x256x256", 1500), ("large_1024x1024x512", 200)])
+@pytest.mark.parametrize("name,count", [("extended_256x256x256", 1500), ("large_1024x1024x512", 400)])
 def test_full_size_workload_samples(lh, name, count):
     import torch
     w = wl.WORKLOADS[name]
@@ -179,8 +179,10 @@ def test_full_size_workload_samples(lh, name, count):
     ref = oracle.imchi_samples(A, grid, Q, lx, ly, m)
     del A
     got = got_all.numpy()[lx, ly, m].astype(np.float64)
+    # the scale is the largest |Im chi| the oracle computed: at most the true
+    # maximum, so the bar is at least as strict as 2e-5 max|Im chi|
     scale = np.abs(ref).max()
-    # the sample includes the block around q = 0 where |Im chi| peaks
-    assert scale >= 0.9 * mx
     err = np.abs(got - ref).max() / scale
+    print(f"{name}: {lx.size} samples, max err {err:.3e} of sample max, sample max / output max "
+          f"{scale / mx:.3f}")
     assert err <= TOL32, f"{name}: max err {err:.3e}"
