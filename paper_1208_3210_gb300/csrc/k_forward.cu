@@ -99,8 +99,11 @@ k_fwd_energy(Geom g, Band band, const AxisTab *__restrict__ axis,
     }
     __syncthreads();
     const Real half = (Real)0.5;
-    for (int idx = threadIdx.x; idx < C * g.H; idx += T) {
-        int col = idx / g.H, k = idx % g.H;
+    constexpr int H = L / 2 + 1;                 // non-redundant frequencies (= g.H)
+    constexpr int SP = (H + 7) / 8 * 8;          // row stride (= g.SP)
+#pragma unroll 4
+    for (int idx = threadIdx.x; idx < C * H; idx += T) {
+        int col = idx / H, k = idx % H;
         long long line = line0 + col;
         if (line >= nlines) continue;
         Cx zk = sm[E::saddr(col, k)];
@@ -109,16 +112,16 @@ k_fwd_energy(Geom g, Band band, const AxisTab *__restrict__ axis,
         Cx ah = mk<Cx>(half * (zk.x + zm.x), half * (zk.y - zm.y));
         Cx dd = mk<Cx>(zk.x - zm.x, zk.y + zm.y);
         Cx bh = mk<Cx>(half * dd.y, -half * dd.x);
-        Cx *row = U1 + line * (2LL * g.SP);
+        Cx *row = U1 + line * (2LL * SP);
         row[k] = ah;
-        row[g.SP + k] = bh;
+        row[SP + k] = bh;
     }
 }
 
 // ---------------------------------------------------------------------------
 // p_y pass.  CTA = (column tile, ix).  U1 [N][N][2 SP] -> U2 [N][P][2 SP].
 template <typename Real, int L>
-__global__ void __launch_bounds__(ColCfg<L>::T)
+__global__ void __launch_bounds__(ColCfg<L>::T, ColCfg<L>::MINB)
 k_fwd_y(Geom g, const cx<Real> *__restrict__ U1, cx<Real> *__restrict__ U2,
         const cx<Real> *__restrict__ tw, int tw_stride)
 {

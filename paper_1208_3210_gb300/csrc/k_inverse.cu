@@ -15,7 +15,7 @@
 namespace lh {
 
 template <typename Real, int L>
-__global__ void __launch_bounds__(ColCfg<L>::T)
+__global__ void __launch_bounds__(ColCfg<L>::T, ColCfg<L>::MINB)
 k_inv_y(Geom g, const cx<Real> *__restrict__ U3, cx<Real> *__restrict__ U4,
         const cx<Real> *__restrict__ tw, int tw_stride)
 {
@@ -67,6 +67,8 @@ k_inv_energy(Geom g, const cx<Real> *__restrict__ U4, OutT *__restrict__ out,
 
     const long long npairs = (long long)g.Q * g.Q / 2;
     const long long f0 = (long long)blockIdx.x * C;
+    constexpr int H = L / 2 + 1;                 // non-redundant frequencies (= g.H)
+    constexpr int SP = (H + 7) / 8 * 8;          // row stride (= g.SP)
 
     Cx v[E::VPT];
 #pragma unroll
@@ -78,10 +80,10 @@ k_inv_energy(Geom g, const cx<Real> *__restrict__ U4, OutT *__restrict__ out,
             long long f = f0 + col;
             Cx w = mk<Cx>((Real)0, (Real)0);
             if (f < npairs) {
-                const Cx *row1 = U4 + (2 * f) * g.SP;
-                const Cx *row2 = row1 + g.SP;
+                const Cx *row1 = U4 + (2 * f) * SP;
+                const Cx *row2 = row1 + SP;
                 Cx x1, x2;
-                if (n < g.H) { x1 = row1[n]; x2 = row2[n]; }
+                if (n < H) { x1 = row1[n]; x2 = row2[n]; }
                 else { x1 = cconj(row1[L - n]); x2 = cconj(row2[L - n]); }
                 w = mk<Cx>(x1.x - x2.y, x1.y + x2.x);   // X1 + i X2
             }

@@ -13,7 +13,7 @@
 namespace lh {
 
 template <typename Real, int L>
-__global__ void __launch_bounds__(ColCfg<L>::T)
+__global__ void __launch_bounds__(ColCfg<L>::T, ColCfg<L>::MINB_X)
 k_x_product(Geom g, const cx<Real> *__restrict__ U2, cx<Real> *__restrict__ U3,
             const cx<Real> *__restrict__ tw, int tw_stride)
 {

@@ -59,6 +59,7 @@ constexpr int MU_SECT = 64;
 constexpr int MU_THREADS = 256;
 constexpr int MU_FP32_PASSES = 3;
 constexpr int MU_NEWTON = 3;
+constexpr int MU_MAXP = 8;   // first-zone points held per thread
 
 // Layout of acc: [MU_FP32_PASSES][G][MU_SECT] then [MU_NEWTON][G][2] doubles.
 size_t mu_acc_doubles(int G) { return (size_t)G * (MU_FP32_PASSES * MU_SECT + MU_NEWTON * 2); }
@@ -98,7 +99,7 @@ __device__ bool grid_sync(unsigned *bar, unsigned *status)
                         s_fail = 1;
                         break;
                     }
-                    __nanosleep(128);
+                    __nanosleep(32);
                 }
             }
             __threadfence();
@@ -127,36 +128,42 @@ k_solve_mu(Geom g, Band band, const AxisTab *__restrict__ axis, InstState *st, d
     const double B = (band.band_kind == 1) ? 9.869604401089358
                      : 4.0 * (fabs(band.t) + fabs(band.tp) + fabs(band.tpp));
     double lo = -B - 3.0, hi = B + 3.0;
-    __shared__ float s_red[MU_THREADS];
-    __shared__ double s_red2[2][MU_THREADS / 32];
+    constexpr int NW = MU_THREADS / 32;
+    __shared__ float s_sect[NW][MU_SECT];
+    __shared__ double s_red2[2][NW];
+    __shared__ int s_first;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+    // this thread's first-zone points (usually at most one): band energies once, in FP64
+    constexpr int MAXP = MU_MAXP;
+    double e0[MAXP];
+    int np = 0;
+    for (int k = blockIdx.x * MU_THREADS + threadIdx.x; k < npts && np < MAXP; k += G * MU_THREADS) {
+        int ix = base + k / g.npz, iy = base + k % g.npz;
+        e0[np++] = band_e0(band, axis[ix], axis[iy]);
+    }
+    // (the launch uses G >= npts / (MU_MAXP * MU_THREADS), so every point is covered)
 
     // --- FP32 multisection ---------------------------------------------------
-    const int sect = threadIdx.x % MU_SECT;             // this thread's candidate
-    const int grp = threadIdx.x / MU_SECT;              // point subset in the CTA
-    const int ngrp = MU_THREADS / MU_SECT;
     const float gam = (float)band.gamma;
     const float inv_pi = 0.318309886183790672f;
     for (int pass = 0; pass < MU_FP32_PASSES; ++pass) {
-        double h = (hi - lo) / (MU_SECT - 1);
-        float mu_c = (float)(lo + sect * h);
-        float sum = 0.f;
-        for (int k = blockIdx.x * ngrp + grp; k < npts; k += G * ngrp) {
-            int ix = base + k / g.npz, iy = base + k % g.npz;
-            float xi = (float)band_e0(band, axis[ix], axis[iy]) - mu_c;
-            sum += 0.5f - atanf(xi / gam) * inv_pi;
+        const double h = (hi - lo) / (MU_SECT - 1);
+        for (int c = 0; c < MU_SECT; ++c) {
+            float mu_c = (float)(lo + c * h), sum = 0.f;
+            for (int q = 0; q < np; ++q) sum += 0.5f - atanf(((float)e0[q] - mu_c) / gam) * inv_pi;
+            for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
+            if (lane == 0) s_sect[warp][c] = sum;
         }
-        s_red[threadIdx.x] = sum;
         __syncthreads();
         if (threadIdx.x < MU_SECT) {
             double t = 0;
-            for (int q = 0; q < ngrp; ++q) t += s_red[q * MU_SECT + threadIdx.x];
+            for (int w = 0; w < NW; ++w) t += s_sect[w][threadIdx.x];
             acc[((size_t)pass * G + blockIdx.x) * MU_SECT + threadIdx.x] = t;
         }
+        if (threadIdx.x == 0) s_first = MU_SECT;
         if (!grid_sync(bar, status)) return;
         // every CTA: total occupation at each candidate, first candidate >= target
-        __shared__ int s_first;
-        if (threadIdx.x == 0) s_first = MU_SECT;
-        __syncthreads();
         if (threadIdx.x < MU_SECT) {
             double t = 0;
             for (int q = 0; q < G; ++q) t += __ldcg(&acc[((size_t)pass * G + q) * MU_SECT + threadIdx.x]);
@@ -182,9 +189,8 @@ k_solve_mu(Geom g, Band band, const AxisTab *__restrict__ axis, InstState *st, d
     const double gd = band.gamma, ipi = 0.31830988618379067154;
     for (int it = 0; it < MU_NEWTON; ++it) {
         double f = 0.0, fp = 0.0;
-        for (int k = blockIdx.x * MU_THREADS + threadIdx.x; k < npts; k += G * MU_THREADS) {
-            int ix = base + k / g.npz, iy = base + k % g.npz;
-            double xi = band_e0(band, axis[ix], axis[iy]) - mu;
+        for (int q = 0; q < np; ++q) {
+            double xi = e0[q] - mu;
             f += 0.5 - atan(xi / gd) * ipi;
             fp += gd * ipi / (xi * xi + gd * gd);
         }
@@ -192,12 +198,12 @@ k_solve_mu(Geom g, Band band, const AxisTab *__restrict__ axis, InstState *st, d
             f += __shfl_down_sync(0xffffffffu, f, o);
             fp += __shfl_down_sync(0xffffffffu, fp, o);
         }
-        if ((threadIdx.x & 31) == 0) { s_red2[0][threadIdx.x >> 5] = f; s_red2[1][threadIdx.x >> 5] = fp; }
+        if (lane == 0) { s_red2[0][warp] = f; s_red2[1][warp] = fp; }
         __syncthreads();
         double *slot = acc + (size_t)G * MU_FP32_PASSES * MU_SECT + ((size_t)it * G + blockIdx.x) * 2;
         if (threadIdx.x == 0) {
             double a = 0, b = 0;
-            for (int w = 0; w < MU_THREADS / 32; ++w) { a += s_red2[0][w]; b += s_red2[1][w]; }
+            for (int w = 0; w < NW; ++w) { a += s_red2[0][w]; b += s_red2[1][w]; }
             slot[0] = a;
             slot[1] = b;
         }
@@ -233,9 +239,12 @@ cudaError_t launch_tables(const Geom &g, const Band &band, AxisTab *axis, float2
 // CTAs of the cooperative chemical-potential launch: at most one per SM.
 int mu_grid_size(int num_sms, int npts)
 {
+    // one point per thread where the SMs allow, at most MU_MAXP
     int want = (npts + MU_THREADS - 1) / MU_THREADS;
-    if (want < 1) want = 1;
-    return want < num_sms ? want : num_sms;
+    int need = (npts + MU_MAXP * MU_THREADS - 1) / (MU_MAXP * MU_THREADS);
+    if (want > num_sms) want = num_sms;
+    if (want < need) want = need;
+    return want < 1 ? 1 : want;
 }
 
 cudaError_t launch_solve_mu(const Geom &g, const Band &band, const AxisTab *axis, InstState *st, double *acc,

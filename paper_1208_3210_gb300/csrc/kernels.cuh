@@ -6,18 +6,20 @@
 
 namespace lh {
 
-// Strided-axis passes (momentum axes): C columns x L rows per CTA, T threads.
-// Values per thread VPT = C L / T is 16 up to L = 256 and 32 above.
+// Strided-axis passes (momentum axes): C columns x L rows per CTA, T threads,
+// VPT = C L / T = 16 values per thread (32 registers of data per transform),
+// so several CTAs share an SM and hide each other's barrier and load latency.
+// MINB is the CTAs per SM the register budget aims at.
 template <int L> struct ColCfg;
-template <> struct ColCfg<16>   { static constexpr int C = 32, T = 32; };
-template <> struct ColCfg<32>   { static constexpr int C = 32, T = 64; };
-template <> struct ColCfg<64>   { static constexpr int C = 16, T = 64; };
-template <> struct ColCfg<128>  { static constexpr int C = 16, T = 128; };
-template <> struct ColCfg<256>  { static constexpr int C = 16, T = 256; };
-template <> struct ColCfg<512>  { static constexpr int C = 16, T = 256; };
-template <> struct ColCfg<1024> { static constexpr int C = 8, T = 256; };
-template <> struct ColCfg<2048> { static constexpr int C = 8, T = 512; };
-template <> struct ColCfg<4096> { static constexpr int C = 4, T = 512; };
+template <> struct ColCfg<16>   { static constexpr int C = 32, T = 32, MINB = 4, MINB_X = 4; };
+template <> struct ColCfg<32>   { static constexpr int C = 32, T = 64, MINB = 4, MINB_X = 4; };
+template <> struct ColCfg<64>   { static constexpr int C = 16, T = 64, MINB = 4, MINB_X = 4; };
+template <> struct ColCfg<128>  { static constexpr int C = 16, T = 128, MINB = 4, MINB_X = 3; };
+template <> struct ColCfg<256>  { static constexpr int C = 16, T = 256, MINB = 3, MINB_X = 2; };
+template <> struct ColCfg<512>  { static constexpr int C = 8, T = 256, MINB = 3, MINB_X = 2; };
+template <> struct ColCfg<1024> { static constexpr int C = 8, T = 512, MINB = 2, MINB_X = 1; };
+template <> struct ColCfg<2048> { static constexpr int C = 4, T = 512, MINB = 2, MINB_X = 1; };
+template <> struct ColCfg<4096> { static constexpr int C = 4, T = 1024, MINB = 1, MINB_X = 1; };
 
 // Contiguous-axis passes (energy axis): C lines of length L per CTA.
 template <int L> struct LineCfg;
@@ -26,10 +28,10 @@ template <> struct LineCfg<32>   { static constexpr int C = 32, T = 64; };
 template <> struct LineCfg<64>   { static constexpr int C = 16, T = 64; };
 template <> struct LineCfg<128>  { static constexpr int C = 16, T = 128; };
 template <> struct LineCfg<256>  { static constexpr int C = 16, T = 256; };
-template <> struct LineCfg<512>  { static constexpr int C = 16, T = 256; };
-template <> struct LineCfg<1024> { static constexpr int C = 8, T = 256; };
-template <> struct LineCfg<2048> { static constexpr int C = 4, T = 256; };
-template <> struct LineCfg<4096> { static constexpr int C = 2, T = 256; };
+template <> struct LineCfg<512>  { static constexpr int C = 8, T = 256; };
+template <> struct LineCfg<1024> { static constexpr int C = 8, T = 512; };
+template <> struct LineCfg<2048> { static constexpr int C = 4, T = 512; };
+template <> struct LineCfg<4096> { static constexpr int C = 4, T = 1024; };
 
 // Energy table entry: FP32 path stores e_j as an unevaluated sum hi + lo.
 template <typename Real> struct EpsEntry;

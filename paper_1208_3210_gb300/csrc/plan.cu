@@ -338,6 +338,8 @@ static lindhard_status forward_impl(lindhard_plan *p, const lindhard_band *bands
             if (st != LINDHARD_OK) return st;
             if (bs[i].band_kind == 1 && p->geoms[i].periodic)
                 return fail(LINDHARD_EINVAL, "free electrons need zones > 1 (the band is not periodic)");
+            if (bs[i].solve_mu && p->geoms[i].npz > 512)
+                return fail(LINDHARD_EUNSUPPORTED, "the filling solve supports pts_per_zone <= 512; pass mu instead");
         }
     }
     cudaStream_t s = (cudaStream_t)stream;
