@@ -109,13 +109,19 @@ typedef struct {
     long long kernels_forward;    /* kernel launches of one forward call       */
 } lindhard_sizes;
 
+/* Plan flag: also allocate the buffers of lindhard_imchi_backward (one more
+ * intermediate of Q x P x (PE/2 + 1) complex values and the per-CTA gradient
+ * partial sums). */
+#define LINDHARD_PLAN_BACKWARD 1u
+
 /* Builds a plan for `batch` instances with the given grids (host array).
  * Validates the grids, picks FFT lengths (the smallest supported length that
  * keeps the circular correlation free of wrap-around: >= N + Q/2 per momentum
  * axis in the extended zone, N in the reduced zone, >= n_eps in energy), and
  * allocates the device workspace and twiddle tables on the current device.
  * Instances are computed one after another and share one workspace sized for
- * the largest.  flags must be 0.  On success *out receives the plan. */
+ * the largest.  flags: 0 or LINDHARD_PLAN_BACKWARD.  On success *out receives
+ * the plan. */
 lindhard_status lindhard_plan_create(const lindhard_grid *grids, int batch,
                                      unsigned flags, lindhard_plan **out);
 
@@ -148,14 +154,21 @@ lindhard_status lindhard_imchi_f64(lindhard_plan *plan, const lindhard_band *ban
                                    const double *A_in, double *out, double *mu_out,
                                    void *stream);
 
-/* Adjoint of lindhard_imchi for L = sum_{l,m} w[l_x][l_y][m] Im chi(q_l, w_m):
- *   w       : device, float32, layout of `out` above.
- *   A_in    : as in lindhard_imchi (NULL => generated from bands).
+/* Adjoint of lindhard_imchi for L = sum_{l,m} w[l_x][l_y][m] Im chi(q_l, w_m).
+ * Eq. 9 is bilinear in the occupied part a and empty part b of A, so
+ *   dL/dA(p, e_j) = -c sum_{s,m} w(s, m) b(p + s, e_{j+m})   (e_j < 0)
+ *   dL/dA(p, e_j) = -c sum_{s,m} w(s, m) a(p - s, e_{j-m})   (e_j >= 0)
+ * with c = de/(2 pi)/npz^2; both are correlations with w and are computed by
+ * FFT like the forward call.  The plan must be created with
+ * LINDHARD_PLAN_BACKWARD and FP32 grids.
+ *   w       : device, float32, layout of `out` of lindhard_imchi.
+ *   A_in    : as in lindhard_imchi (NULL => A generated from bands).
  *   dA      : device, optional, float32, layout of A_in: dL/dA(p_i, e_j).
  *   dparams : device, optional, double [batch][5]:
- *             dL/d(t, t', t'', mu, gamma) through Eqs. 4-5 (A_in must be NULL),
- *             with mu held as an independent parameter.
- * Each gradient is itself a correlation (with w) computed by FFT. */
+ *             dL/d(t, t', t'', mu, gamma) by the chain rule through Eqs. 4-5
+ *             (A_in must be NULL), mu held fixed (a partial derivative even
+ *             when mu was solved from the filling).
+ * At least one of dA and dparams must be non-NULL. */
 lindhard_status lindhard_imchi_backward(lindhard_plan *plan,
                                         const lindhard_band *bands,
                                         const float *A_in, const float *w,

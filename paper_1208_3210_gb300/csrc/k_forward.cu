@@ -136,7 +136,7 @@ k_fwd_y(Geom g, const cx<Real> *__restrict__ U1, cx<Real> *__restrict__ U2,
     const int c = blockIdx.x * C + (int)(threadIdx.x % C);
     const bool valid = c < W && (c % g.SP) < g.H;
     const Cx *src = U1 + (long long)ix * g.N * W + c;
-    Cx *dst = U2 + (long long)ix * g.P * W + c;
+    Cx *dst = U2 + (long long)ix * g.xs2 + c;
 
     Cx v[E::VPT];
 #pragma unroll

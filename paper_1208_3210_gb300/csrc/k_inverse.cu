@@ -28,7 +28,7 @@ k_inv_y(Geom g, const cx<Real> *__restrict__ U3, cx<Real> *__restrict__ U4,
     const int lx = blockIdx.y;
     const int c = blockIdx.x * C + (int)(threadIdx.x % C);
     const bool valid = c < g.H;
-    const Cx *src = U3 + (long long)lx * g.P * g.SP + c;
+    const Cx *src = U3 + (long long)lx * g.xs3 + c;
     Cx *dst = U4 + (long long)lx * g.Q * g.SP + c;
 
     Cx v[E::VPT];

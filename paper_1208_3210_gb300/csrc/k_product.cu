@@ -5,7 +5,7 @@
 //
 // CTA = (column tile of energy frequencies, k_y).  Reads U2 [N][P][2 SP]
 // (rows i_x < N; rows N..P-1 are the zero padding and are not stored), writes
-// U3 [Q][P][SP].  The forward and inverse transforms share the thread
+// U3 [Q][P][SP]; both with the padded plane strides xs2 / xs3.  The forward and inverse transforms share the thread
 // assignment of the last forward / first inverse stage, so the product
 // conj(a^) b^ is formed in registers.
 #include "kernels.cuh"
@@ -29,7 +29,7 @@ k_x_product(Geom g, const cx<Real> *__restrict__ U2, cx<Real> *__restrict__ U3,
     const int ky = blockIdx.y;
     const int c = blockIdx.x * C + (int)(threadIdx.x % C);
     const bool valid = c < g.H;
-    const long long rstride = (long long)g.P * W;     // U2 stride between i_x rows
+    const long long rstride = g.xs2;                  // U2 stride between i_x rows
     const Cx *srcA = U2 + (long long)ky * W + c;      // a^ column
     const Cx *srcB = srcA + g.SP;                     // b^ column
     const Cx zero = mk<Cx>((Real)0, (Real)0);
@@ -53,7 +53,7 @@ k_x_product(Geom g, const cx<Real> *__restrict__ U2, cx<Real> *__restrict__ U3,
     EI::run(va, sm, tw, tw_stride);
     if (valid) {
         Cx *dst = U3 + (long long)ky * g.SP + c;
-        const long long ostride = (long long)g.P * g.SP;
+        const long long ostride = g.xs3;
 #pragma unroll
         for (int b = 0; b < EI::VPT / EI::RL; ++b)
 #pragma unroll

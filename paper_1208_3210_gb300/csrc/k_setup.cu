@@ -48,62 +48,86 @@ __global__ void k_tables(Geom g, Band band, AxisTab *axis, float2 *eps32, double
 // ---------------------------------------------------------------------------
 // Chemical potential.  n(mu) = (2/npz^2) sum_k [1/2 - atan((e0_k - mu)/gamma)/pi]
 // over the first-zone grid (the Lorentzian occupation of Eq. 5 below the Fermi
-// level).  n is strictly increasing.  One cooperative launch of G CTAs:
-//   3 passes of 64-point multisection in FP32 shrink the bracket
-//   [-B-3, B+3] eV (B bounds |e0|) by 63^3;
-//   3 Newton steps in FP64 from the bracket midpoint reach FP64 precision.
-// Per-CTA partial sums go to `acc`; after a grid barrier every CTA adds them
-// in the same order, so all CTAs take identical decisions and the result does
-// not depend on scheduling.
-constexpr int MU_SECT = 64;
+// level).  n is strictly increasing.  One cooperative launch of G CTAs (one
+// per SM):
+//   MU_FP32_PASSES passes of MU_SECT-point multisection in FP32 shrink the
+//   bracket [-B-3, B+3] eV (B bounds |e0|) by (MU_SECT-1)^passes; every thread
+//   owns one candidate and a share of the points;
+//   MU_NEWTON Newton steps in FP64 from the bracket midpoint reach FP64
+//   precision.
+// After each pass the last CTA to arrive at the grid barrier adds the per-CTA
+// partial sums in a fixed order, publishes the new bracket (or mu) and then
+// releases the others, so the result does not depend on scheduling.
+constexpr int MU_SECT = 128;
 constexpr int MU_THREADS = 256;
-constexpr int MU_FP32_PASSES = 3;
+constexpr int MU_FP32_PASSES = 2;
 constexpr int MU_NEWTON = 3;
-constexpr int MU_MAXP = 8;   // first-zone points held per thread
+constexpr int MU_RES = 16;   // result slots at the start of acc
 
-// Layout of acc: [MU_FP32_PASSES][G][MU_SECT] then [MU_NEWTON][G][2] doubles.
-size_t mu_acc_doubles(int G) { return (size_t)G * (MU_FP32_PASSES * MU_SECT + MU_NEWTON * 2); }
+// Layout of acc: [MU_RES] results, then [MU_FP32_PASSES][G][MU_SECT], then [MU_NEWTON][G][2] doubles.
+size_t mu_acc_doubles(int G) { return MU_RES + (size_t)G * (MU_FP32_PASSES * MU_SECT + MU_NEWTON * 2); }
 
 __device__ __forceinline__ double band_e0(const Band &b, const AxisTab &ax, const AxisTab &ay)
 {
     if (b.band_kind == 1) return 0.5 * (ax.p2 + ay.p2);
     return -2.0 * b.t * (ax.c1 + ay.c1) - 4.0 * b.tp * ax.c1 * ay.c1 - 2.0 * b.tpp * (ax.c2 + ay.c2);
 }
-
-// Grid-wide barrier with a bounded wait (about 1 s).  bar[0] counts arrivals,
-// bar[1] is the generation, bar[2] a failure flag for this launch (all three
-// zeroed before the launch).  On timeout the flag and the plan's status word
-// are set, and every wait and later barrier of the launch returns false.
-__device__ bool grid_sync(unsigned *bar, unsigned *status)
+__device__ __forceinline__ float band_e0f(const Band &b, const AxisTab &ax, const AxisTab &ay)
 {
+    if (b.band_kind == 1) return 0.5f * (float)(ax.p2 + ay.p2);
+    float cx = (float)ax.c1, cy = (float)ay.c1;
+    return -2.0f * (float)b.t * (cx + cy) - 4.0f * (float)b.tp * cx * cy
+           - 2.0f * (float)b.tpp * ((float)ax.c2 + (float)ay.c2);
+}
+
+// Grid barrier whose last arriving CTA first runs `on_last` (with all its
+// threads) and then releases the others.  bar[0] counts arrivals, bar[1] is
+// the generation, bar[2] a failure flag; all three are zeroed before the
+// launch.  A waiting CTA records the generation before it arrives; the
+// release (generation + 1) cannot happen before its arrival.  The wait is
+// bounded (about 1 s): on timeout the failure flag and the plan's status word
+// are set, and this and every later barrier of the launch return false.
+template <typename F>
+__device__ bool grid_sync_reduce(unsigned *bar, unsigned *status, F &&on_last)
+{
+    __shared__ int s_last, s_fail;
+    __shared__ unsigned s_gen;
+    volatile unsigned *vgen = bar + 1;
+    volatile unsigned *vfail = bar + 2;
     __syncthreads();
-    __shared__ int s_fail;
     if (threadIdx.x == 0) {
-        volatile unsigned *vgen = bar + 1;
-        volatile unsigned *vfail = bar + 2;
         s_fail = *vfail != 0;
+        s_last = 0;
         if (!s_fail) {
-            unsigned gen = *vgen;
+            s_gen = *vgen;
             __threadfence();
-            if (atomicAdd(bar, 1u) == gridDim.x - 1) {
-                atomicExch(bar, 0u);
-                __threadfence();
-                atomicAdd(bar + 1, 1u);
-            } else {
-                long long t0 = clock64();
-                while (*vgen == gen) {
-                    if (*vfail != 0) { s_fail = 1; break; }
-                    if (clock64() - t0 > 2000000000LL) {
-                        atomicExch(bar + 2, 1u);
-                        atomicCAS(status, (unsigned)DEV_OK, (unsigned)DEV_ETIMEOUT);
-                        s_fail = 1;
-                        break;
-                    }
-                    __nanosleep(32);
-                }
-            }
-            __threadfence();
+            s_last = atomicAdd(bar, 1u) == gridDim.x - 1;
         }
+    }
+    __syncthreads();
+    if (s_fail) return false;
+    if (s_last) {
+        __threadfence();
+        on_last();
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        }
+    } else if (threadIdx.x == 0) {
+        long long t0 = clock64();
+        while (*vgen == s_gen) {
+            if (*vfail != 0) { s_fail = 1; break; }
+            if (clock64() - t0 > 2000000000LL) {
+                atomicExch(bar + 2, 1u);
+                atomicCAS(status, (unsigned)DEV_OK, (unsigned)DEV_ETIMEOUT);
+                s_fail = 1;
+                break;
+            }
+        }
+        __threadfence();
     }
     __syncthreads();
     return s_fail == 0;
@@ -127,70 +151,75 @@ k_solve_mu(Geom g, Band band, const AxisTab *__restrict__ axis, InstState *st, d
     const double target = band.filling * 0.5 * (double)npts;  // sum of occupations
     const double B = (band.band_kind == 1) ? 9.869604401089358
                      : 4.0 * (fabs(band.t) + fabs(band.tp) + fabs(band.tpp));
-    double lo = -B - 3.0, hi = B + 3.0;
+    volatile double *res = acc;                 // result slots
+    double *part32 = acc + MU_RES;
+    double *part64 = part32 + (size_t)MU_FP32_PASSES * G * MU_SECT;
+    constexpr int NGRP = MU_THREADS / MU_SECT;
     constexpr int NW = MU_THREADS / 32;
-    __shared__ float s_sect[NW][MU_SECT];
+    __shared__ float s_part[NGRP][MU_SECT];
     __shared__ double s_red2[2][NW];
     __shared__ int s_first;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
-    // this thread's first-zone points (usually at most one): band energies once, in FP64
-    constexpr int MAXP = MU_MAXP;
-    double e0[MAXP];
-    int np = 0;
-    for (int k = blockIdx.x * MU_THREADS + threadIdx.x; k < npts && np < MAXP; k += G * MU_THREADS) {
-        int ix = base + k / g.npz, iy = base + k % g.npz;
-        e0[np++] = band_e0(band, axis[ix], axis[iy]);
-    }
-    // (the launch uses G >= npts / (MU_MAXP * MU_THREADS), so every point is covered)
-
-    // --- FP32 multisection ---------------------------------------------------
+    double lo = -B - 3.0, hi = B + 3.0;
+    const int cand = threadIdx.x % MU_SECT, grp = threadIdx.x / MU_SECT;
+    const int pg = blockIdx.x * NGRP + grp, npg = G * NGRP;
     const float gam = (float)band.gamma;
     const float inv_pi = 0.318309886183790672f;
+
+    // --- FP32 multisection ---------------------------------------------------
     for (int pass = 0; pass < MU_FP32_PASSES; ++pass) {
         const double h = (hi - lo) / (MU_SECT - 1);
-        for (int c = 0; c < MU_SECT; ++c) {
-            float mu_c = (float)(lo + c * h), sum = 0.f;
-            for (int q = 0; q < np; ++q) sum += 0.5f - atanf(((float)e0[q] - mu_c) / gam) * inv_pi;
-            for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
-            if (lane == 0) s_sect[warp][c] = sum;
+        const float mu_c = (float)(lo + cand * h);
+        float sum = 0.f;
+        for (int k = pg; k < npts; k += npg) {
+            int ix = base + k / g.npz, iy = base + k % g.npz;
+            sum += 0.5f - atanf((band_e0f(band, axis[ix], axis[iy]) - mu_c) / gam) * inv_pi;
         }
+        s_part[grp][cand] = sum;
         __syncthreads();
         if (threadIdx.x < MU_SECT) {
             double t = 0;
-            for (int w = 0; w < NW; ++w) t += s_sect[w][threadIdx.x];
-            acc[((size_t)pass * G + blockIdx.x) * MU_SECT + threadIdx.x] = t;
+            for (int q = 0; q < NGRP; ++q) t += s_part[q][threadIdx.x];
+            part32[((size_t)pass * G + blockIdx.x) * MU_SECT + threadIdx.x] = t;
         }
-        if (threadIdx.x == 0) s_first = MU_SECT;
-        if (!grid_sync(bar, status)) return;
-        // every CTA: total occupation at each candidate, first candidate >= target
-        if (threadIdx.x < MU_SECT) {
-            double t = 0;
-            for (int q = 0; q < G; ++q) t += __ldcg(&acc[((size_t)pass * G + q) * MU_SECT + threadIdx.x]);
-            if (t >= target) atomicMin(&s_first, (int)threadIdx.x);
-        }
-        __syncthreads();
-        int i = s_first;
-        if (pass == 0 && (i == 0 || i == MU_SECT)) {
-            // the filling is not bracketed by [-B-3, B+3] eV
+        bool ok = grid_sync_reduce(bar, status, [&] {
+            if (threadIdx.x == 0) s_first = MU_SECT;
+            __syncthreads();
+            if (threadIdx.x < MU_SECT) {
+                double t = 0;
+                for (int q = 0; q < G; ++q) t += __ldcg(&part32[((size_t)pass * G + q) * MU_SECT + threadIdx.x]);
+                if (t >= target) atomicMin(&s_first, (int)threadIdx.x);
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                int i = s_first;
+                double flag = 0.0;
+                if (pass == 0 && (i == 0 || i == MU_SECT)) flag = 1.0;   // filling not bracketed
+                if (i == 0) i = 1;
+                if (i == MU_SECT) i = MU_SECT - 1;
+                res[3 * pass + 0] = lo + (i - 1) * h;
+                res[3 * pass + 1] = lo + i * h;
+                res[3 * pass + 2] = flag;
+            }
+        });
+        if (!ok) return;
+        if (res[3 * pass + 2] != 0.0) {
             if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(status, (unsigned)DEV_OK, (unsigned)DEV_ENOCONV);
             return;
         }
-        if (i == 0) i = 1;
-        if (i == MU_SECT) i = MU_SECT - 1;
-        double nlo = lo + (i - 1) * h, nhi = lo + i * h;
-        lo = nlo;
-        hi = nhi;
-        __syncthreads();
+        lo = res[3 * pass + 0];
+        hi = res[3 * pass + 1];
     }
 
     // --- FP64 Newton ---------------------------------------------------------
     double mu = 0.5 * (lo + hi), step = 0.0;
     const double gd = band.gamma, ipi = 0.31830988618379067154;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int it = 0; it < MU_NEWTON; ++it) {
         double f = 0.0, fp = 0.0;
-        for (int q = 0; q < np; ++q) {
-            double xi = e0[q] - mu;
+        for (int k = blockIdx.x * MU_THREADS + threadIdx.x; k < npts; k += G * MU_THREADS) {
+            int ix = base + k / g.npz, iy = base + k % g.npz;
+            double xi = band_e0(band, axis[ix], axis[iy]) - mu;
             f += 0.5 - atan(xi / gd) * ipi;
             fp += gd * ipi / (xi * xi + gd * gd);
         }
@@ -200,19 +229,27 @@ k_solve_mu(Geom g, Band band, const AxisTab *__restrict__ axis, InstState *st, d
         }
         if (lane == 0) { s_red2[0][warp] = f; s_red2[1][warp] = fp; }
         __syncthreads();
-        double *slot = acc + (size_t)G * MU_FP32_PASSES * MU_SECT + ((size_t)it * G + blockIdx.x) * 2;
         if (threadIdx.x == 0) {
             double a = 0, b = 0;
             for (int w = 0; w < NW; ++w) { a += s_red2[0][w]; b += s_red2[1][w]; }
-            slot[0] = a;
-            slot[1] = b;
+            part64[((size_t)it * G + blockIdx.x) * 2 + 0] = a;
+            part64[((size_t)it * G + blockIdx.x) * 2 + 1] = b;
         }
-        if (!grid_sync(bar, status)) return;
-        double F = 0, Fp = 0;
-        const double *all = acc + (size_t)G * MU_FP32_PASSES * MU_SECT + (size_t)it * G * 2;
-        for (int q = 0; q < G; ++q) { F += __ldcg(&all[2 * q]); Fp += __ldcg(&all[2 * q + 1]); }
-        step = (F - target) / Fp;          // d/dmu of sum_k occ = sum_k Lorentzian
-        mu -= step;
+        bool ok = grid_sync_reduce(bar, status, [&] {
+            if (threadIdx.x == 0) {
+                double F = 0, Fp = 0;
+                for (int q = 0; q < G; ++q) {
+                    F += __ldcg(&part64[((size_t)it * G + q) * 2 + 0]);
+                    Fp += __ldcg(&part64[((size_t)it * G + q) * 2 + 1]);
+                }
+                double stp = (F - target) / Fp;     // d/dmu of sum_k occ = sum_k Lorentzian
+                res[8 + 2 * it] = mu - stp;
+                res[9 + 2 * it] = stp;
+            }
+        });
+        if (!ok) return;
+        mu = res[8 + 2 * it];
+        step = res[9 + 2 * it];
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         st->mu = mu;
@@ -239,12 +276,8 @@ cudaError_t launch_tables(const Geom &g, const Band &band, AxisTab *axis, float2
 // CTAs of the cooperative chemical-potential launch: at most one per SM.
 int mu_grid_size(int num_sms, int npts)
 {
-    // one point per thread where the SMs allow, at most MU_MAXP
-    int want = (npts + MU_THREADS - 1) / MU_THREADS;
-    int need = (npts + MU_MAXP * MU_THREADS - 1) / (MU_MAXP * MU_THREADS);
-    if (want > num_sms) want = num_sms;
-    if (want < need) want = need;
-    return want < 1 ? 1 : want;
+    (void)npts;
+    return num_sms < 1 ? 1 : num_sms;   // one CTA per SM
 }
 
 cudaError_t launch_solve_mu(const Geom &g, const Band &band, const AxisTab *axis, InstState *st, double *acc,

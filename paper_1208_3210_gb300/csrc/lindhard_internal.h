@@ -19,6 +19,8 @@ struct Geom {
     int PE;         // FFT length along energy
     int H;          // PE / 2 + 1 non-redundant energy frequencies
     int SP;         // row stride of half spectra (H rounded up to 8)
+    long long xs2;  // stride between p_x planes of the [N][P][2 SP] buffers, P 2SP + pad
+    long long xs3;  // stride between q_x planes of the [Q][P][SP] buffers, P SP + pad
     int Q;          // lags kept per momentum axis
     int n_omega;    // energy transfers kept
     int band_kind;  // 0 tight binding, 1 free electrons

@@ -33,6 +33,18 @@ cudaError_t launch_inv_y(const Geom &g, const Work<float> &w, cudaStream_t s);
 cudaError_t launch_inv_y(const Geom &g, const Work<double> &w, cudaStream_t s);
 cudaError_t launch_inv_energy(const Geom &g, const Work<float> &w, float *out, cudaStream_t s);
 cudaError_t launch_inv_energy(const Geom &g, const Work<double> &w, double *out, cudaStream_t s);
+cudaError_t launch_w_energy(const Geom &g, const float *w, float2 *WU1, const float2 *tw, int tw_len,
+                            cudaStream_t s);
+cudaError_t launch_w_y(const Geom &g, const float2 *WU1, float2 *WU2, const float2 *tw, int tw_len, cudaStream_t s);
+cudaError_t launch_bw_product(const Geom &g, float2 *U2, const float2 *WU2, const float2 *tw, int tw_len,
+                              cudaStream_t s);
+cudaError_t launch_bw_inv_y(const Geom &g, const float2 *G3, float2 *G4, const float2 *tw, int tw_len,
+                            cudaStream_t s);
+cudaError_t launch_bw_inv_energy(const Geom &g, const Band &band, const AxisTab *axis, const float2 *eps,
+                                 const InstState *st, const float2 *G4, float *dA, double *partial,
+                                 const float2 *tw, int tw_len, cudaStream_t s);
+int bw_energy_blocks(const Geom &g);
+cudaError_t launch_reduce_params(const double *partial, int nblocks, double *out, cudaStream_t s);
 }  // namespace lh
 
 using namespace lh;
@@ -72,6 +84,9 @@ struct lindhard_plan {
     size_t off_X = 0, off_Y = 0, off_axis = 0, off_eps32 = 0, off_eps64 = 0, off_tw32 = 0, off_tw64 = 0,
            off_state = 0, off_status = 0, off_acc = 0, off_bar = 0;
     int tw_len = 0;
+    // backward buffers (LINDHARD_PLAN_BACKWARD)
+    bool backward = false;
+    size_t off_Z = 0, off_partial = 0;
     // per-pass event timing (lindhard_plan_profile)
     bool profile = false;
     struct Timed { int slot; cudaEvent_t a, b; };
@@ -165,6 +180,12 @@ static lindhard_status make_geom(const lindhard_grid &gr, Geom &g, int &prec)
     g.PE = (int)PE;
     g.H = (int)(PE / 2 + 1);
     g.SP = (g.H + 7) / 8 * 8;
+    // The p_x pass reads and writes rows one plane apart; plane sizes are
+    // multiples of large powers of two (P 2SP 8 bytes = 33 * 2^18 at 2048 x 512),
+    // which concentrates those accesses on few memory channels.  256 bytes of
+    // padding per plane spread them.
+    g.xs2 = (long long)P * 2 * g.SP + 32;
+    g.xs3 = (long long)P * g.SP + 32;
     g.Q = (int)Q;
     g.n_omega = (int)n_omega;
     g.band_kind = 0;
@@ -182,14 +203,15 @@ extern "C" lindhard_status lindhard_plan_create(const lindhard_grid *grids, int 
                                                 lindhard_plan **out)
 {
     if (!grids || !out || batch < 1) return fail(LINDHARD_EINVAL, "grids/out must be non-NULL and batch >= 1");
-    if (flags != 0) return fail(LINDHARD_EINVAL, "flags must be 0");
+    if (flags & ~(unsigned)LINDHARD_PLAN_BACKWARD) return fail(LINDHARD_EINVAL, "unknown plan flags");
     *out = nullptr;
     lindhard_plan *p = new (std::nothrow) lindhard_plan;
     if (!p) return fail(LINDHARD_ENOMEM, "host allocation failed");
     p->batch = batch;
     p->geoms.resize(batch);
     p->precision.resize(batch);
-    size_t maxX = 0, maxY = 0, maxN = 0, maxE = 0;
+    p->backward = (flags & LINDHARD_PLAN_BACKWARD) != 0;
+    size_t maxX = 0, maxY = 0, maxN = 0, maxE = 0, maxZ = 0, maxPart = 0;
     int maxLen = kMinLen, maxNpts = 1;
     for (int i = 0; i < batch; ++i) {
         lindhard_status st = make_geom(grids[i], p->geoms[i], p->precision[i]);
@@ -199,10 +221,18 @@ extern "C" lindhard_status lindhard_plan_create(const lindhard_grid *grids, int 
         }
         const Geom &g = p->geoms[i];
         size_t cb = cx_bytes(p->precision[i]);
-        size_t X = std::max((size_t)g.N * g.N * 2 * g.SP, (size_t)g.Q * g.P * g.SP) * cb;
-        size_t Y = std::max((size_t)g.N * g.P * 2 * g.SP, (size_t)g.Q * g.Q * g.SP) * cb;
+        size_t X = std::max((size_t)g.N * g.N * 2 * g.SP, (size_t)g.Q * (size_t)g.xs3) * cb;
+        size_t Y = std::max((size_t)g.N * (size_t)g.xs2, (size_t)g.Q * g.Q * g.SP) * cb;
         maxX = std::max(maxX, X);
         maxY = std::max(maxY, Y);
+        if (p->backward) {
+            if (p->precision[i] != LINDHARD_FP32) {
+                delete p;
+                return fail(LINDHARD_EUNSUPPORTED, "the backward pass is built for LINDHARD_FP32 grids");
+            }
+            maxZ = std::max(maxZ, (size_t)g.Q * (size_t)g.xs3 * cb);
+            maxPart = std::max(maxPart, (size_t)bw_energy_blocks(g) * 5 * sizeof(double));
+        }
         maxN = std::max(maxN, (size_t)g.N);
         maxE = std::max(maxE, (size_t)g.n_eps);
         maxLen = std::max(maxLen, std::max(g.P, g.PE));
@@ -228,6 +258,8 @@ extern "C" lindhard_status lindhard_plan_create(const lindhard_grid *grids, int 
     p->off_status = o; o = align_up(o + sizeof(unsigned));
     p->off_acc = o; o = align_up(o + mu_acc_doubles(p->mu_G) * sizeof(double));
     p->off_bar = o; o = align_up(o + 3 * sizeof(unsigned));
+    p->off_Z = o; o = align_up(o + maxZ);
+    p->off_partial = o; o = align_up(o + maxPart);
     p->ws_bytes = o;
     e = cudaMalloc(&p->ws, p->ws_bytes);
     if (e != cudaSuccess) {
@@ -389,8 +421,51 @@ extern "C" lindhard_status lindhard_imchi_f64(lindhard_plan *p, const lindhard_b
 extern "C" lindhard_status lindhard_imchi_backward(lindhard_plan *p, const lindhard_band *bands, const float *A_in,
                                                    const float *w, float *dA, double *dparams, void *stream)
 {
-    (void)p; (void)bands; (void)A_in; (void)w; (void)dA; (void)dparams; (void)stream;
-    return fail(LINDHARD_EUNSUPPORTED, "backward is not built yet");
+    if (!p || !w) return fail(LINDHARD_EINVAL, "plan and w must be non-NULL");
+    if (!p->backward) return fail(LINDHARD_EINVAL, "create the plan with LINDHARD_PLAN_BACKWARD");
+    if (!dA && !dparams) return fail(LINDHARD_EINVAL, "nothing to compute: dA and dparams are both NULL");
+    if (dparams && A_in) return fail(LINDHARD_EINVAL, "dparams needs the generated A (A_in must be NULL)");
+    std::vector<Band> bs(p->batch);
+    if (A_in == nullptr) {
+        for (int i = 0; i < p->batch; ++i) {
+            lindhard_status st = make_band(bands ? bands + i : nullptr, bs[i]);
+            if (st != LINDHARD_OK) return st;
+            if (bs[i].band_kind == 1 && p->geoms[i].periodic)
+                return fail(LINDHARD_EINVAL, "free electrons need zones > 1 (the band is not periodic)");
+            if (bs[i].solve_mu && p->geoms[i].npz > 512)
+                return fail(LINDHARD_EUNSUPPORTED, "the filling solve supports pts_per_zone <= 512; pass mu instead");
+        }
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    Work<float> wk = work_of<float>(p);
+    float2 *X = (float2 *)wk.X, *Y = (float2 *)wk.Y, *Z = (float2 *)(p->ws + p->off_Z);
+    const float2 *tw = (const float2 *)wk.tw;
+    double *partial = (double *)(p->ws + p->off_partial);
+    size_t a_off = 0, o_off = 0;
+    for (int i = 0; i < p->batch; ++i) {
+        const Geom &g = p->geoms[i];
+        const Band &b = bs[i];
+        cudaError_t e = cudaSuccess;
+        if (A_in == nullptr) {
+            e = launch_tables(g, b, wk.axis, (float2 *)wk.eps, nullptr, s);
+            if (e == cudaSuccess)
+                e = launch_solve_mu(g, b, wk.axis, wk.state, wk.mu_acc, wk.barrier, wk.status, nullptr, p->mu_G, s);
+        }
+        if (e == cudaSuccess) e = launch_fwd_energy(g, b, wk, A_in ? A_in + a_off : nullptr, s);   // X = U1
+        if (e == cudaSuccess) e = launch_fwd_y(g, wk, s);                                           // Y = U2
+        if (e == cudaSuccess) e = launch_w_energy(g, w + o_off, X, tw, p->tw_len, s);                // X = WU1
+        if (e == cudaSuccess) e = launch_w_y(g, X, Z, tw, p->tw_len, s);                             // Z = WU2
+        if (e == cudaSuccess) e = launch_bw_product(g, Y, Z, tw, p->tw_len, s);                      // Y = G3
+        if (e == cudaSuccess) e = launch_bw_inv_y(g, Y, X, tw, p->tw_len, s);                        // X = G4
+        if (e == cudaSuccess)
+            e = launch_bw_inv_energy(g, b, wk.axis, (const float2 *)wk.eps, wk.state, X, dA ? dA + a_off : nullptr,
+                                     dparams ? partial : nullptr, tw, p->tw_len, s);
+        if (e == cudaSuccess && dparams) e = launch_reduce_params(partial, bw_energy_blocks(g), dparams + 5 * i, s);
+        if (e != cudaSuccess) return cuda_fail(e, "backward launch");
+        a_off += (size_t)g.N * g.N * g.n_eps;
+        o_off += (size_t)g.Q * g.Q * g.n_omega;
+    }
+    return LINDHARD_OK;
 }
 
 extern "C" lindhard_status lindhard_plan_profile(lindhard_plan *p, int enable)

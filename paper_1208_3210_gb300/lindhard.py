@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(HERE, "_build", "liblindhard.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOCONV, EUNSUPPORTED = range(7)
 FP32, FP64 = 0, 2
+PLAN_BACKWARD = 1
 _STATUS_NAMES = {OK: "OK", EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", ETIMEOUT: "ETIMEOUT",
                  ENOCONV: "ENOCONV", EUNSUPPORTED: "EUNSUPPORTED"}
 
@@ -112,14 +113,14 @@ class Plan:
     """A lindhard_plan for one or more instance grids (dicts with zones, npz,
     n_eps, e_max and optional n_omega, q_extent, precision)."""
 
-    def __init__(self, grids: Sequence[dict], precision: int = FP32):
+    def __init__(self, grids: Sequence[dict], precision: int = FP32, backward: bool = False):
         lib = load()
         self.grids = [make_grid(g["zones"], g["npz"], g["n_eps"], g["e_max"], g.get("n_omega", 0),
                                 g.get("q_extent", 0), g.get("precision", precision)) for g in grids]
         self.batch = len(self.grids)
         arr = (Grid * self.batch)(*self.grids)
         h = ctypes.c_void_p()
-        _check(lib.lindhard_plan_create(arr, self.batch, 0, ctypes.byref(h)))
+        _check(lib.lindhard_plan_create(arr, self.batch, PLAN_BACKWARD if backward else 0, ctypes.byref(h)))
         self._h = h
         self.sizes = []
         for i in range(self.batch):
@@ -169,6 +170,13 @@ class Plan:
         return out
 
     def backward(self, w, bands=None, A_in=None, dA=None, dparams=None, stream=None):
+        """Adjoint for L = sum w * Im chi: fills dA (float32, A layout) and/or
+        dparams (float64, [batch][5] = dL/d(t, t', t'', mu, gamma))."""
+        assert w.dtype.is_floating_point and w.is_cuda and w.is_contiguous() and w.numel() == self.out_elems()
+        if dA is not None:
+            assert dA.is_cuda and dA.is_contiguous() and dA.numel() == self.a_elems()
+        if dparams is not None:
+            assert dparams.is_cuda and dparams.numel() >= 5 * self.batch
         _check(load().lindhard_imchi_backward(self._h, self._bands(bands), _ptr(A_in), _ptr(w), _ptr(dA),
                                               _ptr(dparams), _stream(stream)))
         return dA, dparams
