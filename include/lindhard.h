@@ -197,6 +197,30 @@ lindhard_status lindhard_plan_status(lindhard_plan *plan, void *stream);
 /* Releases the plan's device memory.  Synchronises the device first. */
 void lindhard_plan_destroy(lindhard_plan *plan);
 
+/* Bytes of the fixed device array used by lindhard_imchi_noalloc. */
+#define LINDHARD_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+/* Forward call that allocates nothing (the paper has no counterpart: this is
+ * an interface for callers that cannot allocate device memory when they need
+ * Im chi -- inside a framework that owns the device memory pool, on hosts that
+ * forbid allocation after start-up, or where cudaMalloc/cudaFree would
+ * synchronise the device).  It computes exactly what lindhard_imchi computes
+ * for one instance (`grid`, `band`, `A_in`, `out`, `mu_out` as there; FP32
+ * only), with all intermediates in one fixed device array of
+ * LINDHARD_NOALLOC_SCRATCH_BYTES (32 MiB) that every GPU loading the library
+ * holds until the process exits.  Grids whose intermediates do not fit are
+ * rejected with LINDHARD_EINVAL and a message giving the bytes needed (the
+ * 32 x 32 x 48 reduced-zone grid needs about 1.5 MiB; 2 zones of 32 points
+ * with 128 energies about 14 MiB).  The first call on each device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.  All calls share the array, so calls
+ * that can overlap on the GPU (other streams or host threads) race and must be
+ * serialised by the caller.  Device-side failures (a filling with no chemical
+ * potential) are not reported by this entry point; use a plan and
+ * lindhard_plan_status() where that check is needed. */
+lindhard_status lindhard_imchi_noalloc(const lindhard_grid *grid, const lindhard_band *band,
+                                       const float *A_in, float *out, double *mu_out, void *stream);
+
 /* Human-readable text of the last host-side error in this thread. */
 const char *lindhard_last_error(void);
 

@@ -510,3 +510,10 @@ extern "C" void lindhard_plan_destroy(lindhard_plan *p)
 }
 
 extern "C" const char *lindhard_last_error(void) { return g_last_error.c_str(); }
+
+// Helpers shared with other host translation units of the library.
+namespace lh {
+lindhard_status geom_from_grid(const lindhard_grid &gr, Geom &g, int &prec) { return make_geom(gr, g, prec); }
+lindhard_status band_from_params(const lindhard_band *b, Band &o) { return make_band(b, o); }
+lindhard_status set_error(lindhard_status st, const char *msg) { return fail(st, msg); }
+}  // namespace lh

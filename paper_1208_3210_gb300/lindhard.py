@@ -24,7 +24,8 @@ _STATUS_NAMES = {OK: "OK", EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", E
 # Exported symbols, in the order include/lindhard.h declares them.
 SYMBOLS = ("lindhard_plan_create", "lindhard_plan_sizes", "lindhard_plan_workspace_bytes", "lindhard_imchi",
            "lindhard_imchi_f64", "lindhard_imchi_backward", "lindhard_plan_profile", "lindhard_plan_pass_times",
-           "lindhard_plan_status", "lindhard_plan_destroy", "lindhard_last_error")
+           "lindhard_plan_status", "lindhard_plan_destroy", "lindhard_imchi_noalloc", "lindhard_last_error")
+NOALLOC_SCRATCH_BYTES = 32 << 20
 NUM_PASSES = 7
 PASS_NAMES = ("tables", "mu_solve", "energy_fwd", "py_fwd", "px_product", "py_inv", "energy_inv")
 
@@ -77,6 +78,8 @@ def load(path: str = LIB_PATH):
         lib.lindhard_plan_destroy.argtypes = [vp]
         lib.lindhard_plan_destroy.restype = None
         lib.lindhard_last_error.restype = ctypes.c_char_p
+        lib.lindhard_imchi_noalloc.argtypes = [ctypes.POINTER(Grid), ctypes.POINTER(Band), vp, vp, vp, vp]
+        lib.lindhard_imchi_noalloc.restype = ctypes.c_int
         for name in ("lindhard_plan_create", "lindhard_plan_sizes", "lindhard_plan_workspace_bytes",
                      "lindhard_imchi", "lindhard_imchi_f64", "lindhard_imchi_backward", "lindhard_plan_profile",
                      "lindhard_plan_pass_times", "lindhard_plan_status"):
@@ -107,6 +110,20 @@ def _stream(stream):
     import torch
     s = torch.cuda.current_stream() if stream is None else stream
     return ctypes.c_void_p(s.cuda_stream)
+
+
+def imchi_noalloc(grid: dict, band=None, out=None, A_in=None, mu_out=None, stream=None):
+    """One forward call through lindhard_imchi_noalloc, which allocates no
+    device memory: for callers that cannot allocate when they need Im chi.
+    `out` (float32, Q*Q*n_omega elements) must be supplied by the caller; all
+    intermediates live in the library's fixed 32 MiB device array, so calls
+    that could overlap on the GPU must be serialised."""
+    g = make_grid(grid["zones"], grid["npz"], grid["n_eps"], grid["e_max"], grid.get("n_omega", 0),
+                  grid.get("q_extent", 0), FP32)
+    b = None if band is None else (band if isinstance(band, Band) else make_band(**band))
+    _check(load().lindhard_imchi_noalloc(ctypes.byref(g), None if b is None else ctypes.byref(b), _ptr(A_in),
+                                         _ptr(out), _ptr(mu_out), _stream(stream)))
+    return out
 
 
 class Plan:
