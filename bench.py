@@ -48,6 +48,8 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--grid", default=None,
+                    help="zones,npz,n_eps,e_max: replace the workload's grid (for profiling smaller cases)")
     return ap.parse_args()
 
 
@@ -235,6 +237,11 @@ def main():
 
     w = wl.WORKLOADS[args.workload]
     band, grid = w["band"], w["grid"]
+    if args.grid:
+        z, npz, ne, em = args.grid.split(",")
+        grid = wl.grid_params(int(z), int(npz), int(ne), float(em))
+        args.workload = f"{args.workload} grid {args.grid}"
+        args.no_cpu_baseline = True
     plan = lh.Plan([grid])
     s = plan.sizes[0]
     out = torch.empty(plan.out_elems(), dtype=torch.float32, device="cuda")
@@ -304,7 +311,7 @@ def main():
     dom_ms = timed[dom][0] / timed[dom][1]
     peak, peak_kind = measured_peaks()
     achieved = pb[dom] / (dom_ms * 1e-3) / 1e9
-    traffic = recorded_traffic(dom, args.workload)
+    traffic = None if args.grid else recorded_traffic(dom, args.workload)
     launches = int(sum(v[1] for v in ptimes.values()))
     pipeline_bytes = sum(pb.values())
     step_ms = ms_total / args.steps

@@ -33,6 +33,10 @@ __global__ void k_tables(Geom g, Band band, AxisTab *axis, float2 *eps32, double
         a.c2 = cospi(2.0 * u);
         a.g = (band.ff_a == 0.0) ? 1.0 : exp(-p * p * band.ff_a * band.ff_a / 8.0);
         a.p2 = p * p;
+        a.c1f = (float)a.c1;
+        a.c2f = (float)a.c2;
+        a.p2f = (float)a.p2;
+        a.pad = 0.f;
         axis[i] = a;
     }
     if (i < g.n_eps) {
@@ -72,12 +76,14 @@ __device__ __forceinline__ double band_e0(const Band &b, const AxisTab &ax, cons
     if (b.band_kind == 1) return 0.5 * (ax.p2 + ay.p2);
     return -2.0 * b.t * (ax.c1 + ay.c1) - 4.0 * b.tp * ax.c1 * ay.c1 - 2.0 * b.tpp * (ax.c2 + ay.c2);
 }
-__device__ __forceinline__ float band_e0f(const Band &b, const AxisTab &ax, const AxisTab &ay)
+// FP32 band energy from the FP32 table copies; t32 = (t, t', t'') in FP32.
+__device__ __forceinline__ float band_e0f(int kind, const float *t32, const AxisTab *__restrict__ axis, int ix,
+                                          int iy)
 {
-    if (b.band_kind == 1) return 0.5f * (float)(ax.p2 + ay.p2);
-    float cx = (float)ax.c1, cy = (float)ay.c1;
-    return -2.0f * (float)b.t * (cx + cy) - 4.0f * (float)b.tp * cx * cy
-           - 2.0f * (float)b.tpp * ((float)ax.c2 + (float)ay.c2);
+    const float4 ax = *reinterpret_cast<const float4 *>(&axis[ix].c1f);
+    const float4 ay = *reinterpret_cast<const float4 *>(&axis[iy].c1f);
+    if (kind == 1) return 0.5f * (ax.z + ay.z);
+    return -2.0f * t32[0] * (ax.x + ay.x) - 4.0f * t32[1] * ax.x * ay.x - 2.0f * t32[2] * (ax.y + ay.y);
 }
 
 // Grid barrier whose last arriving CTA first runs `on_last` (with all its
@@ -165,15 +171,19 @@ k_solve_mu(Geom g, Band band, const AxisTab *__restrict__ axis, InstState *st, d
     const int pg = blockIdx.x * NGRP + grp, npg = G * NGRP;
     const float gam = (float)band.gamma;
     const float inv_pi = 0.318309886183790672f;
+    const float t32[3] = {(float)band.t, (float)band.tp, (float)band.tpp};
+    __shared__ double s_tot[NGRP][MU_SECT];
+    __shared__ double s_nw[2][NW];
 
     // --- FP32 multisection ---------------------------------------------------
     for (int pass = 0; pass < MU_FP32_PASSES; ++pass) {
         const double h = (hi - lo) / (MU_SECT - 1);
         const float mu_c = (float)(lo + cand * h);
         float sum = 0.f;
+#pragma unroll 4
         for (int k = pg; k < npts; k += npg) {
             int ix = base + k / g.npz, iy = base + k % g.npz;
-            sum += 0.5f - atanf((band_e0f(band, axis[ix], axis[iy]) - mu_c) / gam) * inv_pi;
+            sum += 0.5f - atanf((band_e0f(band.band_kind, t32, axis, ix, iy) - mu_c) / gam) * inv_pi;
         }
         s_part[grp][cand] = sum;
         __syncthreads();
@@ -184,11 +194,17 @@ k_solve_mu(Geom g, Band band, const AxisTab *__restrict__ axis, InstState *st, d
         }
         bool ok = grid_sync_reduce(bar, status, [&] {
             if (threadIdx.x == 0) s_first = MU_SECT;
+            // every thread adds a fixed subset of the CTA partials of its
+            // candidate (loads unrolled so they overlap), then two halves
+            double t = 0;
+#pragma unroll 16
+            for (int q = grp; q < G; q += NGRP) t += __ldcg(&part32[((size_t)pass * G + q) * MU_SECT + cand]);
+            s_tot[grp][cand] = t;
             __syncthreads();
             if (threadIdx.x < MU_SECT) {
-                double t = 0;
-                for (int q = 0; q < G; ++q) t += __ldcg(&part32[((size_t)pass * G + q) * MU_SECT + threadIdx.x]);
-                if (t >= target) atomicMin(&s_first, (int)threadIdx.x);
+                double tt = 0;
+                for (int q = 0; q < NGRP; ++q) tt += s_tot[q][threadIdx.x];
+                if (tt >= target) atomicMin(&s_first, (int)threadIdx.x);
             }
             __syncthreads();
             if (threadIdx.x == 0) {
@@ -236,12 +252,22 @@ k_solve_mu(Geom g, Band band, const AxisTab *__restrict__ axis, InstState *st, d
             part64[((size_t)it * G + blockIdx.x) * 2 + 1] = b;
         }
         bool ok = grid_sync_reduce(bar, status, [&] {
+            // a fixed reduction tree over the CTA partials
+            double F = 0, Fp = 0;
+            for (int q = threadIdx.x; q < G; q += MU_THREADS) {
+                F += __ldcg(&part64[((size_t)it * G + q) * 2 + 0]);
+                Fp += __ldcg(&part64[((size_t)it * G + q) * 2 + 1]);
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                F += __shfl_down_sync(0xffffffffu, F, o);
+                Fp += __shfl_down_sync(0xffffffffu, Fp, o);
+            }
+            if (lane == 0) { s_nw[0][warp] = F; s_nw[1][warp] = Fp; }
+            __syncthreads();
             if (threadIdx.x == 0) {
-                double F = 0, Fp = 0;
-                for (int q = 0; q < G; ++q) {
-                    F += __ldcg(&part64[((size_t)it * G + q) * 2 + 0]);
-                    Fp += __ldcg(&part64[((size_t)it * G + q) * 2 + 1]);
-                }
+                F = 0;
+                Fp = 0;
+                for (int w = 0; w < NW; ++w) { F += s_nw[0][w]; Fp += s_nw[1][w]; }
                 double stp = (F - target) / Fp;     // d/dmu of sum_k occ = sum_k Lorentzian
                 res[8 + 2 * it] = mu - stp;
                 res[9 + 2 * it] = stp;

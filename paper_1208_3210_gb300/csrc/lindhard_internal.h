@@ -50,6 +50,7 @@ struct AxisTab {
     double c2;   // cos(2 p_i)
     double g;    // exp(-p_i^2 ff_a^2 / 8), so |M(p)|^2 = g(px) g(py)
     double p2;   // p_i^2
+    float c1f, c2f, p2f, pad;   // the same rounded to FP32 (for FP32-only uses)
 };
 
 // Workspace of one instance (device pointers into the plan's allocation).
