@@ -169,9 +169,11 @@ struct Fft {
     static constexpr int NS = fft_nstages(L);
     static constexpr int VPT = C * L / T;
     static constexpr int LP = L + L / 16;                    // padded line (MAP_LINE)
-    static constexpr int SMEM_ELEMS = (MAP == MAP_COL) ? L * C : C * LP;
     static constexpr int R0 = fft_radix(L, 0, INV);
     static constexpr int RL = fft_radix(L, NS - 1, INV);
+    // MAP_COL rows: one empty row after every R0 rows, so that the first
+    // exchange's writes (rows R0 apart) fall into different banks
+    static constexpr int SMEM_ELEMS = (MAP == MAP_COL) ? (L + L / R0) * C : C * LP;
     static_assert((C * L) % T == 0, "tile must split evenly over threads");
     static_assert(VPT % R0 == 0 && VPT % RL == 0 && VPT % fft_radix(L, NS > 2 ? 1 : 0, INV) == 0,
                   "values per thread must be a multiple of every radix");
@@ -179,7 +181,7 @@ struct Fft {
 
     __device__ __forceinline__ static int saddr(int col, int n)
     {
-        return MAP == MAP_COL ? n * C + col : col * LP + n + (n >> 4);
+        return MAP == MAP_COL ? (n + n / R0) * C + col : col * LP + n + (n >> 4);
     }
     // butterfly index -> (line, j) for a stage of radix Rs
     template <int Rs>
@@ -251,5 +253,139 @@ struct Fft {
         stage_rest<1>(v, sm, tw, tw_stride);
     }
 };
+
+}  // namespace lh
+
+namespace lh {
+
+// ---------------------------------------------------------------------------
+// Column engine with paired columns: each thread transforms two adjacent
+// columns (2p, 2p + 1) of a C-column tile with the same butterfly indices, so
+// every twiddle is loaded once for both, global and shared-memory accesses
+// move 16 bytes (both columns of a row) per instruction, and each thread has
+// two independent dependency chains in flight.  Layout and Stockham ordering
+// as in Fft<..., MAP_COL, ...>: shared memory [L][C].
+// VPT = (C/2) L / T values per thread per column.
+template <typename Real, int L, int C, int T, bool INV>
+struct FftPair {
+    using Cx = cx<Real>;
+    static constexpr int CP = C / 2;                 // column pairs per tile
+    static constexpr int NS = fft_nstages(L);
+    static constexpr int VPT = CP * L / T;
+    static constexpr int R0 = fft_radix(L, 0, INV);
+    static constexpr int RL = fft_radix(L, NS - 1, INV);
+    static constexpr int SMEM_ELEMS = (L + L / R0) * C;   // one empty row after every R0 rows
+    static_assert(C % 2 == 0 && T % CP == 0 && (CP * L) % T == 0, "tile must split evenly over threads");
+    static_assert(VPT % R0 == 0 && VPT % RL == 0 && VPT % fft_radix(L, NS > 2 ? 1 : 0, INV) == 0,
+                  "values per thread must be a multiple of every radix");
+
+    // the thread's column pair (columns 2p and 2p + 1 of the tile)
+    __device__ __forceinline__ static int pair() { return threadIdx.x % CP; }
+    // row of the b-th butterfly's r-th element before the first stage
+    __device__ __forceinline__ static int first_row(int b, int r)
+    {
+        return (threadIdx.x + b * T) / CP + r * (L / R0);
+    }
+    // row of v[b*RL + r] after the last stage
+    __device__ __forceinline__ static int last_row(int b, int r)
+    {
+        return (threadIdx.x + b * T) / CP + r * (L / RL);
+    }
+
+    __device__ __forceinline__ static int srow(int row) { return (row + row / R0) * C; }
+    __device__ __forceinline__ static void st2(Cx *sm, int row, int p, Cx a, Cx b)
+    {
+        if constexpr (sizeof(Real) == 4) {
+            *reinterpret_cast<float4 *>(&sm[srow(row) + 2 * p]) = make_float4(a.x, a.y, b.x, b.y);
+        } else {
+            sm[srow(row) + 2 * p] = a;
+            sm[srow(row) + 2 * p + 1] = b;
+        }
+    }
+    __device__ __forceinline__ static void ld2(const Cx *sm, int row, int p, Cx &a, Cx &b)
+    {
+        if constexpr (sizeof(Real) == 4) {
+            float4 q = *reinterpret_cast<const float4 *>(&sm[srow(row) + 2 * p]);
+            a = mk<Cx>(q.x, q.y);
+            b = mk<Cx>(q.z, q.w);
+        } else {
+            a = sm[srow(row) + 2 * p];
+            b = sm[srow(row) + 2 * p + 1];
+        }
+    }
+
+    template <int S>
+    __device__ __forceinline__ static void stage_rest(Cx *va, Cx *vb, Cx *sm, const Cx *__restrict__ tw, int tw_stride)
+    {
+        if constexpr (S < NS) {
+            constexpr int Rp = fft_radix(L, S - 1, INV);
+            constexpr int Nsp = fft_ns_before(L, S - 1, INV);
+            constexpr int Rs = fft_radix(L, S, INV);
+            constexpr int Ns = Nsp * Rp;
+            const int p = pair();
+#pragma unroll
+            for (int b = 0; b < VPT / Rp; ++b) {
+                int j = (threadIdx.x + b * T) / CP;
+                int idxD = (j / Nsp) * Nsp * Rp + (j % Nsp);
+#pragma unroll
+                for (int r = 0; r < Rp; ++r) st2(sm, idxD + r * Nsp, p, va[b * Rp + r], vb[b * Rp + r]);
+            }
+            __syncthreads();
+#pragma unroll
+            for (int b = 0; b < VPT / Rs; ++b) {
+                int j = (threadIdx.x + b * T) / CP;
+#pragma unroll
+                for (int r = 0; r < Rs; ++r) ld2(sm, j + r * (L / Rs), p, va[b * Rs + r], vb[b * Rs + r]);
+                int k = j % Ns;
+#pragma unroll
+                for (int r = 1; r < Rs; ++r) {
+                    Cx w = __ldg(&tw[(size_t)(k * r * (L / (Ns * Rs))) * tw_stride]);
+                    va[b * Rs + r] = INV ? cmulc(va[b * Rs + r], w) : cmul(va[b * Rs + r], w);
+                    vb[b * Rs + r] = INV ? cmulc(vb[b * Rs + r], w) : cmul(vb[b * Rs + r], w);
+                }
+                Dft<Rs, INV, Cx>::run(va + b * Rs);
+                Dft<Rs, INV, Cx>::run(vb + b * Rs);
+            }
+            __syncthreads();
+            stage_rest<S + 1>(va, vb, sm, tw, tw_stride);
+        }
+    }
+
+    // Transform both columns in place (inputs per first_row, outputs per
+    // last_row); ends with a __syncthreads().
+    __device__ __forceinline__ static void run(Cx *va, Cx *vb, Cx *sm, const Cx *__restrict__ tw, int tw_stride)
+    {
+#pragma unroll
+        for (int b = 0; b < VPT / R0; ++b) {
+            Dft<R0, INV, Cx>::run(va + b * R0);
+            Dft<R0, INV, Cx>::run(vb + b * R0);
+        }
+        stage_rest<1>(va, vb, sm, tw, tw_stride);
+    }
+};
+
+// 16-byte access to columns (c, c + 1) of a row of complex values.
+template <typename Cx>
+__device__ __forceinline__ void gld2(const Cx *p, Cx &a, Cx &b)
+{
+    if constexpr (sizeof(Cx) == 8) {
+        float4 q = __ldcs(reinterpret_cast<const float4 *>(p));
+        a = mk<Cx>(q.x, q.y);
+        b = mk<Cx>(q.z, q.w);
+    } else {
+        a = p[0];
+        b = p[1];
+    }
+}
+template <typename Cx>
+__device__ __forceinline__ void gst2(Cx *p, Cx a, Cx b)
+{
+    if constexpr (sizeof(Cx) == 8) {
+        *reinterpret_cast<float4 *>(p) = make_float4(a.x, a.y, b.x, b.y);
+    } else {
+        p[0] = a;
+        p[1] = b;
+    }
+}
 
 }  // namespace lh

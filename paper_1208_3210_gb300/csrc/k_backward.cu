@@ -405,8 +405,10 @@ cudaError_t launch_bw_product_t(const Geom &g, float2 *U2, const float2 *WU2, co
                                 cudaStream_t s)
 {
     constexpr int C = ColCfg<L>::C, T = ColCfg<L>::T;
-    using E = Fft<float, L, C, T, MAP_COL, false>;
-    size_t smem = sizeof(float2) * E::SMEM_ELEMS;
+    using EF = Fft<float, L, C, T, MAP_COL, false>;
+    using EI = Fft<float, L, C, T, MAP_COL, true>;
+    constexpr int elems = EF::SMEM_ELEMS > EI::SMEM_ELEMS ? EF::SMEM_ELEMS : EI::SMEM_ELEMS;
+    size_t smem = sizeof(float2) * elems;
     static const cudaError_t e = set_smem(k_bw_product<float, L>, smem);
     if (e != cudaSuccess) return e;
     k_bw_product<float, L><<<dim3((g.H + C - 1) / C, g.P), T, smem, s>>>(g, U2, WU2, tw, tw_len / L);

@@ -70,8 +70,10 @@ template <typename Real, int L>
 cudaError_t launch_x_product_t(const Geom &g, const Work<Real> &w, cudaStream_t s)
 {
     constexpr int C = ColCfg<L>::C, T = ColCfg<L>::T;
-    using E = Fft<Real, L, C, T, MAP_COL, false>;
-    size_t smem = sizeof(cx<Real>) * E::SMEM_ELEMS;
+    using EF = Fft<Real, L, C, T, MAP_COL, false>;
+    using EI = Fft<Real, L, C, T, MAP_COL, true>;
+    constexpr int elems = EF::SMEM_ELEMS > EI::SMEM_ELEMS ? EF::SMEM_ELEMS : EI::SMEM_ELEMS;
+    size_t smem = sizeof(cx<Real>) * elems;
     auto k = k_x_product<Real, L>;
     static const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

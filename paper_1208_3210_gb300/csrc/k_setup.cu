@@ -67,9 +67,11 @@ constexpr int MU_THREADS = 256;
 constexpr int MU_FP32_PASSES = 2;
 constexpr int MU_NEWTON = 3;
 constexpr int MU_RES = 16;   // result slots at the start of acc
+constexpr int MU_BAR_GEN = 32, MU_BAR_FAIL = 64, MU_BAR_WORDS = 96;   // barrier word offsets
 
 // Layout of acc: [MU_RES] results, then [MU_FP32_PASSES][G][MU_SECT], then [MU_NEWTON][G][2] doubles.
 size_t mu_acc_doubles(int G) { return MU_RES + (size_t)G * (MU_FP32_PASSES * MU_SECT + MU_NEWTON * 2); }
+size_t mu_barrier_words() { return MU_BAR_WORDS; }
 
 __device__ __forceinline__ double band_e0(const Band &b, const AxisTab &ax, const AxisTab &ay)
 {
@@ -87,9 +89,10 @@ __device__ __forceinline__ float band_e0f(int kind, const float *t32, const Axis
 }
 
 // Grid barrier whose last arriving CTA first runs `on_last` (with all its
-// threads) and then releases the others.  bar[0] counts arrivals, bar[1] is
-// the generation, bar[2] a failure flag; all three are zeroed before the
-// launch.  A waiting CTA records the generation before it arrives; the
+// threads) and then releases the others.  bar[0] counts arrivals, bar[32] is
+// the generation, bar[64] a failure flag (separate 128-byte lines, so that
+// the waiters' polling does not slow the arrivals' atomics); all are zeroed
+// before the launch.  A waiting CTA records the generation before it arrives; the
 // release (generation + 1) cannot happen before its arrival.  The wait is
 // bounded (about 1 s): on timeout the failure flag and the plan's status word
 // are set, and this and every later barrier of the launch return false.
@@ -98,8 +101,8 @@ __device__ bool grid_sync_reduce(unsigned *bar, unsigned *status, F &&on_last)
 {
     __shared__ int s_last, s_fail;
     __shared__ unsigned s_gen;
-    volatile unsigned *vgen = bar + 1;
-    volatile unsigned *vfail = bar + 2;
+    volatile unsigned *vgen = bar + MU_BAR_GEN;
+    volatile unsigned *vfail = bar + MU_BAR_FAIL;
     __syncthreads();
     if (threadIdx.x == 0) {
         s_fail = *vfail != 0;
@@ -120,14 +123,15 @@ __device__ bool grid_sync_reduce(unsigned *bar, unsigned *status, F &&on_last)
         if (threadIdx.x == 0) {
             atomicExch(bar, 0u);
             __threadfence();
-            atomicAdd(bar + 1, 1u);
+            atomicAdd(bar + MU_BAR_GEN, 1u);
         }
     } else if (threadIdx.x == 0) {
         long long t0 = clock64();
         while (*vgen == s_gen) {
             if (*vfail != 0) { s_fail = 1; break; }
+            __nanosleep(20);
             if (clock64() - t0 > 2000000000LL) {
-                atomicExch(bar + 2, 1u);
+                atomicExch(bar + MU_BAR_FAIL, 1u);
                 atomicCAS(status, (unsigned)DEV_OK, (unsigned)DEV_ETIMEOUT);
                 s_fail = 1;
                 break;
@@ -233,7 +237,8 @@ k_solve_mu(Geom g, Band band, const AxisTab *__restrict__ axis, InstState *st, d
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int it = 0; it < MU_NEWTON; ++it) {
         double f = 0.0, fp = 0.0;
-        for (int k = blockIdx.x * MU_THREADS + threadIdx.x; k < npts; k += G * MU_THREADS) {
+        // points interleaved over the CTAs, so every SM's FP64 units share the work
+        for (int k = threadIdx.x * G + blockIdx.x; k < npts; k += G * MU_THREADS) {
             int ix = base + k / g.npz, iy = base + k % g.npz;
             double xi = band_e0(band, axis[ix], axis[iy]) - mu;
             f += 0.5 - atan(xi / gd) * ipi;
@@ -309,7 +314,7 @@ int mu_grid_size(int num_sms, int npts)
 cudaError_t launch_solve_mu(const Geom &g, const Band &band, const AxisTab *axis, InstState *st, double *acc,
                             unsigned *bar, unsigned *status, double *mu_out, int G, cudaStream_t s)
 {
-    cudaError_t e = cudaMemsetAsync(bar, 0, 3 * sizeof(unsigned), s);
+    cudaError_t e = cudaMemsetAsync(bar, 0, MU_BAR_WORDS * sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(band.solve_mu ? G : 1);

@@ -30,6 +30,7 @@ cudaError_t launch_twiddles(int len, float2 *tw32, double2 *tw64, cudaStream_t s
 cudaError_t launch_tables(const Geom &g, const Band &band, AxisTab *axis, float2 *eps32, double *eps64,
                           cudaStream_t s);
 size_t mu_acc_doubles(int G);
+size_t mu_barrier_words();
 int mu_grid_size(int num_sms, int npts);
 cudaError_t launch_solve_mu(const Geom &g, const Band &band, const AxisTab *axis, InstState *st, double *acc,
                             unsigned *bar, unsigned *status, double *mu_out, int G, cudaStream_t s);
@@ -120,7 +121,7 @@ extern "C" lindhard_status lindhard_imchi_noalloc(const lindhard_grid *grid, con
     off_state = o; o = up256(o + sizeof(InstState));
     off_status = o; o = up256(o + sizeof(unsigned));
     off_acc = o; o = up256(o + mu_acc_doubles(G) * sizeof(double));
-    off_bar = o; o = up256(o + 3 * sizeof(unsigned));
+    off_bar = o; o = up256(o + mu_barrier_words() * sizeof(unsigned));
     if (o > (size_t)LINDHARD_NOALLOC_SCRATCH_BYTES) {
         char msg[160];
         snprintf(msg, sizeof msg, "grid needs %zu bytes of scratch; lindhard_imchi_noalloc has %zu",

@@ -18,6 +18,7 @@ cudaError_t launch_twiddles(int len, float2 *tw32, double2 *tw64, cudaStream_t s
 cudaError_t launch_tables(const Geom &g, const Band &band, AxisTab *axis, float2 *eps32, double *eps64,
                           cudaStream_t s);
 size_t mu_acc_doubles(int G);
+size_t mu_barrier_words();
 int mu_grid_size(int num_sms, int npts);
 cudaError_t launch_solve_mu(const Geom &g, const Band &band, const AxisTab *axis, InstState *st, double *acc,
                             unsigned *bar, unsigned *status, double *mu_out, int G, cudaStream_t s);
@@ -257,7 +258,7 @@ extern "C" lindhard_status lindhard_plan_create(const lindhard_grid *grids, int 
     p->off_state = o; o = align_up(o + sizeof(InstState));
     p->off_status = o; o = align_up(o + sizeof(unsigned));
     p->off_acc = o; o = align_up(o + mu_acc_doubles(p->mu_G) * sizeof(double));
-    p->off_bar = o; o = align_up(o + 3 * sizeof(unsigned));
+    p->off_bar = o; o = align_up(o + mu_barrier_words() * sizeof(unsigned));
     p->off_Z = o; o = align_up(o + maxZ);
     p->off_partial = o; o = align_up(o + maxPart);
     p->ws_bytes = o;
