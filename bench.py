@@ -312,7 +312,8 @@ def main():
     peak, peak_kind = measured_peaks()
     achieved = pb[dom] / (dom_ms * 1e-3) / 1e9
     traffic = None if args.grid else recorded_traffic(dom, args.workload)
-    launches = int(sum(v[1] for v in ptimes.values()))
+    # kernels launched in the timed region: each step is one forward call
+    launches = int(s.kernels_forward) * args.steps
     pipeline_bytes = sum(pb.values())
     step_ms = ms_total / args.steps
 

@@ -36,9 +36,9 @@
  * Work is enqueued on `stream` (a cudaStream_t; NULL = the legacy default
  * stream) and is asynchronous: the call returns once the work is enqueued.
  * Host-side argument errors are returned before anything is enqueued.
- * Errors found on the device (no chemical potential for the filling, a
- * bounded wait that timed out) are recorded in the plan and returned by
- * lindhard_plan_status(), which synchronises the stream.
+ * Errors found on the device (no chemical potential for the filling) are
+ * recorded in the plan and returned by lindhard_plan_status(), which
+ * synchronises the stream.
  * A plan is not thread-safe: use one plan per stream.
  */
 #ifndef LINDHARD_H
@@ -55,7 +55,7 @@ typedef enum {
     LINDHARD_EINVAL = 1,        /* an argument is out of range or NULL       */
     LINDHARD_ENOMEM = 2,        /* device or host allocation failed          */
     LINDHARD_ECUDA = 3,         /* a CUDA runtime call failed                */
-    LINDHARD_ETIMEOUT = 4,      /* a bounded device wait gave up             */
+    LINDHARD_ETIMEOUT = 4,      /* reserved (no kernel of this library waits) */
     LINDHARD_ENOCONV = 5,       /* no chemical potential for the filling     */
     LINDHARD_EUNSUPPORTED = 6   /* grid size or precision not built          */
 } lindhard_status;
@@ -106,7 +106,7 @@ typedef struct {
     long long out_elems;    /* q_extent^2 * n_omega                           */
     long long a_elems;      /* N^2 * n_eps (layout of A_in and dA)           */
     long long hbm_bytes_forward;  /* algorithmic HBM bytes of one forward call */
-    long long kernels_forward;    /* kernel launches of one forward call       */
+    long long kernels_forward;    /* kernel launches of one forward call (A generated, mu solved) */
 } lindhard_sizes;
 
 /* Plan flag: also allocate the buffers of lindhard_imchi_backward (one more

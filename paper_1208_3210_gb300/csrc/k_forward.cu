@@ -160,6 +160,46 @@ k_fwd_y(Geom g, const cx<Real> *__restrict__ U1, cx<Real> *__restrict__ U2,
     }
 }
 
+// Paired-column version of the p_y pass (L >= 128): each thread moves the two
+// adjacent columns (c, c + 1) with 16-byte accesses.
+template <typename Real, int L>
+__global__ void __launch_bounds__(PairCfg<L>::T, PairCfg<L>::MINB)
+k_fwd_y2(Geom g, const cx<Real> *__restrict__ U1, cx<Real> *__restrict__ U2,
+         const cx<Real> *__restrict__ tw, int tw_stride)
+{
+    constexpr int C = PairCfg<L>::C, T = PairCfg<L>::T;
+    using E = FftPair<Real, L, C, T, false>;
+    using Cx = cx<Real>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Cx *sm = reinterpret_cast<Cx *>(smem_raw);
+
+    const int W = 2 * g.SP;                       // row width (a^ and b^)
+    const int ix = blockIdx.y;
+    const int c = blockIdx.x * C + 2 * E::pair(); // first column of the pair
+    const bool valid = c < W && (c % g.SP) < g.H; // (c + 1 is in the same row)
+    const Cx *src = U1 + (long long)ix * g.N * W + c;
+    Cx *dst = U2 + (long long)ix * g.xs2 + c;
+    const Cx zero = mk<Cx>((Real)0, (Real)0);
+
+    Cx va[E::VPT], vb[E::VPT];
+#pragma unroll
+    for (int b = 0; b < E::VPT / E::R0; ++b)
+#pragma unroll
+        for (int r = 0; r < E::R0; ++r) {
+            int n = E::first_row(b, r);
+            if (valid && n < g.N) gld2(src + (long long)n * W, va[b * E::R0 + r], vb[b * E::R0 + r]);
+            else { va[b * E::R0 + r] = zero; vb[b * E::R0 + r] = zero; }
+        }
+    E::run(va, vb, sm, tw, tw_stride);
+    if (valid) {
+#pragma unroll
+        for (int b = 0; b < E::VPT / E::RL; ++b)
+#pragma unroll
+            for (int r = 0; r < E::RL; ++r)
+                gst2(dst + (long long)E::last_row(b, r) * W, va[b * E::RL + r], vb[b * E::RL + r]);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Launchers.
 template <typename Real, int L>
@@ -180,8 +220,23 @@ cudaError_t launch_fwd_energy_t(const Geom &g, const Band &band, const Work<Real
 }
 
 template <typename Real, int L>
+cudaError_t launch_fwd_y2_t(const Geom &g, const Work<Real> &w, cudaStream_t s)
+{
+    constexpr int C = PairCfg<L>::C, T = PairCfg<L>::T;
+    using E = FftPair<Real, L, C, T, false>;
+    size_t smem = sizeof(cx<Real>) * E::SMEM_ELEMS;
+    auto k = k_fwd_y2<Real, L>;
+    static const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((2 * g.SP + C - 1) / C, g.N);
+    k<<<grid, T, smem, s>>>(g, (const cx<Real> *)w.X, (cx<Real> *)w.Y, (const cx<Real> *)w.tw, w.tw_len / L);
+    return cudaGetLastError();
+}
+
+template <typename Real, int L>
 cudaError_t launch_fwd_y_t(const Geom &g, const Work<Real> &w, cudaStream_t s)
 {
+    if constexpr (L >= 128 && sizeof(Real) == 4) return launch_fwd_y2_t<Real, L>(g, w, s);
     constexpr int C = ColCfg<L>::C, T = ColCfg<L>::T;
     using E = Fft<Real, L, C, T, MAP_COL, false>;
     size_t smem = sizeof(cx<Real>) * E::SMEM_ELEMS;

@@ -54,6 +54,45 @@ k_inv_y(Geom g, const cx<Real> *__restrict__ U3, cx<Real> *__restrict__ U4,
     }
 }
 
+// Paired-column version of the inverse p_y pass (L >= 128).
+template <typename Real, int L>
+__global__ void __launch_bounds__(PairCfg<L>::T, PairCfg<L>::MINB)
+k_inv_y2(Geom g, const cx<Real> *__restrict__ U3, cx<Real> *__restrict__ U4,
+         const cx<Real> *__restrict__ tw, int tw_stride)
+{
+    constexpr int C = PairCfg<L>::C, T = PairCfg<L>::T;
+    using E = FftPair<Real, L, C, T, true>;
+    using Cx = cx<Real>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Cx *sm = reinterpret_cast<Cx *>(smem_raw);
+
+    const int lx = blockIdx.y;
+    const int c = blockIdx.x * C + 2 * E::pair();
+    const bool valid = c < g.H;                   // c + 1 < SP: the pair stays in the row
+    const Cx *src = U3 + (long long)lx * g.xs3 + c;
+    Cx *dst = U4 + (long long)lx * g.Q * g.SP + c;
+    const Cx zero = mk<Cx>((Real)0, (Real)0);
+
+    Cx va[E::VPT], vb[E::VPT];
+#pragma unroll
+    for (int b = 0; b < E::VPT / E::R0; ++b)
+#pragma unroll
+        for (int r = 0; r < E::R0; ++r) {
+            if (valid) gld2(src + (long long)E::first_row(b, r) * g.SP, va[b * E::R0 + r], vb[b * E::R0 + r]);
+            else { va[b * E::R0 + r] = zero; vb[b * E::R0 + r] = zero; }
+        }
+    E::run(va, vb, sm, tw, tw_stride);
+    if (valid) {
+#pragma unroll
+        for (int b = 0; b < E::VPT / E::RL; ++b)
+#pragma unroll
+            for (int r = 0; r < E::RL; ++r) {
+                int l = lag_index(E::last_row(b, r), g.P, g.Q);
+                if (l >= 0) gst2(dst + (long long)l * g.SP, va[b * E::RL + r], vb[b * E::RL + r]);
+            }
+    }
+}
+
 template <typename Real, typename OutT, int L>
 __global__ void __launch_bounds__(LineCfg<L>::T)
 k_inv_energy(Geom g, const cx<Real> *__restrict__ U4, OutT *__restrict__ out,
@@ -107,8 +146,23 @@ k_inv_energy(Geom g, const cx<Real> *__restrict__ U4, OutT *__restrict__ out,
 }
 
 template <typename Real, int L>
+cudaError_t launch_inv_y2_t(const Geom &g, const Work<Real> &w, cudaStream_t s)
+{
+    constexpr int C = PairCfg<L>::C, T = PairCfg<L>::T;
+    using E = FftPair<Real, L, C, T, true>;
+    size_t smem = sizeof(cx<Real>) * E::SMEM_ELEMS;
+    auto k = k_inv_y2<Real, L>;
+    static const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((g.H + C - 1) / C, g.Q);
+    k<<<grid, T, smem, s>>>(g, (const cx<Real> *)w.X, (cx<Real> *)w.Y, (const cx<Real> *)w.tw, w.tw_len / L);
+    return cudaGetLastError();
+}
+
+template <typename Real, int L>
 cudaError_t launch_inv_y_t(const Geom &g, const Work<Real> &w, cudaStream_t s)
 {
+    if constexpr (L >= 128 && sizeof(Real) == 4) return launch_inv_y2_t<Real, L>(g, w, s);
     constexpr int C = ColCfg<L>::C, T = ColCfg<L>::T;
     using E = Fft<Real, L, C, T, MAP_COL, true>;
     size_t smem = sizeof(cx<Real>) * E::SMEM_ELEMS;

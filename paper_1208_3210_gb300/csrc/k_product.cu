@@ -18,9 +18,12 @@ k_x_product(Geom g, const cx<Real> *__restrict__ U2, cx<Real> *__restrict__ U3,
             const cx<Real> *__restrict__ tw, int tw_stride)
 {
     constexpr int C = ColCfg<L>::C, T = ColCfg<L>::T;
-    using EF = Fft<Real, L, C, T, MAP_COL, false>;
+    // forward: a^ and b^ of the same column as one pair (shared twiddles and
+    // barriers, two dependency chains per thread); inverse: the product alone
+    using EF = FftPair<Real, L, 2 * C, T, false>;
     using EI = Fft<Real, L, C, T, MAP_COL, true>;
     static_assert(EF::RL == EI::R0, "last forward radix must equal first inverse radix");
+    static_assert(EF::VPT == EI::VPT && EF::CP == C, "forward pairs and inverse columns must coincide");
     using Cx = cx<Real>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Cx *sm = reinterpret_cast<Cx *>(smem_raw);
@@ -39,14 +42,12 @@ k_x_product(Geom g, const cx<Real> *__restrict__ U2, cx<Real> *__restrict__ U3,
     for (int b = 0; b < EF::VPT / EF::R0; ++b)
 #pragma unroll
         for (int r = 0; r < EF::R0; ++r) {
-            int col, n;
-            EF::first_elem(b, r, col, n);
+            int n = EF::first_row(b, r);
             bool ld = valid && n < g.N;
             va[b * EF::R0 + r] = ld ? srcA[(long long)n * rstride] : zero;
             vb[b * EF::R0 + r] = ld ? srcB[(long long)n * rstride] : zero;
         }
-    EF::run(va, sm, tw, tw_stride);
-    EF::run(vb, sm, tw, tw_stride);
+    EF::run(va, vb, sm, tw, tw_stride);
     // conj(a^) * b^ : transform of the correlation sum_p a(p) b(p + q)
 #pragma unroll
     for (int i = 0; i < EF::VPT; ++i) va[i] = cmulc(vb[i], va[i]);

@@ -21,6 +21,17 @@ template <> struct ColCfg<1024> { static constexpr int C = 8, T = 512, MINB = 2,
 template <> struct ColCfg<2048> { static constexpr int C = 4, T = 512, MINB = 2, MINB_X = 1; };
 template <> struct ColCfg<4096> { static constexpr int C = 4, T = 1024, MINB = 1, MINB_X = 1; };
 
+// Strided-axis passes on the paired-column engine (FftPair): C adjacent
+// columns per CTA as C/2 pairs, VPT = (C/2) L / T = 16 values per thread per
+// column.  Used for L >= 128.
+template <int L> struct PairCfg;
+template <> struct PairCfg<128>  { static constexpr int C = 16, T = 64, MINB = 4; };
+template <> struct PairCfg<256>  { static constexpr int C = 16, T = 128, MINB = 4; };
+template <> struct PairCfg<512>  { static constexpr int C = 16, T = 256, MINB = 2; };
+template <> struct PairCfg<1024> { static constexpr int C = 16, T = 512, MINB = 1; };
+template <> struct PairCfg<2048> { static constexpr int C = 8, T = 512, MINB = 1; };
+template <> struct PairCfg<4096> { static constexpr int C = 8, T = 1024, MINB = 1; };
+
 // Contiguous-axis passes (energy axis): C lines of length L per CTA.
 template <int L> struct LineCfg;
 template <> struct LineCfg<16>   { static constexpr int C = 64, T = 64; };

@@ -65,7 +65,7 @@ struct Work {
     InstState *state;      // [1]
     unsigned *status;      // plan-wide device status word
     double *mu_acc;        // scratch for the chemical potential solve
-    unsigned *barrier;     // grid barrier words: counter, generation, failure flag
+    unsigned *barrier;     // arrival counter of the chemical-potential launches
 };
 
 }  // namespace lh

@@ -142,11 +142,11 @@ extern "C" lindhard_status lindhard_imchi_noalloc(const lindhard_grid *grid, con
     w.barrier = (unsigned *)(base + off_bar);
 
     // The array keeps the previous call's contents: the status word and the
-    // grid-barrier words must start at zero (the barrier is cleared by the
-    // chemical-potential launch itself); everything else is written before it
-    // is read.
+    // chemical-potential launches' arrival counter must start at zero;
+    // everything else is written before it is read.
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaMemsetAsync(w.status, 0, sizeof(unsigned), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(w.barrier, 0, mu_barrier_words() * sizeof(unsigned), s);
     if (e == cudaSuccess) e = launch_twiddles(tw_len, (float2 *)(base + off_tw32), (double2 *)(base + off_tw64), s);
     if (e == cudaSuccess && A_in == nullptr) {
         e = launch_tables(g, b, w.axis, (float2 *)w.eps, nullptr, s);

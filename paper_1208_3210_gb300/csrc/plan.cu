@@ -269,6 +269,7 @@ extern "C" lindhard_status lindhard_plan_create(const lindhard_grid *grids, int 
         return fail(LINDHARD_ENOMEM, std::string("workspace cudaMalloc failed: ") + cudaGetErrorString(e));
     }
     e = cudaMemset(p->ws + p->off_status, 0, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(p->ws + p->off_bar, 0, mu_barrier_words() * sizeof(unsigned));
     if (e == cudaSuccess)
         e = launch_twiddles(p->tw_len, (float2 *)(p->ws + p->off_tw32), (double2 *)(p->ws + p->off_tw64), 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -302,7 +303,7 @@ extern "C" lindhard_status lindhard_plan_sizes(const lindhard_plan *p, int index
     long long W3 = (long long)g.Q * g.P * g.H;
     long long W4 = (long long)g.Q * g.Q * g.H;
     out->hbm_bytes_forward = 2 * (W1 + W2 + W3 + W4) * cb + out->out_elems * rb;
-    out->kernels_forward = 7;
+    out->kernels_forward = 11;   // tables, 5 chemical-potential launches, 5 FFT passes
     return LINDHARD_OK;
 }
 
