@@ -39,6 +39,7 @@ k_w_energy(Geom g, const Real *__restrict__ w, cx<Real> *__restrict__ WU1, const
     constexpr int H = L / 2 + 1, SP = (H + 7) / 8 * 8;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Cx *sm = reinterpret_cast<Cx *>(smem_raw);
+    LH_REQUIRE_SMEM(E::SMEM_ELEMS, Cx)
     const long long npairs = (long long)g.Q * g.Q / 2;
     const long long f0 = (long long)blockIdx.x * C;
 
@@ -93,6 +94,7 @@ k_w_y(Geom g, const cx<Real> *__restrict__ WU1, cx<Real> *__restrict__ WU2, cons
     using Cx = cx<Real>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Cx *sm = reinterpret_cast<Cx *>(smem_raw);
+    LH_REQUIRE_SMEM(E::SMEM_ELEMS, Cx)
     const int lx = blockIdx.y;
     const int c = blockIdx.x * C + (int)(threadIdx.x % C);
     const bool valid = c < g.H;
@@ -134,6 +136,7 @@ k_bw_product(Geom g, cx<Real> *__restrict__ U2, const cx<Real> *__restrict__ WU2
     using Cx = cx<Real>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Cx *sm = reinterpret_cast<Cx *>(smem_raw);
+    LH_REQUIRE_SMEM((EF::SMEM_ELEMS > EI::SMEM_ELEMS ? EF::SMEM_ELEMS : EI::SMEM_ELEMS), Cx)
     const int W2 = 2 * g.SP;
     const int ky = blockIdx.y;
     const int c = blockIdx.x * C + (int)(threadIdx.x % C);
@@ -206,6 +209,7 @@ k_bw_inv_y(Geom g, const cx<Real> *__restrict__ G3, cx<Real> *__restrict__ G4, c
     using Cx = cx<Real>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Cx *sm = reinterpret_cast<Cx *>(smem_raw);
+    LH_REQUIRE_SMEM(E::SMEM_ELEMS, Cx)
     const int W2 = 2 * g.SP;
     const int px = blockIdx.y;
     const int c = blockIdx.x * C + (int)(threadIdx.x % C);
@@ -249,6 +253,7 @@ k_bw_inv_energy(Geom g, Band band, const AxisTab *__restrict__ axis,
     constexpr int H = L / 2 + 1, SP = (H + 7) / 8 * 8;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Cx *sm = reinterpret_cast<Cx *>(smem_raw);
+    LH_REQUIRE_SMEM(E::SMEM_ELEMS, Cx)
     __shared__ Real s_xhi[C], s_xlo[C], s_amp[C], s_f[C][4];
     __shared__ double s_red[T / 32][5];
     const long long nlines = (long long)g.N * g.N;

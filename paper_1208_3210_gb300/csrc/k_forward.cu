@@ -28,6 +28,7 @@ k_fwd_energy(Geom g, Band band, const AxisTab *__restrict__ axis,
     using Cx = cx<Real>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Cx *sm = reinterpret_cast<Cx *>(smem_raw);
+    LH_REQUIRE_SMEM(E::SMEM_ELEMS, Cx)
     __shared__ Real s_xhi[C], s_xlo[C], s_amp[C];
 
     const long long nlines = (long long)g.N * g.N;
@@ -130,6 +131,7 @@ k_fwd_y(Geom g, const cx<Real> *__restrict__ U1, cx<Real> *__restrict__ U2,
     using Cx = cx<Real>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Cx *sm = reinterpret_cast<Cx *>(smem_raw);
+    LH_REQUIRE_SMEM(E::SMEM_ELEMS, Cx)
 
     const int W = 2 * g.SP;                       // row width (a^ and b^)
     const int ix = blockIdx.y;
@@ -172,6 +174,7 @@ k_fwd_y2(Geom g, const cx<Real> *__restrict__ U1, cx<Real> *__restrict__ U2,
     using Cx = cx<Real>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Cx *sm = reinterpret_cast<Cx *>(smem_raw);
+    LH_REQUIRE_SMEM(E::SMEM_ELEMS, Cx)
 
     const int W = 2 * g.SP;                       // row width (a^ and b^)
     const int ix = blockIdx.y;

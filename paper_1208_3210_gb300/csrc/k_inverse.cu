@@ -24,6 +24,7 @@ k_inv_y(Geom g, const cx<Real> *__restrict__ U3, cx<Real> *__restrict__ U4,
     using Cx = cx<Real>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Cx *sm = reinterpret_cast<Cx *>(smem_raw);
+    LH_REQUIRE_SMEM(E::SMEM_ELEMS, Cx)
 
     const int lx = blockIdx.y;
     const int c = blockIdx.x * C + (int)(threadIdx.x % C);
@@ -65,6 +66,7 @@ k_inv_y2(Geom g, const cx<Real> *__restrict__ U3, cx<Real> *__restrict__ U4,
     using Cx = cx<Real>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Cx *sm = reinterpret_cast<Cx *>(smem_raw);
+    LH_REQUIRE_SMEM(E::SMEM_ELEMS, Cx)
 
     const int lx = blockIdx.y;
     const int c = blockIdx.x * C + 2 * E::pair();
@@ -103,6 +105,7 @@ k_inv_energy(Geom g, const cx<Real> *__restrict__ U4, OutT *__restrict__ out,
     using Cx = cx<Real>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Cx *sm = reinterpret_cast<Cx *>(smem_raw);
+    LH_REQUIRE_SMEM(E::SMEM_ELEMS, Cx)
 
     const long long npairs = (long long)g.Q * g.Q / 2;
     const long long f0 = (long long)blockIdx.x * C;

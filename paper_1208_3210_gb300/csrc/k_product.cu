@@ -12,21 +12,32 @@
 
 namespace lh {
 
+// Engines of the product pass, shared by the kernel and its launcher.
+// Forward: a^ and b^ of the same column as one pair (shared twiddles and
+// barriers, two dependency chains per thread); inverse: the product alone.
+template <typename Real, int L>
+struct XProduct {
+    static constexpr int C = ColCfg<L>::C, T = ColCfg<L>::T;
+    using EF = FftPair<Real, L, 2 * C, T, false>;
+    using EI = Fft<Real, L, C, T, MAP_COL, true>;
+    static_assert(EF::RL == EI::R0, "last forward radix must equal first inverse radix");
+    static_assert(EF::VPT == EI::VPT && EF::CP == C, "forward pairs and inverse columns must coincide");
+    static constexpr int SMEM_ELEMS = EF::SMEM_ELEMS > EI::SMEM_ELEMS ? EF::SMEM_ELEMS : EI::SMEM_ELEMS;
+};
+
 template <typename Real, int L>
 __global__ void __launch_bounds__(ColCfg<L>::T, ColCfg<L>::MINB_X)
 k_x_product(Geom g, const cx<Real> *__restrict__ U2, cx<Real> *__restrict__ U3,
             const cx<Real> *__restrict__ tw, int tw_stride)
 {
-    constexpr int C = ColCfg<L>::C, T = ColCfg<L>::T;
-    // forward: a^ and b^ of the same column as one pair (shared twiddles and
-    // barriers, two dependency chains per thread); inverse: the product alone
-    using EF = FftPair<Real, L, 2 * C, T, false>;
-    using EI = Fft<Real, L, C, T, MAP_COL, true>;
-    static_assert(EF::RL == EI::R0, "last forward radix must equal first inverse radix");
-    static_assert(EF::VPT == EI::VPT && EF::CP == C, "forward pairs and inverse columns must coincide");
+    using XP = XProduct<Real, L>;
+    constexpr int C = XP::C;
+    using EF = typename XP::EF;
+    using EI = typename XP::EI;
     using Cx = cx<Real>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Cx *sm = reinterpret_cast<Cx *>(smem_raw);
+    LH_REQUIRE_SMEM(XP::SMEM_ELEMS, Cx)
 
     const int W = 2 * g.SP;
     const int ky = blockIdx.y;
@@ -70,11 +81,9 @@ k_x_product(Geom g, const cx<Real> *__restrict__ U2, cx<Real> *__restrict__ U3,
 template <typename Real, int L>
 cudaError_t launch_x_product_t(const Geom &g, const Work<Real> &w, cudaStream_t s)
 {
-    constexpr int C = ColCfg<L>::C, T = ColCfg<L>::T;
-    using EF = Fft<Real, L, C, T, MAP_COL, false>;
-    using EI = Fft<Real, L, C, T, MAP_COL, true>;
-    constexpr int elems = EF::SMEM_ELEMS > EI::SMEM_ELEMS ? EF::SMEM_ELEMS : EI::SMEM_ELEMS;
-    size_t smem = sizeof(cx<Real>) * elems;
+    using XP = XProduct<Real, L>;
+    constexpr int C = XP::C, T = XP::T;
+    size_t smem = sizeof(cx<Real>) * XP::SMEM_ELEMS;
     auto k = k_x_product<Real, L>;
     static const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

@@ -49,6 +49,20 @@ template <typename Real> struct EpsEntry;
 template <> struct EpsEntry<float> { using type = float2; };
 template <> struct EpsEntry<double> { using type = double; };
 
+// Bytes of dynamic shared memory this launch was given.  Every FFT kernel
+// compares it with what its engines address and returns before touching
+// memory when it is short, so a launch configured with too little shared
+// memory gives wrong results (caught by the tests) instead of an
+// out-of-bounds access.
+__device__ __forceinline__ unsigned dyn_smem_bytes()
+{
+    unsigned r;
+    asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(r));
+    return r;
+}
+#define LH_REQUIRE_SMEM(elems, Cx) \
+    if (dyn_smem_bytes() < (unsigned)((elems) * sizeof(Cx))) return;
+
 // Circular index n of an inverse transform of length P -> output lag index
 // l in [0, Q), or -1 when the lag is not kept.
 __device__ __forceinline__ int lag_index(int n, int P, int Q)
