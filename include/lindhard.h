@@ -113,15 +113,26 @@ typedef struct {
  * intermediate of Q x P x (PE/2 + 1) complex values and the per-CTA gradient
  * partial sums). */
 #define LINDHARD_PLAN_BACKWARD 1u
+/* Plan flag: one workspace per instance, and the instances of a call run as
+ * independent branches on the plan's own streams (forked from and joined back
+ * into the caller's stream), so small instances share the GPU. */
+#define LINDHARD_PLAN_CONCURRENT 2u
+/* Plan flag (implies LINDHARD_PLAN_CONCURRENT): lindhard_imchi records its
+ * whole launch sequence for all instances once into a CUDA graph and replays
+ * it; a call whose A_in, out, mu_out or band values differ from the recorded
+ * ones records again (and updates the executable graph in place).  The first
+ * call also runs the sequence once directly. */
+#define LINDHARD_PLAN_GRAPH 4u
 
 /* Builds a plan for `batch` instances with the given grids (host array).
  * Validates the grids, picks FFT lengths (the smallest supported length that
  * keeps the circular correlation free of wrap-around: >= N + Q/2 per momentum
  * axis in the extended zone, N in the reduced zone, >= n_eps in energy), and
  * allocates the device workspace and twiddle tables on the current device.
- * Instances are computed one after another and share one workspace sized for
- * the largest.  flags: 0 or LINDHARD_PLAN_BACKWARD.  On success *out receives
- * the plan. */
+ * Without LINDHARD_PLAN_CONCURRENT instances are computed one after another
+ * and share one workspace sized for the largest.  flags: any of
+ * LINDHARD_PLAN_BACKWARD, LINDHARD_PLAN_CONCURRENT, LINDHARD_PLAN_GRAPH.
+ * On success *out receives the plan. */
 lindhard_status lindhard_plan_create(const lindhard_grid *grids, int batch,
                                      unsigned flags, lindhard_plan **out);
 
@@ -174,9 +185,10 @@ lindhard_status lindhard_imchi_backward(lindhard_plan *plan,
                                         const float *A_in, const float *w,
                                         float *dA, double *dparams, void *stream);
 
-/* Per-pass timing.  With enable != 0 the plan records a CUDA event pair on
- * the call's stream around each of its kernel launches (profiling); enable = 0
- * stops recording.  Either call clears the accumulated times. */
+/* Per-pass timing (sequential plans only).  With enable != 0 the plan
+ * records a CUDA event pair on the call's stream around each of its kernel
+ * launches (profiling); enable = 0 stops recording.  Either call clears the
+ * accumulated times. */
 lindhard_status lindhard_plan_profile(lindhard_plan *plan, int enable);
 
 /* Kernels of one forward call, in launch order (the slots of

@@ -76,14 +76,28 @@ __device__ __forceinline__ double band_e0(const Band &b, const AxisTab &ax, cons
     if (b.band_kind == 1) return 0.5 * (ax.p2 + ay.p2);
     return -2.0 * b.t * (ax.c1 + ay.c1) - 4.0 * b.tp * ax.c1 * ay.c1 - 2.0 * b.tpp * (ax.c2 + ay.c2);
 }
-// FP32 band energy from the FP32 table copies; t32 = (t, t', t'') in FP32.
-__device__ __forceinline__ float band_e0f(int kind, const float *t32, const AxisTab *__restrict__ axis, int ix,
-                                          int iy)
+// The first-zone axis values a CTA needs, staged once in shared memory
+// (pts_per_zone <= 512 for the filling solve).
+constexpr int MU_MAXZ = 512;
+struct ZoneAxis {
+    float c1[MU_MAXZ], c2[MU_MAXZ], p2[MU_MAXZ];
+};
+__device__ __forceinline__ void stage_zone_axis(const Geom &g, const AxisTab *__restrict__ axis, ZoneAxis &z)
 {
-    const float4 ax = *reinterpret_cast<const float4 *>(&axis[ix].c1f);
-    const float4 ay = *reinterpret_cast<const float4 *>(&axis[iy].c1f);
-    if (kind == 1) return 0.5f * (ax.z + ay.z);
-    return -2.0f * t32[0] * (ax.x + ay.x) - 4.0f * t32[1] * ax.x * ay.x - 2.0f * t32[2] * (ax.y + ay.y);
+    const int base = g.N / 2 - g.npz / 2;
+    for (int i = threadIdx.x; i < g.npz; i += blockDim.x) {
+        z.c1[i] = axis[base + i].c1f;
+        z.c2[i] = axis[base + i].c2f;
+        z.p2[i] = axis[base + i].p2f;
+    }
+    __syncthreads();
+}
+// FP32 band energy of first-zone point (i, j); t32 = (t, t', t'') in FP32.
+__device__ __forceinline__ float band_e0f(int kind, const float *t32, const ZoneAxis &z, int i, int j)
+{
+    if (kind == 1) return 0.5f * (z.p2[i] + z.p2[j]);
+    return -2.0f * t32[0] * (z.c1[i] + z.c1[j]) - 4.0f * t32[1] * z.c1[i] * z.c1[j]
+           - 2.0f * t32[2] * (z.c2[i] + z.c2[j]);
 }
 
 // True in every thread of the CTA that finishes last; that CTA resets the
@@ -114,7 +128,6 @@ k_mu_sect(Geom g, Band band, const AxisTab *__restrict__ axis, double *acc, unsi
 {
     const int G = gridDim.x;
     const int npts = g.npz * g.npz;
-    const int base = g.N / 2 - g.npz / 2;       // first-zone indices on the grid
     const double target = band.filling * 0.5 * (double)npts;  // sum of occupations
     double *res = acc;
     double *part = acc + MU_RES + (size_t)pass * G * MU_SECT;
@@ -137,11 +150,14 @@ k_mu_sect(Geom g, Band band, const AxisTab *__restrict__ axis, double *acc, unsi
     const float t32[3] = {(float)band.t, (float)band.tp, (float)band.tpp};
     const double h = (hi - lo) / (MU_SECT - 1);
     const float mu_c = (float)(lo + cand * h);
+    const float inv_gam = 1.0f / gam;
+    __shared__ ZoneAxis za;
+    stage_zone_axis(g, axis, za);
     float sum = 0.f;
 #pragma unroll 4
     for (int k = pg; k < npts; k += npg) {
-        int ix = base + k / g.npz, iy = base + k % g.npz;
-        sum += 0.5f - atanf((band_e0f(band.band_kind, t32, axis, ix, iy) - mu_c) / gam) * inv_pi;
+        int i = k / g.npz, j = k % g.npz;
+        sum += 0.5f - atanf((band_e0f(band.band_kind, t32, za, i, j) - mu_c) * inv_gam) * inv_pi;
     }
     s_tot[grp][cand] = sum;
     __syncthreads();

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "_build", "liblindhard.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOCONV, EUNSUPPORTED = range(7)
 FP32, FP64 = 0, 2
-PLAN_BACKWARD = 1
+PLAN_BACKWARD, PLAN_CONCURRENT, PLAN_GRAPH = 1, 2, 4
 _STATUS_NAMES = {OK: "OK", EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", ETIMEOUT: "ETIMEOUT",
                  ENOCONV: "ENOCONV", EUNSUPPORTED: "EUNSUPPORTED"}
 
@@ -130,14 +130,17 @@ class Plan:
     """A lindhard_plan for one or more instance grids (dicts with zones, npz,
     n_eps, e_max and optional n_omega, q_extent, precision)."""
 
-    def __init__(self, grids: Sequence[dict], precision: int = FP32, backward: bool = False):
+    def __init__(self, grids: Sequence[dict], precision: int = FP32, backward: bool = False,
+                 concurrent: bool = False, graph: bool = False):
         lib = load()
         self.grids = [make_grid(g["zones"], g["npz"], g["n_eps"], g["e_max"], g.get("n_omega", 0),
                                 g.get("q_extent", 0), g.get("precision", precision)) for g in grids]
         self.batch = len(self.grids)
         arr = (Grid * self.batch)(*self.grids)
         h = ctypes.c_void_p()
-        _check(lib.lindhard_plan_create(arr, self.batch, PLAN_BACKWARD if backward else 0, ctypes.byref(h)))
+        flags = (PLAN_BACKWARD if backward else 0) | (PLAN_CONCURRENT if concurrent else 0) | \
+            (PLAN_GRAPH if graph else 0)
+        _check(lib.lindhard_plan_create(arr, self.batch, flags, ctypes.byref(h)))
         self._h = h
         self.sizes = []
         for i in range(self.batch):

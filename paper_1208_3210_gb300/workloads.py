@@ -75,6 +75,12 @@ def batched_instances(count=64, seed=0):
     return out
 
 
+def batched_workload(count=64, seed=0):
+    """(grids, bands) of the batched workload, in instance order."""
+    inst = batched_instances(count, seed)
+    return [x["grid"] for x in inst], [x["band"] for x in inst]
+
+
 def loss_weights(grid, seed=0, dtype=np.float32):
     """w(q_l, w_m) ~ U[0, 1], shape [Q, Q, n_omega], for L = sum w Im chi."""
     rng = np.random.default_rng(seed)
