@@ -80,8 +80,13 @@ def measured_peaks():
 
 
 def source_digest(fname):
-    with open(os.path.join(ROOT, "paper_1208_3210_gb300", "csrc", fname), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    """Hash of a pass's kernel source together with the headers every kernel
+    includes (FFT engine, tile configurations, shared types)."""
+    h = hashlib.sha256()
+    for f in (fname, "fft_engine.cuh", "kernels.cuh", "lindhard_internal.h"):
+        with open(os.path.join(ROOT, "paper_1208_3210_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def recorded_traffic(pass_name, workload):

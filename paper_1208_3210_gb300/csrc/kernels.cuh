@@ -8,26 +8,27 @@ namespace lh {
 
 // Strided-axis passes (momentum axes): C columns x L rows per CTA, T threads,
 // VPT = C L / T = 16 values per thread (32 registers of data per transform),
-// so several CTAs share an SM and hide each other's barrier and load latency.
-// MINB is the CTAs per SM the register budget aims at.
+// 8 for L = 512 (radix 8 x 8 x 8), so several CTAs share an SM and hide each
+// other's barrier and load latency.  MINB is the CTAs per SM the register
+// budget aims at.
 template <int L> struct ColCfg;
 template <> struct ColCfg<16>   { static constexpr int C = 32, T = 32, MINB = 4, MINB_X = 4; };
 template <> struct ColCfg<32>   { static constexpr int C = 32, T = 64, MINB = 4, MINB_X = 4; };
 template <> struct ColCfg<64>   { static constexpr int C = 16, T = 64, MINB = 4, MINB_X = 4; };
 template <> struct ColCfg<128>  { static constexpr int C = 16, T = 128, MINB = 4, MINB_X = 3; };
 template <> struct ColCfg<256>  { static constexpr int C = 16, T = 256, MINB = 3, MINB_X = 2; };
-template <> struct ColCfg<512>  { static constexpr int C = 8, T = 256, MINB = 3, MINB_X = 2; };
+template <> struct ColCfg<512>  { static constexpr int C = 8, T = 512, MINB = 2, MINB_X = 2; };  // VPT 8
 template <> struct ColCfg<1024> { static constexpr int C = 8, T = 512, MINB = 2, MINB_X = 1; };
 template <> struct ColCfg<2048> { static constexpr int C = 4, T = 512, MINB = 2, MINB_X = 1; };
 template <> struct ColCfg<4096> { static constexpr int C = 4, T = 1024, MINB = 1, MINB_X = 1; };
 
 // Strided-axis passes on the paired-column engine (FftPair): C adjacent
 // columns per CTA as C/2 pairs, VPT = (C/2) L / T = 16 values per thread per
-// column.  Used for L >= 128.
+// column (8 for L = 512).  Used for L >= 128.
 template <int L> struct PairCfg;
 template <> struct PairCfg<128>  { static constexpr int C = 16, T = 64, MINB = 4; };
 template <> struct PairCfg<256>  { static constexpr int C = 16, T = 128, MINB = 4; };
-template <> struct PairCfg<512>  { static constexpr int C = 16, T = 256, MINB = 2; };
+template <> struct PairCfg<512>  { static constexpr int C = 16, T = 512, MINB = 2; };  // VPT 8
 template <> struct PairCfg<1024> { static constexpr int C = 16, T = 512, MINB = 1; };
 template <> struct PairCfg<2048> { static constexpr int C = 8, T = 512, MINB = 1; };
 template <> struct PairCfg<4096> { static constexpr int C = 8, T = 1024, MINB = 1; };
