@@ -206,7 +206,7 @@ struct Fft {
     }
 
     template <int S>
-    __device__ __forceinline__ static void stage_rest(Cx *v, Cx *sm, const Cx *__restrict__ tw, int tw_stride)
+    __device__ __forceinline__ static void stage_rest(Cx *v, Cx *sm, const Cx *__restrict__ tw)
     {
         if constexpr (S < NS) {
             constexpr int Rp = fft_radix(L, S - 1, INV);
@@ -230,27 +230,28 @@ struct Fft {
 #pragma unroll
                 for (int r = 0; r < Rs; ++r) v[b * Rs + r] = sm[saddr(col, j + r * (L / Rs))];
                 int k = j % Ns;
-                // twiddle exp(-+ 2 pi i k r / (Ns Rs)) from the table of exp(-2 pi i n / (L tw_stride))
+                // twiddle exp(-+ 2 pi i k r / (Ns Rs)) from the length-L table exp(-2 pi i n / L)
 #pragma unroll
                 for (int r = 1; r < Rs; ++r) {
-                    Cx w = __ldg(&tw[(size_t)(k * r * (L / (Ns * Rs))) * tw_stride]);
+                    Cx w = __ldg(&tw[k * r * (L / (Ns * Rs))]);
                     v[b * Rs + r] = INV ? cmulc(v[b * Rs + r], w) : cmul(v[b * Rs + r], w);
                 }
                 Dft<Rs, INV, Cx>::run(v + b * Rs);
             }
             __syncthreads();
-            stage_rest<S + 1>(v, sm, tw, tw_stride);
+            stage_rest<S + 1>(v, sm, tw);
         }
     }
 
     // Transform the tile in place: v holds the first-stage inputs (see
     // first_elem) on entry and the outputs (see last_elem) on exit.  sm must
-    // hold SMEM_ELEMS elements; the call ends with a __syncthreads().
-    __device__ __forceinline__ static void run(Cx *v, Cx *sm, const Cx *__restrict__ tw, int tw_stride)
+    // hold SMEM_ELEMS elements; tw is the length-L table exp(-2 pi i n / L);
+    // the call ends with a __syncthreads().
+    __device__ __forceinline__ static void run(Cx *v, Cx *sm, const Cx *__restrict__ tw)
     {
 #pragma unroll
         for (int b = 0; b < VPT / R0; ++b) Dft<R0, INV, Cx>::run(v + b * R0);
-        stage_rest<1>(v, sm, tw, tw_stride);
+        stage_rest<1>(v, sm, tw);
     }
 };
 
@@ -315,7 +316,7 @@ struct FftPair {
     }
 
     template <int S>
-    __device__ __forceinline__ static void stage_rest(Cx *va, Cx *vb, Cx *sm, const Cx *__restrict__ tw, int tw_stride)
+    __device__ __forceinline__ static void stage_rest(Cx *va, Cx *vb, Cx *sm, const Cx *__restrict__ tw)
     {
         if constexpr (S < NS) {
             constexpr int Rp = fft_radix(L, S - 1, INV);
@@ -339,7 +340,7 @@ struct FftPair {
                 int k = j % Ns;
 #pragma unroll
                 for (int r = 1; r < Rs; ++r) {
-                    Cx w = __ldg(&tw[(size_t)(k * r * (L / (Ns * Rs))) * tw_stride]);
+                    Cx w = __ldg(&tw[k * r * (L / (Ns * Rs))]);
                     va[b * Rs + r] = INV ? cmulc(va[b * Rs + r], w) : cmul(va[b * Rs + r], w);
                     vb[b * Rs + r] = INV ? cmulc(vb[b * Rs + r], w) : cmul(vb[b * Rs + r], w);
                 }
@@ -347,20 +348,20 @@ struct FftPair {
                 Dft<Rs, INV, Cx>::run(vb + b * Rs);
             }
             __syncthreads();
-            stage_rest<S + 1>(va, vb, sm, tw, tw_stride);
+            stage_rest<S + 1>(va, vb, sm, tw);
         }
     }
 
     // Transform both columns in place (inputs per first_row, outputs per
     // last_row); ends with a __syncthreads().
-    __device__ __forceinline__ static void run(Cx *va, Cx *vb, Cx *sm, const Cx *__restrict__ tw, int tw_stride)
+    __device__ __forceinline__ static void run(Cx *va, Cx *vb, Cx *sm, const Cx *__restrict__ tw)
     {
 #pragma unroll
         for (int b = 0; b < VPT / R0; ++b) {
             Dft<R0, INV, Cx>::run(va + b * R0);
             Dft<R0, INV, Cx>::run(vb + b * R0);
         }
-        stage_rest<1>(va, vb, sm, tw, tw_stride);
+        stage_rest<1>(va, vb, sm, tw);
     }
 };
 

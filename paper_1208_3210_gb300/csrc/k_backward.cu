@@ -30,8 +30,7 @@ namespace lh {
 // --- w along energy -----------------------------------------------------------
 template <typename Real, int L>
 __global__ void __launch_bounds__(LineCfg<L>::T)
-k_w_energy(Geom g, const Real *__restrict__ w, cx<Real> *__restrict__ WU1, const cx<Real> *__restrict__ tw,
-           int tw_stride)
+k_w_energy(Geom g, const Real *__restrict__ w, cx<Real> *__restrict__ WU1, const cx<Real> *__restrict__ tw)
 {
     constexpr int C = LineCfg<L>::C, T = LineCfg<L>::T;
     using E = Fft<Real, L, C, T, MAP_LINE, false>;
@@ -58,7 +57,7 @@ k_w_energy(Geom g, const Real *__restrict__ w, cx<Real> *__restrict__ WU1, const
             }
             v[b * E::R0 + r] = mk<Cx>(x1, x2);
         }
-    E::run(v, sm, tw, tw_stride);
+    E::run(v, sm, tw);
 #pragma unroll
     for (int b = 0; b < E::VPT / E::RL; ++b)
 #pragma unroll
@@ -86,8 +85,7 @@ k_w_energy(Geom g, const Real *__restrict__ w, cx<Real> *__restrict__ WU1, const
 // --- w along q_y ----------------------------------------------------------------
 template <typename Real, int L>
 __global__ void __launch_bounds__(ColCfg<L>::T, ColCfg<L>::MINB)
-k_w_y(Geom g, const cx<Real> *__restrict__ WU1, cx<Real> *__restrict__ WU2, const cx<Real> *__restrict__ tw,
-      int tw_stride)
+k_w_y(Geom g, const cx<Real> *__restrict__ WU1, cx<Real> *__restrict__ WU2, const cx<Real> *__restrict__ tw)
 {
     constexpr int C = ColCfg<L>::C, T = ColCfg<L>::T;
     using E = Fft<Real, L, C, T, MAP_COL, false>;
@@ -110,7 +108,7 @@ k_w_y(Geom g, const cx<Real> *__restrict__ WU1, cx<Real> *__restrict__ WU2, cons
             int l = lag_index(n, g.P, g.Q);
             v[b * E::R0 + r] = (valid && l >= 0) ? src[(long long)l * g.SP] : mk<Cx>((Real)0, (Real)0);
         }
-    E::run(v, sm, tw, tw_stride);
+    E::run(v, sm, tw);
     if (valid) {
 #pragma unroll
         for (int b = 0; b < E::VPT / E::RL; ++b)
@@ -126,8 +124,7 @@ k_w_y(Geom g, const cx<Real> *__restrict__ WU1, cx<Real> *__restrict__ WU2, cons
 // --- products along p_x -----------------------------------------------------------
 template <typename Real, int L>
 __global__ void __launch_bounds__(ColCfg<L>::T, 1)
-k_bw_product(Geom g, cx<Real> *__restrict__ U2, const cx<Real> *__restrict__ WU2, const cx<Real> *__restrict__ tw,
-             int tw_stride)
+k_bw_product(Geom g, cx<Real> *__restrict__ U2, const cx<Real> *__restrict__ WU2, const cx<Real> *__restrict__ tw)
 {
     constexpr int C = ColCfg<L>::C, T = ColCfg<L>::T;
     using EF = Fft<Real, L, C, T, MAP_COL, false>;
@@ -159,11 +156,11 @@ k_bw_product(Geom g, cx<Real> *__restrict__ U2, const cx<Real> *__restrict__ WU2
             vw[b * EF::R0 + r] = (valid && l >= 0) ? colW[(long long)l * wstride] : zero;
             v[b * EF::R0 + r] = (valid && n < g.N) ? colA[(long long)n * rstride] : zero;
         }
-    EF::run(vw, sm, tw, tw_stride);
-    EF::run(v, sm, tw, tw_stride);
+    EF::run(vw, sm, tw);
+    EF::run(v, sm, tw);
 #pragma unroll
     for (int i = 0; i < EF::VPT; ++i) v[i] = cmul(vw[i], v[i]);          // h^ = W^ a^
-    EI::run(v, sm, tw, tw_stride);
+    EI::run(v, sm, tw);
     if (valid) {
 #pragma unroll
         for (int b = 0; b < EI::VPT / EI::RL; ++b)
@@ -182,10 +179,10 @@ k_bw_product(Geom g, cx<Real> *__restrict__ U2, const cx<Real> *__restrict__ WU2
             EF::first_elem(b, r, col, n);
             v[b * EF::R0 + r] = (valid && n < g.N) ? colB[(long long)n * rstride] : zero;
         }
-    EF::run(v, sm, tw, tw_stride);
+    EF::run(v, sm, tw);
 #pragma unroll
     for (int i = 0; i < EF::VPT; ++i) v[i] = cmulc(v[i], vw[i]);         // g^ = conj(W^) b^
-    EI::run(v, sm, tw, tw_stride);
+    EI::run(v, sm, tw);
     if (valid) {
 #pragma unroll
         for (int b = 0; b < EI::VPT / EI::RL; ++b)
@@ -201,8 +198,7 @@ k_bw_product(Geom g, cx<Real> *__restrict__ U2, const cx<Real> *__restrict__ WU2
 // --- inverse along p_y -------------------------------------------------------------
 template <typename Real, int L>
 __global__ void __launch_bounds__(ColCfg<L>::T, ColCfg<L>::MINB)
-k_bw_inv_y(Geom g, const cx<Real> *__restrict__ G3, cx<Real> *__restrict__ G4, const cx<Real> *__restrict__ tw,
-           int tw_stride)
+k_bw_inv_y(Geom g, const cx<Real> *__restrict__ G3, cx<Real> *__restrict__ G4, const cx<Real> *__restrict__ tw)
 {
     constexpr int C = ColCfg<L>::C, T = ColCfg<L>::T;
     using E = Fft<Real, L, C, T, MAP_COL, true>;
@@ -225,7 +221,7 @@ k_bw_inv_y(Geom g, const cx<Real> *__restrict__ G3, cx<Real> *__restrict__ G4, c
             E::first_elem(b, r, col, n);
             v[b * E::R0 + r] = valid ? src[(long long)n * W2] : mk<Cx>((Real)0, (Real)0);
         }
-    E::run(v, sm, tw, tw_stride);
+    E::run(v, sm, tw);
     if (valid) {
 #pragma unroll
         for (int b = 0; b < E::VPT / E::RL; ++b)
@@ -245,7 +241,7 @@ __global__ void __launch_bounds__(LineCfg<L>::T)
 k_bw_inv_energy(Geom g, Band band, const AxisTab *__restrict__ axis,
                 const typename EpsEntry<Real>::type *__restrict__ eps, const InstState *__restrict__ st,
                 const cx<Real> *__restrict__ G4, Real *__restrict__ dA, double *__restrict__ partial,
-                const cx<Real> *__restrict__ tw, int tw_stride)
+                const cx<Real> *__restrict__ tw)
 {
     constexpr int C = LineCfg<L>::C, T = LineCfg<L>::T;
     using E = Fft<Real, L, C, T, MAP_LINE, true>;
@@ -302,7 +298,7 @@ k_bw_inv_energy(Geom g, Band band, const AxisTab *__restrict__ axis,
             }
             v[b * E::R0 + r] = x;
         }
-    E::run(v, sm, tw, tw_stride);   // ends with __syncthreads: s_* visible
+    E::run(v, sm, tw);   // ends with __syncthreads: s_* visible
 
     const Real sc = (Real)g.scale;
     const Real gam = (Real)band.gamma, g2 = gam * gam;
@@ -388,7 +384,7 @@ cudaError_t launch_w_energy_t(const Geom &g, const float *w, float2 *WU1, const 
     static const cudaError_t e = set_smem(k_w_energy<float, L>, smem);
     if (e != cudaSuccess) return e;
     long long npairs = (long long)g.Q * g.Q / 2;
-    k_w_energy<float, L><<<(unsigned)((npairs + C - 1) / C), T, smem, s>>>(g, w, WU1, tw, tw_len / L);
+    k_w_energy<float, L><<<(unsigned)((npairs + C - 1) / C), T, smem, s>>>(g, w, WU1, tw + (L - 16));
     return cudaGetLastError();
 }
 
@@ -401,7 +397,7 @@ cudaError_t launch_w_y_t(const Geom &g, const float2 *WU1, float2 *WU2, const fl
     size_t smem = sizeof(float2) * E::SMEM_ELEMS;
     static const cudaError_t e = set_smem(k_w_y<float, L>, smem);
     if (e != cudaSuccess) return e;
-    k_w_y<float, L><<<dim3((g.H + C - 1) / C, g.Q), T, smem, s>>>(g, WU1, WU2, tw, tw_len / L);
+    k_w_y<float, L><<<dim3((g.H + C - 1) / C, g.Q), T, smem, s>>>(g, WU1, WU2, tw + (L - 16));
     return cudaGetLastError();
 }
 
@@ -416,7 +412,7 @@ cudaError_t launch_bw_product_t(const Geom &g, float2 *U2, const float2 *WU2, co
     size_t smem = sizeof(float2) * elems;
     static const cudaError_t e = set_smem(k_bw_product<float, L>, smem);
     if (e != cudaSuccess) return e;
-    k_bw_product<float, L><<<dim3((g.H + C - 1) / C, g.P), T, smem, s>>>(g, U2, WU2, tw, tw_len / L);
+    k_bw_product<float, L><<<dim3((g.H + C - 1) / C, g.P), T, smem, s>>>(g, U2, WU2, tw + (L - 16));
     return cudaGetLastError();
 }
 
@@ -429,7 +425,7 @@ cudaError_t launch_bw_inv_y_t(const Geom &g, const float2 *G3, float2 *G4, const
     size_t smem = sizeof(float2) * E::SMEM_ELEMS;
     static const cudaError_t e = set_smem(k_bw_inv_y<float, L>, smem);
     if (e != cudaSuccess) return e;
-    k_bw_inv_y<float, L><<<dim3((2 * g.SP + C - 1) / C, g.N), T, smem, s>>>(g, G3, G4, tw, tw_len / L);
+    k_bw_inv_y<float, L><<<dim3((2 * g.SP + C - 1) / C, g.N), T, smem, s>>>(g, G3, G4, tw + (L - 16));
     return cudaGetLastError();
 }
 
@@ -445,7 +441,7 @@ cudaError_t launch_bw_inv_energy_t(const Geom &g, const Band &band, const AxisTa
     if (e != cudaSuccess) return e;
     long long nlines = (long long)g.N * g.N;
     k_bw_inv_energy<float, L><<<(unsigned)((nlines + C - 1) / C), T, smem, s>>>(g, band, axis, eps, st, G4, dA,
-                                                                              partial, tw, tw_len / L);
+                                                                              partial, tw + (L - 16));
     return cudaGetLastError();
 }
 

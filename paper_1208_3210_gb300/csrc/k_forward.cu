@@ -21,7 +21,7 @@ __global__ void __launch_bounds__(LineCfg<L>::T)
 k_fwd_energy(Geom g, Band band, const AxisTab *__restrict__ axis,
              const typename EpsEntry<Real>::type *__restrict__ eps,
              const InstState *__restrict__ st, const Real *__restrict__ A_in,
-             cx<Real> *__restrict__ U1, const cx<Real> *__restrict__ tw, int tw_stride)
+             cx<Real> *__restrict__ U1, const cx<Real> *__restrict__ tw)
 {
     constexpr int C = LineCfg<L>::C, T = LineCfg<L>::T;
     using E = Fft<Real, L, C, T, MAP_LINE, false>;
@@ -86,7 +86,7 @@ k_fwd_energy(Geom g, Band band, const AxisTab *__restrict__ axis,
         }
     }
 
-    E::run(v, sm, tw, tw_stride);
+    E::run(v, sm, tw);
 
     // natural-order spectrum to shared memory, then separate a^ and b^
 #pragma unroll
@@ -124,7 +124,7 @@ k_fwd_energy(Geom g, Band band, const AxisTab *__restrict__ axis,
 template <typename Real, int L>
 __global__ void __launch_bounds__(ColCfg<L>::T, ColCfg<L>::MINB)
 k_fwd_y(Geom g, const cx<Real> *__restrict__ U1, cx<Real> *__restrict__ U2,
-        const cx<Real> *__restrict__ tw, int tw_stride)
+        const cx<Real> *__restrict__ tw)
 {
     constexpr int C = ColCfg<L>::C, T = ColCfg<L>::T;
     using E = Fft<Real, L, C, T, MAP_COL, false>;
@@ -149,7 +149,7 @@ k_fwd_y(Geom g, const cx<Real> *__restrict__ U1, cx<Real> *__restrict__ U2,
             E::first_elem(b, r, col, n);
             v[b * E::R0 + r] = (valid && n < g.N) ? src[(long long)n * W] : mk<Cx>((Real)0, (Real)0);
         }
-    E::run(v, sm, tw, tw_stride);
+    E::run(v, sm, tw);
     if (valid) {
 #pragma unroll
         for (int b = 0; b < E::VPT / E::RL; ++b)
@@ -167,7 +167,7 @@ k_fwd_y(Geom g, const cx<Real> *__restrict__ U1, cx<Real> *__restrict__ U2,
 template <typename Real, int L>
 __global__ void __launch_bounds__(PairCfg<L>::T, PairCfg<L>::MINB)
 k_fwd_y2(Geom g, const cx<Real> *__restrict__ U1, cx<Real> *__restrict__ U2,
-         const cx<Real> *__restrict__ tw, int tw_stride)
+         const cx<Real> *__restrict__ tw)
 {
     constexpr int C = PairCfg<L>::C, T = PairCfg<L>::T;
     using E = FftPair<Real, L, C, T, false>;
@@ -193,7 +193,7 @@ k_fwd_y2(Geom g, const cx<Real> *__restrict__ U1, cx<Real> *__restrict__ U2,
             if (valid && n < g.N) gld2(src + (long long)n * W, va[b * E::R0 + r], vb[b * E::R0 + r]);
             else { va[b * E::R0 + r] = zero; vb[b * E::R0 + r] = zero; }
         }
-    E::run(va, vb, sm, tw, tw_stride);
+    E::run(va, vb, sm, tw);
     if (valid) {
 #pragma unroll
         for (int b = 0; b < E::VPT / E::RL; ++b)
@@ -218,7 +218,7 @@ cudaError_t launch_fwd_energy_t(const Geom &g, const Band &band, const Work<Real
     long long nlines = (long long)g.N * g.N;
     unsigned grid = (unsigned)((nlines + C - 1) / C);
     k<<<grid, T, smem, s>>>(g, band, w.axis, (const typename EpsEntry<Real>::type *)w.eps, w.state, A_in,
-                            (cx<Real> *)w.X, (const cx<Real> *)w.tw, w.tw_len / L);
+                            (cx<Real> *)w.X, twiddles_for<Real>(w, L));
     return cudaGetLastError();
 }
 
@@ -232,7 +232,7 @@ cudaError_t launch_fwd_y2_t(const Geom &g, const Work<Real> &w, cudaStream_t s)
     static const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((2 * g.SP + C - 1) / C, g.N);
-    k<<<grid, T, smem, s>>>(g, (const cx<Real> *)w.X, (cx<Real> *)w.Y, (const cx<Real> *)w.tw, w.tw_len / L);
+    k<<<grid, T, smem, s>>>(g, (const cx<Real> *)w.X, (cx<Real> *)w.Y, twiddles_for<Real>(w, L));
     return cudaGetLastError();
 }
 
@@ -247,7 +247,7 @@ cudaError_t launch_fwd_y_t(const Geom &g, const Work<Real> &w, cudaStream_t s)
     static const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((2 * g.SP + C - 1) / C, g.N);
-    k<<<grid, T, smem, s>>>(g, (const cx<Real> *)w.X, (cx<Real> *)w.Y, (const cx<Real> *)w.tw, w.tw_len / L);
+    k<<<grid, T, smem, s>>>(g, (const cx<Real> *)w.X, (cx<Real> *)w.Y, twiddles_for<Real>(w, L));
     return cudaGetLastError();
 }
 

@@ -17,7 +17,7 @@ namespace lh {
 template <typename Real, int L>
 __global__ void __launch_bounds__(ColCfg<L>::T, ColCfg<L>::MINB)
 k_inv_y(Geom g, const cx<Real> *__restrict__ U3, cx<Real> *__restrict__ U4,
-        const cx<Real> *__restrict__ tw, int tw_stride)
+        const cx<Real> *__restrict__ tw)
 {
     constexpr int C = ColCfg<L>::C, T = ColCfg<L>::T;
     using E = Fft<Real, L, C, T, MAP_COL, true>;
@@ -41,7 +41,7 @@ k_inv_y(Geom g, const cx<Real> *__restrict__ U3, cx<Real> *__restrict__ U4,
             E::first_elem(b, r, col, n);
             v[b * E::R0 + r] = valid ? src[(long long)n * g.SP] : mk<Cx>((Real)0, (Real)0);
         }
-    E::run(v, sm, tw, tw_stride);
+    E::run(v, sm, tw);
     if (valid) {
 #pragma unroll
         for (int b = 0; b < E::VPT / E::RL; ++b)
@@ -59,7 +59,7 @@ k_inv_y(Geom g, const cx<Real> *__restrict__ U3, cx<Real> *__restrict__ U4,
 template <typename Real, int L>
 __global__ void __launch_bounds__(PairCfg<L>::T, PairCfg<L>::MINB)
 k_inv_y2(Geom g, const cx<Real> *__restrict__ U3, cx<Real> *__restrict__ U4,
-         const cx<Real> *__restrict__ tw, int tw_stride)
+         const cx<Real> *__restrict__ tw)
 {
     constexpr int C = PairCfg<L>::C, T = PairCfg<L>::T;
     using E = FftPair<Real, L, C, T, true>;
@@ -83,7 +83,7 @@ k_inv_y2(Geom g, const cx<Real> *__restrict__ U3, cx<Real> *__restrict__ U4,
             if (valid) gld2(src + (long long)E::first_row(b, r) * g.SP, va[b * E::R0 + r], vb[b * E::R0 + r]);
             else { va[b * E::R0 + r] = zero; vb[b * E::R0 + r] = zero; }
         }
-    E::run(va, vb, sm, tw, tw_stride);
+    E::run(va, vb, sm, tw);
     if (valid) {
 #pragma unroll
         for (int b = 0; b < E::VPT / E::RL; ++b)
@@ -98,7 +98,7 @@ k_inv_y2(Geom g, const cx<Real> *__restrict__ U3, cx<Real> *__restrict__ U4,
 template <typename Real, typename OutT, int L>
 __global__ void __launch_bounds__(LineCfg<L>::T)
 k_inv_energy(Geom g, const cx<Real> *__restrict__ U4, OutT *__restrict__ out,
-             const cx<Real> *__restrict__ tw, int tw_stride)
+             const cx<Real> *__restrict__ tw)
 {
     constexpr int C = LineCfg<L>::C, T = LineCfg<L>::T;
     using E = Fft<Real, L, C, T, MAP_LINE, true>;
@@ -131,7 +131,7 @@ k_inv_energy(Geom g, const cx<Real> *__restrict__ U4, OutT *__restrict__ out,
             }
             v[b * E::R0 + r] = w;
         }
-    E::run(v, sm, tw, tw_stride);
+    E::run(v, sm, tw);
     const Real sc = (Real)g.scale;
 #pragma unroll
     for (int b = 0; b < E::VPT / E::RL; ++b)
@@ -158,7 +158,7 @@ cudaError_t launch_inv_y2_t(const Geom &g, const Work<Real> &w, cudaStream_t s)
     static const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((g.H + C - 1) / C, g.Q);
-    k<<<grid, T, smem, s>>>(g, (const cx<Real> *)w.X, (cx<Real> *)w.Y, (const cx<Real> *)w.tw, w.tw_len / L);
+    k<<<grid, T, smem, s>>>(g, (const cx<Real> *)w.X, (cx<Real> *)w.Y, twiddles_for<Real>(w, L));
     return cudaGetLastError();
 }
 
@@ -173,7 +173,7 @@ cudaError_t launch_inv_y_t(const Geom &g, const Work<Real> &w, cudaStream_t s)
     static const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((g.H + C - 1) / C, g.Q);
-    k<<<grid, T, smem, s>>>(g, (const cx<Real> *)w.X, (cx<Real> *)w.Y, (const cx<Real> *)w.tw, w.tw_len / L);
+    k<<<grid, T, smem, s>>>(g, (const cx<Real> *)w.X, (cx<Real> *)w.Y, twiddles_for<Real>(w, L));
     return cudaGetLastError();
 }
 
@@ -188,7 +188,7 @@ cudaError_t launch_inv_energy_t(const Geom &g, const Work<Real> &w, OutT *out, c
     if (e != cudaSuccess) return e;
     long long npairs = (long long)g.Q * g.Q / 2;
     unsigned grid = (unsigned)((npairs + C - 1) / C);
-    k<<<grid, T, smem, s>>>(g, (const cx<Real> *)w.Y, out, (const cx<Real> *)w.tw, w.tw_len / L);
+    k<<<grid, T, smem, s>>>(g, (const cx<Real> *)w.Y, out, twiddles_for<Real>(w, L));
     return cudaGetLastError();
 }
 

@@ -17,7 +17,7 @@ namespace lh {
 // barriers, two dependency chains per thread); inverse: the product alone.
 template <typename Real, int L>
 struct XProduct {
-    static constexpr int C = ColCfg<L>::C, T = ColCfg<L>::T;
+    static constexpr int C = XCfg<L>::C, T = XCfg<L>::T;
     using EF = FftPair<Real, L, 2 * C, T, false>;
     using EI = Fft<Real, L, C, T, MAP_COL, true>;
     static_assert(EF::RL == EI::R0, "last forward radix must equal first inverse radix");
@@ -26,9 +26,9 @@ struct XProduct {
 };
 
 template <typename Real, int L>
-__global__ void __launch_bounds__(ColCfg<L>::T, ColCfg<L>::MINB_X)
+__global__ void __launch_bounds__(XCfg<L>::T, XCfg<L>::MINB)
 k_x_product(Geom g, const cx<Real> *__restrict__ U2, cx<Real> *__restrict__ U3,
-            const cx<Real> *__restrict__ tw, int tw_stride)
+            const cx<Real> *__restrict__ tw)
 {
     using XP = XProduct<Real, L>;
     constexpr int C = XP::C;
@@ -58,11 +58,11 @@ k_x_product(Geom g, const cx<Real> *__restrict__ U2, cx<Real> *__restrict__ U3,
             va[b * EF::R0 + r] = ld ? srcA[(long long)n * rstride] : zero;
             vb[b * EF::R0 + r] = ld ? srcB[(long long)n * rstride] : zero;
         }
-    EF::run(va, vb, sm, tw, tw_stride);
+    EF::run(va, vb, sm, tw);
     // conj(a^) * b^ : transform of the correlation sum_p a(p) b(p + q)
 #pragma unroll
     for (int i = 0; i < EF::VPT; ++i) va[i] = cmulc(vb[i], va[i]);
-    EI::run(va, sm, tw, tw_stride);
+    EI::run(va, sm, tw);
     if (valid) {
         Cx *dst = U3 + (long long)ky * g.SP + c;
         const long long ostride = g.xs3;
@@ -88,7 +88,7 @@ cudaError_t launch_x_product_t(const Geom &g, const Work<Real> &w, cudaStream_t 
     static const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((g.H + C - 1) / C, g.P);
-    k<<<grid, T, smem, s>>>(g, (const cx<Real> *)w.Y, (cx<Real> *)w.X, (const cx<Real> *)w.tw, w.tw_len / L);
+    k<<<grid, T, smem, s>>>(g, (const cx<Real> *)w.Y, (cx<Real> *)w.X, twiddles_for<Real>(w, L));
     return cudaGetLastError();
 }
 

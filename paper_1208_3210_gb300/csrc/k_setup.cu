@@ -7,15 +7,19 @@
 
 namespace lh {
 
-// exp(-2 pi i n / len) for n in [0, len), evaluated in FP64 with sincospi.
-__global__ void k_twiddles(int len, float2 *tw32, double2 *tw64)
+// Twiddle tables exp(-2 pi i n / L), n < L, for every power of two L from 16
+// to max_len, the length-L table at offset L - 16; FP64 sincospi.
+__global__ void k_twiddles(int max_len, float2 *tw32, double2 *tw64)
 {
-    int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= len) return;
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= twiddle_entries(max_len)) return;
+    int L = 16;
+    while (2 * L - 16 <= idx) L *= 2;   // the table that holds idx
+    int n = idx - (L - 16);
     double s, c;
-    sincospi(-2.0 * (double)n / (double)len, &s, &c);
-    tw32[n] = make_float2((float)c, (float)s);
-    tw64[n] = make_double2(c, s);
+    sincospi(-2.0 * (double)n / (double)L, &s, &c);
+    tw32[idx] = make_float2((float)c, (float)s);
+    tw64[idx] = make_double2(c, s);
 }
 
 // Per-axis tables at p_i = (i - N/2) 2 pi / npz and the energy grid
@@ -53,21 +57,25 @@ __global__ void k_tables(Geom g, Band band, AxisTab *axis, float2 *eps32, double
 // Chemical potential.  n(mu) = (2/npz^2) sum_k [1/2 - atan((e0_k - mu)/gamma)/pi]
 // over the first-zone grid (the Lorentzian occupation of Eq. 5 below the Fermi
 // level).  n is strictly increasing in mu.  Five small launches of G CTAs:
-//   2 passes of MU_SECT-point multisection in FP32 shrink the bracket
-//   [-B-3, B+3] eV (B bounds |e0|) by (MU_SECT-1)^2; every thread owns one
-//   candidate and a share of the points;
-//   3 Newton steps in FP64 from the bracket midpoint reach FP64 precision.
+//   3 passes of MU_SECT-point multisection in FP32 shrink the bracket
+//   [-B-3, B+3] eV (B bounds |e0|) by (MU_SECT-1)^3 to a few micro-eV; every
+//   thread owns one candidate and a share of the points;
+//   2 Newton steps in FP64 from the bracket midpoint reach FP64 precision
+//   (the error after a step is about |F''/2F'| times the step squared).
 // Each launch ends the same way: every CTA stores its partial sums, and the
 // last CTA to finish (an atomic counter, which it resets) adds them in a fixed
 // order and publishes the new bracket or mu for the next launch.  No CTA ever
 // waits for another.
 constexpr int MU_SECT = 128;
 constexpr int MU_THREADS = 256;
-constexpr int MU_FP32_PASSES = 2;
-constexpr int MU_NEWTON = 3;
+constexpr int MU_FP32_PASSES = 3;
+constexpr int MU_NEWTON = 2;
+constexpr int MU_SECT_CTAS = 32;   // CTAs of a multisection pass (few partials to add up)
 constexpr int MU_RES = 16;   // result slots at the start of acc
 
-// Layout of acc: [MU_RES] results, then [MU_FP32_PASSES][G][MU_SECT], then [MU_NEWTON][G][2] doubles.
+// Layout of acc: [MU_RES] results (3 per multisection pass from 0, 2 per
+// Newton step from 10), then [MU_FP32_PASSES][G][MU_SECT], then
+// [MU_NEWTON][G][2] doubles.
 size_t mu_acc_doubles(int G) { return MU_RES + (size_t)G * (MU_FP32_PASSES * MU_SECT + MU_NEWTON * 2); }
 size_t mu_barrier_words() { return 32; }   // the arrival counter (one 128-byte line)
 
@@ -210,7 +218,7 @@ k_mu_newton(Geom g, Band band, const AxisTab *__restrict__ axis, InstState *st, 
         return;
     }
     const double mu = (it == 0) ? 0.5 * (res[3 * (MU_FP32_PASSES - 1) + 0] + res[3 * (MU_FP32_PASSES - 1) + 1])
-                                : res[8 + 2 * (it - 1)];
+                                : res[10 + 2 * (it - 1)];
     const double gd = band.gamma, ipi = 0.31830988618379067154;
     constexpr int NW = MU_THREADS / 32;
     __shared__ double s_red[2][NW];
@@ -253,13 +261,14 @@ k_mu_newton(Geom g, Band band, const AxisTab *__restrict__ axis, InstState *st, 
         Fp = 0;
         for (int w = 0; w < NW; ++w) { F += s_red[0][w]; Fp += s_red[1][w]; }
         const double step = (F - target) / Fp;   // d/dmu of sum_k occ = sum_k Lorentzian
-        res[8 + 2 * it] = mu - step;
-        res[9 + 2 * it] = step;
+        res[10 + 2 * it] = mu - step;
+        res[11 + 2 * it] = step;
         if (it == MU_NEWTON - 1) {
             st->mu = mu - step;
             st->last_step = fabs(step);
             if (mu_out) *mu_out = mu - step;
-            if (!(fabs(step) < 1e-9)) atomicCAS(status, (unsigned)DEV_OK, (unsigned)DEV_ENOCONV);
+            // a last step below 1e-7 eV leaves an error of order 1e-12 eV
+            if (!(fabs(step) < 1e-7)) atomicCAS(status, (unsigned)DEV_OK, (unsigned)DEV_ENOCONV);
         }
     }
 }
@@ -274,7 +283,7 @@ __global__ void k_mu_given(double mu, InstState *st, double *mu_out)
 
 cudaError_t launch_twiddles(int len, float2 *tw32, double2 *tw64, cudaStream_t s)
 {
-    k_twiddles<<<(len + 255) / 256, 256, 0, s>>>(len, tw32, tw64);
+    k_twiddles<<<(twiddle_entries(len) + 255) / 256, 256, 0, s>>>(len, tw32, tw64);
     return cudaGetLastError();
 }
 
@@ -300,8 +309,9 @@ cudaError_t launch_solve_mu(const Geom &g, const Band &band, const AxisTab *axis
         k_mu_given<<<1, 1, 0, s>>>(band.mu, st, mu_out);
         return cudaGetLastError();
     }
+    const int Gs = G < MU_SECT_CTAS ? G : MU_SECT_CTAS;
     for (int pass = 0; pass < MU_FP32_PASSES; ++pass)
-        k_mu_sect<<<G, MU_THREADS, 0, s>>>(g, band, axis, acc, bar, pass);
+        k_mu_sect<<<Gs, MU_THREADS, 0, s>>>(g, band, axis, acc, bar, pass);
     for (int it = 0; it < MU_NEWTON; ++it)
         k_mu_newton<<<G, MU_THREADS, 0, s>>>(g, band, axis, st, acc, bar, it, status, mu_out);
     return cudaGetLastError();

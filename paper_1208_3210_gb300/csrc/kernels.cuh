@@ -26,6 +26,10 @@ template <> struct ColCfg<4096> { static constexpr int C = 4, T = 1024, MINB = 1
 // columns per CTA as C/2 pairs, VPT = (C/2) L / T = 16 values per thread per
 // column (8 for L = 512).  Used for L >= 128.
 template <int L> struct PairCfg;
+// The p_x product pass (two operands per thread): its own tile sizes.
+template <int L> struct XCfg { static constexpr int C = ColCfg<L>::C, T = ColCfg<L>::T, MINB = ColCfg<L>::MINB_X; };
+template <> struct XCfg<512> { static constexpr int C = 8, T = 256, MINB = 2; };   // VPT 16
+
 template <> struct PairCfg<128>  { static constexpr int C = 16, T = 64, MINB = 4; };
 template <> struct PairCfg<256>  { static constexpr int C = 16, T = 128, MINB = 4; };
 template <> struct PairCfg<512>  { static constexpr int C = 16, T = 512, MINB = 2; };  // VPT 8
@@ -49,6 +53,16 @@ template <> struct LineCfg<4096> { static constexpr int C = 4, T = 1024; };
 template <typename Real> struct EpsEntry;
 template <> struct EpsEntry<float> { using type = float2; };
 template <> struct EpsEntry<double> { using type = double; };
+
+// Twiddle tables: for every power-of-two length L from 16 up to the plan's
+// longest transform, exp(-2 pi i n / L), n < L, stored contiguously with the
+// length-L table at offset L - 16.
+template <typename Real>
+__host__ __device__ inline const cx<Real> *twiddles_for(const Work<Real> &w, int L)
+{
+    return (const cx<Real> *)w.tw + (L - 16);
+}
+__host__ __device__ constexpr int twiddle_entries(int max_len) { return 2 * max_len - 16; }
 
 // Bytes of dynamic shared memory this launch was given.  Every FFT kernel
 // compares it with what its engines address and returns before touching

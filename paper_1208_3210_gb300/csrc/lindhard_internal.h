@@ -60,8 +60,8 @@ struct Work {
     void *Y;               // y pass output, later inverse-y output
     AxisTab *axis;         // [N]
     void *eps;             // energy table: float2 (hi, lo) or double, [n_eps]
-    const void *tw;        // twiddles exp(-2 pi i n / TWL): float2 or double2
-    int tw_len;            // TWL
+    const void *tw;        // twiddle tables (see twiddles_for): float2 or double2
+    int tw_len;            // longest transform length of the plan
     InstState *state;      // [1]
     unsigned *status;      // plan-wide device status word
     double *mu_acc;        // scratch for the chemical potential solve

@@ -274,8 +274,8 @@ extern "C" lindhard_status lindhard_plan_create(const lindhard_grid *grids, int 
         return n;
     };
     size_t o = 0;
-    p->off_tw32 = o; o = align_up(o + (size_t)maxLen * sizeof(float2));
-    p->off_tw64 = o; o = align_up(o + (size_t)maxLen * sizeof(double2));
+    p->off_tw32 = o; o = align_up(o + (size_t)twiddle_entries(maxLen) * sizeof(float2));
+    p->off_tw64 = o; o = align_up(o + (size_t)twiddle_entries(maxLen) * sizeof(double2));
     p->off_status = o; o = align_up(o + sizeof(unsigned));
     auto place = [&](const Need &n) {
         lindhard_plan::Slot sl;
