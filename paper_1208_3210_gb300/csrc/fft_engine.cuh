@@ -1,6 +1,7 @@
 // Register-resident Stockham FFT engine for one CTA (sm_103a).
 //
-// A CTA transforms C independent lines of power-of-two length L (16..4096).
+// A CTA transforms C independent lines of length L (powers of two 16..4096,
+// and 3 * 2^k from 48 to 1536).
 // Each stage is a radix-R butterfly held in registers; between stages the
 // values go through shared memory once (the Stockham exchange), so an L-point
 // transform with S stages touches shared memory 2(S-1) times per point and
@@ -43,8 +44,13 @@ template <typename C> __device__ __forceinline__ C mul_i(C a) { return mk<C>(-a.
 template <typename C> __device__ __forceinline__ C mul_mi(C a) { return mk<C>(a.y, -a.x); }  // -i * a
 
 // ---------------------------------------------------------------------------
-// Radix schedules (forward order).  L = prod radix(L, s).
-__host__ __device__ constexpr int fft_nstages(int L) { return L <= 16 ? 1 : (L <= 256 ? 2 : 3); }
+// Radix schedules (forward order).  L = prod radix(L, s).  Powers of two up
+// to 4096 and 3 * 2^k from 48 to 1536 (momentum axes padded to exactly 1.5 N).
+__host__ __device__ constexpr bool fft_len_pow2(int L) { return (L & (L - 1)) == 0; }
+__host__ __device__ constexpr int fft_nstages(int L)
+{
+    return fft_len_pow2(L) ? (L <= 16 ? 1 : (L <= 256 ? 2 : 3)) : (L <= 96 ? 2 : 3);
+}
 __host__ __device__ constexpr int fft_fwd_radix(int L, int s)
 {
     return L == 16 ? 16
@@ -55,7 +61,13 @@ __host__ __device__ constexpr int fft_fwd_radix(int L, int s)
          : L == 512 ? 8
          : L == 1024 ? (s == 0 ? 16 : 8)
          : L == 2048 ? (s < 2 ? 16 : 8)
-         : 16; /* 4096 */
+         : L == 4096 ? 16
+         : L == 48 ? (s == 0 ? 8 : 6)
+         : L == 96 ? (s == 0 ? 8 : 12)
+         : L == 192 ? (s < 2 ? 8 : 3)
+         : L == 384 ? (s < 2 ? 8 : 6)
+         : L == 768 ? (s < 2 ? 8 : 12)
+         : /* 1536 */ (s < 2 ? 8 : 24);
 }
 __host__ __device__ constexpr int fft_radix(int L, int s, bool inv)
 {
@@ -65,38 +77,48 @@ __host__ __device__ constexpr int fft_ns_before(int L, int s, bool inv)
 {
     return s == 0 ? 1 : fft_ns_before(L, s - 1, inv) * fft_radix(L, s - 1, inv);
 }
+// every radix of the schedule divides v (values per thread)
+__host__ __device__ constexpr bool fft_radices_divide(int L, int v, int s = 0)
+{
+    return s >= fft_nstages(L) ? true : (v % fft_fwd_radix(L, s) == 0 && fft_radices_divide(L, v, s + 1));
+}
 
 // ---------------------------------------------------------------------------
-// Exact small DFTs in registers.  cos / sin of 2 pi k / 16, k = 0..4.
-__host__ __device__ constexpr double cos16_q(int k)
+// Exact small DFTs in registers.  cos(2 pi m / 48) for m = 0..12 (multiples of
+// 7.5 degrees), which covers every radix used (2, 3, 4, 6, 8, 12, 16, 24).
+__host__ __device__ constexpr double cos48_q(int m)
 {
-    return k == 0 ? 1.0 : k == 1 ? 0.92387953251128675613 : k == 2 ? 0.70710678118654752440
-         : k == 3 ? 0.38268343236508977173 : 0.0;
+    return m == 0 ? 1.0 : m == 1 ? 0.99144486137381041114 : m == 2 ? 0.96592582628906828675
+         : m == 3 ? 0.92387953251128675613 : m == 4 ? 0.86602540378443864676
+         : m == 5 ? 0.79335334029123516458 : m == 6 ? 0.70710678118654752440
+         : m == 7 ? 0.60876142900872063942 : m == 8 ? 0.5
+         : m == 9 ? 0.38268343236508977173 : m == 10 ? 0.25881904510252076235
+         : m == 11 ? 0.13052619222005159155 : 0.0;
 }
-__host__ __device__ constexpr double cos16(int k)
+__host__ __device__ constexpr double cos48(int m)
 {
-    // cos(2 pi k / 16) for any k >= 0, from the first-quadrant values
-    return (k % 16) <= 4 ? cos16_q(k % 16)
-         : (k % 16) <= 8 ? -cos16_q(8 - k % 16)
-         : (k % 16) <= 12 ? -cos16_q(k % 16 - 8)
-         : cos16_q(16 - k % 16);
+    // cos(2 pi m / 48) for any m >= 0, from the first-quadrant values
+    return (m % 48) <= 12 ? cos48_q(m % 48)
+         : (m % 48) <= 24 ? -cos48_q(24 - m % 48)
+         : (m % 48) <= 36 ? -cos48_q(m % 48 - 24)
+         : cos48_q(48 - m % 48);
 }
-__host__ __device__ constexpr double sin16(int k) { return cos16(k + 12); }  // sin x = cos(x - pi/2)
+__host__ __device__ constexpr double sin48(int m) { return cos48(m + 36); }  // sin x = cos(x - pi/2)
 
-// x * exp(-+ 2 pi i K / R) with compile-time R | 16 (INV flips the sign).
+// x * exp(-+ 2 pi i K / R) with compile-time R | 48 (INV flips the sign).
 template <int R, int K, bool INV, typename C>
 __device__ __forceinline__ C twc(C x)
 {
     constexpr int k = ((K % R) + R) % R;
-    constexpr int k16 = k * (16 / R);
+    constexpr int k48 = k * (48 / R);
     using T = decltype(C::x);
-    if constexpr (k16 == 0) return x;
-    else if constexpr (k16 == 8) return mk<C>(-x.x, -x.y);
-    else if constexpr (k16 == 4) return INV ? mul_i(x) : mul_mi(x);
-    else if constexpr (k16 == 12) return INV ? mul_mi(x) : mul_i(x);
+    if constexpr (k48 == 0) return x;
+    else if constexpr (k48 == 24) return mk<C>(-x.x, -x.y);
+    else if constexpr (k48 == 12) return INV ? mul_i(x) : mul_mi(x);
+    else if constexpr (k48 == 36) return INV ? mul_mi(x) : mul_i(x);
     else {
-        constexpr T cr = (T)cos16(k16);
-        constexpr T ci = INV ? (T)sin16(k16) : (T)-sin16(k16);
+        constexpr T cr = (T)cos48(k48);
+        constexpr T ci = INV ? (T)sin48(k48) : (T)-sin48(k48);
         return mk<C>(x.x * cr - x.y * ci, x.x * ci + x.y * cr);
     }
 }
@@ -146,6 +168,37 @@ template <bool INV, typename C> struct Dft<8, INV, C> {
         dit_combine<8, INV, C, 0>(v, e, o);
     }
 };
+template <bool INV, typename C> struct Dft<3, INV, C> {
+    __device__ __forceinline__ static void run(C *v)
+    {
+        using T = decltype(C::x);
+        constexpr T s3 = (T)0.86602540378443864676;   // sin(2 pi / 3)
+        C t1 = cadd(v[1], v[2]);
+        C t2 = mk<C>(v[0].x - (T)0.5 * t1.x, v[0].y - (T)0.5 * t1.y);
+        C d = csub(v[1], v[2]);
+        C t3 = mk<C>(s3 * d.x, s3 * d.y);
+        v[0] = cadd(v[0], t1);
+        // forward: y1 = t2 - i t3, y2 = t2 + i t3 (inverse: the other way round)
+        v[1] = INV ? cadd(t2, mul_i(t3)) : cadd(t2, mul_mi(t3));
+        v[2] = INV ? cadd(t2, mul_mi(t3)) : cadd(t2, mul_i(t3));
+    }
+};
+// Radix 6, 12 and 24: decimation in time into two halves.
+template <int R, bool INV, typename C> struct DftDit {
+    __device__ __forceinline__ static void run(C *v)
+    {
+        C e[R / 2], o[R / 2];
+#pragma unroll
+        for (int i = 0; i < R / 2; ++i) { e[i] = v[2 * i]; o[i] = v[2 * i + 1]; }
+        Dft<R / 2, INV, C>::run(e);
+        Dft<R / 2, INV, C>::run(o);
+        dit_combine<R, INV, C, 0>(v, e, o);
+    }
+};
+template <bool INV, typename C> struct Dft<6, INV, C> : DftDit<6, INV, C> {};
+template <bool INV, typename C> struct Dft<12, INV, C> : DftDit<12, INV, C> {};
+template <bool INV, typename C> struct Dft<24, INV, C> : DftDit<24, INV, C> {};
+
 template <bool INV, typename C> struct Dft<16, INV, C> {
     __device__ __forceinline__ static void run(C *v)
     {
@@ -175,8 +228,7 @@ struct Fft {
     // exchange's writes (rows R0 apart) fall into different banks
     static constexpr int SMEM_ELEMS = (MAP == MAP_COL) ? (L + L / R0) * C : C * LP;
     static_assert((C * L) % T == 0, "tile must split evenly over threads");
-    static_assert(VPT % R0 == 0 && VPT % RL == 0 && VPT % fft_radix(L, NS > 2 ? 1 : 0, INV) == 0,
-                  "values per thread must be a multiple of every radix");
+    static_assert(fft_radices_divide(L, VPT), "values per thread must be a multiple of every radix");
     static_assert(MAP == MAP_LINE || T % C == 0, "column map needs T % C == 0");
 
     __device__ __forceinline__ static int saddr(int col, int n)
@@ -277,8 +329,7 @@ struct FftPair {
     static constexpr int RL = fft_radix(L, NS - 1, INV);
     static constexpr int SMEM_ELEMS = (L + L / R0) * C;   // one empty row after every R0 rows
     static_assert(C % 2 == 0 && T % CP == 0 && (CP * L) % T == 0, "tile must split evenly over threads");
-    static_assert(VPT % R0 == 0 && VPT % RL == 0 && VPT % fft_radix(L, NS > 2 ? 1 : 0, INV) == 0,
-                  "values per thread must be a multiple of every radix");
+    static_assert(fft_radices_divide(L, VPT), "values per thread must be a multiple of every radix");
 
     // the thread's column pair (columns 2p and 2p + 1 of the tile)
     __device__ __forceinline__ static int pair() { return threadIdx.x % CP; }

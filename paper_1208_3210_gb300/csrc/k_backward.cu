@@ -384,7 +384,7 @@ cudaError_t launch_w_energy_t(const Geom &g, const float *w, float2 *WU1, const 
     static const cudaError_t e = set_smem(k_w_energy<float, L>, smem);
     if (e != cudaSuccess) return e;
     long long npairs = (long long)g.Q * g.Q / 2;
-    k_w_energy<float, L><<<(unsigned)((npairs + C - 1) / C), T, smem, s>>>(g, w, WU1, tw + (L - 16));
+    k_w_energy<float, L><<<(unsigned)((npairs + C - 1) / C), T, smem, s>>>(g, w, WU1, tw + twiddle_offset(L));
     return cudaGetLastError();
 }
 
@@ -397,7 +397,7 @@ cudaError_t launch_w_y_t(const Geom &g, const float2 *WU1, float2 *WU2, const fl
     size_t smem = sizeof(float2) * E::SMEM_ELEMS;
     static const cudaError_t e = set_smem(k_w_y<float, L>, smem);
     if (e != cudaSuccess) return e;
-    k_w_y<float, L><<<dim3((g.H + C - 1) / C, g.Q), T, smem, s>>>(g, WU1, WU2, tw + (L - 16));
+    k_w_y<float, L><<<dim3((g.H + C - 1) / C, g.Q), T, smem, s>>>(g, WU1, WU2, tw + twiddle_offset(L));
     return cudaGetLastError();
 }
 
@@ -412,7 +412,7 @@ cudaError_t launch_bw_product_t(const Geom &g, float2 *U2, const float2 *WU2, co
     size_t smem = sizeof(float2) * elems;
     static const cudaError_t e = set_smem(k_bw_product<float, L>, smem);
     if (e != cudaSuccess) return e;
-    k_bw_product<float, L><<<dim3((g.H + C - 1) / C, g.P), T, smem, s>>>(g, U2, WU2, tw + (L - 16));
+    k_bw_product<float, L><<<dim3((g.H + C - 1) / C, g.P), T, smem, s>>>(g, U2, WU2, tw + twiddle_offset(L));
     return cudaGetLastError();
 }
 
@@ -425,7 +425,7 @@ cudaError_t launch_bw_inv_y_t(const Geom &g, const float2 *G3, float2 *G4, const
     size_t smem = sizeof(float2) * E::SMEM_ELEMS;
     static const cudaError_t e = set_smem(k_bw_inv_y<float, L>, smem);
     if (e != cudaSuccess) return e;
-    k_bw_inv_y<float, L><<<dim3((2 * g.SP + C - 1) / C, g.N), T, smem, s>>>(g, G3, G4, tw + (L - 16));
+    k_bw_inv_y<float, L><<<dim3((2 * g.SP + C - 1) / C, g.N), T, smem, s>>>(g, G3, G4, tw + twiddle_offset(L));
     return cudaGetLastError();
 }
 
@@ -441,7 +441,7 @@ cudaError_t launch_bw_inv_energy_t(const Geom &g, const Band &band, const AxisTa
     if (e != cudaSuccess) return e;
     long long nlines = (long long)g.N * g.N;
     k_bw_inv_energy<float, L><<<(unsigned)((nlines + C - 1) / C), T, smem, s>>>(g, band, axis, eps, st, G4, dA,
-                                                                              partial, tw + (L - 16));
+                                                                              partial, tw + twiddle_offset(L));
     return cudaGetLastError();
 }
 
@@ -455,21 +455,21 @@ cudaError_t launch_w_energy(const Geom &g, const float *w, float2 *WU1, const fl
 cudaError_t launch_w_y(const Geom &g, const float2 *WU1, float2 *WU2, const float2 *tw, int tw_len, cudaStream_t s)
 {
 #define CALL(L) launch_w_y_t<L>(g, WU1, WU2, tw, tw_len, s)
-    LH_LEN_SWITCH(g.P, CALL)
+    LH_P_SWITCH(g.P, CALL)
 #undef CALL
 }
 cudaError_t launch_bw_product(const Geom &g, float2 *U2, const float2 *WU2, const float2 *tw, int tw_len,
                               cudaStream_t s)
 {
 #define CALL(L) launch_bw_product_t<L>(g, U2, WU2, tw, tw_len, s)
-    LH_LEN_SWITCH(g.P, CALL)
+    LH_P_SWITCH(g.P, CALL)
 #undef CALL
 }
 cudaError_t launch_bw_inv_y(const Geom &g, const float2 *G3, float2 *G4, const float2 *tw, int tw_len,
                             cudaStream_t s)
 {
 #define CALL(L) launch_bw_inv_y_t<L>(g, G3, G4, tw, tw_len, s)
-    LH_LEN_SWITCH(g.P, CALL)
+    LH_P_SWITCH(g.P, CALL)
 #undef CALL
 }
 cudaError_t launch_bw_inv_energy(const Geom &g, const Band &band, const AxisTab *axis, const float2 *eps,

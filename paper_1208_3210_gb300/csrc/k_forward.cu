@@ -268,7 +268,7 @@ cudaError_t launch_fwd_energy(const Geom &g, const Band &band, const Work<double
 cudaError_t launch_fwd_y(const Geom &g, const Work<float> &w, cudaStream_t s)
 {
 #define CALL(L) launch_fwd_y_t<float, L>(g, w, s)
-    LH_LEN_SWITCH(g.P, CALL)
+    LH_P_SWITCH(g.P, CALL)
 #undef CALL
 }
 cudaError_t launch_fwd_y(const Geom &g, const Work<double> &w, cudaStream_t s)

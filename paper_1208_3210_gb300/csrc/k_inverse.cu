@@ -195,7 +195,7 @@ cudaError_t launch_inv_energy_t(const Geom &g, const Work<Real> &w, OutT *out, c
 cudaError_t launch_inv_y(const Geom &g, const Work<float> &w, cudaStream_t s)
 {
 #define CALL(L) launch_inv_y_t<float, L>(g, w, s)
-    LH_LEN_SWITCH(g.P, CALL)
+    LH_P_SWITCH(g.P, CALL)
 #undef CALL
 }
 cudaError_t launch_inv_y(const Geom &g, const Work<double> &w, cudaStream_t s)

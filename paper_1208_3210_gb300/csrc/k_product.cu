@@ -95,7 +95,7 @@ cudaError_t launch_x_product_t(const Geom &g, const Work<Real> &w, cudaStream_t 
 cudaError_t launch_x_product(const Geom &g, const Work<float> &w, cudaStream_t s)
 {
 #define CALL(L) launch_x_product_t<float, L>(g, w, s)
-    LH_LEN_SWITCH(g.P, CALL)
+    LH_P_SWITCH(g.P, CALL)
 #undef CALL
 }
 cudaError_t launch_x_product(const Geom &g, const Work<double> &w, cudaStream_t s)

@@ -7,15 +7,23 @@
 
 namespace lh {
 
-// Twiddle tables exp(-2 pi i n / L), n < L, for every power of two L from 16
-// to max_len, the length-L table at offset L - 16; FP64 sincospi.
+// Every twiddle table (see twiddle_offset), FP64 sincospi.
 __global__ void k_twiddles(int max_len, float2 *tw32, double2 *tw64)
 {
+    (void)max_len;
     int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= twiddle_entries(max_len)) return;
-    int L = 16;
-    while (2 * L - 16 <= idx) L *= 2;   // the table that holds idx
-    int n = idx - (L - 16);
+    if (idx >= twiddle_entries()) return;
+    int L, n;
+    if (idx < 8176) {                       // powers of two
+        L = 16;
+        while (2 * L - 16 <= idx) L *= 2;   // the table that holds idx
+        n = idx - (L - 16);
+    } else {                                // 3 * 2^k
+        int r = idx - 8176;
+        L = 48;
+        while (2 * L - 48 <= r) L *= 2;
+        n = r - (L - 48);
+    }
     double s, c;
     sincospi(-2.0 * (double)n / (double)L, &s, &c);
     tw32[idx] = make_float2((float)c, (float)s);
@@ -58,19 +66,19 @@ __global__ void k_tables(Geom g, Band band, AxisTab *axis, float2 *eps32, double
 // over the first-zone grid (the Lorentzian occupation of Eq. 5 below the Fermi
 // level).  n is strictly increasing in mu.  Five small launches of G CTAs:
 //   3 passes of MU_SECT-point multisection in FP32 shrink the bracket
-//   [-B-3, B+3] eV (B bounds |e0|) by (MU_SECT-1)^3 to a few micro-eV; every
-//   thread owns one candidate and a share of the points;
+//   [-B-3, B+3] eV (B bounds |e0|) by (MU_SECT-1)^3 to tens of micro-eV;
+//   every thread owns one candidate and a share of the points;
 //   2 Newton steps in FP64 from the bracket midpoint reach FP64 precision
 //   (the error after a step is about |F''/2F'| times the step squared).
 // Each launch ends the same way: every CTA stores its partial sums, and the
 // last CTA to finish (an atomic counter, which it resets) adds them in a fixed
 // order and publishes the new bracket or mu for the next launch.  No CTA ever
 // waits for another.
-constexpr int MU_SECT = 128;
+constexpr int MU_SECT = 64;
 constexpr int MU_THREADS = 256;
 constexpr int MU_FP32_PASSES = 3;
 constexpr int MU_NEWTON = 2;
-constexpr int MU_SECT_CTAS = 32;   // CTAs of a multisection pass (few partials to add up)
+constexpr int MU_SECT_CTAS = 152;  // CTAs of a multisection pass
 constexpr int MU_RES = 16;   // result slots at the start of acc
 
 // Layout of acc: [MU_RES] results (3 per multisection pass from 0, 2 per
@@ -283,7 +291,7 @@ __global__ void k_mu_given(double mu, InstState *st, double *mu_out)
 
 cudaError_t launch_twiddles(int len, float2 *tw32, double2 *tw64, cudaStream_t s)
 {
-    k_twiddles<<<(twiddle_entries(len) + 255) / 256, 256, 0, s>>>(len, tw32, tw64);
+    k_twiddles<<<(twiddle_entries() + 255) / 256, 256, 0, s>>>(len, tw32, tw64);
     return cudaGetLastError();
 }
 

@@ -21,6 +21,13 @@ template <> struct ColCfg<512>  { static constexpr int C = 8, T = 512, MINB = 2,
 template <> struct ColCfg<1024> { static constexpr int C = 8, T = 512, MINB = 2, MINB_X = 1; };
 template <> struct ColCfg<2048> { static constexpr int C = 4, T = 512, MINB = 2, MINB_X = 1; };
 template <> struct ColCfg<4096> { static constexpr int C = 4, T = 1024, MINB = 1, MINB_X = 1; };
+// lengths 3 * 2^k: 24 values per thread (every radix of their schedules divides 24)
+template <> struct ColCfg<48>   { static constexpr int C = 16, T = 32, MINB = 4, MINB_X = 4; };
+template <> struct ColCfg<96>   { static constexpr int C = 16, T = 64, MINB = 4, MINB_X = 3; };
+template <> struct ColCfg<192>  { static constexpr int C = 16, T = 128, MINB = 3, MINB_X = 2; };
+template <> struct ColCfg<384>  { static constexpr int C = 16, T = 256, MINB = 2, MINB_X = 1; };
+template <> struct ColCfg<768>  { static constexpr int C = 8, T = 256, MINB = 2, MINB_X = 1; };
+template <> struct ColCfg<1536> { static constexpr int C = 4, T = 256, MINB = 2, MINB_X = 1; };
 
 // Strided-axis passes on the paired-column engine (FftPair): C adjacent
 // columns per CTA as C/2 pairs, VPT = (C/2) L / T = 16 values per thread per
@@ -29,6 +36,7 @@ template <int L> struct PairCfg;
 // The p_x product pass (two operands per thread): its own tile sizes.
 template <int L> struct XCfg { static constexpr int C = ColCfg<L>::C, T = ColCfg<L>::T, MINB = ColCfg<L>::MINB_X; };
 template <> struct XCfg<512> { static constexpr int C = 8, T = 256, MINB = 2; };   // VPT 16
+template <> struct XCfg<384> { static constexpr int C = 8, T = 128, MINB = 3; };   // VPT 24
 
 template <> struct PairCfg<128>  { static constexpr int C = 16, T = 64, MINB = 4; };
 template <> struct PairCfg<256>  { static constexpr int C = 16, T = 128, MINB = 4; };
@@ -36,6 +44,10 @@ template <> struct PairCfg<512>  { static constexpr int C = 16, T = 512, MINB = 
 template <> struct PairCfg<1024> { static constexpr int C = 16, T = 512, MINB = 1; };
 template <> struct PairCfg<2048> { static constexpr int C = 8, T = 512, MINB = 1; };
 template <> struct PairCfg<4096> { static constexpr int C = 8, T = 1024, MINB = 1; };
+template <> struct PairCfg<192>  { static constexpr int C = 16, T = 64, MINB = 4; };    // VPT 24
+template <> struct PairCfg<384>  { static constexpr int C = 32, T = 256, MINB = 2; };
+template <> struct PairCfg<768>  { static constexpr int C = 16, T = 256, MINB = 2; };
+template <> struct PairCfg<1536> { static constexpr int C = 8, T = 256, MINB = 2; };
 
 // Contiguous-axis passes (energy axis): C lines of length L per CTA.
 template <int L> struct LineCfg;
@@ -54,15 +66,19 @@ template <typename Real> struct EpsEntry;
 template <> struct EpsEntry<float> { using type = float2; };
 template <> struct EpsEntry<double> { using type = double; };
 
-// Twiddle tables: for every power-of-two length L from 16 up to the plan's
-// longest transform, exp(-2 pi i n / L), n < L, stored contiguously with the
-// length-L table at offset L - 16.
+// Twiddle tables exp(-2 pi i n / L), n < L, one per supported length, stored
+// contiguously: powers of two 16..4096 first (the length-L table at offset
+// L - 16), then 3 * 2^k for 48..1536 (at 8176 + L - 48).
+__host__ __device__ constexpr int twiddle_offset(int L)
+{
+    return fft_len_pow2(L) ? L - 16 : 8176 + L - 48;
+}
+__host__ __device__ constexpr int twiddle_entries() { return 8176 + 3024; }
 template <typename Real>
 __host__ __device__ inline const cx<Real> *twiddles_for(const Work<Real> &w, int L)
 {
-    return (const cx<Real> *)w.tw + (L - 16);
+    return (const cx<Real> *)w.tw + twiddle_offset(L);
 }
-__host__ __device__ constexpr int twiddle_entries(int max_len) { return 2 * max_len - 16; }
 
 // Bytes of dynamic shared memory this launch was given.  Every FFT kernel
 // compares it with what its engines address and returns before touching
@@ -99,6 +115,26 @@ __device__ __forceinline__ int lag_index(int n, int P, int Q)
     case 256: return CALL(256);                                   \
     case 512: return CALL(512);                                   \
     case 1024: return CALL(1024);                                 \
+    case 2048: return CALL(2048);                                 \
+    case 4096: return CALL(4096);                                 \
+    default: return cudaErrorInvalidValue;                        \
+    }
+// Momentum-axis lengths (FP32): powers of two and 3 * 2^k.
+#define LH_P_SWITCH(L_, CALL)                                     \
+    switch (L_) {                                                 \
+    case 16: return CALL(16);                                     \
+    case 32: return CALL(32);                                     \
+    case 48: return CALL(48);                                     \
+    case 64: return CALL(64);                                     \
+    case 96: return CALL(96);                                     \
+    case 128: return CALL(128);                                   \
+    case 192: return CALL(192);                                   \
+    case 256: return CALL(256);                                   \
+    case 384: return CALL(384);                                   \
+    case 512: return CALL(512);                                   \
+    case 768: return CALL(768);                                   \
+    case 1024: return CALL(1024);                                 \
+    case 1536: return CALL(1536);                                 \
     case 2048: return CALL(2048);                                 \
     case 4096: return CALL(4096);                                 \
     default: return cudaErrorInvalidValue;                        \

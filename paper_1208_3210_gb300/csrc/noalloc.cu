@@ -116,8 +116,8 @@ extern "C" lindhard_status lindhard_imchi_noalloc(const lindhard_grid *grid, con
     off_Y = o; o = up256(o + (Y > Y4 ? Y : Y4) * sizeof(float2));
     off_axis = o; o = up256(o + (size_t)g.N * sizeof(AxisTab));
     off_eps = o; o = up256(o + (size_t)g.n_eps * sizeof(float2));
-    off_tw32 = o; o = up256(o + (size_t)twiddle_entries(tw_len) * sizeof(float2));
-    off_tw64 = o; o = up256(o + (size_t)twiddle_entries(tw_len) * sizeof(double2));
+    off_tw32 = o; o = up256(o + (size_t)twiddle_entries() * sizeof(float2));
+    off_tw64 = o; o = up256(o + (size_t)twiddle_entries() * sizeof(double2));
     off_state = o; o = up256(o + sizeof(InstState));
     off_status = o; o = up256(o + sizeof(unsigned));
     off_acc = o; o = up256(o + mu_acc_doubles(G) * sizeof(double));

@@ -74,6 +74,16 @@ static long long next_len(long long x)
     while (L < x) L <<= 1;
     return L;
 }
+// Smallest momentum-axis FFT length >= x: a power of two, or for FP32 also
+// 3 * 2^k (48..1536), which pads N to exactly N + Q/2 = 1.5 N when Q = N.
+static long long next_len_p(long long x, int prec)
+{
+    long long L = next_len(x);
+    if (prec == LINDHARD_FP32)
+        for (long long L3 = 48; L3 <= 1536; L3 <<= 1)
+            if (L3 >= x && L3 < L) L = L3;
+    return L;
+}
 
 struct lindhard_plan {
     int batch = 0;
@@ -184,7 +194,7 @@ static lindhard_status make_geom(const lindhard_grid &gr, Geom &g, int &prec)
         P = N;
     } else {
         // lags |s| <= Q/2 of a length-N sequence: no wrap-around when P >= N + Q/2
-        P = next_len(N + Q / 2);
+        P = next_len_p(N + Q / 2, gr.precision);
     }
     // energy: with the occupied/empty split every lag m in [0, PE) is alias-free
     // once PE >= n_eps (the occupied part sits below the empty part).
@@ -274,8 +284,8 @@ extern "C" lindhard_status lindhard_plan_create(const lindhard_grid *grids, int 
         return n;
     };
     size_t o = 0;
-    p->off_tw32 = o; o = align_up(o + (size_t)twiddle_entries(maxLen) * sizeof(float2));
-    p->off_tw64 = o; o = align_up(o + (size_t)twiddle_entries(maxLen) * sizeof(double2));
+    p->off_tw32 = o; o = align_up(o + (size_t)twiddle_entries() * sizeof(float2));
+    p->off_tw64 = o; o = align_up(o + (size_t)twiddle_entries() * sizeof(double2));
     p->off_status = o; o = align_up(o + sizeof(unsigned));
     auto place = [&](const Need &n) {
         lindhard_plan::Slot sl;
