@@ -225,3 +225,64 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+# --- autograd ---------------------------------------------------------------------
+
+PARAM_NAMES = ("t", "tp", "tpp", "mu", "gamma")
+
+
+class ImChiFunction:
+    """torch.autograd.Function over the library's forward and adjoint calls.
+
+    ``ImChiFunction.apply(params, plan, band)``: params is a float64 tensor of
+    shape [batch, 5] holding (t, t', t'', mu, gamma) per instance (mu is used
+    as given, so the gradient is the partial derivative at fixed mu); band
+    supplies the rest of each instance (ff_a, band_kind).  Returns the
+    concatenated Im chi (float32).  backward() calls lindhard_imchi_backward
+    with w = grad_output and returns dL/dparams.  The plan must be created with
+    backward=True."""
+
+    _cls = None
+
+    @classmethod
+    def _get(cls):
+        if cls._cls is None:
+            import torch
+
+            class _F(torch.autograd.Function):
+                @staticmethod
+                def forward(ctx, params, plan, bands):
+                    ctx.plan = plan
+                    ctx.device = params.device
+                    ctx.bands = _bands_with(params, bands)
+                    return plan.imchi(ctx.bands)
+
+                @staticmethod
+                def backward(ctx, grad_out):
+                    plan = ctx.plan
+                    dp = torch.zeros(5 * plan.batch, dtype=torch.float64, device="cuda")
+                    plan.backward(grad_out.contiguous().float(), bands=ctx.bands, dparams=dp)
+                    return dp.reshape(plan.batch, 5).to(ctx.device), None, None
+
+            cls._cls = _F
+        return cls._cls
+
+    @classmethod
+    def apply(cls, params, plan, bands):
+        return cls._get().apply(params, plan, bands)
+
+
+def _bands_with(params, bands):
+    """Bands with (t, t', t'', mu, gamma) taken from params[i] and the filling
+    unset, so that mu is used as given."""
+    vals = params.detach().double().cpu().numpy().reshape(-1, 5)
+    if isinstance(bands, dict):
+        bands = [bands]
+    out = []
+    for i, b in enumerate(bands):
+        d = dict(b)
+        d.update(t=float(vals[i, 0]), tp=float(vals[i, 1]), tpp=float(vals[i, 2]), mu=float(vals[i, 3]),
+                 gamma=float(vals[i, 4]), filling=float("nan"))
+        out.append(d)
+    return out

@@ -154,3 +154,28 @@ def test_gradient_workload_full_size(lh):
         fd = (Lp - Lm) / (2 * h)
         assert dp[r].item() == pytest.approx(fd, rel=2e-2, abs=2e-3 * abs(L)), (name, dp[r].item(), fd)
     plan.close()
+
+
+def test_autograd_function(lh):
+    """torch.autograd through ImChiFunction: the parameter gradient matches the
+    oracle's FP64 chain rule."""
+    import torch
+    grid = _grid(2, 12, 24, e_max=1.5)
+    band = wl.band_params(filling=1.12, gamma=0.08, ff_a=0.8)
+    b = _oracle_band(band, grid)
+    plan = lh.Plan([grid], backward=True)
+    params = torch.tensor([[b["t"], b["tp"], b["tpp"], b["mu"], b["gamma"]]], dtype=torch.float64,
+                          requires_grad=True)
+    w = torch.from_numpy(wl.loss_weights(grid, seed=6)).cuda().reshape(-1)
+    chi = lh.ImChiFunction.apply(params, plan, [band])
+    L = (chi.double() * w.double()).sum()
+    L.backward()
+    g = params.grad.numpy()[0]
+    # oracle gradient (FP64 chain rule through Eqs. 4-5)
+    A = oracle.spectral(b, grid)
+    gref = oracle.grad_A_full(A, grid, grid["q_extent"], w.cpu().numpy().astype(np.float64))
+    d = oracle.spectral_dtheta(b, grid)
+    for r in range(5):
+        terms = gref * d[r]
+        assert abs(g[r] - terms.sum()) <= 1e-4 * np.abs(terms).sum(), (r, g[r], terms.sum())
+    plan.close()
