@@ -202,6 +202,22 @@ lindhard_status lindhard_plan_profile(lindhard_plan *plan, int enable);
  * (launches[LINDHARD_NUM_PASSES]) since profiling was enabled. */
 lindhard_status lindhard_plan_pass_times(lindhard_plan *plan, double *ms, long long *launches);
 
+/* FP64 sum-rule check of a computed output (Sec. 4's sum over q of Im chi,
+ * Fig. 2(b), which counts electron-hole transitions): summing Eq. 9 over every
+ * lag factorises into the energy correlation of the occupied and empty
+ * densities of states,
+ *   sum_q Im chi(q, w_m) = -c sum_j D_a(e_j) D_b(e_{j+m}),  D(e) = sum_p A(p, e).
+ * For instance `index` of the plan, whose grid must keep every lag
+ * (q_extent = N with one zone, 2N with several):
+ *   out      : device, float32, that instance's output of lindhard_imchi.
+ *   band / A_in : as in lindhard_imchi for that instance (A regenerated).
+ *   sum_q    : device, double [n_omega]: left side, reduced from out in FP64.
+ *   dos_corr : device, double [n_omega]: right side, from A in FP64.
+ * Uses the plan's workspace (do not overlap with a call of the same plan). */
+lindhard_status lindhard_sum_rule(lindhard_plan *plan, int index, const lindhard_band *band,
+                                  const float *A_in, const float *out, double *sum_q, double *dos_corr,
+                                  void *stream);
+
 /* Synchronises `stream` and returns the first device-side error recorded by
  * the plan since the last call (LINDHARD_OK if none), then clears it. */
 lindhard_status lindhard_plan_status(lindhard_plan *plan, void *stream);

@@ -45,6 +45,9 @@ cudaError_t launch_bw_inv_energy(const Geom &g, const Band &band, const AxisTab 
                                  const InstState *st, const float2 *G4, float *dA, double *partial,
                                  const float2 *tw, int tw_len, cudaStream_t s);
 int bw_energy_blocks(const Geom &g);
+cudaError_t launch_sum_rule(const Geom &g, const Band &band, const AxisTab *axis, const float2 *eps,
+                            const InstState *st, const float *A_in, const float *out, double *D, double *sum_q,
+                            double *dos_corr, cudaStream_t s);
 cudaError_t launch_reduce_params(const double *partial, int nblocks, double *out, cudaStream_t s);
 }  // namespace lh
 
@@ -629,6 +632,38 @@ extern "C" lindhard_status lindhard_imchi_backward(lindhard_plan *p, const lindh
     }
     ef = fork_end(p, s0);
     return ef == cudaSuccess ? LINDHARD_OK : cuda_fail(ef, "backward launch");
+}
+
+extern "C" lindhard_status lindhard_sum_rule(lindhard_plan *p, int index, const lindhard_band *band,
+                                             const float *A_in, const float *out, double *sum_q, double *dos_corr,
+                                             void *stream)
+{
+    if (!p || !out || !sum_q || !dos_corr) return fail(LINDHARD_EINVAL, "plan, out, sum_q, dos_corr must be non-NULL");
+    if (index < 0 || index >= p->batch) return fail(LINDHARD_EINVAL, "index out of range");
+    if (p->precision[index] != LINDHARD_FP32) return fail(LINDHARD_EINVAL, "the sum rule reads FP32 outputs");
+    const Geom &g = p->geoms[index];
+    if (g.Q != (g.periodic ? g.N : 2 * g.N))
+        return fail(LINDHARD_EINVAL, "the sum rule needs every lag: q_extent = N (one zone) or 2N (several)");
+    Band b = {};
+    if (A_in == nullptr) {
+        lindhard_status st = make_band(band, b);
+        if (st != LINDHARD_OK) return st;
+        if (b.band_kind == 1 && g.periodic) return fail(LINDHARD_EINVAL, "free electrons need zones > 1");
+        if (b.solve_mu && g.npz > 512) return fail(LINDHARD_EUNSUPPORTED, "the filling solve supports npz <= 512");
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    Work<float> w = work_of<float>(p, index);
+    // D(e) lives in the instance's X buffer (at least n_eps doubles)
+    double *D = (double *)w.X;
+    cudaError_t e = cudaSuccess;
+    if (A_in == nullptr) {
+        e = launch_tables(g, b, w.axis, (float2 *)w.eps, nullptr, s);
+        if (e == cudaSuccess)
+            e = launch_solve_mu(g, b, w.axis, w.state, w.mu_acc, w.barrier, w.status, nullptr, p->mu_G, s);
+    }
+    if (e == cudaSuccess)
+        e = launch_sum_rule(g, b, w.axis, (const float2 *)w.eps, w.state, A_in, out, D, sum_q, dos_corr, s);
+    return e == cudaSuccess ? LINDHARD_OK : cuda_fail(e, "sum-rule launch");
 }
 
 extern "C" lindhard_status lindhard_plan_profile(lindhard_plan *p, int enable)

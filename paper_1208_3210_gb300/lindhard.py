@@ -24,7 +24,8 @@ _STATUS_NAMES = {OK: "OK", EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", E
 # Exported symbols, in the order include/lindhard.h declares them.
 SYMBOLS = ("lindhard_plan_create", "lindhard_plan_sizes", "lindhard_plan_workspace_bytes", "lindhard_imchi",
            "lindhard_imchi_f64", "lindhard_imchi_backward", "lindhard_plan_profile", "lindhard_plan_pass_times",
-           "lindhard_plan_status", "lindhard_plan_destroy", "lindhard_imchi_noalloc", "lindhard_last_error")
+           "lindhard_sum_rule", "lindhard_plan_status", "lindhard_plan_destroy", "lindhard_imchi_noalloc",
+           "lindhard_last_error")
 NOALLOC_SCRATCH_BYTES = 32 << 20
 NUM_PASSES = 7
 PASS_NAMES = ("tables", "mu_solve", "energy_fwd", "py_fwd", "px_product", "py_inv", "energy_inv")
@@ -80,6 +81,8 @@ def load(path: str = LIB_PATH):
         lib.lindhard_last_error.restype = ctypes.c_char_p
         lib.lindhard_imchi_noalloc.argtypes = [ctypes.POINTER(Grid), ctypes.POINTER(Band), vp, vp, vp, vp]
         lib.lindhard_imchi_noalloc.restype = ctypes.c_int
+        lib.lindhard_sum_rule.argtypes = [vp, ctypes.c_int, ctypes.POINTER(Band), vp, vp, vp, vp, vp]
+        lib.lindhard_sum_rule.restype = ctypes.c_int
         for name in ("lindhard_plan_create", "lindhard_plan_sizes", "lindhard_plan_workspace_bytes",
                      "lindhard_imchi", "lindhard_imchi_f64", "lindhard_imchi_backward", "lindhard_plan_profile",
                      "lindhard_plan_pass_times", "lindhard_plan_status"):
@@ -211,6 +214,18 @@ class Plan:
         n = (ctypes.c_longlong * NUM_PASSES)()
         _check(load().lindhard_plan_pass_times(self._h, ms, n))
         return {PASS_NAMES[i]: (ms[i], n[i]) for i in range(NUM_PASSES)}
+
+    def sum_rule(self, index, out_i, band=None, A_in=None, stream=None):
+        """(sum_q Im chi(q, w_m), -c sum_j D_a(e_j) D_b(e_{j+m})) in FP64 for
+        instance `index` (its output slice `out_i`)."""
+        import torch
+        n_omega = self.sizes[index].n_omega
+        sq = torch.empty(n_omega, dtype=torch.float64, device="cuda")
+        dc = torch.empty(n_omega, dtype=torch.float64, device="cuda")
+        b = None if band is None else (band if isinstance(band, Band) else make_band(**band))
+        _check(load().lindhard_sum_rule(self._h, int(index), None if b is None else ctypes.byref(b), _ptr(A_in),
+                                        _ptr(out_i), _ptr(sq), _ptr(dc), _stream(stream)))
+        return sq, dc
 
     def status(self, stream=None):
         _check(load().lindhard_plan_status(self._h, _stream(stream)))

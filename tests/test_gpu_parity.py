@@ -186,3 +186,33 @@ def test_full_size_workload_samples(lh, name, count):
     print(f"{name}: {lx.size} samples, max err {err:.3e} of sample max, sample max / output max "
           f"{scale / mx:.3f}")
     assert err <= TOL32, f"{name}: max err {err:.3e}"
+
+
+@pytest.mark.parametrize("cfg", [dict(zones=1, npz=32, n_eps=48, q_extent=32, n_omega=48),
+                                 dict(zones=2, npz=16, n_eps=40, e_max=1.5, q_extent=64, n_omega=40),
+                                 dict(zones=4, npz=16, n_eps=64, e_max=2.0, q_extent=128, n_omega=32)])
+def test_sum_rule_fp64_reductions(lh, cfg):
+    # Summing Eq. 9 over every lag factorises into the energy correlation of
+    # the densities of states (the oracle pins this identity on the CPU); the
+    # library's FP64 reductions of its own output and of its own A agree, and
+    # its density-of-states side agrees with the oracle's.
+    import torch
+    grid = _full_grid(**cfg)
+    band = wl.band_params(filling=1.1, gamma=0.08, ff_a=1.0)
+    plan = lh.Plan([grid])
+    out = plan.imchi([band])
+    sq, dc = plan.sum_rule(0, out, band=band)
+    plan.status()
+    sq, dc = sq.cpu().numpy(), dc.cpu().numpy()
+    scale = np.abs(dc).max()
+    assert scale > 0
+    assert np.abs(sq - dc).max() <= 1e-5 * scale
+    b = _oracle_band(band, grid)
+    A = oracle.spectral(b, grid)
+    _, _, _, c = oracle.grid_sizes(grid["zones"], grid["npz"], grid["n_eps"], grid["e_max"])
+    j = np.arange(grid["n_eps"])
+    D = A.sum(axis=(0, 1))
+    Da, Db = D * (2 * j + 1 < grid["n_eps"]), D * (2 * j + 1 >= grid["n_eps"])
+    ref = np.array([-c * np.dot(Da[: grid["n_eps"] - m], Db[m:]) for m in range(grid["n_omega"])])
+    assert np.abs(dc - ref).max() <= 1e-6 * np.abs(ref).max()
+    plan.close()
