@@ -48,6 +48,8 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="skip the plan-creation timing of engine variants (paired-column engine)")
     ap.add_argument("--grid", default=None,
                     help="zones,npz,n_eps,e_max: replace the workload's grid (for profiling smaller cases)")
     return ap.parse_args()
@@ -245,7 +247,7 @@ def main():
         # independent instances of mixed size, one graph call per step
         count = int(args.workload.split("_")[1])
         grids, bands = wl.batched_workload(count)
-        plan = lh.Plan(grids, graph=True)
+        plan = lh.Plan(grids, graph=True, autotune=not args.no_autotune)
         args.no_cpu_baseline = True
     else:
         w = wl.WORKLOADS[args.workload]
@@ -256,7 +258,7 @@ def main():
             args.workload = f"{args.workload} grid {args.grid}"
             args.no_cpu_baseline = True
         grids, bands = [grid], [band]
-        plan = lh.Plan(grids)
+        plan = lh.Plan(grids, autotune=not args.no_autotune)
     s = plan.sizes[0]
     out = torch.empty(plan.out_elems(), dtype=torch.float32, device="cuda")
     mu = torch.empty(len(grids), dtype=torch.float64, device="cuda")
@@ -349,6 +351,7 @@ def main():
                        "outputs": plan.out_elems(),
                        "l2": "no flush: each step streams {:.2f} GB of intermediates through HBM, "
                              "far above the 129 MB L2".format(pipeline_bytes / 1e9),
+                       "autotune": not args.no_autotune,
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "roofline": {"bound": "hbm", "kernel": KERNEL_NAMES[dom], "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,

@@ -123,6 +123,11 @@ typedef struct {
  * ones records again (and updates the executable graph in place).  The first
  * call also runs the sequence once directly. */
 #define LINDHARD_PLAN_GRAPH 4u
+/* Plan flag: at creation, time the available engine variants of the passes
+ * along p_y for each FP32 grid of the plan (CUDA events, a few launches each)
+ * and use the faster; results are cached per process and, when the
+ * environment variable LINDHARD_TUNE_CACHE names a file, in that JSON file. */
+#define LINDHARD_PLAN_AUTOTUNE 8u
 
 /* Builds a plan for `batch` instances with the given grids (host array).
  * Validates the grids, picks FFT lengths (the smallest supported length that
@@ -131,7 +136,8 @@ typedef struct {
  * allocates the device workspace and twiddle tables on the current device.
  * Without LINDHARD_PLAN_CONCURRENT instances are computed one after another
  * and share one workspace sized for the largest.  flags: any of
- * LINDHARD_PLAN_BACKWARD, LINDHARD_PLAN_CONCURRENT, LINDHARD_PLAN_GRAPH.
+ * LINDHARD_PLAN_BACKWARD, LINDHARD_PLAN_CONCURRENT, LINDHARD_PLAN_GRAPH,
+ * LINDHARD_PLAN_AUTOTUNE.
  * On success *out receives the plan. */
 lindhard_status lindhard_plan_create(const lindhard_grid *grids, int batch,
                                      unsigned flags, lindhard_plan **out);

@@ -236,10 +236,12 @@ cudaError_t launch_fwd_y2_t(const Geom &g, const Work<Real> &w, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// variant 1: paired-column engine (L >= 128, FP32); 0: single-column engine
 template <typename Real, int L>
-cudaError_t launch_fwd_y_t(const Geom &g, const Work<Real> &w, cudaStream_t s)
+cudaError_t launch_fwd_y_t(const Geom &g, const Work<Real> &w, cudaStream_t s, int variant)
 {
-    if constexpr (L >= 128 && sizeof(Real) == 4) return launch_fwd_y2_t<Real, L>(g, w, s);
+    if constexpr (L >= 128 && sizeof(Real) == 4)
+        if (variant == 1) return launch_fwd_y2_t<Real, L>(g, w, s);
     constexpr int C = ColCfg<L>::C, T = ColCfg<L>::T;
     using E = Fft<Real, L, C, T, MAP_COL, false>;
     size_t smem = sizeof(cx<Real>) * E::SMEM_ELEMS;
@@ -265,15 +267,15 @@ cudaError_t launch_fwd_energy(const Geom &g, const Band &band, const Work<double
     LH_LEN_SWITCH_SMALL(g.PE, CALL)
 #undef CALL
 }
-cudaError_t launch_fwd_y(const Geom &g, const Work<float> &w, cudaStream_t s)
+cudaError_t launch_fwd_y(const Geom &g, const Work<float> &w, cudaStream_t s, int variant)
 {
-#define CALL(L) launch_fwd_y_t<float, L>(g, w, s)
+#define CALL(L) launch_fwd_y_t<float, L>(g, w, s, variant)
     LH_P_SWITCH(g.P, CALL)
 #undef CALL
 }
-cudaError_t launch_fwd_y(const Geom &g, const Work<double> &w, cudaStream_t s)
+cudaError_t launch_fwd_y(const Geom &g, const Work<double> &w, cudaStream_t s, int variant)
 {
-#define CALL(L) launch_fwd_y_t<double, L>(g, w, s)
+#define CALL(L) launch_fwd_y_t<double, L>(g, w, s, variant)
     LH_LEN_SWITCH_SMALL(g.P, CALL)
 #undef CALL
 }

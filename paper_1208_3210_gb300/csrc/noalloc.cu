@@ -36,9 +36,9 @@ cudaError_t launch_solve_mu(const Geom &g, const Band &band, const AxisTab *axis
                             unsigned *bar, unsigned *status, double *mu_out, int G, cudaStream_t s);
 cudaError_t launch_fwd_energy(const Geom &g, const Band &band, const Work<float> &w, const float *A_in,
                               cudaStream_t s);
-cudaError_t launch_fwd_y(const Geom &g, const Work<float> &w, cudaStream_t s);
+cudaError_t launch_fwd_y(const Geom &g, const Work<float> &w, cudaStream_t s, int variant);
 cudaError_t launch_x_product(const Geom &g, const Work<float> &w, cudaStream_t s);
-cudaError_t launch_inv_y(const Geom &g, const Work<float> &w, cudaStream_t s);
+cudaError_t launch_inv_y(const Geom &g, const Work<float> &w, cudaStream_t s, int variant);
 cudaError_t launch_inv_energy(const Geom &g, const Work<float> &w, float *out, cudaStream_t s);
 }  // namespace lh
 
@@ -154,9 +154,9 @@ extern "C" lindhard_status lindhard_imchi_noalloc(const lindhard_grid *grid, con
             e = launch_solve_mu(g, b, w.axis, w.state, w.mu_acc, w.barrier, w.status, mu_out, G, s);
     }
     if (e == cudaSuccess) e = launch_fwd_energy(g, b, w, A_in, s);
-    if (e == cudaSuccess) e = launch_fwd_y(g, w, s);
+    if (e == cudaSuccess) e = launch_fwd_y(g, w, s, 1);
     if (e == cudaSuccess) e = launch_x_product(g, w, s);
-    if (e == cudaSuccess) e = launch_inv_y(g, w, s);
+    if (e == cudaSuccess) e = launch_inv_y(g, w, s, 1);
     if (e == cudaSuccess) e = launch_inv_energy(g, w, out, s);
     if (e != cudaSuccess) return set_error(LINDHARD_ECUDA, cudaGetErrorString(e));
     return LINDHARD_OK;

@@ -5,8 +5,14 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <stdlib.h>
+
 #include <algorithm>
+#include <fstream>
+#include <map>
+#include <mutex>
 #include <new>
+#include <sstream>
 #include <string>
 #include <vector>
 
@@ -26,12 +32,12 @@ cudaError_t launch_fwd_energy(const Geom &g, const Band &band, const Work<float>
                               cudaStream_t s);
 cudaError_t launch_fwd_energy(const Geom &g, const Band &band, const Work<double> &w, const double *A_in,
                               cudaStream_t s);
-cudaError_t launch_fwd_y(const Geom &g, const Work<float> &w, cudaStream_t s);
-cudaError_t launch_fwd_y(const Geom &g, const Work<double> &w, cudaStream_t s);
+cudaError_t launch_fwd_y(const Geom &g, const Work<float> &w, cudaStream_t s, int variant);
+cudaError_t launch_fwd_y(const Geom &g, const Work<double> &w, cudaStream_t s, int variant);
 cudaError_t launch_x_product(const Geom &g, const Work<float> &w, cudaStream_t s);
 cudaError_t launch_x_product(const Geom &g, const Work<double> &w, cudaStream_t s);
-cudaError_t launch_inv_y(const Geom &g, const Work<float> &w, cudaStream_t s);
-cudaError_t launch_inv_y(const Geom &g, const Work<double> &w, cudaStream_t s);
+cudaError_t launch_inv_y(const Geom &g, const Work<float> &w, cudaStream_t s, int variant);
+cudaError_t launch_inv_y(const Geom &g, const Work<double> &w, cudaStream_t s, int variant);
 cudaError_t launch_inv_energy(const Geom &g, const Work<float> &w, float *out, cudaStream_t s);
 cudaError_t launch_inv_energy(const Geom &g, const Work<double> &w, double *out, cudaStream_t s);
 cudaError_t launch_w_energy(const Geom &g, const float *w, float2 *WU1, const float2 *tw, int tw_len,
@@ -104,6 +110,9 @@ struct lindhard_plan {
     size_t off_tw32 = 0, off_tw64 = 0, off_status = 0;
     int tw_len = 0;
     bool backward = false;       // LINDHARD_PLAN_BACKWARD
+    // engine variant of the p_y passes per instance (0 single-column,
+    // 1 paired-column); set by the autotuner (LINDHARD_PLAN_AUTOTUNE)
+    std::vector<int> yvar_fwd, yvar_inv;
     bool concurrent = false;     // LINDHARD_PLAN_CONCURRENT
     bool graph = false;          // LINDHARD_PLAN_GRAPH
     // concurrent execution: instances on plan-owned streams, forked from and
@@ -233,11 +242,101 @@ static lindhard_status make_geom(const lindhard_grid &gr, Geom &g, int &prec)
 static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 extern "C" void lindhard_plan_destroy(lindhard_plan *p);
 
+// ---------------------------------------------------------------------------
+// Autotuner.  For every distinct momentum geometry of an FP32 plan it times the
+// single-column and paired-column engines of both p_y passes with CUDA events
+// (on the plan's own workspace; the data are whatever the workspace holds, the
+// timing does not depend on them) and keeps the faster.  Results are cached per
+// process, and in the JSON file named by LINDHARD_TUNE_CACHE when that is set:
+// one entry per line, {"<gpu>|P=..|N=..|PE=..|Q=..|fwd_y": variant, ...},
+// variant 1 = paired-column engine, 0 = single-column engine.  Cached
+// entries are used as they are (a cache file may pin a variant).
+template <typename Real>
+static Work<Real> work_of(lindhard_plan *p, int i);
+
+static std::mutex g_tune_mutex;
+static std::map<std::string, int> g_tune;
+static std::string g_tune_path;   // cache file last merged into g_tune
+
+static void tune_load()
+{
+    const char *path = getenv("LINDHARD_TUNE_CACHE");
+    if (!path || g_tune_path == path) return;
+    g_tune_path = path;
+    std::ifstream f(path);
+    std::string line;
+    while (std::getline(f, line)) {
+        size_t a = line.find('"'), b = line.find('"', a + 1), c = line.find(':', b);
+        if (a == std::string::npos || b == std::string::npos || c == std::string::npos) continue;
+        g_tune[line.substr(a + 1, b - a - 1)] = atoi(line.c_str() + c + 1) ? 1 : 0;
+    }
+}
+static void tune_save()
+{
+    const char *path = getenv("LINDHARD_TUNE_CACHE");
+    if (!path) return;
+    std::ofstream f(path);
+    f << "{\n";
+    size_t i = 0;
+    for (auto &kv : g_tune) f << "  \"" << kv.first << "\": " << kv.second << (++i < g_tune.size() ? ",\n" : "\n");
+    f << "}\n";
+}
+
+template <typename F>
+static float time_launches(F &&launch, cudaEvent_t a, cudaEvent_t b)
+{
+    for (int i = 0; i < 2; ++i) launch();
+    cudaEventRecord(a, 0);
+    for (int i = 0; i < 5; ++i) launch();
+    cudaEventRecord(b, 0);
+    cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    return ms;
+}
+
+static cudaError_t autotune(lindhard_plan *p)
+{
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    tune_load();
+    cudaDeviceProp prop;
+    cudaError_t e = cudaGetDeviceProperties(&prop, p->device);
+    if (e != cudaSuccess) return e;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    for (int i = 0; i < p->batch && e == cudaSuccess; ++i) {
+        const Geom &g = p->geoms[i];
+        if (p->precision[i] != LINDHARD_FP32 || g.P < 128) continue;
+        std::ostringstream key;
+        key << prop.name << "|P=" << g.P << "|N=" << g.N << "|PE=" << g.PE << "|Q=" << g.Q;
+        std::string kf = key.str() + "|fwd_y", ki = key.str() + "|inv_y";
+        if (!g_tune.count(kf) || !g_tune.count(ki)) {
+            Work<float> w = work_of<float>(p, i);
+            float t[2][2];
+            for (int v = 0; v < 2; ++v) {
+                t[0][v] = time_launches([&] { return launch_fwd_y(g, w, 0, v); }, a, b);
+                t[1][v] = time_launches([&] { return launch_inv_y(g, w, 0, v); }, a, b);
+            }
+            e = cudaGetLastError();
+            g_tune[kf] = t[0][1] < t[0][0] ? 1 : 0;
+            g_tune[ki] = t[1][1] < t[1][0] ? 1 : 0;
+        }
+        p->yvar_fwd[i] = g_tune[kf];
+        p->yvar_inv[i] = g_tune[ki];
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    tune_save();
+    return e == cudaSuccess ? cudaDeviceSynchronize() : e;
+}
+
 extern "C" lindhard_status lindhard_plan_create(const lindhard_grid *grids, int batch, unsigned flags,
                                                 lindhard_plan **out)
 {
     if (!grids || !out || batch < 1) return fail(LINDHARD_EINVAL, "grids/out must be non-NULL and batch >= 1");
-    const unsigned known = LINDHARD_PLAN_BACKWARD | LINDHARD_PLAN_CONCURRENT | LINDHARD_PLAN_GRAPH;
+    const unsigned known = LINDHARD_PLAN_BACKWARD | LINDHARD_PLAN_CONCURRENT | LINDHARD_PLAN_GRAPH |
+                           LINDHARD_PLAN_AUTOTUNE;
     if (flags & ~known) return fail(LINDHARD_EINVAL, "unknown plan flags");
     *out = nullptr;
     lindhard_plan *p = new (std::nothrow) lindhard_plan;
@@ -340,6 +439,9 @@ extern "C" lindhard_status lindhard_plan_create(const lindhard_grid *grids, int 
         }
         if (e == cudaSuccess && p->graph) e = cudaStreamCreateWithFlags(&p->origin, cudaStreamNonBlocking);
     }
+    p->yvar_fwd.assign(batch, 1);
+    p->yvar_inv.assign(batch, 1);
+    if (e == cudaSuccess && (flags & LINDHARD_PLAN_AUTOTUNE)) e = autotune(p);
     if (e != cudaSuccess) {
         lindhard_plan_destroy(p);
         return cuda_fail(e, "plan set-up");
@@ -488,9 +590,9 @@ static cudaError_t enqueue_forward(lindhard_plan *p, const std::vector<Band> &bs
         const Real *a_i = A_in ? A_in + a_off : nullptr;
         Real *o_i = out + o_off;
         if (e == cudaSuccess) e = timed(p, 2, s, [&] { return launch_fwd_energy(g, b, w, a_i, s); });
-        if (e == cudaSuccess) e = timed(p, 3, s, [&] { return launch_fwd_y(g, w, s); });
+        if (e == cudaSuccess) e = timed(p, 3, s, [&] { return launch_fwd_y(g, w, s, p->yvar_fwd[i]); });
         if (e == cudaSuccess) e = timed(p, 4, s, [&] { return launch_x_product(g, w, s); });
-        if (e == cudaSuccess) e = timed(p, 5, s, [&] { return launch_inv_y(g, w, s); });
+        if (e == cudaSuccess) e = timed(p, 5, s, [&] { return launch_inv_y(g, w, s, p->yvar_inv[i]); });
         if (e == cudaSuccess) e = timed(p, 6, s, [&] { return launch_inv_energy(g, w, o_i, s); });
         a_off += (size_t)g.N * g.N * g.n_eps;
         o_off += (size_t)g.Q * g.Q * g.n_omega;
@@ -617,7 +719,7 @@ extern "C" lindhard_status lindhard_imchi_backward(lindhard_plan *p, const lindh
                 e = launch_solve_mu(g, b, wk.axis, wk.state, wk.mu_acc, wk.barrier, wk.status, nullptr, p->mu_G, s);
         }
         if (e == cudaSuccess) e = launch_fwd_energy(g, b, wk, A_in ? A_in + a_off : nullptr, s);   // X = U1
-        if (e == cudaSuccess) e = launch_fwd_y(g, wk, s);                                           // Y = U2
+        if (e == cudaSuccess) e = launch_fwd_y(g, wk, s, p->yvar_fwd[i]);                           // Y = U2
         if (e == cudaSuccess) e = launch_w_energy(g, w + o_off, X, tw, p->tw_len, s);                // X = WU1
         if (e == cudaSuccess) e = launch_w_y(g, X, Z, tw, p->tw_len, s);                             // Z = WU2
         if (e == cudaSuccess) e = launch_bw_product(g, Y, Z, tw, p->tw_len, s);                      // Y = G3
