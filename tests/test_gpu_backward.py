@@ -166,14 +166,15 @@ def test_autograd_function(lh):
     plan = lh.Plan([grid], backward=True)
     params = torch.tensor([[b["t"], b["tp"], b["tpp"], b["mu"], b["gamma"]]], dtype=torch.float64,
                           requires_grad=True)
-    w = torch.from_numpy(wl.loss_weights(grid, seed=6)).cuda().reshape(-1)
+    w_np = wl.loss_weights(grid, seed=6)
+    w = torch.from_numpy(w_np).cuda().reshape(-1)
     chi = lh.ImChiFunction.apply(params, plan, [band])
     L = (chi.double() * w.double()).sum()
     L.backward()
     g = params.grad.numpy()[0]
     # oracle gradient (FP64 chain rule through Eqs. 4-5)
     A = oracle.spectral(b, grid)
-    gref = oracle.grad_A_full(A, grid, grid["q_extent"], w.cpu().numpy().astype(np.float64))
+    gref = oracle.grad_A_full(A, grid, grid["q_extent"], w_np.astype(np.float64))
     d = oracle.spectral_dtheta(b, grid)
     for r in range(5):
         terms = gref * d[r]
