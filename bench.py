@@ -37,7 +37,7 @@ PASS_FILES = {  # kernel source of each timed pass (for traffic-record staleness
     "py_inv": "k_inverse.cu", "energy_inv": "k_inverse.cu",
 }
 KERNEL_NAMES = {"batch": "all passes of all instances (graph)", "energy_fwd": "k_fwd_energy", "py_fwd": "k_fwd_y", "px_product": "k_x_product",
-                "py_inv": "k_inv_y", "energy_inv": "k_inv_energy", "tables": "k_tables", "mu_solve": "k_solve_mu"}
+                "py_inv": "k_inv_y", "energy_inv": "k_inv_energy", "tables": "k_setup", "mu_solve": "k_mu_sect, k_mu_halley"}
 
 
 def parse_args():

@@ -73,7 +73,7 @@ typedef struct {
     double filling;     /* electrons per site incl. spin (rigid band, Sec. 3);
                            mu is then solved in FP64 so that
                            (2/npz^2) sum_k [1/2 - atan(xi_k/gamma)/pi] = filling
-                           over the first-zone grid (pts_per_zone <= 512)   */
+                           over the first-zone grid                        */
     double gamma;       /* Lorentzian half-width (Eq. 5), > 0                 */
     double ff_a;        /* |M(p)|^2 = exp(-|p|^2 ff_a^2 / 8); 0 => |M|^2 = 1   */
     int band_kind;      /* 0 tight binding; 1 free electrons, xi = |p|^2/2 - mu */

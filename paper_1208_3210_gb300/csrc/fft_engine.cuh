@@ -44,16 +44,25 @@ template <typename C> __device__ __forceinline__ C mul_i(C a) { return mk<C>(-a.
 template <typename C> __device__ __forceinline__ C mul_mi(C a) { return mk<C>(a.y, -a.x); }  // -i * a
 
 // ---------------------------------------------------------------------------
-// Radix schedules (forward order).  L = prod radix(L, s).  Powers of two up
-// to 4096 and 3 * 2^k from 48 to 1536 (momentum axes padded to exactly 1.5 N).
+// Radix schedules (forward order).  L = prod radix(L, s, F).  Two families:
+//   F = 0: few stages with large radices (8, 16, 24) for powers of two up to
+//          4096 and 3 * 2^k from 48 to 1536 (momentum axes padded to exactly
+//          1.5 N); tiles hold a multiple of 8, 16 or 24 values per thread.
+//   F = 1: radices dividing 12 (6, 12, 4) for 192, 384, 768 and 1536: one or
+//          two more stages, but tiles of 12 values per thread, half the
+//          registers of the 24-value tiles.
+// An engine takes family 0 when its values per thread allow it, else 1.
 __host__ __device__ constexpr bool fft_len_pow2(int L) { return (L & (L - 1)) == 0; }
-__host__ __device__ constexpr int fft_nstages(int L)
+__host__ __device__ constexpr bool fft_has_family1(int L) { return L == 192 || L == 384 || L == 768 || L == 1536; }
+__host__ __device__ constexpr int fft_nstages(int L, int F = 0)
 {
-    return fft_len_pow2(L) ? (L <= 16 ? 1 : (L <= 256 ? 2 : 3)) : (L <= 96 ? 2 : 3);
+    return F == 1 ? (L == 192 ? 3 : (L == 1536 ? 5 : 4))
+         : fft_len_pow2(L) ? (L <= 16 ? 1 : (L <= 256 ? 2 : 3)) : (L <= 96 ? 2 : 3);
 }
-__host__ __device__ constexpr int fft_fwd_radix(int L, int s)
+__host__ __device__ constexpr int fft_fwd_radix(int L, int s, int F = 0)
 {
-    return L == 16 ? 16
+    return F == 1 ? (s == 0 ? (L == 192 || L == 768 ? 12 : 6) : 4)
+         : L == 16 ? 16
          : L == 32 ? (s == 0 ? 8 : 4)
          : L == 64 ? 8
          : L == 128 ? (s == 0 ? 16 : 8)
@@ -69,19 +78,26 @@ __host__ __device__ constexpr int fft_fwd_radix(int L, int s)
          : L == 768 ? (s < 2 ? 8 : 12)
          : /* 1536 */ (s < 2 ? 8 : 24);
 }
-__host__ __device__ constexpr int fft_radix(int L, int s, bool inv)
+__host__ __device__ constexpr int fft_radix(int L, int s, bool inv, int F = 0)
 {
-    return inv ? fft_fwd_radix(L, fft_nstages(L) - 1 - s) : fft_fwd_radix(L, s);
+    return inv ? fft_fwd_radix(L, fft_nstages(L, F) - 1 - s, F) : fft_fwd_radix(L, s, F);
 }
-__host__ __device__ constexpr int fft_ns_before(int L, int s, bool inv)
+__host__ __device__ constexpr int fft_ns_before(int L, int s, bool inv, int F = 0)
 {
-    return s == 0 ? 1 : fft_ns_before(L, s - 1, inv) * fft_radix(L, s - 1, inv);
+    return s == 0 ? 1 : fft_ns_before(L, s - 1, inv, F) * fft_radix(L, s - 1, inv, F);
 }
-// every radix of the schedule divides v (values per thread)
-__host__ __device__ constexpr bool fft_radices_divide(int L, int v, int s = 0)
+__host__ __device__ constexpr int fft_sched_len(int L, int F, int s = 0)
 {
-    return s >= fft_nstages(L) ? true : (v % fft_fwd_radix(L, s) == 0 && fft_radices_divide(L, v, s + 1));
+    return s >= fft_nstages(L, F) ? 1 : fft_fwd_radix(L, s, F) * fft_sched_len(L, F, s + 1);
 }
+// every radix of family F's schedule divides v (values per thread)
+__host__ __device__ constexpr bool fft_radices_divide(int L, int v, int F = 0, int s = 0)
+{
+    return (F == 1 && !fft_has_family1(L)) ? false
+         : s >= fft_nstages(L, F) ? true
+         : (v % fft_fwd_radix(L, s, F) == 0 && fft_radices_divide(L, v, F, s + 1));
+}
+__host__ __device__ constexpr int fft_family(int L, int v) { return fft_radices_divide(L, v, 0) ? 0 : 1; }
 
 // ---------------------------------------------------------------------------
 // Exact small DFTs in registers.  cos(2 pi m / 48) for m = 0..12 (multiples of
@@ -219,16 +235,18 @@ enum { MAP_COL = 0, MAP_LINE = 1 };
 template <typename Real, int L, int C, int T, int MAP, bool INV>
 struct Fft {
     using Cx = cx<Real>;
-    static constexpr int NS = fft_nstages(L);
     static constexpr int VPT = C * L / T;
+    static constexpr int F = fft_family(L, VPT);             // radix schedule family
+    static constexpr int NS = fft_nstages(L, F);
     static constexpr int LP = L + L / 16;                    // padded line (MAP_LINE)
-    static constexpr int R0 = fft_radix(L, 0, INV);
-    static constexpr int RL = fft_radix(L, NS - 1, INV);
+    static constexpr int R0 = fft_radix(L, 0, INV, F);
+    static constexpr int RL = fft_radix(L, NS - 1, INV, F);
     // MAP_COL rows: one empty row after every R0 rows, so that the first
     // exchange's writes (rows R0 apart) fall into different banks
     static constexpr int SMEM_ELEMS = (MAP == MAP_COL) ? (L + L / R0) * C : C * LP;
     static_assert((C * L) % T == 0, "tile must split evenly over threads");
-    static_assert(fft_radices_divide(L, VPT), "values per thread must be a multiple of every radix");
+    static_assert(fft_radices_divide(L, VPT, F), "values per thread must be a multiple of every radix");
+    static_assert(fft_sched_len(L, F) == L, "radix schedule must multiply to L");
     static_assert(MAP == MAP_LINE || T % C == 0, "column map needs T % C == 0");
 
     __device__ __forceinline__ static int saddr(int col, int n)
@@ -261,9 +279,9 @@ struct Fft {
     __device__ __forceinline__ static void stage_rest(Cx *v, Cx *sm, const Cx *__restrict__ tw)
     {
         if constexpr (S < NS) {
-            constexpr int Rp = fft_radix(L, S - 1, INV);
-            constexpr int Nsp = fft_ns_before(L, S - 1, INV);
-            constexpr int Rs = fft_radix(L, S, INV);
+            constexpr int Rp = fft_radix(L, S - 1, INV, F);
+            constexpr int Nsp = fft_ns_before(L, S - 1, INV, F);
+            constexpr int Rs = fft_radix(L, S, INV, F);
             constexpr int Ns = Nsp * Rp;
             // write the previous stage's outputs (Stockham order)
 #pragma unroll
@@ -323,13 +341,15 @@ template <typename Real, int L, int C, int T, bool INV>
 struct FftPair {
     using Cx = cx<Real>;
     static constexpr int CP = C / 2;                 // column pairs per tile
-    static constexpr int NS = fft_nstages(L);
     static constexpr int VPT = CP * L / T;
-    static constexpr int R0 = fft_radix(L, 0, INV);
-    static constexpr int RL = fft_radix(L, NS - 1, INV);
+    static constexpr int F = fft_family(L, VPT);     // radix schedule family
+    static constexpr int NS = fft_nstages(L, F);
+    static constexpr int R0 = fft_radix(L, 0, INV, F);
+    static constexpr int RL = fft_radix(L, NS - 1, INV, F);
     static constexpr int SMEM_ELEMS = (L + L / R0) * C;   // one empty row after every R0 rows
     static_assert(C % 2 == 0 && T % CP == 0 && (CP * L) % T == 0, "tile must split evenly over threads");
-    static_assert(fft_radices_divide(L, VPT), "values per thread must be a multiple of every radix");
+    static_assert(fft_radices_divide(L, VPT, F), "values per thread must be a multiple of every radix");
+    static_assert(fft_sched_len(L, F) == L, "radix schedule must multiply to L");
 
     // the thread's column pair (columns 2p and 2p + 1 of the tile)
     __device__ __forceinline__ static int pair() { return threadIdx.x % CP; }
@@ -370,9 +390,9 @@ struct FftPair {
     __device__ __forceinline__ static void stage_rest(Cx *va, Cx *vb, Cx *sm, const Cx *__restrict__ tw)
     {
         if constexpr (S < NS) {
-            constexpr int Rp = fft_radix(L, S - 1, INV);
-            constexpr int Nsp = fft_ns_before(L, S - 1, INV);
-            constexpr int Rs = fft_radix(L, S, INV);
+            constexpr int Rp = fft_radix(L, S - 1, INV, F);
+            constexpr int Nsp = fft_ns_before(L, S - 1, INV, F);
+            constexpr int Rs = fft_radix(L, S, INV, F);
             constexpr int Ns = Nsp * Rp;
             const int p = pair();
 #pragma unroll

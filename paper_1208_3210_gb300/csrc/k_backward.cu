@@ -371,7 +371,7 @@ __global__ void k_reduce_params(const double *__restrict__ partial, int nblocks,
 template <typename K>
 static cudaError_t set_smem(K k, size_t smem)
 {
-    return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return smem_attrs(k, smem);
 }
 
 template <int L>

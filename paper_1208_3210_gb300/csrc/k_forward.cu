@@ -77,7 +77,8 @@ k_fwd_energy(Geom g, Band band, const AxisTab *__restrict__ axis,
                         e = eps[n] - s_xhi[col];
                     }
                     Real d = e * e + g2;
-                    if constexpr (sizeof(Real) == 4) A = s_amp[col] * __frcp_rn(d);
+                    // FP32: the hardware reciprocal (2 ulp; d lies in [gamma^2, 4 e_max^2])
+                    if constexpr (sizeof(Real) == 4) A = __fdividef(s_amp[col], d);
                     else A = s_amp[col] / d;
                 }
             }
@@ -101,21 +102,26 @@ k_fwd_energy(Geom g, Band band, const AxisTab *__restrict__ axis,
     __syncthreads();
     const Real half = (Real)0.5;
     constexpr int H = L / 2 + 1;                 // non-redundant frequencies (= g.H)
-    constexpr int SP = (H + 7) / 8 * 8;          // row stride (= g.SP)
-#pragma unroll 4
-    for (int idx = threadIdx.x; idx < C * H; idx += T) {
-        int col = idx / H, k = idx % H;
-        long long line = line0 + col;
-        if (line >= nlines) continue;
+    constexpr int SP = (H + 7) / 8 * 8;          // row stride (= g.SP); SP >= H + 1
+    constexpr int HP = (H + 1) / 2;              // frequency pairs (k, k + 1), k even
+    // a^ = (Z(k) + conj Z(-k)) / 2 ; b^ = (Z(k) - conj Z(-k)) / 2i
+    auto sep = [&](int col, int k, Cx &ah, Cx &bh) {
         Cx zk = sm[E::saddr(col, k)];
         Cx zm = sm[E::saddr(col, (L - k) & (L - 1))];
-        // a^ = (Z(k) + conj Z(-k)) / 2 ; b^ = (Z(k) - conj Z(-k)) / 2i
-        Cx ah = mk<Cx>(half * (zk.x + zm.x), half * (zk.y - zm.y));
-        Cx dd = mk<Cx>(zk.x - zm.x, zk.y + zm.y);
-        Cx bh = mk<Cx>(half * dd.y, -half * dd.x);
+        ah = mk<Cx>(half * (zk.x + zm.x), half * (zk.y - zm.y));
+        bh = mk<Cx>(half * (zk.y + zm.y), -half * (zk.x - zm.x));
+    };
+#pragma unroll 4
+    for (int idx = threadIdx.x; idx < C * HP; idx += T) {
+        int col = idx / HP, k = 2 * (idx % HP);
+        long long line = line0 + col;
+        if (line >= nlines) continue;
+        Cx a0, b0, a1, b1;
+        sep(col, k, a0, b0);
+        sep(col, k + 1, a1, b1);   // k + 1 = H lands in the row's padding
         Cx *row = U1 + line * (2LL * SP);
-        row[k] = ah;
-        row[SP + k] = bh;
+        gst2(row + k, a0, a1);
+        gst2(row + SP + k, b0, b1);
     }
 }
 
@@ -164,12 +170,12 @@ k_fwd_y(Geom g, const cx<Real> *__restrict__ U1, cx<Real> *__restrict__ U2,
 
 // Paired-column version of the p_y pass (L >= 128): each thread moves the two
 // adjacent columns (c, c + 1) with 16-byte accesses.
-template <typename Real, int L>
-__global__ void __launch_bounds__(PairCfg<L>::T, PairCfg<L>::MINB)
+template <typename Real, int L, typename Cfg>
+__global__ void __launch_bounds__(Cfg::T, Cfg::MINB)
 k_fwd_y2(Geom g, const cx<Real> *__restrict__ U1, cx<Real> *__restrict__ U2,
          const cx<Real> *__restrict__ tw)
 {
-    constexpr int C = PairCfg<L>::C, T = PairCfg<L>::T;
+    constexpr int C = Cfg::C, T = Cfg::T;
     using E = FftPair<Real, L, C, T, false>;
     using Cx = cx<Real>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -213,7 +219,7 @@ cudaError_t launch_fwd_energy_t(const Geom &g, const Band &band, const Work<Real
     using E = Fft<Real, L, C, T, MAP_LINE, false>;
     size_t smem = sizeof(cx<Real>) * E::SMEM_ELEMS;
     auto k = k_fwd_energy<Real, L>;
-    static const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    static const cudaError_t e = smem_attrs(k, smem);
     if (e != cudaSuccess) return e;
     long long nlines = (long long)g.N * g.N;
     unsigned grid = (unsigned)((nlines + C - 1) / C);
@@ -222,31 +228,35 @@ cudaError_t launch_fwd_energy_t(const Geom &g, const Band &band, const Work<Real
     return cudaGetLastError();
 }
 
-template <typename Real, int L>
+template <typename Real, int L, typename Cfg>
 cudaError_t launch_fwd_y2_t(const Geom &g, const Work<Real> &w, cudaStream_t s)
 {
-    constexpr int C = PairCfg<L>::C, T = PairCfg<L>::T;
+    constexpr int C = Cfg::C, T = Cfg::T;
     using E = FftPair<Real, L, C, T, false>;
     size_t smem = sizeof(cx<Real>) * E::SMEM_ELEMS;
-    auto k = k_fwd_y2<Real, L>;
-    static const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto k = k_fwd_y2<Real, L, Cfg>;
+    static const cudaError_t e = smem_attrs(k, smem);
     if (e != cudaSuccess) return e;
     dim3 grid((2 * g.SP + C - 1) / C, g.N);
     k<<<grid, T, smem, s>>>(g, (const cx<Real> *)w.X, (cx<Real> *)w.Y, twiddles_for<Real>(w, L));
     return cudaGetLastError();
 }
 
-// variant 1: paired-column engine (L >= 128, FP32); 0: single-column engine
+// variant 0: single-column engine; 1: paired-column engine (L >= 128, FP32);
+// 2: paired-column engine with 12 values per thread (3 * 2^k >= 192, FP32)
 template <typename Real, int L>
 cudaError_t launch_fwd_y_t(const Geom &g, const Work<Real> &w, cudaStream_t s, int variant)
 {
-    if constexpr (L >= 128 && sizeof(Real) == 4)
-        if (variant == 1) return launch_fwd_y2_t<Real, L>(g, w, s);
+    if constexpr (L >= 128 && sizeof(Real) == 4) {
+        if (variant == 1) return launch_fwd_y2_t<Real, L, PairCfg<L>>(g, w, s);
+        if constexpr (fft_has_family1(L))
+            if (variant == 2) return launch_fwd_y2_t<Real, L, PairCfg12<L>>(g, w, s);
+    }
     constexpr int C = ColCfg<L>::C, T = ColCfg<L>::T;
     using E = Fft<Real, L, C, T, MAP_COL, false>;
     size_t smem = sizeof(cx<Real>) * E::SMEM_ELEMS;
     auto k = k_fwd_y<Real, L>;
-    static const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    static const cudaError_t e = smem_attrs(k, smem);
     if (e != cudaSuccess) return e;
     dim3 grid((2 * g.SP + C - 1) / C, g.N);
     k<<<grid, T, smem, s>>>(g, (const cx<Real> *)w.X, (cx<Real> *)w.Y, twiddles_for<Real>(w, L));
@@ -267,8 +277,11 @@ cudaError_t launch_fwd_energy(const Geom &g, const Band &band, const Work<double
     LH_LEN_SWITCH_SMALL(g.PE, CALL)
 #undef CALL
 }
+cudaError_t launch_fwd_y_tma(const Geom &g, const Work<float> &w, cudaStream_t s, int variant);
+// variants 3, 4: the TMA-staged persistent kernels of k_tma.cu
 cudaError_t launch_fwd_y(const Geom &g, const Work<float> &w, cudaStream_t s, int variant)
 {
+    if (variant >= 3) return launch_fwd_y_tma(g, w, s, variant);
 #define CALL(L) launch_fwd_y_t<float, L>(g, w, s, variant)
     LH_P_SWITCH(g.P, CALL)
 #undef CALL

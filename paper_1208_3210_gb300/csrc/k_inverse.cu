@@ -56,12 +56,12 @@ k_inv_y(Geom g, const cx<Real> *__restrict__ U3, cx<Real> *__restrict__ U4,
 }
 
 // Paired-column version of the inverse p_y pass (L >= 128).
-template <typename Real, int L>
-__global__ void __launch_bounds__(PairCfg<L>::T, PairCfg<L>::MINB)
+template <typename Real, int L, typename Cfg>
+__global__ void __launch_bounds__(Cfg::T, Cfg::MINB)
 k_inv_y2(Geom g, const cx<Real> *__restrict__ U3, cx<Real> *__restrict__ U4,
          const cx<Real> *__restrict__ tw)
 {
-    constexpr int C = PairCfg<L>::C, T = PairCfg<L>::T;
+    constexpr int C = Cfg::C, T = Cfg::T;
     using E = FftPair<Real, L, C, T, true>;
     using Cx = cx<Real>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -148,31 +148,35 @@ k_inv_energy(Geom g, const cx<Real> *__restrict__ U4, OutT *__restrict__ out,
         }
 }
 
-template <typename Real, int L>
+template <typename Real, int L, typename Cfg>
 cudaError_t launch_inv_y2_t(const Geom &g, const Work<Real> &w, cudaStream_t s)
 {
-    constexpr int C = PairCfg<L>::C, T = PairCfg<L>::T;
+    constexpr int C = Cfg::C, T = Cfg::T;
     using E = FftPair<Real, L, C, T, true>;
     size_t smem = sizeof(cx<Real>) * E::SMEM_ELEMS;
-    auto k = k_inv_y2<Real, L>;
-    static const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto k = k_inv_y2<Real, L, Cfg>;
+    static const cudaError_t e = smem_attrs(k, smem);
     if (e != cudaSuccess) return e;
     dim3 grid((g.H + C - 1) / C, g.Q);
     k<<<grid, T, smem, s>>>(g, (const cx<Real> *)w.X, (cx<Real> *)w.Y, twiddles_for<Real>(w, L));
     return cudaGetLastError();
 }
 
-// variant 1: paired-column engine (L >= 128, FP32); 0: single-column engine
+// variant 0: single-column engine; 1: paired-column engine (L >= 128, FP32);
+// 2: paired-column engine with 12 values per thread (3 * 2^k >= 192, FP32)
 template <typename Real, int L>
 cudaError_t launch_inv_y_t(const Geom &g, const Work<Real> &w, cudaStream_t s, int variant)
 {
-    if constexpr (L >= 128 && sizeof(Real) == 4)
-        if (variant == 1) return launch_inv_y2_t<Real, L>(g, w, s);
+    if constexpr (L >= 128 && sizeof(Real) == 4) {
+        if (variant == 1) return launch_inv_y2_t<Real, L, PairCfg<L>>(g, w, s);
+        if constexpr (fft_has_family1(L))
+            if (variant == 2) return launch_inv_y2_t<Real, L, PairCfg12<L>>(g, w, s);
+    }
     constexpr int C = ColCfg<L>::C, T = ColCfg<L>::T;
     using E = Fft<Real, L, C, T, MAP_COL, true>;
     size_t smem = sizeof(cx<Real>) * E::SMEM_ELEMS;
     auto k = k_inv_y<Real, L>;
-    static const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    static const cudaError_t e = smem_attrs(k, smem);
     if (e != cudaSuccess) return e;
     dim3 grid((g.H + C - 1) / C, g.Q);
     k<<<grid, T, smem, s>>>(g, (const cx<Real> *)w.X, (cx<Real> *)w.Y, twiddles_for<Real>(w, L));
@@ -186,7 +190,7 @@ cudaError_t launch_inv_energy_t(const Geom &g, const Work<Real> &w, OutT *out, c
     using E = Fft<Real, L, C, T, MAP_LINE, true>;
     size_t smem = sizeof(cx<Real>) * E::SMEM_ELEMS;
     auto k = k_inv_energy<Real, OutT, L>;
-    static const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    static const cudaError_t e = smem_attrs(k, smem);
     if (e != cudaSuccess) return e;
     long long npairs = (long long)g.Q * g.Q / 2;
     unsigned grid = (unsigned)((npairs + C - 1) / C);
@@ -194,8 +198,11 @@ cudaError_t launch_inv_energy_t(const Geom &g, const Work<Real> &w, OutT *out, c
     return cudaGetLastError();
 }
 
+cudaError_t launch_inv_y_tma(const Geom &g, const Work<float> &w, cudaStream_t s, int variant);
+// variants 3, 4: the TMA-staged persistent kernels of k_tma.cu
 cudaError_t launch_inv_y(const Geom &g, const Work<float> &w, cudaStream_t s, int variant)
 {
+    if (variant >= 3) return launch_inv_y_tma(g, w, s, variant);
 #define CALL(L) launch_inv_y_t<float, L>(g, w, s, variant)
     LH_P_SWITCH(g.P, CALL)
 #undef CALL

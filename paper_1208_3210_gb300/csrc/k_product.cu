@@ -15,9 +15,9 @@ namespace lh {
 // Engines of the product pass, shared by the kernel and its launcher.
 // Forward: a^ and b^ of the same column as one pair (shared twiddles and
 // barriers, two dependency chains per thread); inverse: the product alone.
-template <typename Real, int L>
+template <typename Real, int L, typename Cfg>
 struct XProduct {
-    static constexpr int C = XCfg<L>::C, T = XCfg<L>::T;
+    static constexpr int C = Cfg::C, T = Cfg::T;
     using EF = FftPair<Real, L, 2 * C, T, false>;
     using EI = Fft<Real, L, C, T, MAP_COL, true>;
     static_assert(EF::RL == EI::R0, "last forward radix must equal first inverse radix");
@@ -25,12 +25,12 @@ struct XProduct {
     static constexpr int SMEM_ELEMS = EF::SMEM_ELEMS > EI::SMEM_ELEMS ? EF::SMEM_ELEMS : EI::SMEM_ELEMS;
 };
 
-template <typename Real, int L>
-__global__ void __launch_bounds__(XCfg<L>::T, XCfg<L>::MINB)
+template <typename Real, int L, typename Cfg>
+__global__ void __launch_bounds__(Cfg::T, Cfg::MINB)
 k_x_product(Geom g, const cx<Real> *__restrict__ U2, cx<Real> *__restrict__ U3,
             const cx<Real> *__restrict__ tw)
 {
-    using XP = XProduct<Real, L>;
+    using XP = XProduct<Real, L, Cfg>;
     constexpr int C = XP::C;
     using EF = typename XP::EF;
     using EI = typename XP::EI;
@@ -78,29 +78,41 @@ k_x_product(Geom g, const cx<Real> *__restrict__ U2, cx<Real> *__restrict__ U3,
     }
 }
 
-template <typename Real, int L>
-cudaError_t launch_x_product_t(const Geom &g, const Work<Real> &w, cudaStream_t s)
+template <typename Real, int L, typename Cfg>
+cudaError_t launch_x_product_c(const Geom &g, const Work<Real> &w, cudaStream_t s)
 {
-    using XP = XProduct<Real, L>;
+    using XP = XProduct<Real, L, Cfg>;
     constexpr int C = XP::C, T = XP::T;
     size_t smem = sizeof(cx<Real>) * XP::SMEM_ELEMS;
-    auto k = k_x_product<Real, L>;
-    static const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto k = k_x_product<Real, L, Cfg>;
+    static const cudaError_t e = smem_attrs(k, smem);
     if (e != cudaSuccess) return e;
     dim3 grid((g.H + C - 1) / C, g.P);
     k<<<grid, T, smem, s>>>(g, (const cx<Real> *)w.Y, (cx<Real> *)w.X, twiddles_for<Real>(w, L));
     return cudaGetLastError();
 }
 
-cudaError_t launch_x_product(const Geom &g, const Work<float> &w, cudaStream_t s)
+// variant 0: the tiles of XCfg; 1: 12 values per thread (3 * 2^k >= 192, FP32)
+template <typename Real, int L>
+cudaError_t launch_x_product_t(const Geom &g, const Work<Real> &w, cudaStream_t s, int variant)
 {
-#define CALL(L) launch_x_product_t<float, L>(g, w, s)
+    if constexpr (sizeof(Real) == 4 && fft_has_family1(L))
+        if (variant == 1) return launch_x_product_c<Real, L, XCfg12<L>>(g, w, s);
+    return launch_x_product_c<Real, L, XCfg<L>>(g, w, s);
+}
+
+cudaError_t launch_x_product_tma(const Geom &g, const Work<float> &w, cudaStream_t s, int variant);
+// variants 2, 3: the TMA-staged persistent kernels of k_tma.cu
+cudaError_t launch_x_product(const Geom &g, const Work<float> &w, cudaStream_t s, int variant)
+{
+    if (variant >= 2) return launch_x_product_tma(g, w, s, variant);
+#define CALL(L) launch_x_product_t<float, L>(g, w, s, variant)
     LH_P_SWITCH(g.P, CALL)
 #undef CALL
 }
-cudaError_t launch_x_product(const Geom &g, const Work<double> &w, cudaStream_t s)
+cudaError_t launch_x_product(const Geom &g, const Work<double> &w, cudaStream_t s, int variant)
 {
-#define CALL(L) launch_x_product_t<double, L>(g, w, s)
+#define CALL(L) launch_x_product_t<double, L>(g, w, s, variant)
     LH_LEN_SWITCH_SMALL(g.P, CALL)
 #undef CALL
 }

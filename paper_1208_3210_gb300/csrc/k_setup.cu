@@ -30,97 +30,364 @@ __global__ void k_twiddles(int max_len, float2 *tw32, double2 *tw64)
     tw64[idx] = make_double2(c, s);
 }
 
-// Per-axis tables at p_i = (i - N/2) 2 pi / npz and the energy grid
+// ---------------------------------------------------------------------------
+// Set-up and chemical potential.
+//
+// Tables: per-axis values at p_i = (i - N/2) 2 pi / npz and the energy grid
 // e_j = -e_max + (j + 1/2) de, all in FP64.  The FP32 path stores e_j as an
 // unevaluated pair hi + lo so that e_j - xi_p keeps full precision near the
 // Lorentzian peak.
-__global__ void k_tables(Geom g, Band band, AxisTab *axis, float2 *eps32, double *eps64)
+//
+// Chemical potential (Sec. 3: the Fermi level is placed to hold the requested
+// electron count).  n(mu) = (2/npz^2) sum_k occ(e0_k - mu) with the Lorentzian
+// occupation occ(xi) = 1/2 - atan(xi/gamma)/pi of Eq. 5 below the Fermi level,
+// summed over the first-zone grid p = 2 pi r / npz, r in [-npz/2, npz/2).
+// n is strictly increasing in mu.  Both band kinds depend on p_x and p_y only
+// through even functions (cos p, cos 2p, p^2) and are symmetric under
+// p_x <-> p_y, so the sum runs over the classes m = |r| in [0, npz/2] with
+// weights w(0) = w(npz/2) = 1, w(m) = 2 otherwise, and over pairs
+// m_x <= m_y (twice for m_x < m_y): (npz/2 + 1)(npz/2 + 2)/2 terms instead of
+// npz^2 (561 instead of 4096 at npz = 64).
+//
+// Launches (no CTA ever waits for another):
+//   k_setup     multisection pass 0 over [-B-3, B+3] eV on G CTAs, and the
+//               tables on further CTAs of the same launch (their FP64 cospi and
+//               exp chains run beside the multisection, not before it)
+//   k_mu_sect   further multisection passes (one, or two when gamma < 0.02 eV)
+//   k_mu_halley one FP64 Halley step from the midpoint of the last bracket
+// A multisection pass samples NC = 8 G candidates (G CTAs, eight candidates
+// each) in FP32.  Every CTA sums the whole zone for its own candidates (the
+// pairs' band energies and weights staged in shared memory, lane % 8 picks
+// the candidate), so no cross-CTA reduction is needed; it records the first
+// of its candidates whose total reaches the target, and the next launch's CTAs
+// each take the minimum over the G records.  Two passes shrink the bracket by
+// (NC - 1)^2 (to about 1e-5 eV), three to below FP32 resolution; FP32
+// rounding moves the sampled n(mu) by the equivalent of some 1e-7 eV at most.
+// The Halley step (cubic convergence; its error is of order (d/gamma)^2 d for
+// a distance d to the root) then lands at FP64 precision.  Its per-CTA sums of
+// n (FP64), gamma n' and gamma^2 n'' (FP32 terms: they only scale the step)
+// are stored, and the last CTA to finish (an atomic counter) adds them in a
+// fixed tree order and forms the step.
+//
+// On this GPU a dependent FP64 operation takes about 60 cycles, an FP64
+// division about 450 and an FP64 atan about 1900, so the few FP64 steps on
+// the critical path use constants computed on the host.
+constexpr int MU_THREADS = 512;      // multisection CTAs
+constexpr int MU_NT_THREADS = 128;   // Halley CTAs (at most; one warp when the pairs fit)
+constexpr int MU_TAB_THREADS = 32;   // table entries per table CTA
+constexpr int MU_NCPT = 8;           // candidates per CTA
+constexpr int MU_MAX_PASSES = 3;
+constexpr int MU_RES = 16;           // doubles of results at the start of acc
+constexpr int MU_MAXC = 2049;        // classes for npz <= 4096
+constexpr int MU_CHUNK = 2048;       // pairs staged per round
+constexpr float MU_SECT_SCALE = 4294967296.0f;   // 2^32
+
+// Layout of acc: res[3 p + 0, 1, 2] = (lo, hi, not-bracketed flag) of the
+// interval pass p sampled (p = passes: that of the Halley step); then
+// [G][4] doubles of per-CTA Halley sums; then [MU_MAX_PASSES][G] int first
+// crossings (index in the CTA's candidates, MU_NCPT = none).
+size_t mu_acc_doubles(int G) { return MU_RES + 4 * (size_t)G + ((size_t)MU_MAX_PASSES * G + 1) / 2; }
+size_t mu_barrier_words() { return 32; }   // the arrival counter (one 128-byte line)
+
+// CTAs of each chemical-potential launch: one per SM.
+int mu_grid_size(int num_sms, int npts)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < g.N) {
-        double u = 2.0 * (double)(i - g.N / 2) / (double)g.npz;   // p_i / pi
-        double p = u * 3.14159265358979323846;
-        AxisTab a;
-        a.c1 = cospi(u);
-        a.c2 = cospi(2.0 * u);
-        a.g = (band.ff_a == 0.0) ? 1.0 : exp(-p * p * band.ff_a * band.ff_a / 8.0);
-        a.p2 = p * p;
-        a.c1f = (float)a.c1;
-        a.c2f = (float)a.c2;
-        a.p2f = (float)a.p2;
-        a.pad = 0.f;
-        axis[i] = a;
-    }
-    if (i < g.n_eps) {
-        double e = -g.e_max + ((double)i + 0.5) * g.de;
-        if (eps32) {
-            float hi = (float)e;
-            eps32[i] = make_float2(hi, (float)(e - (double)hi));
-        }
-        if (eps64) eps64[i] = e;
-    }
+    (void)npts;
+    return num_sms < 1 ? 1 : num_sms;
 }
 
-// ---------------------------------------------------------------------------
-// Chemical potential.  n(mu) = (2/npz^2) sum_k [1/2 - atan((e0_k - mu)/gamma)/pi]
-// over the first-zone grid (the Lorentzian occupation of Eq. 5 below the Fermi
-// level).  n is strictly increasing in mu.  Five small launches of G CTAs:
-//   3 passes of MU_SECT-point multisection in FP32 shrink the bracket
-//   [-B-3, B+3] eV (B bounds |e0|) by (MU_SECT-1)^3 to tens of micro-eV;
-//   every thread owns one candidate and a share of the points;
-//   2 Newton steps in FP64 from the bracket midpoint reach FP64 precision
-//   (the error after a step is about |F''/2F'| times the step squared).
-// Each launch ends the same way: every CTA stores its partial sums, and the
-// last CTA to finish (an atomic counter, which it resets) adds them in a fixed
-// order and publishes the new bracket or mu for the next launch.  No CTA ever
-// waits for another.
-constexpr int MU_SECT = 64;
-constexpr int MU_THREADS = 256;
-constexpr int MU_FP32_PASSES = 3;
-constexpr int MU_NEWTON = 2;
-constexpr int MU_SECT_CTAS = 152;  // CTAs of a multisection pass
-constexpr int MU_RES = 16;   // result slots at the start of acc
+// Host-computed constants of one solve.
+struct MuConst {
+    double inv_nc1;      // 1 / (NC - 1)
+    double inv_gam;      // 1 / gamma
+    double target;       // filling npz^2 / 2 (sum of occupations)
+    long long target32;  // the same in 2^-32 fixed point
+    double B;            // bracket half-width - 3 eV
+    int NC, passes;
+};
 
-// Layout of acc: [MU_RES] results (3 per multisection pass from 0, 2 per
-// Newton step from 10), then [MU_FP32_PASSES][G][MU_SECT], then
-// [MU_NEWTON][G][2] doubles.
-size_t mu_acc_doubles(int G) { return MU_RES + (size_t)G * (MU_FP32_PASSES * MU_SECT + MU_NEWTON * 2); }
-size_t mu_barrier_words() { return 32; }   // the arrival counter (one 128-byte line)
+__device__ __forceinline__ int *mu_cross(double *acc, int G, int pass)
+{
+    return (int *)(acc + MU_RES + 4 * (size_t)G) + (size_t)pass * G;
+}
 
 __device__ __forceinline__ double band_e0(const Band &b, const AxisTab &ax, const AxisTab &ay)
 {
     if (b.band_kind == 1) return 0.5 * (ax.p2 + ay.p2);
     return -2.0 * b.t * (ax.c1 + ay.c1) - 4.0 * b.tp * ax.c1 * ay.c1 - 2.0 * b.tpp * (ax.c2 + ay.c2);
 }
-// The first-zone axis values a CTA needs, staged once in shared memory
-// (pts_per_zone <= 512 for the filling solve).
-constexpr int MU_MAXZ = 512;
-struct ZoneAxis {
-    float c1[MU_MAXZ], c2[MU_MAXZ], p2[MU_MAXZ];
-};
-__device__ __forceinline__ void stage_zone_axis(const Geom &g, const AxisTab *__restrict__ axis, ZoneAxis &z)
+
+// Pair index k in [0, (h+1)(h+2)/2) -> classes (a, b), 0 <= a <= b <= h, row
+// a holding b = a..h; row a starts at a (2h + 3 - a) / 2.
+__device__ __forceinline__ void tri_pair(int k, int h, int &a, int &b)
 {
-    const int base = g.N / 2 - g.npz / 2;
-    for (int i = threadIdx.x; i < g.npz; i += blockDim.x) {
-        z.c1[i] = axis[base + i].c1f;
-        z.c2[i] = axis[base + i].c2f;
-        z.p2[i] = axis[base + i].p2f;
-    }
-    __syncthreads();
+    const float c = 2.0f * (float)h + 3.0f;
+    int x = (int)((c - sqrtf(c * c - 8.0f * (float)k)) * 0.5f);
+    x = max(0, min(x, h));
+    while (x < h && (x + 1) * (2 * h + 2 - x) / 2 <= k) ++x;
+    while (x > 0 && x * (2 * h + 3 - x) / 2 > k) --x;
+    a = x;
+    b = x + (k - x * (2 * h + 3 - x) / 2);
 }
-// FP32 band energy of first-zone point (i, j); t32 = (t, t', t'') in FP32.
-__device__ __forceinline__ float band_e0f(int kind, const float *t32, const ZoneAxis &z, int i, int j)
+// Multiplicity of pair (a, b): w(a) w(b), twice when a != b.
+__device__ __forceinline__ int pair_weight(int a, int b, int h)
 {
-    if (kind == 1) return 0.5f * (z.p2[i] + z.p2[j]);
-    return -2.0f * t32[0] * (z.c1[i] + z.c1[j]) - 4.0f * t32[1] * z.c1[i] * z.c1[j]
-           - 2.0f * t32[2] * (z.c2[i] + z.c2[j]);
+    int wa = (a == 0 || a == h) ? 1 : 2, wb = (b == 0 || b == h) ? 1 : 2;
+    return wa * wb * (a == b ? 1 : 2);
 }
 
-// True in every thread of the CTA that finishes last; that CTA resets the
-// counter for the next launch.  Partial sums written before the call are
-// visible to it.
-__device__ __forceinline__ bool last_cta(unsigned *counter)
+struct MuBracket {
+    int wmin[MU_THREADS / 32];
+    double lo, hi, step;
+    int flag;
+};
+struct MuShared {
+    float c1[MU_MAXC], c2[MU_MAXC], p2[MU_MAXC];   // class values in FP32
+    float2 ew[MU_CHUNK];                           // (band energy, weight) of staged pairs
+    long long red[MU_THREADS / 32][MU_NCPT];
+    float mu_c[MU_NCPT];
+    MuBracket br;
+};
+
+// Class values at p = 2 pi m / npz, FP32 (the multisection only needs them to
+// about 1e-7).
+__device__ __forceinline__ void stage_classes(const Geom &g, MuShared &sh)
 {
+    const int h = g.npz / 2;
+    const float inv = 2.0f / (float)g.npz;
+    for (int m = threadIdx.x; m <= h; m += blockDim.x) {
+        float u = (float)m * inv;                  // p / pi
+        float p = u * 3.14159265358979f;
+        sh.c1[m] = cospif(u);
+        sh.c2[m] = cospif(2.0f * u);
+        sh.p2[m] = p * p;
+    }
+}
+
+// Bracket from the first-crossing records of pass p: sh.lo, sh.hi, sh.flag
+// (read after the next __syncthreads).  Every thread takes part.
+__device__ __forceinline__ void bracket_from(const double *res, const int *cross_p, const MuConst &mc, int p,
+                                             MuBracket &sh)
+{
+    const int G = mc.NC / MU_NCPT;
+    double plo = 0.0, phi = 0.0, pflag = 0.0;
+    if (threadIdx.x == 0) {   // issued together with the records' loads
+        plo = __ldcg(res + 3 * p);
+        phi = __ldcg(res + 3 * p + 1);
+        pflag = __ldcg(res + 3 * p + 2);
+    }
+    int first = mc.NC;
+    for (int j = threadIdx.x; j < G; j += blockDim.x) {
+        int q = __ldcg(cross_p + j);
+        if (q < MU_NCPT) first = min(first, MU_NCPT * j + q);
+    }
+    first = (int)__reduce_min_sync(0xffffffffu, (unsigned)first);
+    if ((threadIdx.x & 31) == 0) sh.wmin[threadIdx.x >> 5] = first;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int c = mc.NC;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) c = min(c, sh.wmin[w]);
+        sh.flag = pflag != 0.0 || (p == 0 && (c == 0 || c == mc.NC));
+        c = max(1, min(c, mc.NC - 1));
+        const double step = (phi - plo) * mc.inv_nc1;
+        sh.lo = plo + (double)(c - 1) * step;
+        sh.hi = sh.lo + step;
+    }
+}
+
+// One multisection pass over [sh.br.lo, sh.br.hi] (set by thread 0 before the
+// call): this CTA's candidates; records the first one whose total reaches
+// the target in cross[blockIdx.x].
+__device__ __forceinline__ void sect_pass(const Geom &g, const Band &band, const MuConst &mc, MuShared &sh,
+                                          int *cross)
+{
+    const int h = g.npz / 2;
+    const int npairs = (h + 1) * (h + 2) / 2;
+    const int c0 = MU_NCPT * blockIdx.x;
+    if (threadIdx.x == 0) sh.br.step = (sh.br.hi - sh.br.lo) * mc.inv_nc1;
+    __syncthreads();
+    if (threadIdx.x < MU_NCPT) sh.mu_c[threadIdx.x] = (float)(sh.br.lo + (double)(c0 + (int)threadIdx.x) * sh.br.step);
+    const float inv_gam = (float)mc.inv_gam, inv_pi = 0.318309886183790672f;
+    const float t = (float)band.t, tp = (float)band.tp, tpp = (float)band.tpp;
+    const bool free_e = band.band_kind == 1;
+    const int q = threadIdx.x % MU_NCPT;        // this thread's candidate
+    constexpr int LANES = MU_THREADS / MU_NCPT;  // threads per candidate
+    long long acc = 0;
+    for (int base = 0; base < npairs; base += MU_CHUNK) {
+        const int n = min(MU_CHUNK, npairs - base);
+        __syncthreads();   // previous chunk consumed; mu_c written
+        for (int k = threadIdx.x; k < n; k += MU_THREADS) {
+            int a, b;
+            tri_pair(base + k, h, a, b);
+            const float e = free_e ? 0.5f * (sh.p2[a] + sh.p2[b])
+                                   : -2.0f * t * (sh.c1[a] + sh.c1[b]) - 4.0f * tp * sh.c1[a] * sh.c1[b]
+                                         - 2.0f * tpp * (sh.c2[a] + sh.c2[b]);
+            sh.ew[k] = make_float2(e, (float)pair_weight(a, b, h));
+        }
+        __syncthreads();
+        const float mu = sh.mu_c[q];
+        float s[4] = {0.f, 0.f, 0.f, 0.f};   // four chains; at most MU_CHUNK / LANES terms of at most 8
+        int k = threadIdx.x / MU_NCPT;
+        for (; k + 3 * LANES < n; k += 4 * LANES) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const float2 ew = sh.ew[k + u * LANES];
+                s[u] += ew.y * (0.5f - atanf((ew.x - mu) * inv_gam) * inv_pi);
+            }
+        }
+        for (; k < n; k += LANES) {
+            const float2 ew = sh.ew[k];
+            s[0] += ew.y * (0.5f - atanf((ew.x - mu) * inv_gam) * inv_pi);
+        }
+        acc += __float2ll_rn(((s[0] + s[1]) + (s[2] + s[3])) * MU_SECT_SCALE);
+    }
+    // lanes l, l ^ 8, l ^ 16, l ^ 24 share a candidate
+    acc += __shfl_xor_sync(0xffffffffu, acc, 8);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 16);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane < MU_NCPT) sh.red[warp][lane] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        long long tsum = 0;
+        if (lane < MU_NCPT)
+            for (int w = 0; w < MU_THREADS / 32; ++w) tsum += sh.red[w][lane];
+        unsigned hit = __ballot_sync(0xffffffffu, lane < MU_NCPT && tsum >= mc.target32);
+        if (lane == 0) cross[blockIdx.x] = hit ? __ffs(hit) - 1 : MU_NCPT;
+    }
+    (void)c0;
+}
+
+// Set-up launch.  CTAs [0, G): multisection pass 0 (mu from the filling);
+// CTAs [G, G + GT): the per-axis tables and the energy grid, one entry per
+// thread of their first warp; without a filling solve only the table CTAs run
+// and the first of them records the given mu.
+__global__ void __launch_bounds__(MU_THREADS, 2)
+k_setup(Geom g, Band band, AxisTab *axis, float2 *eps32, double *eps64, InstState *st, double *acc,
+        unsigned *counter, double *mu_out, MuConst mc, int G)
+{
+    if ((int)blockIdx.x >= G) {
+        const int tb = blockIdx.x - G;
+        if (!band.solve_mu && tb == 0 && threadIdx.x == 0) {
+            st->mu = band.mu;
+            st->last_step = 0.0;
+            if (mu_out) *mu_out = band.mu;
+        }
+        const int i = tb * MU_TAB_THREADS + threadIdx.x;
+        if (threadIdx.x >= MU_TAB_THREADS) return;
+        if (i < g.N) {
+            double u = 2.0 * (double)(i - g.N / 2) / (double)g.npz;   // p_i / pi
+            double p = u * 3.14159265358979323846;
+            AxisTab a;
+            a.c1 = cospi(u);
+            a.c2 = cospi(2.0 * u);
+            a.g = (band.ff_a == 0.0) ? 1.0 : exp(-p * p * band.ff_a * band.ff_a / 8.0);
+            a.p2 = p * p;
+            a.c1f = (float)a.c1;
+            a.c2f = (float)a.c2;
+            a.p2f = (float)a.p2;
+            a.pad = 0.f;
+            axis[i] = a;
+        }
+        if (i < g.n_eps) {
+            double e = -g.e_max + ((double)i + 0.5) * g.de;
+            if (eps32) {
+                float hi = (float)e;
+                eps32[i] = make_float2(hi, (float)(e - (double)hi));
+            }
+            if (eps64) eps64[i] = e;
+        }
+        return;
+    }
+    __shared__ MuShared sh;
+    stage_classes(g, sh);
+    if (threadIdx.x == 0) {
+        sh.br.lo = -mc.B - 3.0;
+        sh.br.hi = mc.B + 3.0;
+        if (blockIdx.x == 0) {
+            acc[0] = sh.br.lo;
+            acc[1] = sh.br.hi;
+            acc[2] = 0.0;
+            *counter = 0;
+        }
+    }
+    sect_pass(g, band, mc, sh, mu_cross(acc, G, 0));
+}
+
+// Multisection pass `pass` >= 1.
+__global__ void __launch_bounds__(MU_THREADS, 2)
+k_mu_sect(Geom g, Band band, double *acc, int pass, MuConst mc)
+{
+    __shared__ MuShared sh;
+    const int G = gridDim.x;
+    stage_classes(g, sh);
+    bracket_from(acc, mu_cross(acc, G, pass - 1), mc, pass - 1, sh.br);
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        acc[3 * pass + 0] = sh.br.lo;
+        acc[3 * pass + 1] = sh.br.hi;
+        acc[3 * pass + 2] = sh.br.flag;
+    }
+    __syncthreads();
+    if (sh.br.flag) return;   // the filling was not bracketed
+    sect_pass(g, band, mc, sh, mu_cross(acc, G, pass));
+}
+
+// Halley step in FP64 from the midpoint of the last bracket; publishes mu.
+__global__ void __launch_bounds__(MU_NT_THREADS)
+k_mu_halley(Geom g, Band band, const AxisTab *__restrict__ axis, InstState *st, double *acc, unsigned *counter,
+            unsigned *status, double *mu_out, MuConst mc)
+{
+    const int P = mc.passes, G = gridDim.x;
+    __shared__ struct { MuBracket br; } sh;
+    __shared__ double s_red[MU_NT_THREADS / 32][3];
+    double *part = acc + MU_RES;   // [G][4]
+    bracket_from(acc, mu_cross(acc, G, P - 1), mc, P - 1, sh.br);
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        acc[3 * P + 0] = sh.br.lo;
+        acc[3 * P + 1] = sh.br.hi;
+        acc[3 * P + 2] = sh.br.flag;
+    }
+    __syncthreads();
+    const double mu = 0.5 * (sh.br.lo + sh.br.hi);
+    if (sh.br.flag) {   // the filling was not bracketed
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            atomicCAS(status, (unsigned)DEV_OK, (unsigned)DEV_ENOCONV);
+            st->mu = mu;
+            st->last_step = INFINITY;
+            if (mu_out) *mu_out = mu;
+        }
+        return;
+    }
+    const int h = g.npz / 2, npairs = (h + 1) * (h + 2) / 2, c = g.N / 2;
+    const double igam = mc.inv_gam, ipi = 0.31830988618379067154;
+    double f = 0.0;
+    float f1 = 0.f, f2 = 0.f;
+    // pairs interleaved over the CTAs first, so every SM's FP64 units share the work
+    for (int k = blockIdx.x + G * threadIdx.x; k < npairs; k += G * (int)blockDim.x) {
+        int a, b;
+        tri_pair(k, h, a, b);
+        const int w = pair_weight(a, b, h);
+        const double x = (band_e0(band, axis[c - a], axis[c - b]) - mu) * igam;   // xi / gamma
+        f += (double)w * (0.5 - atan(x) * ipi);                                   // occupation
+        const float xf = (float)x, r = 1.0f / (1.0f + xf * xf);                    // gamma^2 / (xi^2 + gamma^2)
+        f1 += (float)w * r * (float)ipi;                                           // gamma d occ / d mu
+        f2 += (float)w * 2.0f * xf * r * r * (float)ipi;                           // gamma^2 d^2 occ / d mu^2
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) {
+        f += __shfl_down_sync(0xffffffffu, f, o);
+        f1 += __shfl_down_sync(0xffffffffu, f1, o);
+        f2 += __shfl_down_sync(0xffffffffu, f2, o);
+    }
+    if (lane == 0) { s_red[warp][0] = f; s_red[warp][1] = f1; s_red[warp][2] = f2; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double F = 0, F1 = 0, F2 = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { F += s_red[w][0]; F1 += s_red[w][1]; F2 += s_red[w][2]; }
+        part[4 * (size_t)blockIdx.x + 0] = F;
+        part[4 * (size_t)blockIdx.x + 1] = F1;
+        part[4 * (size_t)blockIdx.x + 2] = F2;
+    }
+    // the last CTA to finish adds the partial sums in a fixed order
     __shared__ int s_last;
     __threadfence();
     __syncthreads();
@@ -129,164 +396,50 @@ __device__ __forceinline__ bool last_cta(unsigned *counter)
         if (s_last) *counter = 0;   // no other CTA touches it again in this launch
     }
     __syncthreads();
-    if (s_last) __threadfence();
-    return s_last;
-}
-
-__device__ __forceinline__ double mu_bracket_B(const Band &band)
-{
-    return (band.band_kind == 1) ? 9.869604401089358 : 4.0 * (fabs(band.t) + fabs(band.tp) + fabs(band.tpp));
-}
-
-// One multisection pass: candidates mu_c = lo + c (hi - lo)/(MU_SECT - 1).
-__global__ void __launch_bounds__(MU_THREADS)
-k_mu_sect(Geom g, Band band, const AxisTab *__restrict__ axis, double *acc, unsigned *counter, int pass)
-{
-    const int G = gridDim.x;
-    const int npts = g.npz * g.npz;
-    const double target = band.filling * 0.5 * (double)npts;  // sum of occupations
-    double *res = acc;
-    double *part = acc + MU_RES + (size_t)pass * G * MU_SECT;
-    double lo, hi;
-    if (pass == 0) {
-        lo = -mu_bracket_B(band) - 3.0;
-        hi = -lo;
-    } else {
-        if (res[3 * (pass - 1) + 2] != 0.0) return;   // not bracketed: nothing to refine
-        lo = res[3 * (pass - 1) + 0];
-        hi = res[3 * (pass - 1) + 1];
-    }
-    constexpr int NGRP = MU_THREADS / MU_SECT;
-    __shared__ double s_tot[NGRP][MU_SECT];
-    __shared__ int s_first;
-    const int cand = threadIdx.x % MU_SECT, grp = threadIdx.x / MU_SECT;
-    const int pg = blockIdx.x * NGRP + grp, npg = G * NGRP;
-    const float gam = (float)band.gamma;
-    const float inv_pi = 0.318309886183790672f;
-    const float t32[3] = {(float)band.t, (float)band.tp, (float)band.tpp};
-    const double h = (hi - lo) / (MU_SECT - 1);
-    const float mu_c = (float)(lo + cand * h);
-    const float inv_gam = 1.0f / gam;
-    __shared__ ZoneAxis za;
-    stage_zone_axis(g, axis, za);
-    float sum = 0.f;
-#pragma unroll 4
-    for (int k = pg; k < npts; k += npg) {
-        int i = k / g.npz, j = k % g.npz;
-        sum += 0.5f - atanf((band_e0f(band.band_kind, t32, za, i, j) - mu_c) * inv_gam) * inv_pi;
-    }
-    s_tot[grp][cand] = sum;
-    __syncthreads();
-    if (threadIdx.x < MU_SECT) {
-        double t = 0;
-        for (int q = 0; q < NGRP; ++q) t += s_tot[q][threadIdx.x];
-        part[(size_t)blockIdx.x * MU_SECT + threadIdx.x] = t;
-    }
-    if (!last_cta(counter)) return;
-    // last CTA: totals per candidate in a fixed order, first one >= target
-    if (threadIdx.x == 0) s_first = MU_SECT;
-    double t = 0;
-#pragma unroll 16
-    for (int q = grp; q < G; q += NGRP) t += __ldcg(&part[(size_t)q * MU_SECT + cand]);
-    __syncthreads();
-    s_tot[grp][cand] = t;
-    __syncthreads();
-    if (threadIdx.x < MU_SECT) {
-        double tt = 0;
-        for (int q = 0; q < NGRP; ++q) tt += s_tot[q][threadIdx.x];
-        if (tt >= target) atomicMin(&s_first, (int)threadIdx.x);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int i = s_first;
-        double flag = 0.0;
-        if (pass == 0 && (i == 0 || i == MU_SECT)) flag = 1.0;   // filling not bracketed
-        if (i == 0) i = 1;
-        if (i == MU_SECT) i = MU_SECT - 1;
-        res[3 * pass + 0] = lo + (i - 1) * h;
-        res[3 * pass + 1] = lo + i * h;
-        res[3 * pass + 2] = flag;
-    }
-}
-
-// One Newton step in FP64; the last step also publishes mu.
-__global__ void __launch_bounds__(MU_THREADS)
-k_mu_newton(Geom g, Band band, const AxisTab *__restrict__ axis, InstState *st, double *acc, unsigned *counter,
-            int it, unsigned *status, double *mu_out)
-{
-    const int G = gridDim.x;
-    const int npts = g.npz * g.npz;
-    const int base = g.N / 2 - g.npz / 2;
-    const double target = band.filling * 0.5 * (double)npts;
-    double *res = acc;
-    double *part = acc + MU_RES + (size_t)MU_FP32_PASSES * G * MU_SECT + (size_t)it * G * 2;
-    if (res[2] != 0.0) {   // the filling was not bracketed
-        if (it == MU_NEWTON - 1 && blockIdx.x == 0 && threadIdx.x == 0)
-            atomicCAS(status, (unsigned)DEV_OK, (unsigned)DEV_ENOCONV);
-        return;
-    }
-    const double mu = (it == 0) ? 0.5 * (res[3 * (MU_FP32_PASSES - 1) + 0] + res[3 * (MU_FP32_PASSES - 1) + 1])
-                                : res[10 + 2 * (it - 1)];
-    const double gd = band.gamma, ipi = 0.31830988618379067154;
-    constexpr int NW = MU_THREADS / 32;
-    __shared__ double s_red[2][NW];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    double f = 0.0, fp = 0.0;
-    // points interleaved over the CTAs, so every SM's FP64 units share the work
-    for (int k = threadIdx.x * G + blockIdx.x; k < npts; k += G * MU_THREADS) {
-        int ix = base + k / g.npz, iy = base + k % g.npz;
-        double xi = band_e0(band, axis[ix], axis[iy]) - mu;
-        f += 0.5 - atan(xi / gd) * ipi;
-        fp += gd * ipi / (xi * xi + gd * gd);
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        f += __shfl_down_sync(0xffffffffu, f, o);
-        fp += __shfl_down_sync(0xffffffffu, fp, o);
-    }
-    if (lane == 0) { s_red[0][warp] = f; s_red[1][warp] = fp; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double a = 0, b = 0;
-        for (int w = 0; w < NW; ++w) { a += s_red[0][w]; b += s_red[1][w]; }
-        part[(size_t)blockIdx.x * 2 + 0] = a;
-        part[(size_t)blockIdx.x * 2 + 1] = b;
-    }
-    if (!last_cta(counter)) return;
-    double F = 0, Fp = 0;
-    for (int q = threadIdx.x; q < G; q += MU_THREADS) {
-        F += __ldcg(&part[(size_t)q * 2 + 0]);
-        Fp += __ldcg(&part[(size_t)q * 2 + 1]);
+    if (!s_last) return;
+    __threadfence();
+    double F = 0.0, F1 = 0.0, F2 = 0.0;
+    for (int q = threadIdx.x; q < G; q += (int)blockDim.x) {
+        F += __ldcg(part + 4 * (size_t)q + 0);
+        F1 += __ldcg(part + 4 * (size_t)q + 1);
+        F2 += __ldcg(part + 4 * (size_t)q + 2);
     }
     for (int o = 16; o > 0; o >>= 1) {
         F += __shfl_down_sync(0xffffffffu, F, o);
-        Fp += __shfl_down_sync(0xffffffffu, Fp, o);
+        F1 += __shfl_down_sync(0xffffffffu, F1, o);
+        F2 += __shfl_down_sync(0xffffffffu, F2, o);
     }
     __syncthreads();
-    if (lane == 0) { s_red[0][warp] = F; s_red[1][warp] = Fp; }
+    if (lane == 0) { s_red[warp][0] = F; s_red[warp][1] = F1; s_red[warp][2] = F2; }
     __syncthreads();
     if (threadIdx.x == 0) {
-        F = 0;
-        Fp = 0;
-        for (int w = 0; w < NW; ++w) { F += s_red[0][w]; Fp += s_red[1][w]; }
-        const double step = (F - target) / Fp;   // d/dmu of sum_k occ = sum_k Lorentzian
-        res[10 + 2 * it] = mu - step;
-        res[11 + 2 * it] = step;
-        if (it == MU_NEWTON - 1) {
-            st->mu = mu - step;
-            st->last_step = fabs(step);
-            if (mu_out) *mu_out = mu - step;
-            // a last step below 1e-7 eV leaves an error of order 1e-12 eV
-            if (!(fabs(step) < 1e-7)) atomicCAS(status, (unsigned)DEV_OK, (unsigned)DEV_ENOCONV);
-        }
+        F = F1 = F2 = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { F += s_red[w][0]; F1 += s_red[w][1]; F2 += s_red[w][2]; }
+        const double d = F - mc.target;                   // n - target
+        const double d1 = F1 * igam, d2 = F2 * igam * igam;  // dn/dmu, d2n/dmu2
+        const double step = 2.0 * d * d1 / (2.0 * d1 * d1 - d * d2);
+        const double mu_new = mu - step;
+        st->mu = mu_new;
+        st->last_step = fabs(step);
+        if (mu_out) *mu_out = mu_new;
+        // the root lies within the last bracket up to FP32 noise (below
+        // 1e-6 eV); a larger step means the multisection went wrong
+        if (!(fabs(step) <= 2.0 * (sh.br.hi - sh.br.lo) + 1e-5))
+            atomicCAS(status, (unsigned)DEV_OK, (unsigned)DEV_ENOCONV);
     }
 }
 
-// mu given by the caller.
-__global__ void k_mu_given(double mu, InstState *st, double *mu_out)
+static MuConst mu_const(const Geom &g, const Band &band, int G)
 {
-    st->mu = mu;
-    st->last_step = 0.0;
-    if (mu_out) *mu_out = mu;
+    MuConst mc;
+    mc.NC = MU_NCPT * G;
+    mc.passes = band.gamma < 0.02 ? 3 : 2;
+    mc.inv_nc1 = 1.0 / (double)(mc.NC - 1);
+    mc.inv_gam = 1.0 / band.gamma;
+    mc.target = band.filling * 0.5 * (double)g.npz * (double)g.npz;
+    mc.target32 = llrint(mc.target * (double)MU_SECT_SCALE);
+    mc.B = (band.band_kind == 1) ? 9.869604401089358 : 4.0 * (fabs(band.t) + fabs(band.tp) + fabs(band.tpp));
+    return mc;
 }
 
 cudaError_t launch_twiddles(int len, float2 *tw32, double2 *tw64, cudaStream_t s)
@@ -295,33 +448,31 @@ cudaError_t launch_twiddles(int len, float2 *tw32, double2 *tw64, cudaStream_t s
     return cudaGetLastError();
 }
 
-cudaError_t launch_tables(const Geom &g, const Band &band, AxisTab *axis, float2 *eps32, double *eps64,
-                          cudaStream_t s)
+// Tables plus the first chemical-potential launch (multisection pass 0, or
+// the given mu).
+cudaError_t launch_setup(const Geom &g, const Band &band, AxisTab *axis, float2 *eps32, double *eps64,
+                         InstState *st, double *acc, unsigned *bar, double *mu_out, int G, cudaStream_t s)
 {
-    int n = g.N > g.n_eps ? g.N : g.n_eps;
-    k_tables<<<(n + 127) / 128, 128, 0, s>>>(g, band, axis, eps32, eps64);
+    const int ntab = g.N > g.n_eps ? g.N : g.n_eps;
+    const int GT = (ntab + MU_TAB_THREADS - 1) / MU_TAB_THREADS;
+    const int Gs = band.solve_mu ? G : 0;
+    k_setup<<<Gs + GT, MU_THREADS, 0, s>>>(g, band, axis, eps32, eps64, st, acc, bar, mu_out, mu_const(g, band, G),
+                                           Gs);
     return cudaGetLastError();
 }
 
-// CTAs of each chemical-potential launch: one per SM.
-int mu_grid_size(int num_sms, int npts)
-{
-    (void)npts;
-    return num_sms < 1 ? 1 : num_sms;   // one CTA per SM
-}
-
+// The remaining chemical-potential launches (none for a given mu).
 cudaError_t launch_solve_mu(const Geom &g, const Band &band, const AxisTab *axis, InstState *st, double *acc,
                             unsigned *bar, unsigned *status, double *mu_out, int G, cudaStream_t s)
 {
-    if (!band.solve_mu) {
-        k_mu_given<<<1, 1, 0, s>>>(band.mu, st, mu_out);
-        return cudaGetLastError();
-    }
-    const int Gs = G < MU_SECT_CTAS ? G : MU_SECT_CTAS;
-    for (int pass = 0; pass < MU_FP32_PASSES; ++pass)
-        k_mu_sect<<<Gs, MU_THREADS, 0, s>>>(g, band, axis, acc, bar, pass);
-    for (int it = 0; it < MU_NEWTON; ++it)
-        k_mu_newton<<<G, MU_THREADS, 0, s>>>(g, band, axis, st, acc, bar, it, status, mu_out);
+    if (!band.solve_mu) return cudaSuccess;
+    const MuConst mc = mu_const(g, band, G);
+    for (int pass = 1; pass < mc.passes; ++pass) k_mu_sect<<<G, MU_THREADS, 0, s>>>(g, band, acc, pass, mc);
+    // one warp per CTA when every CTA has at most 32 pairs (the FP64 chains
+    // then run side by side and the reductions are short)
+    const int h = g.npz / 2, npairs = (h + 1) * (h + 2) / 2;
+    const int T = npairs <= 32 * G ? 32 : MU_NT_THREADS;
+    k_mu_halley<<<G, T, 0, s>>>(g, band, axis, st, acc, bar, status, mu_out, mc);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,517 @@
+// TMA-staged, software-pipelined momentum passes (FP32).
+//
+// The same transforms as k_fwd_y2 / k_inv_y2 / k_x_product (Sec. 3: FFTs
+// along p_y, the p_x product pass, the inverse along p_y), restructured for
+// latency: persistent CTAs walk the column tiles, and while a CTA transforms
+// one tile in registers, the tensor memory accelerator already copies the
+// next tile's input columns from HBM into a shared-memory staging buffer
+// (cp.async.bulk.tensor, completion counted on an mbarrier).  The copy of tile
+// i + 1 is issued once every thread has moved tile i from the staging buffer
+// into registers, so one buffer suffices; the FFT exchanges use a separate
+// shared-memory region.  Waits are bounded (1 s of %globaltimer): a CTA that
+// gives up records DEV_ETIMEOUT in the status word, waits (bounded) for its
+// copy in flight and leaves.
+//
+// Tensor maps (3D, FP32 elements, no swizzle) are encoded on the host per
+// launch from the workspace pointers; a complex value is two floats, so a
+// column offset c is the float coordinate 2c (16-byte aligned for even c).
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+
+#include "kernels.cuh"
+
+namespace lh {
+
+// ---------------------------------------------------------------------------
+// Device helpers (inline PTX).
+__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Wait for the phase with the given parity, at most ~1 s.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsigned parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try_wait(bar, parity))
+        if (global_ns() - t0 > 1000000000ull) return false;
+    return true;
+}
+// Generic-proxy accesses of shared memory before this point are ordered
+// before later async-proxy (TMA) writes to it.
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z,
+                                            unsigned long long *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(smem_addr(dst)), "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z),
+        "r"(smem_addr(bar))
+        : "memory");
+}
+
+// Shared-memory layout of a pipelined CTA: [staging][FFT exchange][mbarrier].
+// The staging buffer starts at the (128-byte aligned) dynamic base.
+struct TmaSmem {
+    size_t stage_bytes, fft_bytes;
+    __host__ __device__ size_t total() const { return stage_bytes + fft_bytes + 16; }
+};
+
+// Records a timeout once; every thread of the CTA calls it with the same ok.
+__device__ __forceinline__ bool tile_ready(unsigned long long *bar, unsigned parity, unsigned *status)
+{
+    const bool ok = mbar_wait_bounded(bar, parity);
+    const int all = __syncthreads_and(ok ? 1 : 0);
+    if (!all && threadIdx.x == 0) atomicCAS(status, (unsigned)DEV_OK, (unsigned)DEV_ETIMEOUT);
+    return all != 0;
+}
+// After a timeout: give the copy in flight (bounded) time to land before the
+// CTA's shared memory is released.
+__device__ __forceinline__ void drain(unsigned long long *bar, unsigned parity)
+{
+    if (threadIdx.x == 0) (void)mbar_wait_bounded(bar, parity);
+    __syncthreads();
+}
+
+// CTAs per SM the register budget is sized for: the tile config's own count,
+// unless shared memory (staging for an estimated number of rows plus the FFT
+// exchange) admits fewer.
+__host__ __device__ constexpr int tma_minb(int minb, long long bytes)
+{
+    return bytes <= 0 ? minb : (225000 / bytes < 1 ? 1 : (225000 / bytes < minb ? (int)(225000 / bytes) : minb));
+}
+// Rows staged per tile in the usual geometry: N = 2P/3 for 3 * 2^k lengths
+// (rounded up to 256-row boxes beyond 256), P otherwise.
+__host__ __device__ constexpr long long tma_rows_est(int L, bool all_rows)
+{
+    return all_rows || fft_len_pow2(L) ? (L <= 256 ? L : (L + 255) / 256 * 256)
+                                       : (2 * L / 3 <= 256 ? 2 * L / 3 : (2 * L / 3 + 255) / 256 * 256);
+}
+template <int L, typename Cfg, bool INV>
+struct PairTmaBounds {
+    using E = FftPair<float, L, Cfg::C, Cfg::T, INV>;
+    static constexpr int MINB =
+        tma_minb(Cfg::MINB, tma_rows_est(L, INV) * Cfg::C * 8 + (long long)E::SMEM_ELEMS * 8 + 16);
+};
+template <int L, typename Cfg>
+struct XTmaBounds {
+    using EF = FftPair<float, L, 2 * Cfg::C, Cfg::T, false>;
+    static constexpr int MINB =
+        tma_minb(Cfg::MINB, 2 * tma_rows_est(L, false) * Cfg::C * 8 + (long long)EF::SMEM_ELEMS * 8 + 16);
+};
+
+// ---------------------------------------------------------------------------
+// p_y forward: U1 [N][N][2 SP] -> U2 [N][P][2 SP].  Tile = (column tile of C
+// columns, i_x); staging [NR][C] (NR = N rounded up to the box height).
+template <int L, typename Cfg>
+__global__ void __launch_bounds__(Cfg::T, (PairTmaBounds<L, Cfg, false>::MINB))
+k_fwd_y_tma(Geom g, const __grid_constant__ CUtensorMap map, float2 *__restrict__ U2,
+            const float2 *__restrict__ tw, unsigned *status, int box_rows)
+{
+    constexpr int C = Cfg::C, T = Cfg::T;
+    using E = FftPair<float, L, C, T, false>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int nbox = (g.N + box_rows - 1) / box_rows, NR = nbox * box_rows;
+    const TmaSmem lay{(size_t)NR * C * sizeof(float2), (size_t)E::SMEM_ELEMS * sizeof(float2)};
+    if (dyn_smem_bytes() < lay.total()) return;
+    float2 *stage = reinterpret_cast<float2 *>(smem_raw);
+    float2 *sm = reinterpret_cast<float2 *>(smem_raw + lay.stage_bytes);
+    unsigned long long *bar = reinterpret_cast<unsigned long long *>(smem_raw + lay.stage_bytes + lay.fft_bytes);
+
+    const int W = 2 * g.SP, tiles_x = (W + C - 1) / C, ntiles = tiles_x * g.N;
+    const unsigned tx = (unsigned)(nbox * box_rows * C * sizeof(float2));
+    auto issue = [&](int t) {
+        const int ix = t / tiles_x, c0 = (t % tiles_x) * C;
+        mbar_expect_tx(bar, tx);
+        for (int q = 0; q < nbox; ++q) tma_load_3d(stage + (size_t)q * box_rows * C, &map, 2 * c0, q * box_rows, ix, bar);
+    };
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        if ((int)blockIdx.x < ntiles) issue(blockIdx.x);
+    }
+    __syncthreads();
+    unsigned parity = 0;
+    const int p = E::pair();
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int ix = t / tiles_x, c0 = (t % tiles_x) * C;
+        if (!tile_ready(bar, parity, status)) { drain(bar, parity); return; }
+        parity ^= 1u;
+        float2 va[E::VPT], vb[E::VPT];
+#pragma unroll
+        for (int b = 0; b < E::VPT / E::R0; ++b)
+#pragma unroll
+            for (int r = 0; r < E::R0; ++r) {
+                const int n = E::first_row(b, r);
+                if (n < g.N) {
+                    float4 q = *reinterpret_cast<const float4 *>(&stage[(size_t)n * C + 2 * p]);
+                    va[b * E::R0 + r] = make_float2(q.x, q.y);
+                    vb[b * E::R0 + r] = make_float2(q.z, q.w);
+                } else {
+                    va[b * E::R0 + r] = make_float2(0.f, 0.f);
+                    vb[b * E::R0 + r] = make_float2(0.f, 0.f);
+                }
+            }
+        __syncthreads();   // the staging buffer is free
+        if (threadIdx.x == 0 && t + (int)gridDim.x < ntiles) {
+            fence_proxy_async();
+            issue(t + gridDim.x);
+        }
+        E::run(va, vb, sm, tw);
+        const int c = c0 + 2 * p;
+        if (c < W && (c % g.SP) < g.H) {   // (c + 1 is in the same row)
+            float2 *dst = U2 + (long long)ix * g.xs2 + c;
+#pragma unroll
+            for (int b = 0; b < E::VPT / E::RL; ++b)
+#pragma unroll
+                for (int r = 0; r < E::RL; ++r)
+                    gst2(dst + (long long)E::last_row(b, r) * W, va[b * E::RL + r], vb[b * E::RL + r]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// p_y inverse: U3 [Q][P][SP] (plane stride xs3) -> U4 [Q][Q][SP].  Tile =
+// (column tile over [0, H), l_x); staging [NR][C], NR = P rounded up.
+template <int L, typename Cfg>
+__global__ void __launch_bounds__(Cfg::T, (PairTmaBounds<L, Cfg, true>::MINB))
+k_inv_y_tma(Geom g, const __grid_constant__ CUtensorMap map, float2 *__restrict__ U4,
+            const float2 *__restrict__ tw, unsigned *status, int box_rows)
+{
+    constexpr int C = Cfg::C, T = Cfg::T;
+    using E = FftPair<float, L, C, T, true>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int nbox = (L + box_rows - 1) / box_rows, NR = nbox * box_rows;
+    const TmaSmem lay{(size_t)NR * C * sizeof(float2), (size_t)E::SMEM_ELEMS * sizeof(float2)};
+    if (dyn_smem_bytes() < lay.total()) return;
+    float2 *stage = reinterpret_cast<float2 *>(smem_raw);
+    float2 *sm = reinterpret_cast<float2 *>(smem_raw + lay.stage_bytes);
+    unsigned long long *bar = reinterpret_cast<unsigned long long *>(smem_raw + lay.stage_bytes + lay.fft_bytes);
+
+    const int tiles_x = (g.H + C - 1) / C, ntiles = tiles_x * g.Q;
+    const unsigned tx = (unsigned)(nbox * box_rows * C * sizeof(float2));
+    auto issue = [&](int t) {
+        const int lx = t / tiles_x, c0 = (t % tiles_x) * C;
+        mbar_expect_tx(bar, tx);
+        for (int q = 0; q < nbox; ++q) tma_load_3d(stage + (size_t)q * box_rows * C, &map, 2 * c0, q * box_rows, lx, bar);
+    };
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        if ((int)blockIdx.x < ntiles) issue(blockIdx.x);
+    }
+    __syncthreads();
+    unsigned parity = 0;
+    const int p = E::pair();
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int lx = t / tiles_x, c0 = (t % tiles_x) * C;
+        if (!tile_ready(bar, parity, status)) { drain(bar, parity); return; }
+        parity ^= 1u;
+        float2 va[E::VPT], vb[E::VPT];
+#pragma unroll
+        for (int b = 0; b < E::VPT / E::R0; ++b)
+#pragma unroll
+            for (int r = 0; r < E::R0; ++r) {
+                float4 q = *reinterpret_cast<const float4 *>(&stage[(size_t)E::first_row(b, r) * C + 2 * p]);
+                va[b * E::R0 + r] = make_float2(q.x, q.y);
+                vb[b * E::R0 + r] = make_float2(q.z, q.w);
+            }
+        __syncthreads();
+        if (threadIdx.x == 0 && t + (int)gridDim.x < ntiles) {
+            fence_proxy_async();
+            issue(t + gridDim.x);
+        }
+        E::run(va, vb, sm, tw);
+        const int c = c0 + 2 * p;
+        if (c < g.H) {
+            float2 *dst = U4 + (long long)lx * g.Q * g.SP + c;
+#pragma unroll
+            for (int b = 0; b < E::VPT / E::RL; ++b)
+#pragma unroll
+                for (int r = 0; r < E::RL; ++r) {
+                    const int l = lag_index(E::last_row(b, r), g.P, g.Q);
+                    if (l >= 0) gst2(dst + (long long)l * g.SP, va[b * E::RL + r], vb[b * E::RL + r]);
+                }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// p_x pass with the conjugate product: U2 [N][P][2 SP] (plane stride xs2) ->
+// U3 [Q][P][SP].  Tile = (column tile over [0, H), k_y); staging a^ [NR][C]
+// then b^ [NR][C], NR = N rounded up.
+template <int L, typename Cfg>
+__global__ void __launch_bounds__(Cfg::T, (XTmaBounds<L, Cfg>::MINB))
+k_x_product_tma(Geom g, const __grid_constant__ CUtensorMap map, float2 *__restrict__ U3,
+                const float2 *__restrict__ tw, unsigned *status, int box_rows)
+{
+    constexpr int C = Cfg::C, T = Cfg::T;
+    using EF = FftPair<float, L, 2 * C, T, false>;
+    using EI = Fft<float, L, C, T, MAP_COL, true>;
+    static_assert(EF::RL == EI::R0 && EF::VPT == EI::VPT && EF::CP == C, "forward and inverse tiles must coincide");
+    constexpr int FFT_ELEMS = EF::SMEM_ELEMS > EI::SMEM_ELEMS ? EF::SMEM_ELEMS : EI::SMEM_ELEMS;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int nbox = (g.N + box_rows - 1) / box_rows, NR = nbox * box_rows;
+    const TmaSmem lay{2 * (size_t)NR * C * sizeof(float2), (size_t)FFT_ELEMS * sizeof(float2)};
+    if (dyn_smem_bytes() < lay.total()) return;
+    float2 *stage_a = reinterpret_cast<float2 *>(smem_raw);
+    float2 *stage_b = stage_a + (size_t)NR * C;
+    float2 *sm = reinterpret_cast<float2 *>(smem_raw + lay.stage_bytes);
+    unsigned long long *bar = reinterpret_cast<unsigned long long *>(smem_raw + lay.stage_bytes + lay.fft_bytes);
+
+    const int tiles_x = (g.H + C - 1) / C, ntiles = tiles_x * g.P;
+    const unsigned tx = (unsigned)(2 * nbox * box_rows * C * sizeof(float2));
+    auto issue = [&](int t) {
+        const int ky = t / tiles_x, c0 = (t % tiles_x) * C;
+        mbar_expect_tx(bar, tx);
+        for (int q = 0; q < nbox; ++q) {
+            tma_load_3d(stage_a + (size_t)q * box_rows * C, &map, 2 * c0, ky, q * box_rows, bar);
+            tma_load_3d(stage_b + (size_t)q * box_rows * C, &map, 2 * (g.SP + c0), ky, q * box_rows, bar);
+        }
+    };
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        if ((int)blockIdx.x < ntiles) issue(blockIdx.x);
+    }
+    __syncthreads();
+    unsigned parity = 0;
+    const int col = (int)(threadIdx.x % C);
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int ky = t / tiles_x, c0 = (t % tiles_x) * C;
+        if (!tile_ready(bar, parity, status)) { drain(bar, parity); return; }
+        parity ^= 1u;
+        float2 va[EF::VPT], vb[EF::VPT];
+#pragma unroll
+        for (int b = 0; b < EF::VPT / EF::R0; ++b)
+#pragma unroll
+            for (int r = 0; r < EF::R0; ++r) {
+                const int n = EF::first_row(b, r);
+                const bool ld = n < g.N;
+                va[b * EF::R0 + r] = ld ? stage_a[(size_t)n * C + col] : make_float2(0.f, 0.f);
+                vb[b * EF::R0 + r] = ld ? stage_b[(size_t)n * C + col] : make_float2(0.f, 0.f);
+            }
+        __syncthreads();
+        if (threadIdx.x == 0 && t + (int)gridDim.x < ntiles) {
+            fence_proxy_async();
+            issue(t + gridDim.x);
+        }
+        EF::run(va, vb, sm, tw);
+#pragma unroll
+        for (int i = 0; i < EF::VPT; ++i) va[i] = cmulc(vb[i], va[i]);   // conj(a^) b^
+        EI::run(va, sm, tw);
+        const int c = c0 + col;
+        if (c < g.H) {
+            float2 *dst = U3 + (long long)ky * g.SP + c;
+#pragma unroll
+            for (int b = 0; b < EI::VPT / EI::RL; ++b)
+#pragma unroll
+                for (int r = 0; r < EI::RL; ++r) {
+                    int cl, n;
+                    EI::last_elem(b, r, cl, n);
+                    const int l = lag_index(n, g.P, g.Q);
+                    if (l >= 0) dst[(long long)l * g.xs3] = va[b * EI::RL + r];
+                }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host side.
+
+// Rows per box (at most 256, the TMA limit): the n rows split evenly into
+// ceil(n / 256) boxes, so little staging goes to rows past the end.
+static int tma_box_rows(int n)
+{
+    const int nbox = (n + 255) / 256;
+    return (n + nbox - 1) / nbox;
+}
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            f = nullptr;
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    }();
+    return fn;
+}
+
+// 3D FP32 tensor map: dims (fastest first) d0 x d1 x d2, byte strides s1, s2,
+// box b0 x b1 x b2 (floats / rows).
+static cudaError_t make_map(CUtensorMap *m, const void *base, unsigned long long d0, unsigned long long d1,
+                            unsigned long long d2, unsigned long long s1, unsigned long long s2, unsigned b0,
+                            unsigned b1, unsigned b2)
+{
+    auto fn = encode_fn();
+    if (!fn) return cudaErrorNotSupported;
+    const cuuint64_t dims[3] = {d0, d1, d2};
+    const cuuint64_t strides[2] = {s1, s2};
+    const cuuint32_t box[3] = {b0, b1, b2};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(base), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// Persistent grid: every SM filled to its occupancy, no more CTAs than tiles.
+template <typename K>
+static cudaError_t persistent_grid(K k, int T, size_t smem, int ntiles, int &grid)
+{
+    int dev = 0, sms = 0, per = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, T, smem);
+    if (e != cudaSuccess) return e;
+    if (per < 1) return cudaErrorInvalidConfiguration;
+    grid = std::min(ntiles, sms * per);
+    return cudaSuccess;
+}
+
+template <int L, typename Cfg>
+static cudaError_t launch_fwd_y_tma_t(const Geom &g, const Work<float> &w, cudaStream_t s)
+{
+    constexpr int C = Cfg::C, T = Cfg::T;
+    using E = FftPair<float, L, C, T, false>;
+    const int box_rows = tma_box_rows(g.N), nbox = (g.N + box_rows - 1) / box_rows;
+    const TmaSmem lay{(size_t)nbox * box_rows * C * sizeof(float2), (size_t)E::SMEM_ELEMS * sizeof(float2)};
+    auto k = k_fwd_y_tma<L, Cfg>;
+    cudaError_t e = smem_attrs(k, lay.total());
+    CUtensorMap map;
+    if (e == cudaSuccess)
+        e = make_map(&map, w.X, 4ull * g.SP, (unsigned long long)g.N, (unsigned long long)g.N, 16ull * g.SP,
+                     16ull * g.SP * g.N, 2 * C, box_rows, 1);
+    int grid = 0;
+    const int ntiles = ((2 * g.SP + C - 1) / C) * g.N;
+    if (e == cudaSuccess) e = persistent_grid(k, T, lay.total(), ntiles, grid);
+    if (e != cudaSuccess) return e;
+    k<<<grid, T, lay.total(), s>>>(g, map, (float2 *)w.Y, twiddles_for<float>(w, L), w.status, box_rows);
+    return cudaGetLastError();
+}
+
+template <int L, typename Cfg>
+static cudaError_t launch_inv_y_tma_t(const Geom &g, const Work<float> &w, cudaStream_t s)
+{
+    constexpr int C = Cfg::C, T = Cfg::T;
+    using E = FftPair<float, L, C, T, true>;
+    const int box_rows = tma_box_rows(L), nbox = (L + box_rows - 1) / box_rows;
+    const TmaSmem lay{(size_t)nbox * box_rows * C * sizeof(float2), (size_t)E::SMEM_ELEMS * sizeof(float2)};
+    auto k = k_inv_y_tma<L, Cfg>;
+    cudaError_t e = smem_attrs(k, lay.total());
+    CUtensorMap map;
+    if (e == cudaSuccess)
+        e = make_map(&map, w.X, 2ull * g.SP, (unsigned long long)g.P, (unsigned long long)g.Q, 8ull * g.SP,
+                     8ull * (unsigned long long)g.xs3, 2 * C, box_rows, 1);
+    int grid = 0;
+    const int ntiles = ((g.H + C - 1) / C) * g.Q;
+    if (e == cudaSuccess) e = persistent_grid(k, T, lay.total(), ntiles, grid);
+    if (e != cudaSuccess) return e;
+    k<<<grid, T, lay.total(), s>>>(g, map, (float2 *)w.Y, twiddles_for<float>(w, L), w.status, box_rows);
+    return cudaGetLastError();
+}
+
+template <int L, typename Cfg>
+static cudaError_t launch_x_product_tma_t(const Geom &g, const Work<float> &w, cudaStream_t s)
+{
+    constexpr int C = Cfg::C, T = Cfg::T;
+    using EF = FftPair<float, L, 2 * C, T, false>;
+    using EI = Fft<float, L, C, T, MAP_COL, true>;
+    constexpr int FFT_ELEMS = EF::SMEM_ELEMS > EI::SMEM_ELEMS ? EF::SMEM_ELEMS : EI::SMEM_ELEMS;
+    const int box_rows = tma_box_rows(g.N), nbox = (g.N + box_rows - 1) / box_rows;
+    const TmaSmem lay{2 * (size_t)nbox * box_rows * C * sizeof(float2), (size_t)FFT_ELEMS * sizeof(float2)};
+    auto k = k_x_product_tma<L, Cfg>;
+    cudaError_t e = smem_attrs(k, lay.total());
+    CUtensorMap map;
+    if (e == cudaSuccess)
+        e = make_map(&map, w.Y, 4ull * g.SP, (unsigned long long)g.P, (unsigned long long)g.N, 16ull * g.SP,
+                     8ull * (unsigned long long)g.xs2, 2 * C, 1, box_rows);
+    int grid = 0;
+    const int ntiles = ((g.H + C - 1) / C) * g.P;
+    if (e == cudaSuccess) e = persistent_grid(k, T, lay.total(), ntiles, grid);
+    if (e != cudaSuccess) return e;
+    k<<<grid, T, lay.total(), s>>>(g, map, (float2 *)w.X, twiddles_for<float>(w, L), w.status, box_rows);
+    return cudaGetLastError();
+}
+
+// Entry points.  p_y passes: variant 3 = PairCfg tiles, 4 = PairCfg12 tiles;
+// product pass: variant 2 = XCfg tiles, 3 = XCfg12 tiles.  Lengths >= 128.
+template <int L>
+static cudaError_t fwd_y_tma(const Geom &g, const Work<float> &w, cudaStream_t s, int variant)
+{
+    if constexpr (L >= 128) {
+        if (variant == 3) return launch_fwd_y_tma_t<L, PairCfg<L>>(g, w, s);
+        if constexpr (fft_has_family1(L))
+            if (variant == 4) return launch_fwd_y_tma_t<L, PairCfg12<L>>(g, w, s);
+    }
+    return cudaErrorInvalidValue;
+}
+template <int L>
+static cudaError_t inv_y_tma(const Geom &g, const Work<float> &w, cudaStream_t s, int variant)
+{
+    if constexpr (L >= 128) {
+        if (variant == 3) return launch_inv_y_tma_t<L, PairCfg<L>>(g, w, s);
+        if constexpr (fft_has_family1(L))
+            if (variant == 4) return launch_inv_y_tma_t<L, PairCfg12<L>>(g, w, s);
+    }
+    return cudaErrorInvalidValue;
+}
+template <int L>
+static cudaError_t x_product_tma(const Geom &g, const Work<float> &w, cudaStream_t s, int variant)
+{
+    if constexpr (L >= 128) {
+        if (variant == 2) return launch_x_product_tma_t<L, XCfg<L>>(g, w, s);
+        if constexpr (fft_has_family1(L))
+            if (variant == 3) return launch_x_product_tma_t<L, XCfg12<L>>(g, w, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_fwd_y_tma(const Geom &g, const Work<float> &w, cudaStream_t s, int variant)
+{
+#define CALL(L) fwd_y_tma<L>(g, w, s, variant)
+    LH_P_SWITCH(g.P, CALL)
+#undef CALL
+}
+cudaError_t launch_inv_y_tma(const Geom &g, const Work<float> &w, cudaStream_t s, int variant)
+{
+#define CALL(L) inv_y_tma<L>(g, w, s, variant)
+    LH_P_SWITCH(g.P, CALL)
+#undef CALL
+}
+cudaError_t launch_x_product_tma(const Geom &g, const Work<float> &w, cudaStream_t s, int variant)
+{
+#define CALL(L) x_product_tma<L>(g, w, s, variant)
+    LH_P_SWITCH(g.P, CALL)
+#undef CALL
+}
+
+}  // namespace lh

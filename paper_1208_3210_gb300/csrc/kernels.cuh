@@ -49,6 +49,22 @@ template <> struct PairCfg<384>  { static constexpr int C = 32, T = 256, MINB = 
 template <> struct PairCfg<768>  { static constexpr int C = 16, T = 256, MINB = 2; };
 template <> struct PairCfg<1536> { static constexpr int C = 8, T = 256, MINB = 2; };
 
+// Tiles with 12 values per thread per column (radix family 1) at the 3 * 2^k
+// lengths from 192: half the registers of the 24-value tiles above (so no
+// spills and up to twice the warps per SM), one or two more exchanges.
+// Paired p_y passes: VPT = (C/2) L / T = 12.
+template <int L> struct PairCfg12;
+template <> struct PairCfg12<192>  { static constexpr int C = 16, T = 128, MINB = 4; };
+template <> struct PairCfg12<384>  { static constexpr int C = 16, T = 256, MINB = 2; };
+template <> struct PairCfg12<768>  { static constexpr int C = 16, T = 512, MINB = 1; };
+template <> struct PairCfg12<1536> { static constexpr int C = 8, T = 512, MINB = 1; };
+// Product pass: VPT = C L / T = 12.
+template <int L> struct XCfg12;
+template <> struct XCfg12<192>  { static constexpr int C = 8, T = 128, MINB = 4; };
+template <> struct XCfg12<384>  { static constexpr int C = 8, T = 256, MINB = 2; };
+template <> struct XCfg12<768>  { static constexpr int C = 8, T = 512, MINB = 1; };
+template <> struct XCfg12<1536> { static constexpr int C = 4, T = 512, MINB = 1; };
+
 // Contiguous-axis passes (energy axis): C lines of length L per CTA.
 template <int L> struct LineCfg;
 template <> struct LineCfg<16>   { static constexpr int C = 64, T = 64; };
@@ -85,6 +101,15 @@ __host__ __device__ inline const cx<Real> *twiddles_for(const Work<Real> &w, int
 // memory when it is short, so a launch configured with too little shared
 // memory gives wrong results (caught by the tests) instead of an
 // out-of-bounds access.
+// Dynamic shared-memory limit of a kernel.  (The L1/shared carveout is left
+// to the driver: pinning it to the largest shared share slowed the FFT passes,
+// which read twiddles through L1, by 10-20%.)
+template <typename K>
+inline cudaError_t smem_attrs(K k, size_t dyn)
+{
+    return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+}
+
 __device__ __forceinline__ unsigned dyn_smem_bytes()
 {
     unsigned r;

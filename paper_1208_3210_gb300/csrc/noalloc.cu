@@ -27,8 +27,8 @@ lindhard_status geom_from_grid(const lindhard_grid &gr, Geom &g, int &prec);
 lindhard_status band_from_params(const lindhard_band *b, Band &o);
 lindhard_status set_error(lindhard_status st, const char *msg);
 cudaError_t launch_twiddles(int len, float2 *tw32, double2 *tw64, cudaStream_t s);
-cudaError_t launch_tables(const Geom &g, const Band &band, AxisTab *axis, float2 *eps32, double *eps64,
-                          cudaStream_t s);
+cudaError_t launch_setup(const Geom &g, const Band &band, AxisTab *axis, float2 *eps32, double *eps64,
+                         InstState *st, double *acc, unsigned *bar, double *mu_out, int G, cudaStream_t s);
 size_t mu_acc_doubles(int G);
 size_t mu_barrier_words();
 int mu_grid_size(int num_sms, int npts);
@@ -37,7 +37,7 @@ cudaError_t launch_solve_mu(const Geom &g, const Band &band, const AxisTab *axis
 cudaError_t launch_fwd_energy(const Geom &g, const Band &band, const Work<float> &w, const float *A_in,
                               cudaStream_t s);
 cudaError_t launch_fwd_y(const Geom &g, const Work<float> &w, cudaStream_t s, int variant);
-cudaError_t launch_x_product(const Geom &g, const Work<float> &w, cudaStream_t s);
+cudaError_t launch_x_product(const Geom &g, const Work<float> &w, cudaStream_t s, int variant);
 cudaError_t launch_inv_y(const Geom &g, const Work<float> &w, cudaStream_t s, int variant);
 cudaError_t launch_inv_energy(const Geom &g, const Work<float> &w, float *out, cudaStream_t s);
 }  // namespace lh
@@ -98,8 +98,6 @@ extern "C" lindhard_status lindhard_imchi_noalloc(const lindhard_grid *grid, con
         if (st != LINDHARD_OK) return st;
         if (b.band_kind == 1 && g.periodic)
             return set_error(LINDHARD_EINVAL, "free electrons need zones > 1 (the band is not periodic)");
-        if (b.solve_mu && g.npz > 512)
-            return set_error(LINDHARD_EUNSUPPORTED, "the filling solve supports pts_per_zone <= 512");
     }
     unsigned char *base = nullptr;
     int num_sms = 0;
@@ -149,13 +147,13 @@ extern "C" lindhard_status lindhard_imchi_noalloc(const lindhard_grid *grid, con
     if (e == cudaSuccess) e = cudaMemsetAsync(w.barrier, 0, mu_barrier_words() * sizeof(unsigned), s);
     if (e == cudaSuccess) e = launch_twiddles(tw_len, (float2 *)(base + off_tw32), (double2 *)(base + off_tw64), s);
     if (e == cudaSuccess && A_in == nullptr) {
-        e = launch_tables(g, b, w.axis, (float2 *)w.eps, nullptr, s);
+        e = launch_setup(g, b, w.axis, (float2 *)w.eps, nullptr, w.state, w.mu_acc, w.barrier, mu_out, G, s);
         if (e == cudaSuccess)
             e = launch_solve_mu(g, b, w.axis, w.state, w.mu_acc, w.barrier, w.status, mu_out, G, s);
     }
     if (e == cudaSuccess) e = launch_fwd_energy(g, b, w, A_in, s);
     if (e == cudaSuccess) e = launch_fwd_y(g, w, s, 1);
-    if (e == cudaSuccess) e = launch_x_product(g, w, s);
+    if (e == cudaSuccess) e = launch_x_product(g, w, s, 0);
     if (e == cudaSuccess) e = launch_inv_y(g, w, s, 1);
     if (e == cudaSuccess) e = launch_inv_energy(g, w, out, s);
     if (e != cudaSuccess) return set_error(LINDHARD_ECUDA, cudaGetErrorString(e));

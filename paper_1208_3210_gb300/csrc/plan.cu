@@ -21,8 +21,8 @@
 namespace lh {
 // launchers (k_*.cu)
 cudaError_t launch_twiddles(int len, float2 *tw32, double2 *tw64, cudaStream_t s);
-cudaError_t launch_tables(const Geom &g, const Band &band, AxisTab *axis, float2 *eps32, double *eps64,
-                          cudaStream_t s);
+cudaError_t launch_setup(const Geom &g, const Band &band, AxisTab *axis, float2 *eps32, double *eps64,
+                         InstState *st, double *acc, unsigned *bar, double *mu_out, int G, cudaStream_t s);
 size_t mu_acc_doubles(int G);
 size_t mu_barrier_words();
 int mu_grid_size(int num_sms, int npts);
@@ -34,8 +34,8 @@ cudaError_t launch_fwd_energy(const Geom &g, const Band &band, const Work<double
                               cudaStream_t s);
 cudaError_t launch_fwd_y(const Geom &g, const Work<float> &w, cudaStream_t s, int variant);
 cudaError_t launch_fwd_y(const Geom &g, const Work<double> &w, cudaStream_t s, int variant);
-cudaError_t launch_x_product(const Geom &g, const Work<float> &w, cudaStream_t s);
-cudaError_t launch_x_product(const Geom &g, const Work<double> &w, cudaStream_t s);
+cudaError_t launch_x_product(const Geom &g, const Work<float> &w, cudaStream_t s, int variant);
+cudaError_t launch_x_product(const Geom &g, const Work<double> &w, cudaStream_t s, int variant);
 cudaError_t launch_inv_y(const Geom &g, const Work<float> &w, cudaStream_t s, int variant);
 cudaError_t launch_inv_y(const Geom &g, const Work<double> &w, cudaStream_t s, int variant);
 cudaError_t launch_inv_energy(const Geom &g, const Work<float> &w, float *out, cudaStream_t s);
@@ -110,9 +110,12 @@ struct lindhard_plan {
     size_t off_tw32 = 0, off_tw64 = 0, off_status = 0;
     int tw_len = 0;
     bool backward = false;       // LINDHARD_PLAN_BACKWARD
-    // engine variant of the p_y passes per instance (0 single-column,
-    // 1 paired-column); set by the autotuner (LINDHARD_PLAN_AUTOTUNE)
-    std::vector<int> yvar_fwd, yvar_inv;
+    // engine variants per instance, set by the autotuner
+    // (LINDHARD_PLAN_AUTOTUNE): p_y passes 0 single-column, 1 paired-column,
+    // 2 paired-column with 12 values per thread, 3 and 4 the TMA-staged
+    // persistent forms of 1 and 2; product pass 0 default tile, 1 tile with
+    // 12 values per thread, 2 and 3 their TMA-staged persistent forms
+    std::vector<int> yvar_fwd, yvar_inv, xvar;
     bool concurrent = false;     // LINDHARD_PLAN_CONCURRENT
     bool graph = false;          // LINDHARD_PLAN_GRAPH
     // concurrent execution: instances on plan-owned streams, forked from and
@@ -244,13 +247,14 @@ extern "C" void lindhard_plan_destroy(lindhard_plan *p);
 
 // ---------------------------------------------------------------------------
 // Autotuner.  For every distinct momentum geometry of an FP32 plan it times the
-// single-column and paired-column engines of both p_y passes with CUDA events
+// engine variants of the two p_y passes and of the product pass with CUDA events
 // (on the plan's own workspace; the data are whatever the workspace holds, the
 // timing does not depend on them) and keeps the faster.  Results are cached per
 // process, and in the JSON file named by LINDHARD_TUNE_CACHE when that is set:
-// one entry per line, {"<gpu>|P=..|N=..|PE=..|Q=..|fwd_y": variant, ...},
-// variant 1 = paired-column engine, 0 = single-column engine.  Cached
-// entries are used as they are (a cache file may pin a variant).
+// one entry per line, {"<gpu>|P=..|N=..|PE=..|Q=..|fwd_y": variant, ...}
+// (also |inv_y and |x_product; variants as for lindhard_plan::yvar_fwd and
+// xvar).  Cached entries in range are used as they are (a cache file may pin
+// a variant).
 template <typename Real>
 static Work<Real> work_of(lindhard_plan *p, int i);
 
@@ -268,7 +272,7 @@ static void tune_load()
     while (std::getline(f, line)) {
         size_t a = line.find('"'), b = line.find('"', a + 1), c = line.find(':', b);
         if (a == std::string::npos || b == std::string::npos || c == std::string::npos) continue;
-        g_tune[line.substr(a + 1, b - a - 1)] = atoi(line.c_str() + c + 1) ? 1 : 0;
+        g_tune[line.substr(a + 1, b - a - 1)] = atoi(line.c_str() + c + 1);
     }
 }
 static void tune_save()
@@ -310,20 +314,38 @@ static cudaError_t autotune(lindhard_plan *p)
         if (p->precision[i] != LINDHARD_FP32 || g.P < 128) continue;
         std::ostringstream key;
         key << prop.name << "|P=" << g.P << "|N=" << g.N << "|PE=" << g.PE << "|Q=" << g.Q;
-        std::string kf = key.str() + "|fwd_y", ki = key.str() + "|inv_y";
-        if (!g_tune.count(kf) || !g_tune.count(ki)) {
-            Work<float> w = work_of<float>(p, i);
-            float t[2][2];
-            for (int v = 0; v < 2; ++v) {
-                t[0][v] = time_launches([&] { return launch_fwd_y(g, w, 0, v); }, a, b);
-                t[1][v] = time_launches([&] { return launch_inv_y(g, w, 0, v); }, a, b);
-            }
-            e = cudaGetLastError();
-            g_tune[kf] = t[0][1] < t[0][0] ? 1 : 0;
-            g_tune[ki] = t[1][1] < t[1][0] ? 1 : 0;
+        const std::string kf = key.str() + "|fwd_y", ki = key.str() + "|inv_y", kx = key.str() + "|x_product";
+        const bool f1 = fft_has_family1(g.P);
+        std::vector<int> vy = {0, 1, 3}, vx = {0, 2};
+        if (f1) {
+            vy.push_back(2);
+            vy.push_back(4);
+            vx.push_back(1);
+            vx.push_back(3);
         }
-        p->yvar_fwd[i] = g_tune[kf];
-        p->yvar_inv[i] = g_tune[ki];
+        Work<float> w = work_of<float>(p, i);
+        // fastest of the variants of one pass (timed only when not cached)
+        auto pick = [&](const std::string &k, const std::vector<int> &vs, auto launch) {
+            if (!g_tune.count(k) || std::find(vs.begin(), vs.end(), g_tune[k]) == vs.end()) {
+                int best = vs[0];
+                float tbest = 0.f;
+                bool any = false;
+                for (size_t j = 0; j < vs.size(); ++j) {
+                    if (launch(vs[j]) != cudaSuccess) {   // a variant that cannot run here
+                        (void)cudaGetLastError();
+                        continue;
+                    }
+                    float t = time_launches([&] { return launch(vs[j]); }, a, b);
+                    if (!any || t < tbest) { best = vs[j]; tbest = t; any = true; }
+                }
+                g_tune[k] = best;
+            }
+            return g_tune[k];
+        };
+        p->yvar_fwd[i] = pick(kf, vy, [&](int v) { return launch_fwd_y(g, w, 0, v); });
+        p->yvar_inv[i] = pick(ki, vy, [&](int v) { return launch_inv_y(g, w, 0, v); });
+        p->xvar[i] = pick(kx, vx, [&](int v) { return launch_x_product(g, w, 0, v); });
+        e = cudaGetLastError();
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
@@ -441,6 +463,7 @@ extern "C" lindhard_status lindhard_plan_create(const lindhard_grid *grids, int 
     }
     p->yvar_fwd.assign(batch, 1);
     p->yvar_inv.assign(batch, 1);
+    p->xvar.assign(batch, 0);
     if (e == cudaSuccess && (flags & LINDHARD_PLAN_AUTOTUNE)) e = autotune(p);
     if (e != cudaSuccess) {
         lindhard_plan_destroy(p);
@@ -471,7 +494,7 @@ extern "C" lindhard_status lindhard_plan_sizes(const lindhard_plan *p, int index
     long long W3 = (long long)g.Q * g.P * g.H;
     long long W4 = (long long)g.Q * g.Q * g.H;
     out->hbm_bytes_forward = 2 * (W1 + W2 + W3 + W4) * cb + out->out_elems * rb;
-    out->kernels_forward = 11;   // tables, 5 chemical-potential launches, 5 FFT passes
+    out->kernels_forward = 9;   // set-up (tables + multisection pass 0), 3 chemical-potential launches, 5 FFT passes
     return LINDHARD_OK;
 }
 
@@ -557,8 +580,6 @@ static lindhard_status bands_of(lindhard_plan *p, const lindhard_band *bands, st
         if (st != LINDHARD_OK) return st;
         if (bs[i].band_kind == 1 && p->geoms[i].periodic)
             return fail(LINDHARD_EINVAL, "free electrons need zones > 1 (the band is not periodic)");
-        if (bs[i].solve_mu && p->geoms[i].npz > 512)
-            return fail(LINDHARD_EUNSUPPORTED, "the filling solve supports pts_per_zone <= 512; pass mu instead");
     }
     return LINDHARD_OK;
 }
@@ -578,8 +599,9 @@ static cudaError_t enqueue_forward(lindhard_plan *p, const std::vector<Band> &bs
         Work<Real> w = work_of<Real>(p, i);
         if (A_in == nullptr) {
             e = timed(p, 0, s, [&] {
-                return launch_tables(g, b, w.axis, sizeof(Real) == 4 ? (float2 *)w.eps : nullptr,
-                                     sizeof(Real) == 8 ? (double *)w.eps : nullptr, s);
+                return launch_setup(g, b, w.axis, sizeof(Real) == 4 ? (float2 *)w.eps : nullptr,
+                                    sizeof(Real) == 8 ? (double *)w.eps : nullptr, w.state, w.mu_acc, w.barrier,
+                                    mu_out ? mu_out + i : nullptr, p->mu_G, s);
             });
             if (e == cudaSuccess)
                 e = timed(p, 1, s, [&] {
@@ -591,7 +613,7 @@ static cudaError_t enqueue_forward(lindhard_plan *p, const std::vector<Band> &bs
         Real *o_i = out + o_off;
         if (e == cudaSuccess) e = timed(p, 2, s, [&] { return launch_fwd_energy(g, b, w, a_i, s); });
         if (e == cudaSuccess) e = timed(p, 3, s, [&] { return launch_fwd_y(g, w, s, p->yvar_fwd[i]); });
-        if (e == cudaSuccess) e = timed(p, 4, s, [&] { return launch_x_product(g, w, s); });
+        if (e == cudaSuccess) e = timed(p, 4, s, [&] { return launch_x_product(g, w, s, p->xvar[i]); });
         if (e == cudaSuccess) e = timed(p, 5, s, [&] { return launch_inv_y(g, w, s, p->yvar_inv[i]); });
         if (e == cudaSuccess) e = timed(p, 6, s, [&] { return launch_inv_energy(g, w, o_i, s); });
         a_off += (size_t)g.N * g.N * g.n_eps;
@@ -695,8 +717,6 @@ extern "C" lindhard_status lindhard_imchi_backward(lindhard_plan *p, const lindh
             if (st != LINDHARD_OK) return st;
             if (bs[i].band_kind == 1 && p->geoms[i].periodic)
                 return fail(LINDHARD_EINVAL, "free electrons need zones > 1 (the band is not periodic)");
-            if (bs[i].solve_mu && p->geoms[i].npz > 512)
-                return fail(LINDHARD_EUNSUPPORTED, "the filling solve supports pts_per_zone <= 512; pass mu instead");
         }
     }
     cudaStream_t s0 = (cudaStream_t)stream;
@@ -714,7 +734,8 @@ extern "C" lindhard_status lindhard_imchi_backward(lindhard_plan *p, const lindh
         double *partial = (double *)(p->ws + sl.partial);
         cudaError_t e = cudaSuccess;
         if (A_in == nullptr) {
-            e = launch_tables(g, b, wk.axis, (float2 *)wk.eps, nullptr, s);
+            e = launch_setup(g, b, wk.axis, (float2 *)wk.eps, nullptr, wk.state, wk.mu_acc, wk.barrier, nullptr,
+                             p->mu_G, s);
             if (e == cudaSuccess)
                 e = launch_solve_mu(g, b, wk.axis, wk.state, wk.mu_acc, wk.barrier, wk.status, nullptr, p->mu_G, s);
         }
@@ -751,7 +772,6 @@ extern "C" lindhard_status lindhard_sum_rule(lindhard_plan *p, int index, const 
         lindhard_status st = make_band(band, b);
         if (st != LINDHARD_OK) return st;
         if (b.band_kind == 1 && g.periodic) return fail(LINDHARD_EINVAL, "free electrons need zones > 1");
-        if (b.solve_mu && g.npz > 512) return fail(LINDHARD_EUNSUPPORTED, "the filling solve supports npz <= 512");
     }
     cudaStream_t s = (cudaStream_t)stream;
     Work<float> w = work_of<float>(p, index);
@@ -759,7 +779,7 @@ extern "C" lindhard_status lindhard_sum_rule(lindhard_plan *p, int index, const 
     double *D = (double *)w.X;
     cudaError_t e = cudaSuccess;
     if (A_in == nullptr) {
-        e = launch_tables(g, b, w.axis, (float2 *)w.eps, nullptr, s);
+        e = launch_setup(g, b, w.axis, (float2 *)w.eps, nullptr, w.state, w.mu_acc, w.barrier, nullptr, p->mu_G, s);
         if (e == cudaSuccess)
             e = launch_solve_mu(g, b, w.axis, w.state, w.mu_acc, w.barrier, w.status, nullptr, p->mu_G, s);
     }

@@ -1,6 +1,8 @@
-"""The autotuned plan (LINDHARD_PLAN_AUTOTUNE): both engine variants of the
-p_y passes agree with the FP64 oracle, whichever one a cache file pins, and a
-fresh tune writes its choices to the cache file named by LINDHARD_TUNE_CACHE.
+"""The autotuned plan (LINDHARD_PLAN_AUTOTUNE): every engine variant of the
+p_y passes (single-column, paired, paired with 12 values per thread) and of
+the product pass (default tile, 12 values per thread) agrees with the FP64
+oracle, whichever one a cache file pins, and a fresh tune writes its choices
+to the cache file named by LINDHARD_TUNE_CACHE.
 """
 import json
 import math
@@ -34,7 +36,7 @@ def _keys(grid, sizes):
     import torch
     base = (f"{torch.cuda.get_device_name(0)}|P={sizes.fft_p}|N={sizes.N}|PE={sizes.fft_e}"
             f"|Q={sizes.q_extent}")
-    return base + "|fwd_y", base + "|inv_y"
+    return base + "|fwd_y", base + "|inv_y", base + "|x_product"
 
 
 def _oracle_samples(grid, band, count=250):
@@ -50,13 +52,19 @@ def test_pinned_variants_match_oracle(lh, grid, tmp_path, monkeypatch):
     import torch
     band = wl.band_params(filling=1.1, gamma=0.06, ff_a=0.7)
     (lx, ly, m), ref = _oracle_samples(grid, band)
+    probe = lh.Plan([grid])
+    kf, ki, kx = _keys(grid, probe.sizes[0])
+    three_pow = probe.sizes[0].fft_p % 3 == 0
+    probe.close()
+    # (p_y variant, product variant): 0/1/2 = single-column, paired, paired
+    # with 12 values per thread; 3/4 = TMA-staged forms of 1/2.  Product:
+    # 0/1 = default and 12-value tiles, 2/3 = their TMA-staged forms.  The
+    # 12-value tiles exist for 3 * 2^k only.
+    combos = [(0, 0), (1, 0), (3, 2)] + ([(2, 1), (1, 1), (4, 3), (3, 3)] if three_pow else [])
     outs = []
-    for v in (0, 1):
-        probe = lh.Plan([grid])
-        kf, ki = _keys(grid, probe.sizes[0])
-        probe.close()
-        path = tmp_path / f"tune_{v}.json"
-        path.write_text(json.dumps({kf: v, ki: v}, indent=0))
+    for vy, vx in combos:
+        path = tmp_path / f"tune_{vy}{vx}.json"
+        path.write_text(json.dumps({kf: vy, ki: vy, kx: vx}, indent=0))
         monkeypatch.setenv("LINDHARD_TUNE_CACHE", str(path))
         plan = lh.Plan([grid], autotune=True)
         out = plan.imchi([band])
@@ -65,10 +73,11 @@ def test_pinned_variants_match_oracle(lh, grid, tmp_path, monkeypatch):
         got = out.reshape(s.q_extent, s.q_extent, s.n_omega).cpu().numpy().astype(np.float64)
         plan.close()
         err = np.abs(got[lx, ly, m] - ref).max() / np.abs(ref).max()
-        assert err <= TOL32, (v, err)
+        assert err <= TOL32, (vy, vx, err)
         outs.append(got)
-    # the two engines compute the same transforms: agreement well inside the bar
-    assert np.abs(outs[0] - outs[1]).max() <= TOL32 * np.abs(outs[1]).max()
+    # the engines compute the same transforms: agreement well inside the bar
+    for o in outs[1:]:
+        assert np.abs(o - outs[0]).max() <= TOL32 * np.abs(outs[0]).max()
     torch.cuda.synchronize()
 
 
@@ -81,10 +90,10 @@ def test_fresh_tune_writes_cache_and_matches_default(lh, tmp_path, monkeypatch):
     plan = lh.Plan([grid], autotune=True)
     out_t = plan.imchi([band])
     plan.status()
-    kf, ki = _keys(grid, plan.sizes[0])
+    kf, ki, kx = _keys(grid, plan.sizes[0])
     plan.close()
     entries = json.loads(path.read_text())
-    assert entries[kf] in (0, 1) and entries[ki] in (0, 1)
+    assert entries[kf] in range(5) and entries[ki] in range(5) and entries[kx] in range(4)
     base = lh.Plan([grid])
     out_d = base.imchi([band])
     base.status()
@@ -92,5 +101,30 @@ def test_fresh_tune_writes_cache_and_matches_default(lh, tmp_path, monkeypatch):
     mx = float(out_d.abs().max())
     assert mx > 0 and not math.isnan(mx)
     assert float((out_t - out_d).abs().max()) <= TOL32 * mx
+    del out_t, out_d
+    torch.cuda.empty_cache()
+
+
+def test_tma_variants_full_size_match_default(lh, tmp_path, monkeypatch):
+    """The TMA-staged persistent passes on the extended 256 x 256 x 256 grid
+    (P = 384, 256-row tiles, many tiles per CTA) against the default engines."""
+    import torch
+    w = wl.WORKLOADS["extended_256x256x256"]
+    grid, band = w["grid"], w["band"]
+    base = lh.Plan([grid])
+    out_d = base.imchi([band])
+    base.status()
+    kf, ki, kx = _keys(grid, base.sizes[0])
+    base.close()
+    mx = float(out_d.abs().max())
+    for vy, vx in [(3, 2), (4, 3)]:
+        path = tmp_path / f"tma_{vy}{vx}.json"
+        path.write_text(json.dumps({kf: vy, ki: vy, kx: vx}, indent=0))
+        monkeypatch.setenv("LINDHARD_TUNE_CACHE", str(path))
+        plan = lh.Plan([grid], autotune=True)
+        out_t = plan.imchi([band])
+        plan.status()
+        plan.close()
+        assert float((out_t - out_d).abs().max()) <= TOL32 * mx, (vy, vx)
     del out_t, out_d
     torch.cuda.empty_cache()
