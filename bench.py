@@ -32,9 +32,17 @@ sys.path.insert(0, ROOT)
 
 DEFAULT_WORKLOAD = "extended_256x256x256"
 FALLBACK_HBM_GBS = 6800.0
-PASS_FILES = {  # kernel source of each timed pass (for traffic-record staleness)
-    "energy_fwd": "k_forward.cu", "py_fwd": "k_forward.cu", "px_product": "k_product.cu",
-    "py_inv": "k_inverse.cu", "energy_inv": "k_inverse.cu",
+PASS_FILES = {  # kernel sources of each timed pass (for traffic-record staleness)
+    "energy_fwd": ("k_forward.cu",), "py_fwd": ("k_forward.cu", "k_tma.cu"),
+    "px_product": ("k_product.cu", "k_tma.cu"), "py_inv": ("k_inverse.cu", "k_tma.cu"),
+    "energy_inv": ("k_inverse.cu",),
+}
+# kernel of each pass by engine variant (lindhard_plan_variants)
+VARIANT_KERNELS = {
+    "py_fwd": ["k_fwd_y", "k_fwd_y2", "k_fwd_y2 (12-value tiles)", "k_fwd_y_tma", "k_fwd_y_tma (12-value tiles)"],
+    "py_inv": ["k_inv_y", "k_inv_y2", "k_inv_y2 (12-value tiles)", "k_inv_y_tma", "k_inv_y_tma (12-value tiles)"],
+    "px_product": ["k_x_product", "k_x_product (12-value tiles)", "k_x_product_tma",
+                   "k_x_product_tma (12-value tiles)"],
 }
 KERNEL_NAMES = {"batch": "all passes of all instances (graph)", "energy_fwd": "k_fwd_energy", "py_fwd": "k_fwd_y", "px_product": "k_x_product",
                 "py_inv": "k_inv_y", "energy_inv": "k_inv_energy", "tables": "k_setup", "mu_solve": "k_mu_sect, k_mu_halley"}
@@ -81,11 +89,11 @@ def measured_peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def source_digest(fname):
-    """Hash of a pass's kernel source together with the headers every kernel
+def source_digest(fnames):
+    """Hash of a pass's kernel sources together with the headers every kernel
     includes (FFT engine, tile configurations, shared types)."""
     h = hashlib.sha256()
-    for f in (fname, "fft_engine.cuh", "kernels.cuh", "lindhard_internal.h"):
+    for f in tuple(fnames) + ("fft_engine.cuh", "kernels.cuh", "lindhard_internal.h"):
         with open(os.path.join(ROOT, "paper_1208_3210_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -324,7 +332,8 @@ def main():
     step_ms = ms_total / args.steps
     peak, peak_kind = measured_peaks()
     # kernels launched in the timed region: each step is one forward call
-    launches = sum(int(plan.sizes[i].kernels_forward) for i in range(len(grids))) * args.steps
+    launches = sum(int(plan.sizes[i].kernels_forward) + (1 if bands[i]["gamma"] < 0.02 else 0)
+                   for i in range(len(grids))) * args.steps
     if batched:
         # concurrent instances: no per-pass split, the batch as one unit
         pipeline_bytes = sum(sum(pass_bytes(plan.sizes[i]).values()) for i in range(len(grids)))
@@ -339,6 +348,8 @@ def main():
         achieved = pb[dom] / (dom_ms * 1e-3) / 1e9
         traffic = None if args.grid else recorded_traffic(dom, args.workload)
         pipeline_bytes = sum(pb.values())
+    variants = plan.variants(0) if not batched else {}
+    dom_kernel = (VARIANT_KERNELS[dom][variants[dom]] if dom in VARIANT_KERNELS else KERNEL_NAMES[dom])
 
     if rank == 0:
         line = {
@@ -352,8 +363,9 @@ def main():
                        "l2": "no flush: each step streams {:.2f} GB of intermediates through HBM, "
                              "far above the 129 MB L2".format(pipeline_bytes / 1e9),
                        "autotune": not args.no_autotune,
+                       "variants": variants,
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-            "roofline": {"bound": "hbm", "kernel": KERNEL_NAMES[dom], "achieved": achieved, "peak": peak,
+            "roofline": {"bound": "hbm", "kernel": dom_kernel, "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
                          "traffic": traffic, "algorithmic_bytes": pb[dom], "launch_ms": dom_ms,
                          "pipeline_frac": pipeline_bytes / (step_ms * 1e-3) / 1e9 / peak},

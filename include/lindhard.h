@@ -106,7 +106,9 @@ typedef struct {
     long long out_elems;    /* q_extent^2 * n_omega                           */
     long long a_elems;      /* N^2 * n_eps (layout of A_in and dA)           */
     long long hbm_bytes_forward;  /* algorithmic HBM bytes of one forward call */
-    long long kernels_forward;    /* kernel launches of one forward call (A generated, mu solved) */
+    long long kernels_forward;    /* kernel launches of one forward call with A generated and mu
+                                     solved: one more when gamma < 0.02 eV (a third multisection
+                                     pass); three fewer with a caller-supplied A               */
 } lindhard_sizes;
 
 /* Plan flag: also allocate the buffers of lindhard_imchi_backward (one more
@@ -223,6 +225,15 @@ lindhard_status lindhard_plan_pass_times(lindhard_plan *plan, double *ms, long l
 lindhard_status lindhard_sum_rule(lindhard_plan *plan, int index, const lindhard_band *band,
                                   const float *A_in, const float *out, double *sum_q, double *dos_corr,
                                   void *stream);
+
+/* Engine variants the plan runs for instance `index` (set by
+ * LINDHARD_PLAN_AUTOTUNE, else the defaults): out[0], out[1] = forward and
+ * inverse passes along p_y (0 single-column engine, 1 paired columns,
+ * 2 paired columns with 12 values per thread, 3 and 4 the TMA-staged
+ * persistent forms of 1 and 2); out[2] = the p_x product pass (0 default
+ * tile, 1 tile with 12 values per thread, 2 and 3 their TMA-staged forms).
+ * out: host, int[3]. */
+lindhard_status lindhard_plan_variants(const lindhard_plan *plan, int index, int *out);
 
 /* Synchronises `stream` and returns the first device-side error recorded by
  * the plan since the last call (LINDHARD_OK if none), then clears it. */

@@ -494,7 +494,7 @@ extern "C" lindhard_status lindhard_plan_sizes(const lindhard_plan *p, int index
     long long W3 = (long long)g.Q * g.P * g.H;
     long long W4 = (long long)g.Q * g.Q * g.H;
     out->hbm_bytes_forward = 2 * (W1 + W2 + W3 + W4) * cb + out->out_elems * rb;
-    out->kernels_forward = 9;   // set-up (tables + multisection pass 0), 3 chemical-potential launches, 5 FFT passes
+    out->kernels_forward = 8;   // set-up (tables + multisection pass 0), multisection pass 1, Halley step, 5 FFT passes
     return LINDHARD_OK;
 }
 
@@ -803,6 +803,16 @@ extern "C" lindhard_status lindhard_plan_pass_times(lindhard_plan *p, double *ms
     if (!p || !ms || !launches) return fail(LINDHARD_EINVAL, "plan/ms/launches must be non-NULL");
     drain_events(p);
     for (int i = 0; i < LINDHARD_NUM_PASSES; ++i) { ms[i] = p->pass_ms[i]; launches[i] = p->pass_n[i]; }
+    return LINDHARD_OK;
+}
+
+extern "C" lindhard_status lindhard_plan_variants(const lindhard_plan *p, int index, int *out)
+{
+    if (!p || !out) return fail(LINDHARD_EINVAL, "plan and out must be non-NULL");
+    if (index < 0 || index >= p->batch) return fail(LINDHARD_EINVAL, "index out of range");
+    out[0] = p->yvar_fwd[index];
+    out[1] = p->yvar_inv[index];
+    out[2] = p->xvar[index];
     return LINDHARD_OK;
 }
 

@@ -24,8 +24,8 @@ _STATUS_NAMES = {OK: "OK", EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", E
 # Exported symbols, in the order include/lindhard.h declares them.
 SYMBOLS = ("lindhard_plan_create", "lindhard_plan_sizes", "lindhard_plan_workspace_bytes", "lindhard_imchi",
            "lindhard_imchi_f64", "lindhard_imchi_backward", "lindhard_plan_profile", "lindhard_plan_pass_times",
-           "lindhard_sum_rule", "lindhard_plan_status", "lindhard_plan_destroy", "lindhard_imchi_noalloc",
-           "lindhard_last_error")
+           "lindhard_sum_rule", "lindhard_plan_variants", "lindhard_plan_status", "lindhard_plan_destroy",
+           "lindhard_imchi_noalloc", "lindhard_last_error")
 NOALLOC_SCRATCH_BYTES = 32 << 20
 NUM_PASSES = 7
 PASS_NAMES = ("tables", "mu_solve", "energy_fwd", "py_fwd", "px_product", "py_inv", "energy_inv")
@@ -76,6 +76,7 @@ def load(path: str = LIB_PATH):
         lib.lindhard_plan_profile.argtypes = [vp, ctypes.c_int]
         lib.lindhard_plan_pass_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]
         lib.lindhard_plan_status.argtypes = [vp, vp]
+        lib.lindhard_plan_variants.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
         lib.lindhard_plan_destroy.argtypes = [vp]
         lib.lindhard_plan_destroy.restype = None
         lib.lindhard_last_error.restype = ctypes.c_char_p
@@ -229,6 +230,12 @@ class Plan:
 
     def status(self, stream=None):
         _check(load().lindhard_plan_status(self._h, _stream(stream)))
+
+    def variants(self, index=0):
+        """Engine variants of instance `index`: {"py_fwd", "py_inv", "px_product"}."""
+        v = (ctypes.c_int * 3)()
+        _check(load().lindhard_plan_variants(self._h, index, v))
+        return {"py_fwd": v[0], "py_inv": v[1], "px_product": v[2]}
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
