@@ -39,8 +39,10 @@ PASS_FILES = {  # kernel sources of each timed pass (for traffic-record stalenes
 }
 # kernel of each pass by engine variant (lindhard_plan_variants)
 VARIANT_KERNELS = {
-    "py_fwd": ["k_fwd_y", "k_fwd_y2", "k_fwd_y2 (12-value tiles)", "k_fwd_y_tma", "k_fwd_y_tma (12-value tiles)"],
-    "py_inv": ["k_inv_y", "k_inv_y2", "k_inv_y2 (12-value tiles)", "k_inv_y_tma", "k_inv_y_tma (12-value tiles)"],
+    "py_fwd": ["k_fwd_y", "k_fwd_y2", "k_fwd_y2 (12-value tiles)", "k_fwd_y_tma", "k_fwd_y_tma (12-value tiles)",
+               "k_y_col_tma (forward)"],
+    "py_inv": ["k_inv_y", "k_inv_y2", "k_inv_y2 (12-value tiles)", "k_inv_y_tma", "k_inv_y_tma (12-value tiles)",
+               "k_y_col_tma (inverse)"],
     "px_product": ["k_x_product", "k_x_product (12-value tiles)", "k_x_product_tma",
                    "k_x_product_tma (12-value tiles)"],
 }

@@ -229,8 +229,8 @@ lindhard_status lindhard_sum_rule(lindhard_plan *plan, int index, const lindhard
 /* Engine variants the plan runs for instance `index` (set by
  * LINDHARD_PLAN_AUTOTUNE, else the defaults): out[0], out[1] = forward and
  * inverse passes along p_y (0 single-column engine, 1 paired columns,
- * 2 paired columns with 12 values per thread, 3 and 4 the TMA-staged
- * persistent forms of 1 and 2); out[2] = the p_x product pass (0 default
+ * 2 paired columns with 12 values per thread, 3, 4 and 5 the TMA-staged
+ * persistent forms of 1, 2 and 0); out[2] = the p_x product pass (0 default
  * tile, 1 tile with 12 values per thread, 2 and 3 their TMA-staged forms).
  * out: host, int[3]. */
 lindhard_status lindhard_plan_variants(const lindhard_plan *plan, int index, int *out);

@@ -346,7 +346,14 @@ struct FftPair {
     static constexpr int NS = fft_nstages(L, F);
     static constexpr int R0 = fft_radix(L, 0, INV, F);
     static constexpr int RL = fft_radix(L, NS - 1, INV, F);
-    static constexpr int SMEM_ELEMS = (L + L / R0) * C;   // one empty row after every R0 rows
+    // Rows of C complex values.  With at least 8 pairs per row every 16-byte
+    // access phase of a warp (8 threads) lies in one 128-byte row segment, so
+    // rows are stored back to back (addresses linear in the row: no per-value
+    // index arithmetic); narrower tiles get one empty row after every R0 rows
+    // so that the first exchange's writes (rows R0 apart) fall into different
+    // banks.
+    static constexpr bool LIN = CP >= 8;
+    static constexpr int SMEM_ELEMS = LIN ? L * C : (L + L / R0) * C;
     static_assert(C % 2 == 0 && T % CP == 0 && (CP * L) % T == 0, "tile must split evenly over threads");
     static_assert(fft_radices_divide(L, VPT, F), "values per thread must be a multiple of every radix");
     static_assert(fft_sched_len(L, F) == L, "radix schedule must multiply to L");
@@ -364,7 +371,7 @@ struct FftPair {
         return (threadIdx.x + b * T) / CP + r * (L / RL);
     }
 
-    __device__ __forceinline__ static int srow(int row) { return (row + row / R0) * C; }
+    __device__ __forceinline__ static int srow(int row) { return LIN ? row * C : (row + row / R0) * C; }
     __device__ __forceinline__ static void st2(Cx *sm, int row, int p, Cx a, Cx b)
     {
         if constexpr (sizeof(Real) == 4) {

@@ -342,6 +342,97 @@ k_x_product_tma(Geom g, const __grid_constant__ CUtensorMap map, float2 *__restr
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// Single-column forms of the two p_y passes (ColCfg tiles, 8-byte values):
+// each thread transforms one column; same staging and pipeline as above.
+template <int L, bool INV>
+struct ColTmaBounds {
+    using E = Fft<float, L, ColCfg<L>::C, ColCfg<L>::T, MAP_COL, INV>;
+    static constexpr int MINB =
+        tma_minb(ColCfg<L>::MINB, tma_rows_est(L, INV) * ColCfg<L>::C * 8 + (long long)E::SMEM_ELEMS * 8 + 16);
+};
+
+template <int L, bool INV>
+__global__ void __launch_bounds__(ColCfg<L>::T, (ColTmaBounds<L, INV>::MINB))
+k_y_col_tma(Geom g, const __grid_constant__ CUtensorMap map, float2 *__restrict__ out,
+            const float2 *__restrict__ tw, unsigned *status, int box_rows)
+{
+    constexpr int C = ColCfg<L>::C, T = ColCfg<L>::T;
+    using E = Fft<float, L, C, T, MAP_COL, INV>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int rows = INV ? L : g.N;   // input rows per column
+    const int nbox = (rows + box_rows - 1) / box_rows, NR = nbox * box_rows;
+    const TmaSmem lay{(size_t)NR * C * sizeof(float2), (size_t)E::SMEM_ELEMS * sizeof(float2)};
+    if (dyn_smem_bytes() < lay.total()) return;
+    float2 *stage = reinterpret_cast<float2 *>(smem_raw);
+    float2 *sm = reinterpret_cast<float2 *>(smem_raw + lay.stage_bytes);
+    unsigned long long *bar = reinterpret_cast<unsigned long long *>(smem_raw + lay.stage_bytes + lay.fft_bytes);
+
+    // forward: columns of U1 rows (2 SP wide), planes i_x; inverse: columns
+    // [0, H) of U3 rows (SP wide), planes l_x
+    const int W = INV ? g.SP : 2 * g.SP;
+    const int tiles_x = INV ? (g.H + C - 1) / C : (W + C - 1) / C;
+    const int ntiles = tiles_x * (INV ? g.Q : g.N);
+    const unsigned tx = (unsigned)(nbox * box_rows * C * sizeof(float2));
+    auto issue = [&](int t) {
+        const int pl = t / tiles_x, c0 = (t % tiles_x) * C;
+        mbar_expect_tx(bar, tx);
+        for (int q = 0; q < nbox; ++q) tma_load_3d(stage + (size_t)q * box_rows * C, &map, 2 * c0, q * box_rows, pl, bar);
+    };
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        if ((int)blockIdx.x < ntiles) issue(blockIdx.x);
+    }
+    __syncthreads();
+    unsigned parity = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int pl = t / tiles_x, c0 = (t % tiles_x) * C;
+        if (!tile_ready(bar, parity, status)) { drain(bar, parity); return; }
+        parity ^= 1u;
+        float2 v[E::VPT];
+#pragma unroll
+        for (int b = 0; b < E::VPT / E::R0; ++b)
+#pragma unroll
+            for (int r = 0; r < E::R0; ++r) {
+                int col, n;
+                E::first_elem(b, r, col, n);
+                v[b * E::R0 + r] = n < rows ? stage[(size_t)n * C + col] : make_float2(0.f, 0.f);
+            }
+        __syncthreads();
+        if (threadIdx.x == 0 && t + (int)gridDim.x < ntiles) {
+            fence_proxy_async();
+            issue(t + gridDim.x);
+        }
+        E::run(v, sm, tw);
+        const int c = c0 + (int)(threadIdx.x % C);
+        if (INV) {
+            if (c < g.H) {
+                float2 *dst = out + (long long)pl * g.Q * g.SP + c;
+#pragma unroll
+                for (int b = 0; b < E::VPT / E::RL; ++b)
+#pragma unroll
+                    for (int r = 0; r < E::RL; ++r) {
+                        int col, n;
+                        E::last_elem(b, r, col, n);
+                        const int l = lag_index(n, g.P, g.Q);
+                        if (l >= 0) dst[(long long)l * g.SP] = v[b * E::RL + r];
+                    }
+            }
+        } else if (c < W && (c % g.SP) < g.H) {
+            float2 *dst = out + (long long)pl * g.xs2 + c;
+#pragma unroll
+            for (int b = 0; b < E::VPT / E::RL; ++b)
+#pragma unroll
+                for (int r = 0; r < E::RL; ++r) {
+                    int col, n;
+                    E::last_elem(b, r, col, n);
+                    dst[(long long)n * W] = v[b * E::RL + r];
+                }
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Host side.
 
@@ -462,13 +553,46 @@ static cudaError_t launch_x_product_tma_t(const Geom &g, const Work<float> &w, c
     return cudaGetLastError();
 }
 
-// Entry points.  p_y passes: variant 3 = PairCfg tiles, 4 = PairCfg12 tiles;
+
+template <int L, bool INV>
+static cudaError_t launch_y_col_tma_t(const Geom &g, const Work<float> &w, cudaStream_t s)
+{
+    constexpr int C = ColCfg<L>::C, T = ColCfg<L>::T;
+    using E = Fft<float, L, C, T, MAP_COL, INV>;
+    const int rows = INV ? L : g.N;
+    const int box_rows = tma_box_rows(rows), nbox = (rows + box_rows - 1) / box_rows;
+    const TmaSmem lay{(size_t)nbox * box_rows * C * sizeof(float2), (size_t)E::SMEM_ELEMS * sizeof(float2)};
+    auto k = k_y_col_tma<L, INV>;
+    cudaError_t e = smem_attrs(k, lay.total());
+    CUtensorMap map;
+    int ntiles = 0;
+    if (e == cudaSuccess) {
+        if (INV) {
+            e = make_map(&map, w.X, 2ull * g.SP, (unsigned long long)g.P, (unsigned long long)g.Q, 8ull * g.SP,
+                         8ull * (unsigned long long)g.xs3, 2 * C, box_rows, 1);
+            ntiles = ((g.H + C - 1) / C) * g.Q;
+        } else {
+            e = make_map(&map, w.X, 4ull * g.SP, (unsigned long long)g.N, (unsigned long long)g.N, 16ull * g.SP,
+                         16ull * g.SP * g.N, 2 * C, box_rows, 1);
+            ntiles = ((2 * g.SP + C - 1) / C) * g.N;
+        }
+    }
+    int grid = 0;
+    if (e == cudaSuccess) e = persistent_grid(k, T, lay.total(), ntiles, grid);
+    if (e != cudaSuccess) return e;
+    k<<<grid, T, lay.total(), s>>>(g, map, (float2 *)w.Y, twiddles_for<float>(w, L), w.status, box_rows);
+    return cudaGetLastError();
+}
+
+// Entry points.  p_y passes: variant 3 = PairCfg tiles, 4 = PairCfg12 tiles,
+// 5 = single-column ColCfg tiles;
 // product pass: variant 2 = XCfg tiles, 3 = XCfg12 tiles.  Lengths >= 128.
 template <int L>
 static cudaError_t fwd_y_tma(const Geom &g, const Work<float> &w, cudaStream_t s, int variant)
 {
     if constexpr (L >= 128) {
         if (variant == 3) return launch_fwd_y_tma_t<L, PairCfg<L>>(g, w, s);
+        if (variant == 5) return launch_y_col_tma_t<L, false>(g, w, s);
         if constexpr (fft_has_family1(L))
             if (variant == 4) return launch_fwd_y_tma_t<L, PairCfg12<L>>(g, w, s);
     }
@@ -479,6 +603,7 @@ static cudaError_t inv_y_tma(const Geom &g, const Work<float> &w, cudaStream_t s
 {
     if constexpr (L >= 128) {
         if (variant == 3) return launch_inv_y_tma_t<L, PairCfg<L>>(g, w, s);
+        if (variant == 5) return launch_y_col_tma_t<L, true>(g, w, s);
         if constexpr (fft_has_family1(L))
             if (variant == 4) return launch_inv_y_tma_t<L, PairCfg12<L>>(g, w, s);
     }
