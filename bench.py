@@ -44,7 +44,7 @@ VARIANT_KERNELS = {
     "py_inv": ["k_inv_y", "k_inv_y2", "k_inv_y2 (12-value tiles)", "k_inv_y_tma", "k_inv_y_tma (12-value tiles)",
                "k_y_col_tma (inverse)"],
     "px_product": ["k_x_product", "k_x_product (12-value tiles)", "k_x_product_tma",
-                   "k_x_product_tma (12-value tiles)"],
+                   "k_x_product_tma (12-value tiles)", "k_x_product (one more CTA per SM)"],
 }
 KERNEL_NAMES = {"batch": "all passes of all instances (graph)", "energy_fwd": "k_fwd_energy", "py_fwd": "k_fwd_y", "px_product": "k_x_product",
                 "py_inv": "k_inv_y", "energy_inv": "k_inv_energy", "tables": "k_setup", "mu_solve": "k_mu_sect, k_mu_halley"}

@@ -92,12 +92,15 @@ cudaError_t launch_x_product_c(const Geom &g, const Work<Real> &w, cudaStream_t 
     return cudaGetLastError();
 }
 
-// variant 0: the tiles of XCfg; 1: 12 values per thread (3 * 2^k >= 192, FP32)
+// variant 0: the tiles of XCfg; 1: 12 values per thread (3 * 2^k >= 192,
+// FP32); 4: XCfg tiles with one more CTA per SM (FP32, L >= 128)
 template <typename Real, int L>
 cudaError_t launch_x_product_t(const Geom &g, const Work<Real> &w, cudaStream_t s, int variant)
 {
     if constexpr (sizeof(Real) == 4 && fft_has_family1(L))
         if (variant == 1) return launch_x_product_c<Real, L, XCfg12<L>>(g, w, s);
+    if constexpr (sizeof(Real) == 4 && L >= 128)
+        if (variant == 4) return launch_x_product_c<Real, L, XCfgHi<L>>(g, w, s);
     return launch_x_product_c<Real, L, XCfg<L>>(g, w, s);
 }
 
@@ -105,7 +108,7 @@ cudaError_t launch_x_product_tma(const Geom &g, const Work<float> &w, cudaStream
 // variants 2, 3: the TMA-staged persistent kernels of k_tma.cu
 cudaError_t launch_x_product(const Geom &g, const Work<float> &w, cudaStream_t s, int variant)
 {
-    if (variant >= 2) return launch_x_product_tma(g, w, s, variant);
+    if (variant == 2 || variant == 3) return launch_x_product_tma(g, w, s, variant);
 #define CALL(L) launch_x_product_t<float, L>(g, w, s, variant)
     LH_P_SWITCH(g.P, CALL)
 #undef CALL

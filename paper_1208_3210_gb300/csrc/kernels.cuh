@@ -58,6 +58,9 @@ template <> struct PairCfg12<192>  { static constexpr int C = 16, T = 128, MINB 
 template <> struct PairCfg12<384>  { static constexpr int C = 16, T = 256, MINB = 2; };
 template <> struct PairCfg12<768>  { static constexpr int C = 16, T = 512, MINB = 1; };
 template <> struct PairCfg12<1536> { static constexpr int C = 8, T = 512, MINB = 1; };
+// Product pass, default tile with one more CTA per SM (registers capped
+// accordingly; the autotuner weighs the spills against the extra warps).
+template <int L> struct XCfgHi { static constexpr int C = XCfg<L>::C, T = XCfg<L>::T, MINB = XCfg<L>::MINB + 1; };
 // Product pass: VPT = C L / T = 12.
 template <int L> struct XCfg12;
 template <> struct XCfg12<192>  { static constexpr int C = 8, T = 128, MINB = 4; };

@@ -114,7 +114,8 @@ struct lindhard_plan {
     // (LINDHARD_PLAN_AUTOTUNE): p_y passes 0 single-column, 1 paired-column,
     // 2 paired-column with 12 values per thread, 3, 4 and 5 the TMA-staged
     // persistent forms of 1, 2 and 0; product pass 0 default tile, 1 tile with
-    // 12 values per thread, 2 and 3 their TMA-staged persistent forms
+    // 12 values per thread, 2 and 3 their TMA-staged persistent forms, 4 the
+    // default tile with one more CTA per SM
     std::vector<int> yvar_fwd, yvar_inv, xvar;
     bool concurrent = false;     // LINDHARD_PLAN_CONCURRENT
     bool graph = false;          // LINDHARD_PLAN_GRAPH
@@ -316,7 +317,7 @@ static cudaError_t autotune(lindhard_plan *p)
         key << prop.name << "|P=" << g.P << "|N=" << g.N << "|PE=" << g.PE << "|Q=" << g.Q;
         const std::string kf = key.str() + "|fwd_y", ki = key.str() + "|inv_y", kx = key.str() + "|x_product";
         const bool f1 = fft_has_family1(g.P);
-        std::vector<int> vy = {0, 1, 3, 5}, vx = {0, 2};
+        std::vector<int> vy = {0, 1, 3, 5}, vx = {0, 2, 4};
         if (f1) {
             vy.push_back(2);
             vy.push_back(4);

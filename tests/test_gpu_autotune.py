@@ -60,7 +60,7 @@ def test_pinned_variants_match_oracle(lh, grid, tmp_path, monkeypatch):
     # with 12 values per thread; 3/4 = TMA-staged forms of 1/2.  Product:
     # 0/1 = default and 12-value tiles, 2/3 = their TMA-staged forms.  The
     # 12-value tiles exist for 3 * 2^k only.
-    combos = [(0, 0), (1, 0), (3, 2), (5, 0)] + ([(2, 1), (1, 1), (4, 3), (3, 3)] if three_pow else [])
+    combos = [(0, 0), (1, 0), (3, 2), (5, 4)] + ([(2, 1), (1, 1), (4, 3), (3, 3)] if three_pow else [])
     outs = []
     for vy, vx in combos:
         path = tmp_path / f"tune_{vy}{vx}.json"
@@ -93,7 +93,7 @@ def test_fresh_tune_writes_cache_and_matches_default(lh, tmp_path, monkeypatch):
     kf, ki, kx = _keys(grid, plan.sizes[0])
     plan.close()
     entries = json.loads(path.read_text())
-    assert entries[kf] in range(6) and entries[ki] in range(6) and entries[kx] in range(4)
+    assert entries[kf] in range(6) and entries[ki] in range(6) and entries[kx] in range(5)
     base = lh.Plan([grid])
     out_d = base.imchi([band])
     base.status()
