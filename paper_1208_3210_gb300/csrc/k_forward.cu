@@ -35,22 +35,43 @@ k_fwd_energy(Geom g, Band band, const AxisTab *__restrict__ axis,
     const long long line0 = (long long)blockIdx.x * C;
 
     if (A_in == nullptr && threadIdx.x < C) {
-        // band energy and |M|^2 of this line's momentum point, in FP64
+        // band energy xi_p = e0(p) - mu and |M(p)|^2 gamma / pi of this line's
+        // momentum point (Eqs. 4-5)
         long long line = line0 + threadIdx.x;
         if (line < nlines) {
             int ix = (int)(line / g.N), iy = (int)(line % g.N);
-            AxisTab ax = axis[ix], ay = axis[iy];
-            double e0;
-            if (band.band_kind == 1)
-                e0 = 0.5 * (ax.p2 + ay.p2);
-            else
-                e0 = -2.0 * band.t * (ax.c1 + ay.c1) - 4.0 * band.tp * ax.c1 * ay.c1
-                     - 2.0 * band.tpp * (ax.c2 + ay.c2);
-            double xi = e0 - st->mu;
-            double amp = ax.g * ay.g * band.gamma / 3.14159265358979323846;  // |M|^2 gamma / pi
-            s_xhi[threadIdx.x] = (Real)xi;
-            s_xlo[threadIdx.x] = (Real)(xi - (double)(Real)xi);
-            s_amp[threadIdx.x] = (Real)amp;
+            const AxisTab &ax = axis[ix], &ay = axis[iy];
+            if constexpr (sizeof(Real) == 4) {
+                // double-float (about 1e-14 eV): a chain of FP32 operations of a
+                // few cycles each, where FP64 operations cost about 60 here and
+                // hold the CTA at the barrier below
+                F2 e0;
+                if (band.band_kind == 1) {
+                    e0 = f2_add(F2{ax.p2h, ax.p2l}, F2{ay.p2h, ay.p2l});
+                    e0.h *= 0.5f;   // exact
+                    e0.l *= 0.5f;
+                } else {
+                    const F2 cx{ax.c1h, ax.c1l}, cy{ay.c1h, ay.c1l};
+                    e0 = f2_add(f2_add(f2_mul(F2{band.k1[0], band.k1[1]}, f2_add(cx, cy)),
+                                       f2_mul(F2{band.k2[0], band.k2[1]}, f2_mul(cx, cy))),
+                                f2_mul(F2{band.k3[0], band.k3[1]}, f2_add(F2{ax.c2h, ax.c2l}, F2{ay.c2h, ay.c2l})));
+                }
+                const F2 xi = f2_add(e0, F2{-st->mu_hi, -st->mu_lo});
+                s_xhi[threadIdx.x] = xi.h;
+                s_xlo[threadIdx.x] = xi.l;
+                s_amp[threadIdx.x] = ax.gf * ay.gf * band.gam_pi;
+            } else {
+                double e0;
+                if (band.band_kind == 1)
+                    e0 = 0.5 * (ax.p2 + ay.p2);
+                else
+                    e0 = -2.0 * band.t * (ax.c1 + ay.c1) - 4.0 * band.tp * ax.c1 * ay.c1
+                         - 2.0 * band.tpp * (ax.c2 + ay.c2);
+                double xi = e0 - st->mu;
+                s_xhi[threadIdx.x] = (Real)xi;
+                s_xlo[threadIdx.x] = (Real)(xi - (double)(Real)xi);
+                s_amp[threadIdx.x] = (Real)(ax.g * ay.g * band.gamma / 3.14159265358979323846);
+            }
         }
     }
     __syncthreads();

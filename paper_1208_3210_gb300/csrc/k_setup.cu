@@ -268,7 +268,7 @@ k_setup(Geom g, Band band, AxisTab *axis, float2 *eps32, double *eps64, InstStat
     if ((int)blockIdx.x >= G) {
         const int tb = blockIdx.x - G;
         if (!band.solve_mu && tb == 0 && threadIdx.x == 0) {
-            st->mu = band.mu;
+            set_mu(st, band.mu);
             st->last_step = 0.0;
             if (mu_out) *mu_out = band.mu;
         }
@@ -282,9 +282,13 @@ k_setup(Geom g, Band band, AxisTab *axis, float2 *eps32, double *eps64, InstStat
             a.c2 = cospi(2.0 * u);
             a.g = (band.ff_a == 0.0) ? 1.0 : exp(-p * p * band.ff_a * band.ff_a / 8.0);
             a.p2 = p * p;
-            a.c1f = (float)a.c1;
-            a.c2f = (float)a.c2;
-            a.p2f = (float)a.p2;
+            a.c1h = (float)a.c1;
+            a.c1l = (float)(a.c1 - (double)a.c1h);
+            a.c2h = (float)a.c2;
+            a.c2l = (float)(a.c2 - (double)a.c2h);
+            a.p2h = (float)a.p2;
+            a.p2l = (float)(a.p2 - (double)a.p2h);
+            a.gf = (float)a.g;
             a.pad = 0.f;
             axis[i] = a;
         }
@@ -351,7 +355,7 @@ k_mu_halley(Geom g, Band band, const AxisTab *__restrict__ axis, InstState *st, 
     if (sh.br.flag) {   // the filling was not bracketed
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             atomicCAS(status, (unsigned)DEV_OK, (unsigned)DEV_ENOCONV);
-            st->mu = mu;
+            set_mu(st, mu);
             st->last_step = INFINITY;
             if (mu_out) *mu_out = mu;
         }
@@ -419,7 +423,7 @@ k_mu_halley(Geom g, Band band, const AxisTab *__restrict__ axis, InstState *st, 
         const double d1 = F1 * igam, d2 = F2 * igam * igam;  // dn/dmu, d2n/dmu2
         const double step = 2.0 * d * d1 / (2.0 * d1 * d1 - d * d2);
         const double mu_new = mu - step;
-        st->mu = mu_new;
+        set_mu(st, mu_new);
         st->last_step = fabs(step);
         if (mu_out) *mu_out = mu_new;
         // the root lies within the last bracket up to FP32 noise (below

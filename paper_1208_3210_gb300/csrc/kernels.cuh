@@ -104,6 +104,30 @@ __host__ __device__ inline const cx<Real> *twiddles_for(const Work<Real> &w, int
 // memory when it is short, so a launch configured with too little shared
 // memory gives wrong results (caught by the tests) instead of an
 // out-of-bounds access.
+// Unevaluated FP32 pairs hi + lo (double-float arithmetic, Dekker 1971):
+// error-free sums (Knuth's TwoSum), FMA-based error-free products, and their
+// renormalisation.  Explicitly rounded intrinsics keep the compiler from
+// contracting the additions into FMAs, which would break the error terms.
+struct F2 { float h, l; };
+__device__ __forceinline__ F2 f2_fast(float a, float b)   // |a| >= |b|
+{
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ F2 f2_add(F2 a, F2 b)
+{
+    const float s = __fadd_rn(a.h, b.h), bb = __fsub_rn(s, a.h);
+    const float e = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, bb)), __fsub_rn(b.h, bb));
+    return f2_fast(s, __fadd_rn(e, __fadd_rn(a.l, b.l)));
+}
+__device__ __forceinline__ F2 f2_mul(F2 a, F2 b)
+{
+    const float p = __fmul_rn(a.h, b.h);
+    float e = __fmaf_rn(a.h, b.h, -p);
+    e = __fmaf_rn(a.h, b.l, __fmaf_rn(a.l, b.h, e));
+    return f2_fast(p, e);
+}
+
 // Dynamic shared-memory limit of a kernel.  (The L1/shared carveout is left
 // to the driver: pinning it to the largest shared share slowed the FFT passes,
 // which read twiddles through L1, by 10-20%.)

@@ -33,13 +33,27 @@ struct Band {
     double t, tp, tpp, mu, filling, gamma, ff_a;
     int band_kind;
     int solve_mu;   // 1: mu from filling
+    // FP32 forms for the energy pass: -2t, -4t', -2t'' as unevaluated
+    // (hi, lo) pairs, and gamma / pi
+    float k1[2], k2[2], k3[2], gam_pi;
 };
 
 // Device-side per-instance state written by the set-up kernels.
 struct InstState {
     double mu;          // chemical potential used
     double last_step;   // size of the last Newton correction (convergence check)
+    float mu_hi, mu_lo; // mu as an unevaluated FP32 pair
+    float pad[2];
 };
+
+// mu into the state, with its FP32 (hi, lo) pair.
+__host__ __device__ inline void set_mu(InstState *st, double mu)
+{
+    st->mu = mu;
+    const float h = (float)mu;
+    st->mu_hi = h;
+    st->mu_lo = (float)(mu - (double)h);
+}
 
 // Status word codes recorded on the device.
 enum { DEV_OK = 0, DEV_ENOCONV = 1, DEV_ETIMEOUT = 2 };
@@ -50,7 +64,8 @@ struct AxisTab {
     double c2;   // cos(2 p_i)
     double g;    // exp(-p_i^2 ff_a^2 / 8), so |M(p)|^2 = g(px) g(py)
     double p2;   // p_i^2
-    float c1f, c2f, p2f, pad;   // the same rounded to FP32 (for FP32-only uses)
+    // the same as unevaluated FP32 pairs hi + lo (hi = fl(x)), and g in FP32
+    float c1h, c1l, c2h, c2l, p2h, p2l, gf, pad;
 };
 
 // Workspace of one instance (device pointers into the plan's allocation).

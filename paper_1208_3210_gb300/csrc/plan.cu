@@ -524,6 +524,14 @@ static lindhard_status make_band(const lindhard_band *b, Band &o)
     o.ff_a = b->ff_a;
     o.band_kind = b->band_kind;
     o.solve_mu = isnan(b->filling) ? 0 : 1;
+    auto pair = [](double x, float *out) {
+        out[0] = (float)x;
+        out[1] = (float)(x - (double)out[0]);
+    };
+    pair(-2.0 * b->t, o.k1);
+    pair(-4.0 * b->tp, o.k2);
+    pair(-2.0 * b->tpp, o.k3);
+    o.gam_pi = (float)(b->gamma / M_PI);
     if (o.solve_mu) {
         if (!(b->filling > 0 && b->filling < 2)) return fail(LINDHARD_EINVAL, "filling must be in (0, 2) or NaN");
     } else if (!isfinite(b->mu)) {
