@@ -35,7 +35,7 @@ FALLBACK_HBM_GBS = 6800.0
 PASS_FILES = {  # kernel sources of each timed pass (for traffic-record staleness)
     "energy_fwd": ("k_forward.cu",), "py_fwd": ("k_forward.cu", "k_tma.cu"),
     "px_product": ("k_product.cu", "k_tma.cu"), "py_inv": ("k_inverse.cu", "k_tma.cu"),
-    "energy_inv": ("k_inverse.cu",),
+    "energy_inv": ("k_inverse.cu", "k_tma.cu"),
 }
 # kernel of each pass by engine variant (lindhard_plan_variants)
 VARIANT_KERNELS = {
@@ -45,6 +45,7 @@ VARIANT_KERNELS = {
                "k_y_col_tma (inverse)"],
     "px_product": ["k_x_product", "k_x_product (12-value tiles)", "k_x_product_tma",
                    "k_x_product_tma (12-value tiles)", "k_x_product (one more CTA per SM)"],
+    "energy_inv": ["k_inv_energy", "k_inv_energy_tma"],
 }
 KERNEL_NAMES = {"batch": "all passes of all instances (graph)", "energy_fwd": "k_fwd_energy", "py_fwd": "k_fwd_y", "px_product": "k_x_product",
                 "py_inv": "k_inv_y", "energy_inv": "k_inv_energy", "tables": "k_setup", "mu_solve": "k_mu_sect, k_mu_halley"}
@@ -351,6 +352,35 @@ def main():
         traffic = None if args.grid else recorded_traffic(dom, args.workload)
         pipeline_bytes = sum(pb.values())
     variants = plan.variants(0) if not batched else {}
+    plain = None
+    if batched:
+        # the same instances one after another on one stream, no graph: the
+        # plain form the batched graph call is compared with (outside the
+        # timed region above)
+        seq = lh.Plan(grids, autotune=not args.no_autotune)
+        seq_out = torch.empty(seq.out_elems(), dtype=torch.float32, device="cuda")
+        for _ in range(3):
+            seq.imchi(bands, out=seq_out, mu_out=mu)
+        seq.status()
+        seq_steps = max(3, min(args.steps, 20))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(seq_steps):
+            seq.imchi(bands, out=seq_out, mu_out=mu)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        seq.status()
+        seq_ms = e0.elapsed_time(e1) / seq_steps
+        # the two forms compute the same outputs
+        seq.imchi(bands, out=seq_out, mu_out=mu)
+        plan.imchi(bands, out=out, mu_out=mu)
+        torch.cuda.synchronize()
+        diff = float((seq_out - out).abs().max() / out.abs().max().clamp_min(1e-30))
+        seq.close()
+        del seq_out
+        plain = {"ms_per_step": seq_ms, "value": outputs_per_step / world / (seq_ms * 1e-3),
+                 "speedup_batched": seq_ms / step_ms, "max_rel_diff": diff}
     dom_kernel = (VARIANT_KERNELS[dom][variants[dom]] if dom in VARIANT_KERNELS else KERNEL_NAMES[dom])
 
     if rank == 0:
@@ -377,6 +407,8 @@ def main():
                     "d2h_bytes_per_step": 4 * plan.out_elems(), "steps": e2e_steps},
             "gpu_launches": launches,
         }
+        if plain is not None:
+            line["plain_sequential"] = plain
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.workload)
         print(json.dumps(line), flush=True)

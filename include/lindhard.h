@@ -232,8 +232,9 @@ lindhard_status lindhard_sum_rule(lindhard_plan *plan, int index, const lindhard
  * 2 paired columns with 12 values per thread, 3, 4 and 5 the TMA-staged
  * persistent forms of 1, 2 and 0); out[2] = the p_x product pass (0 default
  * tile, 1 tile with 12 values per thread, 2 and 3 their TMA-staged forms,
- * 4 the default tile with one more CTA per SM).
- * out: host, int[3]. */
+ * 4 the default tile with one more CTA per SM); out[3] = the inverse energy
+ * pass (0 default, 1 TMA-staged persistent form).
+ * out: host, int[4]. */
 lindhard_status lindhard_plan_variants(const lindhard_plan *plan, int index, int *out);
 
 /* Synchronises `stream` and returns the first device-side error recorded by

@@ -213,14 +213,18 @@ cudaError_t launch_inv_y(const Geom &g, const Work<double> &w, cudaStream_t s, i
     LH_LEN_SWITCH_SMALL(g.P, CALL)
 #undef CALL
 }
-cudaError_t launch_inv_energy(const Geom &g, const Work<float> &w, float *out, cudaStream_t s)
+cudaError_t launch_inv_energy_tma(const Geom &g, const Work<float> &w, float *out, cudaStream_t s);
+// variant 1: the TMA-staged persistent kernel of k_tma.cu
+cudaError_t launch_inv_energy(const Geom &g, const Work<float> &w, float *out, cudaStream_t s, int variant)
 {
+    if (variant == 1) return launch_inv_energy_tma(g, w, out, s);
 #define CALL(L) launch_inv_energy_t<float, float, L>(g, w, out, s)
     LH_LEN_SWITCH(g.PE, CALL)
 #undef CALL
 }
-cudaError_t launch_inv_energy(const Geom &g, const Work<double> &w, double *out, cudaStream_t s)
+cudaError_t launch_inv_energy(const Geom &g, const Work<double> &w, double *out, cudaStream_t s, int variant)
 {
+    (void)variant;
 #define CALL(L) launch_inv_energy_t<double, double, L>(g, w, out, s)
     LH_LEN_SWITCH_SMALL(g.PE, CALL)
 #undef CALL

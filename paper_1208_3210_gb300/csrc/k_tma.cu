@@ -460,6 +460,81 @@ k_y_col_tma(Geom g, const __grid_constant__ CUtensorMap map, float2 *__restrict_
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// Inverse energy pass (same transform as k_inv_energy): U4 [Q^2][SP] rows ->
+// out [Q^2][n_omega].  Tile = C pairs of rows (2 C rows), staged as nbx
+// boxes of bx columns: [nbx][2 C][bx] complex.
+template <int L>
+__global__ void __launch_bounds__(LineCfg<L>::T)
+k_inv_energy_tma(Geom g, const __grid_constant__ CUtensorMap map, float *__restrict__ out,
+                 const float2 *__restrict__ tw, unsigned *status, int bx, int nbx)
+{
+    constexpr int C = LineCfg<L>::C, T = LineCfg<L>::T;
+    using E = Fft<float, L, C, T, MAP_LINE, true>;
+    constexpr int H = L / 2 + 1;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const TmaSmem lay{(size_t)nbx * 2 * C * bx * sizeof(float2), (size_t)E::SMEM_ELEMS * sizeof(float2)};
+    if (dyn_smem_bytes() < lay.total()) return;
+    float2 *stage = reinterpret_cast<float2 *>(smem_raw);
+    float2 *sm = reinterpret_cast<float2 *>(smem_raw + lay.stage_bytes);
+    unsigned long long *bar = reinterpret_cast<unsigned long long *>(smem_raw + lay.stage_bytes + lay.fft_bytes);
+
+    const long long npairs = (long long)g.Q * g.Q / 2;
+    const int ntiles = (int)((npairs + C - 1) / C);
+    const unsigned tx = (unsigned)(nbx * 2 * C * bx * sizeof(float2));
+    const TileRun run(ntiles, false);
+    auto issue = [&](int t) {
+        mbar_expect_tx(bar, tx);
+        for (int q = 0; q < nbx; ++q) tma_load_3d(stage + (size_t)q * 2 * C * bx, &map, 2 * q * bx, 2 * t * C, 0, bar);
+    };
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        if (run.t < run.end) issue(run.t);
+    }
+    __syncthreads();
+    // element m of staged row rr
+    auto at = [&](int rr, int m) { const int q = m / bx; return stage[((size_t)q * 2 * C + rr) * bx + (m - q * bx)]; };
+    unsigned parity = 0;
+    const float sc = (float)g.scale;
+    for (int t = run.t; t < run.end; t += run.step) {
+        const long long f0 = (long long)t * C;
+        if (!tile_ready(bar, parity, status)) { drain(bar, parity); return; }
+        parity ^= 1u;
+        float2 v[E::VPT];
+#pragma unroll
+        for (int b = 0; b < E::VPT / E::R0; ++b)
+#pragma unroll
+            for (int r = 0; r < E::R0; ++r) {
+                int col, n;
+                E::first_elem(b, r, col, n);
+                float2 x1, x2;
+                if (n < H) { x1 = at(2 * col, n); x2 = at(2 * col + 1, n); }
+                else { x1 = cconj(at(2 * col, L - n)); x2 = cconj(at(2 * col + 1, L - n)); }
+                v[b * E::R0 + r] = make_float2(x1.x - x2.y, x1.y + x2.x);   // X1 + i X2
+            }
+        __syncthreads();
+        if (threadIdx.x == 0 && t + run.step < run.end) {
+            fence_proxy_async();
+            issue(t + run.step);
+        }
+        E::run(v, sm, tw);
+#pragma unroll
+        for (int b = 0; b < E::VPT / E::RL; ++b)
+#pragma unroll
+            for (int r = 0; r < E::RL; ++r) {
+                int col, n;
+                E::last_elem(b, r, col, n);
+                const long long f = f0 + col;
+                if (f < npairs && n < g.n_omega) {
+                    const float2 w = v[b * E::RL + r];
+                    out[(2 * f) * g.n_omega + n] = sc * w.x;
+                    out[(2 * f + 1) * g.n_omega + n] = sc * w.y;
+                }
+            }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Host side.
 
@@ -609,6 +684,47 @@ static cudaError_t launch_y_col_tma_t(const Geom &g, const Work<float> &w, cudaS
     if (e != cudaSuccess) return e;
     k<<<grid, T, lay.total(), s>>>(g, map, (float2 *)w.Y, twiddles_for<float>(w, L), w.status, box_rows);
     return cudaGetLastError();
+}
+
+
+// Columns per box for rows of SP complex values: at most 128 (256 floats, the
+// TMA box limit), dividing SP evenly into an even count.
+static bool energy_boxes(int SP, int &bx, int &nbx)
+{
+    for (nbx = (2 * SP + 255) / 256; nbx <= SP; ++nbx)
+        if (SP % nbx == 0 && (SP / nbx) % 2 == 0 && 2 * (SP / nbx) <= 256) {
+            bx = SP / nbx;
+            return true;
+        }
+    return false;
+}
+
+template <int L>
+static cudaError_t launch_inv_energy_tma_t(const Geom &g, const Work<float> &w, float *out, cudaStream_t s)
+{
+    constexpr int C = LineCfg<L>::C, T = LineCfg<L>::T;
+    using E = Fft<float, L, C, T, MAP_LINE, true>;
+    int bx = 0, nbx = 0;
+    if (!energy_boxes(g.SP, bx, nbx)) return cudaErrorNotSupported;
+    const TmaSmem lay{(size_t)nbx * 2 * C * bx * sizeof(float2), (size_t)E::SMEM_ELEMS * sizeof(float2)};
+    auto k = k_inv_energy_tma<L>;
+    cudaError_t e = smem_attrs(k, lay.total());
+    CUtensorMap map;
+    const unsigned long long rows = (unsigned long long)g.Q * g.Q;
+    if (e == cudaSuccess) e = make_map(&map, w.Y, 2ull * g.SP, rows, 1ull, 8ull * g.SP, 8ull * g.SP * rows, 2 * bx, 2 * C, 1);
+    int grid = 0;
+    const int ntiles = (int)(((long long)g.Q * g.Q / 2 + C - 1) / C);
+    if (e == cudaSuccess) e = persistent_grid(k, T, lay.total(), ntiles, grid);
+    if (e != cudaSuccess) return e;
+    k<<<grid, T, lay.total(), s>>>(g, map, out, twiddles_for<float>(w, L), w.status, bx, nbx);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_inv_energy_tma(const Geom &g, const Work<float> &w, float *out, cudaStream_t s)
+{
+#define CALL(L) launch_inv_energy_tma_t<L>(g, w, out, s)
+    LH_LEN_SWITCH(g.PE, CALL)
+#undef CALL
 }
 
 // Entry points.  p_y passes: variant 3 = PairCfg tiles, 4 = PairCfg12 tiles,

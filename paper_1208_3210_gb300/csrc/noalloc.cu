@@ -39,7 +39,7 @@ cudaError_t launch_fwd_energy(const Geom &g, const Band &band, const Work<float>
 cudaError_t launch_fwd_y(const Geom &g, const Work<float> &w, cudaStream_t s, int variant);
 cudaError_t launch_x_product(const Geom &g, const Work<float> &w, cudaStream_t s, int variant);
 cudaError_t launch_inv_y(const Geom &g, const Work<float> &w, cudaStream_t s, int variant);
-cudaError_t launch_inv_energy(const Geom &g, const Work<float> &w, float *out, cudaStream_t s);
+cudaError_t launch_inv_energy(const Geom &g, const Work<float> &w, float *out, cudaStream_t s, int variant);
 }  // namespace lh
 
 using namespace lh;
@@ -155,7 +155,7 @@ extern "C" lindhard_status lindhard_imchi_noalloc(const lindhard_grid *grid, con
     if (e == cudaSuccess) e = launch_fwd_y(g, w, s, 1);
     if (e == cudaSuccess) e = launch_x_product(g, w, s, 0);
     if (e == cudaSuccess) e = launch_inv_y(g, w, s, 1);
-    if (e == cudaSuccess) e = launch_inv_energy(g, w, out, s);
+    if (e == cudaSuccess) e = launch_inv_energy(g, w, out, s, 0);
     if (e != cudaSuccess) return set_error(LINDHARD_ECUDA, cudaGetErrorString(e));
     return LINDHARD_OK;
 }

@@ -38,8 +38,8 @@ cudaError_t launch_x_product(const Geom &g, const Work<float> &w, cudaStream_t s
 cudaError_t launch_x_product(const Geom &g, const Work<double> &w, cudaStream_t s, int variant);
 cudaError_t launch_inv_y(const Geom &g, const Work<float> &w, cudaStream_t s, int variant);
 cudaError_t launch_inv_y(const Geom &g, const Work<double> &w, cudaStream_t s, int variant);
-cudaError_t launch_inv_energy(const Geom &g, const Work<float> &w, float *out, cudaStream_t s);
-cudaError_t launch_inv_energy(const Geom &g, const Work<double> &w, double *out, cudaStream_t s);
+cudaError_t launch_inv_energy(const Geom &g, const Work<float> &w, float *out, cudaStream_t s, int variant);
+cudaError_t launch_inv_energy(const Geom &g, const Work<double> &w, double *out, cudaStream_t s, int variant);
 cudaError_t launch_w_energy(const Geom &g, const float *w, float2 *WU1, const float2 *tw, int tw_len,
                             cudaStream_t s);
 cudaError_t launch_w_y(const Geom &g, const float2 *WU1, float2 *WU2, const float2 *tw, int tw_len, cudaStream_t s);
@@ -117,6 +117,8 @@ struct lindhard_plan {
     // 12 values per thread, 2 and 3 their TMA-staged persistent forms, 4 the
     // default tile with one more CTA per SM
     std::vector<int> yvar_fwd, yvar_inv, xvar;
+    // inverse energy pass: 0 default, 1 TMA-staged persistent form
+    std::vector<int> evar;
     bool concurrent = false;     // LINDHARD_PLAN_CONCURRENT
     bool graph = false;          // LINDHARD_PLAN_GRAPH
     // concurrent execution: instances on plan-owned streams, forked from and
@@ -315,7 +317,8 @@ static cudaError_t autotune(lindhard_plan *p)
         if (p->precision[i] != LINDHARD_FP32 || g.P < 128) continue;
         std::ostringstream key;
         key << prop.name << "|P=" << g.P << "|N=" << g.N << "|PE=" << g.PE << "|Q=" << g.Q;
-        const std::string kf = key.str() + "|fwd_y", ki = key.str() + "|inv_y", kx = key.str() + "|x_product";
+        const std::string kf = key.str() + "|fwd_y", ki = key.str() + "|inv_y", kx = key.str() + "|x_product",
+                          ke = key.str() + "|inv_energy";
         const bool f1 = fft_has_family1(g.P);
         std::vector<int> vy = {0, 1, 3, 5}, vx = {0, 2, 4};
         if (f1) {
@@ -346,6 +349,9 @@ static cudaError_t autotune(lindhard_plan *p)
         p->yvar_fwd[i] = pick(kf, vy, [&](int v) { return launch_fwd_y(g, w, 0, v); });
         p->yvar_inv[i] = pick(ki, vy, [&](int v) { return launch_inv_y(g, w, 0, v); });
         p->xvar[i] = pick(kx, vx, [&](int v) { return launch_x_product(g, w, 0, v); });
+        // the inverse energy pass writes the caller's output: time it into the
+        // workspace's X buffer (at least as large as the output)
+        p->evar[i] = pick(ke, {0, 1}, [&](int v) { return launch_inv_energy(g, w, (float *)w.X, 0, v); });
         e = cudaGetLastError();
     }
     cudaEventDestroy(a);
@@ -465,6 +471,7 @@ extern "C" lindhard_status lindhard_plan_create(const lindhard_grid *grids, int 
     p->yvar_fwd.assign(batch, 1);
     p->yvar_inv.assign(batch, 1);
     p->xvar.assign(batch, 0);
+    p->evar.assign(batch, 0);
     if (e == cudaSuccess && (flags & LINDHARD_PLAN_AUTOTUNE)) e = autotune(p);
     if (e != cudaSuccess) {
         lindhard_plan_destroy(p);
@@ -624,7 +631,7 @@ static cudaError_t enqueue_forward(lindhard_plan *p, const std::vector<Band> &bs
         if (e == cudaSuccess) e = timed(p, 3, s, [&] { return launch_fwd_y(g, w, s, p->yvar_fwd[i]); });
         if (e == cudaSuccess) e = timed(p, 4, s, [&] { return launch_x_product(g, w, s, p->xvar[i]); });
         if (e == cudaSuccess) e = timed(p, 5, s, [&] { return launch_inv_y(g, w, s, p->yvar_inv[i]); });
-        if (e == cudaSuccess) e = timed(p, 6, s, [&] { return launch_inv_energy(g, w, o_i, s); });
+        if (e == cudaSuccess) e = timed(p, 6, s, [&] { return launch_inv_energy(g, w, o_i, s, p->evar[i]); });
         a_off += (size_t)g.N * g.N * g.n_eps;
         o_off += (size_t)g.Q * g.Q * g.n_omega;
     }
@@ -822,6 +829,7 @@ extern "C" lindhard_status lindhard_plan_variants(const lindhard_plan *p, int in
     out[0] = p->yvar_fwd[index];
     out[1] = p->yvar_inv[index];
     out[2] = p->xvar[index];
+    out[3] = p->evar[index];
     return LINDHARD_OK;
 }
 

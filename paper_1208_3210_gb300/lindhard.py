@@ -232,10 +232,10 @@ class Plan:
         _check(load().lindhard_plan_status(self._h, _stream(stream)))
 
     def variants(self, index=0):
-        """Engine variants of instance `index`: {"py_fwd", "py_inv", "px_product"}."""
-        v = (ctypes.c_int * 3)()
+        """Engine variants of instance `index`: {"py_fwd", "py_inv", "px_product", "energy_inv"}."""
+        v = (ctypes.c_int * 4)()
         _check(load().lindhard_plan_variants(self._h, index, v))
-        return {"py_fwd": v[0], "py_inv": v[1], "px_product": v[2]}
+        return {"py_fwd": v[0], "py_inv": v[1], "px_product": v[2], "energy_inv": v[3]}
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

@@ -36,7 +36,7 @@ def _keys(grid, sizes):
     import torch
     base = (f"{torch.cuda.get_device_name(0)}|P={sizes.fft_p}|N={sizes.N}|PE={sizes.fft_e}"
             f"|Q={sizes.q_extent}")
-    return base + "|fwd_y", base + "|inv_y", base + "|x_product"
+    return base + "|fwd_y", base + "|inv_y", base + "|x_product", base + "|inv_energy"
 
 
 def _oracle_samples(grid, band, count=250):
@@ -53,7 +53,7 @@ def test_pinned_variants_match_oracle(lh, grid, tmp_path, monkeypatch):
     band = wl.band_params(filling=1.1, gamma=0.06, ff_a=0.7)
     (lx, ly, m), ref = _oracle_samples(grid, band)
     probe = lh.Plan([grid])
-    kf, ki, kx = _keys(grid, probe.sizes[0])
+    kf, ki, kx, ke = _keys(grid, probe.sizes[0])
     three_pow = probe.sizes[0].fft_p % 3 == 0
     probe.close()
     # (p_y variant, product variant): 0/1/2 = single-column, paired, paired
@@ -62,9 +62,10 @@ def test_pinned_variants_match_oracle(lh, grid, tmp_path, monkeypatch):
     # 12-value tiles exist for 3 * 2^k only.
     combos = [(0, 0), (1, 0), (3, 2), (5, 4)] + ([(2, 1), (1, 1), (4, 3), (3, 3)] if three_pow else [])
     outs = []
-    for vy, vx in combos:
+    for j, (vy, vx) in enumerate(combos):
+        ve = j % 2   # inverse energy pass: default and TMA-staged forms in turn
         path = tmp_path / f"tune_{vy}{vx}.json"
-        path.write_text(json.dumps({kf: vy, ki: vy, kx: vx}, indent=0))
+        path.write_text(json.dumps({kf: vy, ki: vy, kx: vx, ke: ve}, indent=0))
         monkeypatch.setenv("LINDHARD_TUNE_CACHE", str(path))
         plan = lh.Plan([grid], autotune=True)
         out = plan.imchi([band])
@@ -73,7 +74,7 @@ def test_pinned_variants_match_oracle(lh, grid, tmp_path, monkeypatch):
         got = out.reshape(s.q_extent, s.q_extent, s.n_omega).cpu().numpy().astype(np.float64)
         plan.close()
         err = np.abs(got[lx, ly, m] - ref).max() / np.abs(ref).max()
-        assert err <= TOL32, (vy, vx, err)
+        assert err <= TOL32, (vy, vx, ve, err)
         outs.append(got)
     # the engines compute the same transforms: agreement well inside the bar
     for o in outs[1:]:
@@ -90,10 +91,10 @@ def test_fresh_tune_writes_cache_and_matches_default(lh, tmp_path, monkeypatch):
     plan = lh.Plan([grid], autotune=True)
     out_t = plan.imchi([band])
     plan.status()
-    kf, ki, kx = _keys(grid, plan.sizes[0])
+    kf, ki, kx, ke = _keys(grid, plan.sizes[0])
     plan.close()
     entries = json.loads(path.read_text())
-    assert entries[kf] in range(6) and entries[ki] in range(6) and entries[kx] in range(5)
+    assert entries[kf] in range(6) and entries[ki] in range(6) and entries[kx] in range(5) and entries[ke] in (0, 1)
     base = lh.Plan([grid])
     out_d = base.imchi([band])
     base.status()
@@ -114,17 +115,17 @@ def test_tma_variants_full_size_match_default(lh, tmp_path, monkeypatch):
     base = lh.Plan([grid])
     out_d = base.imchi([band])
     base.status()
-    kf, ki, kx = _keys(grid, base.sizes[0])
+    kf, ki, kx, ke = _keys(grid, base.sizes[0])
     base.close()
     mx = float(out_d.abs().max())
-    for vy, vx in [(3, 2), (4, 3), (5, 2)]:
+    for vy, vx, ve in [(3, 2, 1), (4, 3, 0), (5, 2, 1)]:
         path = tmp_path / f"tma_{vy}{vx}.json"
-        path.write_text(json.dumps({kf: vy, ki: vy, kx: vx}, indent=0))
+        path.write_text(json.dumps({kf: vy, ki: vy, kx: vx, ke: ve}, indent=0))
         monkeypatch.setenv("LINDHARD_TUNE_CACHE", str(path))
         plan = lh.Plan([grid], autotune=True)
         out_t = plan.imchi([band])
         plan.status()
         plan.close()
-        assert float((out_t - out_d).abs().max()) <= TOL32 * mx, (vy, vx)
+        assert float((out_t - out_d).abs().max()) <= TOL32 * mx, (vy, vx, ve)
     del out_t, out_d
     torch.cuda.empty_cache()
