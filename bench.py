@@ -40,11 +40,12 @@ PASS_FILES = {  # kernel sources of each timed pass (for traffic-record stalenes
 # kernel of each pass by engine variant (lindhard_plan_variants)
 VARIANT_KERNELS = {
     "py_fwd": ["k_fwd_y", "k_fwd_y2", "k_fwd_y2 (12-value tiles)", "k_fwd_y_tma", "k_fwd_y_tma (12-value tiles)",
-               "k_y_col_tma (forward)"],
+               "k_y_col_tma (forward)", "k_fwd_y2 (double-width tile)"],
     "py_inv": ["k_inv_y", "k_inv_y2", "k_inv_y2 (12-value tiles)", "k_inv_y_tma", "k_inv_y_tma (12-value tiles)",
-               "k_y_col_tma (inverse)"],
+               "k_y_col_tma (inverse)", "k_inv_y2 (double-width tile)"],
     "px_product": ["k_x_product", "k_x_product (12-value tiles)", "k_x_product_tma",
-                   "k_x_product_tma (12-value tiles)", "k_x_product (one more CTA per SM)"],
+                   "k_x_product_tma (12-value tiles)", "k_x_product (one more CTA per SM)",
+                   "k_x_product (double-width tile)"],
     "energy_inv": ["k_inv_energy", "k_inv_energy_tma"],
 }
 KERNEL_NAMES = {"batch": "all passes of all instances (graph)", "energy_fwd": "k_fwd_energy", "py_fwd": "k_fwd_y", "px_product": "k_x_product",

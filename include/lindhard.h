@@ -230,9 +230,11 @@ lindhard_status lindhard_sum_rule(lindhard_plan *plan, int index, const lindhard
  * LINDHARD_PLAN_AUTOTUNE, else the defaults): out[0], out[1] = forward and
  * inverse passes along p_y (0 single-column engine, 1 paired columns,
  * 2 paired columns with 12 values per thread, 3, 4 and 5 the TMA-staged
- * persistent forms of 1, 2 and 0); out[2] = the p_x product pass (0 default
+ * persistent forms of 1, 2 and 0, 6 paired columns on double-width tiles);
+ * out[2] = the p_x product pass (0 default
  * tile, 1 tile with 12 values per thread, 2 and 3 their TMA-staged forms,
- * 4 the default tile with one more CTA per SM); out[3] = the inverse energy
+ * 4 the default tile with one more CTA per SM, 5 the default tile twice as
+ * wide); out[3] = the inverse energy
  * pass (0 default, 1 TMA-staged persistent form).
  * out: host, int[4]. */
 lindhard_status lindhard_plan_variants(const lindhard_plan *plan, int index, int *out);

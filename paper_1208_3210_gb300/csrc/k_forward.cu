@@ -264,7 +264,8 @@ cudaError_t launch_fwd_y2_t(const Geom &g, const Work<Real> &w, cudaStream_t s)
 }
 
 // variant 0: single-column engine; 1: paired-column engine (L >= 128, FP32);
-// 2: paired-column engine with 12 values per thread (3 * 2^k >= 192, FP32)
+// 2: paired-column engine with 12 values per thread (3 * 2^k >= 192, FP32);
+// 6: paired-column engine on tiles twice as wide (L >= 384, FP32)
 template <typename Real, int L>
 cudaError_t launch_fwd_y_t(const Geom &g, const Work<Real> &w, cudaStream_t s, int variant)
 {
@@ -272,6 +273,8 @@ cudaError_t launch_fwd_y_t(const Geom &g, const Work<Real> &w, cudaStream_t s, i
         if (variant == 1) return launch_fwd_y2_t<Real, L, PairCfg<L>>(g, w, s);
         if constexpr (fft_has_family1(L))
             if (variant == 2) return launch_fwd_y2_t<Real, L, PairCfg12<L>>(g, w, s);
+        if constexpr (L >= 384 && PairCfg<L>::T <= 512)
+            if (variant == 6) return launch_fwd_y2_t<Real, L, PairCfgW<L>>(g, w, s);
     }
     constexpr int C = ColCfg<L>::C, T = ColCfg<L>::T;
     using E = Fft<Real, L, C, T, MAP_COL, false>;
@@ -302,7 +305,7 @@ cudaError_t launch_fwd_y_tma(const Geom &g, const Work<float> &w, cudaStream_t s
 // variants 3, 4: the TMA-staged persistent kernels of k_tma.cu
 cudaError_t launch_fwd_y(const Geom &g, const Work<float> &w, cudaStream_t s, int variant)
 {
-    if (variant >= 3) return launch_fwd_y_tma(g, w, s, variant);
+    if (variant >= 3 && variant <= 5) return launch_fwd_y_tma(g, w, s, variant);
 #define CALL(L) launch_fwd_y_t<float, L>(g, w, s, variant)
     LH_P_SWITCH(g.P, CALL)
 #undef CALL

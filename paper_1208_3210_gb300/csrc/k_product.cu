@@ -93,7 +93,8 @@ cudaError_t launch_x_product_c(const Geom &g, const Work<Real> &w, cudaStream_t 
 }
 
 // variant 0: the tiles of XCfg; 1: 12 values per thread (3 * 2^k >= 192,
-// FP32); 4: XCfg tiles with one more CTA per SM (FP32, L >= 128)
+// FP32); 4: XCfg tiles with one more CTA per SM (FP32, L >= 128); 5: XCfg
+// tiles twice as wide (FP32, L >= 384)
 template <typename Real, int L>
 cudaError_t launch_x_product_t(const Geom &g, const Work<Real> &w, cudaStream_t s, int variant)
 {
@@ -101,6 +102,8 @@ cudaError_t launch_x_product_t(const Geom &g, const Work<Real> &w, cudaStream_t 
         if (variant == 1) return launch_x_product_c<Real, L, XCfg12<L>>(g, w, s);
     if constexpr (sizeof(Real) == 4 && L >= 128)
         if (variant == 4) return launch_x_product_c<Real, L, XCfgHi<L>>(g, w, s);
+    if constexpr (sizeof(Real) == 4 && L >= 384 && XCfg<L>::T <= 256)
+        if (variant == 5) return launch_x_product_c<Real, L, XCfgW<L>>(g, w, s);
     return launch_x_product_c<Real, L, XCfg<L>>(g, w, s);
 }
 

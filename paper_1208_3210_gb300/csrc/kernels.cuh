@@ -49,6 +49,10 @@ template <> struct PairCfg<384>  { static constexpr int C = 32, T = 256, MINB = 
 template <> struct PairCfg<768>  { static constexpr int C = 16, T = 256, MINB = 2; };
 template <> struct PairCfg<1536> { static constexpr int C = 8, T = 256, MINB = 2; };
 
+// Paired p_y tiles twice as wide (twice the columns and threads, one CTA per
+// SM): 128-byte row segments at 1536.
+template <int L> struct PairCfgW { static constexpr int C = 2 * PairCfg<L>::C, T = 2 * PairCfg<L>::T, MINB = 1; };
+
 // Tiles with 12 values per thread per column (radix family 1) at the 3 * 2^k
 // lengths from 192: half the registers of the 24-value tiles above (so no
 // spills and up to twice the warps per SM), one or two more exchanges.
@@ -61,6 +65,9 @@ template <> struct PairCfg12<1536> { static constexpr int C = 8, T = 512, MINB =
 // Product pass, default tile with one more CTA per SM (registers capped
 // accordingly; the autotuner weighs the spills against the extra warps).
 template <int L> struct XCfgHi { static constexpr int C = XCfg<L>::C, T = XCfg<L>::T, MINB = XCfg<L>::MINB + 1; };
+// Product pass, default tile twice as wide (twice the columns and threads,
+// one CTA per SM): longer contiguous row segments on the strided planes.
+template <int L> struct XCfgW { static constexpr int C = 2 * XCfg<L>::C, T = 2 * XCfg<L>::T, MINB = 1; };
 // Product pass: VPT = C L / T = 12.
 template <int L> struct XCfg12;
 template <> struct XCfg12<192>  { static constexpr int C = 8, T = 128, MINB = 4; };

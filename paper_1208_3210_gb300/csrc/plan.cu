@@ -113,9 +113,10 @@ struct lindhard_plan {
     // engine variants per instance, set by the autotuner
     // (LINDHARD_PLAN_AUTOTUNE): p_y passes 0 single-column, 1 paired-column,
     // 2 paired-column with 12 values per thread, 3, 4 and 5 the TMA-staged
-    // persistent forms of 1, 2 and 0; product pass 0 default tile, 1 tile with
+    // persistent forms of 1, 2 and 0, 6 paired columns on double-width tiles;
+    // product pass 0 default tile, 1 tile with
     // 12 values per thread, 2 and 3 their TMA-staged persistent forms, 4 the
-    // default tile with one more CTA per SM
+    // default tile with one more CTA per SM, 5 the default tile twice as wide
     std::vector<int> yvar_fwd, yvar_inv, xvar;
     // inverse energy pass: 0 default, 1 TMA-staged persistent form
     std::vector<int> evar;
@@ -321,6 +322,10 @@ static cudaError_t autotune(lindhard_plan *p)
                           ke = key.str() + "|inv_energy";
         const bool f1 = fft_has_family1(g.P);
         std::vector<int> vy = {0, 1, 3, 5}, vx = {0, 2, 4};
+        if (g.P >= 384) {
+            vx.push_back(5);
+            vy.push_back(6);
+        }
         if (f1) {
             vy.push_back(2);
             vy.push_back(4);
