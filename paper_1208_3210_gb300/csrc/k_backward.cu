@@ -17,8 +17,8 @@
 //   k_bw_product    : FFT along p_x of W^, a^, b^; h^ = W^ a^, g^ = conj(W^) b^;
 //                     inverse along p_x, keep p_x < N.  Written over U2 in
 //                     place (each CTA reads its column tile fully before it
-//                     writes it): G3 [N][P][2][SP] = (h^, g^).
-//   k_bw_inv_y      : inverse along p_y, keep p_y < N.         G4 [N][N][2][SP]
+//                     writes it): G3 [N][P][SP][2] = (h^, g^) interleaved.
+//   k_bw_inv_y      : inverse along p_y, keep p_y < N.         G4 [N][N][SP][2]
 //   k_bw_inv_energy : inverse real FFT along energy of g and h together
 //                     (g + i h), dL/dA = scale * (Re on occupied cells, Im on
 //                     empty ones); optionally the chain rule through Eqs. 4-5
@@ -139,8 +139,8 @@ k_bw_product(Geom g, cx<Real> *__restrict__ U2, const cx<Real> *__restrict__ WU2
     const int c = blockIdx.x * C + (int)(threadIdx.x % C);
     const bool valid = c < g.H;
     const long long rstride = g.xs2;
-    Cx *colA = U2 + (long long)ky * W2 + c;        // a^ column, later h^
-    Cx *colB = colA + g.SP;                         // b^ column, later g^
+    Cx *colA = U2 + (long long)ky * W2 + 2 * c;    // a^ column, later h^
+    Cx *colB = colA + 1;                            // b^ column, later g^ (interleaved)
     const Cx *colW = WU2 + (long long)ky * g.SP + c;
     const long long wstride = g.xs3;
     const Cx zero = mk<Cx>((Real)0, (Real)0);
@@ -209,7 +209,7 @@ k_bw_inv_y(Geom g, const cx<Real> *__restrict__ G3, cx<Real> *__restrict__ G4, c
     const int W2 = 2 * g.SP;
     const int px = blockIdx.y;
     const int c = blockIdx.x * C + (int)(threadIdx.x % C);
-    const bool valid = c < W2 && (c % g.SP) < g.H;
+    const bool valid = c < W2 && ab_col_valid(c, g.H);
     const Cx *src = G3 + (long long)px * g.xs2 + c;
     Cx *dst = G4 + (long long)px * g.N * W2 + c;
     Cx v[E::VPT];
@@ -289,11 +289,10 @@ k_bw_inv_energy(Geom g, Band band, const AxisTab *__restrict__ axis,
             long long line = line0 + col;
             Cx x = mk<Cx>((Real)0, (Real)0);
             if (line < nlines) {
-                const Cx *rowh = G4 + line * (2LL * SP);   // h^ half spectrum
-                const Cx *rowg = rowh + SP;                // g^ half spectrum
+                const Cx *row = G4 + line * (2LL * SP);    // (h^, g^) interleaved
                 Cx xg, xh;
-                if (n < H) { xg = rowg[n]; xh = rowh[n]; }
-                else { xg = cconj(rowg[L - n]); xh = cconj(rowh[L - n]); }
+                if (n < H) { xh = row[2 * n]; xg = row[2 * n + 1]; }
+                else { xh = cconj(row[2 * (L - n)]); xg = cconj(row[2 * (L - n) + 1]); }
                 x = mk<Cx>(xg.x - xh.y, xg.y + xh.x);      // g^ + i h^
             }
             v[b * E::R0 + r] = x;

@@ -15,7 +15,7 @@ namespace lh {
 
 // ---------------------------------------------------------------------------
 // Energy pass.  One CTA = C momentum points (lines), output U1 layout
-// [N*N lines][2][SP] complex: row 0 = a^, row 1 = b^.
+// [N*N lines][SP][2] complex: (a^(k), b^(k)) interleaved.
 template <typename Real, int L>
 __global__ void __launch_bounds__(LineCfg<L>::T)
 k_fwd_energy(Geom g, Band band, const AxisTab *__restrict__ axis,
@@ -140,9 +140,9 @@ k_fwd_energy(Geom g, Band band, const AxisTab *__restrict__ axis,
         Cx a0, b0, a1, b1;
         sep(col, k, a0, b0);
         sep(col, k + 1, a1, b1);   // k + 1 = H lands in the row's padding
-        Cx *row = U1 + line * (2LL * SP);
-        gst2(row + k, a0, a1);
-        gst2(row + SP + k, b0, b1);
+        Cx *row = U1 + line * (2LL * SP) + 2 * k;
+        gst2(row, a0, b0);
+        gst2(row + 2, a1, b1);
     }
 }
 
@@ -163,7 +163,7 @@ k_fwd_y(Geom g, const cx<Real> *__restrict__ U1, cx<Real> *__restrict__ U2,
     const int W = 2 * g.SP;                       // row width (a^ and b^)
     const int ix = blockIdx.y;
     const int c = blockIdx.x * C + (int)(threadIdx.x % C);
-    const bool valid = c < W && (c % g.SP) < g.H;
+    const bool valid = c < W && ab_col_valid(c, g.H);
     const Cx *src = U1 + (long long)ix * g.N * W + c;
     Cx *dst = U2 + (long long)ix * g.xs2 + c;
 
@@ -206,7 +206,7 @@ k_fwd_y2(Geom g, const cx<Real> *__restrict__ U1, cx<Real> *__restrict__ U2,
     const int W = 2 * g.SP;                       // row width (a^ and b^)
     const int ix = blockIdx.y;
     const int c = blockIdx.x * C + 2 * E::pair(); // first column of the pair
-    const bool valid = c < W && (c % g.SP) < g.H; // (c + 1 is in the same row)
+    const bool valid = c < W && ab_col_valid(c, g.H); // (c, c + 1) = (a^, b^) of one frequency
     const Cx *src = U1 + (long long)ix * g.N * W + c;
     Cx *dst = U2 + (long long)ix * g.xs2 + c;
     const Cx zero = mk<Cx>((Real)0, (Real)0);

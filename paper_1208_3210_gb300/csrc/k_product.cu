@@ -44,8 +44,7 @@ k_x_product(Geom g, const cx<Real> *__restrict__ U2, cx<Real> *__restrict__ U3,
     const int c = blockIdx.x * C + (int)(threadIdx.x % C);
     const bool valid = c < g.H;
     const long long rstride = g.xs2;                  // U2 stride between i_x rows
-    const Cx *srcA = U2 + (long long)ky * W + c;      // a^ column
-    const Cx *srcB = srcA + g.SP;                     // b^ column
+    const Cx *src = U2 + (long long)ky * W + 2 * c;   // (a^, b^) of frequency c
     const Cx zero = mk<Cx>((Real)0, (Real)0);
 
     Cx va[EF::VPT], vb[EF::VPT];
@@ -55,8 +54,8 @@ k_x_product(Geom g, const cx<Real> *__restrict__ U2, cx<Real> *__restrict__ U3,
         for (int r = 0; r < EF::R0; ++r) {
             int n = EF::first_row(b, r);
             bool ld = valid && n < g.N;
-            va[b * EF::R0 + r] = ld ? srcA[(long long)n * rstride] : zero;
-            vb[b * EF::R0 + r] = ld ? srcB[(long long)n * rstride] : zero;
+            if (ld) gld2(src + (long long)n * rstride, va[b * EF::R0 + r], vb[b * EF::R0 + r]);
+            else { va[b * EF::R0 + r] = zero; vb[b * EF::R0 + r] = zero; }
         }
     EF::run(va, vb, sm, tw);
     // conj(a^) * b^ : transform of the correlation sum_p a(p) b(p + q)

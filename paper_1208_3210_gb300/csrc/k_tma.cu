@@ -211,7 +211,7 @@ k_fwd_y_tma(Geom g, const __grid_constant__ CUtensorMap map, float2 *__restrict_
         }
         E::run(va, vb, sm, tw);
         const int c = c0 + 2 * p;
-        if (c < W && (c % g.SP) < g.H) {   // (c + 1 is in the same row)
+        if (c < W && ab_col_valid(c, g.H)) {   // (c, c + 1) = (a^, b^) of one frequency
             float2 *dst = U2 + (long long)ix * g.xs2 + c;
 #pragma unroll
             for (int b = 0; b < E::VPT / E::RL; ++b)
@@ -290,8 +290,9 @@ k_inv_y_tma(Geom g, const __grid_constant__ CUtensorMap map, float2 *__restrict_
 
 // ---------------------------------------------------------------------------
 // p_x pass with the conjugate product: U2 [N][P][2 SP] (plane stride xs2) ->
-// U3 [Q][P][SP].  Tile = (column tile over [0, H), k_y); staging a^ [NR][C]
-// then b^ [NR][C], NR = N rounded up.
+// U3 [Q][P][SP].  Tile = (column tile over [0, H), k_y); staging
+// [NR][C][2] = (a^, b^) of each frequency (one box per row block), NR = N
+// rounded up.
 template <int L, typename Cfg>
 __global__ void __launch_bounds__(Cfg::T, (XTmaBounds<L, Cfg>::MINB))
 k_x_product_tma(Geom g, const __grid_constant__ CUtensorMap map, float2 *__restrict__ U3,
@@ -306,8 +307,7 @@ k_x_product_tma(Geom g, const __grid_constant__ CUtensorMap map, float2 *__restr
     const int nbox = (g.N + box_rows - 1) / box_rows, NR = nbox * box_rows;
     const TmaSmem lay{2 * (size_t)NR * C * sizeof(float2), (size_t)FFT_ELEMS * sizeof(float2)};
     if (dyn_smem_bytes() < lay.total()) return;
-    float2 *stage_a = reinterpret_cast<float2 *>(smem_raw);
-    float2 *stage_b = stage_a + (size_t)NR * C;
+    float2 *stage = reinterpret_cast<float2 *>(smem_raw);   // [NR][C][2]: (a^, b^) per frequency
     float2 *sm = reinterpret_cast<float2 *>(smem_raw + lay.stage_bytes);
     unsigned long long *bar = reinterpret_cast<unsigned long long *>(smem_raw + lay.stage_bytes + lay.fft_bytes);
 
@@ -317,8 +317,7 @@ k_x_product_tma(Geom g, const __grid_constant__ CUtensorMap map, float2 *__restr
         const int ky = t / tiles_x, c0 = (t % tiles_x) * C;
         mbar_expect_tx(bar, tx);
         for (int q = 0; q < nbox; ++q) {
-            tma_load_3d(stage_a + (size_t)q * box_rows * C, &map, 2 * c0, ky, q * box_rows, bar);
-            tma_load_3d(stage_b + (size_t)q * box_rows * C, &map, 2 * (g.SP + c0), ky, q * box_rows, bar);
+            tma_load_3d(stage + (size_t)q * box_rows * 2 * C, &map, 4 * c0, ky, q * box_rows, bar);
         }
     };
     const TileRun run(ntiles, false);
@@ -340,8 +339,14 @@ k_x_product_tma(Geom g, const __grid_constant__ CUtensorMap map, float2 *__restr
             for (int r = 0; r < EF::R0; ++r) {
                 const int n = EF::first_row(b, r);
                 const bool ld = n < g.N;
-                va[b * EF::R0 + r] = ld ? stage_a[(size_t)n * C + col] : make_float2(0.f, 0.f);
-                vb[b * EF::R0 + r] = ld ? stage_b[(size_t)n * C + col] : make_float2(0.f, 0.f);
+                if (ld) {
+                    const float4 q = *reinterpret_cast<const float4 *>(&stage[((size_t)n * C + col) * 2]);
+                    va[b * EF::R0 + r] = make_float2(q.x, q.y);
+                    vb[b * EF::R0 + r] = make_float2(q.z, q.w);
+                } else {
+                    va[b * EF::R0 + r] = make_float2(0.f, 0.f);
+                    vb[b * EF::R0 + r] = make_float2(0.f, 0.f);
+                }
             }
         __syncthreads();
         if (threadIdx.x == 0 && t + run.step < run.end) {
@@ -446,7 +451,7 @@ k_y_col_tma(Geom g, const __grid_constant__ CUtensorMap map, float2 *__restrict_
                         if (l >= 0) dst[(long long)l * g.SP] = v[b * E::RL + r];
                     }
             }
-        } else if (c < W && (c % g.SP) < g.H) {
+        } else if (c < W && ab_col_valid(c, g.H)) {
             float2 *dst = out + (long long)pl * g.xs2 + c;
 #pragma unroll
             for (int b = 0; b < E::VPT / E::RL; ++b)
@@ -646,7 +651,7 @@ static cudaError_t launch_x_product_tma_t(const Geom &g, const Work<float> &w, c
     CUtensorMap map;
     if (e == cudaSuccess)
         e = make_map(&map, w.Y, 4ull * g.SP, (unsigned long long)g.P, (unsigned long long)g.N, 16ull * g.SP,
-                     8ull * (unsigned long long)g.xs2, 2 * C, 1, box_rows);
+                     8ull * (unsigned long long)g.xs2, 4 * C, 1, box_rows);
     int grid = 0;
     const int ntiles = ((g.H + C - 1) / C) * g.P;
     if (e == cudaSuccess) e = persistent_grid(k, T, lay.total(), ntiles, grid);

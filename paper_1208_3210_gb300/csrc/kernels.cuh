@@ -135,6 +135,12 @@ __device__ __forceinline__ F2 f2_mul(F2 a, F2 b)
     return f2_fast(p, e);
 }
 
+// Rows of the forward intermediates U1 and U2 (and of the adjoint's G3, G4)
+// hold the two half spectra interleaved: column 2k is the first (a^, or h^ in
+// the adjoint), column 2k + 1 the second (b^, or g^), k in [0, SP).  A tile
+// of frequencies then reads both spectra from one contiguous row segment.
+__host__ __device__ inline bool ab_col_valid(int c, int H) { return (c >> 1) < H; }
+
 // Dynamic shared-memory limit of a kernel.  (The L1/shared carveout is left
 // to the driver: pinning it to the largest shared share slowed the FFT passes,
 // which read twiddles through L1, by 10-20%.)
