@@ -123,26 +123,20 @@ k_fwd_energy(Geom g, Band band, const AxisTab *__restrict__ axis,
     __syncthreads();
     const Real half = (Real)0.5;
     constexpr int H = L / 2 + 1;                 // non-redundant frequencies (= g.H)
-    constexpr int SP = (H + 7) / 8 * 8;          // row stride (= g.SP); SP >= H + 1
-    constexpr int HP = (H + 1) / 2;              // frequency pairs (k, k + 1), k even
-    // a^ = (Z(k) + conj Z(-k)) / 2 ; b^ = (Z(k) - conj Z(-k)) / 2i
-    auto sep = [&](int col, int k, Cx &ah, Cx &bh) {
-        Cx zk = sm[E::saddr(col, k)];
-        Cx zm = sm[E::saddr(col, (L - k) & (L - 1))];
-        ah = mk<Cx>(half * (zk.x + zm.x), half * (zk.y - zm.y));
-        bh = mk<Cx>(half * (zk.y + zm.y), -half * (zk.x - zm.x));
-    };
+    constexpr int SP = (H + 7) / 8 * 8;          // row stride (= g.SP)
+    // a^ = (Z(k) + conj Z(-k)) / 2 ; b^ = (Z(k) - conj Z(-k)) / 2i, stored as
+    // the adjacent pair (a^(k), b^(k)): one 16-byte store per frequency, a
+    // warp's stores one contiguous run
 #pragma unroll 4
-    for (int idx = threadIdx.x; idx < C * HP; idx += T) {
-        int col = idx / HP, k = 2 * (idx % HP);
+    for (int idx = threadIdx.x; idx < C * H; idx += T) {
+        int col = idx / H, k = idx % H;
         long long line = line0 + col;
         if (line >= nlines) continue;
-        Cx a0, b0, a1, b1;
-        sep(col, k, a0, b0);
-        sep(col, k + 1, a1, b1);   // k + 1 = H lands in the row's padding
-        Cx *row = U1 + line * (2LL * SP) + 2 * k;
-        gst2(row, a0, b0);
-        gst2(row + 2, a1, b1);
+        Cx zk = sm[E::saddr(col, k)];
+        Cx zm = sm[E::saddr(col, (L - k) & (L - 1))];
+        Cx ah = mk<Cx>(half * (zk.x + zm.x), half * (zk.y - zm.y));
+        Cx bh = mk<Cx>(half * (zk.y + zm.y), -half * (zk.x - zm.x));
+        gst2(U1 + line * (2LL * SP) + 2 * k, ah, bh);
     }
 }
 
