@@ -294,13 +294,26 @@ def main():
         step()
     plan.status()
 
-    # --- device-timed region: inputs resident, per-pass events recorded live ---
+    # --- per-pass split from a short profiled run: every pass bracketed by
+    # events (this perturbs the step, so it stays outside the timed region) ---
+    ptimes = {}
+    if not batched:
+        plan.profile(True)
+        for _ in range(max(3, min(args.steps // 10, 50))):
+            step()
+        ptimes = plan.pass_times()
+        plan.profile(False)
+        pb0 = pass_bytes(s)
+        dom_pass = max((k for k in ptimes if k in pb0 and ptimes[k][1] > 0), key=lambda k: ptimes[k][0])
+
+    # --- device-timed region: inputs resident; the dominant pass's events are
+    # recorded live on its launch stream ---
     cvd = os.environ.get("CUDA_VISIBLE_DEVICES")
     gpu_index = int(cvd.split(",")[local_rank]) if cvd else local_rank
     clocks = ClockSampler(gpu_index)
     time.sleep(0.3)
     if not batched:
-        plan.profile(True)
+        plan.profile(True, passes=[dom_pass])
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
     torch.cuda.synchronize()
@@ -312,23 +325,38 @@ def main():
     barrier()
     clk = clocks.stop()
     ms_total = max_over_ranks(ev0.elapsed_time(ev1))
-    ptimes = plan.pass_times() if not batched else {}
+    dom_live = plan.pass_times() if not batched else {}
     if not batched:
         plan.profile(False)
     plan.status()
 
-    # --- end to end through the public call: result read back to pinned host ---
-    host_out = torch.empty(plan.out_elems(), dtype=torch.float32, pin_memory=True)
+    # --- end to end through the public call: every step's result read back to
+    # pinned host memory, streamed the way a caller overlaps transfers: two
+    # device and host output buffers, each step's copy on a copy stream,
+    # overlapped with the next step's computation ---
+    host_outs = [torch.empty(plan.out_elems(), dtype=torch.float32, pin_memory=True) for _ in range(2)]
+    dev_outs = [out, torch.empty_like(out)]
+    copy_stream = torch.cuda.Stream()
+    ready = [torch.cuda.Event() for _ in range(2)]
+    copied = [torch.cuda.Event() for _ in range(2)]
     e2e_steps = max(3, min(args.steps, 200))
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        step()
-        host_out.copy_(out, non_blocking=True)
+    for i in range(e2e_steps):
+        b = i % 2
+        if i >= 2:
+            stream.wait_event(copied[b])   # the copy that last read this buffer
+        plan.imchi(bands, out=dev_outs[b], mu_out=mu)
+        ready[b].record(stream)
+        copy_stream.wait_event(ready[b])
+        with torch.cuda.stream(copy_stream):
+            host_outs[b].copy_(dev_outs[b], non_blocking=True)
+        copied[b].record(copy_stream)
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(time.perf_counter() - t0)
     barrier()
+    del dev_outs[1]
 
     outputs_per_step = plan.out_elems() * world
     value = outputs_per_step * args.steps / (ms_total * 1e-3)
@@ -344,11 +372,11 @@ def main():
         dom, pb, dom_ms, traffic = "batch", {"batch": pipeline_bytes}, step_ms, None
         achieved = pipeline_bytes / (step_ms * 1e-3) / 1e9
     else:
-        # roofline of the dominant kernel (largest share of device time)
+        # roofline of the dominant kernel (largest share of device time in the
+        # profiled run), its duration from the events of the timed region
         pb = pass_bytes(s)
-        timed = {k: v for k, v in ptimes.items() if k in pb and v[1] > 0}
-        dom = max(timed, key=lambda k: timed[k][0])
-        dom_ms = timed[dom][0] / timed[dom][1]
+        dom = dom_pass
+        dom_ms = dom_live[dom][0] / dom_live[dom][1]
         achieved = pb[dom] / (dom_ms * 1e-3) / 1e9
         traffic = None if args.grid else recorded_traffic(dom, args.workload)
         pipeline_bytes = sum(pb.values())
@@ -403,9 +431,13 @@ def main():
                          "traffic": traffic, "algorithmic_bytes": pb[dom], "launch_ms": dom_ms,
                          "pipeline_frac": pipeline_bytes / (step_ms * 1e-3) / 1e9 / peak},
             "passes_ms": {k: round(v[0] / max(v[1], 1), 5) for k, v in ptimes.items()},
+            "passes_note": "per-pass means from a profiled run before the timed region (events around every "
+                           "pass); the timed region records events around the dominant pass only",
             "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]},
             "e2e": {"value": e2e_value, "unit": "outputs/s", "h2d_bytes_per_step": 64 * len(grids),
-                    "d2h_bytes_per_step": 4 * plan.out_elems(), "steps": e2e_steps},
+                    "d2h_bytes_per_step": 4 * plan.out_elems(), "steps": e2e_steps,
+                    "transfer": "each step's result to pinned host memory on a copy stream, double-buffered, "
+                                "overlapped with the next step"},
             "gpu_launches": launches,
         }
         if plain is not None:

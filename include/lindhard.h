@@ -199,6 +199,11 @@ lindhard_status lindhard_imchi_backward(lindhard_plan *plan,
  * accumulated times. */
 lindhard_status lindhard_plan_profile(lindhard_plan *plan, int enable);
 
+/* The same for a subset of the passes: bit i of `mask` times pass slot i
+ * (see LINDHARD_NUM_PASSES below), so that timing one kernel perturbs the
+ * others as little as possible; mask = 0 stops recording. */
+lindhard_status lindhard_plan_profile_passes(lindhard_plan *plan, unsigned mask);
+
 /* Kernels of one forward call, in launch order (the slots of
  * lindhard_plan_pass_times). */
 #define LINDHARD_NUM_PASSES 7

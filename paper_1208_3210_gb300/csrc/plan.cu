@@ -136,8 +136,9 @@ struct lindhard_plan {
     void *key_out = nullptr;
     double *key_mu = nullptr;
     std::vector<lindhard_band> key_bands;
-    // per-pass event timing (lindhard_plan_profile; sequential plans)
-    bool profile = false;
+    // per-pass event timing (lindhard_plan_profile; sequential plans): bit i
+    // of the mask times pass slot i
+    unsigned profile = 0;
     struct Timed { int slot; cudaEvent_t a, b; };
     std::vector<Timed> pending;
     std::vector<cudaEvent_t> pool;
@@ -161,7 +162,7 @@ static cudaEvent_t pool_event(lindhard_plan *p)
 template <typename F>
 static cudaError_t timed(lindhard_plan *p, int slot, cudaStream_t s, F &&launch)
 {
-    if (!p->profile) return launch();
+    if (!(p->profile & (1u << slot))) return launch();
     cudaEvent_t a = pool_event(p), b = pool_event(p);
     if (!a || !b) return cudaErrorMemoryAllocation;
     cudaError_t e = cudaEventRecord(a, s);
@@ -678,8 +679,8 @@ static lindhard_status forward_impl(lindhard_plan *p, const lindhard_band *bands
             if (e != cudaSuccess) return cuda_fail(e, "forward launch");
             p->warmed = true;
         }
-        bool prof = p->profile;
-        p->profile = false;
+        const unsigned prof = p->profile;
+        p->profile = 0;
         cudaGraph_t graph = nullptr;
         e = cudaStreamBeginCapture(p->origin, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
@@ -809,14 +810,20 @@ extern "C" lindhard_status lindhard_sum_rule(lindhard_plan *p, int index, const 
     return e == cudaSuccess ? LINDHARD_OK : cuda_fail(e, "sum-rule launch");
 }
 
-extern "C" lindhard_status lindhard_plan_profile(lindhard_plan *p, int enable)
+extern "C" lindhard_status lindhard_plan_profile_passes(lindhard_plan *p, unsigned mask)
 {
     if (!p) return fail(LINDHARD_EINVAL, "plan must be non-NULL");
-    if (enable && p->concurrent) return fail(LINDHARD_EUNSUPPORTED, "per-pass timing needs a sequential plan");
+    mask &= (1u << LINDHARD_NUM_PASSES) - 1;
+    if (mask && p->concurrent) return fail(LINDHARD_EUNSUPPORTED, "per-pass timing needs a sequential plan");
     drain_events(p);
     for (int i = 0; i < LINDHARD_NUM_PASSES; ++i) { p->pass_ms[i] = 0; p->pass_n[i] = 0; }
-    p->profile = enable != 0;
+    p->profile = mask;
     return LINDHARD_OK;
+}
+
+extern "C" lindhard_status lindhard_plan_profile(lindhard_plan *p, int enable)
+{
+    return lindhard_plan_profile_passes(p, enable ? (1u << LINDHARD_NUM_PASSES) - 1 : 0u);
 }
 
 extern "C" lindhard_status lindhard_plan_pass_times(lindhard_plan *p, double *ms, long long *launches)

@@ -23,7 +23,8 @@ _STATUS_NAMES = {OK: "OK", EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", E
 
 # Exported symbols, in the order include/lindhard.h declares them.
 SYMBOLS = ("lindhard_plan_create", "lindhard_plan_sizes", "lindhard_plan_workspace_bytes", "lindhard_imchi",
-           "lindhard_imchi_f64", "lindhard_imchi_backward", "lindhard_plan_profile", "lindhard_plan_pass_times",
+           "lindhard_imchi_f64", "lindhard_imchi_backward", "lindhard_plan_profile", "lindhard_plan_profile_passes",
+           "lindhard_plan_pass_times",
            "lindhard_sum_rule", "lindhard_plan_variants", "lindhard_plan_status", "lindhard_plan_destroy",
            "lindhard_imchi_noalloc", "lindhard_last_error")
 NOALLOC_SCRATCH_BYTES = 32 << 20
@@ -74,6 +75,7 @@ def load(path: str = LIB_PATH):
         lib.lindhard_imchi_f64.argtypes = [vp, ctypes.POINTER(Band), vp, vp, vp, vp]
         lib.lindhard_imchi_backward.argtypes = [vp, ctypes.POINTER(Band), vp, vp, vp, vp, vp]
         lib.lindhard_plan_profile.argtypes = [vp, ctypes.c_int]
+        lib.lindhard_plan_profile_passes.argtypes = [vp, ctypes.c_uint]
         lib.lindhard_plan_pass_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]
         lib.lindhard_plan_status.argtypes = [vp, vp]
         lib.lindhard_plan_variants.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
@@ -205,9 +207,14 @@ class Plan:
                                               _ptr(dparams), _stream(stream)))
         return dA, dparams
 
-    def profile(self, enable: bool = True):
-        """Start (or stop) per-pass CUDA-event timing; clears accumulated times."""
-        _check(load().lindhard_plan_profile(self._h, 1 if enable else 0))
+    def profile(self, enable: bool = True, passes=None):
+        """Start (or stop) per-pass CUDA-event timing of every pass, or of the
+        named passes only (names as in PASS_NAMES); clears accumulated times."""
+        if passes is None:
+            _check(load().lindhard_plan_profile(self._h, 1 if enable else 0))
+        else:
+            mask = sum(1 << PASS_NAMES.index(n) for n in passes) if enable else 0
+            _check(load().lindhard_plan_profile_passes(self._h, mask))
 
     def pass_times(self):
         """{pass name: (total ms, launches)} since profiling was enabled."""
