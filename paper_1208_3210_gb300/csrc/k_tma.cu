@@ -468,8 +468,9 @@ k_y_col_tma(Geom g, const __grid_constant__ CUtensorMap map, float2 *__restrict_
 
 // ---------------------------------------------------------------------------
 // Inverse energy pass (same transform as k_inv_energy): U4 [Q^2][SP] rows ->
-// out [Q^2][n_omega].  Tile = C pairs of rows (2 C rows), staged as nbx
-// boxes of bx columns: [nbx][2 C][bx] complex.
+// out [Q^2][n_omega].  Tile = C pairs of rows (2 C rows), staged by one box
+// of a 3D view (row split into nbx chunks of bx columns) as plain
+// [2 C][SP] complex.
 template <int L>
 __global__ void __launch_bounds__(LineCfg<L>::T)
 k_inv_energy_tma(Geom g, const __grid_constant__ CUtensorMap map, float *__restrict__ out,
@@ -491,7 +492,7 @@ k_inv_energy_tma(Geom g, const __grid_constant__ CUtensorMap map, float *__restr
     const TileRun run(ntiles, false);
     auto issue = [&](int t) {
         mbar_expect_tx(bar, tx);
-        for (int q = 0; q < nbx; ++q) tma_load_3d(stage + (size_t)q * 2 * C * bx, &map, 2 * q * bx, 2 * t * C, 0, bar);
+        tma_load_3d(stage, &map, 0, 0, 2 * t * C, bar);
     };
     if (threadIdx.x == 0) {
         mbar_init(bar, 1);
@@ -499,7 +500,8 @@ k_inv_energy_tma(Geom g, const __grid_constant__ CUtensorMap map, float *__restr
     }
     __syncthreads();
     // element m of staged row rr
-    auto at = [&](int rr, int m) { const int q = m / bx; return stage[((size_t)q * 2 * C + rr) * bx + (m - q * bx)]; };
+    const int SPs = nbx * bx;
+    auto at = [&](int rr, int m) { return stage[(size_t)rr * SPs + m]; };
     unsigned parity = 0;
     const float sc = (float)g.scale;
     for (int t = run.t; t < run.end; t += run.step) {
@@ -716,7 +718,9 @@ static cudaError_t launch_inv_energy_tma_t(const Geom &g, const Work<float> &w, 
     cudaError_t e = smem_attrs(k, lay.total());
     CUtensorMap map;
     const unsigned long long rows = (unsigned long long)g.Q * g.Q;
-    if (e == cudaSuccess) e = make_map(&map, w.Y, 2ull * g.SP, rows, 1ull, 8ull * g.SP, 8ull * g.SP * rows, 2 * bx, 2 * C, 1);
+    // 3D view of the rows: (2 bx floats, nbx chunks, rows); one box = 2 C rows
+    if (e == cudaSuccess)
+        e = make_map(&map, w.Y, 2ull * bx, (unsigned long long)nbx, rows, 8ull * bx, 8ull * g.SP, 2 * bx, nbx, 2 * C);
     int grid = 0;
     const int ntiles = (int)(((long long)g.Q * g.Q / 2 + C - 1) / C);
     if (e == cudaSuccess) e = persistent_grid(k, T, lay.total(), ntiles, grid);
