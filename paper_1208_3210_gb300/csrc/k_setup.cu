@@ -198,8 +198,26 @@ __device__ __forceinline__ void bracket_from(const double *res, const int *cross
 // One multisection pass over [sh.br.lo, sh.br.hi] (set by thread 0 before the
 // call): this CTA's candidates; records the first one whose total reaches
 // the target in cross[blockIdx.x].
+// Band energies and weights of pairs [base, base + n) into sh.ew (FP32).
+__device__ __forceinline__ void stage_pairs(const Geom &g, const Band &band, MuShared &sh, int base, int n)
+{
+    const int h = g.npz / 2;
+    const float t = (float)band.t, tp = (float)band.tp, tpp = (float)band.tpp;
+    const bool free_e = band.band_kind == 1;
+    for (int k = threadIdx.x; k < n; k += MU_THREADS) {
+        int a, b;
+        tri_pair(base + k, h, a, b);
+        const float e = free_e ? 0.5f * (sh.p2[a] + sh.p2[b])
+                               : -2.0f * t * (sh.c1[a] + sh.c1[b]) - 4.0f * tp * sh.c1[a] * sh.c1[b]
+                                     - 2.0f * tpp * (sh.c2[a] + sh.c2[b]);
+        sh.ew[k] = make_float2(e, (float)pair_weight(a, b, h));
+    }
+}
+
+// prestaged: the first chunk of pairs is already in sh.ew (staged before the
+// bracket was known; the classes must then have been staged and synchronised)
 __device__ __forceinline__ void sect_pass(const Geom &g, const Band &band, const MuConst &mc, MuShared &sh,
-                                          int *cross)
+                                          int *cross, bool prestaged = false)
 {
     const int h = g.npz / 2;
     const int npairs = (h + 1) * (h + 2) / 2;
@@ -208,22 +226,13 @@ __device__ __forceinline__ void sect_pass(const Geom &g, const Band &band, const
     __syncthreads();
     if (threadIdx.x < MU_NCPT) sh.mu_c[threadIdx.x] = (float)(sh.br.lo + (double)(c0 + (int)threadIdx.x) * sh.br.step);
     const float inv_gam = (float)mc.inv_gam, inv_pi = 0.318309886183790672f;
-    const float t = (float)band.t, tp = (float)band.tp, tpp = (float)band.tpp;
-    const bool free_e = band.band_kind == 1;
     const int q = threadIdx.x % MU_NCPT;        // this thread's candidate
     constexpr int LANES = MU_THREADS / MU_NCPT;  // threads per candidate
     long long acc = 0;
     for (int base = 0; base < npairs; base += MU_CHUNK) {
         const int n = min(MU_CHUNK, npairs - base);
         __syncthreads();   // previous chunk consumed; mu_c written
-        for (int k = threadIdx.x; k < n; k += MU_THREADS) {
-            int a, b;
-            tri_pair(base + k, h, a, b);
-            const float e = free_e ? 0.5f * (sh.p2[a] + sh.p2[b])
-                                   : -2.0f * t * (sh.c1[a] + sh.c1[b]) - 4.0f * tp * sh.c1[a] * sh.c1[b]
-                                         - 2.0f * tpp * (sh.c2[a] + sh.c2[b]);
-            sh.ew[k] = make_float2(e, (float)pair_weight(a, b, h));
-        }
+        if (!(prestaged && base == 0)) stage_pairs(g, band, sh, base, n);
         __syncthreads();
         const float mu = sh.mu_c[q];
         float s[4] = {0.f, 0.f, 0.f, 0.f};   // four chains; at most MU_CHUNK / LANES terms of at most 8
@@ -324,6 +333,10 @@ k_mu_sect(Geom g, Band band, double *acc, int pass, MuConst mc)
     __shared__ MuShared sh;
     const int G = gridDim.x;
     stage_classes(g, sh);
+    __syncthreads();
+    // the first chunk of pair energies does not depend on the bracket
+    const int h = g.npz / 2, npairs = (h + 1) * (h + 2) / 2;
+    stage_pairs(g, band, sh, 0, min(MU_CHUNK, npairs));
     bracket_from(acc, mu_cross(acc, G, pass - 1), mc, pass - 1, sh.br);
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         acc[3 * pass + 0] = sh.br.lo;
@@ -332,7 +345,7 @@ k_mu_sect(Geom g, Band band, double *acc, int pass, MuConst mc)
     }
     __syncthreads();
     if (sh.br.flag) return;   // the filling was not bracketed
-    sect_pass(g, band, mc, sh, mu_cross(acc, G, pass));
+    sect_pass(g, band, mc, sh, mu_cross(acc, G, pass), true);
 }
 
 // Halley step in FP64 from the midpoint of the last bracket; publishes mu.
@@ -344,6 +357,18 @@ k_mu_halley(Geom g, Band band, const AxisTab *__restrict__ axis, InstState *st, 
     __shared__ struct { MuBracket br; } sh;
     __shared__ double s_red[MU_NT_THREADS / 32][3];
     double *part = acc + MU_RES;   // [G][4]
+    const int h = g.npz / 2, npairs = (h + 1) * (h + 2) / 2, c = g.N / 2;
+    // the band energy of this thread's first pair does not depend on mu: its
+    // loads and FP64 chain overlap the bracket search
+    const int k0 = blockIdx.x + G * threadIdx.x;
+    double e0_first = 0.0;
+    int w_first = 0;
+    if (k0 < npairs) {
+        int a, b;
+        tri_pair(k0, h, a, b);
+        w_first = pair_weight(a, b, h);
+        e0_first = band_e0(band, axis[c - a], axis[c - b]);
+    }
     bracket_from(acc, mu_cross(acc, G, P - 1), mc, P - 1, sh.br);
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         acc[3 * P + 0] = sh.br.lo;
@@ -361,16 +386,20 @@ k_mu_halley(Geom g, Band band, const AxisTab *__restrict__ axis, InstState *st, 
         }
         return;
     }
-    const int h = g.npz / 2, npairs = (h + 1) * (h + 2) / 2, c = g.N / 2;
     const double igam = mc.inv_gam, ipi = 0.31830988618379067154;
     double f = 0.0;
     float f1 = 0.f, f2 = 0.f;
     // pairs interleaved over the CTAs first, so every SM's FP64 units share the work
-    for (int k = blockIdx.x + G * threadIdx.x; k < npairs; k += G * (int)blockDim.x) {
-        int a, b;
-        tri_pair(k, h, a, b);
-        const int w = pair_weight(a, b, h);
-        const double x = (band_e0(band, axis[c - a], axis[c - b]) - mu) * igam;   // xi / gamma
+    for (int k = k0; k < npairs; k += G * (int)blockDim.x) {
+        double e0 = e0_first;
+        int w = w_first;
+        if (k != k0) {
+            int a, b;
+            tri_pair(k, h, a, b);
+            w = pair_weight(a, b, h);
+            e0 = band_e0(band, axis[c - a], axis[c - b]);
+        }
+        const double x = (e0 - mu) * igam;                                       // xi / gamma
         f += (double)w * (0.5 - atan(x) * ipi);                                   // occupation
         const float xf = (float)x, r = 1.0f / (1.0f + xf * xf);                    // gamma^2 / (xi^2 + gamma^2)
         f1 += (float)w * r * (float)ipi;                                           // gamma d occ / d mu
