@@ -127,16 +127,19 @@ k_fwd_energy(Geom g, Band band, const AxisTab *__restrict__ axis,
     // a^ = (Z(k) + conj Z(-k)) / 2 ; b^ = (Z(k) - conj Z(-k)) / 2i, stored as
     // the adjacent pair (a^(k), b^(k)): one 16-byte store per frequency, a
     // warp's stores one contiguous run
-#pragma unroll 4
-    for (int idx = threadIdx.x; idx < C * H; idx += T) {
-        int col = idx / H, k = idx % H;
-        long long line = line0 + col;
+    // one warp per line, lanes over the frequencies (no index division)
+    for (int col = threadIdx.x >> 5; col < C; col += T >> 5) {
+        const long long line = line0 + col;
         if (line >= nlines) continue;
-        Cx zk = sm[E::saddr(col, k)];
-        Cx zm = sm[E::saddr(col, (L - k) & (L - 1))];
-        Cx ah = mk<Cx>(half * (zk.x + zm.x), half * (zk.y - zm.y));
-        Cx bh = mk<Cx>(half * (zk.y + zm.y), -half * (zk.x - zm.x));
-        gst2(U1 + line * (2LL * SP) + 2 * k, ah, bh);
+        Cx *row = U1 + line * (2LL * SP);
+#pragma unroll 2
+        for (int k = threadIdx.x & 31; k < H; k += 32) {
+            Cx zk = sm[E::saddr(col, k)];
+            Cx zm = sm[E::saddr(col, (L - k) & (L - 1))];
+            Cx ah = mk<Cx>(half * (zk.x + zm.x), half * (zk.y - zm.y));
+            Cx bh = mk<Cx>(half * (zk.y + zm.y), -half * (zk.x - zm.x));
+            gst2(row + 2 * k, ah, bh);
+        }
     }
 }
 
