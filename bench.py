@@ -67,11 +67,6 @@ def parse_args():
     return ap.parse_args()
 
 
-def rank_info():
-    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
-            int(os.environ.get("WORLD_SIZE", "1")))
-
-
 def pass_bytes(s):
     """Algorithmic HBM bytes of each pass for one instance (FP32, 8-byte
     complex): every intermediate written once and read once, counting only its
@@ -191,6 +186,7 @@ def cpu_baseline(workload, seconds=15.0, seed=7):
 
 
 def run_reference(args):
+    from paper_1208_3210_gb300.replicas import rank_info
     rank, _, world = rank_info()
     if rank != 0:
         return
@@ -238,7 +234,8 @@ def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
-    rank, local_rank, world = rank_info()
+    from paper_1208_3210_gb300 import replicas
+    rank, local_rank, world = replicas.rank_info()
     import torch
     import torch.distributed as dist
 
@@ -284,11 +281,7 @@ def main():
             dist.barrier()
 
     def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return replicas.max_over_ranks(x, world, "cuda")
 
     for _ in range(max(3, args.warmup)):
         step()
@@ -359,8 +352,8 @@ def main():
     del dev_outs[1]
 
     outputs_per_step = plan.out_elems() * world
-    value = outputs_per_step * args.steps / (ms_total * 1e-3)
-    e2e_value = outputs_per_step * e2e_steps / e2e_s
+    value = replicas.whole_job_rate(plan.out_elems(), world, args.steps, ms_total * 1e-3)
+    e2e_value = replicas.whole_job_rate(plan.out_elems(), world, e2e_steps, e2e_s)
     step_ms = ms_total / args.steps
     peak, peak_kind = measured_peaks()
     # kernels launched in the timed region: each step is one forward call
