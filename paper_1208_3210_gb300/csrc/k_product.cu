@@ -123,3 +123,27 @@ cudaError_t launch_x_product(const Geom &g, const Work<double> &w, cudaStream_t 
 }
 
 }  // namespace lh
+
+namespace lh {
+// Every momentum length's default tiles (the engines a plan runs without the
+// autotuner) fit in the 227 KB of shared memory a CTA can have.
+template <int L>
+constexpr bool default_tiles_fit()
+{
+    constexpr size_t cap = 227 * 1024;
+    using XP = XProduct<float, L, XCfg<L>>;
+    constexpr size_t col = sizeof(float2) * Fft<float, L, ColCfg<L>::C, ColCfg<L>::T, MAP_COL, true>::SMEM_ELEMS;
+    constexpr size_t x = sizeof(float2) * XP::SMEM_ELEMS;
+    if constexpr (L >= 128) {
+        constexpr size_t pair = sizeof(float2) * FftPair<float, L, PairCfg<L>::C, PairCfg<L>::T, false>::SMEM_ELEMS;
+        return col <= cap && x <= cap && pair <= cap;
+    }
+    return col <= cap && x <= cap;
+}
+static_assert(default_tiles_fit<16>() && default_tiles_fit<32>() && default_tiles_fit<48>() &&
+                  default_tiles_fit<64>() && default_tiles_fit<96>() && default_tiles_fit<128>() &&
+                  default_tiles_fit<192>() && default_tiles_fit<256>() && default_tiles_fit<384>() &&
+                  default_tiles_fit<512>() && default_tiles_fit<768>() && default_tiles_fit<1024>() &&
+                  default_tiles_fit<1536>() && default_tiles_fit<2048>() && default_tiles_fit<4096>(),
+              "a default tile exceeds the shared memory of a CTA");
+}  // namespace lh

@@ -411,7 +411,7 @@ k_y_col_tma(Geom g, const __grid_constant__ CUtensorMap map, float2 *__restrict_
         mbar_expect_tx(bar, tx);
         for (int q = 0; q < nbox; ++q) tma_load_3d(stage + (size_t)q * box_rows * C, &map, 2 * c0, q * box_rows, pl, bar);
     };
-    const TileRun run(ntiles, false);
+    const TileRun run(ntiles, !INV);   // forward: contiguous runs, as the paired forward pass
     if (threadIdx.x == 0) {
         mbar_init(bar, 1);
         if (run.t < run.end) issue(run.t);

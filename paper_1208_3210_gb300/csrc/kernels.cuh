@@ -37,13 +37,14 @@ template <int L> struct PairCfg;
 template <int L> struct XCfg { static constexpr int C = ColCfg<L>::C, T = ColCfg<L>::T, MINB = ColCfg<L>::MINB_X; };
 template <> struct XCfg<512> { static constexpr int C = 8, T = 256, MINB = 2; };   // VPT 16
 template <> struct XCfg<384> { static constexpr int C = 8, T = 128, MINB = 3; };   // VPT 24
+template <> struct XCfg<4096> { static constexpr int C = 2, T = 512, MINB = 1; };  // VPT 16, 139 KB
 
 template <> struct PairCfg<128>  { static constexpr int C = 16, T = 64, MINB = 4; };
 template <> struct PairCfg<256>  { static constexpr int C = 16, T = 128, MINB = 4; };
 template <> struct PairCfg<512>  { static constexpr int C = 16, T = 512, MINB = 2; };  // VPT 8
 template <> struct PairCfg<1024> { static constexpr int C = 16, T = 512, MINB = 1; };
 template <> struct PairCfg<2048> { static constexpr int C = 8, T = 512, MINB = 1; };
-template <> struct PairCfg<4096> { static constexpr int C = 8, T = 1024, MINB = 1; };
+template <> struct PairCfg<4096> { static constexpr int C = 4, T = 512, MINB = 1; };    // 139 KB of shared memory
 template <> struct PairCfg<192>  { static constexpr int C = 16, T = 64, MINB = 4; };    // VPT 24
 template <> struct PairCfg<384>  { static constexpr int C = 32, T = 256, MINB = 2; };
 template <> struct PairCfg<768>  { static constexpr int C = 16, T = 256, MINB = 2; };

@@ -216,3 +216,29 @@ def test_sum_rule_fp64_reductions(lh, cfg):
     ref = np.array([-c * np.dot(Da[: grid["n_eps"] - m], Db[m:]) for m in range(grid["n_omega"])])
     assert np.abs(dc - ref).max() <= 1e-6 * np.abs(ref).max()
     plan.close()
+
+
+def test_fft_length_4096_samples(lh):
+    """N = 2048 with Q = 2048 lags pads the momentum axes to P = 4096 (the
+    longest compiled length; its tiles must fit in shared memory): seeded
+    samples against the oracle, default and autotuned plans."""
+    import torch
+    grid = wl.grid_params(16, 128, 16, 1.0, q_extent=2048)
+    band = wl.band_params(filling=1.1, gamma=0.08, ff_a=1.0)
+    b = _oracle_band(band, grid)
+    lx, ly, m = wl.output_samples(grid, 60, seed=11, near_origin=4)
+    A = oracle.spectral(b, grid)
+    ref = oracle.imchi_samples(A, grid, grid["q_extent"], lx, ly, m)
+    del A
+    for autotune in (False, True):
+        plan = lh.Plan([grid], autotune=autotune)
+        assert plan.sizes[0].fft_p == 4096
+        out = plan.imchi([band])
+        plan.status()
+        s = plan.sizes[0]
+        got = out.reshape(s.q_extent, s.q_extent, s.n_omega).cpu().numpy()[lx, ly, m].astype(np.float64)
+        plan.close()
+        del out
+        torch.cuda.empty_cache()
+        err = np.abs(got - ref).max() / np.abs(ref).max()
+        assert err <= TOL32, (autotune, err)
