@@ -62,6 +62,14 @@ typedef enum {
 
 typedef enum {
     LINDHARD_FP32 = 0,          /* FP32 SIMT FFT, FP32 intermediates          */
+    LINDHARD_SPLITBF16_TC = 1,  /* as LINDHARD_FP32, but the inverse p_y pass
+                                   runs its two DFT stages (P = R1 R2) as
+                                   matrix products on the tensor cores: BF16
+                                   hi + lo operands, three products
+                                   (hi.hi + lo.hi + hi.lo), FP32 accumulation.
+                                   Momentum FFT lengths 128, 192, 256, 384,
+                                   512, 768, 1024, 1536; forward only (plans
+                                   with LINDHARD_PLAN_BACKWARD reject it)    */
     LINDHARD_FP64 = 2           /* FP64 everywhere; FFT lengths <= 256 only   */
 } lindhard_precision;
 

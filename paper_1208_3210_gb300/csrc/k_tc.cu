@@ -1,0 +1,389 @@
+// Tensor-core form of the inverse p_y pass (precision LINDHARD_SPLITBF16_TC).
+//
+// The same transform as k_inv_y / k_inv_y2 (Sec. 3: inverse Fourier transform
+// of the product spectrum along p_y, keeping the Q lags q_y), with both DFT
+// stages of a two-stage decomposition P = R1 * R2 run as dense matrix
+// products on the fifth-generation tensor cores (tcgen05.mma, accumulators in
+// tensor memory):
+//
+//   n = n1 + R1 n2,  m = m2 + R2 m1,
+//   y(m) = sum_n1 e^{+2 pi i n1 m1 / R1} [ e^{+2 pi i n1 m2 / P}
+//                 sum_n2 e^{+2 pi i n2 m2 / R2} x(n1 + R1 n2) ].
+//
+// Stage 1 is a product [C R1 lines x 2 R2] . [2 R2 x 2 R2]^T with the DFT of
+// size R2 embedded as a real matrix (re/im interleaved along K and N); the
+// twiddle e^{+2 pi i n1 m2 / P} is applied in FP32 registers between the
+// stages; stage 2 is [C R2 lines x 2 R1] . [2 R1 x 2 R1]^T.  Operands are
+// split into BF16 hi + lo parts (x = hi + lo to about 2^-16 relative) and
+// each product takes three terms, hi.hi + lo.hi + hi.lo, accumulated in FP32
+// in tensor memory.  The DFT matrices are built once per plan in FP64 and
+// split on the device (k_tc_mats).
+//
+// One CTA transforms C columns of one q_x plane: thread t owns line t of
+// stage 1 (n1 = t / C, column t % C) and line t of stage 2 (m2 = t / C);
+// tensor-memory lane = t % 128, row block t / 128 in its own columns.  One
+// thread issues the MMAs and commits them to an mbarrier; every wait is
+// bounded (1 s of %globaltimer) and a CTA that gives up records
+// DEV_ETIMEOUT, still frees its tensor memory and returns.
+#include <cuda_bf16.h>
+
+#include "async.cuh"
+#include "kernels.cuh"
+
+namespace lh {
+
+// ---------------------------------------------------------------------------
+// tcgen05 helpers (inline PTX).
+//
+// Shared-memory matrix descriptor of a K-major operand without swizzle: core
+// matrices of 8 rows x 16 bytes; lbo = byte distance between core matrices
+// adjacent along K, sbo = between core matrices adjacent along M (or N);
+// bit 46 is the descriptor version of this architecture.
+__device__ __forceinline__ unsigned long long tc_desc(unsigned addr, unsigned lbo, unsigned sbo)
+{
+    return (unsigned long long)((addr & 0x3FFFFu) >> 4) | ((unsigned long long)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((unsigned long long)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+// Instruction descriptor of kind::f16 with BF16 A and B, FP32 accumulator,
+// both operands K-major, shape M x N (x 16).
+__host__ __device__ constexpr unsigned tc_idesc_bf16(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(N >> 3) << 17) | ((unsigned)(M >> 4) << 24);
+}
+// Byte offset of element (row, k) of a K-major BF16 operand with 16-byte
+// chunks of one 8-row group back to back (lbo = 128) and row groups sbo apart.
+__host__ __device__ constexpr unsigned tc_koff(int row, int k, int sbo)
+{
+    return (unsigned)((row % 8) * 16 + (row / 8) * sbo + (k / 8) * 128 + (k % 8) * 2);
+}
+
+__device__ __forceinline__ void tc_alloc(unsigned *slot, unsigned cols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(slot)), "r"(cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tc_dealloc(unsigned taddr, unsigned cols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(cols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// D (+)= A . B^T, one instruction of K = 16 (issued by a single thread)
+__device__ __forceinline__ void tc_mma(unsigned d_tmem, unsigned long long a, unsigned long long b, unsigned idesc,
+                                       bool accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"((unsigned)accumulate)
+        : "memory");
+}
+// The mbarrier completes one phase when every MMA issued so far by this thread is done.
+__device__ __forceinline__ void tc_commit(unsigned long long *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar))
+                 : "memory");
+}
+// 16 / 32 consecutive FP32 columns of this thread's tensor-memory lane.
+__device__ __forceinline__ void tc_ld16(unsigned taddr, float *v)
+{
+    unsigned r[16];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                 : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tc_ld32(unsigned taddr, float *v)
+{
+    unsigned r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+template <int NC>
+__device__ __forceinline__ void tc_ld(unsigned taddr, float *v)
+{
+    static_assert(NC % 16 == 0, "whole 16-column loads");
+#pragma unroll
+    for (int c = 0; c + 32 <= NC; c += 32) tc_ld32(taddr + c, v + c);
+    if constexpr (NC % 32 == 16) tc_ld16(taddr + (NC - 16), v + (NC - 16));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// x = hi + lo with hi, lo BF16 (re in the low half of each word): hi is x
+// rounded to 8 significant bits, lo the exact FP32 remainder rounded again.
+__device__ __forceinline__ void bf16_split(float2 x, unsigned &hi, unsigned &lo)
+{
+    const __nv_bfloat162 h = __floats2bfloat162_rn(x.x, x.y);
+    const float2 hf = __bfloat1622float2(h);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(x.x - hf.x, x.y - hf.y);
+    hi = *reinterpret_cast<const unsigned *>(&h);
+    lo = *reinterpret_cast<const unsigned *>(&l);
+}
+
+// ---------------------------------------------------------------------------
+// Decompositions P = R1 * R2 and columns per CTA (C R1 and C R2 multiples of
+// 128, the M of one MMA; R1, R2 multiples of 8, so that 2 R is a multiple of
+// the K = 16 of one instruction).
+__host__ __device__ constexpr int tc_r1(int P)
+{
+    return P == 128 ? 8 : P == 192 ? 8 : P == 256 ? 16 : P == 384 ? 16 : P == 512 ? 16 : P == 768 ? 16 : P == 1024 ? 32
+         : P == 1536 ? 32 : 0;
+}
+__host__ __device__ constexpr int tc_cols(int P)
+{
+    return P == 128 ? 16 : P == 192 ? 16 : P == 256 ? 8 : P == 384 ? 16 : P == 512 ? 8 : P == 768 ? 8 : P == 1024 ? 4
+         : P == 1536 ? 8 : 0;
+}
+bool tc_supported(int P) { return tc_r1(P) != 0; }
+
+template <int R1, int R2, int C>
+struct TcInvY {
+    static constexpr int ROWS1 = C * R1, ROWS2 = C * R2;
+    static constexpr int NB1 = ROWS1 / 128, NB2 = ROWS2 / 128;
+    static constexpr int T = 128 * (NB1 > NB2 ? NB1 : NB2);
+    static constexpr int K1 = 2 * R2, K2 = 2 * R1;                    // K = N of each stage
+    static constexpr int SBO1 = K1 / 8 * 128, SBO2 = K2 / 8 * 128;    // bytes per 8-row group
+    static constexpr int ABYTES = ROWS1 * K1 * 2;                      // = ROWS2 * K2 * 2
+    static constexpr int B1BYTES = K1 * K1 * 2, B2BYTES = K2 * K2 * 2;
+    // [A hi][A lo][B1 hi][B1 lo][B2 hi][B2 lo][mbarrier][tensor-memory address]
+    static constexpr int OFF_ALO = ABYTES, OFF_B1 = 2 * ABYTES, OFF_B2 = OFF_B1 + 2 * B1BYTES;
+    static constexpr int MAT_BYTES = 2 * B1BYTES + 2 * B2BYTES;
+    static constexpr int OFF_BAR = OFF_B1 + MAT_BYTES;
+    static constexpr int SMEM = OFF_BAR + 16;
+    static constexpr int DCOLS = NB1 * K1 > NB2 * K2 ? NB1 * K1 : NB2 * K2;
+    static constexpr int COLS = DCOLS <= 32 ? 32 : DCOLS <= 64 ? 64 : DCOLS <= 128 ? 128 : DCOLS <= 256 ? 256 : 512;
+    // two CTAs per SM when shared memory, tensor memory and the registers a
+    // thread keeps live (2 max(R1, R2) values and addressing) allow it
+    static constexpr int MINB =
+        (2 * SMEM <= 227 * 1024 && 2 * COLS <= 512 && 2 * (R1 > R2 ? R1 : R2) + 32 <= 65536 / (2 * T)) ? 2 : 1;
+    static_assert(ROWS1 % 128 == 0 && ROWS2 % 128 == 0, "stage rows must fill whole M = 128 blocks");
+    static_assert(R1 % 8 == 0 && R2 % 8 == 0, "2 R must be a multiple of K = 16");
+    static_assert(ROWS1 * K1 == ROWS2 * K2, "both stages hold C P complex values");
+    static_assert(DCOLS <= 512 && SMEM <= 227 * 1024, "tensor or shared memory");
+};
+
+// Byte offset of length P's matrices in the table built by k_tc_mats (the
+// shared-memory image [B1 hi][B1 lo][B2 hi][B2 lo] of TcInvY).
+__host__ __device__ constexpr int tc_mats_bytes_of(int P)
+{
+    return tc_r1(P) == 0 ? 0 : 16 * ((P / tc_r1(P)) * (P / tc_r1(P)) + tc_r1(P) * tc_r1(P));
+}
+__host__ __device__ constexpr int tc_mats_offset(int P)
+{
+    return P == 128 ? 0
+         : P == 192 ? tc_mats_offset(128) + tc_mats_bytes_of(128)
+         : P == 256 ? tc_mats_offset(192) + tc_mats_bytes_of(192)
+         : P == 384 ? tc_mats_offset(256) + tc_mats_bytes_of(256)
+         : P == 512 ? tc_mats_offset(384) + tc_mats_bytes_of(384)
+         : P == 768 ? tc_mats_offset(512) + tc_mats_bytes_of(512)
+         : P == 1024 ? tc_mats_offset(768) + tc_mats_bytes_of(768)
+         : P == 1536 ? tc_mats_offset(1024) + tc_mats_bytes_of(1024)
+         : tc_mats_offset(1536) + tc_mats_bytes_of(1536);   // total
+}
+size_t tc_mats_bytes() { return (size_t)tc_mats_offset(0); }
+
+// The real embedding of the inverse DFT of size R, split into BF16 hi and lo:
+// row 2m + o (output m, o = re/im), column 2r + i (input r, i = re/im) of
+//   [[cos t, -sin t], [sin t, cos t]],  t = 2 pi r m / R,
+// written as a K-major operand (tc_koff, sbo = 2R / 8 * 128).
+__global__ void k_tc_mats(unsigned char *out)
+{
+    const int lens[8] = {128, 192, 256, 384, 512, 768, 1024, 1536};
+    const int P = lens[blockIdx.y];
+    const int R1 = tc_r1(P), R2 = P / R1;
+    unsigned char *base = out + tc_mats_offset(P);
+    const int e1 = 4 * R2 * R2, e2 = 4 * R1 * R1;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < e1 + e2; i += gridDim.x * blockDim.x) {
+        const bool st1 = i < e1;
+        const int R = st1 ? R2 : R1, j = st1 ? i : i - e1;
+        const int row = j / (2 * R), col = j % (2 * R);
+        const int m = row / 2, o = row % 2, r = col / 2, ii = col % 2;
+        double s, c;
+        sincospi(2.0 * (double)((r * m) % R) / (double)R, &s, &c);
+        const double v = (o == ii) ? c : (o == 0 ? -s : s);
+        const __nv_bfloat16 hi = __double2bfloat16(v);
+        const __nv_bfloat16 lo = __double2bfloat16(v - (double)__bfloat162float(hi));
+        const int bytes = 4 * R * R * 2;                  // one matrix, hi or lo
+        unsigned char *mat = base + (st1 ? 0 : 2 * (4 * R2 * R2 * 2));
+        const unsigned off = tc_koff(row, col, 2 * R / 8 * 128);
+        *reinterpret_cast<__nv_bfloat16 *>(mat + off) = hi;
+        *reinterpret_cast<__nv_bfloat16 *>(mat + bytes + off) = lo;
+    }
+}
+
+cudaError_t launch_tc_mats(void *buf, cudaStream_t s)
+{
+    k_tc_mats<<<dim3(8, 8), 256, 0, s>>>(static_cast<unsigned char *>(buf));
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// The pass.  U3 [Q][P][SP] -> U4 [Q][Q][SP]; grid (ceil(H / C), Q).
+template <int R1, int R2, int C>
+__global__ void __launch_bounds__(TcInvY<R1, R2, C>::T, TcInvY<R1, R2, C>::MINB)
+k_inv_y_tc(Geom g, const float2 *__restrict__ U3, float2 *__restrict__ U4, const float2 *__restrict__ tw,
+           const uint4 *__restrict__ mats, unsigned *status)
+{
+    using S = TcInvY<R1, R2, C>;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    if (dyn_smem_bytes() < (unsigned)S::SMEM) return;
+    unsigned long long *bar = reinterpret_cast<unsigned long long *>(smem + S::OFF_BAR);
+    unsigned *slot = reinterpret_cast<unsigned *>(smem + S::OFF_BAR + 8);
+    const int t = threadIdx.x, warp = t >> 5;
+    const int lx = blockIdx.y, c0 = blockIdx.x * C;
+    const int c = t % C;
+    const bool valid = c0 + c < g.H;
+    const unsigned sbase = smem_addr(smem);
+    constexpr unsigned IDESC1 = tc_idesc_bf16(128, S::K1), IDESC2 = tc_idesc_bf16(128, S::K2);
+
+    // both stages' DFT matrices: a straight copy of their shared-memory image
+    for (int i = t; i < S::MAT_BYTES / 16; i += S::T) reinterpret_cast<uint4 *>(smem + S::OFF_B1)[i] = mats[i];
+    if (t == 0) mbar_init(bar, 1);
+    if (warp == 0) tc_alloc(slot, S::COLS);
+
+    // stage-1 operand: line t = (n1, c) holds x(n1 + R1 n2), n2 < R2
+    if (t < S::ROWS1) {
+        const int n1 = t / C;
+        const float2 *src = U3 + (long long)lx * g.xs3 + (long long)n1 * g.SP + c0 + c;
+        float2 x[R2];
+#pragma unroll
+        for (int n2 = 0; n2 < R2; ++n2)
+            x[n2] = valid ? __ldcs(src + (long long)(R1 * n2) * g.SP) : make_float2(0.f, 0.f);
+        unsigned char *row = smem + tc_koff(t, 0, S::SBO1);
+#pragma unroll
+        for (int j = 0; j < R2 / 4; ++j) {
+            unsigned h[4], l[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) bf16_split(x[4 * j + q], h[q], l[q]);
+            *reinterpret_cast<uint4 *>(row + j * 128) = make_uint4(h[0], h[1], h[2], h[3]);
+            *reinterpret_cast<uint4 *>(row + S::OFF_ALO + j * 128) = make_uint4(l[0], l[1], l[2], l[3]);
+        }
+    }
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const unsigned tmem = *slot;
+
+    // stage 1: D1[b] = A hi . B1 hi + A lo . B1 hi + A hi . B1 lo per 128-line block b
+    if (t == 0) {
+#pragma unroll 1
+        for (int b = 0; b < S::NB1; ++b)
+#pragma unroll 1
+            for (int term = 0; term < 3; ++term) {
+                const unsigned a0 = sbase + (term == 1 ? S::OFF_ALO : 0) + b * 16 * S::SBO1;
+                const unsigned b0 = sbase + S::OFF_B1 + (term == 2 ? S::B1BYTES : 0);
+#pragma unroll 1
+                for (int ks = 0; ks < S::K1 / 16; ++ks)
+                    tc_mma(tmem + b * S::K1, tc_desc(a0 + ks * 256, 128, S::SBO1), tc_desc(b0 + ks * 256, 128, S::SBO1),
+                           IDESC1, term > 0 || ks > 0);
+            }
+        tc_commit(bar);
+    }
+    bool ok = __syncthreads_and(mbar_wait_bounded(bar, 0) ? 1 : 0) != 0;
+    tc_fence_after();
+
+    // twiddle e^{+2 pi i n1 m2 / P} in FP32, split, and scatter as the
+    // stage-2 operand: line (m2, c) = m2 C + c, K position 2 n1 (+1)
+    if (ok && t < S::ROWS1) {
+        const int n1 = t / C, b = warp / 4;
+        float d[S::K1];
+        tc_ld<S::K1>(tmem + ((unsigned)((warp % 4) * 32) << 16) + (unsigned)(b * S::K1), d);
+#pragma unroll
+        for (int m2 = 0; m2 < R2; ++m2) {
+            float2 z = make_float2(d[2 * m2], d[2 * m2 + 1]);
+            if (m2 > 0) z = cmulc(z, __ldg(&tw[n1 * m2]));
+            unsigned h, l;
+            bf16_split(z, h, l);
+            const unsigned off = tc_koff(m2 * C + c, 2 * n1, S::SBO2);
+            *reinterpret_cast<unsigned *>(smem + off) = h;
+            *reinterpret_cast<unsigned *>(smem + S::OFF_ALO + off) = l;
+        }
+    }
+    fence_proxy_async();
+    tc_fence_before();
+    ok = __syncthreads_and(ok ? 1 : 0) != 0;
+    tc_fence_after();
+
+    // stage 2: D2[b] = A2 hi . B2 hi + A2 lo . B2 hi + A2 hi . B2 lo
+    if (ok && t == 0) {
+#pragma unroll 1
+        for (int b = 0; b < S::NB2; ++b)
+#pragma unroll 1
+            for (int term = 0; term < 3; ++term) {
+                const unsigned a0 = sbase + (term == 1 ? S::OFF_ALO : 0) + b * 16 * S::SBO2;
+                const unsigned b0 = sbase + S::OFF_B2 + (term == 2 ? S::B2BYTES : 0);
+#pragma unroll 1
+                for (int ks = 0; ks < S::K2 / 16; ++ks)
+                    tc_mma(tmem + b * S::K2, tc_desc(a0 + ks * 256, 128, S::SBO2), tc_desc(b0 + ks * 256, 128, S::SBO2),
+                           IDESC2, term > 0 || ks > 0);
+            }
+        tc_commit(bar);
+    }
+    if (ok) ok = __syncthreads_and(mbar_wait_bounded(bar, 1) ? 1 : 0) != 0;
+    tc_fence_after();
+
+    // outputs y(m2 + R2 m1), m1 < R1, of line (m2, c); keep the Q lags
+    if (ok && t < S::ROWS2) {
+        const int m2 = t / C, b = warp / 4;
+        float d[S::K2];
+        tc_ld<S::K2>(tmem + ((unsigned)((warp % 4) * 32) << 16) + (unsigned)(b * S::K2), d);
+        if (valid) {
+            float2 *dst = U4 + (long long)lx * g.Q * g.SP + c0 + c;
+#pragma unroll
+            for (int m1 = 0; m1 < R1; ++m1) {
+                const int l = lag_index(m2 + R2 * m1, R1 * R2, g.Q);
+                if (l >= 0) __stcs(dst + (long long)l * g.SP, make_float2(d[2 * m1], d[2 * m1 + 1]));
+            }
+        }
+    }
+    if (!ok && t == 0) atomicCAS(status, (unsigned)DEV_OK, (unsigned)DEV_ETIMEOUT);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tc_dealloc(tmem, S::COLS);
+}
+
+template <int P>
+cudaError_t launch_inv_y_tc_t(const Geom &g, const Work<float> &w, cudaStream_t s)
+{
+    constexpr int R1 = tc_r1(P), R2 = P / R1, C = tc_cols(P);
+    using S = TcInvY<R1, R2, C>;
+    auto k = k_inv_y_tc<R1, R2, C>;
+    static const cudaError_t e = smem_attrs(k, (size_t)S::SMEM);
+    if (e != cudaSuccess) return e;
+    if (w.tc == nullptr) return cudaErrorInvalidValue;
+    dim3 grid((g.H + C - 1) / C, g.Q);
+    k<<<grid, S::T, S::SMEM, s>>>(g, (const float2 *)w.X, (float2 *)w.Y, twiddles_for<float>(w, P),
+                                 reinterpret_cast<const uint4 *>(static_cast<const unsigned char *>(w.tc) +
+                                                                 tc_mats_offset(P)),
+                                 w.status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_inv_y_tc(const Geom &g, const Work<float> &w, cudaStream_t s)
+{
+    switch (g.P) {
+    case 128: return launch_inv_y_tc_t<128>(g, w, s);
+    case 192: return launch_inv_y_tc_t<192>(g, w, s);
+    case 256: return launch_inv_y_tc_t<256>(g, w, s);
+    case 384: return launch_inv_y_tc_t<384>(g, w, s);
+    case 512: return launch_inv_y_tc_t<512>(g, w, s);
+    case 768: return launch_inv_y_tc_t<768>(g, w, s);
+    case 1024: return launch_inv_y_tc_t<1024>(g, w, s);
+    case 1536: return launch_inv_y_tc_t<1536>(g, w, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace lh

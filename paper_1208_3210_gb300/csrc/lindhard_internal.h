@@ -77,6 +77,7 @@ struct Work {
     void *eps;             // energy table: float2 (hi, lo) or double, [n_eps]
     const void *tw;        // twiddle tables (see twiddles_for): float2 or double2
     int tw_len;            // longest transform length of the plan
+    const void *tc;        // tensor-core DFT matrices (k_tc.cu), or null
     InstState *state;      // [1]
     unsigned *status;      // plan-wide device status word
     double *mu_acc;        // scratch for the chemical potential solve

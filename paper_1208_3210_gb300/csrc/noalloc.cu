@@ -134,6 +134,7 @@ extern "C" lindhard_status lindhard_imchi_noalloc(const lindhard_grid *grid, con
     w.eps = base + off_eps;
     w.tw = base + off_tw32;
     w.tw_len = tw_len;
+    w.tc = nullptr;
     w.state = (InstState *)(base + off_state);
     w.status = (unsigned *)(base + off_status);
     w.mu_acc = (double *)(base + off_acc);

@@ -37,6 +37,9 @@ cudaError_t launch_fwd_y(const Geom &g, const Work<double> &w, cudaStream_t s, i
 cudaError_t launch_x_product(const Geom &g, const Work<float> &w, cudaStream_t s, int variant);
 cudaError_t launch_x_product(const Geom &g, const Work<double> &w, cudaStream_t s, int variant);
 cudaError_t launch_inv_y(const Geom &g, const Work<float> &w, cudaStream_t s, int variant);
+bool tc_supported(int P);
+size_t tc_mats_bytes();
+cudaError_t launch_tc_mats(void *buf, cudaStream_t s);
 cudaError_t launch_inv_y(const Geom &g, const Work<double> &w, cudaStream_t s, int variant);
 cudaError_t launch_inv_energy(const Geom &g, const Work<float> &w, float *out, cudaStream_t s, int variant);
 cudaError_t launch_inv_energy(const Geom &g, const Work<double> &w, double *out, cudaStream_t s, int variant);
@@ -88,7 +91,7 @@ static long long next_len(long long x)
 static long long next_len_p(long long x, int prec)
 {
     long long L = next_len(x);
-    if (prec == LINDHARD_FP32)
+    if (prec != LINDHARD_FP64)
         for (long long L3 = 48; L3 <= 1536; L3 <<= 1)
             if (L3 >= x && L3 < L) L = L3;
     return L;
@@ -107,7 +110,7 @@ struct lindhard_plan {
         size_t X = 0, Y = 0, Z = 0, partial = 0, axis = 0, eps32 = 0, eps64 = 0, state = 0, acc = 0, bar = 0;
     };
     std::vector<Slot> slots;
-    size_t off_tw32 = 0, off_tw64 = 0, off_status = 0;
+    size_t off_tw32 = 0, off_tw64 = 0, off_status = 0, off_tc = 0;
     int tw_len = 0;
     bool backward = false;       // LINDHARD_PLAN_BACKWARD
     // engine variants per instance, set by the autotuner
@@ -196,8 +199,8 @@ static lindhard_status make_geom(const lindhard_grid &gr, Geom &g, int &prec)
     if (gr.pts_per_zone < 2 || gr.pts_per_zone % 2) return fail(LINDHARD_EINVAL, "pts_per_zone must be even and >= 2");
     if (gr.n_eps < 2) return fail(LINDHARD_EINVAL, "n_eps must be >= 2");
     if (!(gr.e_max > 0) || !isfinite(gr.e_max)) return fail(LINDHARD_EINVAL, "e_max must be finite and > 0");
-    if (gr.precision != LINDHARD_FP32 && gr.precision != LINDHARD_FP64)
-        return fail(LINDHARD_EUNSUPPORTED, "precision must be LINDHARD_FP32 or LINDHARD_FP64");
+    if (gr.precision != LINDHARD_FP32 && gr.precision != LINDHARD_FP64 && gr.precision != LINDHARD_SPLITBF16_TC)
+        return fail(LINDHARD_EUNSUPPORTED, "precision must be LINDHARD_FP32, LINDHARD_SPLITBF16_TC or LINDHARD_FP64");
     long long N = (long long)gr.zones * gr.pts_per_zone;
     if (N > kMaxLen) return fail(LINDHARD_EUNSUPPORTED, "zones * pts_per_zone exceeds 4096");
     long long n_omega = gr.n_omega ? gr.n_omega : gr.n_eps / 2;
@@ -221,6 +224,9 @@ static lindhard_status make_geom(const lindhard_grid &gr, Geom &g, int &prec)
     long long PE = next_len(gr.n_eps);
     long long maxlen = gr.precision == LINDHARD_FP64 ? kMaxLen64 : kMaxLen;
     if (P > maxlen || PE > maxlen) return fail(LINDHARD_EUNSUPPORTED, "FFT length beyond the compiled range");
+    if (gr.precision == LINDHARD_SPLITBF16_TC && !tc_supported((int)P))
+        return fail(LINDHARD_EUNSUPPORTED, "no tensor-core form for this momentum FFT length "
+                                           "(128, 192, 256, 384, 512, 768, 1024, 1536)");
     g.N = (int)N;
     g.npz = gr.pts_per_zone;
     g.periodic = periodic;
@@ -316,7 +322,7 @@ static cudaError_t autotune(lindhard_plan *p)
     cudaEventCreate(&b);
     for (int i = 0; i < p->batch && e == cudaSuccess; ++i) {
         const Geom &g = p->geoms[i];
-        if (p->precision[i] != LINDHARD_FP32 || g.P < 128) continue;
+        if (p->precision[i] == LINDHARD_FP64 || g.P < 128) continue;
         std::ostringstream key;
         key << prop.name << "|P=" << g.P << "|N=" << g.N << "|PE=" << g.PE << "|Q=" << g.Q;
         const std::string kf = key.str() + "|fwd_y", ki = key.str() + "|inv_y", kx = key.str() + "|x_product",
@@ -353,7 +359,8 @@ static cudaError_t autotune(lindhard_plan *p)
             return g_tune[k];
         };
         p->yvar_fwd[i] = pick(kf, vy, [&](int v) { return launch_fwd_y(g, w, 0, v); });
-        p->yvar_inv[i] = pick(ki, vy, [&](int v) { return launch_inv_y(g, w, 0, v); });
+        if (p->precision[i] != LINDHARD_SPLITBF16_TC)
+            p->yvar_inv[i] = pick(ki, vy, [&](int v) { return launch_inv_y(g, w, 0, v); });
         p->xvar[i] = pick(kx, vx, [&](int v) { return launch_x_product(g, w, 0, v); });
         // the inverse energy pass writes the caller's output: time it into the
         // workspace's X buffer (at least as large as the output)
@@ -424,6 +431,11 @@ extern "C" lindhard_status lindhard_plan_create(const lindhard_grid *grids, int 
     p->off_tw32 = o; o = align_up(o + (size_t)twiddle_entries() * sizeof(float2));
     p->off_tw64 = o; o = align_up(o + (size_t)twiddle_entries() * sizeof(double2));
     p->off_status = o; o = align_up(o + sizeof(unsigned));
+    // tensor-core DFT matrices of every supported length (plans with a
+    // LINDHARD_SPLITBF16_TC grid only)
+    if (std::count(p->precision.begin(), p->precision.end(), (int)LINDHARD_SPLITBF16_TC) > 0) {
+        p->off_tc = o; o = align_up(o + tc_mats_bytes());
+    }
     auto place = [&](const Need &n) {
         lindhard_plan::Slot sl;
         sl.X = o; o = align_up(o + n.X);
@@ -462,6 +474,7 @@ extern "C" lindhard_status lindhard_plan_create(const lindhard_grid *grids, int 
         if (e == cudaSuccess) e = cudaMemset(p->ws + sl.bar, 0, mu_barrier_words() * sizeof(unsigned));
     if (e == cudaSuccess)
         e = launch_twiddles(p->tw_len, (float2 *)(p->ws + p->off_tw32), (double2 *)(p->ws + p->off_tw64), 0);
+    if (e == cudaSuccess && p->off_tc) e = launch_tc_mats(p->ws + p->off_tc, 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e == cudaSuccess && p->concurrent) {
         int ns = std::min(batch, 16);
@@ -476,6 +489,8 @@ extern "C" lindhard_status lindhard_plan_create(const lindhard_grid *grids, int 
     }
     p->yvar_fwd.assign(batch, 1);
     p->yvar_inv.assign(batch, 1);
+    for (int i = 0; i < batch; ++i)
+        if (p->precision[i] == LINDHARD_SPLITBF16_TC) p->yvar_inv[i] = 7;   // tensor-core inverse p_y pass
     p->xvar.assign(batch, 0);
     p->evar.assign(batch, 0);
     if (e == cudaSuccess && (flags & LINDHARD_PLAN_AUTOTUNE)) e = autotune(p);
@@ -564,6 +579,7 @@ static Work<Real> work_of(lindhard_plan *p, int i)
     w.eps = sizeof(Real) == 4 ? (void *)(p->ws + sl.eps32) : (void *)(p->ws + sl.eps64);
     w.tw = sizeof(Real) == 4 ? (const void *)(p->ws + p->off_tw32) : (const void *)(p->ws + p->off_tw64);
     w.tw_len = p->tw_len;
+    w.tc = p->off_tc ? (const void *)(p->ws + p->off_tc) : nullptr;
     w.state = (InstState *)(p->ws + sl.state);
     w.status = (unsigned *)(p->ws + p->off_status);
     w.mu_acc = (double *)(p->ws + sl.acc);
@@ -651,7 +667,7 @@ static lindhard_status forward_impl(lindhard_plan *p, const lindhard_band *bands
 {
     if (!p || !out) return fail(LINDHARD_EINVAL, "plan and out must be non-NULL");
     for (int i = 0; i < p->batch; ++i)
-        if (p->precision[i] != want_prec)
+        if ((p->precision[i] == LINDHARD_FP64) != (want_prec == LINDHARD_FP64))
             return fail(LINDHARD_EINVAL, "plan precision does not match the entry point");
     std::vector<Band> bs(p->batch);
     if (A_in == nullptr) {
@@ -785,7 +801,7 @@ extern "C" lindhard_status lindhard_sum_rule(lindhard_plan *p, int index, const 
 {
     if (!p || !out || !sum_q || !dos_corr) return fail(LINDHARD_EINVAL, "plan, out, sum_q, dos_corr must be non-NULL");
     if (index < 0 || index >= p->batch) return fail(LINDHARD_EINVAL, "index out of range");
-    if (p->precision[index] != LINDHARD_FP32) return fail(LINDHARD_EINVAL, "the sum rule reads FP32 outputs");
+    if (p->precision[index] == LINDHARD_FP64) return fail(LINDHARD_EINVAL, "the sum rule reads FP32 outputs");
     const Geom &g = p->geoms[index];
     if (g.Q != (g.periodic ? g.N : 2 * g.N))
         return fail(LINDHARD_EINVAL, "the sum rule needs every lag: q_extent = N (one zone) or 2N (several)");

@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "liblindhard.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOCONV, EUNSUPPORTED = range(7)
-FP32, FP64 = 0, 2
+FP32, SPLITBF16_TC, FP64 = 0, 1, 2
 PLAN_BACKWARD, PLAN_CONCURRENT, PLAN_GRAPH, PLAN_AUTOTUNE = 1, 2, 4, 8
 _STATUS_NAMES = {OK: "OK", EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", ETIMEOUT: "ETIMEOUT",
                  ENOCONV: "ENOCONV", EUNSUPPORTED: "EUNSUPPORTED"}

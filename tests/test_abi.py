@@ -59,7 +59,8 @@ def _create(lib, grid):
     (dict(zones=1, npz=32, n_eps=48, e_max=1.0, q_extent=34), 1),
     (dict(zones=64, npz=128, n_eps=48, e_max=1.0), 6),        # N beyond the compiled FFT range
     (dict(zones=2, npz=96, n_eps=48, e_max=1.0, precision=2), 6),  # FP64 only up to length 256
-    (dict(zones=2, npz=32, n_eps=48, e_max=1.0, precision=1), 6),
+    (dict(zones=2, npz=32, n_eps=48, e_max=1.0, precision=1), 6),  # no tensor-core form for P = 96
+    (dict(zones=2, npz=32, n_eps=48, e_max=1.0, precision=3), 6),  # no such precision
 ])
 def test_plan_rejects_bad_grids_on_host(lib, kw, expect):
     from paper_1208_3210_gb300 import lindhard as lh
@@ -69,6 +70,17 @@ def test_plan_rejects_bad_grids_on_host(lib, kw, expect):
     assert st == expect, lib.lindhard_last_error().decode()
     assert not h.value
     assert lib.lindhard_last_error().decode()
+
+
+def test_tensor_core_precision_rejects_backward_plans(lib):
+    # N = 128 pads to P = 192, a length with a tensor-core form; the backward
+    # pass is built for LINDHARD_FP32 only (checked before any CUDA call)
+    from paper_1208_3210_gb300 import lindhard as lh
+    g = lh.make_grid(2, 64, 16, 1.0, 0, 0, lh.SPLITBF16_TC)
+    h = ctypes.c_void_p()
+    st = lib.lindhard_plan_create(ctypes.byref(g), 1, lh.PLAN_BACKWARD, ctypes.byref(h))
+    assert st == lh.EUNSUPPORTED and not h.value
+    assert "backward" in lib.lindhard_last_error().decode()
 
 
 def test_null_arguments(lib):
