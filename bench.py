@@ -42,7 +42,7 @@ VARIANT_KERNELS = {
     "py_fwd": ["k_fwd_y", "k_fwd_y2", "k_fwd_y2 (12-value tiles)", "k_fwd_y_tma", "k_fwd_y_tma (12-value tiles)",
                "k_y_col_tma (forward)", "k_fwd_y2 (double-width tile)"],
     "py_inv": ["k_inv_y", "k_inv_y2", "k_inv_y2 (12-value tiles)", "k_inv_y_tma", "k_inv_y_tma (12-value tiles)",
-               "k_y_col_tma (inverse)", "k_inv_y2 (double-width tile)"],
+               "k_y_col_tma (inverse)", "k_inv_y2 (double-width tile)", "k_inv_y_tc (tensor cores)"],
     "px_product": ["k_x_product", "k_x_product (12-value tiles)", "k_x_product_tma",
                    "k_x_product_tma (12-value tiles)", "k_x_product (one more CTA per SM)",
                    "k_x_product (double-width tile)"],
@@ -62,6 +62,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip the plan-creation timing of engine variants (paired-column engine)")
+    ap.add_argument("--no-tc", action="store_true",
+                    help="skip the comparison with the tensor-core form (LINDHARD_SPLITBF16_TC)")
     ap.add_argument("--grid", default=None,
                     help="zones,npz,n_eps,e_max: replace the workload's grid (for profiling smaller cases)")
     return ap.parse_args()
@@ -228,6 +230,44 @@ def run_reference(args):
                              "sample": f"{per_step} uniformly drawn outputs per step, FP64 direct double sum"},
             "e2e": {"value": value, "unit": "outputs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def tensor_core_form(lh, grids, bands, out_fp32, steps, autotune, mu, stream):
+    """The same call with precision LINDHARD_SPLITBF16_TC (the inverse p_y pass
+    on the tensor cores): device time per call, the inverse p_y pass alone,
+    and the largest difference from the FP32 SIMT result, outside the timed
+    region of the FP32 form."""
+    import torch
+    tgrids = [dict(g, precision=lh.SPLITBF16_TC) for g in grids]
+    try:
+        tp = lh.Plan(tgrids, autotune=autotune)
+    except Exception as exc:   # no tensor-core form for this length
+        return {"unavailable": str(exc)}
+    tout = torch.empty(tp.out_elems(), dtype=torch.float32, device="cuda")
+    for _ in range(3):
+        tp.imchi(bands, out=tout, mu_out=mu)
+    tp.status()
+    tp.profile(True)
+    for _ in range(max(3, min(steps // 10, 50))):
+        tp.imchi(bands, out=tout, mu_out=mu)
+    pt = tp.pass_times()
+    tp.profile(False)
+    n = max(3, min(steps, 200))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(n):
+        tp.imchi(bands, out=tout, mu_out=mu)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    tp.status()
+    ms = e0.elapsed_time(e1) / n
+    diff = float((tout - out_fp32).abs().max() / out_fp32.abs().max().clamp_min(1e-30))
+    res = {"ms_per_step": ms, "value": tp.out_elems() / (ms * 1e-3), "steps": n,
+           "py_inv_ms": round(pt["py_inv"][0] / max(pt["py_inv"][1], 1), 5),
+           "max_rel_diff_vs_fp32": diff, "variants": tp.variants(0)}
+    tp.close()
+    return res
 
 
 def main():
@@ -417,6 +457,13 @@ def main():
         plain = {"ms_per_step": seq_ms, "value": outputs_per_step / world / (seq_ms * 1e-3),
                  "speedup_batched": seq_ms / step_ms, "max_rel_diff": diff}
     dom_kernel = (VARIANT_KERNELS[dom][variants[dom]] if dom in VARIANT_KERNELS else KERNEL_NAMES[dom])
+    tc = None
+    if not batched and not args.no_tc:
+        plan.imchi(bands, out=out, mu_out=mu)
+        tc = tensor_core_form(lh, grids, bands, out, args.steps, not args.no_autotune, mu, stream)
+        if "py_inv_ms" in tc:
+            tc["py_inv_ms_fp32"] = round(ptimes["py_inv"][0] / max(ptimes["py_inv"][1], 1), 5)
+            tc["py_inv_roofline_frac"] = pb["py_inv"] / (tc["py_inv_ms"] * 1e-3) / 1e9 / peak
 
     if rank == 0:
         line = {
@@ -448,6 +495,8 @@ def main():
         }
         if plain is not None:
             line["plain_sequential"] = plain
+        if tc is not None:
+            line["tensor_core"] = tc
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.workload)
         print(json.dumps(line), flush=True)
