@@ -33,9 +33,10 @@ sys.path.insert(0, ROOT)
 DEFAULT_WORKLOAD = "extended_256x256x256"
 FALLBACK_HBM_GBS = 6800.0
 PASS_FILES = {  # kernel sources of each timed pass (for traffic-record staleness)
-    "energy_fwd": ("k_forward.cu",), "py_fwd": ("k_forward.cu", "k_tma.cu"),
-    "px_product": ("k_product.cu", "k_tma.cu"), "py_inv": ("k_inverse.cu", "k_tma.cu"),
-    "energy_inv": ("k_inverse.cu", "k_tma.cu"),
+    "energy_fwd": ("k_forward.cu",), "py_fwd": ("k_forward.cu", "k_tma.cu", "tma.cuh", "async.cuh"),
+    "px_product": ("k_product.cu", "k_tma.cu", "tma.cuh", "async.cuh"),
+    "py_inv": ("k_inverse.cu", "k_tma.cu", "tma.cuh", "async.cuh"),
+    "energy_inv": ("k_inverse.cu", "k_tma.cu", "tma.cuh", "async.cuh"),
 }
 # kernel of each pass by engine variant (lindhard_plan_variants)
 VARIANT_KERNELS = {
@@ -62,6 +63,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip the plan-creation timing of engine variants (paired-column engine)")
+    ap.add_argument("--precision", choices=["fp32", "tc"], default="fp32",
+                    help="tc: grids with LINDHARD_SPLITBF16_TC (the inverse p_y pass on the tensor cores)")
     ap.add_argument("--no-tc", action="store_true",
                     help="skip the comparison with the tensor-core form (LINDHARD_SPLITBF16_TC)")
     ap.add_argument("--grid", default=None,
@@ -292,10 +295,14 @@ def main():
         dist.barrier()
 
     batched = args.workload.startswith("batched_")
+    prec = lh.SPLITBF16_TC if args.precision == "tc" else lh.FP32
+    if prec != lh.FP32:
+        args.no_tc = True   # the timed form is the tensor-core one already
     if batched:
         # independent instances of mixed size, one graph call per step
         count = int(args.workload.split("_")[1])
         grids, bands = wl.batched_workload(count)
+        grids = [dict(g, precision=prec) for g in grids]
         plan = lh.Plan(grids, graph=True, autotune=not args.no_autotune)
         args.no_cpu_baseline = True
     else:
@@ -306,7 +313,7 @@ def main():
             grid = wl.grid_params(int(z), int(npz), int(ne), float(em))
             args.workload = f"{args.workload} grid {args.grid}"
             args.no_cpu_baseline = True
-        grids, bands = [grid], [band]
+        grids, bands = [dict(grid, precision=prec)], [band]
         plan = lh.Plan(grids, autotune=not args.no_autotune)
     s = plan.sizes[0]
     out = torch.empty(plan.out_elems(), dtype=torch.float32, device="cuda")
@@ -371,11 +378,12 @@ def main():
     dev_outs = [out, torch.empty_like(out)]
     # a caller repeating the call replays it as a CUDA graph (LINDHARD_PLAN_GRAPH):
     # one graph plan per output buffer, so neither records again
-    e2e_plans = [plan, plan] if batched else [lh.Plan(grids, graph=True, autotune=not args.no_autotune)
-                                              for _ in range(2)]
+    e2e_plans = ([plan, lh.Plan(grids, graph=True, autotune=not args.no_autotune)] if batched else
+                 [lh.Plan(grids, graph=True, autotune=not args.no_autotune) for _ in range(2)])
     for b in range(2):
         for _ in range(3):
             e2e_plans[b].imchi(bands, out=dev_outs[b], mu_out=mu)
+        host_outs[b].copy_(dev_outs[b])
     torch.cuda.synchronize()
     copy_stream = torch.cuda.Stream()
     ready = [torch.cuda.Event() for _ in range(2)]
@@ -399,8 +407,8 @@ def main():
     barrier()
     for p_ in e2e_plans:
         p_.status()
-    if not batched:
-        for p_ in e2e_plans:
+    for p_ in e2e_plans:
+        if p_ is not plan:
             p_.close()
     del dev_outs[1]
 
@@ -469,7 +477,9 @@ def main():
         line = {
             "metric": "Im chi(q,w) outputs/s", "value": value, "unit": "outputs/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if prec == lh.FP32 else "f32, p_y inverse as bf16 hi/lo products (f32 accumulation)",
+            "data": "synthetic",
             "config": {"workload": args.workload,
                        "grid": f"{len(grids)} instances" if batched else f"{s.N}x{s.N} p x {s.n_eps} e",
                        "fft": "mixed" if batched else f"{s.fft_p}x{s.fft_p}x{s.fft_e}",
@@ -477,6 +487,7 @@ def main():
                        "l2": "no flush: each step streams {:.2f} GB of intermediates through HBM, "
                              "far above the 129 MB L2".format(pipeline_bytes / 1e9),
                        "autotune": not args.no_autotune,
+                       "precision": args.precision,
                        "variants": variants,
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "roofline": {"bound": "hbm", "kernel": dom_kernel, "achieved": achieved, "peak": peak,

@@ -358,16 +358,25 @@ k_inv_y_tc(Geom g, const __grid_constant__ CUtensorMap map, float2 *__restrict__
         }
     };
     // stage-2 operand from the stage-1 accumulators: twiddle e^{+2 pi i n1 m2 / P}
-    // in FP32, split, scatter to line (m2, c) = m2 C + c at K position 2 n1
+    // in FP32, split, scatter to line (m2, c) = m2 C + c at K position 2 n1.
+    // The twiddles are powers of w = e^{-2 pi i n1 / P}: read from the table
+    // every 8th power and advanced by one complex product in between (at
+    // most 7 roundings, about 1e-6, well below the BF16 split's 2^-16), so
+    // that a tile waits on 3 table reads per line instead of R2 - 1.
     auto operand2 = [&](int part) {
         if (t < S::ROWS1) {
             const int n1 = t / C, b = warp / 4;
+            const float2 w1 = __ldg(&tw[n1]);
             float d[S::K1];
             tc_ld<S::K1>(tmem + ((unsigned)((warp % 4) * 32) << 16) + (unsigned)(b * S::K1), d);
+            float2 wp = make_float2(1.f, 0.f);
 #pragma unroll
             for (int m2 = 0; m2 < R2; ++m2) {
                 float2 z = make_float2(d[2 * m2], d[2 * m2 + 1]);
-                if (m2 > 0) z = cmulc(z, __ldg(&tw[n1 * m2]));
+                if (m2 > 0) {
+                    wp = (m2 % 8 == 0) ? __ldg(&tw[n1 * m2]) : cmul(wp, w1);
+                    z = cmulc(z, wp);
+                }
                 unsigned h, l;
                 bf16_split(z, h, l);
                 const unsigned off = tc_koff(m2 * C + c, 2 * n1, S::SBO2);
