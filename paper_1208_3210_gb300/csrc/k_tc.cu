@@ -173,9 +173,11 @@ struct TcInvY {
     static constexpr int MAT_BYTES = 2 * B1BYTES + 2 * B2BYTES;
     static constexpr int OFF_BAR = OFF_B1 + MAT_BYTES;
     static constexpr int SMEM = OFF_BAR + 32;
-    // SEQ re-reads the stage-1 accumulators for the lo part: separate columns
-    static constexpr int D2COL = SEQ ? NB1 * K1 : 0;
-    static constexpr int DCOLS = SEQ ? NB1 * K1 + NB2 * K2 : (NB1 * K1 > NB2 * K2 ? NB1 * K1 : NB2 * K2);
+    // stage-2 accumulators in their own columns: a tile's results are read
+    // out while the next tile's stage-1 products run (and SEQ re-reads the
+    // stage-1 accumulators for the lo part)
+    static constexpr int D2COL = NB1 * K1;
+    static constexpr int DCOLS = NB1 * K1 + NB2 * K2;
     static constexpr int COLS = DCOLS <= 32 ? 32 : DCOLS <= 64 ? 64 : DCOLS <= 128 ? 128 : DCOLS <= 256 ? 256 : 512;
     // CTAs per SM (up to 4) that shared memory (228 KB, 1 KB reserved per
     // CTA), tensor memory (512 columns) and the registers a thread keeps live
@@ -386,8 +388,27 @@ k_inv_y_tc(Geom g, const __grid_constant__ CUtensorMap map, float2 *__restrict__
         }
     };
 
-    for (int tile = run.t; tile < run.end; tile += run.step) {
+    // outputs y(m2 + R2 m1), m1 < R1, of line (m2, c) of a finished tile; keep the Q lags
+    auto outputs = [&](int tile) {
         const int lx = tile / tiles_x, c0 = (tile % tiles_x) * C;
+        if (t < S::ROWS2) {
+            const int m2 = t / C, b = warp / 4;
+            float d[S::K2];
+            tc_ld<S::K2>(tmem + ((unsigned)((warp % 4) * 32) << 16) + (unsigned)(S::D2COL + b * S::K2), d);
+            if (c0 + c < g.H) {
+                float2 *dst = U4 + (long long)lx * g.Q * g.SP + c0 + c;
+#pragma unroll
+                for (int m1 = 0; m1 < R1; ++m1) {
+                    const int l = lag_index(m2 + R2 * m1, S::P, g.Q);
+                    if (l >= 0) __stcs(dst + (long long)l * g.SP, make_float2(d[2 * m1], d[2 * m1 + 1]));
+                }
+            }
+        }
+        tc_fence_before();
+    };
+
+    int prev = -1;   // tile whose stage-2 results wait in tensor memory
+    for (int tile = run.t; tile < run.end; tile += run.step) {
         if (!tile_ready(bar_t, pt, status)) { ok = false; break; }
         pt ^= 1u;
         inflight = false;
@@ -401,6 +422,9 @@ k_inv_y_tc(Geom g, const __grid_constant__ CUtensorMap map, float2 *__restrict__
             tc_commit(bar_m);
         }
         if (!SEQ) inflight = more;
+        // the previous tile's results leave while these products run
+        if (prev >= 0) outputs(prev);
+        prev = -1;
         if (!products_done()) break;
         if constexpr (SEQ) {
             operand1(2);
@@ -430,22 +454,9 @@ k_inv_y_tc(Geom g, const __grid_constant__ CUtensorMap map, float2 *__restrict__
             }
             if (!products_done()) break;
         }
-        // outputs y(m2 + R2 m1), m1 < R1, of line (m2, c); keep the Q lags
-        if (t < S::ROWS2) {
-            const int m2 = t / C, b = warp / 4;
-            float d[S::K2];
-            tc_ld<S::K2>(tmem + ((unsigned)((warp % 4) * 32) << 16) + (unsigned)(S::D2COL + b * S::K2), d);
-            if (c0 + c < g.H) {
-                float2 *dst = U4 + (long long)lx * g.Q * g.SP + c0 + c;
-#pragma unroll
-                for (int m1 = 0; m1 < R1; ++m1) {
-                    const int l = lag_index(m2 + R2 * m1, S::P, g.Q);
-                    if (l >= 0) __stcs(dst + (long long)l * g.SP, make_float2(d[2 * m1], d[2 * m1 + 1]));
-                }
-            }
-        }
-        tc_fence_before();
+        prev = tile;
     }
+    if (ok && prev >= 0) outputs(prev);
     // a copy still in flight after a timeout lands before the CTA leaves
     if (!ok && inflight) drain(bar_t, pt);
     tc_fence_before();
