@@ -56,6 +56,10 @@ def _load():
             lib.lo_spectral.restype = None
             lib.lo_spectral.argtypes = ([ctypes.c_int] + [ctypes.c_double] * 6
                                         + [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, _dp])
+            lib.lo_kk_real.restype = None
+            lib.lo_kk_real.argtypes = [ctypes.c_long, ctypes.c_int, _dp, _dp]
+            lib.lo_rpa.restype = None
+            lib.lo_rpa.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, _dp, _dp, _dp]
             lib.lo_imchi_samples.restype = None
             lib.lo_imchi_samples.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, _dp,
                                              ctypes.c_int, ctypes.c_long, _ip, _ip, _ip, _dp]
@@ -77,6 +81,28 @@ def _d(a):
 
 def _i(a):
     return a.ctypes.data_as(_ip)
+
+
+def kk_real(im: np.ndarray) -> np.ndarray:
+    """Re chi from Im chi along the last axis (transfers w_m = m de) by the
+    Kramers-Kronig relation of Sec. 4 in Maclaurin's discretisation (odd Im chi
+    in w, zero beyond the window); see lo_kk_real."""
+    im = np.ascontiguousarray(im, dtype=np.float64)
+    n_omega = im.shape[-1]
+    out = np.empty_like(im)
+    _load().lo_kk_real(ctypes.c_long(im.size // n_omega), n_omega, _d(im), _d(out))
+    return out
+
+
+def rpa(re: np.ndarray, im: np.ndarray, dp: float, v0: float) -> np.ndarray:
+    """chi_RPA = chi / (1 - V_q chi), V_q = v0 / |q|^2 (Sec. 4), for chi on the
+    lag grid [Q][Q][n_omega]; returns [Q][Q][n_omega] complex."""
+    re = np.ascontiguousarray(re, dtype=np.float64)
+    im = np.ascontiguousarray(im, dtype=np.float64)
+    Q, _, n_omega = re.shape
+    out = np.empty(re.shape + (2,), dtype=np.float64)
+    _load().lo_rpa(Q, n_omega, float(dp), float(v0), _d(re), _d(im), _d(out))
+    return out[..., 0] + 1j * out[..., 1]
 
 
 def num_threads() -> int:

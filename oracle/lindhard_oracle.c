@@ -250,6 +250,62 @@ void lo_spectral_dtheta(double t, double tp, double tpp, double mu,
         }
 }
 
+/* Real part of chi by the Kramers-Kronig relation (Sec. 4: "the real part of
+ * the Lindhard susceptibility ... by applying Kramers-Kronig relation"):
+ *   Re chi(w) = (1/pi) P Int Im chi(w') / (w' - w) dw'
+ * over the whole line, with Im chi(q, -w) = -Im chi(q, w) (the bands of this
+ * problem have A(-p, e) = A(p, e), so chi(-q) = chi(q)), on the transfer grid
+ * w_k = k de, k < n_omega (Im chi taken as zero beyond the computed window).
+ * The principal value is Maclaurin's rule on a uniform grid:
+ *   P Int g(t) / (t - x_m) dt ~ 2 h sum_{k - m odd} g(t_k) / (t_k - x_m),
+ * and folding the negative transfers onto the positive ones gives
+ *   Re chi_m = (4/pi) sum_{k >= 1, k - m odd} k Im chi_k / (k^2 - m^2).
+ * im, re: [n_lines][n_omega]. */
+void lo_kk_real(long n_lines, int n_omega, const double *im, double *re)
+{
+#pragma omp parallel for schedule(static)
+    for (long l = 0; l < n_lines; ++l) {
+        const double *x = im + l * n_omega;
+        for (int m = 0; m < n_omega; ++m) {
+            double s = 0.0;
+            for (int k = 1; k < n_omega; ++k)
+                if ((k - m) % 2 != 0)
+                    s += (double)k * x[k] / ((double)k * k - (double)m * m);
+            re[l * n_omega + m] = 4.0 / LO_PI * s;
+        }
+    }
+}
+
+/* RPA susceptibility (Sec. 4): chi_RPA = chi / (1 - V_q chi), with the Coulomb
+ * interaction V_q = v0 / |q|^2 (the paper gives only its 1/q^2 decay; v0 in
+ * eV a^2, lattice constant a = 1).  chi = re + i im at lag (l_x, l_y),
+ * q = ((l_x - Q/2) dp, (l_y - Q/2) dp).  At q = 0, V is infinite and chi_RPA
+ * takes its limit 0 (v0 = 0: no interaction, chi_RPA = chi everywhere).
+ * out: [Q][Q][n_omega][2] (re, im). */
+void lo_rpa(int Q, int n_omega, double dp, double v0, const double *re, const double *im, double *out)
+{
+#pragma omp parallel for schedule(static)
+    for (long l = 0; l < (long)Q * Q; ++l) {
+        const double qx = (double)(l / Q - Q / 2) * dp, qy = (double)(l % Q - Q / 2) * dp;
+        const double q2 = qx * qx + qy * qy;
+        for (int m = 0; m < n_omega; ++m) {
+            const long at = l * n_omega + m;
+            if (q2 == 0.0 && v0 != 0.0) {
+                out[2 * at] = 0.0;
+                out[2 * at + 1] = 0.0;
+                continue;
+            }
+            const double V = v0 == 0.0 ? 0.0 : v0 / q2;
+            const double a = re[at], b = im[at];
+            /* (a + i b) / (1 - V a - i V b) */
+            const double dr = 1.0 - V * a, di = -V * b;
+            const double den = dr * dr + di * di;
+            out[2 * at] = (a * dr + b * di) / den;
+            out[2 * at + 1] = (b * dr - a * di) / den;
+        }
+    }
+}
+
 int lo_num_threads(void)
 {
 #ifdef _OPENMP

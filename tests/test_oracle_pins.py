@@ -307,3 +307,64 @@ def test_grad_params_central_difference():
         fd = (oracle.loss(oracle.spectral(bp, grid), grid, Q, w)
               - oracle.loss(oracle.spectral(bm, grid), grid, Q, w)) / (2 * h)
         assert g[r] == pytest.approx(fd, rel=2e-5, abs=1e-9 * abs(fd) + 1e-12)
+
+
+# --- Kramers-Kronig real part and RPA (Sec. 4) -----------------------------------
+
+def _oscillator(w, w0, gamma, s=1.0):
+    """A causal response with its poles in the lower half plane:
+    chi(w) = -s / (w0^2 - w^2 - i gamma w), Im chi < 0 for w > 0 (the sign of
+    Im chi of Eq. 9); its real part is fixed by analyticity."""
+    d = (w0 ** 2 - w ** 2) ** 2 + (gamma * w) ** 2
+    return -s * (w0 ** 2 - w ** 2) / d, -s * gamma * w / d
+
+
+@pytest.mark.parametrize("gamma", [0.2, 0.5])
+def test_kk_reproduces_the_real_part_of_a_causal_response(gamma):
+    # Re chi from Im chi alone against the closed form.  Maclaurin's rule
+    # converges faster than any power of the step for an analytic response, so
+    # what remains is the window's tail, (2/pi) Int_W^inf Im chi(w')/w' dw' ~
+    # (2/pi) gamma / (3 W^3): doubling the window W cuts it about eightfold.
+    def err(h, W):
+        w = np.arange(int(round(W / h))) * h
+        re_ref, im = _oscillator(w, 1.0, gamma)
+        re = oracle.kk_real(im[None, :])[0]
+        keep = w <= 3.0
+        return np.abs(re[keep] - re_ref[keep]).max() / np.abs(re_ref[keep]).max()
+    e40, e80 = err(0.01, 40.0), err(0.01, 80.0)
+    tail = 2.0 / math.pi * gamma / (3 * 40.0 ** 3)
+    assert e40 < 2 * tail + 1e-7, (e40, tail)
+    assert e80 < e40 / 4, (e40, e80)
+    assert err(0.04, 40.0) < 1e-3
+
+
+def test_kk_static_lindhard_response_is_negative():
+    # Re chi(q, 0) = (4/pi) sum_{k odd} Im chi_k / k with Im chi <= 0 (Eq. 9):
+    # the static Lindhard response is negative wherever Im chi is not zero
+    grid = _grid(2, 12, 32, 1.5)
+    b = _band(oracle.solve_mu(0, T, TP, TPP, 0.08, 12, 1.1), 0.08, 1.0)
+    A = oracle.spectral(b, grid)
+    im = oracle.imchi_full(A, grid, 24, 16)
+    re = oracle.kk_real(im)
+    assert (re[:, :, 0] <= 0).all()
+    assert re[:, :, 0].min() < 0
+
+
+def test_rpa_shifts_the_pole_to_the_plasmon_frequency():
+    # chi_L = -s / (w0^2 - w^2 - i g w) gives chi_RPA = chi_L / (1 - V chi_L)
+    # = -s / (w0^2 + V s - w^2 - i g w): the peak of -Im chi_RPA moves from w0
+    # to sqrt(w0^2 + V s) (the plasmon of Sec. 4), with V = v0 / |q|^2.
+    h, w0, g, s, v0, dp = 0.002, 1.0, 0.02, 1.0, 1.25, 1.0
+    w = np.arange(int(round(20.0 / h))) * h
+    _, im1 = _oscillator(w, w0, g, s)
+    Q = 2
+    im = np.broadcast_to(im1, (Q, Q, w.size)).copy()
+    re = oracle.kk_real(im)
+    chi = oracle.rpa(re, im, dp, v0)
+    # lag (1, 0): q = (0, -dp), V = v0 / dp^2; lag (0, 0): q = (-dp, -dp), V = v0 / (2 dp^2)
+    for (lx, ly), V in (((1, 0), v0 / dp ** 2), ((0, 0), v0 / (2 * dp ** 2))):
+        peak = w[np.argmax(-chi[lx, ly].imag)]
+        assert abs(peak - math.sqrt(w0 ** 2 + V * s)) < 5 * h, (lx, ly, peak)
+    assert np.all(chi[1, 1] == 0)                     # q = 0: V infinite, chi_RPA -> 0
+    same = oracle.rpa(re, im, dp, 0.0)                # no interaction: chi_RPA = chi_L
+    assert np.array_equal(same, re + 1j * im)
