@@ -239,6 +239,26 @@ lindhard_status lindhard_sum_rule(lindhard_plan *plan, int index, const lindhard
                                   const float *A_in, const float *out, double *sum_q, double *dos_corr,
                                   void *stream);
 
+/* Real part of chi by the Kramers-Kronig relation and the RPA susceptibility
+ * (Sec. 4): for instance `index`,
+ *   Re chi(q, w_m) = sum_k W(m, k) Im chi(q, w_k),
+ *   W(m, k) = (4/pi) k / (k^2 - m^2) for k >= 1 with k - m odd, else 0
+ * (the principal value by Maclaurin's rule on the transfer grid, Im chi odd
+ * in w, zero beyond the n_omega computed transfers), and
+ *   chi_RPA = chi / (1 - V_q chi),  chi = Re chi + i Im chi,  V_q = v0 / |q|^2,
+ * q = ((l_x - Q/2) dp, (l_y - Q/2) dp), v0 in eV (lattice constant 1); at
+ * q = 0 chi_RPA is 0 (its limit), unless v0 = 0 (then chi_RPA = chi).
+ * imchi: device, the instance's [Q][Q][n_omega] block as lindhard_imchi wrote
+ * it.  re_out: device [Q][Q][n_omega].  rpa_out: device [Q][Q][n_omega][2]
+ * (re, im; 8-byte aligned), or NULL.  variant 0: the far field |k - m| >= 8
+ * on the tensor cores (BF16 hi/lo, three products, FP32 accumulation) and the
+ * near band in FP32, n_omega <= 256; variant 1: FP32 SIMT throughout,
+ * n_omega <= 1536 (otherwise LINDHARD_EUNSUPPORTED).  Plans whose grid is
+ * LINDHARD_FP64 are rejected (LINDHARD_EINVAL).  Enqueued on `stream`; no
+ * synchronisation. */
+lindhard_status lindhard_kk_rpa(lindhard_plan *plan, int index, const float *imchi, float *re_out,
+                                float *rpa_out, double v0, int variant, void *stream);
+
 /* Engine variants the plan runs for instance `index` (set by
  * LINDHARD_PLAN_AUTOTUNE, else the defaults): out[0], out[1] = forward and
  * inverse passes along p_y (0 single-column engine, 1 paired columns,

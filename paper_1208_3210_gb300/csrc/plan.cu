@@ -38,6 +38,10 @@ cudaError_t launch_x_product(const Geom &g, const Work<float> &w, cudaStream_t s
 cudaError_t launch_x_product(const Geom &g, const Work<double> &w, cudaStream_t s, int variant);
 cudaError_t launch_inv_y(const Geom &g, const Work<float> &w, cudaStream_t s, int variant);
 bool tc_supported(int P);
+size_t kk_table_bytes(int nw);
+cudaError_t launch_kk_tables(int nw, void *tab, cudaStream_t s);
+cudaError_t launch_kk_rpa(const Geom &g, const float *im, float *re, float2 *rpa, const void *tab, double v0,
+                          int variant, unsigned *status, cudaStream_t s);
 size_t tc_mats_bytes();
 cudaError_t launch_tc_mats(void *buf, cudaStream_t s);
 cudaError_t launch_inv_y(const Geom &g, const Work<double> &w, cudaStream_t s, int variant);
@@ -111,6 +115,7 @@ struct lindhard_plan {
     };
     std::vector<Slot> slots;
     size_t off_tw32 = 0, off_tw64 = 0, off_status = 0, off_tc = 0;
+    std::vector<size_t> off_kk;   // Kramers-Kronig weight tables per instance (FP32 grids)
     int tw_len = 0;
     bool backward = false;       // LINDHARD_PLAN_BACKWARD
     // engine variants per instance, set by the autotuner
@@ -436,6 +441,11 @@ extern "C" lindhard_status lindhard_plan_create(const lindhard_grid *grids, int 
     if (std::count(p->precision.begin(), p->precision.end(), (int)LINDHARD_SPLITBF16_TC) > 0) {
         p->off_tc = o; o = align_up(o + tc_mats_bytes());
     }
+    p->off_kk.assign(batch, 0);
+    for (int i = 0; i < batch; ++i)
+        if (p->precision[i] != LINDHARD_FP64) {
+            p->off_kk[i] = o; o = align_up(o + kk_table_bytes(p->geoms[i].n_omega));
+        }
     auto place = [&](const Need &n) {
         lindhard_plan::Slot sl;
         sl.X = o; o = align_up(o + n.X);
@@ -475,6 +485,8 @@ extern "C" lindhard_status lindhard_plan_create(const lindhard_grid *grids, int 
     if (e == cudaSuccess)
         e = launch_twiddles(p->tw_len, (float2 *)(p->ws + p->off_tw32), (double2 *)(p->ws + p->off_tw64), 0);
     if (e == cudaSuccess && p->off_tc) e = launch_tc_mats(p->ws + p->off_tc, 0);
+    for (int i = 0; i < batch && e == cudaSuccess; ++i)
+        if (p->off_kk[i]) e = launch_kk_tables(p->geoms[i].n_omega, p->ws + p->off_kk[i], 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e == cudaSuccess && p->concurrent) {
         int ns = std::min(batch, 16);
@@ -824,6 +836,25 @@ extern "C" lindhard_status lindhard_sum_rule(lindhard_plan *p, int index, const 
     if (e == cudaSuccess)
         e = launch_sum_rule(g, b, w.axis, (const float2 *)w.eps, w.state, A_in, out, D, sum_q, dos_corr, s);
     return e == cudaSuccess ? LINDHARD_OK : cuda_fail(e, "sum-rule launch");
+}
+
+extern "C" lindhard_status lindhard_kk_rpa(lindhard_plan *p, int index, const float *imchi, float *re_out,
+                                           float *rpa_out, double v0, int variant, void *stream)
+{
+    if (!p || !imchi || !re_out) return fail(LINDHARD_EINVAL, "plan, imchi and re_out must be non-NULL");
+    if (index < 0 || index >= p->batch) return fail(LINDHARD_EINVAL, "index out of range");
+    if (p->precision[index] == LINDHARD_FP64) return fail(LINDHARD_EINVAL, "the Kramers-Kronig pass reads FP32 outputs");
+    if (variant != 0 && variant != 1) return fail(LINDHARD_EINVAL, "variant must be 0 (tensor cores) or 1 (FP32 SIMT)");
+    if (!isfinite(v0)) return fail(LINDHARD_EINVAL, "v0 must be finite");
+    const Geom &g = p->geoms[index];
+    if (g.n_omega > (variant == 0 ? 256 : 1536))
+        return fail(LINDHARD_EUNSUPPORTED, variant == 0 ? "the tensor-core form takes n_omega <= 256"
+                                                        : "the SIMT form takes n_omega <= 1536");
+    if (rpa_out && (reinterpret_cast<uintptr_t>(rpa_out) & 7u))
+        return fail(LINDHARD_EINVAL, "rpa_out must be 8-byte aligned");
+    cudaError_t e = launch_kk_rpa(g, imchi, re_out, reinterpret_cast<float2 *>(rpa_out), p->ws + p->off_kk[index], v0,
+                                  variant, (unsigned *)(p->ws + p->off_status), (cudaStream_t)stream);
+    return e == cudaSuccess ? LINDHARD_OK : cuda_fail(e, "Kramers-Kronig launch");
 }
 
 extern "C" lindhard_status lindhard_plan_profile_passes(lindhard_plan *p, unsigned mask)

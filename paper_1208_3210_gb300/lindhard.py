@@ -25,7 +25,7 @@ _STATUS_NAMES = {OK: "OK", EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", E
 SYMBOLS = ("lindhard_plan_create", "lindhard_plan_sizes", "lindhard_plan_workspace_bytes", "lindhard_imchi",
            "lindhard_imchi_f64", "lindhard_imchi_backward", "lindhard_plan_profile", "lindhard_plan_profile_passes",
            "lindhard_plan_pass_times",
-           "lindhard_sum_rule", "lindhard_plan_variants", "lindhard_plan_status", "lindhard_plan_destroy",
+           "lindhard_sum_rule", "lindhard_kk_rpa", "lindhard_plan_variants", "lindhard_plan_status", "lindhard_plan_destroy",
            "lindhard_imchi_noalloc", "lindhard_last_error")
 NOALLOC_SCRATCH_BYTES = 32 << 20
 NUM_PASSES = 7
@@ -86,6 +86,8 @@ def load(path: str = LIB_PATH):
         lib.lindhard_imchi_noalloc.restype = ctypes.c_int
         lib.lindhard_sum_rule.argtypes = [vp, ctypes.c_int, ctypes.POINTER(Band), vp, vp, vp, vp, vp]
         lib.lindhard_sum_rule.restype = ctypes.c_int
+        lib.lindhard_kk_rpa.argtypes = [vp, ctypes.c_int, vp, vp, vp, ctypes.c_double, ctypes.c_int, vp]
+        lib.lindhard_kk_rpa.restype = ctypes.c_int
         for name in ("lindhard_plan_create", "lindhard_plan_sizes", "lindhard_plan_workspace_bytes",
                      "lindhard_imchi", "lindhard_imchi_f64", "lindhard_imchi_backward", "lindhard_plan_profile",
                      "lindhard_plan_pass_times", "lindhard_plan_status"):
@@ -234,6 +236,23 @@ class Plan:
         _check(load().lindhard_sum_rule(self._h, int(index), None if b is None else ctypes.byref(b), _ptr(A_in),
                                         _ptr(out_i), _ptr(sq), _ptr(dc), _stream(stream)))
         return sq, dc
+
+    def kk_rpa(self, out_i, index=0, v0=0.0, rpa=True, variant=0, stream=None):
+        """Re chi by Kramers-Kronig and chi_RPA = chi / (1 - v0/|q|^2 chi) for
+        instance `index` from its Im chi block `out_i` (device float32
+        [Q][Q][n_omega] or flat).  variant 0: tensor cores (n_omega <= 256);
+        1: FP32 SIMT.  Returns (Re chi, chi_RPA as complex64 or None), shaped
+        [Q][Q][n_omega]."""
+        import torch
+        s = self.sizes[index]
+        shape = (s.q_extent, s.q_extent, s.n_omega)
+        assert out_i.dtype == torch.float32 and out_i.is_cuda and out_i.is_contiguous()
+        assert out_i.numel() == s.out_elems
+        re = torch.empty(shape, dtype=torch.float32, device="cuda")
+        rp = torch.empty(shape + (2,), dtype=torch.float32, device="cuda") if rpa else None
+        _check(load().lindhard_kk_rpa(self._h, int(index), _ptr(out_i), _ptr(re), _ptr(rp), float(v0), int(variant),
+                                      _stream(stream)))
+        return re, (torch.view_as_complex(rp) if rpa else None)
 
     def status(self, stream=None):
         _check(load().lindhard_plan_status(self._h, _stream(stream)))

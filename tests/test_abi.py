@@ -88,4 +88,5 @@ def test_null_arguments(lib):
     assert lib.lindhard_plan_create(None, 1, 0, ctypes.byref(h)) == 1
     assert lib.lindhard_imchi(None, None, None, None, None, None) == 1
     assert lib.lindhard_plan_status(None, None) == 1
+    assert lib.lindhard_kk_rpa(None, 0, None, None, None, 0.0, 0, None) == 1
     lib.lindhard_plan_destroy(None)
