@@ -273,6 +273,40 @@ def tensor_core_form(lh, grids, bands, out_fp32, steps, autotune, mu, stream):
     return res
 
 
+def kk_rpa_form(plan, out, steps, stream, peak, v0=0.05):
+    """The Kramers-Kronig real part and chi_RPA (lindhard_kk_rpa, V_q = v0/|q|^2)
+    of the instance's Im chi, both forms: device time per call, HBM bytes
+    (Im chi read, Re chi and chi_RPA written) over that time, and the largest
+    difference between the forms; outside the timed region of the forward call."""
+    import torch
+    s = plan.sizes[0]
+    nbytes = 16 * s.q_extent * s.q_extent * s.n_omega
+    res = {"v0_ev": v0, "bytes_per_call": nbytes}
+    outs = {}
+    for v, name in ((0, "tensor_core"), (1, "fp32_simt")):
+        try:
+            plan.kk_rpa(out, v0=v0, variant=v)
+        except Exception as exc:
+            res[name] = {"unavailable": str(exc)}
+            continue
+        n = max(3, min(steps, 200))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(n):
+            r = plan.kk_rpa(out, v0=v0, variant=v)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        plan.status()
+        ms = e0.elapsed_time(e1) / n
+        outs[v] = r[0]
+        res[name] = {"ms": ms, "gbs": nbytes / (ms * 1e-3) / 1e9, "frac_of_hbm_peak": nbytes / (ms * 1e-3) / 1e9 / peak,
+                     "calls": n}
+    if 0 in outs and 1 in outs:
+        res["max_rel_diff_tc_vs_fp32"] = float((outs[0] - outs[1]).abs().max() / outs[1].abs().max().clamp_min(1e-30))
+    return res
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
@@ -466,8 +500,10 @@ def main():
                  "speedup_batched": seq_ms / step_ms, "max_rel_diff": diff}
     dom_kernel = (VARIANT_KERNELS[dom][variants[dom]] if dom in VARIANT_KERNELS else KERNEL_NAMES[dom])
     tc = None
+    kk = None
     if not batched and not args.no_tc:
         plan.imchi(bands, out=out, mu_out=mu)
+        kk = kk_rpa_form(plan, out, args.steps, stream, peak)
         tc = tensor_core_form(lh, grids, bands, out, args.steps, not args.no_autotune, mu, stream)
         if "py_inv_ms" in tc:
             tc["py_inv_ms_fp32"] = round(ptimes["py_inv"][0] / max(ptimes["py_inv"][1], 1), 5)
@@ -508,6 +544,8 @@ def main():
             line["plain_sequential"] = plain
         if tc is not None:
             line["tensor_core"] = tc
+        if kk is not None:
+            line["kk_rpa"] = kk
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.workload)
         print(json.dumps(line), flush=True)

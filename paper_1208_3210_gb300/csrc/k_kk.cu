@@ -107,22 +107,40 @@ __device__ __forceinline__ float kk_vq(long long l, int Q, double dp, double v0,
 }
 
 // ---------------------------------------------------------------------------
-// Tensor-core form.  Shared memory: [A hi][A lo] (one parity's operand, 128
-// lines x KP) [Be hi][Be lo][Bo hi][Bo lo] [mbarrier][tensor-memory address].
+// Tensor-core form.  One CTA of 256 threads per block of 128 lines (persistent
+// over blocks).  Shared memory: [work][Be hi][Be lo][Bo hi][Bo lo][mbarrier]
+// [tensor-memory address]; the work region holds one parity's operand (hi,
+// lo: 128 lines x KP) while the products run, then the epilogue's chunks.
+//   operand: each warp reads whole rows of Im chi (32 consecutive transfers
+//            per load, coalesced) and pairs neighbouring elements of one
+//            parity with a shuffle before the BF16 split;
+//   epilogue, per chunk of 32 transfers: the accumulators of the 128 lines go
+//            to shared memory (transposed), the chunk's Im chi with a halo
+//            of 8 is loaded row by row, and the lanes run along the
+//            transfers for the near band, chi_RPA and the stores (coalesced).
+// The next block's rows are prefetched into L2 (cp.async.bulk.prefetch).
 template <int KP>
 struct KkTc {
-    static constexpr int T = 128;
+    static constexpr int T = 256, CH = 32, HALO = 8;
     static constexpr int SBO = KP / 8 * 128;
     static constexpr int ABYTES = 128 * KP * 2, BBYTES = KP * KP * 2;
-    static constexpr int OFF_B = 2 * ABYTES, OFF_BAR = OFF_B + 4 * BBYTES;
+    static constexpr int RE_LD = CH + 1, IM_LD = CH + 2 * HALO + 1;       // padded rows of the epilogue tiles
+    static constexpr int EPI = 128 * (RE_LD + IM_LD + 1) * 4;       // + V_q of each line
+    static constexpr int WORK = 2 * ABYTES > EPI ? 2 * ABYTES : EPI;
+    static constexpr int OFF_B = (WORK + 1023) / 1024 * 1024, OFF_BAR = OFF_B + 4 * BBYTES;
     static constexpr int SMEM = OFF_BAR + 16;
     static constexpr int COLS = 2 * KP <= 32 ? 32 : 2 * KP <= 64 ? 64 : 2 * KP <= 128 ? 128 : 256;
-    static constexpr bool fits(int m) { return m * (SMEM + 1024) <= 228 * 1024 && m * COLS <= 512 && m * T * 168 <= 65536; }
-    static constexpr int MINB = fits(3) ? 3 : fits(2) ? 2 : 1;
+    static constexpr bool fits(int m) { return m * (SMEM + 1024) <= 228 * 1024 && m * COLS <= 512 && m * T * 128 <= 65536; }
+    static constexpr int MINB = fits(2) ? 2 : 1;
 };
 
+__device__ __forceinline__ void prefetch_l2(const void *p, unsigned bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 template <int KP>
-__global__ void __launch_bounds__(128, KkTc<KP>::MINB)
+__global__ void __launch_bounds__(256, KkTc<KP>::MINB)
 k_kk_tc(long long nlines, int nw, int Q, double dp, double v0, const float *__restrict__ im, float *__restrict__ re,
         float2 *__restrict__ rpa, const uint4 *__restrict__ mats, const float *__restrict__ band,
         unsigned *status)
@@ -132,7 +150,10 @@ k_kk_tc(long long nlines, int nw, int Q, double dp, double v0, const float *__re
     if (dyn_smem_bytes() < (unsigned)S::SMEM) return;
     unsigned long long *bar = reinterpret_cast<unsigned long long *>(smem + S::OFF_BAR);
     unsigned *slot = reinterpret_cast<unsigned *>(smem + S::OFF_BAR + 8);
-    const int t = threadIdx.x, warp = t >> 5;
+    float *reT = reinterpret_cast<float *>(smem);                    // [128][RE_LD]
+    float *imS = reT + 128 * S::RE_LD;                               // [128][IM_LD]
+    float *vS = imS + 128 * S::IM_LD;                                // [128] V_q (NaN: chi_RPA = 0)
+    const int t = threadIdx.x, warp = t >> 5, ln = t & 31;
     constexpr unsigned IDESC = tc_idesc_bf16(128, KP);
 
     for (int i = t; i < 4 * S::BBYTES / 16; i += S::T) reinterpret_cast<uint4 *>(smem + S::OFF_B)[i] = mats[i];
@@ -148,28 +169,48 @@ k_kk_tc(long long nlines, int nw, int Q, double dp, double v0, const float *__re
     const unsigned lane = (unsigned)((warp % 4) * 32) << 16;
     unsigned pm = 0;
     bool ok = true;
-
+    // near-band weights of this lane's transfer in each chunk are loaded per chunk
     const long long nblk = (nlines + 127) / 128;
+    auto prefetch = [&](long long blk) {
+        if (blk >= nblk) return;
+        const long long l0 = blk * 128, nl = min(128LL, nlines - l0);
+        // the 16-byte aligned part of the block's rows (the instance's block may
+        // start anywhere in the caller's output)
+        const unsigned long long a = reinterpret_cast<unsigned long long>(im + l0 * nw);
+        const unsigned long long b = a + (unsigned long long)(nl * nw) * 4ull;
+        const unsigned long long a16 = (a + 15) & ~15ull, b16 = b & ~15ull;
+        if (b16 > a16) prefetch_l2(reinterpret_cast<const void *>(a16), (unsigned)(b16 - a16));
+    };
+    if (t == 0) prefetch(blockIdx.x);
+
     for (long long blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
-        const long long line = blk * 128 + t;
-        const bool valid = line < nlines;
-        const float *row = im + line * nw;
+        const long long l0 = blk * 128;
+        if (t == 0) prefetch(blk + gridDim.x);
         // p = 0: even outputs from the odd inputs (Be); p = 1: odd outputs from the even inputs (Bo)
         for (int p = 0; p < 2 && ok; ++p) {
-            // operand row t: element j is x(2j + 1 - p); one 16-byte chunk holds j..j+7
-            unsigned char *arow = smem + tc_koff(t, 0, S::SBO);
+            // element j of a row is x(2j + 1 - p); lane k of a 32-transfer load pairs
+            // with lane k + 2 (element j + 1), and lanes with (k - (1 - p)) % 4 == 0 store
+            // the warp's 16 rows are loaded back to back (16 loads in flight per lane)
 #pragma unroll 1
-            for (int j8 = 0; j8 < KP / 8; ++j8) {
-                unsigned h[4], l[4];
+            for (int c = 0; c < KP / 16; ++c) {
+                const int k = 32 * c + ln;
+                float v[16];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int k0 = 2 * (8 * j8 + 2 * q) + 1 - p, k1 = k0 + 2;
-                    const float2 x = make_float2(valid && k0 < nw ? __ldg(row + k0) : 0.f,
-                                                 valid && k1 < nw ? __ldg(row + k1) : 0.f);
-                    bf16_split(x, h[q], l[q]);
+                for (int i = 0; i < 16; ++i) {
+                    const long long line = l0 + warp * 16 + i;
+                    v[i] = (line < nlines && k < nw) ? __ldg(im + line * nw + k) : 0.f;
                 }
-                *reinterpret_cast<uint4 *>(arow + j8 * 128) = make_uint4(h[0], h[1], h[2], h[3]);
-                *reinterpret_cast<uint4 *>(arow + S::ABYTES + j8 * 128) = make_uint4(l[0], l[1], l[2], l[3]);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const float w = __shfl_down_sync(0xffffffffu, v[i], 2);
+                    if (((ln - (1 - p)) & 3) == 0) {
+                        unsigned h, l;
+                        bf16_split(make_float2(v[i], w), h, l);
+                        const unsigned off = tc_koff(warp * 16 + i, (k - (1 - p)) >> 1, S::SBO);
+                        *reinterpret_cast<unsigned *>(smem + off) = h;
+                        *reinterpret_cast<unsigned *>(smem + S::ABYTES + off) = l;
+                    }
+                }
             }
             fence_proxy_async();
             tc_fence_before();
@@ -193,29 +234,59 @@ k_kk_tc(long long nlines, int nw, int Q, double dp, double v0, const float *__re
             tc_fence_after();
         }
         if (!ok) break;
-        // epilogue: far field from tensor memory + near band in FP32, Re chi and chi_RPA
-        bool zero;
-        const float V = kk_vq(line, Q, dp, v0, &zero);
+        // epilogue, chunks of 32 transfers m0 .. m0 + 31
 #pragma unroll 1
-        for (int i0 = 0; i0 < KP; i0 += 16) {
-            float de[16], dq[16];
-            tc_ld<16>(tmem + lane + (unsigned)i0, de);        // m = 2 (i0 + q)
-            tc_ld<16>(tmem + lane + (unsigned)(KP + i0), dq); // m = 2 (i0 + q) + 1
-            if (valid) {
+        for (int m0 = 0; m0 < nw; m0 += S::CH) {
+            {   // accumulators -> reT[line][q]: warps 0-3 the even transfers, 4-7 the odd ones
+                float d[16];
+                tc_ld<16>(tmem + lane + (unsigned)((warp < 4 ? 0 : KP) + m0 / 2), d);
+                const int li = (warp % 4) * 32 + ln;
 #pragma unroll
-                for (int q = 0; q < 32; ++q) {
-                    const int m = 2 * i0 + q;
-                    if (m >= nw) break;
-                    float r = (q & 1) ? dq[q >> 1] : de[q >> 1];
+                for (int q = 0; q < 16; ++q) reT[li * S::RE_LD + 2 * q + (warp < 4 ? 0 : 1)] = d[q];
+            }
+            if (m0 == 0 && t < 128) {    // V_q of the block's lines, once (an FP64 division each)
+                bool zero;
+                const float V = kk_vq(l0 + t, Q, dp, v0, &zero);
+                vS[t] = zero ? __int_as_float(0x7fc00000) : V;
+            }
+            {   // Im chi of the chunk with a halo of 8 on each side: the warp's 16 rows,
+                // all loads issued before the first store
+                const int k0 = m0 - S::HALO + ln, k1 = k0 + 32;
+                float a[16], b[16];
 #pragma unroll
-                    for (int d = 0; d < KK_BAND; ++d) {
-                        const int k = m + 2 * d - (KK_BAND - 1);
-                        if (k >= 1 && k < nw) r = fmaf(__ldg(band + m * KK_BAND + d), __ldg(row + k), r);
-                    }
-                    re[line * nw + m] = r;
-                    if (rpa) rpa[line * nw + m] = kk_rpa(r, __ldg(row + m), V, zero);
+                for (int i = 0; i < 16; ++i) {
+                    const long long line = l0 + warp * 16 + i;
+                    const float *row = im + line * nw;
+                    a[i] = (line < nlines && k0 >= 0 && k0 < nw) ? __ldg(row + k0) : 0.f;
+                    b[i] = (line < nlines && ln < 2 * S::HALO && k1 < nw) ? __ldg(row + k1) : 0.f;
+                }
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    imS[(warp * 16 + i) * S::IM_LD + ln] = a[i];
+                    if (ln < 2 * S::HALO) imS[(warp * 16 + i) * S::IM_LD + 32 + ln] = b[i];
                 }
             }
+            __syncthreads();
+            // lanes along the transfers: near band in FP32, Re chi, chi_RPA, coalesced stores
+            const int m = m0 + ln;
+            float wb[KK_BAND];
+#pragma unroll
+            for (int d = 0; d < KK_BAND; ++d) wb[d] = (m < nw) ? __ldg(band + m * KK_BAND + d) : 0.f;
+#pragma unroll 4
+            for (int li = warp * 16; li < warp * 16 + 16; ++li) {
+                const long long line = l0 + li;
+                if (line >= nlines || m >= nw) continue;
+                const float *xs = imS + li * S::IM_LD + ln + S::HALO;     // xs[o] = Im chi(m + o)
+                float r = reT[li * S::RE_LD + ln];
+#pragma unroll
+                for (int d = 0; d < KK_BAND; ++d) r = fmaf(wb[d], xs[2 * d - (KK_BAND - 1)], r);
+                re[line * nw + m] = r;
+                if (rpa) {
+                    const float V = vS[li];
+                    rpa[line * nw + m] = kk_rpa(r, xs[0], isnan(V) ? 0.f : V, isnan(V));
+                }
+            }
+            __syncthreads();
         }
         tc_fence_before();
     }
@@ -225,38 +296,66 @@ k_kk_tc(long long nlines, int nw, int Q, double dp, double v0, const float *__re
 }
 
 // ---------------------------------------------------------------------------
-// FP32 SIMT form: LB lines per CTA staged in shared memory (rows padded to
-// nw + 1 floats), one thread per line, the weights of a transfer read once
-// per warp from the table (the same address for every lane).
-__global__ void __launch_bounds__(128)
+// FP32 SIMT form: LB lines per CTA of 256 threads staged in shared memory
+// (rows padded with one zero to nw + 1 floats), V_q per line beside them.
+// Warp w takes lines w LPW .. w LPW + LPW - 1 and its lanes run along the
+// transfers: each weight W(m, k) is read once per warp step (coalesced) and
+// applied to the warp's LPW lines from registers; stores are coalesced.
+constexpr int KK_SIMT_LPW = 8;
+__host__ __device__ constexpr int kk_simt_lines(int nw)
+{
+    // 8 warps x up to 8 lines, at most ~96 KB of rows (two CTAs per SM)
+    return (96 * 1024) / (4 * (nw + 1)) >= 64 ? 64 : ((96 * 1024) / (4 * (nw + 1))) / 8 * 8 < 8 ? 8
+         : ((96 * 1024) / (4 * (nw + 1))) / 8 * 8;
+}
+
+__global__ void __launch_bounds__(256)
 k_kk_simt(long long nlines, int nw, int Q, double dp, double v0, const float *__restrict__ im, float *__restrict__ re,
           float2 *__restrict__ rpa, const float *__restrict__ hs, int LB)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float *rows = reinterpret_cast<float *>(smem_raw);
-    if (dyn_smem_bytes() < (unsigned)(LB * (nw + 1) * 4)) return;
+    float *rows = reinterpret_cast<float *>(smem_raw);          // [LB][nw + 1]
+    float *vS = rows + LB * (nw + 1);                           // [LB] V_q (NaN: chi_RPA = 0)
+    if (dyn_smem_bytes() < (unsigned)((LB * (nw + 1) + LB) * 4)) return;
     const long long l0 = (long long)blockIdx.x * LB;
-    for (int i = threadIdx.x; i < LB * nw; i += blockDim.x) {
-        const int l = i / nw, k = i % nw;
-        rows[l * (nw + 1) + k] = (l0 + l < nlines) ? im[(l0 + l) * nw + k] : 0.f;
+#pragma unroll 8
+    for (int i = threadIdx.x; i < LB * (nw + 1); i += blockDim.x) {
+        const int l = i / (nw + 1), k = i % (nw + 1);
+        rows[i] = (k < nw && l0 + l < nlines) ? im[(l0 + l) * nw + k] : 0.f;
+    }
+    if (threadIdx.x < LB) {
+        bool zero;
+        const float V = kk_vq(l0 + threadIdx.x, Q, dp, v0, &zero);
+        vS[threadIdx.x] = zero ? __int_as_float(0x7fc00000) : V;
     }
     __syncthreads();
-    const int t = threadIdx.x;
-    const long long line = l0 + t;
-    if (t >= LB || line >= nlines) return;
-    const float *x = rows + t * (nw + 1);
-    bool zero;
-    const float V = kk_vq(line, Q, dp, v0, &zero);
+    const int warp = threadIdx.x >> 5, ln = threadIdx.x & 31, lpw = LB / 8;
     const int H = (nw + 1) / 2;
-    for (int m = 0; m < nw; ++m) {
-        float s = 0.f;
-        const int k0 = 1 - (m & 1);
+    for (int m0 = 0; m0 < nw; m0 += 32) {
+        const int m = m0 + ln, k0 = 1 - (m & 1);
+        float s[KK_SIMT_LPW];
+#pragma unroll
+        for (int i = 0; i < KK_SIMT_LPW; ++i) s[i] = 0.f;
+#pragma unroll 4
         for (int j = 0; j < H; ++j) {
-            const int k = 2 * j + k0;
-            if (k < nw) s = fmaf(__ldg(hs + (size_t)j * nw + m), x[k], s);
+            const float h = (m < nw) ? __ldg(hs + (size_t)j * nw + m) : 0.f;
+            const int k = 2 * j + k0;                           // <= nw: the padding zero
+#pragma unroll
+            for (int i = 0; i < KK_SIMT_LPW; ++i)
+                if (i < lpw) s[i] = fmaf(h, rows[(warp * lpw + i) * (nw + 1) + k], s[i]);
         }
-        re[line * nw + m] = s;
-        if (rpa) rpa[line * nw + m] = kk_rpa(s, x[m], V, zero);
+        if (m < nw) {
+#pragma unroll
+            for (int i = 0; i < KK_SIMT_LPW; ++i) {
+                const int l = warp * lpw + i;
+                if (i >= lpw || l0 + l >= nlines) continue;
+                re[(l0 + l) * nw + m] = s[i];
+                if (rpa) {
+                    const float V = vS[l];
+                    rpa[(l0 + l) * nw + m] = kk_rpa(s[i], rows[l * (nw + 1) + m], isnan(V) ? 0.f : V, isnan(V));
+                }
+            }
+        }
     }
 }
 
@@ -295,13 +394,13 @@ cudaError_t launch_kk_rpa(const Geom &g, const float *im, float *re, float2 *rpa
         }
     }
     if (variant != 1 || nw > KK_MAX_SIMT) return cudaErrorNotSupported;
-    const int LB = nw <= 384 ? 128 : 32;
-    const size_t smem = (size_t)LB * (nw + 1) * 4;
-    static const cudaError_t e0 = smem_attrs(k_kk_simt, std::max<size_t>(128ull * 385 * 4, 32ull * (KK_MAX_SIMT + 1) * 4));
+    const int LB = kk_simt_lines(nw);
+    const size_t smem = (size_t)(LB * (nw + 1) + LB) * 4;
+    static const cudaError_t e0 = smem_attrs(k_kk_simt, 100 * 1024);
     if (e0 != cudaSuccess) return e0;
     const long long nlines = (long long)g.Q * g.Q;
     const int grid = (int)((nlines + LB - 1) / LB);
-    k_kk_simt<<<grid, LB, smem, s>>>(nlines, nw, g.Q, g.dp, v0, im, re, rpa,
+    k_kk_simt<<<grid, 256, smem, s>>>(nlines, nw, g.Q, g.dp, v0, im, re, rpa,
                                      reinterpret_cast<const float *>(static_cast<const unsigned char *>(tab) +
                                                                      kk_simt_off(nw)),
                                      LB);
