@@ -56,6 +56,8 @@ def _load():
             lib.lo_spectral.restype = None
             lib.lo_spectral.argtypes = ([ctypes.c_int] + [ctypes.c_double] * 6
                                         + [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, _dp])
+            lib.lo_dmu_dparams.restype = None
+            lib.lo_dmu_dparams.argtypes = [ctypes.c_int] + [ctypes.c_double] * 4 + [ctypes.c_int, ctypes.c_double, _dp]
             lib.lo_kk_real.restype = None
             lib.lo_kk_real.argtypes = [ctypes.c_long, ctypes.c_int, _dp, _dp]
             lib.lo_rpa.restype = None
@@ -81,6 +83,14 @@ def _d(a):
 
 def _i(a):
     return a.ctypes.data_as(_ip)
+
+
+def dmu_dparams(kind, t, tp, tpp, gamma, npz, mu) -> np.ndarray:
+    """dmu/d(t, t', t'', gamma) at fixed filling (implicit function theorem on
+    the rigid-band count of Sec. 3); see lo_dmu_dparams."""
+    out = np.zeros(4)
+    _load().lo_dmu_dparams(int(kind), float(t), float(tp), float(tpp), float(gamma), int(npz), float(mu), _d(out))
+    return out
 
 
 def kk_real(im: np.ndarray) -> np.ndarray:

@@ -92,6 +92,35 @@ int lo_mu(int kind, double t, double tp, double tpp, double gamma, int npz,
     return 0;
 }
 
+/* Derivatives of mu at fixed filling (the rigid band of Sec. 3): the filling
+ * n(mu; t, t', t'', gamma) of lo_filling is held constant, so by the implicit
+ * function theorem dmu/dtheta = -(dn/dtheta) / (dn/dmu), with, per state,
+ *   d/dmu    [1/2 - atan(xi/gamma)/pi] =  gamma / (pi (xi^2 + gamma^2)),
+ *   d/dtheta [ ... ]                   = -gamma / (pi (xi^2 + gamma^2)) dxi/dtheta,
+ *   d/dgamma [ ... ]                   =  xi / (pi (xi^2 + gamma^2)),
+ * dxi/d(t, t', t'') = (-2 (cos px + cos py), -4 cos px cos py,
+ * -2 (cos 2px + cos 2py)) for the tight-binding band, 0 for free electrons.
+ * out[0..3] = dmu/d(t, t', t'', gamma). */
+void lo_dmu_dparams(int kind, double t, double tp, double tpp, double gamma, int npz, double mu, double *out)
+{
+    double dp = 2.0 * LO_PI / npz, dn_dmu = 0.0, dn[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int ix = 0; ix < npz; ++ix)
+        for (int iy = 0; iy < npz; ++iy) {
+            double px = (ix - npz / 2) * dp, py = (iy - npz / 2) * dp;
+            double xi = lo_band(kind, t, tp, tpp, px, py) - mu;
+            double D = xi * xi + gamma * gamma;
+            double w = gamma / (LO_PI * D);
+            dn_dmu += w;
+            if (kind == 0) {
+                dn[0] -= w * (-2.0 * (cos(px) + cos(py)));
+                dn[1] -= w * (-4.0 * cos(px) * cos(py));
+                dn[2] -= w * (-2.0 * (cos(2.0 * px) + cos(2.0 * py)));
+            }
+            dn[3] += xi / (LO_PI * D);
+        }
+    for (int r = 0; r < 4; ++r) out[r] = -dn[r] / dn_dmu;   /* the measure 2/npz^2 cancels */
+}
+
 /* Spectral function A(p_i, e_j) on the grid (Eqs. 4-5), layout [N][N][n_eps]
  * with the energy index fastest.  |M(p)|^2 = exp(-|p|^2 ff_a^2 / 8) stands in
  * for the Bloch momentum density of Eq. 7; ff_a == 0 means |M|^2 = 1. */

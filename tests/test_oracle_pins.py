@@ -368,3 +368,26 @@ def test_rpa_shifts_the_pole_to_the_plasmon_frequency():
     assert np.all(chi[1, 1] == 0)                     # q = 0: V infinite, chi_RPA -> 0
     same = oracle.rpa(re, im, dp, 0.0)                # no interaction: chi_RPA = chi_L
     assert np.array_equal(same, re + 1j * im)
+
+
+# --- dmu/dtheta at fixed filling (the implicit gradient of the rigid band) ----------
+
+@pytest.mark.parametrize("kind,fill,gamma", [(0, 1.15, 0.05), (0, 0.7, 0.2), (1, 0.3, 0.1)])
+def test_dmu_dparams_matches_central_differences_of_the_mu_solve(kind, fill, gamma):
+    # the analytic implicit-function derivative against central differences of
+    # the oracle's own bisection for mu (a different computation of the same
+    # quantity); h = 1e-4 eV leaves a truncation of order h^2
+    npz = 24
+    th = [T, TP, TPP, gamma] if kind == 0 else [0.0, 0.0, 0.0, gamma]
+    mu = oracle.solve_mu(kind, *th[:3], gamma, npz, fill)
+    got = oracle.dmu_dparams(kind, *th[:3], gamma, npz, mu)
+    h = 1e-4
+    for r in range(4):
+        if kind == 1 and r < 3:
+            assert got[r] == 0.0           # free electrons: no hoppings
+            continue
+        up, dn = list(th), list(th)
+        up[r] += h
+        dn[r] -= h
+        fd = (oracle.solve_mu(kind, *up[:3], up[3], npz, fill) - oracle.solve_mu(kind, *dn[:3], dn[3], npz, fill)) / (2 * h)
+        assert abs(got[r] - fd) <= 1e-6 * max(1.0, abs(fd)), (r, got[r], fd)
