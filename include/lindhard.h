@@ -239,6 +239,19 @@ lindhard_status lindhard_sum_rule(lindhard_plan *plan, int index, const lindhard
                                   const float *A_in, const float *out, double *sum_q, double *dos_corr,
                                   void *stream);
 
+/* dmu/d(t, t', t'', gamma) at fixed filling, at chemical potential mu (e.g.
+ * the value lindhard_imchi returned in mu_out): the rigid-band count of
+ * lindhard_band.filling, n(mu) = (2/npz^2) sum_k [1/2 - atan(xi_k/gamma)/pi]
+ * over the first-zone grid, is held fixed, so by the implicit function theorem
+ * dmu/dtheta = -(dn/dtheta)/(dn/dmu) (Sec. 3 places mu to hold the filling).
+ * With the partial derivatives at fixed mu from lindhard_imchi_backward, the
+ * gradient at fixed filling is dL/dtheta + dL/dmu dmu/dtheta.  Uses t, tp,
+ * tpp, gamma and band_kind of `band` and the instance's npz; FP64 reductions
+ * on the device, summed on the host in a fixed order.  out: host double[4].
+ * Synchronises `stream`. */
+lindhard_status lindhard_dmu_dparams(lindhard_plan *plan, int index, const lindhard_band *band, double mu,
+                                     double *out, void *stream);
+
 /* Real part of chi by the Kramers-Kronig relation and the RPA susceptibility
  * (Sec. 4): for instance `index`,
  *   Re chi(q, w_m) = sum_k W(m, k) Im chi(q, w_k),

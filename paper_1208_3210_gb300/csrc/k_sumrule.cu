@@ -74,6 +74,65 @@ __global__ void k_sum_q(Geom g, const float *__restrict__ out, double *sum_q)
     for (int m = threadIdx.x; m < g.n_omega; m += blockDim.x) atomicAdd(&sum_q[m], s_q[m]);
 }
 
+// dmu/d(t, t', t'', gamma) at fixed filling (the rigid band of Sec. 3): the
+// filling n = (2/npz^2) sum_k [1/2 - atan(xi_k/gamma)/pi] over the first-zone
+// grid is held fixed, so dmu/dtheta = -(dn/dtheta) / (dn/dmu).  Per state,
+// with D = xi^2 + gamma^2: dn/dmu ~ gamma/(pi D); dn/dtheta ~ -gamma/(pi D)
+// dxi/dtheta, dxi/d(t, t', t'') = (-2 (cos px + cos py), -4 cos px cos py,
+// -2 (cos 2px + cos 2py)) (0 for free electrons); dn/dgamma ~ xi/(pi D).
+// Each CTA reduces its share of the npz^2 states in FP64 (fixed-order tree)
+// into part[blockIdx.x][5]; the host adds the CTAs in order.
+constexpr int DMU_THREADS = 256;
+__global__ void __launch_bounds__(DMU_THREADS)
+k_dmu_partials(int kind, double t, double tp, double tpp, double gamma, int npz, double mu, double *part)
+{
+    extern __shared__ double sd[];                  // c1[npz], c2[npz], p2[npz], red[5][DMU_THREADS]
+    double *c1 = sd, *c2 = sd + npz, *p2 = sd + 2 * npz, *red = sd + 3 * npz;
+    const double pi = 3.14159265358979323846, dp = 2.0 * pi / npz;
+    for (int i = threadIdx.x; i < npz; i += blockDim.x) {
+        const double p = (double)(i - npz / 2) * dp;
+        c1[i] = cos(p);
+        c2[i] = cos(2.0 * p);
+        p2[i] = p * p;
+    }
+    __syncthreads();
+    double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    const long long n = (long long)npz * npz;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int ix = (int)(idx / npz), iy = (int)(idx % npz);
+        const double e0 = kind == 1 ? 0.5 * (p2[ix] + p2[iy])
+                                    : -2.0 * t * (c1[ix] + c1[iy]) - 4.0 * tp * c1[ix] * c1[iy]
+                                          - 2.0 * tpp * (c2[ix] + c2[iy]);
+        const double xi = e0 - mu, D = xi * xi + gamma * gamma, w = gamma / (pi * D);
+        acc[0] += w;
+        if (kind == 0) {
+            acc[1] += w * 2.0 * (c1[ix] + c1[iy]);
+            acc[2] += w * 4.0 * c1[ix] * c1[iy];
+            acc[3] += w * 2.0 * (c2[ix] + c2[iy]);
+        }
+        acc[4] += xi / (pi * D);
+    }
+    for (int r = 0; r < 5; ++r) red[r * DMU_THREADS + threadIdx.x] = acc[r];
+    __syncthreads();
+    for (int h = DMU_THREADS / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h)
+            for (int r = 0; r < 5; ++r) red[r * DMU_THREADS + threadIdx.x] += red[r * DMU_THREADS + threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x < 5) part[blockIdx.x * 5 + threadIdx.x] = red[threadIdx.x * DMU_THREADS];
+}
+
+cudaError_t launch_dmu_partials(int kind, double t, double tp, double tpp, double gamma, int npz, double mu,
+                                double *part, int blocks, cudaStream_t s)
+{
+    const size_t smem = sizeof(double) * (3 * (size_t)npz + 5 * DMU_THREADS);
+    static const cudaError_t e0 = smem_attrs(k_dmu_partials, sizeof(double) * (3 * 4096 + 5 * DMU_THREADS));
+    if (e0 != cudaSuccess) return e0;
+    k_dmu_partials<<<blocks, DMU_THREADS, smem, s>>>(kind, t, tp, tpp, gamma, npz, mu, part);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_sum_rule(const Geom &g, const Band &band, const AxisTab *axis, const float2 *eps,
                             const InstState *st, const float *A_in, const float *out, double *D, double *sum_q,
                             double *dos_corr, cudaStream_t s)

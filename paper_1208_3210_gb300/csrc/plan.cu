@@ -39,6 +39,9 @@ cudaError_t launch_x_product(const Geom &g, const Work<double> &w, cudaStream_t 
 cudaError_t launch_inv_y(const Geom &g, const Work<float> &w, cudaStream_t s, int variant);
 bool tc_supported(int P);
 size_t kk_table_bytes(int nw);
+cudaError_t launch_dmu_partials(int kind, double t, double tp, double tpp, double gamma, int npz, double mu,
+                                double *part, int blocks, cudaStream_t s);
+constexpr int kDmuBlocks = 128;
 cudaError_t launch_kk_tables(int nw, void *tab, cudaStream_t s);
 cudaError_t launch_kk_rpa(const Geom &g, const float *im, float *re, float2 *rpa, const void *tab, double v0,
                           int variant, unsigned *status, cudaStream_t s);
@@ -114,7 +117,7 @@ struct lindhard_plan {
         size_t X = 0, Y = 0, Z = 0, partial = 0, axis = 0, eps32 = 0, eps64 = 0, state = 0, acc = 0, bar = 0;
     };
     std::vector<Slot> slots;
-    size_t off_tw32 = 0, off_tw64 = 0, off_status = 0, off_tc = 0;
+    size_t off_tw32 = 0, off_tw64 = 0, off_status = 0, off_tc = 0, off_dmu = 0;
     std::vector<size_t> off_kk;   // Kramers-Kronig weight tables per instance (FP32 grids)
     int tw_len = 0;
     bool backward = false;       // LINDHARD_PLAN_BACKWARD
@@ -436,6 +439,7 @@ extern "C" lindhard_status lindhard_plan_create(const lindhard_grid *grids, int 
     p->off_tw32 = o; o = align_up(o + (size_t)twiddle_entries() * sizeof(float2));
     p->off_tw64 = o; o = align_up(o + (size_t)twiddle_entries() * sizeof(double2));
     p->off_status = o; o = align_up(o + sizeof(unsigned));
+    p->off_dmu = o; o = align_up(o + sizeof(double) * 5 * kDmuBlocks);
     // tensor-core DFT matrices of every supported length (plans with a
     // LINDHARD_SPLITBF16_TC grid only)
     if (std::count(p->precision.begin(), p->precision.end(), (int)LINDHARD_SPLITBF16_TC) > 0) {
@@ -836,6 +840,30 @@ extern "C" lindhard_status lindhard_sum_rule(lindhard_plan *p, int index, const 
     if (e == cudaSuccess)
         e = launch_sum_rule(g, b, w.axis, (const float2 *)w.eps, w.state, A_in, out, D, sum_q, dos_corr, s);
     return e == cudaSuccess ? LINDHARD_OK : cuda_fail(e, "sum-rule launch");
+}
+
+extern "C" lindhard_status lindhard_dmu_dparams(lindhard_plan *p, int index, const lindhard_band *band, double mu,
+                                                double *out, void *stream)
+{
+    if (!p || !band || !out) return fail(LINDHARD_EINVAL, "plan, band and out must be non-NULL");
+    if (index < 0 || index >= p->batch) return fail(LINDHARD_EINVAL, "index out of range");
+    if (!isfinite(mu) || !(band->gamma > 0) || !isfinite(band->gamma) || !isfinite(band->t) || !isfinite(band->tp) ||
+        !isfinite(band->tpp) || (band->band_kind != 0 && band->band_kind != 1))
+        return fail(LINDHARD_EINVAL, "band parameters and mu must be finite, gamma > 0, band_kind 0 or 1");
+    cudaStream_t s = (cudaStream_t)stream;
+    double *part = (double *)(p->ws + p->off_dmu);
+    cudaError_t e = launch_dmu_partials(band->band_kind, band->t, band->tp, band->tpp, band->gamma,
+                                        p->geoms[index].npz, mu, part, kDmuBlocks, s);
+    double h[5 * kDmuBlocks];
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, part, sizeof h, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "dmu reduction");
+    double sum[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int b = 0; b < kDmuBlocks; ++b)
+        for (int r = 0; r < 5; ++r) sum[r] += h[b * 5 + r];
+    if (!(sum[0] > 0)) return fail(LINDHARD_EINVAL, "dn/dmu vanishes at this mu");
+    for (int r = 0; r < 4; ++r) out[r] = -sum[r + 1] / sum[0];
+    return LINDHARD_OK;
 }
 
 extern "C" lindhard_status lindhard_kk_rpa(lindhard_plan *p, int index, const float *imchi, float *re_out,

@@ -25,7 +25,7 @@ _STATUS_NAMES = {OK: "OK", EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", E
 SYMBOLS = ("lindhard_plan_create", "lindhard_plan_sizes", "lindhard_plan_workspace_bytes", "lindhard_imchi",
            "lindhard_imchi_f64", "lindhard_imchi_backward", "lindhard_plan_profile", "lindhard_plan_profile_passes",
            "lindhard_plan_pass_times",
-           "lindhard_sum_rule", "lindhard_kk_rpa", "lindhard_plan_variants", "lindhard_plan_status", "lindhard_plan_destroy",
+           "lindhard_sum_rule", "lindhard_dmu_dparams", "lindhard_kk_rpa", "lindhard_plan_variants", "lindhard_plan_status", "lindhard_plan_destroy",
            "lindhard_imchi_noalloc", "lindhard_last_error")
 NOALLOC_SCRATCH_BYTES = 32 << 20
 NUM_PASSES = 7
@@ -86,6 +86,9 @@ def load(path: str = LIB_PATH):
         lib.lindhard_imchi_noalloc.restype = ctypes.c_int
         lib.lindhard_sum_rule.argtypes = [vp, ctypes.c_int, ctypes.POINTER(Band), vp, vp, vp, vp, vp]
         lib.lindhard_sum_rule.restype = ctypes.c_int
+        lib.lindhard_dmu_dparams.argtypes = [vp, ctypes.c_int, ctypes.POINTER(Band), ctypes.c_double,
+                                             ctypes.POINTER(ctypes.c_double), vp]
+        lib.lindhard_dmu_dparams.restype = ctypes.c_int
         lib.lindhard_kk_rpa.argtypes = [vp, ctypes.c_int, vp, vp, vp, ctypes.c_double, ctypes.c_int, vp]
         lib.lindhard_kk_rpa.restype = ctypes.c_int
         for name in ("lindhard_plan_create", "lindhard_plan_sizes", "lindhard_plan_workspace_bytes",
@@ -236,6 +239,15 @@ class Plan:
         _check(load().lindhard_sum_rule(self._h, int(index), None if b is None else ctypes.byref(b), _ptr(A_in),
                                         _ptr(out_i), _ptr(sq), _ptr(dc), _stream(stream)))
         return sq, dc
+
+    def dmu_dparams(self, band, mu, index=0, stream=None):
+        """dmu/d(t, t', t'', gamma) at fixed filling, at chemical potential mu
+        (numpy float64 [4])."""
+        import numpy as np
+        b = band if isinstance(band, Band) else make_band(**band)
+        out = (ctypes.c_double * 4)()
+        _check(load().lindhard_dmu_dparams(self._h, int(index), ctypes.byref(b), float(mu), out, _stream(stream)))
+        return np.array(list(out))
 
     def kk_rpa(self, out_i, index=0, v0=0.0, rpa=True, variant=0, stream=None):
         """Re chi by Kramers-Kronig and chi_RPA = chi / (1 - v0/|q|^2 chi) for

@@ -180,3 +180,43 @@ def test_autograd_function(lh):
         terms = gref * d[r]
         assert abs(g[r] - terms.sum()) <= 1e-4 * np.abs(terms).sum(), (r, g[r], terms.sum())
     plan.close()
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_gradient_at_fixed_filling(lh, kind):
+    """dL/dtheta at fixed filling = dL/dtheta at fixed mu + dL/dmu dmu/dtheta
+    (lindhard_dmu_dparams), against central differences of the FP64 oracle
+    loss with mu solved again from the filling at every step (h = 1e-4 eV)."""
+    grid = _grid(2, 8, 24, 1.2)
+    if kind == 0:
+        band = wl.band_params(filling=1.1, gamma=0.08, ff_a=0.9)
+    else:
+        band = wl.band_params(filling=0.4, gamma=0.1, ff_a=0.0, kind=1, t=0.0, tp=0.0, tpp=0.0)
+    Q, n_omega = grid["q_extent"], grid["n_omega"]
+    w = np.random.default_rng(9).uniform(0, 1, (Q, Q, n_omega)).astype(np.float32).astype(np.float64)
+    _, dp = _gpu_backward(lh, grid, band, w)
+    b = _oracle_band(band, grid)
+    plan = lh.Plan([grid])
+    dmu = plan.dmu_dparams(band, b["mu"])
+    plan.close()
+    ref = oracle.dmu_dparams(b["kind"], b["t"], b["tp"], b["tpp"], b["gamma"], grid["npz"], b["mu"])
+    assert np.allclose(dmu, ref, rtol=1e-10, atol=1e-14), (dmu, ref)
+    total = np.array([dp[0], dp[1], dp[2], dp[4]]) + dp[3] * dmu      # d/d(t, t', t'', gamma)
+
+    def loss(bb):
+        bb = dict(bb)
+        bb["mu"] = oracle.solve_mu(bb["kind"], bb["t"], bb["tp"], bb["tpp"], bb["gamma"], grid["npz"], bb["filling"])
+        return oracle.loss(oracle.spectral(bb, grid), grid, Q, w)
+
+    h = 1e-4
+    for r, name in enumerate(["t", "tp", "tpp", "gamma"]):
+        if kind == 1 and r < 3:
+            assert dmu[r] == 0.0
+            continue
+        up, dn = dict(band), dict(band)
+        up[name] += h
+        dn[name] -= h
+        fd = (loss(up) - loss(dn)) / (2 * h)
+        scale = abs(fd) + abs(dp[r if r < 3 else 4]) + abs(dp[3] * dmu[r])
+        print(f"kind {kind} d/d{name}: total {total[r]:.6e}, central difference {fd:.6e}")
+        assert abs(total[r] - fd) <= 2e-4 * scale, (name, total[r], fd)
