@@ -91,11 +91,13 @@ cudaError_t launch_kk_tables(int nw, void *tab, cudaStream_t s)
 }
 
 // chi_RPA from chi = (r, x) at one transfer; V = 0 returns chi unchanged.
+// The reciprocal of |1 - V chi|^2 is the hardware approximation (2 ulp),
+// far inside the FP32 bar of chi_RPA.
 __device__ __forceinline__ float2 kk_rpa(float r, float x, float V, bool zero)
 {
     if (zero) return make_float2(0.f, 0.f);
     const float dr = 1.f - V * r, di = -V * x;
-    const float inv = 1.f / (dr * dr + di * di);
+    const float inv = __fdividef(1.f, dr * dr + di * di);
     return make_float2((r * dr + x * di) * inv, (x * dr - r * di) * inv);
 }
 // V_q of lag line l = l_x Q + l_y; *zero when q = 0 with an interaction
@@ -272,18 +274,22 @@ k_kk_tc(long long nlines, int nw, int Q, double dp, double v0, const float *__re
             float wb[KK_BAND];
 #pragma unroll
             for (int d = 0; d < KK_BAND; ++d) wb[d] = (m < nw) ? __ldg(band + m * KK_BAND + d) : 0.f;
+            if (m < nw) {
+                const int nli = (int)min(16LL, nlines - (l0 + warp * 16));   // lines of this warp in range
+                float *ro = re + (l0 + warp * 16) * nw + m;
+                float2 *po = rpa ? rpa + (l0 + warp * 16) * nw + m : nullptr;
 #pragma unroll 4
-            for (int li = warp * 16; li < warp * 16 + 16; ++li) {
-                const long long line = l0 + li;
-                if (line >= nlines || m >= nw) continue;
-                const float *xs = imS + li * S::IM_LD + ln + S::HALO;     // xs[o] = Im chi(m + o)
-                float r = reT[li * S::RE_LD + ln];
+                for (int i = 0; i < nli; ++i) {
+                    const int li = warp * 16 + i;
+                    const float *xs = imS + li * S::IM_LD + ln + S::HALO;     // xs[o] = Im chi(m + o)
+                    float r = reT[li * S::RE_LD + ln];
 #pragma unroll
-                for (int d = 0; d < KK_BAND; ++d) r = fmaf(wb[d], xs[2 * d - (KK_BAND - 1)], r);
-                re[line * nw + m] = r;
-                if (rpa) {
-                    const float V = vS[li];
-                    rpa[line * nw + m] = kk_rpa(r, xs[0], isnan(V) ? 0.f : V, isnan(V));
+                    for (int d = 0; d < KK_BAND; ++d) r = fmaf(wb[d], xs[2 * d - (KK_BAND - 1)], r);
+                    ro[(size_t)i * nw] = r;
+                    if (po) {
+                        const float V = vS[li];
+                        po[(size_t)i * nw] = kk_rpa(r, xs[0], isnan(V) ? 0.f : V, isnan(V));
+                    }
                 }
             }
             __syncthreads();
