@@ -55,7 +55,9 @@ typedef enum {
     LINDHARD_EINVAL = 1,        /* an argument is out of range or NULL       */
     LINDHARD_ENOMEM = 2,        /* device or host allocation failed          */
     LINDHARD_ECUDA = 3,         /* a CUDA runtime call failed                */
-    LINDHARD_ETIMEOUT = 4,      /* reserved (no kernel of this library waits) */
+    LINDHARD_ETIMEOUT = 4,      /* a bounded device wait (TMA copy or tensor-core
+                                   products, 1 s) gave up; reported by
+                                   lindhard_plan_status                       */
     LINDHARD_ENOCONV = 5,       /* no chemical potential for the filling     */
     LINDHARD_EUNSUPPORTED = 6   /* grid size or precision not built          */
 } lindhard_status;
