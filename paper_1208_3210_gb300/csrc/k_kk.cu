@@ -128,7 +128,10 @@ struct KkTc {
     static constexpr int ABYTES = 128 * KP * 2, BBYTES = KP * KP * 2;
     static constexpr int RE_LD = CH + 1, IM_LD = CH + 2 * HALO + 1;       // padded rows of the epilogue tiles
     static constexpr int EPI = 128 * (RE_LD + IM_LD + 1) * 4;       // + V_q of each line
-    static constexpr int WORK = 2 * ABYTES > EPI ? 2 * ABYTES : EPI;
+    // both parities' operands side by side when they fit beside two CTAs per SM
+    static constexpr bool BOTH = KP <= 64;
+    static constexpr int AREG = (BOTH ? 4 : 2) * ABYTES;
+    static constexpr int WORK = AREG > EPI ? AREG : EPI;
     static constexpr int OFF_B = (WORK + 1023) / 1024 * 1024, OFF_BAR = OFF_B + 4 * BBYTES;
     static constexpr int SMEM = OFF_BAR + 16;
     static constexpr int COLS = 2 * KP <= 32 ? 32 : 2 * KP <= 64 ? 64 : 2 * KP <= 128 ? 128 : 256;
@@ -189,10 +192,13 @@ k_kk_tc(long long nlines, int nw, int Q, double dp, double v0, const float *__re
         const long long l0 = blk * 128;
         if (t == 0) prefetch(blk + gridDim.x);
         // p = 0: even outputs from the odd inputs (Be); p = 1: odd outputs from the even inputs (Bo)
-        for (int p = 0; p < 2 && ok; ++p) {
-            // element j of a row is x(2j + 1 - p); lane k of a 32-transfer load pairs
-            // with lane k + 2 (element j + 1), and lanes with (k - (1 - p)) % 4 == 0 store
-            // the warp's 16 rows are loaded back to back (16 loads in flight per lane)
+        // Operand of parity p (its hi part at aoff(p), lo at aoff(p) + ABYTES):
+        // element j of a row is x(2j + 1 - p); lane k of a 32-transfer load pairs
+        // with lane k + 2 (element j + 1), and lanes with (k - (1 - p)) % 4 == 0
+        // store.  The warp's 16 rows are loaded back to back (16 loads in flight
+        // per lane).  BOTH: one pass over the rows builds both parities.
+        auto aoff = [](int p) { return S::BOTH ? 2 * p * S::ABYTES : 0; };
+        auto build = [&](int p0, int p1) {
 #pragma unroll 1
             for (int c = 0; c < KP / 16; ++c) {
                 const int k = 32 * c + ln;
@@ -205,35 +211,56 @@ k_kk_tc(long long nlines, int nw, int Q, double dp, double v0, const float *__re
 #pragma unroll
                 for (int i = 0; i < 16; ++i) {
                     const float w = __shfl_down_sync(0xffffffffu, v[i], 2);
-                    if (((ln - (1 - p)) & 3) == 0) {
-                        unsigned h, l;
-                        bf16_split(make_float2(v[i], w), h, l);
-                        const unsigned off = tc_koff(warp * 16 + i, (k - (1 - p)) >> 1, S::SBO);
-                        *reinterpret_cast<unsigned *>(smem + off) = h;
-                        *reinterpret_cast<unsigned *>(smem + S::ABYTES + off) = l;
-                    }
+                    for (int p = p0; p <= p1; ++p)
+                        if (((ln - (1 - p)) & 3) == 0) {
+                            unsigned h, l;
+                            bf16_split(make_float2(v[i], w), h, l);
+                            const unsigned off = aoff(p) + tc_koff(warp * 16 + i, (k - (1 - p)) >> 1, S::SBO);
+                            *reinterpret_cast<unsigned *>(smem + off) = h;
+                            *reinterpret_cast<unsigned *>(smem + S::ABYTES + off) = l;
+                        }
                 }
             }
             fence_proxy_async();
             tc_fence_before();
             __syncthreads();
             tc_fence_after();
+        };
+        // products of parity p into accumulator columns p KP (thread 0)
+        auto products = [&](int p) {
+            const unsigned long long a0 = dA + (unsigned long long)(aoff(p) >> 4);
+            const unsigned long long b0 = dB + (unsigned long long)((2 * p * S::BBYTES) >> 4);
+#pragma unroll
+            for (int term = 0; term < 3; ++term) {
+                const unsigned long long a = a0 + (unsigned long long)(((term == 1) ? S::ABYTES : 0) >> 4);
+                const unsigned long long b = b0 + (unsigned long long)(((term == 2) ? S::BBYTES : 0) >> 4);
+#pragma unroll
+                for (int ks = 0; ks < KP / 16; ++ks)
+                    tc_mma(tmem + p * KP, a + (unsigned long long)((ks * 256) >> 4),
+                           b + (unsigned long long)((ks * 256) >> 4), IDESC, term > 0 || ks > 0);
+            }
+        };
+        if constexpr (S::BOTH) {
+            build(0, 1);
             if (t == 0) {
-                const unsigned long long b0 = dB + (unsigned long long)((2 * p * S::BBYTES) >> 4);
-#pragma unroll
-                for (int term = 0; term < 3; ++term) {
-                    const unsigned long long a = dA + (unsigned long long)(((term == 1) ? S::ABYTES : 0) >> 4);
-                    const unsigned long long b = b0 + (unsigned long long)(((term == 2) ? S::BBYTES : 0) >> 4);
-#pragma unroll
-                    for (int ks = 0; ks < KP / 16; ++ks)
-                        tc_mma(tmem + p * KP, a + (unsigned long long)((ks * 256) >> 4),
-                               b + (unsigned long long)((ks * 256) >> 4), IDESC, term > 0 || ks > 0);
-                }
+                products(0);
+                products(1);
                 tc_commit(bar);
             }
             ok = tile_ready(bar, pm, status);
             pm ^= 1u;
             tc_fence_after();
+        } else {
+            for (int p = 0; p < 2 && ok; ++p) {
+                build(p, p);
+                if (t == 0) {
+                    products(p);
+                    tc_commit(bar);
+                }
+                ok = tile_ready(bar, pm, status);
+                pm ^= 1u;
+                tc_fence_after();
+            }
         }
         if (!ok) break;
         // epilogue, chunks of 32 transfers m0 .. m0 + 31
