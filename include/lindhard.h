@@ -254,6 +254,21 @@ lindhard_status lindhard_sum_rule(lindhard_plan *plan, int index, const lindhard
 lindhard_status lindhard_dmu_dparams(lindhard_plan *plan, int index, const lindhard_band *band, double mu,
                                      double *out, void *stream);
 
+/* Envelope of -Im chi along the [100] cut q = (q_x, 0) at transfer index m,
+ * fitted by the Lorentzian shape 1 / (1 + (q/k0)^2) (Sec. 4, Fig. 5: the
+ * decay of -Im chi with the momentum transfer).  For every reciprocal-lattice
+ * zone n >= 0 along the cut (lag offsets [n npz - npz/2, n npz + npz/2) from
+ * l_x = Q/2, with l_y = Q/2) that the lag window holds whole, the largest
+ * -Im chi and its q form one point; the
+ * points are normalised by the largest of them and k0 minimises the squared
+ * residuals over the points with q > 0 (golden-section search over ln k0 in
+ * [ln dp, ln (Q dp)]).  k0 in units of 1/a (lattice constant a = 1).
+ * imchi: device, the instance's [Q][Q][n_omega] block.  k0: host double.
+ * q_out, y_out: host double[max_points] for the points, or NULL; npoints: host
+ * int (the number of points), or NULL.  Synchronises `stream`. */
+lindhard_status lindhard_envelope_k0(lindhard_plan *plan, int index, const float *imchi, int m, double *k0,
+                                     double *q_out, double *y_out, int max_points, int *npoints, void *stream);
+
 /* Real part of chi by the Kramers-Kronig relation and the RPA susceptibility
  * (Sec. 4): for instance `index`,
  *   Re chi(q, w_m) = sum_k W(m, k) Im chi(q, w_k),

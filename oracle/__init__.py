@@ -228,3 +228,55 @@ def loss(A: np.ndarray, grid: dict, q_extent: int, w: np.ndarray) -> float:
     """L = sum_{l,m} w(l,m) Im chi(q_l, w_m) from the direct sum (small grids only)."""
     chi = imchi_full(A, grid, q_extent, w.shape[2])
     return float(np.sum(w * chi))
+
+
+def envelope_k0(imchi: np.ndarray, npz: int, m: int):
+    """Envelope of -Im chi along the [100] cut (Sec. 4, Fig. 5): the cut is
+    q = (q_x, 0), lags l_x with l_y = Q/2, at transfer index m.  Each zone
+    n >= 0 of the reciprocal lattice along the cut (lag offsets
+    [n npz - npz/2, n npz + npz/2) from Q/2) that the lag window holds whole
+    contributes its maximum of
+    -Im chi and where it sits; normalised by the largest of them, the points
+    are fitted by the Lorentzian shape 1 / (1 + (q/k0)^2) in least squares over
+    the points with q > 0.  The one-parameter fit is a golden-section search
+    over ln k0 in [ln dp, ln (Q dp)], 200 steps.  Returns (k0 in units of 1/a,
+    q of the zone maxima, normalised maxima)."""
+    Q = imchi.shape[0]
+    dp = 2.0 * math.pi / npz
+    cut = -np.asarray(imchi[:, Q // 2, m], dtype=np.float64)
+    qs, ys = [], []
+    n = 0
+    while True:
+        lo = Q // 2 + n * npz - npz // 2
+        hi = lo + npz
+        if lo < 0 or hi > Q:         # only zones the lag window holds whole
+            break
+        seg = cut[lo:hi]
+        i = int(np.argmax(seg))      # first index of the maximum
+        qs.append((lo + i - Q // 2) * dp)
+        ys.append(seg[i])
+        n += 1
+    qs, ys = np.array(qs), np.array(ys)
+    if len(ys) == 0 or not ys.max() > 0:
+        raise ValueError("-Im chi has no positive zone maximum on the cut")
+    ys = ys / ys.max()
+    keep = qs > 0
+
+    def cost(lk):
+        k = math.exp(lk)
+        return float(np.sum((ys[keep] - 1.0 / (1.0 + (qs[keep] / k) ** 2)) ** 2))
+
+    a, b = math.log(dp), math.log(Q * dp)
+    g = (math.sqrt(5.0) - 1.0) / 2.0
+    c, d = b - g * (b - a), a + g * (b - a)
+    fc, fd = cost(c), cost(d)
+    for _ in range(200):
+        if fc <= fd:
+            b, d, fd = d, c, fc
+            c = b - g * (b - a)
+            fc = cost(c)
+        else:
+            a, c, fc = c, d, fd
+            d = a + g * (b - a)
+            fd = cost(d)
+    return math.exp(0.5 * (a + b)), qs, ys

@@ -866,6 +866,83 @@ extern "C" lindhard_status lindhard_dmu_dparams(lindhard_plan *p, int index, con
     return LINDHARD_OK;
 }
 
+// Envelope of -Im chi along the [100] cut q = (q_x, 0) at transfer index m
+// (Sec. 4, Fig. 5: its decay with q fitted by 1 / (1 + (q/k0)^2)).  The cut
+// (Q values, stride Q n_omega floats in the output) is read with one strided
+// copy; the zone maxima and the one-parameter least-squares fit are host work
+// on Q values: for each reciprocal-lattice zone n >= 0 along the cut (lag
+// offsets [n npz - npz/2, n npz + npz/2) from Q/2) that the lag window holds
+// whole, the first largest -Im chi
+// and its q; normalised by the largest of them; k0 minimises the squared
+// residuals over the points with q > 0 (golden-section search over ln k0 in
+// [ln dp, ln (Q dp)], 200 steps).
+extern "C" lindhard_status lindhard_envelope_k0(lindhard_plan *p, int index, const float *imchi, int m, double *k0,
+                                                double *q_out, double *y_out, int max_points, int *npoints,
+                                                void *stream)
+{
+    if (!p || !imchi || !k0) return fail(LINDHARD_EINVAL, "plan, imchi and k0 must be non-NULL");
+    if (index < 0 || index >= p->batch) return fail(LINDHARD_EINVAL, "index out of range");
+    if (p->precision[index] == LINDHARD_FP64) return fail(LINDHARD_EINVAL, "the envelope reads FP32 outputs");
+    const Geom &g = p->geoms[index];
+    if (m < 0 || m >= g.n_omega) return fail(LINDHARD_EINVAL, "transfer index out of range");
+    if ((q_out || y_out) && max_points < 1) return fail(LINDHARD_EINVAL, "max_points must be >= 1");
+    const int Q = g.Q, npz = g.npz;
+    std::vector<float> cut(Q);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpy2DAsync(cut.data(), sizeof(float), imchi + (size_t)(Q / 2) * g.n_omega + m,
+                                      sizeof(float) * (size_t)Q * g.n_omega, sizeof(float), Q,
+                                      cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "cut copy");
+    const double dp = 2.0 * M_PI / npz;
+    std::vector<double> qs, ys;
+    for (int n = 0;; ++n) {
+        const int lo = Q / 2 + n * npz - npz / 2, hi = lo + npz;
+        if (lo < 0 || hi > Q) break;   // only zones the lag window holds whole
+        int best = lo;
+        for (int l = lo + 1; l < hi; ++l)
+            if (-(double)cut[l] > -(double)cut[best]) best = l;
+        qs.push_back((best - Q / 2) * dp);
+        ys.push_back(-(double)cut[best]);
+    }
+    double ymax = 0.0;
+    for (double y : ys) ymax = std::max(ymax, y);
+    if (qs.empty() || !(ymax > 0)) return fail(LINDHARD_EINVAL, "-Im chi has no positive zone maximum on the cut");
+    for (double &y : ys) y /= ymax;
+    auto cost = [&](double lk) {
+        const double k = exp(lk);
+        double c = 0.0;
+        for (size_t i = 0; i < qs.size(); ++i)
+            if (qs[i] > 0) {
+                const double r = ys[i] - 1.0 / (1.0 + (qs[i] / k) * (qs[i] / k));
+                c += r * r;
+            }
+        return c;
+    };
+    double a = log(dp), b = log(Q * dp);
+    const double gr = (sqrt(5.0) - 1.0) / 2.0;
+    double c = b - gr * (b - a), d = a + gr * (b - a), fc = cost(c), fd = cost(d);
+    for (int it = 0; it < 200; ++it) {
+        if (fc <= fd) {
+            b = d; d = c; fd = fc;
+            c = b - gr * (b - a);
+            fc = cost(c);
+        } else {
+            a = c; c = d; fc = fd;
+            d = a + gr * (b - a);
+            fd = cost(d);
+        }
+    }
+    *k0 = exp(0.5 * (a + b));
+    const int np = (int)qs.size();
+    if (npoints) *npoints = np;
+    for (int i = 0; i < std::min(np, max_points); ++i) {
+        if (q_out) q_out[i] = qs[i];
+        if (y_out) y_out[i] = ys[i];
+    }
+    return LINDHARD_OK;
+}
+
 extern "C" lindhard_status lindhard_kk_rpa(lindhard_plan *p, int index, const float *imchi, float *re_out,
                                            float *rpa_out, double v0, int variant, void *stream)
 {

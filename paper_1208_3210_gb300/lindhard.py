@@ -25,7 +25,7 @@ _STATUS_NAMES = {OK: "OK", EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", E
 SYMBOLS = ("lindhard_plan_create", "lindhard_plan_sizes", "lindhard_plan_workspace_bytes", "lindhard_imchi",
            "lindhard_imchi_f64", "lindhard_imchi_backward", "lindhard_plan_profile", "lindhard_plan_profile_passes",
            "lindhard_plan_pass_times",
-           "lindhard_sum_rule", "lindhard_dmu_dparams", "lindhard_kk_rpa", "lindhard_plan_variants", "lindhard_plan_status", "lindhard_plan_destroy",
+           "lindhard_sum_rule", "lindhard_dmu_dparams", "lindhard_envelope_k0", "lindhard_kk_rpa", "lindhard_plan_variants", "lindhard_plan_status", "lindhard_plan_destroy",
            "lindhard_imchi_noalloc", "lindhard_last_error")
 NOALLOC_SCRATCH_BYTES = 32 << 20
 NUM_PASSES = 7
@@ -89,6 +89,10 @@ def load(path: str = LIB_PATH):
         lib.lindhard_dmu_dparams.argtypes = [vp, ctypes.c_int, ctypes.POINTER(Band), ctypes.c_double,
                                              ctypes.POINTER(ctypes.c_double), vp]
         lib.lindhard_dmu_dparams.restype = ctypes.c_int
+        lib.lindhard_envelope_k0.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                             ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                             ctypes.c_int, ctypes.POINTER(ctypes.c_int), vp]
+        lib.lindhard_envelope_k0.restype = ctypes.c_int
         lib.lindhard_kk_rpa.argtypes = [vp, ctypes.c_int, vp, vp, vp, ctypes.c_double, ctypes.c_int, vp]
         lib.lindhard_kk_rpa.restype = ctypes.c_int
         for name in ("lindhard_plan_create", "lindhard_plan_sizes", "lindhard_plan_workspace_bytes",
@@ -248,6 +252,22 @@ class Plan:
         out = (ctypes.c_double * 4)()
         _check(load().lindhard_dmu_dparams(self._h, int(index), ctypes.byref(b), float(mu), out, _stream(stream)))
         return np.array(list(out))
+
+    def envelope_k0(self, out_i, m, index=0, stream=None):
+        """k0 of the Lorentzian envelope 1 / (1 + (q/k0)^2) of -Im chi along the
+        [100] cut at transfer index m, with the zone maxima (q, normalised
+        -Im chi) it was fitted to."""
+        import numpy as np
+        s = self.sizes[index]
+        cap = s.q_extent // max(1, self.grids[index].pts_per_zone) + 2
+        k0 = ctypes.c_double()
+        q = (ctypes.c_double * cap)()
+        y = (ctypes.c_double * cap)()
+        n = ctypes.c_int()
+        _check(load().lindhard_envelope_k0(self._h, int(index), _ptr(out_i), int(m), ctypes.byref(k0), q, y, cap,
+                                           ctypes.byref(n), _stream(stream)))
+        k = min(n.value, cap)
+        return k0.value, np.array(list(q)[:k]), np.array(list(y)[:k])
 
     def kk_rpa(self, out_i, index=0, v0=0.0, rpa=True, variant=0, stream=None):
         """Re chi by Kramers-Kronig and chi_RPA = chi / (1 - v0/|q|^2 chi) for

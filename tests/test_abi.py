@@ -89,4 +89,6 @@ def test_null_arguments(lib):
     assert lib.lindhard_imchi(None, None, None, None, None, None) == 1
     assert lib.lindhard_plan_status(None, None) == 1
     assert lib.lindhard_kk_rpa(None, 0, None, None, None, 0.0, 0, None) == 1
+    assert lib.lindhard_envelope_k0(None, 0, None, 0, None, None, None, 0, None, None) == 1
+    assert lib.lindhard_dmu_dparams(None, 0, None, 0.0, None, None) == 1
     lib.lindhard_plan_destroy(None)

@@ -1,0 +1,88 @@
+"""Envelope of -Im chi along the [100] cut (Sec. 4, Fig. 5) through the C-ABI
+against oracle.envelope_k0.
+
+On the GPU's own Im chi the library and the oracle read the same FP32 cut and
+take the same zone decisions, so the zone maxima must agree exactly and k0 to
+the golden-section resolution; against the oracle's direct-sum Im chi the
+zone maxima agree within the FP32 bar.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1208_3210_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lh():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1208_3210_gb300 import build, lindhard
+    build.build()
+    return lindhard
+
+
+def _imchi(lh, grid, band):
+    plan = lh.Plan([grid])
+    out = plan.imchi([band])
+    plan.status()
+    s = plan.sizes[0]
+    return plan, out, out.reshape(s.q_extent, s.q_extent, s.n_omega).cpu().numpy()
+
+
+@pytest.mark.parametrize("name,ms", [("small", (1, 3, 7, 15)), ("extended_256x256x256", (1, 10, 40, 100))])
+def test_envelope_matches_the_oracle_on_the_gpu_output(lh, name, ms):
+    if name == "small":
+        grid = wl.grid_params(8, 16, 32, 1.5)
+        band = wl.band_params(filling=1.1, gamma=0.08, ff_a=0.8)
+    else:
+        grid, band = wl.WORKLOADS[name]["grid"], wl.WORKLOADS[name]["band"]
+    plan, out, im = _imchi(lh, grid, band)
+    for m in ms:
+        k0, q, y = plan.envelope_k0(out, m)
+        k0_ref, q_ref, y_ref = oracle.envelope_k0(im, grid["npz"], m)
+        print(f"{name} m={m}: k0 {k0:.6f} (oracle {k0_ref:.6f}) from {len(q)} zone maxima")
+        assert np.array_equal(q, q_ref) and np.array_equal(y, y_ref)
+        assert abs(k0 - k0_ref) <= 1e-9 * k0_ref
+    plan.close()
+
+
+def test_envelope_against_the_direct_sum(lh):
+    """Against the direct sum the zone maxima are compared where they are
+    unique: each zone's largest -Im chi (the value) agrees within the FP32 bar,
+    and each lag the library picked holds a value within twice that bar of its
+    zone's direct-sum maximum (near-ties may pick another lag)."""
+    grid = wl.grid_params(8, 16, 32, 1.5)
+    band = wl.band_params(filling=1.1, gamma=0.08, ff_a=0.8)
+    plan, out, _ = _imchi(lh, grid, band)
+    b = dict(band)
+    b["mu"] = oracle.solve_mu(b["kind"], b["t"], b["tp"], b["tpp"], b["gamma"], grid["npz"], b["filling"])
+    Q, npz = grid["q_extent"], grid["npz"]
+    im_ref = oracle.imchi_full(oracle.spectral(b, grid), grid, Q, grid["n_omega"])
+    tol = 2e-5 * np.abs(im_ref).max()
+    dp = 2 * np.pi / npz
+    for m in (1, 5, 9):
+        k0, q, y = plan.envelope_k0(out, m)
+        _, q_ref, y_ref = oracle.envelope_k0(im_ref, npz, m)
+        cut = -im_ref[:, Q // 2, m]
+        zmax_ref = y_ref * max(cut[np.rint(qq / dp).astype(int) + Q // 2] for qq in q_ref)
+        picked = cut[np.rint(q / dp).astype(int) + Q // 2]
+        zmax = -(out.reshape(Q, Q, -1)[:, Q // 2, m].cpu().numpy())[np.rint(q / dp).astype(int) + Q // 2]
+        print(f"m={m}: k0 {k0:.4f} from {len(q)} zone maxima")
+        assert len(q) == len(q_ref) and k0 > 0
+        assert np.abs(zmax - zmax_ref).max() <= tol
+        assert np.all(picked >= zmax_ref - 2 * tol)
+    plan.close()
+
+
+def test_envelope_argument_checks(lh):
+    grid = wl.grid_params(8, 16, 32, 1.5)
+    plan, out, _ = _imchi(lh, grid, wl.band_params(filling=1.1, gamma=0.08))
+    with pytest.raises(lh.LindhardError, match="EINVAL"):
+        plan.envelope_k0(out, 16)                            # m >= n_omega
+    with pytest.raises(lh.LindhardError, match="EINVAL"):
+        plan.envelope_k0(out, -1)
+    plan.close()

@@ -391,3 +391,44 @@ def test_dmu_dparams_matches_central_differences_of_the_mu_solve(kind, fill, gam
         dn[r] -= h
         fd = (oracle.solve_mu(kind, *up[:3], up[3], npz, fill) - oracle.solve_mu(kind, *dn[:3], dn[3], npz, fill)) / (2 * h)
         assert abs(got[r] - fd) <= 1e-6 * max(1.0, abs(fd)), (r, got[r], fd)
+
+
+# --- envelope of -Im chi along the [100] cut (Sec. 4, Fig. 5) -----------------------
+
+def _spiky_cut(Q, npz, k, floor=0.05):
+    """-Im chi on the [100] cut equal to 1 / (1 + (q/k)^2) at the zone centres
+    q = 2 pi n and to a small fraction of it elsewhere: the zone maxima lie
+    exactly on the Lorentzian envelope."""
+    dp = 2 * math.pi / npz
+    q = (np.arange(Q) - Q // 2) * dp
+    env = 1.0 / (1.0 + (q / k) ** 2)
+    centre = ((np.arange(Q) - Q // 2) % npz) == 0
+    im = np.zeros((Q, Q, 3))
+    im[:, Q // 2, 2] = -np.where(centre, env, floor * env)
+    return im
+
+
+@pytest.mark.parametrize("k", [1.3, 4.0, 11.0])
+def test_envelope_recovers_a_lorentzian_envelope(k):
+    Q, npz = 512, 32
+    k0, qs, ys = oracle.envelope_k0(_spiky_cut(Q, npz, k), npz, 2)
+    assert abs(k0 - k) <= 1e-6 * k, (k0, k)
+    assert np.allclose(qs, 2 * math.pi * np.arange(len(qs)))      # one point per zone, at its centre
+    # the fit sees only the cut at l_y = Q/2 and transfer m, scaled freely
+    im = _spiky_cut(Q, npz, k) * 7.5
+    im[:, : Q // 2, :] = -3.0
+    im[:, Q // 2, :2] = -9.0
+    assert abs(oracle.envelope_k0(im, npz, 2)[0] - k) <= 1e-6 * k
+
+
+def test_envelope_of_the_lindhard_response_decays():
+    # on an extended grid the zone maxima of -Im chi fall off with q (the form
+    # factor |M(p)|^2 and the band) and the fitted k0 is finite and positive
+    grid = _grid(4, 8, 24, 1.5)
+    b = _band(oracle.solve_mu(0, T, TP, TPP, 0.08, 8, 1.1), 0.08, 1.0)
+    im = oracle.imchi_full(oracle.spectral(b, grid), grid, 32, 12)
+    k0, qs, ys = oracle.envelope_k0(im, 8, 6)
+    assert 0 < k0 < 32 * 2 * math.pi / 8 and ys.max() == 1.0
+    assert ys[-1] < ys[0]
+    with pytest.raises(ValueError):              # omega = 0: Im chi vanishes identically
+        oracle.envelope_k0(im, 8, 0)
