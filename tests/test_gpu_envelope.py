@@ -2,8 +2,10 @@
 against oracle.envelope_k0.
 
 On the GPU's own Im chi the library and the oracle read the same FP32 cut and
-take the same zone decisions, so the zone maxima must agree exactly and k0 to
-the golden-section resolution; against the oracle's direct-sum Im chi the
+take the same zone decisions, so the zone maxima must agree exactly; k0 agrees
+to 1e-6 (the two sum the cost in different orders, and near its flat minimum
+the golden-section comparisons can then go either way, which moves k0 by about
+the square root of the FP64 rounding, 1e-8); against the oracle's direct-sum Im chi the
 zone maxima agree within the FP32 bar.
 """
 import numpy as np
@@ -46,7 +48,7 @@ def test_envelope_matches_the_oracle_on_the_gpu_output(lh, name, ms):
         k0_ref, q_ref, y_ref = oracle.envelope_k0(im, grid["npz"], m)
         print(f"{name} m={m}: k0 {k0:.6f} (oracle {k0_ref:.6f}) from {len(q)} zone maxima")
         assert np.array_equal(q, q_ref) and np.array_equal(y, y_ref)
-        assert abs(k0 - k0_ref) <= 1e-9 * k0_ref
+        assert abs(k0 - k0_ref) <= 1e-6 * k0_ref      # cost comparisons near the flat minimum round differently
     plan.close()
 
 
