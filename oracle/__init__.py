@@ -65,6 +65,10 @@ def _load():
             lib.lo_imchi_samples.restype = None
             lib.lo_imchi_samples.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, _dp,
                                              ctypes.c_int, ctypes.c_long, _ip, _ip, _ip, _dp]
+            lib.lo_thermal_samples.restype = None
+            lib.lo_thermal_samples.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, _dp,
+                                               ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_long, _ip, _ip,
+                                               _ip, _dp]
             lib.lo_grad_A_samples.restype = None
             lib.lo_grad_A_samples.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, _dp,
                                               ctypes.c_int, ctypes.c_int, _dp, ctypes.c_long, _ip, _ip, _ip, _dp]
@@ -181,6 +185,37 @@ def imchi_full(A: np.ndarray, grid: dict, q_extent: int, n_omega: int) -> np.nda
     Q = q_extent
     lx, ly, m = np.meshgrid(np.arange(Q), np.arange(Q), np.arange(n_omega), indexing="ij")
     return imchi_samples(A, grid, Q, lx.ravel(), ly.ravel(), m.ravel()).reshape(Q, Q, n_omega)
+
+
+IMCHI_T, SQW = 1, 2
+
+
+def thermal_samples(A: np.ndarray, grid: dict, q_extent: int, kT: float, quantity: int, lx, ly, m) -> np.ndarray:
+    """Finite temperature kT > 0 (Eq. 1, Eq. A1) at the given output indices
+    (direct double sum, FP64): quantity IMCHI_T gives Im chi_T with the
+    occupation difference f(e) - f(e + w); SQW gives the dynamical structure
+    factor S(q, w) = -(1/pi) Im chi_T / (1 - exp(-w/kT)), summed as
+    (c/pi) sum A A f(e) [1 - f(e + w)].  m may be negative."""
+    assert kT > 0 and quantity in (IMCHI_T, SQW)
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    lx = np.ascontiguousarray(lx, dtype=np.int32)
+    ly = np.ascontiguousarray(ly, dtype=np.int32)
+    m = np.ascontiguousarray(m, dtype=np.int32)
+    n = lx.size
+    assert ly.size == n and m.size == n
+    N = grid["zones"] * grid["npz"]
+    assert A.shape == (N, N, grid["n_eps"])
+    out = np.empty(n, dtype=np.float64)
+    _load().lo_thermal_samples(grid["zones"], grid["npz"], grid["n_eps"], grid["e_max"], _d(A), int(q_extent),
+                               float(kT), int(quantity), n, _i(lx), _i(ly), _i(m), _d(out))
+    return out
+
+
+def thermal_full(A: np.ndarray, grid: dict, q_extent: int, n_omega: int, kT: float, quantity: int) -> np.ndarray:
+    """Every output of thermal_samples, shape [Q, Q, n_omega] (small grids only)."""
+    Q = q_extent
+    lx, ly, m = np.meshgrid(np.arange(Q), np.arange(Q), np.arange(n_omega), indexing="ij")
+    return thermal_samples(A, grid, Q, kT, quantity, lx.ravel(), ly.ravel(), m.ravel()).reshape(Q, Q, n_omega)
 
 
 def grad_A_samples(A: np.ndarray, grid: dict, q_extent: int, w: np.ndarray, ix, iy, j) -> np.ndarray:

@@ -194,6 +194,60 @@ void lo_imchi_samples(int zones, int npz, int n_eps, double e_max,
     }
 }
 
+/* Finite temperature (Sec. 2 Eq. 1, Appendix A Eq. A1).  The Fermi function
+ * of the grid energy (measured from mu) at temperature kT > 0:
+ *   f(e) = 1 / (exp(e / kT) + 1),   1 - f(e) = 1 / (exp(-e / kT) + 1).
+ * With the matrix element F of Eq. A1, the occupation difference
+ * f(e) - f(e + w) replaces the T = 0 window [-w, 0] of Eq. A3:
+ *   quantity 1: Im chi_T(q, w_m) = -c sum_{j, p} A(p, e_j) A(p+q, e_{j+m})
+ *                                      [f(e_j) - f(e_{j+m})]
+ *   quantity 2: S(q, w_m) = -(1/pi) Im chi_T(q, w_m) / (1 - exp(-w_m / kT))
+ * (the fluctuation-dissipation relation, Eq. 1), summed here in the form
+ * that also holds at w = 0:
+ *   S(q, w_m) = (c/pi) sum_{j, p} A(p, e_j) A(p+q, e_{j+m}) f(e_j) [1 - f(e_{j+m})]
+ * (f(e) [1 - f(e + w)] (1 - exp(-w/kT)) = f(e) - f(e + w) for every e, w).
+ * The sums run over cells with 0 <= j, j + m < n_eps; m may be negative.
+ * Same grid, lags and prefactor c = (de / 2 pi) / npz^2 as lo_imchi_samples. */
+void lo_thermal_samples(int zones, int npz, int n_eps, double e_max,
+                        const double *A, int q_extent, double kT, int quantity,
+                        long n, const int *lx, const int *ly, const int *m, double *out)
+{
+    long N = (long)zones * npz;
+    int periodic = (zones == 1);
+    double de = 2.0 * e_max / n_eps;
+    double c = de / (2.0 * LO_PI) / ((double)npz * (double)npz);
+    double *f = (double *)malloc(sizeof(double) * 2 * (size_t)n_eps);
+    double *fe = f + n_eps;            /* 1 - f */
+    for (int j = 0; j < n_eps; ++j) {
+        double e = -e_max + (j + 0.5) * de;
+        f[j] = 1.0 / (exp(e / kT) + 1.0);
+        fe[j] = 1.0 / (exp(-e / kT) + 1.0);
+    }
+#pragma omp parallel for schedule(dynamic, 1)
+    for (long k = 0; k < n; ++k) {
+        long sx = lx[k] - q_extent / 2, sy = ly[k] - q_extent / 2;
+        int mm = m[k];
+        double sum = 0.0;
+        for (long ix = 0; ix < N; ++ix) {
+            long jx = lo_shift(ix, sx, N, periodic);
+            if (jx < 0) continue;
+            for (long iy = 0; iy < N; ++iy) {
+                long jy = lo_shift(iy, sy, N, periodic);
+                if (jy < 0) continue;
+                const double *a = A + ((size_t)ix * N + iy) * n_eps;
+                const double *b = A + ((size_t)jx * N + jy) * n_eps;
+                for (int j = 0; j < n_eps; ++j) {
+                    if (j + mm < 0 || j + mm >= n_eps) continue;
+                    double wgt = quantity == 1 ? f[j] - f[j + mm] : f[j] * fe[j + mm];
+                    sum += a[j] * b[j + mm] * wgt;
+                }
+            }
+        }
+        out[k] = quantity == 1 ? -c * sum : c / LO_PI * sum;
+    }
+    free(f);
+}
+
 /* Gradient of L = sum_{l,m} w[l_x][l_y][m] Im chi(q_l, w_m) with respect to
  * A(p_i, e_j), at n sample points (ix[k], iy[k], j[k]).  Eq. 9 is bilinear in
  * the occupied part a = A [e < 0] and the empty part b = A [e >= 0]:

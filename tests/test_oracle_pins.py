@@ -432,3 +432,123 @@ def test_envelope_of_the_lindhard_response_decays():
     assert ys[-1] < ys[0]
     with pytest.raises(ValueError):              # omega = 0: Im chi vanishes identically
         oracle.envelope_k0(im, 8, 0)
+
+
+# --- finite temperature: Im chi_T and S(q, w) (Eq. 1, Appendix A Eq. A1) -----------
+
+def _fermi(grid, kT):
+    n_eps = grid["n_eps"]
+    e = -grid["e_max"] + (np.arange(n_eps) + 0.5) * (2 * grid["e_max"] / n_eps)
+    return 1.0 / (np.exp(e / kT) + 1.0), 1.0 / (np.exp(-e / kT) + 1.0)
+
+
+def _thermal_fft(A, grid, Q, n_omega, kT):
+    """Im chi_T and S through the convolution theorem: C(q, w) = sum A f (p, e)
+    A (1 - f) (p + q, e + w) over every lag by zero-padded FP64 numpy FFTs;
+    Im chi_T = -c [C(q, w) - C(-q, -w)], S = (c/pi) C(q, w)."""
+    N, _, n_eps = A.shape
+    f, fe = _fermi(grid, kT)
+    periodic = grid["zones"] == 1
+    P = N if periodic else 2 * N
+    PE = 2 * n_eps
+    fa = np.fft.fftn(A * f, s=(P, P, PE), axes=(0, 1, 2))
+    fb = np.fft.fftn(A * fe, s=(P, P, PE), axes=(0, 1, 2))
+    corr = np.fft.ifftn(np.conj(fa) * fb).real
+    s = (np.arange(Q) - Q // 2) % P
+    sn = (-(np.arange(Q) - Q // 2)) % P
+    m = np.arange(n_omega)
+    C = corr[np.ix_(s, s, m)]
+    Cn = corr[np.ix_(sn, sn, (-m) % PE)]
+    _, _, _, c = oracle.grid_sizes(grid["zones"], grid["npz"], n_eps, grid["e_max"])
+    return -c * (C - Cn), c / math.pi * C
+
+
+def _thermal_case(zones, npz, n_eps, e_max, gamma=0.1, ff_a=0.8):
+    grid = _grid(zones, npz, n_eps, e_max)
+    b = _band(oracle.solve_mu(0, T, TP, TPP, gamma, npz, 1.1), gamma, ff_a)
+    return grid, oracle.spectral(b, grid)
+
+
+def test_thermal_zero_temperature_limit():
+    # kT far below the half cell de/2: every grid occupation is exactly 0 or 1
+    # and the finite-temperature sums reduce term by term to Eq. 9
+    grid, A = _thermal_case(2, 8, 24, 1.5)
+    Q, nw = 16, 12
+    kT = (2 * 1.5 / 24) / 4000
+    ref = oracle.imchi_full(A, grid, Q, nw)
+    im = oracle.thermal_full(A, grid, Q, nw, kT, oracle.IMCHI_T)
+    s = oracle.thermal_full(A, grid, Q, nw, kT, oracle.SQW)
+    assert np.array_equal(im, ref)
+    assert np.allclose(s[..., 1:], -ref[..., 1:] / math.pi, rtol=1e-14, atol=0)
+    assert np.all(s[..., 0] == 0.0)
+
+
+@pytest.mark.parametrize("zones,npz,n_eps,kT", [(2, 8, 24, 0.03), (2, 8, 23, 0.3), (1, 16, 20, 0.1)])
+def test_thermal_against_fft_correlation(zones, npz, n_eps, kT):
+    grid, A = _thermal_case(zones, npz, n_eps, 1.5)
+    Q = zones * npz if zones == 1 else 2 * zones * npz
+    nw = n_eps // 2
+    im_fft, s_fft = _thermal_fft(A, grid, Q, nw, kT)
+    im = oracle.thermal_full(A, grid, Q, nw, kT, oracle.IMCHI_T)
+    s = oracle.thermal_full(A, grid, Q, nw, kT, oracle.SQW)
+    assert np.abs(im - im_fft).max() <= 1e-12 * np.abs(im_fft).max()
+    assert np.abs(s - s_fft).max() <= 1e-12 * np.abs(s_fft).max()
+    assert np.abs(im[..., 0]).max() <= 1e-13 * np.abs(im).max()     # Im chi_T(q, 0) = 0 (inversion-symmetric A)
+
+
+def test_fluctuation_dissipation_and_detailed_balance():
+    # Eq. 1: S (1 - exp(-w/kT)) = -Im chi_T / pi; and S(-q, -w) = exp(-w/kT) S(q, w),
+    # on a random A with no symmetry
+    grid = _grid(2, 6, 18, 1.2)
+    A = np.random.default_rng(5).random((12, 12, 18))
+    kT, Q = 0.15, 24
+    de = 2 * 1.2 / 18
+    rng = np.random.default_rng(6)
+    lx, ly = rng.integers(1, Q, 60), rng.integers(1, Q, 60)
+    m = rng.integers(1, 10, 60)
+    im = oracle.thermal_samples(A, grid, Q, kT, oracle.IMCHI_T, lx, ly, m)
+    s = oracle.thermal_samples(A, grid, Q, kT, oracle.SQW, lx, ly, m)
+    boltz = np.exp(-m * de / kT)
+    assert np.allclose(s * (1 - boltz), -im / math.pi, rtol=1e-12, atol=0)
+    s_rev = oracle.thermal_samples(A, grid, Q, kT, oracle.SQW, Q - lx, Q - ly, -m)
+    im_rev = oracle.thermal_samples(A, grid, Q, kT, oracle.IMCHI_T, Q - lx, Q - ly, -m)
+    assert np.allclose(s_rev, boltz * s, rtol=1e-12, atol=0)
+    assert np.allclose(im_rev, -im, rtol=1e-12, atol=0)
+
+
+def test_thermal_high_temperature_limit():
+    # kT >> the window: f(e) - f(e + w) -> w / 4kT and f (1 - f) -> 1/4, so
+    # both reduce to the unweighted correlation of A with itself
+    grid, A = _thermal_case(2, 6, 16, 1.0)
+    Q, nw, kT = 12, 8, 1e6
+    _, _, de, c = oracle.grid_sizes(2, 6, 16, 1.0)
+    lx, ly, m = [a.ravel() for a in np.meshgrid(np.arange(Q), np.arange(Q), np.arange(1, nw), indexing="ij")]
+    N = 12
+    plain = np.zeros(lx.size)
+    for k in range(lx.size):
+        sx, sy = lx[k] - Q // 2, ly[k] - Q // 2
+        x0, x1 = max(0, -sx), min(N, N - sx)
+        y0, y1 = max(0, -sy), min(N, N - sy)
+        a = A[x0:x1, y0:y1, : 16 - m[k]]
+        b = A[x0 + sx:x1 + sx, y0 + sy:y1 + sy, m[k]:]
+        plain[k] = np.sum(a * b)
+    im = oracle.thermal_samples(A, grid, Q, kT, oracle.IMCHI_T, lx, ly, m)
+    s = oracle.thermal_samples(A, grid, Q, kT, oracle.SQW, lx, ly, m)
+    w = m * de
+    assert np.allclose(im * 4 * kT / w, -c * plain, rtol=1e-9, atol=0)
+    assert np.allclose(s * 4 * math.pi / c, plain, rtol=1e-5, atol=0)
+
+
+def test_thermal_sum_rule():
+    # summed over every lag the momentum correlation factorises into densities
+    # of states D(e_j) = sum_p A(p, e_j):
+    #   sum_q Im chi_T(q, w_m) = -c sum_j D_j D_{j+m} [f_j - f_{j+m}]
+    grid, A = _thermal_case(2, 6, 20, 1.5)
+    Q, nw, kT = 24, 10, 0.07
+    _, _, _, c = oracle.grid_sizes(2, 6, 20, 1.5)
+    im = oracle.thermal_full(A, grid, Q, nw, kT, oracle.IMCHI_T)
+    D = A.sum(axis=(0, 1))
+    f, _ = _fermi(grid, kT)
+    for mm in range(nw):
+        ref = -c * sum(D[j] * D[j + mm] * (f[j] - f[j + mm]) for j in range(20 - mm))
+        assert abs(im[..., mm].sum() - ref) <= 1e-12 * max(abs(ref), np.abs(im).max())
