@@ -75,6 +75,23 @@ typedef enum {
     LINDHARD_FP64 = 2           /* FP64 everywhere; FFT lengths <= 256 only   */
 } lindhard_precision;
 
+/* What a grid's output holds (lindhard_grid.quantity).  With kT > 0 the
+ * Fermi function f(e) = 1 / (exp(e / kT) + 1) of the grid energy (measured
+ * from mu) replaces the T = 0 split: the occupied part is A f, the empty part
+ * A (1 - f) (Appendix A, Eq. A1, whose occupation difference f(e) - f(e + w)
+ * reduces to the window [-w, 0] of Eq. A3 at T = 0). */
+typedef enum {
+    LINDHARD_IMCHI = 0,         /* Im chi(q, w) at T = 0 (Eq. 9); band.kT = 0  */
+    LINDHARD_IMCHI_T = 1,       /* Im chi_T(q, w) = -c sum_{p,j} A(p, e_j)
+                                   A(p + q, e_{j+m}) [f(e_j) - f(e_{j+m})],
+                                   c = (de / 2 pi) / pts_per_zone^2; band.kT > 0 */
+    LINDHARD_SQW = 2            /* dynamical structure factor (Sec. 2, Eq. 1):
+                                   S(q, w) = -(1/pi) Im chi_T(q, w) / (1 - exp(-w/kT)),
+                                   computed as (c / pi) sum A(p, e_j) A(p + q, e_{j+m})
+                                   f(e_j) [1 - f(e_{j+m})], the same quantity
+                                   with its w -> 0 limit at m = 0; >= 0; band.kT > 0 */
+} lindhard_quantity;
+
 /* One instance's physics, eV, lattice constant 1 (Sec. 2 Eqs. 4-5, Sec. 3). */
 typedef struct {
     double t, tp, tpp;  /* tight-binding hoppings: xi_p = -2t (cos px + cos py)
@@ -88,6 +105,12 @@ typedef struct {
     double ff_a;        /* |M(p)|^2 = exp(-|p|^2 ff_a^2 / 8); 0 => |M|^2 = 1   */
     int band_kind;      /* 0 tight binding; 1 free electrons, xi = |p|^2/2 - mu */
     int reserved;       /* must be 0                                          */
+    double kT;          /* temperature, eV: 0 for LINDHARD_IMCHI grids, finite
+                           and > 0 for LINDHARD_IMCHI_T and LINDHARD_SQW.  The
+                           filling fixes mu by the T = 0 count above (the
+                           thermal shift of mu is not applied; give mu with
+                           filling = NaN to set it).  With a caller-supplied A
+                           only kT is read.                                   */
 } lindhard_band;
 
 /* One instance's grid. */
@@ -100,7 +123,9 @@ typedef struct {
     int q_extent;       /* lags kept per axis, even; 0 => N; <= 2N (zones > 1),
                            <= N (zones == 1)                                 */
     int precision;      /* lindhard_precision                                 */
-    int reserved;       /* must be 0                                          */
+    int quantity;       /* lindhard_quantity; LINDHARD_IMCHI_T and LINDHARD_SQW
+                           pad the energy FFT to PE >= n_eps + n_omega - 1
+                           (the occupied and empty parts overlap in energy)  */
 } lindhard_grid;
 
 typedef struct lindhard_plan lindhard_plan;
@@ -162,12 +187,14 @@ lindhard_status lindhard_plan_sizes(const lindhard_plan *plan, int index,
 lindhard_status lindhard_plan_workspace_bytes(const lindhard_plan *plan,
                                               size_t *out);
 
-/* Forward: Im chi(q_l, w_m) for every instance (Eq. 9).
+/* Forward: Im chi(q_l, w_m) for every instance (Eq. 9), or the finite-
+ * temperature quantity its grid names (lindhard_quantity).
  *   bands : host [batch]; read before return.
  *   A_in  : device, optional.  NULL => A is generated from bands (Eqs. 4-5).
  *           Otherwise the batch-concatenated caller A(p_i, e_j), float32,
  *           layout [N][N][n_eps] per instance (e fastest), and bands are
- *           ignored (may be NULL).
+ *           ignored (may be NULL) unless a grid is LINDHARD_IMCHI_T or
+ *           LINDHARD_SQW: then bands[i].kT is read.
  *   out   : device, float32, batch-concatenated, layout [Q][Q][n_omega] per
  *           instance (w fastest).
  * Every grid of the plan must use LINDHARD_FP32 (see lindhard_imchi_f64).
@@ -197,7 +224,8 @@ lindhard_status lindhard_imchi_f64(lindhard_plan *plan, const lindhard_band *ban
  *             dL/d(t, t', t'', mu, gamma) by the chain rule through Eqs. 4-5
  *             (A_in must be NULL), mu held fixed (a partial derivative even
  *             when mu was solved from the filling).
- * At least one of dA and dparams must be non-NULL. */
+ * At least one of dA and dparams must be non-NULL.  LINDHARD_IMCHI grids only
+ * (others: LINDHARD_EUNSUPPORTED). */
 lindhard_status lindhard_imchi_backward(lindhard_plan *plan,
                                         const lindhard_band *bands,
                                         const float *A_in, const float *w,
@@ -236,7 +264,8 @@ lindhard_status lindhard_plan_pass_times(lindhard_plan *plan, double *ms, long l
  *   band / A_in : as in lindhard_imchi for that instance (A regenerated).
  *   sum_q    : device, double [n_omega]: left side, reduced from out in FP64.
  *   dos_corr : device, double [n_omega]: right side, from A in FP64.
- * Uses the plan's workspace (do not overlap with a call of the same plan). */
+ * Uses the plan's workspace (do not overlap with a call of the same plan).
+ * LINDHARD_IMCHI grids only (others: LINDHARD_EUNSUPPORTED). */
 lindhard_status lindhard_sum_rule(lindhard_plan *plan, int index, const lindhard_band *band,
                                   const float *A_in, const float *out, double *sum_q, double *dos_corr,
                                   void *stream);
@@ -265,7 +294,8 @@ lindhard_status lindhard_dmu_dparams(lindhard_plan *plan, int index, const lindh
  * [ln dp, ln (Q dp)]).  k0 in units of 1/a (lattice constant a = 1).
  * imchi: device, the instance's [Q][Q][n_omega] block.  k0: host double.
  * q_out, y_out: host double[max_points] for the points, or NULL; npoints: host
- * int (the number of points), or NULL.  Synchronises `stream`. */
+ * int (the number of points), or NULL.  Im chi grids (LINDHARD_IMCHI,
+ * LINDHARD_IMCHI_T) only.  Synchronises `stream`. */
 lindhard_status lindhard_envelope_k0(lindhard_plan *plan, int index, const float *imchi, int m, double *k0,
                                      double *q_out, double *y_out, int max_points, int *npoints, void *stream);
 
@@ -284,8 +314,9 @@ lindhard_status lindhard_envelope_k0(lindhard_plan *plan, int index, const float
  * on the tensor cores (BF16 hi/lo, three products, FP32 accumulation) and the
  * near band in FP32, n_omega <= 256; variant 1: FP32 SIMT throughout,
  * n_omega <= 1536 (otherwise LINDHARD_EUNSUPPORTED).  Plans whose grid is
- * LINDHARD_FP64 are rejected (LINDHARD_EINVAL).  Enqueued on `stream`; no
- * synchronisation. */
+ * LINDHARD_FP64 are rejected (LINDHARD_EINVAL), and so are LINDHARD_SQW
+ * grids (the relation reads Im chi; LINDHARD_IMCHI_T is accepted).  Enqueued
+ * on `stream`; no synchronisation. */
 lindhard_status lindhard_kk_rpa(lindhard_plan *plan, int index, const float *imchi, float *re_out,
                                 float *rpa_out, double v0, int variant, void *stream);
 

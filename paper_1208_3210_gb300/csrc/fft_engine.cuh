@@ -40,6 +40,11 @@ template <typename C> __device__ __forceinline__ C csub(C a, C b) { return mk<C>
 template <typename C> __device__ __forceinline__ C cmul(C a, C b) { return mk<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
 template <typename C> __device__ __forceinline__ C cmulc(C a, C b) { return mk<C>(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y); } // a * conj(b)
 template <typename C> __device__ __forceinline__ C cconj(C a) { return mk<C>(a.x, -a.y); }
+// odd ? p - conj(p) = 2 i Im p : p (the transform of the odd part of a real sequence)
+template <typename C> __device__ __forceinline__ C odd_part(C p, bool odd)
+{
+    return odd ? mk<C>(decltype(p.x)(0), p.y + p.y) : p;
+}
 template <typename C> __device__ __forceinline__ C mul_i(C a) { return mk<C>(-a.y, a.x); }   //  i * a
 template <typename C> __device__ __forceinline__ C mul_mi(C a) { return mk<C>(a.y, -a.x); }  // -i * a
 

@@ -3,7 +3,8 @@
 //
 //   k_fwd_energy : generates A(p, e) for a tile of momentum points (Eqs. 4-5),
 //                  splits it at e = 0 into the occupied part a and the empty
-//                  part b (T = 0 split, Appendix A Eq. A3), transforms
+//                  part b (T = 0 split, Appendix A Eq. A3; at temperature
+//                  kT > 0, a = A f and b = A (1 - f), Eq. A1), transforms
 //                  z = a + i b along energy, and separates the two transforms
 //                  a^(k) = (Z(k) + conj Z(-k)) / 2, b^(k) = (Z(k) - conj Z(-k)) / 2i
 //                  for the non-redundant frequencies k in [0, PE/2].
@@ -103,8 +104,24 @@ k_fwd_energy(Geom g, Band band, const AxisTab *__restrict__ axis,
                     else A = s_amp[col] / d;
                 }
             }
-            // occupied (e_n < 0) -> real part, empty -> imaginary part
-            v[b * E::R0 + r] = (n < g.J0) ? mk<Cx>(A, (Real)0) : mk<Cx>((Real)0, A);
+            if (band.kT > 0) {
+                // finite temperature (Appendix A, Eq. A1): occupied part A f,
+                // empty part A (1 - f), f = 1 / (exp(x) + 1), x = e_n / kT, both
+                // from u = exp(-|x|) so that neither loses digits to 1 - f
+                Real x, u;
+                if constexpr (sizeof(Real) == 4) {
+                    x = (Real)(2 * n + 1 - g.n_eps) * band.x_step;
+                    u = expf(-fabsf(x));
+                } else {
+                    x = (Real)(2 * n + 1 - g.n_eps) * (Real)band.x_step64;
+                    u = exp(-fabs(x));
+                }
+                const Real big = (Real)1 / ((Real)1 + u), small = u * big;
+                v[b * E::R0 + r] = x < 0 ? mk<Cx>(A * big, A * small) : mk<Cx>(A * small, A * big);
+            } else {
+                // occupied (e_n < 0) -> real part, empty -> imaginary part
+                v[b * E::R0 + r] = (n < g.J0) ? mk<Cx>(A, (Real)0) : mk<Cx>((Real)0, A);
+            }
         }
     }
 

@@ -58,9 +58,11 @@ k_x_product(Geom g, const cx<Real> *__restrict__ U2, cx<Real> *__restrict__ U3,
             else { va[b * EF::R0 + r] = zero; vb[b * EF::R0 + r] = zero; }
         }
     EF::run(va, vb, sm, tw);
-    // conj(a^) * b^ : transform of the correlation sum_p a(p) b(p + q)
+    // conj(a^) * b^ : transform of the correlation C(q) = sum_p a(p) b(p + q);
+    // for Im chi_T its odd part C(q) - C(-q), transform P - conj(P) = 2 i Im P
+    const bool odd = g.quantity == LINDHARD_IMCHI_T;
 #pragma unroll
-    for (int i = 0; i < EF::VPT; ++i) va[i] = cmulc(vb[i], va[i]);
+    for (int i = 0; i < EF::VPT; ++i) va[i] = odd_part(cmulc(vb[i], va[i]), odd);
     EI::run(va, sm, tw);
     if (valid) {
         Cx *dst = U3 + (long long)ky * g.SP + c;

@@ -233,6 +233,7 @@ k_x_product_tma(Geom g, const __grid_constant__ CUtensorMap map, float2 *__restr
     __syncthreads();
     unsigned parity = 0;
     const int col = (int)(threadIdx.x % C);
+    const bool odd = g.quantity == LINDHARD_IMCHI_T;   // Im chi_T: the odd part P - conj(P)
     for (int t = run.t; t < run.end; t += run.step) {
         const int ky = t / tiles_x, c0 = (t % tiles_x) * C;
         if (!tile_ready(bar, parity, status)) { drain(bar, parity); return; }
@@ -260,7 +261,7 @@ k_x_product_tma(Geom g, const __grid_constant__ CUtensorMap map, float2 *__restr
         }
         EF::run(va, vb, sm, tw);
 #pragma unroll
-        for (int i = 0; i < EF::VPT; ++i) va[i] = cmulc(vb[i], va[i]);   // conj(a^) b^
+        for (int i = 0; i < EF::VPT; ++i) va[i] = odd_part(cmulc(vb[i], va[i]), odd);   // conj(a^) b^
         EI::run(va, sm, tw);
         const int c = c0 + col;
         if (c < g.H) {

@@ -24,8 +24,10 @@ struct Geom {
     int Q;          // lags kept per momentum axis
     int n_omega;    // energy transfers kept
     int band_kind;  // 0 tight binding, 1 free electrons
+    int quantity;   // lindhard_quantity: 0 Im chi (T = 0), 1 Im chi_T, 2 S(q, w)
     double e_max, de, dp;
     double scale;   // -(de / 2 pi) / npz^2 / (P * P * PE): Eq. 9 prefactor and FFT norm
+                    // (for S(q, w): +(de / 2 pi) / npz^2 / pi / (P * P * PE))
 };
 
 // Per-call physics of one instance, passed by value to the kernels.
@@ -36,6 +38,9 @@ struct Band {
     // FP32 forms for the energy pass: -2t, -4t', -2t'' as unevaluated
     // (hi, lo) pairs, and gamma / pi
     float k1[2], k2[2], k3[2], gam_pi;
+    // temperature (0: the T = 0 split); e_j / kT = (2 j + 1 - n_eps) x_step
+    double kT, x_step64;
+    float x_step;
 };
 
 // Device-side per-instance state written by the set-up kernels.

@@ -24,7 +24,7 @@
 
 namespace lh {
 lindhard_status geom_from_grid(const lindhard_grid &gr, Geom &g, int &prec);
-lindhard_status band_from_params(const lindhard_band *b, Band &o);
+lindhard_status band_for_call(const Geom &g, const lindhard_band *b, bool generate, Band &o);
 lindhard_status set_error(lindhard_status st, const char *msg);
 cudaError_t launch_twiddles(int len, float2 *tw32, double2 *tw64, cudaStream_t s);
 cudaError_t launch_setup(const Geom &g, const Band &band, AxisTab *axis, float2 *eps32, double *eps64,
@@ -93,12 +93,8 @@ extern "C" lindhard_status lindhard_imchi_noalloc(const lindhard_grid *grid, con
     if (st != LINDHARD_OK) return st;
     if (prec != LINDHARD_FP32) return set_error(LINDHARD_EINVAL, "lindhard_imchi_noalloc computes in FP32 only");
     Band b = {};
-    if (A_in == nullptr) {
-        st = band_from_params(band, b);
-        if (st != LINDHARD_OK) return st;
-        if (b.band_kind == 1 && g.periodic)
-            return set_error(LINDHARD_EINVAL, "free electrons need zones > 1 (the band is not periodic)");
-    }
+    st = band_for_call(g, band, A_in == nullptr, b);
+    if (st != LINDHARD_OK) return st;
     unsigned char *base = nullptr;
     int num_sms = 0;
     st = scratch_for_device(&base, &num_sms);

@@ -202,7 +202,8 @@ static size_t cx_bytes(int prec) { return prec == LINDHARD_FP64 ? 16 : 8; }
 
 static lindhard_status make_geom(const lindhard_grid &gr, Geom &g, int &prec)
 {
-    if (gr.reserved != 0) return fail(LINDHARD_EINVAL, "grid.reserved must be 0");
+    if (gr.quantity != LINDHARD_IMCHI && gr.quantity != LINDHARD_IMCHI_T && gr.quantity != LINDHARD_SQW)
+        return fail(LINDHARD_EINVAL, "quantity must be LINDHARD_IMCHI, LINDHARD_IMCHI_T or LINDHARD_SQW");
     if (gr.zones < 1) return fail(LINDHARD_EINVAL, "zones must be >= 1");
     if (gr.pts_per_zone < 2 || gr.pts_per_zone % 2) return fail(LINDHARD_EINVAL, "pts_per_zone must be even and >= 2");
     if (gr.n_eps < 2) return fail(LINDHARD_EINVAL, "n_eps must be >= 2");
@@ -228,8 +229,11 @@ static lindhard_status make_geom(const lindhard_grid &gr, Geom &g, int &prec)
         P = next_len_p(N + Q / 2, gr.precision);
     }
     // energy: with the occupied/empty split every lag m in [0, PE) is alias-free
-    // once PE >= n_eps (the occupied part sits below the empty part).
-    long long PE = next_len(gr.n_eps);
+    // once PE >= n_eps (the occupied part sits below the empty part).  At
+    // finite temperature both parts cover the whole window, lags run over
+    // (-n_eps, n_eps), and the kept ones [0, n_omega) and their mirrors
+    // (-n_omega, 0] stay clear of wrapped partners once PE >= n_eps + n_omega - 1.
+    long long PE = gr.quantity == LINDHARD_IMCHI ? next_len(gr.n_eps) : next_len(gr.n_eps + n_omega - 1);
     long long maxlen = gr.precision == LINDHARD_FP64 ? kMaxLen64 : kMaxLen;
     if (P > maxlen || PE > maxlen) return fail(LINDHARD_EUNSUPPORTED, "FFT length beyond the compiled range");
     if (gr.precision == LINDHARD_SPLITBF16_TC && !tc_supported((int)P))
@@ -257,6 +261,8 @@ static lindhard_status make_geom(const lindhard_grid &gr, Geom &g, int &prec)
     g.de = 2.0 * gr.e_max / gr.n_eps;
     g.dp = 2.0 * M_PI / gr.pts_per_zone;
     g.scale = -(g.de / (2.0 * M_PI)) / ((double)g.npz * g.npz) / ((double)P * P * PE);
+    g.quantity = gr.quantity;
+    if (gr.quantity == LINDHARD_SQW) g.scale = -g.scale / M_PI;   // (c / pi) sum A A f (1 - f)
     prec = gr.precision;
     return LINDHARD_OK;
 }
@@ -550,6 +556,30 @@ extern "C" lindhard_status lindhard_plan_workspace_bytes(const lindhard_plan *p,
     return LINDHARD_OK;
 }
 
+// The temperature fields of a band (all that a caller-supplied A needs).
+static lindhard_status band_temperature(const lindhard_band *b, Band &o)
+{
+    if (!(b->kT >= 0) || !isfinite(b->kT)) return fail(LINDHARD_EINVAL, "kT must be finite and >= 0");
+    o.kT = b->kT;
+    o.x_step64 = 0.0;
+    o.x_step = 0.0f;
+    return LINDHARD_OK;
+}
+
+// kT against the grid's quantity, and e_j / kT = (2 j + 1 - n_eps) x_step.
+static lindhard_status band_for_geom(const Geom &g, Band &o)
+{
+    if (g.quantity == LINDHARD_IMCHI && o.kT != 0.0)
+        return fail(LINDHARD_EINVAL, "kT must be 0 for LINDHARD_IMCHI grids (use LINDHARD_IMCHI_T or LINDHARD_SQW)");
+    if (g.quantity != LINDHARD_IMCHI && !(o.kT > 0))
+        return fail(LINDHARD_EINVAL, "LINDHARD_IMCHI_T and LINDHARD_SQW grids need kT > 0");
+    if (o.kT > 0) {
+        o.x_step64 = 0.5 * g.de / o.kT;
+        o.x_step = (float)o.x_step64;
+    }
+    return LINDHARD_OK;
+}
+
 static lindhard_status make_band(const lindhard_band *b, Band &o)
 {
     if (!b) return fail(LINDHARD_EINVAL, "bands must be non-NULL when A is generated");
@@ -576,6 +606,8 @@ static lindhard_status make_band(const lindhard_band *b, Band &o)
     pair(-4.0 * b->tp, o.k2);
     pair(-2.0 * b->tpp, o.k3);
     o.gam_pi = (float)(b->gamma / M_PI);
+    lindhard_status st = band_temperature(b, o);
+    if (st != LINDHARD_OK) return st;
     if (o.solve_mu) {
         if (!(b->filling > 0 && b->filling < 2)) return fail(LINDHARD_EINVAL, "filling must be in (0, 2) or NaN");
     } else if (!isfinite(b->mu)) {
@@ -627,13 +659,29 @@ static cudaError_t fork_end(lindhard_plan *p, cudaStream_t s)
     return e;
 }
 
-static lindhard_status bands_of(lindhard_plan *p, const lindhard_band *bands, std::vector<Band> &bs)
+// The band of one instance for a call: every field when A is generated; with
+// a caller-supplied A only the temperature, and only for finite-temperature
+// grids.
+static lindhard_status band_of_instance(const Geom &g, const lindhard_band *b, bool generate, Band &o)
+{
+    lindhard_status st = LINDHARD_OK;
+    o = Band{};
+    if (generate) {
+        st = make_band(b, o);
+        if (st == LINDHARD_OK && o.band_kind == 1 && g.periodic)
+            st = fail(LINDHARD_EINVAL, "free electrons need zones > 1 (the band is not periodic)");
+    } else if (g.quantity != LINDHARD_IMCHI) {
+        if (!b) return fail(LINDHARD_EINVAL, "finite-temperature grids need bands (kT) with a caller-supplied A");
+        st = band_temperature(b, o);
+    }
+    return st == LINDHARD_OK ? band_for_geom(g, o) : st;
+}
+
+static lindhard_status bands_of(lindhard_plan *p, const lindhard_band *bands, bool generate, std::vector<Band> &bs)
 {
     for (int i = 0; i < p->batch; ++i) {
-        lindhard_status st = make_band(bands ? bands + i : nullptr, bs[i]);
+        lindhard_status st = band_of_instance(p->geoms[i], bands ? bands + i : nullptr, generate, bs[i]);
         if (st != LINDHARD_OK) return st;
-        if (bs[i].band_kind == 1 && p->geoms[i].periodic)
-            return fail(LINDHARD_EINVAL, "free electrons need zones > 1 (the band is not periodic)");
     }
     return LINDHARD_OK;
 }
@@ -686,8 +734,8 @@ static lindhard_status forward_impl(lindhard_plan *p, const lindhard_band *bands
         if ((p->precision[i] == LINDHARD_FP64) != (want_prec == LINDHARD_FP64))
             return fail(LINDHARD_EINVAL, "plan precision does not match the entry point");
     std::vector<Band> bs(p->batch);
-    if (A_in == nullptr) {
-        lindhard_status st = bands_of(p, bands, bs);
+    {
+        lindhard_status st = bands_of(p, bands, A_in == nullptr, bs);
         if (st != LINDHARD_OK) return st;
     }
     cudaStream_t s = (cudaStream_t)stream;
@@ -699,7 +747,10 @@ static lindhard_status forward_impl(lindhard_plan *p, const lindhard_band *bands
     // values; a call that differs in any of them captures again and updates
     // the executable graph in place.
     bool same = p->exec && p->key_A == (const void *)A_in && p->key_out == (void *)out && p->key_mu == mu_out;
-    if (same && A_in == nullptr) {
+    bool reads_bands = A_in == nullptr;
+    for (int i = 0; i < p->batch; ++i) reads_bands = reads_bands || p->geoms[i].quantity != LINDHARD_IMCHI;
+    if (same && reads_bands) {
+        same = p->key_bands.size() == (size_t)p->batch;
         for (int i = 0; i < p->batch && same; ++i) same = memcmp(&p->key_bands[i], &bands[i], sizeof(lindhard_band)) == 0;
     }
     cudaError_t e = cudaSuccess;
@@ -764,14 +815,13 @@ extern "C" lindhard_status lindhard_imchi_backward(lindhard_plan *p, const lindh
     if (!p->backward) return fail(LINDHARD_EINVAL, "create the plan with LINDHARD_PLAN_BACKWARD");
     if (!dA && !dparams) return fail(LINDHARD_EINVAL, "nothing to compute: dA and dparams are both NULL");
     if (dparams && A_in) return fail(LINDHARD_EINVAL, "dparams needs the generated A (A_in must be NULL)");
+    for (int i = 0; i < p->batch; ++i)
+        if (p->geoms[i].quantity != LINDHARD_IMCHI)
+            return fail(LINDHARD_EUNSUPPORTED, "the adjoint is built for LINDHARD_IMCHI grids only");
     std::vector<Band> bs(p->batch);
-    if (A_in == nullptr) {
-        for (int i = 0; i < p->batch; ++i) {
-            lindhard_status st = make_band(bands ? bands + i : nullptr, bs[i]);
-            if (st != LINDHARD_OK) return st;
-            if (bs[i].band_kind == 1 && p->geoms[i].periodic)
-                return fail(LINDHARD_EINVAL, "free electrons need zones > 1 (the band is not periodic)");
-        }
+    {
+        lindhard_status st = bands_of(p, bands, A_in == nullptr, bs);
+        if (st != LINDHARD_OK) return st;
     }
     cudaStream_t s0 = (cudaStream_t)stream;
     size_t a_off = 0, o_off = 0;
@@ -819,13 +869,13 @@ extern "C" lindhard_status lindhard_sum_rule(lindhard_plan *p, int index, const 
     if (index < 0 || index >= p->batch) return fail(LINDHARD_EINVAL, "index out of range");
     if (p->precision[index] == LINDHARD_FP64) return fail(LINDHARD_EINVAL, "the sum rule reads FP32 outputs");
     const Geom &g = p->geoms[index];
+    if (g.quantity != LINDHARD_IMCHI) return fail(LINDHARD_EUNSUPPORTED, "the sum rule is built for LINDHARD_IMCHI grids only");
     if (g.Q != (g.periodic ? g.N : 2 * g.N))
         return fail(LINDHARD_EINVAL, "the sum rule needs every lag: q_extent = N (one zone) or 2N (several)");
     Band b = {};
-    if (A_in == nullptr) {
-        lindhard_status st = make_band(band, b);
+    {
+        lindhard_status st = band_of_instance(g, band, A_in == nullptr, b);
         if (st != LINDHARD_OK) return st;
-        if (b.band_kind == 1 && g.periodic) return fail(LINDHARD_EINVAL, "free electrons need zones > 1");
     }
     cudaStream_t s = (cudaStream_t)stream;
     Work<float> w = work_of<float>(p, index);
@@ -884,6 +934,7 @@ extern "C" lindhard_status lindhard_envelope_k0(lindhard_plan *p, int index, con
     if (index < 0 || index >= p->batch) return fail(LINDHARD_EINVAL, "index out of range");
     if (p->precision[index] == LINDHARD_FP64) return fail(LINDHARD_EINVAL, "the envelope reads FP32 outputs");
     const Geom &g = p->geoms[index];
+    if (g.quantity == LINDHARD_SQW) return fail(LINDHARD_EINVAL, "the envelope reads Im chi (not S(q, w))");
     if (m < 0 || m >= g.n_omega) return fail(LINDHARD_EINVAL, "transfer index out of range");
     if ((q_out || y_out) && max_points < 1) return fail(LINDHARD_EINVAL, "max_points must be >= 1");
     const int Q = g.Q, npz = g.npz;
@@ -952,6 +1003,7 @@ extern "C" lindhard_status lindhard_kk_rpa(lindhard_plan *p, int index, const fl
     if (variant != 0 && variant != 1) return fail(LINDHARD_EINVAL, "variant must be 0 (tensor cores) or 1 (FP32 SIMT)");
     if (!isfinite(v0)) return fail(LINDHARD_EINVAL, "v0 must be finite");
     const Geom &g = p->geoms[index];
+    if (g.quantity == LINDHARD_SQW) return fail(LINDHARD_EINVAL, "the Kramers-Kronig pass reads Im chi (not S(q, w))");
     if (g.n_omega > (variant == 0 ? 256 : 1536))
         return fail(LINDHARD_EUNSUPPORTED, variant == 0 ? "the tensor-core form takes n_omega <= 256"
                                                         : "the SIMT form takes n_omega <= 1536");
@@ -1031,6 +1083,9 @@ extern "C" const char *lindhard_last_error(void) { return g_last_error.c_str(); 
 // Helpers shared with other host translation units of the library.
 namespace lh {
 lindhard_status geom_from_grid(const lindhard_grid &gr, Geom &g, int &prec) { return make_geom(gr, g, prec); }
-lindhard_status band_from_params(const lindhard_band *b, Band &o) { return make_band(b, o); }
+lindhard_status band_for_call(const Geom &g, const lindhard_band *b, bool generate, Band &o)
+{
+    return band_of_instance(g, b, generate, o);
+}
 lindhard_status set_error(lindhard_status st, const char *msg) { return fail(st, msg); }
 }  // namespace lh

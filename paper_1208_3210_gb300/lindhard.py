@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(HERE, "_build", "liblindhard.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOCONV, EUNSUPPORTED = range(7)
 FP32, SPLITBF16_TC, FP64 = 0, 1, 2
+IMCHI, IMCHI_T, SQW = 0, 1, 2          # lindhard_quantity
 PLAN_BACKWARD, PLAN_CONCURRENT, PLAN_GRAPH, PLAN_AUTOTUNE = 1, 2, 4, 8
 _STATUS_NAMES = {OK: "OK", EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", ETIMEOUT: "ETIMEOUT",
                  ENOCONV: "ENOCONV", EUNSUPPORTED: "EUNSUPPORTED"}
@@ -41,13 +42,14 @@ class LindhardError(RuntimeError):
 class Band(ctypes.Structure):
     _fields_ = [("t", ctypes.c_double), ("tp", ctypes.c_double), ("tpp", ctypes.c_double),
                 ("mu", ctypes.c_double), ("filling", ctypes.c_double), ("gamma", ctypes.c_double),
-                ("ff_a", ctypes.c_double), ("band_kind", ctypes.c_int), ("reserved", ctypes.c_int)]
+                ("ff_a", ctypes.c_double), ("band_kind", ctypes.c_int), ("reserved", ctypes.c_int),
+                ("kT", ctypes.c_double)]
 
 
 class Grid(ctypes.Structure):
     _fields_ = [("zones", ctypes.c_int), ("pts_per_zone", ctypes.c_int), ("n_eps", ctypes.c_int),
                 ("e_max", ctypes.c_double), ("n_omega", ctypes.c_int), ("q_extent", ctypes.c_int),
-                ("precision", ctypes.c_int), ("reserved", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("quantity", ctypes.c_int)]
 
 
 class Sizes(ctypes.Structure):
@@ -108,13 +110,15 @@ def _check(status: int):
         raise LindhardError(status, load().lindhard_last_error().decode())
 
 
-def make_grid(zones, npz, n_eps, e_max, n_omega=0, q_extent=0, precision=FP32) -> Grid:
-    return Grid(int(zones), int(npz), int(n_eps), float(e_max), int(n_omega), int(q_extent), int(precision), 0)
+def make_grid(zones, npz, n_eps, e_max, n_omega=0, q_extent=0, precision=FP32, quantity=IMCHI) -> Grid:
+    return Grid(int(zones), int(npz), int(n_eps), float(e_max), int(n_omega), int(q_extent), int(precision),
+                int(quantity))
 
 
 def make_band(t=0.42, tp=-0.10, tpp=0.065, mu=float("nan"), filling=1.15, gamma=0.05, ff_a=0.0,
-              kind=0, **_ignored) -> Band:
-    return Band(float(t), float(tp), float(tpp), float(mu), float(filling), float(gamma), float(ff_a), int(kind), 0)
+              kind=0, kT=0.0, **_ignored) -> Band:
+    return Band(float(t), float(tp), float(tpp), float(mu), float(filling), float(gamma), float(ff_a), int(kind), 0,
+                float(kT))
 
 
 def _ptr(t):
@@ -134,7 +138,7 @@ def imchi_noalloc(grid: dict, band=None, out=None, A_in=None, mu_out=None, strea
     intermediates live in the library's fixed 32 MiB device array, so calls
     that could overlap on the GPU must be serialised."""
     g = make_grid(grid["zones"], grid["npz"], grid["n_eps"], grid["e_max"], grid.get("n_omega", 0),
-                  grid.get("q_extent", 0), FP32)
+                  grid.get("q_extent", 0), FP32, grid.get("quantity", IMCHI))
     b = None if band is None else (band if isinstance(band, Band) else make_band(**band))
     _check(load().lindhard_imchi_noalloc(ctypes.byref(g), None if b is None else ctypes.byref(b), _ptr(A_in),
                                          _ptr(out), _ptr(mu_out), _stream(stream)))
@@ -143,13 +147,14 @@ def imchi_noalloc(grid: dict, band=None, out=None, A_in=None, mu_out=None, strea
 
 class Plan:
     """A lindhard_plan for one or more instance grids (dicts with zones, npz,
-    n_eps, e_max and optional n_omega, q_extent, precision)."""
+    n_eps, e_max and optional n_omega, q_extent, precision, quantity)."""
 
     def __init__(self, grids: Sequence[dict], precision: int = FP32, backward: bool = False,
                  concurrent: bool = False, graph: bool = False, autotune: bool = False):
         lib = load()
         self.grids = [make_grid(g["zones"], g["npz"], g["n_eps"], g["e_max"], g.get("n_omega", 0),
-                                g.get("q_extent", 0), g.get("precision", precision)) for g in grids]
+                                g.get("q_extent", 0), g.get("precision", precision), g.get("quantity", IMCHI))
+                      for g in grids]
         self.batch = len(self.grids)
         arr = (Grid * self.batch)(*self.grids)
         h = ctypes.c_void_p()

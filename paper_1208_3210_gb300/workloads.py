@@ -31,13 +31,14 @@ def band_params(filling=1.15, gamma=0.05, ff_a=0.0, mu=float("nan"), **over):
     return p
 
 
-def grid_params(zones, npz, n_eps, e_max, n_omega=0, q_extent=0):
+def grid_params(zones, npz, n_eps, e_max, n_omega=0, q_extent=0, **extra):
     """One instance's grid: zones per axis, points per zone per axis, energy
-    count and half-window.  n_omega = 0 => n_eps // 2, q_extent = 0 => N."""
+    count and half-window.  n_omega = 0 => n_eps // 2, q_extent = 0 => N.
+    extra: optional keys passed through (precision, quantity)."""
     N = zones * npz
     return dict(zones=int(zones), npz=int(npz), n_eps=int(n_eps), e_max=float(e_max),
                 n_omega=int(n_omega) if n_omega else int(n_eps) // 2,
-                q_extent=int(q_extent) if q_extent else int(N))
+                q_extent=int(q_extent) if q_extent else int(N), **extra)
 
 
 # The five workloads.  Sizes follow the problem statement of each:

@@ -61,11 +61,14 @@ def _create(lib, grid):
     (dict(zones=2, npz=96, n_eps=48, e_max=1.0, precision=2), 6),  # FP64 only up to length 256
     (dict(zones=2, npz=32, n_eps=48, e_max=1.0, precision=1), 6),  # no tensor-core form for P = 96
     (dict(zones=2, npz=32, n_eps=48, e_max=1.0, precision=3), 6),  # no such precision
+    (dict(zones=2, npz=32, n_eps=48, e_max=1.0, quantity=3), 1),   # no such quantity
+    (dict(zones=2, npz=32, n_eps=48, e_max=1.0, quantity=-1), 1),
+    (dict(zones=1, npz=32, n_eps=200, e_max=1.0, quantity=2, precision=2), 6),  # finite T pads PE to 512 > 256 (FP64)
 ])
 def test_plan_rejects_bad_grids_on_host(lib, kw, expect):
     from paper_1208_3210_gb300 import lindhard as lh
     g = lh.make_grid(kw["zones"], kw["npz"], kw["n_eps"], kw["e_max"], kw.get("n_omega", 0),
-                     kw.get("q_extent", 0), kw.get("precision", 0))
+                     kw.get("q_extent", 0), kw.get("precision", 0), kw.get("quantity", 0))
     st, h = _create(lib, g)
     assert st == expect, lib.lindhard_last_error().decode()
     assert not h.value
@@ -92,3 +95,23 @@ def test_null_arguments(lib):
     assert lib.lindhard_envelope_k0(None, 0, None, 0, None, None, None, 0, None, None) == 1
     assert lib.lindhard_dmu_dparams(None, 0, None, 0.0, None, None) == 1
     lib.lindhard_plan_destroy(None)
+
+
+@pytest.mark.parametrize("quantity,kT,a_in,band,msg", [
+    (0, 0.05, False, True, "kT must be 0"),                  # T = 0 grid with a temperature
+    (1, 0.0, False, True, "need kT > 0"),                    # finite-temperature grid at kT = 0
+    (2, float("nan"), False, True, "kT must be finite"),
+    (2, -0.1, False, True, "kT must be finite"),
+    (1, 0.05, True, False, "need bands"),                    # caller A, but no band for kT
+    (2, 0.0, True, True, "need kT > 0"),                     # caller A: kT still read and checked
+])
+def test_temperature_arguments_on_host(lib, quantity, kT, a_in, band, msg):
+    # the no-allocation entry checks grid and band before it touches a device
+    from paper_1208_3210_gb300 import lindhard as lh
+    g = lh.make_grid(2, 16, 32, 1.0, quantity=quantity)
+    b = lh.make_band(kT=kT)
+    fake = ctypes.c_void_p(256)
+    st = lib.lindhard_imchi_noalloc(ctypes.byref(g), ctypes.byref(b) if band else None,
+                                    fake if a_in else None, fake, None, None)
+    assert st == lh.EINVAL
+    assert msg in lib.lindhard_last_error().decode()
