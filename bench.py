@@ -307,6 +307,41 @@ def kk_rpa_form(plan, out, steps, stream, peak, v0=0.05):
     return res
 
 
+def thermal_form(lh, grids, bands, steps, autotune, stream, kT=0.025):
+    """The finite-temperature quantities (grid quantity LINDHARD_IMCHI_T and
+    LINDHARD_SQW at kT, energy FFT padded to PE >= n_eps + n_omega - 1): device
+    time per call and outputs/s, outside the timed region of the T = 0 call."""
+    import torch
+    res = {"kT_ev": kT}
+    for q, name in ((lh.IMCHI_T, "imchi_T"), (lh.SQW, "S_qw")):
+        qgrids = [dict(g, quantity=q) for g in grids]
+        qbands = [dict(b, kT=kT) for b in bands]
+        try:
+            qp = lh.Plan(qgrids, autotune=autotune)
+        except Exception as exc:
+            res[name] = {"unavailable": str(exc)}
+            continue
+        qout = torch.empty(qp.out_elems(), dtype=torch.float32, device="cuda")
+        for _ in range(3):
+            qp.imchi(qbands, out=qout)
+        qp.status()
+        n = max(3, min(steps, 200))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(n):
+            qp.imchi(qbands, out=qout)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        qp.status()
+        ms = e0.elapsed_time(e1) / n
+        res[name] = {"ms_per_step": ms, "value": qp.out_elems() / (ms * 1e-3), "steps": n,
+                     "fft_e": qp.sizes[0].fft_e, "variants": qp.variants(0)}
+        qp.close()
+        del qout
+    return res
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
@@ -501,9 +536,11 @@ def main():
     dom_kernel = (VARIANT_KERNELS[dom][variants[dom]] if dom in VARIANT_KERNELS else KERNEL_NAMES[dom])
     tc = None
     kk = None
+    thermal = None
     if not batched and not args.no_tc:
         plan.imchi(bands, out=out, mu_out=mu)
         kk = kk_rpa_form(plan, out, args.steps, stream, peak)
+        thermal = thermal_form(lh, grids, bands, args.steps, not args.no_autotune, stream)
         tc = tensor_core_form(lh, grids, bands, out, args.steps, not args.no_autotune, mu, stream)
         if "py_inv_ms" in tc:
             tc["py_inv_ms_fp32"] = round(ptimes["py_inv"][0] / max(ptimes["py_inv"][1], 1), 5)
@@ -546,6 +583,8 @@ def main():
             line["tensor_core"] = tc
         if kk is not None:
             line["kk_rpa"] = kk
+        if thermal is not None:
+            line["finite_temperature"] = thermal
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.workload)
         print(json.dumps(line), flush=True)

@@ -138,7 +138,7 @@ def test_thermal_product_variants(lh, tmp_path, monkeypatch):
     for vx in (0, 1, 2, 3, 4):
         path = tmp_path / f"tune_{vx}.json"
         path.write_text(json.dumps({base + "|fwd_y": 1, base + "|inv_y": 1, base + "|x_product": vx,
-                                    base + "|inv_energy": vx % 2}))
+                                    base + "|inv_energy": vx % 2}, indent=0))   # one entry per line
         monkeypatch.setenv("LINDHARD_TUNE_CACHE", str(path))
         plan = lh.Plan([grid], autotune=True)
         out = plan.imchi([band])
