@@ -165,6 +165,17 @@ typedef struct {
  * and use the faster; results are cached per process and, when the
  * environment variable LINDHARD_TUNE_CACHE names a file, in that JSON file. */
 #define LINDHARD_PLAN_AUTOTUNE 8u
+/* Plan flag: compute Im chi in the paper's own arrangement (Sec. 3) instead of
+ * the 3D transform: a 2D FFT over momentum for every energy plane (the
+ * occupied plane e_t and the empty plane e_{J0+t} packed into one complex
+ * transform), the energy sum of Eq. 9 done directly for every momentum
+ * frequency k, C(k, w_m) = sum_j conj(a^_j(k)) b^_{j+m}(k) (FP32 fused
+ * multiply-adds), and a 2D inverse FFT for every transfer.  Same outputs as
+ * the 3D form up to rounding; kept to compare the two.  LINDHARD_FP32,
+ * LINDHARD_IMCHI grids with n_eps <= 1024 and n_omega <= 512 only; forward
+ * only (not with LINDHARD_PLAN_BACKWARD); LINDHARD_PLAN_AUTOTUNE tunes
+ * nothing in this form.  Otherwise LINDHARD_EUNSUPPORTED. */
+#define LINDHARD_PLAN_ENERGY_DIRECT 16u
 
 /* Builds a plan for `batch` instances with the given grids (host array).
  * Validates the grids, picks FFT lengths (the smallest supported length that
@@ -174,7 +185,7 @@ typedef struct {
  * Without LINDHARD_PLAN_CONCURRENT instances are computed one after another
  * and share one workspace sized for the largest.  flags: any of
  * LINDHARD_PLAN_BACKWARD, LINDHARD_PLAN_CONCURRENT, LINDHARD_PLAN_GRAPH,
- * LINDHARD_PLAN_AUTOTUNE.
+ * LINDHARD_PLAN_AUTOTUNE, LINDHARD_PLAN_ENERGY_DIRECT.
  * On success *out receives the plan. */
 lindhard_status lindhard_plan_create(const lindhard_grid *grids, int batch,
                                      unsigned flags, lindhard_plan **out);

@@ -43,24 +43,8 @@ k_fwd_energy(Geom g, Band band, const AxisTab *__restrict__ axis,
             int ix = (int)(line / g.N), iy = (int)(line % g.N);
             const AxisTab &ax = axis[ix], &ay = axis[iy];
             if constexpr (sizeof(Real) == 4) {
-                // double-float (about 1e-14 eV): a chain of FP32 operations of a
-                // few cycles each, where FP64 operations cost about 60 here and
-                // hold the CTA at the barrier below
-                F2 e0;
-                if (band.band_kind == 1) {
-                    e0 = f2_add(F2{ax.p2h, ax.p2l}, F2{ay.p2h, ay.p2l});
-                    e0.h *= 0.5f;   // exact
-                    e0.l *= 0.5f;
-                } else {
-                    const F2 cx{ax.c1h, ax.c1l}, cy{ay.c1h, ay.c1l};
-                    e0 = f2_add(f2_add(f2_mul(F2{band.k1[0], band.k1[1]}, f2_add(cx, cy)),
-                                       f2_mul(F2{band.k2[0], band.k2[1]}, f2_mul(cx, cy))),
-                                f2_mul(F2{band.k3[0], band.k3[1]}, f2_add(F2{ax.c2h, ax.c2l}, F2{ay.c2h, ay.c2l})));
-                }
-                const F2 xi = f2_add(e0, F2{-st->mu_hi, -st->mu_lo});
-                s_xhi[threadIdx.x] = xi.h;
-                s_xlo[threadIdx.x] = xi.l;
-                s_amp[threadIdx.x] = ax.gf * ay.gf * band.gam_pi;
+                // double-float: FP64 operations would hold the CTA at the barrier below
+                band_point_f32(band, ax, ay, st, s_xhi[threadIdx.x], s_xlo[threadIdx.x], s_amp[threadIdx.x]);
             } else {
                 double e0;
                 if (band.band_kind == 1)

@@ -136,6 +136,30 @@ __device__ __forceinline__ F2 f2_mul(F2 a, F2 b)
     return f2_fast(p, e);
 }
 
+// Band energy xi_p = e0(p) - mu as an unevaluated FP32 pair (hi, lo), and the
+// amplitude |M(p)|^2 gamma / pi, of the momentum point with axis entries
+// (ax, ay) (Eqs. 4-5): double-float, about 1e-14 eV, in a chain of FP32
+// operations of a few cycles each where FP64 operations cost about 60.
+__device__ __forceinline__ void band_point_f32(const Band &band, const AxisTab &ax, const AxisTab &ay,
+                                               const InstState *st, float &xhi, float &xlo, float &amp)
+{
+    F2 e0;
+    if (band.band_kind == 1) {
+        e0 = f2_add(F2{ax.p2h, ax.p2l}, F2{ay.p2h, ay.p2l});
+        e0.h *= 0.5f;   // exact
+        e0.l *= 0.5f;
+    } else {
+        const F2 cx{ax.c1h, ax.c1l}, cy{ay.c1h, ay.c1l};
+        e0 = f2_add(f2_add(f2_mul(F2{band.k1[0], band.k1[1]}, f2_add(cx, cy)),
+                           f2_mul(F2{band.k2[0], band.k2[1]}, f2_mul(cx, cy))),
+                    f2_mul(F2{band.k3[0], band.k3[1]}, f2_add(F2{ax.c2h, ax.c2l}, F2{ay.c2h, ay.c2l})));
+    }
+    const F2 xi = f2_add(e0, F2{-st->mu_hi, -st->mu_lo});
+    xhi = xi.h;
+    xlo = xi.l;
+    amp = ax.gf * ay.gf * band.gam_pi;
+}
+
 // Rows of the forward intermediates U1 and U2 (and of the adjoint's G3, G4)
 // hold the two half spectra interleaved: column 2k is the first (a^, or h^ in
 // the adjoint), column 2k + 1 the second (b^, or g^), k in [0, SP).  A tile

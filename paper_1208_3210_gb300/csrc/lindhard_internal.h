@@ -30,6 +30,34 @@ struct Geom {
                     // (for S(q, w): +(de / 2 pi) / npz^2 / pi / (P * P * PE))
 };
 
+// Layouts of the energy-direct form (the paper's own arrangement, Sec. 3: a 2D
+// transform over momentum for every energy plane, the energy sum done directly
+// for every momentum frequency).  The energy planes are packed in pairs,
+// z_t = A(., e_t) + i A(., e_{J0 + t}), t < T = n_eps - J0 (occupied plane t,
+// empty plane J0 + t), as the columns of the layouts the p_y passes read.
+struct DirectGeom {
+    Geom t;          // planes: [N][N][2 SPt] -> [N][P][2 SPt] (SP = H = SPt, xs2)
+    Geom o;          // transfers: [Q][P][SPo] -> [Q][Q][SPo] (SP = SPo, H = n_omega, xs3)
+    int T;           // plane pairs
+    long long zs;    // plane stride of the momentum transforms Z [P][P][2 SPt]
+    long long cs;    // plane stride of the correlations C [P][P][SPo]
+};
+inline DirectGeom direct_geom(const Geom &g)
+{
+    DirectGeom d;
+    d.T = g.n_eps - g.J0;
+    d.t = g;
+    d.t.SP = d.t.H = ((d.T + 1) / 2 + 7) / 8 * 8;
+    d.t.xs2 = (long long)g.P * 2 * d.t.SP + 32;
+    d.o = g;
+    d.o.SP = (g.n_omega + 7) / 8 * 8;
+    d.o.H = g.n_omega;
+    d.o.xs3 = (long long)g.P * d.o.SP + 32;
+    d.zs = (long long)g.P * 2 * d.t.SP + 32;
+    d.cs = (long long)g.P * d.o.SP + 32;
+    return d;
+}
+
 // Per-call physics of one instance, passed by value to the kernels.
 struct Band {
     double t, tp, tpp, mu, filling, gamma, ff_a;

@@ -37,6 +37,9 @@ cudaError_t launch_fwd_y(const Geom &g, const Work<double> &w, cudaStream_t s, i
 cudaError_t launch_x_product(const Geom &g, const Work<float> &w, cudaStream_t s, int variant);
 cudaError_t launch_x_product(const Geom &g, const Work<double> &w, cudaStream_t s, int variant);
 cudaError_t launch_inv_y(const Geom &g, const Work<float> &w, cudaStream_t s, int variant);
+bool direct_supported(const Geom &g);
+cudaError_t launch_direct_stage(int stage, const Geom &g, const Band &band, const Work<float> &w,
+                                const float *A_in, float *out, cudaStream_t s);
 bool tc_supported(int P);
 size_t kk_table_bytes(int nw);
 cudaError_t launch_dmu_partials(int kind, double t, double tp, double tpp, double gamma, int npz, double mu,
@@ -133,6 +136,7 @@ struct lindhard_plan {
     std::vector<int> evar;
     bool concurrent = false;     // LINDHARD_PLAN_CONCURRENT
     bool graph = false;          // LINDHARD_PLAN_GRAPH
+    bool direct = false;         // LINDHARD_PLAN_ENERGY_DIRECT
     // concurrent execution: instances on plan-owned streams, forked from and
     // joined back into the caller's stream with events
     std::vector<cudaStream_t> streams;
@@ -392,7 +396,7 @@ extern "C" lindhard_status lindhard_plan_create(const lindhard_grid *grids, int 
 {
     if (!grids || !out || batch < 1) return fail(LINDHARD_EINVAL, "grids/out must be non-NULL and batch >= 1");
     const unsigned known = LINDHARD_PLAN_BACKWARD | LINDHARD_PLAN_CONCURRENT | LINDHARD_PLAN_GRAPH |
-                           LINDHARD_PLAN_AUTOTUNE;
+                           LINDHARD_PLAN_AUTOTUNE | LINDHARD_PLAN_ENERGY_DIRECT;
     if (flags & ~known) return fail(LINDHARD_EINVAL, "unknown plan flags");
     *out = nullptr;
     lindhard_plan *p = new (std::nothrow) lindhard_plan;
@@ -403,6 +407,11 @@ extern "C" lindhard_status lindhard_plan_create(const lindhard_grid *grids, int 
     p->backward = (flags & LINDHARD_PLAN_BACKWARD) != 0;
     p->graph = (flags & LINDHARD_PLAN_GRAPH) != 0;
     p->concurrent = p->graph || (flags & LINDHARD_PLAN_CONCURRENT) != 0;
+    p->direct = (flags & LINDHARD_PLAN_ENERGY_DIRECT) != 0;
+    if (p->direct && p->backward) {
+        delete p;
+        return fail(LINDHARD_EUNSUPPORTED, "the energy-direct form is forward only (no LINDHARD_PLAN_BACKWARD)");
+    }
     int maxLen = kMinLen, maxNpts = 1;
     for (int i = 0; i < batch; ++i) {
         lindhard_status st = make_geom(grids[i], p->geoms[i], p->precision[i]);
@@ -413,6 +422,12 @@ extern "C" lindhard_status lindhard_plan_create(const lindhard_grid *grids, int 
         if (p->backward && p->precision[i] != LINDHARD_FP32) {
             delete p;
             return fail(LINDHARD_EUNSUPPORTED, "the backward pass is built for LINDHARD_FP32 grids");
+        }
+        if (p->direct && (p->precision[i] != LINDHARD_FP32 || p->geoms[i].quantity != LINDHARD_IMCHI ||
+                          !direct_supported(p->geoms[i]))) {
+            delete p;
+            return fail(LINDHARD_EUNSUPPORTED, "the energy-direct form takes LINDHARD_FP32, LINDHARD_IMCHI grids "
+                                               "with n_eps <= 1024 and n_omega <= 512");
         }
         maxLen = std::max(maxLen, std::max(p->geoms[i].P, p->geoms[i].PE));
         maxNpts = std::max(maxNpts, p->geoms[i].npz * p->geoms[i].npz);
@@ -434,6 +449,15 @@ extern "C" lindhard_status lindhard_plan_create(const lindhard_grid *grids, int 
         Need n;
         n.X = std::max((size_t)g.N * g.N * 2 * g.SP, (size_t)g.Q * (size_t)g.xs3) * cb;
         n.Y = std::max((size_t)g.N * (size_t)g.xs2, (size_t)g.Q * g.Q * g.SP) * cb;
+        if (p->direct) {
+            // X: planes, then the momentum transforms Z, then [Q][P][SPo];
+            // Y: [N][P][2 SPt], then the correlations C, then [Q][Q][SPo]
+            const DirectGeom d = direct_geom(g);
+            n.X = std::max({(size_t)g.N * g.N * 2 * d.t.SP, (size_t)g.P * (size_t)d.zs,
+                            (size_t)g.Q * (size_t)d.o.xs3}) * cb;
+            n.Y = std::max({(size_t)g.N * (size_t)d.t.xs2, (size_t)g.P * (size_t)d.cs,
+                            (size_t)g.Q * g.Q * d.o.SP}) * cb;
+        }
         n.Z = p->backward ? (size_t)g.Q * (size_t)g.xs3 * cb : 0;
         n.partial = p->backward ? (size_t)bw_energy_blocks(g) * 5 * sizeof(double) : 0;
         n.axis = (size_t)g.N * sizeof(AxisTab);
@@ -515,7 +539,7 @@ extern "C" lindhard_status lindhard_plan_create(const lindhard_grid *grids, int 
         if (p->precision[i] == LINDHARD_SPLITBF16_TC) p->yvar_inv[i] = 7;   // tensor-core inverse p_y pass
     p->xvar.assign(batch, 0);
     p->evar.assign(batch, 0);
-    if (e == cudaSuccess && (flags & LINDHARD_PLAN_AUTOTUNE)) e = autotune(p);
+    if (e == cudaSuccess && (flags & LINDHARD_PLAN_AUTOTUNE) && !p->direct) e = autotune(p);
     if (e != cudaSuccess) {
         lindhard_plan_destroy(p);
         return cuda_fail(e, "plan set-up");
@@ -546,6 +570,16 @@ extern "C" lindhard_status lindhard_plan_sizes(const lindhard_plan *p, int index
     long long W4 = (long long)g.Q * g.Q * g.H;
     out->hbm_bytes_forward = 2 * (W1 + W2 + W3 + W4) * cb + out->out_elems * rb;
     out->kernels_forward = 8;   // set-up (tables + multisection pass 0), multisection pass 1, Halley step, 5 FFT passes
+    if (p->direct) {
+        // planes, p_y, p_x, correlation, k_x inverse, k_y inverse, output; the
+        // same write-once read-once count over the direct form's intermediates
+        const DirectGeom d = direct_geom(g);
+        const long long T = d.T, n = g.n_omega;
+        out->hbm_bytes_forward = 2 * ((long long)g.N * g.N * T + (long long)g.N * g.P * T + (long long)g.P * g.P * T +
+                                      (long long)g.P * g.P * n + (long long)g.Q * g.P * n + (long long)g.Q * g.Q * n) * cb +
+                                 out->out_elems * rb;
+        out->kernels_forward = 10;
+    }
     return LINDHARD_OK;
 }
 
@@ -713,6 +747,16 @@ static cudaError_t enqueue_forward(lindhard_plan *p, const std::vector<Band> &bs
         }
         const Real *a_i = A_in ? A_in + a_off : nullptr;
         Real *o_i = out + o_off;
+        if constexpr (sizeof(Real) == 4) {
+            if (p->direct) {
+                // planes, p_y, p_x + energy correlation + k_x inverse, k_y inverse, output
+                for (int k = 0; k < 5 && e == cudaSuccess; ++k)
+                    e = timed(p, 2 + k, s, [&] { return launch_direct_stage(k, g, b, w, a_i, o_i, s); });
+                a_off += (size_t)g.N * g.N * g.n_eps;
+                o_off += (size_t)g.Q * g.Q * g.n_omega;
+                continue;
+            }
+        }
         if (e == cudaSuccess) e = timed(p, 2, s, [&] { return launch_fwd_energy(g, b, w, a_i, s); });
         if (e == cudaSuccess) e = timed(p, 3, s, [&] { return launch_fwd_y(g, w, s, p->yvar_fwd[i]); });
         if (e == cudaSuccess) e = timed(p, 4, s, [&] { return launch_x_product(g, w, s, p->xvar[i]); });

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "_build", "liblindhard.so")
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOCONV, EUNSUPPORTED = range(7)
 FP32, SPLITBF16_TC, FP64 = 0, 1, 2
 IMCHI, IMCHI_T, SQW = 0, 1, 2          # lindhard_quantity
-PLAN_BACKWARD, PLAN_CONCURRENT, PLAN_GRAPH, PLAN_AUTOTUNE = 1, 2, 4, 8
+PLAN_BACKWARD, PLAN_CONCURRENT, PLAN_GRAPH, PLAN_AUTOTUNE, PLAN_ENERGY_DIRECT = 1, 2, 4, 8, 16
 _STATUS_NAMES = {OK: "OK", EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", ETIMEOUT: "ETIMEOUT",
                  ENOCONV: "ENOCONV", EUNSUPPORTED: "EUNSUPPORTED"}
 
@@ -150,7 +150,8 @@ class Plan:
     n_eps, e_max and optional n_omega, q_extent, precision, quantity)."""
 
     def __init__(self, grids: Sequence[dict], precision: int = FP32, backward: bool = False,
-                 concurrent: bool = False, graph: bool = False, autotune: bool = False):
+                 concurrent: bool = False, graph: bool = False, autotune: bool = False,
+                 energy_direct: bool = False):
         lib = load()
         self.grids = [make_grid(g["zones"], g["npz"], g["n_eps"], g["e_max"], g.get("n_omega", 0),
                                 g.get("q_extent", 0), g.get("precision", precision), g.get("quantity", IMCHI))
@@ -159,7 +160,8 @@ class Plan:
         arr = (Grid * self.batch)(*self.grids)
         h = ctypes.c_void_p()
         flags = (PLAN_BACKWARD if backward else 0) | (PLAN_CONCURRENT if concurrent else 0) | \
-            (PLAN_GRAPH if graph else 0) | (PLAN_AUTOTUNE if autotune else 0)
+            (PLAN_GRAPH if graph else 0) | (PLAN_AUTOTUNE if autotune else 0) | \
+            (PLAN_ENERGY_DIRECT if energy_direct else 0)
         _check(lib.lindhard_plan_create(arr, self.batch, flags, ctypes.byref(h)))
         self._h = h
         self.sizes = []

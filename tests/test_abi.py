@@ -115,3 +115,21 @@ def test_temperature_arguments_on_host(lib, quantity, kT, a_in, band, msg):
                                     fake if a_in else None, fake, None, None)
     assert st == lh.EINVAL
     assert msg in lib.lindhard_last_error().decode()
+
+
+@pytest.mark.parametrize("kw,flags,msg", [
+    (dict(), 1 | 16, "forward only"),                                   # with LINDHARD_PLAN_BACKWARD
+    (dict(precision=2), 16, "energy-direct form takes"),                # FP64
+    (dict(precision=1), 16, "energy-direct form takes"),                # tensor-core precision
+    (dict(quantity=2), 16, "energy-direct form takes"),                 # finite temperature
+    (dict(n_eps=2048), 16, "energy-direct form takes"),                 # n_eps > 1024
+    (dict(n_eps=1024, n_omega=600), 16, "energy-direct form takes"),    # n_omega > 512
+])
+def test_energy_direct_plan_rejections_on_host(lib, kw, flags, msg):
+    from paper_1208_3210_gb300 import lindhard as lh
+    g = lh.make_grid(2, 64, kw.get("n_eps", 32), 1.0, kw.get("n_omega", 0), 0, kw.get("precision", 0),
+                     kw.get("quantity", 0))
+    h = ctypes.c_void_p()
+    st = lib.lindhard_plan_create(ctypes.byref(g), 1, flags, ctypes.byref(h))
+    assert st == lh.EUNSUPPORTED and not h.value
+    assert msg in lib.lindhard_last_error().decode()
