@@ -115,8 +115,13 @@ k_outer_fft(int ncols, int nin, int Q, long long istride, int iw, long long ostr
 constexpr int kCorrWarps = 8;
 
 __host__ __device__ inline long long corr_pairs(int P) { return 2LL * (P / 2 + 1) + (long long)(P / 2 - 1) * P; }
-// shared floats2 of one warp: a^ (J0 rounded up to R) and b^ (that + 32 R)
-__host__ __device__ inline int corr_a_len(int J0, int R) { return (J0 + R - 1) / R * R; }
+// shared float2s of one warp: a^ (J0 rounded up to R, and to 2 so that every
+// warp's arrays start on 16 bytes) and b^ (that + 32 R)
+__host__ __device__ inline int corr_a_len(int J0, int R)
+{
+    const int q = R < 2 ? 2 : R;
+    return (J0 + q - 1) / q * q;
+}
 
 template <int R>
 __global__ void __launch_bounds__(kCorrWarps * 32)
@@ -165,16 +170,33 @@ k_direct_corr(Geom g, int T, int W, long long zs, int SPo, long long cs, const f
         w[r] = bs[m0 + r];
     }
     for (int j0 = 0; j0 < AL; j0 += R) {
+        float2 a[R];
+        if constexpr (R % 2 == 0) {
+            // j0 and m0 are multiples of R: every pair below starts on 16 bytes
+            const float4 *b4 = reinterpret_cast<const float4 *>(bs + j0 + R + m0);
+            const float4 *a4 = reinterpret_cast<const float4 *>(as + j0);
 #pragma unroll
-        for (int i = 0; i < R; ++i) w[R + i] = bs[j0 + R + m0 + i];
+            for (int i = 0; i < R / 2; ++i) {
+                const float4 q = b4[i], u = a4[i];
+                w[R + 2 * i] = make_float2(q.x, q.y);
+                w[R + 2 * i + 1] = make_float2(q.z, q.w);
+                a[2 * i] = make_float2(u.x, u.y);
+                a[2 * i + 1] = make_float2(u.z, u.w);
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+                w[R + i] = bs[j0 + R + m0 + i];
+                a[i] = as[j0 + i];
+            }
+        }
 #pragma unroll
         for (int jj = 0; jj < R; ++jj) {
-            const float2 a = as[j0 + jj];
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const float2 b = w[jj + r];
-                acc[r].x = fmaf(a.x, b.x, fmaf(-a.y, b.y, acc[r].x));
-                acc[r].y = fmaf(a.x, b.y, fmaf(a.y, b.x, acc[r].y));
+                acc[r].x = fmaf(a[jj].x, b.x, fmaf(-a[jj].y, b.y, acc[r].x));
+                acc[r].y = fmaf(a[jj].x, b.y, fmaf(a[jj].y, b.x, acc[r].y));
             }
         }
 #pragma unroll
