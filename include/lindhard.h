@@ -276,7 +276,10 @@ lindhard_status lindhard_plan_pass_times(lindhard_plan *plan, double *ms, long l
  *   sum_q    : device, double [n_omega]: left side, reduced from out in FP64.
  *   dos_corr : device, double [n_omega]: right side, from A in FP64.
  * Uses the plan's workspace (do not overlap with a call of the same plan).
- * LINDHARD_IMCHI grids only (others: LINDHARD_EUNSUPPORTED). */
+ * Finite-temperature grids: the same exchange of sums with a = A f and
+ * b = A (1 - f) gives dos_corr = -c sum_j D(e_j) D(e_{j+m}) [f(e_j) - f(e_{j+m})]
+ * (LINDHARD_IMCHI_T) and (c/pi) sum_j D(e_j) D(e_{j+m}) f(e_j) [1 - f(e_{j+m})]
+ * (LINDHARD_SQW), D(e) = sum_p A(p, e); band.kT is read. */
 lindhard_status lindhard_sum_rule(lindhard_plan *plan, int index, const lindhard_band *band,
                                   const float *A_in, const float *out, double *sum_q, double *dos_corr,
                                   void *stream);

@@ -1,5 +1,6 @@
 // FP64 sum-rule reductions (a check of a computed output, not part of the
-// forward call).  Summing Eq. 9 over every lag q factorises:
+// forward call).  Summing Eq. 9 over every lag q factorises (and so do the
+// finite-temperature quantities, with Fermi weights: see k_dos_corr):
 //   sum_q Im chi(q, w_m) = -c sum_j D_a(e_j) D_b(e_{j+m}),
 //   D_a(e) = sum_p a(p, e),  D_b(e) = sum_p b(p, e),
 // (swap the order of the momentum sums), which holds exactly on the grid when
@@ -49,16 +50,27 @@ __global__ void k_dos(Geom g, Band band, const AxisTab *__restrict__ axis, const
     for (int j = threadIdx.x; j < g.n_eps; j += blockDim.x) atomicAdd(&D[j], s_d[j]);
 }
 
-// dos_corr[m] = -c sum_j D_a(e_j) D_b(e_{j+m}), c = de/(2 pi)/npz^2.
-__global__ void k_dos_corr(Geom g, const double *__restrict__ D, double *dos_corr)
+// dos_corr[m] = -c sum_j D_a(e_j) D_b(e_{j+m}), c = de/(2 pi)/npz^2.  At
+// temperature kT > 0 (a = A f, b = A (1 - f), Eq. A1) the same exchange of
+// sums gives
+//   Im chi_T: -c sum_j D(e_j) D(e_{j+m}) [f(e_j) - f(e_{j+m})],
+//   S:     (c/pi) sum_j D(e_j) D(e_{j+m}) f(e_j) [1 - f(e_{j+m})],
+// f(e_j) = 1 / (exp((2j + 1 - n_eps) x_step) + 1) in FP64.
+__global__ void k_dos_corr(Geom g, double x_step, const double *__restrict__ D, double *dos_corr)
 {
     int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= g.n_omega) return;
-    const double c = (g.de / (2.0 * 3.14159265358979323846)) / ((double)g.npz * g.npz);
+    const double pi = 3.14159265358979323846;
+    const double c = (g.de / (2.0 * pi)) / ((double)g.npz * g.npz);
+    auto occ = [&](int j) { return 1.0 / (exp((double)(2 * j + 1 - g.n_eps) * x_step) + 1.0); };
+    auto emp = [&](int j) { return 1.0 / (exp(-(double)(2 * j + 1 - g.n_eps) * x_step) + 1.0); };
     double s = 0.0;
-    for (int j = 0; j + m < g.n_eps; ++j)
-        if (j < g.J0 && j + m >= g.J0) s += D[j] * D[j + m];
-    dos_corr[m] = -c * s;
+    for (int j = 0; j + m < g.n_eps; ++j) {
+        if (g.quantity == LINDHARD_IMCHI_T) s += D[j] * D[j + m] * (occ(j) - occ(j + m));
+        else if (g.quantity == LINDHARD_SQW) s += D[j] * D[j + m] * (occ(j) * emp(j + m));
+        else if (j < g.J0 && j + m >= g.J0) s += D[j] * D[j + m];
+    }
+    dos_corr[m] = g.quantity == LINDHARD_SQW ? c / pi * s : -c * s;
 }
 
 // sum_q[m] = sum over all lags of out[l_x][l_y][m], FP64.
@@ -142,7 +154,7 @@ cudaError_t launch_sum_rule(const Geom &g, const Band &band, const AxisTab *axis
     if (e != cudaSuccess) return e;
     int T = 256;
     k_dos<<<1024, T, sizeof(double) * g.n_eps, s>>>(g, band, axis, eps, st, A_in, D);
-    k_dos_corr<<<(g.n_omega + 127) / 128, 128, 0, s>>>(g, D, dos_corr);
+    k_dos_corr<<<(g.n_omega + 127) / 128, 128, 0, s>>>(g, band.x_step64, D, dos_corr);
     k_sum_q<<<1024, T, sizeof(double) * g.n_omega, s>>>(g, out, sum_q);
     return cudaGetLastError();
 }

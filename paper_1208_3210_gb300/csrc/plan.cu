@@ -913,7 +913,6 @@ extern "C" lindhard_status lindhard_sum_rule(lindhard_plan *p, int index, const 
     if (index < 0 || index >= p->batch) return fail(LINDHARD_EINVAL, "index out of range");
     if (p->precision[index] == LINDHARD_FP64) return fail(LINDHARD_EINVAL, "the sum rule reads FP32 outputs");
     const Geom &g = p->geoms[index];
-    if (g.quantity != LINDHARD_IMCHI) return fail(LINDHARD_EUNSUPPORTED, "the sum rule is built for LINDHARD_IMCHI grids only");
     if (g.Q != (g.periodic ? g.N : 2 * g.N))
         return fail(LINDHARD_EINVAL, "the sum rule needs every lag: q_extent = N (one zone) or 2N (several)");
     Band b = {};

@@ -201,3 +201,61 @@ def test_thermal_full_size_extended_workload(lh, quantity):
     plan.close()
     del out, got
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("quantity", [1, 2], ids=["imchi_T", "S"])
+@pytest.mark.parametrize("cfg", [dict(zones=1, npz=32, n_eps=48, e_max=1.0, q_extent=32, n_omega=48),
+                                 dict(zones=2, npz=16, n_eps=40, e_max=1.5, q_extent=64, n_omega=40)],
+                         ids=["reduced", "extended_all_lags"])
+def test_thermal_sum_rule(lh, cfg, quantity):
+    # summed over every lag the finite-temperature outputs factorise into
+    # Fermi-weighted energy correlations of the density of states D(e): the
+    # library's FP64 reduction of its own output against its own D, and its D
+    # side against numpy on the oracle's A
+    grid = dict(wl.grid_params(cfg["zones"], cfg["npz"], cfg["n_eps"], cfg["e_max"], n_omega=cfg["n_omega"],
+                               q_extent=cfg["q_extent"]), quantity=quantity)
+    kT = 0.06
+    band = dict(wl.band_params(filling=1.1, gamma=0.08, ff_a=1.0), kT=kT)
+    plan = lh.Plan([grid])
+    out = plan.imchi([band])
+    sq, dc = plan.sum_rule(0, out, band=band)
+    plan.status()
+    sq, dc = sq.cpu().numpy(), dc.cpu().numpy()
+    scale = np.abs(dc).max()
+    assert scale > 0
+    err = np.abs(sq - dc).max() / scale
+    A = oracle.spectral(_solved(band, grid), grid)
+    D = A.sum(axis=(0, 1))
+    n, de = grid["n_eps"], 2 * grid["e_max"] / grid["n_eps"]
+    e = -grid["e_max"] + (np.arange(n) + 0.5) * de
+    f, fe = 1 / (np.exp(e / kT) + 1), 1 / (np.exp(-e / kT) + 1)
+    c = de / (2 * math.pi) / grid["npz"] ** 2
+    if quantity == 1:
+        ref = np.array([-c * np.sum(D[: n - m] * D[m:] * (f[: n - m] - f[m:])) for m in range(grid["n_omega"])])
+    else:
+        ref = np.array([c / math.pi * np.sum(D[: n - m] * D[m:] * f[: n - m] * fe[m:]) for m in range(grid["n_omega"])])
+    err_d = np.abs(dc - ref).max() / np.abs(ref).max()
+    print(f"quantity {quantity}: sum over q against the DOS side {err:.2e}, DOS side against numpy {err_d:.2e}")
+    assert err <= 1e-5 and err_d <= 1e-6
+    plan.close()
+
+
+def test_thermal_tensor_core_precision_and_noalloc(lh):
+    """The finite-temperature weights and the odd-part product combine with
+    the tensor-core inverse p_y pass and with the entry that allocates
+    nothing."""
+    import torch
+    grid = wl.grid_params(2, 32, 16, 1.0, q_extent=128, quantity=1)   # every lag: P = 128, a tensor-core length
+    band = dict(wl.band_params(filling=1.1, gamma=0.06, ff_a=0.8), kT=0.05)
+    A = oracle.spectral(_solved(band, grid), grid)
+    ref = oracle.thermal_full(A, grid, grid["q_extent"], grid["n_omega"], 0.05, 1)
+    mx = np.abs(ref).max()
+    tc, _ = _gpu(lh, grid, band, precision=lh.SPLITBF16_TC)
+    e_tc = np.abs(tc - ref).max() / mx
+    out = torch.empty(grid["q_extent"] ** 2 * grid["n_omega"], dtype=torch.float32, device="cuda")
+    lh.imchi_noalloc(grid, band, out=out)
+    torch.cuda.synchronize()
+    na = out.reshape(ref.shape).cpu().numpy().astype(np.float64)
+    e_na = np.abs(na - ref).max() / mx
+    print(f"Im chi_T: tensor-core inverse p_y {e_tc:.2e}, no-allocation entry {e_na:.2e} of max")
+    assert e_tc <= TOL32 and e_na <= TOL32
