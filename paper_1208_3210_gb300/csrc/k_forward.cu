@@ -136,7 +136,7 @@ k_fwd_energy(Geom g, Band band, const AxisTab *__restrict__ axis,
 #pragma unroll 2
         for (int k = threadIdx.x & 31; k < H; k += 32) {
             Cx zk = sm[E::saddr(col, k)];
-            Cx zm = sm[E::saddr(col, (L - k) & (L - 1))];
+            Cx zm = sm[E::saddr(col, k == 0 ? 0 : L - k)];
             Cx ah = mk<Cx>(half * (zk.x + zm.x), half * (zk.y - zm.y));
             Cx bh = mk<Cx>(half * (zk.y + zm.y), -half * (zk.x - zm.x));
             gst2(row + 2 * k, ah, bh);
@@ -289,7 +289,7 @@ cudaError_t launch_fwd_energy(const Geom &g, const Band &band, const Work<float>
                               cudaStream_t s)
 {
 #define CALL(L) launch_fwd_energy_t<float, L>(g, band, w, A_in, s)
-    LH_LEN_SWITCH(g.PE, CALL)
+    LH_P_SWITCH(g.PE, CALL)
 #undef CALL
 }
 cudaError_t launch_fwd_energy(const Geom &g, const Band &band, const Work<double> &w, const double *A_in,

@@ -224,7 +224,7 @@ cudaError_t launch_inv_energy(const Geom &g, const Work<float> &w, float *out, c
 {
     if (variant == 1) return launch_inv_energy_tma(g, w, out, s);
 #define CALL(L) launch_inv_energy_t<float, float, L>(g, w, out, s)
-    LH_LEN_SWITCH(g.PE, CALL)
+    LH_P_SWITCH(g.PE, CALL)
 #undef CALL
 }
 cudaError_t launch_inv_energy(const Geom &g, const Work<double> &w, double *out, cudaStream_t s, int variant)

@@ -586,7 +586,7 @@ static cudaError_t launch_inv_energy_tma_t(const Geom &g, const Work<float> &w, 
 cudaError_t launch_inv_energy_tma(const Geom &g, const Work<float> &w, float *out, cudaStream_t s)
 {
 #define CALL(L) launch_inv_energy_tma_t<L>(g, w, out, s)
-    LH_LEN_SWITCH(g.PE, CALL)
+    LH_P_SWITCH(g.PE, CALL)
 #undef CALL
 }
 

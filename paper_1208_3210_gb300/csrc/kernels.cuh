@@ -87,6 +87,14 @@ template <> struct LineCfg<512>  { static constexpr int C = 8, T = 256; };
 template <> struct LineCfg<1024> { static constexpr int C = 8, T = 512; };
 template <> struct LineCfg<2048> { static constexpr int C = 4, T = 512; };
 template <> struct LineCfg<4096> { static constexpr int C = 4, T = 1024; };
+// energy lengths 3 * 2^k (finite temperature pads the energy axis to
+// n_eps + n_omega - 1): 24 values per thread
+template <> struct LineCfg<48>   { static constexpr int C = 32, T = 64; };
+template <> struct LineCfg<96>   { static constexpr int C = 16, T = 64; };
+template <> struct LineCfg<192>  { static constexpr int C = 16, T = 128; };
+template <> struct LineCfg<384>  { static constexpr int C = 16, T = 256; };
+template <> struct LineCfg<768>  { static constexpr int C = 8, T = 256; };
+template <> struct LineCfg<1536> { static constexpr int C = 4, T = 256; };
 
 // Energy table entry: FP32 path stores e_j as an unevaluated sum hi + lo.
 template <typename Real> struct EpsEntry;

@@ -237,7 +237,8 @@ static lindhard_status make_geom(const lindhard_grid &gr, Geom &g, int &prec)
     // finite temperature both parts cover the whole window, lags run over
     // (-n_eps, n_eps), and the kept ones [0, n_omega) and their mirrors
     // (-n_omega, 0] stay clear of wrapped partners once PE >= n_eps + n_omega - 1.
-    long long PE = gr.quantity == LINDHARD_IMCHI ? next_len(gr.n_eps) : next_len(gr.n_eps + n_omega - 1);
+    // (FP32 forms: lengths 3 * 2^k too, e.g. 384 instead of 512 for n_eps 256, n_omega 128)
+    long long PE = gr.quantity == LINDHARD_IMCHI ? next_len(gr.n_eps) : next_len_p(gr.n_eps + n_omega - 1, gr.precision);
     long long maxlen = gr.precision == LINDHARD_FP64 ? kMaxLen64 : kMaxLen;
     if (P > maxlen || PE > maxlen) return fail(LINDHARD_EUNSUPPORTED, "FFT length beyond the compiled range");
     if (gr.precision == LINDHARD_SPLITBF16_TC && !tc_supported((int)P))
