@@ -127,3 +127,22 @@ def test_direct_graph_batch_bit_identical(lh):
         n = alone.size
         assert np.array_equal(out[off:off + n], alone.ravel().astype(np.float32))
         off += n
+
+
+@pytest.mark.parametrize("grid", [wl.grid_params(2, 8, 2, 1.0, n_omega=2),
+                                  wl.grid_params(2, 8, 7, 1.0, n_omega=7, q_extent=2),
+                                  wl.grid_params(1, 16, 3, 1.0, n_omega=3),
+                                  wl.grid_params(3, 8, 17, 1.3, n_omega=9, q_extent=48)],
+                         ids=["n_eps2", "one_lag_pair", "reduced_n_eps3", "three_zones_all_lags"])
+def test_direct_edge_cases(lh, grid):
+    # the smallest energy grids (one occupied and one empty plane; odd counts),
+    # the smallest lag window and an odd zone count, every output against the oracle
+    band = wl.band_params(filling=1.1, gamma=0.1, ff_a=0.5)
+    got = _run(lh, grid, band)
+    A = oracle.spectral(_solved(band, grid), grid)
+    ref = oracle.imchi_full(A, grid, grid["q_extent"], grid["n_omega"])
+    mx = np.abs(ref).max()
+    assert mx > 0
+    err = np.abs(got - ref).max() / mx
+    print(f"n_eps {grid['n_eps']}, n_omega {grid['n_omega']}, Q {grid['q_extent']}: {err:.2e} of max")
+    assert err <= TOL

@@ -259,3 +259,28 @@ def test_thermal_tensor_core_precision_and_noalloc(lh):
     e_na = np.abs(na - ref).max() / mx
     print(f"Im chi_T: tensor-core inverse p_y {e_tc:.2e}, no-allocation entry {e_na:.2e} of max")
     assert e_tc <= TOL32 and e_na <= TOL32
+
+
+@pytest.mark.parametrize("grid,kT", [(wl.grid_params(2, 8, 2, 1.0, n_omega=2), 0.1),
+                                     (wl.grid_params(2, 8, 24, 1.0, n_omega=24), 0.05),
+                                     (wl.grid_params(2, 8, 24, 1.0), 1.0),
+                                     (wl.grid_params(2, 8, 24, 1.0), 1e-7),
+                                     (wl.grid_params(1, 16, 9, 1.0, n_omega=9, q_extent=2), 0.2)],
+                         ids=["n_eps2", "n_omega_eq_n_eps", "kT_1eV", "kT_1e-7", "one_lag_pair"])
+@pytest.mark.parametrize("quantity", [1, 2], ids=["imchi_T", "S"])
+def test_thermal_edge_cases(lh, grid, kT, quantity):
+    # the smallest energy grid, every transfer kept (PE >= 2 n_eps - 1), a
+    # temperature as large as the window's half-width (the odd part C(q, w) -
+    # C(-q, -w) then cancels to about w/4kT of either term, the most FP32
+    # rounding it amplifies here) and one far below the half cell (weights
+    # exactly 0 or 1), the smallest lag window
+    band = dict(wl.band_params(filling=1.1, gamma=0.1, ff_a=0.5), kT=kT)
+    got, fft_e = _gpu(lh, dict(grid, quantity=quantity), band)
+    assert fft_e >= grid["n_eps"] + grid["n_omega"] - 1
+    A = oracle.spectral(_solved(band, grid), grid)
+    ref = oracle.thermal_full(A, grid, grid["q_extent"], grid["n_omega"], kT, quantity)
+    mx = np.abs(ref).max()
+    assert mx > 0
+    err = np.abs(got - ref).max() / mx
+    print(f"n_eps {grid['n_eps']}, n_omega {grid['n_omega']}, kT {kT}, quantity {quantity}: {err:.2e} of max")
+    assert err <= TOL32
