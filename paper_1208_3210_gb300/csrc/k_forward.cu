@@ -17,7 +17,8 @@ namespace lh {
 // ---------------------------------------------------------------------------
 // Energy pass.  One CTA = C momentum points (lines), output U1 layout
 // [N*N lines][SP][2] complex: (a^(k), b^(k)) interleaved.
-template <typename Real, int L>
+// THERMAL: the finite-temperature weights (band.kT > 0) instead of the split.
+template <typename Real, int L, bool THERMAL>
 __global__ void __launch_bounds__(LineCfg<L>::T)
 k_fwd_energy(Geom g, Band band, const AxisTab *__restrict__ axis,
              const typename EpsEntry<Real>::type *__restrict__ eps,
@@ -88,7 +89,7 @@ k_fwd_energy(Geom g, Band band, const AxisTab *__restrict__ axis,
                     else A = s_amp[col] / d;
                 }
             }
-            if (band.kT > 0) {
+            if constexpr (THERMAL) {
                 // finite temperature (Appendix A, Eq. A1): occupied part A f,
                 // empty part A (1 - f), f = 1 / (exp(x) + 1), x = e_n / kT, both
                 // from u = exp(-|x|) so that neither loses digits to 1 - f
@@ -237,9 +238,11 @@ cudaError_t launch_fwd_energy_t(const Geom &g, const Band &band, const Work<Real
     constexpr int C = LineCfg<L>::C, T = LineCfg<L>::T;
     using E = Fft<Real, L, C, T, MAP_LINE, false>;
     size_t smem = sizeof(cx<Real>) * E::SMEM_ELEMS;
-    auto k = k_fwd_energy<Real, L>;
-    static const cudaError_t e = smem_attrs(k, smem);
-    if (e != cudaSuccess) return e;
+    auto k = band.kT > 0 ? k_fwd_energy<Real, L, true> : k_fwd_energy<Real, L, false>;
+    static const cudaError_t e0 = smem_attrs(k_fwd_energy<Real, L, false>, smem);
+    static const cudaError_t e1 = smem_attrs(k_fwd_energy<Real, L, true>, smem);
+    if (e0 != cudaSuccess) return e0;
+    if (e1 != cudaSuccess) return e1;
     long long nlines = (long long)g.N * g.N;
     unsigned grid = (unsigned)((nlines + C - 1) / C);
     k<<<grid, T, smem, s>>>(g, band, w.axis, (const typename EpsEntry<Real>::type *)w.eps, w.state, A_in,
