@@ -525,8 +525,11 @@ def main():
     e2e_value = replicas.whole_job_rate(plan.out_elems(), world, e2e_steps, e2e_s)
     step_ms = ms_total / args.steps
     peak, peak_kind = measured_peaks()
-    # kernels launched in the timed region: each step is one forward call
-    launches = sum(int(plan.sizes[i].kernels_forward) + (1 if bands[i]["gamma"] < 0.02 else 0)
+    # kernels launched in the timed region: each step is one forward call; a
+    # third multisection pass when gamma < 0.02 eV and the solve spans
+    # several CTAs (more than 98 points per zone)
+    launches = sum(int(plan.sizes[i].kernels_forward)
+                   + (1 if bands[i]["gamma"] < 0.02 and grids[i]["npz"] > 98 else 0)
                    for i in range(len(grids))) * args.steps
     if batched:
         # concurrent instances: no per-pass split, the batch as one unit

@@ -142,8 +142,10 @@ typedef struct {
     long long a_elems;      /* N^2 * n_eps (layout of A_in and dA)           */
     long long hbm_bytes_forward;  /* algorithmic HBM bytes of one forward call */
     long long kernels_forward;    /* kernel launches of one forward call with A generated and mu
-                                     solved: one more when gamma < 0.02 eV (a third multisection
-                                     pass); three fewer with a caller-supplied A               */
+                                     solved: with more than 98 points per zone one more when
+                                     gamma < 0.02 eV (a third multisection pass); with at most 98
+                                     the whole solve runs in the set-up launch (two fewer); with
+                                     a caller-supplied A only the FFT passes                    */
 } lindhard_sizes;
 
 /* Plan flag: also allocate the buffers of lindhard_imchi_backward (one more

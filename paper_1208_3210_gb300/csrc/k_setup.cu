@@ -49,7 +49,8 @@ __global__ void k_twiddles(int max_len, float2 *tw32, double2 *tw64)
 // m_x <= m_y (twice for m_x < m_y): (npz/2 + 1)(npz/2 + 2)/2 terms instead of
 // npz^2 (561 instead of 4096 at npz = 64).
 //
-// Launches (no CTA ever waits for another):
+// Launches (no CTA ever waits for another; zones of at most 98 points per
+// axis instead solve in one CTA of k_setup, see mu_solve_one_cta):
 //   k_setup     multisection pass 0 over [-B-3, B+3] eV on G CTAs, and the
 //               tables on further CTAs of the same launch (their FP64 cospi and
 //               exp chains run beside the multisection, not before it)
@@ -104,7 +105,20 @@ struct MuConst {
     long long target32;  // the same in 2^-32 fixed point
     double B;            // bracket half-width - 3 eV
     int NC, passes;
+    int single;          // the whole solve in one CTA of the set-up launch
 };
+
+// Zones small enough for the one-CTA solve: every pass and the Halley step in
+// one CTA of the set-up launch, beside the table CTAs, and no further launch
+// (npz <= 98).  The multi-CTA passes cost two more launches and their
+// grid-wide exchanges, which dominate at these sizes.
+constexpr int MU_SINGLE_MAX_PAIRS = 1300;
+constexpr int MU_SINGLE_NC = 32;     // candidates per pass: one per lane
+__host__ __device__ inline bool mu_single(const Geom &g)
+{
+    const int h = g.npz / 2;
+    return (h + 1) * (h + 2) / 2 <= MU_SINGLE_MAX_PAIRS;
+}
 
 __device__ __forceinline__ int *mu_cross(double *acc, int G, int pass)
 {
@@ -115,6 +129,14 @@ __device__ __forceinline__ double band_e0(const Band &b, const AxisTab &ax, cons
 {
     if (b.band_kind == 1) return 0.5 * (ax.p2 + ay.p2);
     return -2.0 * b.t * (ax.c1 + ay.c1) - 4.0 * b.tp * ax.c1 * ay.c1 - 2.0 * b.tpp * (ax.c2 + ay.c2);
+}
+
+// The same from FP64 class values (cos p, cos 2p, p^2 of the two axes).
+__device__ __forceinline__ double band_e0_cls(const Band &b, double c1a, double c1b, double c2a, double c2b,
+                                              double p2a, double p2b)
+{
+    if (b.band_kind == 1) return 0.5 * (p2a + p2b);
+    return -2.0 * b.t * (c1a + c1b) - 4.0 * b.tp * c1a * c1b - 2.0 * b.tpp * (c2a + c2b);
 }
 
 // Pair index k in [0, (h+1)(h+2)/2) -> classes (a, b), 0 <= a <= b <= h, row
@@ -266,13 +288,124 @@ __device__ __forceinline__ void sect_pass(const Geom &g, const Band &band, const
     (void)c0;
 }
 
+// One-CTA solve (mu_single): MU_SINGLE_NC candidates per multisection pass
+// (lane l of every warp takes candidate l; warp w sums the pairs k = w mod 16),
+// four passes (five when gamma < 0.02 eV) from the full bracket, each shrinking
+// it 31-fold (to about 1e-5 eV, 4e-7 eV with five), then the FP64 Halley step
+// of k_mu_halley from the midpoint.  All sums are in a fixed order.
+__device__ void mu_solve_one_cta(const Geom &g, const Band &band, const MuConst &mc, MuShared &sh, InstState *st,
+                                 unsigned *status, double *mu_out)
+{
+    constexpr int NC = MU_SINGLE_NC, LANES = MU_THREADS / NC, NW = MU_THREADS / 32;
+    static_assert(NC == 32 && NW * 32 * sizeof(long long) <= sizeof(sh.c1), "candidate sums reuse the class table");
+    const int h = g.npz / 2, npairs = (h + 1) * (h + 2) / 2;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    stage_pairs(g, band, sh, 0, npairs);                        // npairs <= MU_CHUNK
+    if (threadIdx.x == 0) {
+        sh.br.lo = -mc.B - 3.0;
+        sh.br.hi = mc.B + 3.0;
+        sh.br.flag = 0;
+    }
+    __syncthreads();
+    long long *red = reinterpret_cast<long long *>(sh.c1);     // [NW][NC]; the FP32 classes are staged
+    const float inv_gam = (float)mc.inv_gam, inv_pi = 0.318309886183790672f;
+    const int passes = band.gamma < 0.02 ? 5 : 4;
+    for (int pass = 0; pass < passes && !sh.br.flag; ++pass) {
+        const double lo = sh.br.lo, step = (sh.br.hi - lo) * (1.0 / (NC - 1));
+        const float mu = (float)(lo + (double)lane * step);
+        float acc4[4] = {0.f, 0.f, 0.f, 0.f};
+        int k = warp;
+        for (; k + 3 * LANES < npairs; k += 4 * LANES) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const float2 ew = sh.ew[k + u * LANES];
+                acc4[u] += ew.y * (0.5f - atanf((ew.x - mu) * inv_gam) * inv_pi);
+            }
+        }
+        for (; k < npairs; k += LANES) {
+            const float2 ew = sh.ew[k];
+            acc4[0] += ew.y * (0.5f - atanf((ew.x - mu) * inv_gam) * inv_pi);
+        }
+        red[warp * NC + lane] = __float2ll_rn(((acc4[0] + acc4[1]) + (acc4[2] + acc4[3])) * MU_SECT_SCALE);
+        __syncthreads();
+        if (warp == 0) {
+            long long tsum = 0;
+            for (int w = 0; w < NW; ++w) tsum += red[w * NC + lane];
+            const unsigned hit = __ballot_sync(0xffffffffu, tsum >= mc.target32);
+            if (lane == 0) {
+                int c = hit ? __ffs(hit) - 1 : NC;   // first candidate at or above the filling
+                if (pass == 0 && (c == 0 || c == NC)) sh.br.flag = 1;
+                c = max(1, min(c, NC - 1));
+                sh.br.lo = lo + (double)(c - 1) * step;
+                sh.br.hi = sh.br.lo + step;
+            }
+        }
+        __syncthreads();
+    }
+    const double mu = 0.5 * (sh.br.lo + sh.br.hi);
+    if (sh.br.flag) {   // the filling was not bracketed
+        if (threadIdx.x == 0) {
+            atomicCAS(status, (unsigned)DEV_OK, (unsigned)DEV_ENOCONV);
+            set_mu(st, mu);
+            st->last_step = INFINITY;
+            if (mu_out) *mu_out = mu;
+        }
+        return;
+    }
+    // FP64 class values, the same expressions as the axis tables at p_i = -2 pi m / npz
+    double *d1 = reinterpret_cast<double *>(sh.c2), *d2 = d1 + (h + 1), *dp = d2 + (h + 1);
+    for (int m = threadIdx.x; m <= h; m += blockDim.x) {
+        const double u = 2.0 * (double)(-m) / (double)g.npz;
+        const double p = u * 3.14159265358979323846;
+        d1[m] = cospi(u);
+        d2[m] = cospi(2.0 * u);
+        dp[m] = p * p;
+    }
+    __syncthreads();
+    const double igam = mc.inv_gam, ipi = 0.31830988618379067154;
+    double f = 0.0;
+    float f1 = 0.f, f2 = 0.f;
+    for (int k = threadIdx.x; k < npairs; k += blockDim.x) {
+        int a, b;
+        tri_pair(k, h, a, b);
+        const int w = pair_weight(a, b, h);
+        const double x = (band_e0_cls(band, d1[a], d1[b], d2[a], d2[b], dp[a], dp[b]) - mu) * igam;
+        f += (double)w * (0.5 - atan(x) * ipi);
+        const float xf = (float)x, r = 1.0f / (1.0f + xf * xf);
+        f1 += (float)w * r * (float)ipi;
+        f2 += (float)w * 2.0f * xf * r * r * (float)ipi;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        f += __shfl_down_sync(0xffffffffu, f, o);
+        f1 += __shfl_down_sync(0xffffffffu, f1, o);
+        f2 += __shfl_down_sync(0xffffffffu, f2, o);
+    }
+    double *hs = reinterpret_cast<double *>(sh.c1);   // [NW][3]
+    __syncthreads();                                  // the candidate sums in sh.c1 are consumed
+    if (lane == 0) { hs[3 * warp] = f; hs[3 * warp + 1] = f1; hs[3 * warp + 2] = f2; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double F = 0.0, F1 = 0.0, F2 = 0.0;
+        for (int w = 0; w < NW; ++w) { F += hs[3 * w]; F1 += hs[3 * w + 1]; F2 += hs[3 * w + 2]; }
+        const double d = F - mc.target;
+        const double dd1 = F1 * igam, dd2 = F2 * igam * igam;
+        const double stp = 2.0 * d * dd1 / (2.0 * dd1 * dd1 - d * dd2);
+        const double mu_new = mu - stp;
+        set_mu(st, mu_new);
+        st->last_step = fabs(stp);
+        if (mu_out) *mu_out = mu_new;
+        if (!(fabs(stp) <= 2.0 * (sh.br.hi - sh.br.lo) + 1e-5))
+            atomicCAS(status, (unsigned)DEV_OK, (unsigned)DEV_ENOCONV);
+    }
+}
+
 // Set-up launch.  CTAs [0, G): multisection pass 0 (mu from the filling);
 // CTAs [G, G + GT): the per-axis tables and the energy grid, one entry per
 // thread of their first warp; without a filling solve only the table CTAs run
 // and the first of them records the given mu.
 __global__ void __launch_bounds__(MU_THREADS, 2)
 k_setup(Geom g, Band band, AxisTab *axis, float2 *eps32, double *eps64, InstState *st, double *acc,
-        unsigned *counter, double *mu_out, MuConst mc, int G)
+        unsigned *counter, unsigned *status, double *mu_out, MuConst mc, int G)
 {
     if ((int)blockIdx.x >= G) {
         const int tb = blockIdx.x - G;
@@ -313,6 +446,11 @@ k_setup(Geom g, Band band, AxisTab *axis, float2 *eps32, double *eps64, InstStat
     }
     __shared__ MuShared sh;
     stage_classes(g, sh);
+    if (mc.single) {
+        __syncthreads();
+        mu_solve_one_cta(g, band, mc, sh, st, status, mu_out);
+        return;
+    }
     if (threadIdx.x == 0) {
         sh.br.lo = -mc.B - 3.0;
         sh.br.hi = mc.B + 3.0;
@@ -467,6 +605,7 @@ static MuConst mu_const(const Geom &g, const Band &band, int G)
     MuConst mc;
     mc.NC = MU_NCPT * G;
     mc.passes = band.gamma < 0.02 ? 3 : 2;
+    mc.single = mu_single(g) ? 1 : 0;
     mc.inv_nc1 = 1.0 / (double)(mc.NC - 1);
     mc.inv_gam = 1.0 / band.gamma;
     mc.target = band.filling * 0.5 * (double)g.npz * (double)g.npz;
@@ -484,21 +623,25 @@ cudaError_t launch_twiddles(int len, float2 *tw32, double2 *tw64, cudaStream_t s
 // Tables plus the first chemical-potential launch (multisection pass 0, or
 // the given mu).
 cudaError_t launch_setup(const Geom &g, const Band &band, AxisTab *axis, float2 *eps32, double *eps64,
-                         InstState *st, double *acc, unsigned *bar, double *mu_out, int G, cudaStream_t s)
+                         InstState *st, double *acc, unsigned *bar, unsigned *status, double *mu_out, int G,
+                         cudaStream_t s)
 {
     const int ntab = g.N > g.n_eps ? g.N : g.n_eps;
     const int GT = (ntab + MU_TAB_THREADS - 1) / MU_TAB_THREADS;
-    const int Gs = band.solve_mu ? G : 0;
-    k_setup<<<Gs + GT, MU_THREADS, 0, s>>>(g, band, axis, eps32, eps64, st, acc, bar, mu_out, mu_const(g, band, G),
-                                           Gs);
+    const int Gs = band.solve_mu ? (mu_single(g) ? 1 : G) : 0;
+    k_setup<<<Gs + GT, MU_THREADS, 0, s>>>(g, band, axis, eps32, eps64, st, acc, bar, status, mu_out,
+                                           mu_const(g, band, G), Gs);
     return cudaGetLastError();
 }
+
+// Whether the chemical potential is solved inside the set-up launch.
+bool mu_solve_in_setup(const Geom &g) { return mu_single(g); }
 
 // The remaining chemical-potential launches (none for a given mu).
 cudaError_t launch_solve_mu(const Geom &g, const Band &band, const AxisTab *axis, InstState *st, double *acc,
                             unsigned *bar, unsigned *status, double *mu_out, int G, cudaStream_t s)
 {
-    if (!band.solve_mu) return cudaSuccess;
+    if (!band.solve_mu || mu_single(g)) return cudaSuccess;   // solved in the set-up launch
     const MuConst mc = mu_const(g, band, G);
     for (int pass = 1; pass < mc.passes; ++pass) k_mu_sect<<<G, MU_THREADS, 0, s>>>(g, band, acc, pass, mc);
     // one warp per CTA when every CTA has at most 32 pairs (the FP64 chains

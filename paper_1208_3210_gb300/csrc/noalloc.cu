@@ -28,7 +28,8 @@ lindhard_status band_for_call(const Geom &g, const lindhard_band *b, bool genera
 lindhard_status set_error(lindhard_status st, const char *msg);
 cudaError_t launch_twiddles(int len, float2 *tw32, double2 *tw64, cudaStream_t s);
 cudaError_t launch_setup(const Geom &g, const Band &band, AxisTab *axis, float2 *eps32, double *eps64,
-                         InstState *st, double *acc, unsigned *bar, double *mu_out, int G, cudaStream_t s);
+                         InstState *st, double *acc, unsigned *bar, unsigned *status, double *mu_out, int G,
+                         cudaStream_t s);
 size_t mu_acc_doubles(int G);
 size_t mu_barrier_words();
 int mu_grid_size(int num_sms, int npts);
@@ -144,7 +145,7 @@ extern "C" lindhard_status lindhard_imchi_noalloc(const lindhard_grid *grid, con
     if (e == cudaSuccess) e = cudaMemsetAsync(w.barrier, 0, mu_barrier_words() * sizeof(unsigned), s);
     if (e == cudaSuccess) e = launch_twiddles(tw_len, (float2 *)(base + off_tw32), (double2 *)(base + off_tw64), s);
     if (e == cudaSuccess && A_in == nullptr) {
-        e = launch_setup(g, b, w.axis, (float2 *)w.eps, nullptr, w.state, w.mu_acc, w.barrier, mu_out, G, s);
+        e = launch_setup(g, b, w.axis, (float2 *)w.eps, nullptr, w.state, w.mu_acc, w.barrier, w.status, mu_out, G, s);
         if (e == cudaSuccess)
             e = launch_solve_mu(g, b, w.axis, w.state, w.mu_acc, w.barrier, w.status, mu_out, G, s);
     }

@@ -22,7 +22,8 @@ namespace lh {
 // launchers (k_*.cu)
 cudaError_t launch_twiddles(int len, float2 *tw32, double2 *tw64, cudaStream_t s);
 cudaError_t launch_setup(const Geom &g, const Band &band, AxisTab *axis, float2 *eps32, double *eps64,
-                         InstState *st, double *acc, unsigned *bar, double *mu_out, int G, cudaStream_t s);
+                         InstState *st, double *acc, unsigned *bar, unsigned *status, double *mu_out, int G,
+                         cudaStream_t s);
 size_t mu_acc_doubles(int G);
 size_t mu_barrier_words();
 int mu_grid_size(int num_sms, int npts);
@@ -38,6 +39,7 @@ cudaError_t launch_x_product(const Geom &g, const Work<float> &w, cudaStream_t s
 cudaError_t launch_x_product(const Geom &g, const Work<double> &w, cudaStream_t s, int variant);
 cudaError_t launch_inv_y(const Geom &g, const Work<float> &w, cudaStream_t s, int variant);
 bool direct_supported(const Geom &g);
+bool mu_solve_in_setup(const Geom &g);
 cudaError_t launch_direct_stage(int stage, const Geom &g, const Band &band, const Work<float> &w,
                                 const float *A_in, float *out, cudaStream_t s);
 bool tc_supported(int P);
@@ -570,7 +572,9 @@ extern "C" lindhard_status lindhard_plan_sizes(const lindhard_plan *p, int index
     long long W3 = (long long)g.Q * g.P * g.H;
     long long W4 = (long long)g.Q * g.Q * g.H;
     out->hbm_bytes_forward = 2 * (W1 + W2 + W3 + W4) * cb + out->out_elems * rb;
-    out->kernels_forward = 8;   // set-up (tables + multisection pass 0), multisection pass 1, Halley step, 5 FFT passes
+    // set-up (tables + multisection pass 0), multisection pass 1, Halley step, 5 FFT passes;
+    // zones of at most 98 points solve mu inside the set-up launch
+    out->kernels_forward = mu_solve_in_setup(g) ? 6 : 8;
     if (p->direct) {
         // planes, p_y, p_x, correlation, k_x inverse, k_y inverse, output; the
         // same write-once read-once count over the direct form's intermediates
@@ -579,7 +583,7 @@ extern "C" lindhard_status lindhard_plan_sizes(const lindhard_plan *p, int index
         out->hbm_bytes_forward = 2 * ((long long)g.N * g.N * T + (long long)g.N * g.P * T + (long long)g.P * g.P * T +
                                       (long long)g.P * g.P * n + (long long)g.Q * g.P * n + (long long)g.Q * g.Q * n) * cb +
                                  out->out_elems * rb;
-        out->kernels_forward = 10;
+        out->kernels_forward = mu_solve_in_setup(g) ? 8 : 10;
     }
     return LINDHARD_OK;
 }
@@ -738,7 +742,7 @@ static cudaError_t enqueue_forward(lindhard_plan *p, const std::vector<Band> &bs
             e = timed(p, 0, s, [&] {
                 return launch_setup(g, b, w.axis, sizeof(Real) == 4 ? (float2 *)w.eps : nullptr,
                                     sizeof(Real) == 8 ? (double *)w.eps : nullptr, w.state, w.mu_acc, w.barrier,
-                                    mu_out ? mu_out + i : nullptr, p->mu_G, s);
+                                    w.status, mu_out ? mu_out + i : nullptr, p->mu_G, s);
             });
             if (e == cudaSuccess)
                 e = timed(p, 1, s, [&] {
@@ -883,8 +887,8 @@ extern "C" lindhard_status lindhard_imchi_backward(lindhard_plan *p, const lindh
         double *partial = (double *)(p->ws + sl.partial);
         cudaError_t e = cudaSuccess;
         if (A_in == nullptr) {
-            e = launch_setup(g, b, wk.axis, (float2 *)wk.eps, nullptr, wk.state, wk.mu_acc, wk.barrier, nullptr,
-                             p->mu_G, s);
+            e = launch_setup(g, b, wk.axis, (float2 *)wk.eps, nullptr, wk.state, wk.mu_acc, wk.barrier, wk.status,
+                             nullptr, p->mu_G, s);
             if (e == cudaSuccess)
                 e = launch_solve_mu(g, b, wk.axis, wk.state, wk.mu_acc, wk.barrier, wk.status, nullptr, p->mu_G, s);
         }
@@ -927,7 +931,8 @@ extern "C" lindhard_status lindhard_sum_rule(lindhard_plan *p, int index, const 
     double *D = (double *)w.X;
     cudaError_t e = cudaSuccess;
     if (A_in == nullptr) {
-        e = launch_setup(g, b, w.axis, (float2 *)w.eps, nullptr, w.state, w.mu_acc, w.barrier, nullptr, p->mu_G, s);
+        e = launch_setup(g, b, w.axis, (float2 *)w.eps, nullptr, w.state, w.mu_acc, w.barrier, w.status, nullptr,
+                         p->mu_G, s);
         if (e == cudaSuccess)
             e = launch_solve_mu(g, b, w.axis, w.state, w.mu_acc, w.barrier, w.status, nullptr, p->mu_G, s);
     }

@@ -3,7 +3,9 @@
 Lorentzian one of Eq. 5).  Covers the three-pass multisection taken for
 gamma < 0.02 eV, zones beyond 512 points per axis, the free-electron band,
 fillings far from half filling, and a filling the search interval cannot
-reach (reported as LINDHARD_ENOCONV by lindhard_plan_status)."""
+reach (reported as LINDHARD_ENOCONV by lindhard_plan_status).  Zones of at
+most 98 points per axis solve in one CTA of the set-up launch, larger ones in
+the multi-CTA passes: both paths are checked on each side of the boundary."""
 import math
 
 import numpy as np
@@ -81,3 +83,23 @@ def test_unreachable_filling_reports_enoconv(lh):
     ok = wl.band_params(filling=1.15, gamma=0.2)
     ref = oracle.solve_mu(0, ok["t"], ok["tp"], ok["tpp"], 0.2, 16, 1.15)
     assert abs(_gpu_mu(lh, grid, ok) - ref) < 1e-10
+
+
+@pytest.mark.parametrize("gamma", [0.005, 0.019, 0.05])
+@pytest.mark.parametrize("npz", [64, 96, 98, 100, 128])
+def test_mu_on_both_solve_paths(lh, npz, gamma):
+    # npz <= 98: the one-CTA solve (four or five passes of 32 candidates and
+    # the Halley step in the set-up launch); npz >= 100: the multi-CTA passes
+    grid = wl.grid_params(1, npz, 16, 1.0) if npz in (64, 128) else wl.grid_params(2, npz, 16, 1.0)
+    band = wl.band_params(filling=1.13, gamma=gamma)
+    ref = oracle.solve_mu(0, band["t"], band["tp"], band["tpp"], gamma, npz, 1.13)
+    got = _gpu_mu(lh, grid, band)
+    assert abs(got - ref) < 1e-10, (npz, gamma, got, ref)
+
+
+@pytest.mark.parametrize("npz", [16, 128])
+def test_enoconv_on_both_solve_paths(lh, npz):
+    grid = wl.grid_params(1, npz, 16, 1.0)
+    band = wl.band_params(filling=1.9999, gamma=0.2)
+    with pytest.raises(lh.LindhardError, match="ENOCONV"):
+        _gpu_mu(lh, grid, band)
