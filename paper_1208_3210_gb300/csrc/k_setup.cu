@@ -2,6 +2,7 @@
 // and the rigid-band chemical potential (Sec. 3: the Fermi level is shifted to
 // hold the requested electron count).
 #include <math.h>
+#include <stddef.h>
 
 #include "kernels.cuh"
 
@@ -113,6 +114,7 @@ struct MuConst {
 // (npz <= 98).  The multi-CTA passes cost two more launches and their
 // grid-wide exchanges, which dominate at these sizes.
 constexpr int MU_SINGLE_MAX_PAIRS = 1300;
+constexpr int MU_SINGLE_MAX_H = 49;  // (h + 1)(h + 2) / 2 <= 1300
 constexpr int MU_SINGLE_NC = 32;     // candidates per pass: one per lane
 __host__ __device__ inline bool mu_single(const Geom &g)
 {
@@ -297,7 +299,13 @@ __device__ void mu_solve_one_cta(const Geom &g, const Band &band, const MuConst 
                                  unsigned *status, double *mu_out)
 {
     constexpr int NC = MU_SINGLE_NC, LANES = MU_THREADS / NC, NW = MU_THREADS / 32;
-    static_assert(NC == 32 && NW * 32 * sizeof(long long) <= sizeof(sh.c1), "candidate sums reuse the class table");
+    // 8-byte scratch lives in sh.c1 (offset 0 of MuShared, so 8-byte aligned;
+    // sh.c2 and sh.p2 start at 4 mod 8): the candidate sums [NW][NC] during
+    // the passes, then 3 (h + 1) class values and [NW][3] Halley sums
+    static_assert(offsetof(MuShared, c1) == 0 && alignof(MuShared) >= 8, "sh.c1 must be 8-byte aligned");
+    static_assert(NC == 32 && NW * NC * sizeof(long long) <= sizeof(sh.c1) &&
+                      (3 * (MU_SINGLE_MAX_H + 1) + 3 * NW) * sizeof(double) <= sizeof(sh.c1),
+                  "scratch fits in the class table");
     const int h = g.npz / 2, npairs = (h + 1) * (h + 2) / 2;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     stage_pairs(g, band, sh, 0, npairs);                        // npairs <= MU_CHUNK
@@ -353,7 +361,8 @@ __device__ void mu_solve_one_cta(const Geom &g, const Band &band, const MuConst 
         return;
     }
     // FP64 class values, the same expressions as the axis tables at p_i = -2 pi m / npz
-    double *d1 = reinterpret_cast<double *>(sh.c2), *d2 = d1 + (h + 1), *dp = d2 + (h + 1);
+    // (in sh.c1, the one 8-byte aligned scratch of MuShared; the candidate sums are consumed)
+    double *d1 = reinterpret_cast<double *>(sh.c1), *d2 = d1 + (h + 1), *dp = d2 + (h + 1);
     for (int m = threadIdx.x; m <= h; m += blockDim.x) {
         const double u = 2.0 * (double)(-m) / (double)g.npz;
         const double p = u * 3.14159265358979323846;
@@ -380,8 +389,7 @@ __device__ void mu_solve_one_cta(const Geom &g, const Band &band, const MuConst 
         f1 += __shfl_down_sync(0xffffffffu, f1, o);
         f2 += __shfl_down_sync(0xffffffffu, f2, o);
     }
-    double *hs = reinterpret_cast<double *>(sh.c1);   // [NW][3]
-    __syncthreads();                                  // the candidate sums in sh.c1 are consumed
+    double *hs = dp + (h + 1);   // [NW][3], after the class values
     if (lane == 0) { hs[3 * warp] = f; hs[3 * warp + 1] = f1; hs[3 * warp + 2] = f2; }
     __syncthreads();
     if (threadIdx.x == 0) {
