@@ -51,7 +51,8 @@ __global__ void k_twiddles(int max_len, float2 *tw32, double2 *tw64)
 // npz^2 (561 instead of 4096 at npz = 64).
 //
 // Launches (no CTA ever waits for another; zones of at most 98 points per
-// axis instead solve in one CTA of k_setup, see mu_solve_one_cta):
+// axis instead solve in one CTA of k_setup by a bracketed Newton iteration,
+// see mu_solve_one_cta):
 //   k_setup     multisection pass 0 over [-B-3, B+3] eV on G CTAs, and the
 //               tables on further CTAs of the same launch (their FP64 cospi and
 //               exp chains run beside the multisection, not before it)
@@ -115,7 +116,6 @@ struct MuConst {
 // grid-wide exchanges, which dominate at these sizes.
 constexpr int MU_SINGLE_MAX_PAIRS = 1300;
 constexpr int MU_SINGLE_MAX_H = 49;  // (h + 1)(h + 2) / 2 <= 1300
-constexpr int MU_SINGLE_NC = 32;     // candidates per pass: one per lane
 __host__ __device__ inline bool mu_single(const Geom &g)
 {
     const int h = g.npz / 2;
@@ -164,6 +164,7 @@ struct MuBracket {
     int wmin[MU_THREADS / 32];
     double lo, hi, step;
     int flag;
+    int wmin_done;   // one-CTA solve: the search has converged
 };
 struct MuShared {
     float c1[MU_MAXC], c2[MU_MAXC], p2[MU_MAXC];   // class values in FP32
@@ -290,21 +291,23 @@ __device__ __forceinline__ void sect_pass(const Geom &g, const Band &band, const
     (void)c0;
 }
 
-// One-CTA solve (mu_single): MU_SINGLE_NC candidates per multisection pass
-// (lane l of every warp takes candidate l; warp w sums the pairs k = w mod 16),
-// four passes (five when gamma < 0.02 eV) from the full bracket, each shrinking
-// it 31-fold (to about 1e-5 eV, 4e-7 eV with five), then the FP64 Halley step
-// of k_mu_halley from the midpoint.  All sums are in a fixed order.
+// One-CTA solve (mu_single): a bracketed Newton iteration in FP32 (each step
+// sums n and dn/dmu over the pairs, one or two per thread, in a fixed order;
+// a step that leaves the bracket, or a flat n, falls back to bisection) from
+// the full bracket until the step is below 1e-6 eV, then the FP64 Halley step
+// of k_mu_halley from there.  n is increasing, so the bracket always holds the
+// root; the first evaluation checks that both ends straddle the filling.
+constexpr int MU_NEWTON_MAX = 64;    // bisection alone reaches 1e-6 eV in 24 steps
 __device__ void mu_solve_one_cta(const Geom &g, const Band &band, const MuConst &mc, MuShared &sh, InstState *st,
                                  unsigned *status, double *mu_out)
 {
-    constexpr int NC = MU_SINGLE_NC, LANES = MU_THREADS / NC, NW = MU_THREADS / 32;
+    constexpr int NW = MU_THREADS / 32;
     // 8-byte scratch lives in sh.c1 (offset 0 of MuShared, so 8-byte aligned;
-    // sh.c2 and sh.p2 start at 4 mod 8): the candidate sums [NW][NC] during
-    // the passes, then 3 (h + 1) class values and [NW][3] Halley sums
+    // sh.c2 and sh.p2 start at 4 mod 8): the per-warp sums of the search,
+    // then 3 (h + 1) class values and [NW][3] Halley sums
     static_assert(offsetof(MuShared, c1) == 0 && alignof(MuShared) >= 8, "sh.c1 must be 8-byte aligned");
-    static_assert(NC == 32 && NW * NC * sizeof(long long) <= sizeof(sh.c1) &&
-                      (3 * (MU_SINGLE_MAX_H + 1) + 3 * NW) * sizeof(double) <= sizeof(sh.c1),
+    static_assert((3 * (MU_SINGLE_MAX_H + 1) + 3 * NW) * sizeof(double) <= sizeof(sh.c1) &&
+                      2 * NW * sizeof(float) <= sizeof(sh.c1),
                   "scratch fits in the class table");
     const int h = g.npz / 2, npairs = (h + 1) * (h + 2) / 2;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -312,45 +315,52 @@ __device__ void mu_solve_one_cta(const Geom &g, const Band &band, const MuConst 
     if (threadIdx.x == 0) {
         sh.br.lo = -mc.B - 3.0;
         sh.br.hi = mc.B + 3.0;
+        sh.br.step = 0.0;                                       // the current estimate
         sh.br.flag = 0;
     }
     __syncthreads();
-    long long *red = reinterpret_cast<long long *>(sh.c1);     // [NW][NC]; the FP32 classes are staged
+    float *red = reinterpret_cast<float *>(sh.c1);             // [NW][2]
     const float inv_gam = (float)mc.inv_gam, inv_pi = 0.318309886183790672f;
-    const int passes = band.gamma < 0.02 ? 5 : 4;
-    for (int pass = 0; pass < passes && !sh.br.flag; ++pass) {
-        const double lo = sh.br.lo, step = (sh.br.hi - lo) * (1.0 / (NC - 1));
-        const float mu = (float)(lo + (double)lane * step);
-        float acc4[4] = {0.f, 0.f, 0.f, 0.f};
-        int k = warp;
-        for (; k + 3 * LANES < npairs; k += 4 * LANES) {
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const float2 ew = sh.ew[k + u * LANES];
-                acc4[u] += ew.y * (0.5f - atanf((ew.x - mu) * inv_gam) * inv_pi);
-            }
-        }
-        for (; k < npairs; k += LANES) {
+    const float target = (float)mc.target;
+    // it = 0: n at both ends of the bracket; it >= 1: n and dn/dmu at the estimate
+    for (int it = 0; it < MU_NEWTON_MAX; ++it) {
+        const float m0 = (float)(it == 0 ? sh.br.lo : sh.br.step), m1 = (float)sh.br.hi;
+        float n0 = 0.f, n1 = 0.f;   // it = 0: n(lo), n(hi); else n(mu), gamma dn/dmu
+        for (int k = threadIdx.x; k < npairs; k += MU_THREADS) {
             const float2 ew = sh.ew[k];
-            acc4[0] += ew.y * (0.5f - atanf((ew.x - mu) * inv_gam) * inv_pi);
+            const float x = (ew.x - m0) * inv_gam;
+            n0 += ew.y * (0.5f - atanf(x) * inv_pi);
+            if (it == 0) n1 += ew.y * (0.5f - atanf((ew.x - m1) * inv_gam) * inv_pi);
+            else n1 += ew.y * (inv_pi / (1.0f + x * x));
         }
-        red[warp * NC + lane] = __float2ll_rn(((acc4[0] + acc4[1]) + (acc4[2] + acc4[3])) * MU_SECT_SCALE);
+        for (int o = 16; o > 0; o >>= 1) {
+            n0 += __shfl_down_sync(0xffffffffu, n0, o);
+            n1 += __shfl_down_sync(0xffffffffu, n1, o);
+        }
+        if (lane == 0) { red[2 * warp] = n0; red[2 * warp + 1] = n1; }
         __syncthreads();
-        if (warp == 0) {
-            long long tsum = 0;
-            for (int w = 0; w < NW; ++w) tsum += red[w * NC + lane];
-            const unsigned hit = __ballot_sync(0xffffffffu, tsum >= mc.target32);
-            if (lane == 0) {
-                int c = hit ? __ffs(hit) - 1 : NC;   // first candidate at or above the filling
-                if (pass == 0 && (c == 0 || c == NC)) sh.br.flag = 1;
-                c = max(1, min(c, NC - 1));
-                sh.br.lo = lo + (double)(c - 1) * step;
-                sh.br.hi = sh.br.lo + step;
+        int done = 0;
+        if (threadIdx.x == 0) {
+            float N0 = 0.f, N1 = 0.f;
+            for (int w = 0; w < NW; ++w) { N0 += red[2 * w]; N1 += red[2 * w + 1]; }
+            if (it == 0) {
+                if (!(N0 < target && N1 >= target)) { sh.br.flag = 1; done = 1; }   // not bracketed
+                sh.br.step = 0.5 * (sh.br.lo + sh.br.hi);
+            } else {
+                const double mu = sh.br.step, F = (double)N0 - mc.target;
+                if (F < 0.0) sh.br.lo = mu; else sh.br.hi = mu;
+                const double slope = (double)N1 * mc.inv_gam;          // dn/dmu
+                double nxt = slope > 0.0 ? mu - F / slope : sh.br.lo - 1.0;
+                if (!(nxt > sh.br.lo && nxt < sh.br.hi)) nxt = 0.5 * (sh.br.lo + sh.br.hi);
+                done = fabs(nxt - mu) < 1e-6 || sh.br.hi - sh.br.lo < 1e-6;
+                sh.br.step = nxt;
             }
+            sh.br.wmin_done = done;
         }
         __syncthreads();
+        if (sh.br.wmin_done) break;
     }
-    const double mu = 0.5 * (sh.br.lo + sh.br.hi);
+    const double mu = sh.br.step;
     if (sh.br.flag) {   // the filling was not bracketed
         if (threadIdx.x == 0) {
             atomicCAS(status, (unsigned)DEV_OK, (unsigned)DEV_ENOCONV);
@@ -361,7 +371,7 @@ __device__ void mu_solve_one_cta(const Geom &g, const Band &band, const MuConst 
         return;
     }
     // FP64 class values, the same expressions as the axis tables at p_i = -2 pi m / npz
-    // (in sh.c1, the one 8-byte aligned scratch of MuShared; the candidate sums are consumed)
+    // (in sh.c1, the one 8-byte aligned scratch of MuShared; the search sums are consumed)
     double *d1 = reinterpret_cast<double *>(sh.c1), *d2 = d1 + (h + 1), *dp = d2 + (h + 1);
     for (int m = threadIdx.x; m <= h; m += blockDim.x) {
         const double u = 2.0 * (double)(-m) / (double)g.npz;
@@ -402,8 +412,9 @@ __device__ void mu_solve_one_cta(const Geom &g, const Band &band, const MuConst 
         set_mu(st, mu_new);
         st->last_step = fabs(stp);
         if (mu_out) *mu_out = mu_new;
-        if (!(fabs(stp) <= 2.0 * (sh.br.hi - sh.br.lo) + 1e-5))
-            atomicCAS(status, (unsigned)DEV_OK, (unsigned)DEV_ENOCONV);
+        // the FP32 search stops within about 1e-6 eV of the root: a larger
+        // FP64 correction means it went wrong
+        if (!(fabs(stp) <= 1e-4)) atomicCAS(status, (unsigned)DEV_OK, (unsigned)DEV_ENOCONV);
     }
 }
 

@@ -88,8 +88,8 @@ def test_unreachable_filling_reports_enoconv(lh):
 @pytest.mark.parametrize("gamma", [0.005, 0.019, 0.05])
 @pytest.mark.parametrize("npz", [64, 96, 98, 100, 128])
 def test_mu_on_both_solve_paths(lh, npz, gamma):
-    # npz <= 98: the one-CTA solve (four or five passes of 32 candidates and
-    # the Halley step in the set-up launch); npz >= 100: the multi-CTA passes
+    # npz <= 98: the one-CTA solve (a bracketed Newton iteration and the
+    # Halley step in the set-up launch); npz >= 100: the multi-CTA passes
     grid = wl.grid_params(1, npz, 16, 1.0) if npz in (64, 128) else wl.grid_params(2, npz, 16, 1.0)
     band = wl.band_params(filling=1.13, gamma=gamma)
     ref = oracle.solve_mu(0, band["t"], band["tp"], band["tpp"], gamma, npz, 1.13)
