@@ -347,10 +347,11 @@ __device__ void mu_solve_one_cta(const Geom &g, const Band &band, const MuConst 
                 if (!(N0 < target && N1 >= target)) { sh.br.flag = 1; done = 1; }   // not bracketed
                 sh.br.step = 0.5 * (sh.br.lo + sh.br.hi);
             } else {
-                const double mu = sh.br.step, F = (double)N0 - mc.target;
-                if (F < 0.0) sh.br.lo = mu; else sh.br.hi = mu;
-                const double slope = (double)N1 * mc.inv_gam;          // dn/dmu
-                double nxt = slope > 0.0 ? mu - F / slope : sh.br.lo - 1.0;
+                // FP32 step (an FP64 division costs some 450 cycles on this critical path)
+                const double mu = sh.br.step;
+                const float F = N0 - target, slope = N1 * inv_gam;   // n - target, dn/dmu
+                if (F < 0.f) sh.br.lo = mu; else sh.br.hi = mu;
+                double nxt = slope > 0.f ? mu - (double)(F / slope) : sh.br.lo - 1.0;
                 if (!(nxt > sh.br.lo && nxt < sh.br.hi)) nxt = 0.5 * (sh.br.lo + sh.br.hi);
                 done = fabs(nxt - mu) < 1e-6 || sh.br.hi - sh.br.lo < 1e-6;
                 sh.br.step = nxt;
@@ -402,9 +403,17 @@ __device__ void mu_solve_one_cta(const Geom &g, const Band &band, const MuConst 
     double *hs = dp + (h + 1);   // [NW][3], after the class values
     if (lane == 0) { hs[3 * warp] = f; hs[3 * warp + 1] = f1; hs[3 * warp + 2] = f2; }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double F = 0.0, F1 = 0.0, F2 = 0.0;
-        for (int w = 0; w < NW; ++w) { F += hs[3 * w]; F1 += hs[3 * w + 1]; F2 += hs[3 * w + 2]; }
+    if (warp == 0) {
+        // the NW warp sums by a shuffle tree (a chain of NW dependent FP64 adds
+        // would cost some 60 cycles each)
+        double F = lane < NW ? hs[3 * lane] : 0.0, F1 = lane < NW ? hs[3 * lane + 1] : 0.0,
+               F2 = lane < NW ? hs[3 * lane + 2] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) {
+            F += __shfl_down_sync(0xffffffffu, F, o);
+            F1 += __shfl_down_sync(0xffffffffu, F1, o);
+            F2 += __shfl_down_sync(0xffffffffu, F2, o);
+        }
+        if (lane != 0) return;
         const double d = F - mc.target;
         const double dd1 = F1 * igam, dd2 = F2 * igam * igam;
         const double stp = 2.0 * d * dd1 / (2.0 * dd1 * dd1 - d * dd2);
