@@ -103,15 +103,18 @@ def source_digest(fnames):
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(pass_name, workload):
+def recorded_traffic(pass_name, workload, variant):
     """DRAM bytes per launch from the committed ncu summary, or None when the
-    kernel source changed since the counters were taken."""
+    kernel source changed since the counters were taken or the plan runs
+    another engine variant of the pass than the one captured."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         rec = json.load(open(p))[workload][pass_name]
     except Exception:
         return None
     if rec.get("source_sha256_16") != source_digest(PASS_FILES[pass_name]):
+        return None
+    if rec.get("variant", 0) != variant:
         return None
     return rec.get("dram_bytes_per_launch")
 
@@ -543,9 +546,10 @@ def main():
         dom = dom_pass
         dom_ms = dom_live[dom][0] / dom_live[dom][1]
         achieved = pb[dom] / (dom_ms * 1e-3) / 1e9
-        traffic = None if args.grid else recorded_traffic(dom, args.workload)
         pipeline_bytes = sum(pb.values())
     variants = plan.variants(0) if not batched else {}
+    if not batched:
+        traffic = None if args.grid else recorded_traffic(dom, args.workload, variants.get(dom, 0))
     plain = None
     if batched:
         # the same instances one after another on one stream, no graph: the
