@@ -9,6 +9,7 @@
 
 #include <algorithm>
 #include <fstream>
+#include <iterator>
 #include <map>
 #include <mutex>
 #include <new>
@@ -286,12 +287,19 @@ extern "C" void lindhard_plan_destroy(lindhard_plan *p);
 // one entry per line, {"<gpu>|P=..|N=..|PE=..|Q=..|fwd_y": variant, ...}
 // (also |inv_y and |x_product; variants as for lindhard_plan::yvar_fwd and
 // xvar).  Cached entries in range are used as they are (a cache file may pin
-// a variant).
+// a variant).  Entries read from a cache file stay with that file: when the
+// variable names another file they are dropped (entries timed in the process
+// are kept), and a save writes only the timed entries and those of its own
+// file, so variants pinned in one file never leak into another.
 template <typename Real>
 static Work<Real> work_of(lindhard_plan *p, int i);
 
 static std::mutex g_tune_mutex;
-static std::map<std::string, int> g_tune;
+struct TuneEntry {
+    int variant;
+    std::string origin;   // the cache file it was read from; empty: timed here
+};
+static std::map<std::string, TuneEntry> g_tune;
 static std::string g_tune_path;   // cache file last merged into g_tune
 
 static void tune_load()
@@ -299,22 +307,27 @@ static void tune_load()
     const char *path = getenv("LINDHARD_TUNE_CACHE");
     if (!path || g_tune_path == path) return;
     g_tune_path = path;
+    for (auto it = g_tune.begin(); it != g_tune.end();)   // another file's entries
+        it = it->second.origin.empty() ? std::next(it) : g_tune.erase(it);
     std::ifstream f(path);
     std::string line;
     while (std::getline(f, line)) {
         size_t a = line.find('"'), b = line.find('"', a + 1), c = line.find(':', b);
         if (a == std::string::npos || b == std::string::npos || c == std::string::npos) continue;
-        g_tune[line.substr(a + 1, b - a - 1)] = atoi(line.c_str() + c + 1);
+        g_tune[line.substr(a + 1, b - a - 1)] = TuneEntry{atoi(line.c_str() + c + 1), g_tune_path};
     }
 }
 static void tune_save()
 {
     const char *path = getenv("LINDHARD_TUNE_CACHE");
     if (!path) return;
+    std::vector<std::pair<std::string, int>> out;
+    for (auto &kv : g_tune)
+        if (kv.second.origin.empty() || kv.second.origin == path) out.emplace_back(kv.first, kv.second.variant);
     std::ofstream f(path);
     f << "{\n";
-    size_t i = 0;
-    for (auto &kv : g_tune) f << "  \"" << kv.first << "\": " << kv.second << (++i < g_tune.size() ? ",\n" : "\n");
+    for (size_t i = 0; i < out.size(); ++i)
+        f << "  \"" << out[i].first << "\": " << out[i].second << (i + 1 < out.size() ? ",\n" : "\n");
     f << "}\n";
 }
 
@@ -363,7 +376,7 @@ static cudaError_t autotune(lindhard_plan *p)
         Work<float> w = work_of<float>(p, i);
         // fastest of the variants of one pass (timed only when not cached)
         auto pick = [&](const std::string &k, const std::vector<int> &vs, auto launch) {
-            if (!g_tune.count(k) || std::find(vs.begin(), vs.end(), g_tune[k]) == vs.end()) {
+            if (!g_tune.count(k) || std::find(vs.begin(), vs.end(), g_tune[k].variant) == vs.end()) {
                 int best = vs[0];
                 float tbest = 0.f;
                 bool any = false;
@@ -375,9 +388,9 @@ static cudaError_t autotune(lindhard_plan *p)
                     float t = time_launches([&] { return launch(vs[j]); }, a, b);
                     if (!any || t < tbest) { best = vs[j]; tbest = t; any = true; }
                 }
-                g_tune[k] = best;
+                g_tune[k] = TuneEntry{best, std::string()};
             }
-            return g_tune[k];
+            return g_tune[k].variant;
         };
         p->yvar_fwd[i] = pick(kf, vy, [&](int v) { return launch_fwd_y(g, w, 0, v); });
         if (p->precision[i] != LINDHARD_SPLITBF16_TC)

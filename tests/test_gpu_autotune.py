@@ -129,3 +129,23 @@ def test_tma_variants_full_size_match_default(lh, tmp_path, monkeypatch):
         assert float((out_t - out_d).abs().max()) <= TOL32 * mx, (vy, vx, ve)
     del out_t, out_d
     torch.cuda.empty_cache()
+
+
+def test_pinned_entries_stay_with_their_file(lh, tmp_path, monkeypatch):
+    # variants pinned in one cache file are used while it is named, and are
+    # neither used nor written once the variable names another file
+    probe = lh.Plan([GRIDS[1]])
+    kf, ki, kx, ke = _keys(GRIDS[1], probe.sizes[0])
+    probe.close()
+    pinned = tmp_path / "pinned.json"
+    pinned.write_text(json.dumps({kf: 0, ki: 0, kx: 0, ke: 0}, indent=0))
+    monkeypatch.setenv("LINDHARD_TUNE_CACHE", str(pinned))
+    plan = lh.Plan([GRIDS[1]], autotune=True)
+    assert plan.variants() == {"py_fwd": 0, "py_inv": 0, "px_product": 0, "energy_inv": 0}
+    plan.close()
+    other = tmp_path / "other.json"
+    monkeypatch.setenv("LINDHARD_TUNE_CACHE", str(other))
+    plan = lh.Plan([GRIDS[0]], autotune=True)
+    plan.close()
+    written = json.loads(other.read_text())
+    assert written and not any(k in written for k in (kf, ki, kx, ke))
