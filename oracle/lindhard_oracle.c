@@ -15,7 +15,7 @@
  *                     a Lorentzian of unit weight centred on the band energy.
  *   Sec. 3 (rigid band): mu shifted to hold the requested electron count.
  *
- * Discretisation (each choice is a reading of the paper, listed in the design doc):
+ * Discretisation (each choice is a reading of where the paper is silent):
  *   lattice constant 1, zone width 2 pi, N = zones * npz points per axis,
  *   p_i = (i - N/2) * dp, dp = 2 pi / npz;
  *   cell-centred energies e_j = -E + (j + 1/2) de, de = 2E / n_eps;
