@@ -160,15 +160,24 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def workload_instance(workload):
+    """(band, grid, note) of the instance a CPU leg samples: the workload's own
+    single instance, or the first instance of a batched workload."""
+    from paper_1208_3210_gb300 import workloads as wl
+    if workload.startswith("batched_"):
+        inst = wl.batched_instances(int(workload.split("_")[1]))[0]
+        return dict(inst["band"]), inst["grid"], f"instance 0 of {workload}"
+    w = wl.WORKLOADS[workload]
+    return dict(w["band"]), w["grid"], workload
+
+
 def cpu_baseline(workload, seconds=15.0, seed=7):
     """The FP64 oracle (direct double sum of Eq. 9) on a bounded seeded sample
     of this workload's outputs, on all host cores."""
     import numpy as np
 
     import oracle
-    from paper_1208_3210_gb300 import workloads as wl
-    w = wl.WORKLOADS[workload]
-    band, grid = dict(w["band"]), w["grid"]
+    band, grid, workload = workload_instance(workload)
     t0 = time.perf_counter()
     band["mu"] = oracle.solve_mu(band["kind"], band["t"], band["tp"], band["tpp"], band["gamma"], grid["npz"],
                                  band["filling"])
@@ -234,9 +243,7 @@ def run_reference(args):
     import numpy as np
 
     import oracle
-    from paper_1208_3210_gb300 import workloads as wl
-    w = wl.WORKLOADS[args.workload]
-    band, grid = dict(w["band"]), w["grid"]
+    band, grid, _ = workload_instance(args.workload)
     band["mu"] = oracle.solve_mu(band["kind"], band["t"], band["tp"], band["tpp"], band["gamma"], grid["npz"],
                                  band["filling"])
     A = oracle.spectral(band, grid)
@@ -245,7 +252,10 @@ def run_reference(args):
     t0 = time.perf_counter()
     oracle.imchi_samples(A, grid, Q, rng.integers(0, Q, 16).astype(np.int32),
                          rng.integers(0, Q, 16).astype(np.int32), rng.integers(0, n_omega, 16).astype(np.int32))
-    per_step = max(16, int(16 / max(time.perf_counter() - t0, 1e-6) * 2.0))   # ~2 s of CPU work per step
+    # each step a bounded sample: about 2 s of CPU work, less when the whole
+    # --steps + --warmup run would otherwise exceed about two minutes
+    per_step_s = min(2.0, 120.0 / max(1, args.steps + args.warmup))
+    per_step = max(16, int(16 / max(time.perf_counter() - t0, 1e-6) * per_step_s))
 
     def step():
         lx = rng.integers(0, Q, per_step).astype(np.int32)
