@@ -133,3 +133,28 @@ def test_energy_direct_plan_rejections_on_host(lib, kw, flags, msg):
     st = lib.lindhard_plan_create(ctypes.byref(g), 1, flags, ctypes.byref(h))
     assert st == lh.EUNSUPPORTED and not h.value
     assert msg in lib.lindhard_last_error().decode()
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes mirrors of lindhard_band, lindhard_grid and lindhard_sizes
+    have the sizes and field offsets the C compiler gives the header's structs."""
+    import subprocess
+    from paper_1208_3210_gb300 import lindhard as lh
+    fields = {"lindhard_band": (lh.Band, [f[0] for f in lh.Band._fields_]),
+              "lindhard_grid": (lh.Grid, [f[0] for f in lh.Grid._fields_]),
+              "lindhard_sizes": (lh.Sizes, [f[0] for f in lh.Sizes._fields_])}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "lindhard.h"', "int main(void) {"]
+    for name, (_, names) in fields.items():
+        lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
+        for f in names:
+            lines.append(f'printf("{name}.{f} %zu\\n", offsetof({name}, {f}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)])
+    got = dict(line.split() for line in subprocess.check_output([str(exe)]).decode().splitlines())
+    for name, (cls, names) in fields.items():
+        assert int(got[name]) == ctypes.sizeof(cls), name
+        for f in names:
+            assert int(got[f"{name}.{f}"]) == getattr(cls, f).offset, (name, f)
