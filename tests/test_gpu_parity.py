@@ -13,6 +13,7 @@ import numpy as np
 import pytest
 
 import oracle
+from tail_report import format_rows, tail_report
 from paper_1208_3210_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
@@ -185,6 +186,8 @@ def test_full_size_workload_samples(lh, name, count):
     err = np.abs(got - ref).max() / scale
     print(f"{name}: {lx.size} samples, max err {err:.3e} of sample max, sample max / output max "
           f"{scale / mx:.3f}")
+    # the large-|q| tail apart (the bar above is relative to the maximum)
+    print(format_rows(tail_report(grid, lx, ly, m, got, ref, scale)))
     assert err <= TOL32, f"{name}: max err {err:.3e}"
 
 
