@@ -202,7 +202,26 @@ def cpu_baseline(workload, seconds=15.0, seed=7):
            "sample": f"FP64 direct double sum of Eq. 9 at {n} uniformly drawn outputs (q, w) of "
                      f"{workload} in {dt:.1f} s; A(p, e) tabulated once beforehand ({t_setup:.1f} s, untimed)"}
     res["fft_method"] = cpu_fft_method(A, grid, lx, ly, m, ref)
+    res["host"] = host_cpu()
     return res
+
+
+def host_cpu():
+    """The host cores the CPU legs may use and the processor model."""
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    try:
+        affinity = len(os.sched_getaffinity(0))
+    except Exception:
+        affinity = os.cpu_count() or 1
+    return {"affinity_cores": affinity, "model": model or "unknown"}
 
 
 def cpu_fft_method(A, grid, lx, ly, m, ref, max_points=1.2e8):
