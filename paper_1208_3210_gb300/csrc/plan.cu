@@ -626,7 +626,10 @@ static lindhard_status band_for_geom(const Geom &g, Band &o)
     if (g.quantity != LINDHARD_IMCHI && !(o.kT > 0))
         return fail(LINDHARD_EINVAL, "LINDHARD_IMCHI_T and LINDHARD_SQW grids need kT > 0");
     if (o.kT > 0) {
-        o.x_step64 = 0.5 * g.de / o.kT;
+        // capped so that the centre cell of an odd grid (2j + 1 = n_eps) keeps
+        // x = 0 * step = 0 (f = 1/2) for any kT; every other cell saturates to
+        // f = 0 or 1 long before the cap
+        o.x_step64 = std::min(0.5 * g.de / o.kT, 1e30);
         o.x_step = (float)o.x_step64;
     }
     return LINDHARD_OK;
