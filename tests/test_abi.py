@@ -106,15 +106,34 @@ def test_null_arguments(lib):
     (2, 0.0, True, True, "need kT > 0"),                     # caller A: kT still read and checked
 ])
 def test_temperature_arguments_on_host(lib, quantity, kT, a_in, band, msg):
-    # the no-allocation entry checks grid and band before it touches a device
+    # The no-allocation entry checks grid and band before it touches a device.
+    # The call gets a made-up device address for its buffers, so it runs in a
+    # child process that sees no GPU: should the host checks ever let a case
+    # through, the child's first CUDA call fails there instead of a kernel
+    # writing through that address on a shared GPU.
+    import subprocess
+    import sys
+    code = f"""
+import ctypes, sys
+sys.path.insert(0, {ROOT!r})
+from paper_1208_3210_gb300 import lindhard as lh
+lib = lh.load()
+g = lh.make_grid(2, 16, 32, 1.0, quantity={quantity})
+b = lh.make_band(kT={kT!r})
+fake = ctypes.c_void_p(256)
+st = lib.lindhard_imchi_noalloc(ctypes.byref(g), {'ctypes.byref(b)' if band else 'None'},
+                                {'fake' if a_in else 'None'}, fake, None, None)
+print(st)
+print(lib.lindhard_last_error().decode())
+"""
+    env = dict(os.environ, CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, "-c", code.replace("nan", "float('nan')")], env=env,
+                       capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stderr
+    st, err = r.stdout.split("\n", 1)
     from paper_1208_3210_gb300 import lindhard as lh
-    g = lh.make_grid(2, 16, 32, 1.0, quantity=quantity)
-    b = lh.make_band(kT=kT)
-    fake = ctypes.c_void_p(256)
-    st = lib.lindhard_imchi_noalloc(ctypes.byref(g), ctypes.byref(b) if band else None,
-                                    fake if a_in else None, fake, None, None)
-    assert st == lh.EINVAL
-    assert msg in lib.lindhard_last_error().decode()
+    assert int(st) == lh.EINVAL
+    assert msg in err
 
 
 @pytest.mark.parametrize("kw,flags,msg", [

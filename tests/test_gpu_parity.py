@@ -153,7 +153,8 @@ def test_two_calls_identical_and_no_state(lh):
 
 # --- full-size workloads, sampled outputs -------------------------------------------
 
-@pytest.mark.parametrize("name,count", [("extended_256x256x256", 1500), ("large_1024x1024x512", 400)])
+# (the large workload, and every engine variant it can run, is in test_gpu_large.py)
+@pytest.mark.parametrize("name,count", [("extended_256x256x256", 1500)])
 def test_full_size_workload_samples(lh, name, count):
     import torch
     w = wl.WORKLOADS[name]
