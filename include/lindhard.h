@@ -340,11 +340,15 @@ lindhard_status lindhard_kk_rpa(lindhard_plan *plan, int index, const float *imc
  * LINDHARD_PLAN_AUTOTUNE, else the defaults): out[0], out[1] = forward and
  * inverse passes along p_y (0 single-column engine, 1 paired columns,
  * 2 paired columns with 12 values per thread, 3, 4 and 5 the TMA-staged
- * persistent forms of 1, 2 and 0, 6 paired columns on double-width tiles);
+ * persistent forms of 1, 2 and 0, 6 paired columns on double-width tiles,
+ * 7 the tensor-core inverse, 8 and 9 the pruned engine on 8 and 4 column
+ * pairs: a radix-24 stage at the padded end, for a padding of exactly one
+ * third, N = 2P/3 forward and Q = 2P/3 inverse);
  * out[2] = the p_x product pass (0 default
  * tile, 1 tile with 12 values per thread, 2 and 3 their TMA-staged forms,
  * 4 the default tile with one more CTA per SM, 5 the default tile twice as
- * wide); out[3] = the inverse energy
+ * wide, 6 and 7 the pruned engine on 8 and 4 columns, N = Q = 2P/3);
+ * out[3] = the inverse energy
  * pass (0 default, 1 TMA-staged persistent form).
  * out: host, int[4]. */
 lindhard_status lindhard_plan_variants(const lindhard_plan *plan, int index, int *out);

@@ -1,0 +1,261 @@
+// Energy pass with one warp per momentum point (FP32, T = 0 split).
+//
+// The same transform as k_fwd_energy (Eqs. 4-5 generated on chip, the T = 0
+// split of Sec. 3 / Appendix A Eq. A3, z = a + i b transformed along energy,
+// a^ and b^ separated for the non-redundant frequencies k <= L/2), arranged
+// so that
+//   * the L/16 threads of one line (momentum point) sit in one warp (a warp
+//     holds 32 / (L/16) lines at a time): every exchange of a line stays in
+//     its warp (__syncwarp, no CTA barrier), the warp's lines' band energies
+//     are computed by one lane each and broadcast by shuffles, and every
+//     thread keeps its line's band energy and amplitude in registers;
+//   * every shared-memory address is a per-butterfly base plus compile-time
+//     offsets (one pad value every 16 spreads the Stockham writes over the
+//     banks), the twiddles 16-byte loads from per-stage tables;
+//   * in the last stage a thread owns butterflies j and L/8 - j, so it holds
+//     Z(k) and Z(L - k) together and separates a^(k) = (Z(k) + conj Z(L - k))/2
+//     and b^(k) = (Z(k) - conj Z(L - k))/2i in registers (no natural-order
+//     copy of the spectrum); a warp's stores of one line are contiguous.
+// Schedules (forward): 128 = 4.4.8, 256 = 4.8.8, 512 = 8.8.8; 16 values per
+// thread.  Output U1 [N*N lines][SP][2] as k_fwd_energy writes it.
+#include "kernels.cuh"
+
+namespace lh {
+
+__host__ __device__ constexpr bool et_supported(int L) { return L == 128 || L == 256 || L == 512; }
+__host__ __device__ constexpr int et_radix(int L, int s)
+{
+    return s == 2 ? 8 : L == 512 ? 8 : L == 256 ? (s == 0 ? 4 : 8) : 4;
+}
+__host__ __device__ constexpr int et_ns(int L, int s) { return s == 0 ? 1 : et_ns(L, s - 1) * et_radix(L, s - 1); }
+// per-stage twiddle tables [k][Rs], k < Ns, stages 1 and 2 of 128, 256, 512
+__host__ __device__ constexpr int et_table_offset(int L, int s)
+{
+    return (L == 128 ? 0 : L == 256 ? 16 + 128 : 16 + 128 + 32 + 256) + (s == 2 ? et_ns(L, 2) : 0);
+}
+__host__ __device__ constexpr int et_twiddle_entries() { return 16 + 128 + 32 + 256 + 64 + 512; }
+
+__global__ void k_et_twiddles(float2 *out)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= et_twiddle_entries()) return;
+    const int Ls[3] = {128, 256, 512};
+    for (int i = 0; i < 3; ++i)
+        for (int s = 1; s <= 2; ++s) {
+            const int L = Ls[i], off = et_table_offset(L, s), n = et_ns(L, s + 1), Rs = et_radix(L, s);
+            if (e >= off && e < off + n) {
+                const int k = (e - off) / Rs, r = (e - off) % Rs;
+                double sn, cs;
+                sincospi(-2.0 * (double)((k * r) % n) / (double)n, &sn, &cs);
+                out[e] = make_float2((float)cs, (float)sn);
+                return;
+            }
+        }
+}
+cudaError_t launch_et_twiddles(float2 *out, cudaStream_t s)
+{
+    k_et_twiddles<<<(et_twiddle_entries() + 255) / 256, 256, 0, s>>>(out);
+    return cudaGetLastError();
+}
+size_t et_twiddle_bytes() { return (size_t)et_twiddle_entries() * sizeof(float2); }
+bool et_applies(const Geom &g, const Band &band) { return et_supported(g.PE) && !(band.kT > 0); }
+
+// Per warp: ET_LPW lines, LPI = 32 / TPL at a time (TPL = L/16 threads per
+// line); shared memory per warp LPI lines of L + L/16 values.
+constexpr int ET_LPW = 4, ET_WARPS = 8;
+template <int L>
+struct EtGeo {
+    static constexpr int TPL = L / 16, LPI = 32 / TPL, LP = L + L / 16;
+    static constexpr int R0 = et_radix(L, 0), R1 = et_radix(L, 1), R2 = 8;
+    static constexpr int N1 = et_ns(L, 1), N2 = et_ns(L, 2);
+    static constexpr int WARP_ELEMS = LPI * LP;
+    static_assert(R0 * R1 * R2 == L && 16 % R0 == 0 && 16 % R1 == 0, "schedule");
+    static_assert((L / R1) % 16 == 0 && (L / 8) % 16 == 0 && N2 % 16 == 0 && ET_LPW % LPI == 0,
+                  "compile-time padded offsets");
+};
+__host__ __device__ constexpr int et_pad(int n) { return n + n / 16; }
+
+// 1/x as the hardware approximation (relative error about 2^-23; x lies in
+// [gamma^2, 4 e_max^2 + gamma^2], away from zero, subnormals and overflow)
+__device__ __forceinline__ float et_rcp(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// FULL: n_eps == L (no energy padding; occupied rows n < L/2).  GEN: A is
+// generated (else read from the caller's A_in).
+template <int L, bool FULL, bool GEN>
+__global__ void __launch_bounds__(32 * ET_WARPS)
+k_fwd_energy_warp(Geom g, Band band, const AxisTab *__restrict__ axis, const float2 *__restrict__ eps,
+                  const InstState *__restrict__ st, const float *__restrict__ A_in, float2 *__restrict__ U1,
+                  const float2 *__restrict__ etw)
+{
+    using G = EtGeo<L>;
+    constexpr int TPL = G::TPL, LPI = G::LPI, LP = G::LP, R0 = G::R0, R1 = G::R1, R2 = G::R2;
+    constexpr int N1 = G::N1, N2 = G::N2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    LH_REQUIRE_SMEM(ET_WARPS * G::WARP_ELEMS, float2)
+    const int lane = (int)threadIdx.x % 32, warp = (int)threadIdx.x / 32;
+    const int sl = lane / TPL, u = lane % TPL;
+    float2 *sm = reinterpret_cast<float2 *>(smem_raw) + warp * G::WARP_ELEMS + sl * LP;
+    const long long nlines = (long long)g.N * g.N;
+    const long long line0 = ((long long)blockIdx.x * ET_WARPS + warp) * ET_LPW;
+    const float g2 = band.gam2;
+    const float2 *tw1 = etw + et_table_offset(L, 1), *tw2 = etw + et_table_offset(L, 2);
+
+    // band energy xi_p = e0(p) - mu (double-float) and |M(p)|^2 gamma / pi of
+    // the warp's lines (Eqs. 4-5), one lane per line; the amplitude carries
+    // the 1/2 of the a^ / b^ separation below (exact), and is 0 for lines
+    // past the end (their values come out 0, no branch per value)
+    float bx = 0.f, bl = 0.f, ba = 0.f;
+    if (GEN && lane < ET_LPW && line0 + lane < nlines) {
+        const long long line = line0 + lane;
+        const int ix = (int)(line / g.N), iy = (int)(line - (long long)ix * g.N);
+        band_point_f32(band, axis[ix], axis[iy], st, bx, bl, ba);
+        ba *= 0.5f;
+    }
+
+    for (int it = 0; it < ET_LPW; it += LPI) {
+        const long long line = line0 + it + sl;
+        const bool live = line < nlines;
+        const float xhi = __shfl_sync(0xffffffffu, bx, it + sl), xlo = __shfl_sync(0xffffffffu, bl, it + sl);
+        const float amp = __shfl_sync(0xffffffffu, ba, it + sl);
+
+        // stage 0: butterflies j = u + b TPL, rows j + r L/R0
+        float2 v[16];
+#pragma unroll
+        for (int b = 0; b < 16 / R0; ++b) {
+            const int j = u + b * TPL;
+#pragma unroll
+            for (int r = 0; r < R0; ++r) {
+                const int n = j + r * (L / R0);
+                float A;
+                if constexpr (GEN) {
+                    const float2 ej = __ldg(&eps[FULL ? n : min(n, g.n_eps - 1)]);
+                    const float e = (ej.x - xhi) + (ej.y - xlo);
+                    A = amp * et_rcp(fmaf(e, e, g2));
+                    if (!FULL && n >= g.n_eps) A = 0.f;
+                } else {
+                    A = (live && (FULL || n < g.n_eps)) ? 0.5f * A_in[line * g.n_eps + n] : 0.f;
+                }
+                // occupied (e_n < 0) -> real part, empty -> imaginary part
+                const bool occ = FULL ? (r < R0 / 2) : (2 * n + 1 < g.n_eps);
+                v[b * R0 + r] = occ ? make_float2(A, 0.f) : make_float2(0.f, A);
+            }
+            Dft<R0, false, float2>::run(v + b * R0);
+        }
+        // exchange 1 (outputs at j R0 + r) and stage 1: butterflies u + b TPL
+        __syncwarp();
+#pragma unroll
+        for (int b = 0; b < 16 / R0; ++b) {
+            const int base = (u + b * TPL) * R0;
+            const int pb = base + base / 16;
+#pragma unroll
+            for (int r = 0; r < R0; ++r) sm[pb + r] = v[b * R0 + r];
+        }
+        __syncwarp();
+#pragma unroll
+        for (int b = 0; b < 16 / R1; ++b) {
+            const int j = u + b * TPL;
+            const int pj = et_pad(j);
+#pragma unroll
+            for (int r = 0; r < R1; ++r) v[b * R1 + r] = sm[pj + et_pad(r * (L / R1))];
+            const float4 *w4 = reinterpret_cast<const float4 *>(tw1 + (j % N1) * R1);
+#pragma unroll
+            for (int h = 0; h < R1 / 2; ++h) {
+                const float4 q = __ldg(w4 + h);
+                if (h > 0) v[b * R1 + 2 * h] = cmul(v[b * R1 + 2 * h], make_float2(q.x, q.y));
+                v[b * R1 + 2 * h + 1] = cmul(v[b * R1 + 2 * h + 1], make_float2(q.z, q.w));
+            }
+            Dft<R1, false, float2>::run(v + b * R1);
+        }
+        // exchange 2 (outputs at (j / N1) N2 + j % N1 + r N1) and stage 2:
+        // butterflies u and L/8 - u (u = 0: 0 and L/16), so that Z(k) and
+        // Z(L - k) end in the same thread
+        __syncwarp();
+#pragma unroll
+        for (int b = 0; b < 16 / R1; ++b) {
+            const int j = u + b * TPL;
+            const int base = (j / N1) * N2 + j % N1;   // base % 16 = j % N1 < N1
+            const int pb = base + base / 16;
+#pragma unroll
+            for (int r = 0; r < R1; ++r) sm[pb + r * N1 + (r * N1) / 16] = v[b * R1 + r];
+        }
+        __syncwarp();
+        const int j2[2] = {u, u == 0 ? TPL : L / 8 - u};
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const int pj = et_pad(j2[b]);
+#pragma unroll
+            for (int r = 0; r < R2; ++r) v[b * R2 + r] = sm[pj + et_pad(r * (L / 8))];
+            const float4 *w4 = reinterpret_cast<const float4 *>(tw2 + j2[b] * R2);   // j < N2
+#pragma unroll
+            for (int h = 0; h < R2 / 2; ++h) {
+                const float4 q = __ldg(w4 + h);
+                if (h > 0) v[b * R2 + 2 * h] = cmul(v[b * R2 + 2 * h], make_float2(q.x, q.y));
+                v[b * R2 + 2 * h + 1] = cmul(v[b * R2 + 2 * h + 1], make_float2(q.z, q.w));
+            }
+            Dft<R2, false, float2>::run(v + b * R2);
+        }
+
+        // Z(j + r L/8) in v[b 8 + r]; the partner Z(L - k) of (j2[0], r) is
+        // (j2[1], 7 - r) for u > 0; of (0, r) it is (0, 8 - r), of (L/16, r)
+        // it is (L/16, 7 - r)
+        if (live) {
+            float2 *row = U1 + line * (2LL * g.SP);
+            // a^ = (Z(k) + conj Z(-k)) / 2, b^ = (Z(k) - conj Z(-k)) / 2i, the
+            // 1/2 already in Z (the amplitude)
+            auto put = [&](int k, float2 zk, float2 zm) {
+                gst2(row + 2 * k, make_float2(zk.x + zm.x, zk.y - zm.y), make_float2(zk.y + zm.y, zm.x - zk.x));
+            };
+            const bool u0 = u == 0;
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                put(j2[0] + r * (L / 8), v[r], u0 ? v[(8 - r) & 7] : v[8 + 7 - r]);
+                put(j2[1] + r * (L / 8), v[8 + r], u0 ? v[8 + 7 - r] : v[7 - r]);
+            }
+            if (u0) put(L / 2, v[4], v[4]);
+        }
+        __syncwarp();   // the next line's exchange overwrites this one's
+    }
+}
+
+template <int L>
+cudaError_t launch_fwd_energy_col_t(const Geom &g, const Band &band, const Work<float> &w, const float *A_in,
+                                    cudaStream_t s)
+{
+    const long long nlines = (long long)g.N * g.N;
+    const long long per = (long long)ET_WARPS * ET_LPW;
+    const unsigned grid = (unsigned)((nlines + per - 1) / per);
+    const size_t smem = sizeof(float2) * ET_WARPS * EtGeo<L>::WARP_ELEMS;
+    static const cudaError_t e0 = smem_attrs(k_fwd_energy_warp<L, true, true>, smem);
+    static const cudaError_t e1 = smem_attrs(k_fwd_energy_warp<L, false, true>, smem);
+    static const cudaError_t e2 = smem_attrs(k_fwd_energy_warp<L, true, false>, smem);
+    static const cudaError_t e3 = smem_attrs(k_fwd_energy_warp<L, false, false>, smem);
+    if (e0 != cudaSuccess) return e0;
+    if (e1 != cudaSuccess) return e1;
+    if (e2 != cudaSuccess) return e2;
+    if (e3 != cudaSuccess) return e3;
+    const bool full = g.n_eps == L;
+    auto k = A_in ? (full ? k_fwd_energy_warp<L, true, false> : k_fwd_energy_warp<L, false, false>)
+                  : (full ? k_fwd_energy_warp<L, true, true> : k_fwd_energy_warp<L, false, true>);
+    k<<<grid, 32 * ET_WARPS, smem, s>>>(g, band, w.axis, (const float2 *)w.eps, w.state, A_in, (float2 *)w.X,
+                                        (const float2 *)w.etw);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fwd_energy_col(const Geom &g, const Band &band, const Work<float> &w, const float *A_in,
+                                  cudaStream_t s)
+{
+    if (!w.etw) return cudaErrorInvalidValue;
+    switch (g.PE) {
+    case 128: return launch_fwd_energy_col_t<128>(g, band, w, A_in, s);
+    case 256: return launch_fwd_energy_col_t<256>(g, band, w, A_in, s);
+    case 512: return launch_fwd_energy_col_t<512>(g, band, w, A_in, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace lh

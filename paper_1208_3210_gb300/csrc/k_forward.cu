@@ -288,9 +288,15 @@ cudaError_t launch_fwd_y_t(const Geom &g, const Work<Real> &w, cudaStream_t s, i
     return cudaGetLastError();
 }
 
+bool et_applies(const Geom &g, const Band &band);
+cudaError_t launch_fwd_energy_col(const Geom &g, const Band &band, const Work<float> &w, const float *A_in,
+                                  cudaStream_t s);
+// FP32: lengths 128, 256 and 512 at T = 0 take the lines-across-lanes pass of
+// k_energy.cu when the plan has its twiddle tables
 cudaError_t launch_fwd_energy(const Geom &g, const Band &band, const Work<float> &w, const float *A_in,
                               cudaStream_t s)
 {
+    if (w.etw && et_applies(g, band)) return launch_fwd_energy_col(g, band, w, A_in, s);
 #define CALL(L) launch_fwd_energy_t<float, L>(g, band, w, A_in, s)
     LH_P_SWITCH(g.PE, CALL)
 #undef CALL
@@ -303,10 +309,13 @@ cudaError_t launch_fwd_energy(const Geom &g, const Band &band, const Work<double
 #undef CALL
 }
 cudaError_t launch_fwd_y_tma(const Geom &g, const Work<float> &w, cudaStream_t s, int variant);
-// variants 3, 4: the TMA-staged persistent kernels of k_tma.cu
+cudaError_t launch_fwd_y_pr(const Geom &g, const Work<float> &w, cudaStream_t s, int variant);
+// variants 3, 4, 5: the TMA-staged persistent kernels of k_tma.cu; 8, 9: the
+// pruned engine of k_pruned.cu (one-third padding)
 cudaError_t launch_fwd_y(const Geom &g, const Work<float> &w, cudaStream_t s, int variant)
 {
     if (variant >= 3 && variant <= 5) return launch_fwd_y_tma(g, w, s, variant);
+    if (variant == 8 || variant == 9) return launch_fwd_y_pr(g, w, s, variant);
 #define CALL(L) launch_fwd_y_t<float, L>(g, w, s, variant)
     LH_P_SWITCH(g.P, CALL)
 #undef CALL

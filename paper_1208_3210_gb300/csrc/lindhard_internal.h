@@ -65,7 +65,7 @@ struct Band {
     int solve_mu;   // 1: mu from filling
     // FP32 forms for the energy pass: -2t, -4t', -2t'' as unevaluated
     // (hi, lo) pairs, and gamma / pi
-    float k1[2], k2[2], k3[2], gam_pi;
+    float k1[2], k2[2], k3[2], gam_pi, gam2;
     // temperature (0: the T = 0 split); e_j / kT = (2 j + 1 - n_eps) x_step
     double kT, x_step64;
     float x_step;
@@ -111,6 +111,8 @@ struct Work {
     const void *tw;        // twiddle tables (see twiddles_for): float2 or double2
     int tw_len;            // longest transform length of the plan
     const void *tc;        // tensor-core DFT matrices (k_tc.cu), or null
+    const void *ptw = nullptr;   // per-stage twiddle tables of the pruned engine (FP32), or null
+    const void *etw = nullptr;   // per-stage twiddle tables of the lines-across-lanes energy pass, or null
     InstState *state;      // [1]
     unsigned *status;      // plan-wide device status word
     double *mu_acc;        // scratch for the chemical potential solve

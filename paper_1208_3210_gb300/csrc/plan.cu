@@ -52,6 +52,12 @@ cudaError_t launch_kk_tables(int nw, void *tab, cudaStream_t s);
 cudaError_t launch_kk_rpa(const Geom &g, const float *im, float *re, float2 *rpa, const void *tab, double v0,
                           int variant, unsigned *status, cudaStream_t s);
 size_t tc_mats_bytes();
+size_t pr_twiddle_bytes();
+size_t et_twiddle_bytes();
+cudaError_t launch_et_twiddles(float2 *out, cudaStream_t s);
+cudaError_t launch_pr_twiddles(float2 *out, cudaStream_t s);
+bool pr_fwd_applies(const Geom &g);
+bool pr_inv_applies(const Geom &g);
 cudaError_t launch_tc_mats(void *buf, cudaStream_t s);
 cudaError_t launch_inv_y(const Geom &g, const Work<double> &w, cudaStream_t s, int variant);
 cudaError_t launch_inv_energy(const Geom &g, const Work<float> &w, float *out, cudaStream_t s, int variant);
@@ -123,7 +129,7 @@ struct lindhard_plan {
         size_t X = 0, Y = 0, Z = 0, partial = 0, axis = 0, eps32 = 0, eps64 = 0, state = 0, acc = 0, bar = 0;
     };
     std::vector<Slot> slots;
-    size_t off_tw32 = 0, off_tw64 = 0, off_status = 0, off_tc = 0, off_dmu = 0;
+    size_t off_tw32 = 0, off_tw64 = 0, off_status = 0, off_tc = 0, off_dmu = 0, off_prtw = 0, off_etw = 0;
     std::vector<size_t> off_kk;   // Kramers-Kronig weight tables per instance (FP32 grids)
     int tw_len = 0;
     bool backward = false;       // LINDHARD_PLAN_BACKWARD
@@ -373,6 +379,12 @@ static cudaError_t autotune(lindhard_plan *p)
             vx.push_back(1);
             vx.push_back(3);
         }
+        // the pruned engine (one-third padding): forward p_y and inverse p_y
+        // separately (N and Q), the product pass needs both
+        std::vector<int> vyf = vy, vyi = vy;
+        if (pr_fwd_applies(g)) { vyf.push_back(8); vyf.push_back(9); }
+        if (pr_inv_applies(g)) { vyi.push_back(8); vyi.push_back(9); }
+        if (pr_fwd_applies(g) && pr_inv_applies(g)) { vx.push_back(6); vx.push_back(7); }
         Work<float> w = work_of<float>(p, i);
         // fastest of the variants of one pass (timed only when not cached)
         auto pick = [&](const std::string &k, const std::vector<int> &vs, auto launch) {
@@ -392,9 +404,9 @@ static cudaError_t autotune(lindhard_plan *p)
             }
             return g_tune[k].variant;
         };
-        p->yvar_fwd[i] = pick(kf, vy, [&](int v) { return launch_fwd_y(g, w, 0, v); });
+        p->yvar_fwd[i] = pick(kf, vyf, [&](int v) { return launch_fwd_y(g, w, 0, v); });
         if (p->precision[i] != LINDHARD_SPLITBF16_TC)
-            p->yvar_inv[i] = pick(ki, vy, [&](int v) { return launch_inv_y(g, w, 0, v); });
+            p->yvar_inv[i] = pick(ki, vyi, [&](int v) { return launch_inv_y(g, w, 0, v); });
         p->xvar[i] = pick(kx, vx, [&](int v) { return launch_x_product(g, w, 0, v); });
         // the inverse energy pass writes the caller's output: time it into the
         // workspace's X buffer (at least as large as the output)
@@ -485,6 +497,8 @@ extern "C" lindhard_status lindhard_plan_create(const lindhard_grid *grids, int 
     p->off_tw32 = o; o = align_up(o + (size_t)twiddle_entries() * sizeof(float2));
     p->off_tw64 = o; o = align_up(o + (size_t)twiddle_entries() * sizeof(double2));
     p->off_status = o; o = align_up(o + sizeof(unsigned));
+    p->off_prtw = o; o = align_up(o + pr_twiddle_bytes());   // pruned engine's per-stage twiddles
+    p->off_etw = o; o = align_up(o + et_twiddle_bytes());     // energy pass's per-stage twiddles
     p->off_dmu = o; o = align_up(o + sizeof(double) * 5 * kDmuBlocks);
     // tensor-core DFT matrices of every supported length (plans with a
     // LINDHARD_SPLITBF16_TC grid only)
@@ -534,6 +548,8 @@ extern "C" lindhard_status lindhard_plan_create(const lindhard_grid *grids, int 
         if (e == cudaSuccess) e = cudaMemset(p->ws + sl.bar, 0, mu_barrier_words() * sizeof(unsigned));
     if (e == cudaSuccess)
         e = launch_twiddles(p->tw_len, (float2 *)(p->ws + p->off_tw32), (double2 *)(p->ws + p->off_tw64), 0);
+    if (e == cudaSuccess) e = launch_pr_twiddles((float2 *)(p->ws + p->off_prtw), 0);
+    if (e == cudaSuccess) e = launch_et_twiddles((float2 *)(p->ws + p->off_etw), 0);
     if (e == cudaSuccess && p->off_tc) e = launch_tc_mats(p->ws + p->off_tc, 0);
     for (int i = 0; i < batch && e == cudaSuccess; ++i)
         if (p->off_kk[i]) e = launch_kk_tables(p->geoms[i].n_omega, p->ws + p->off_kk[i], 0);
@@ -661,6 +677,7 @@ static lindhard_status make_band(const lindhard_band *b, Band &o)
     pair(-4.0 * b->tp, o.k2);
     pair(-2.0 * b->tpp, o.k3);
     o.gam_pi = (float)(b->gamma / M_PI);
+    o.gam2 = (float)(b->gamma * b->gamma);
     lindhard_status st = band_temperature(b, o);
     if (st != LINDHARD_OK) return st;
     if (o.solve_mu) {
@@ -683,6 +700,8 @@ static Work<Real> work_of(lindhard_plan *p, int i)
     w.tw = sizeof(Real) == 4 ? (const void *)(p->ws + p->off_tw32) : (const void *)(p->ws + p->off_tw64);
     w.tw_len = p->tw_len;
     w.tc = p->off_tc ? (const void *)(p->ws + p->off_tc) : nullptr;
+    w.ptw = sizeof(Real) == 4 ? (const void *)(p->ws + p->off_prtw) : nullptr;
+    w.etw = sizeof(Real) == 4 ? (const void *)(p->ws + p->off_etw) : nullptr;
     w.state = (InstState *)(p->ws + sl.state);
     w.status = (unsigned *)(p->ws + p->off_status);
     w.mu_acc = (double *)(p->ws + sl.acc);

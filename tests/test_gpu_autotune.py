@@ -94,7 +94,7 @@ def test_fresh_tune_writes_cache_and_matches_default(lh, tmp_path, monkeypatch):
     kf, ki, kx, ke = _keys(grid, plan.sizes[0])
     plan.close()
     entries = json.loads(path.read_text())
-    assert entries[kf] in range(7) and entries[ki] in range(7) and entries[kx] in range(6) and entries[ke] in (0, 1)
+    assert entries[kf] in range(10) and entries[ki] in range(10) and entries[kx] in range(8) and entries[ke] in (0, 1)
     base = lh.Plan([grid])
     out_d = base.imchi([band])
     base.status()
