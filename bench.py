@@ -33,11 +33,11 @@ sys.path.insert(0, ROOT)
 DEFAULT_WORKLOAD = "large_1024x1024x512"
 FALLBACK_HBM_GBS = 6800.0
 PASS_FILES = {  # kernel sources of each timed pass (for traffic-record staleness)
-    "energy_fwd": ("k_forward.cu",),
+    "energy_fwd": ("k_forward.cu", "k_energy.cu"),
     "py_fwd": ("k_forward.cu", "k_tma.cu", "tma.cuh", "async.cuh", "k_pruned.cu", "fft_pruned.cuh"),
     "px_product": ("k_product.cu", "k_tma.cu", "tma.cuh", "async.cuh", "k_pruned.cu", "fft_pruned.cuh"),
     "py_inv": ("k_inverse.cu", "k_tma.cu", "tma.cuh", "async.cuh", "k_pruned.cu", "fft_pruned.cuh"),
-    "energy_inv": ("k_inverse.cu", "k_tma.cu", "tma.cuh", "async.cuh"),
+    "energy_inv": ("k_inverse.cu", "k_tma.cu", "tma.cuh", "async.cuh", "k_energy.cu"),
 }
 # kernel of each pass by engine variant (lindhard_plan_variants)
 VARIANT_KERNELS = {
@@ -51,7 +51,7 @@ VARIANT_KERNELS = {
                    "k_x_product_tma (12-value tiles)", "k_x_product (one more CTA per SM)",
                    "k_x_product (double-width tile)", "k_x_product_pr (pruned, 8 columns)",
                    "k_x_product_pr (pruned, 4 columns)"],
-    "energy_inv": ["k_inv_energy", "k_inv_energy_tma"],
+    "energy_inv": ["k_inv_energy", "k_inv_energy_tma", "k_inv_energy_warp"],
 }
 KERNEL_NAMES = {"batch": "all passes of all instances (graph)", "energy_fwd": "k_fwd_energy", "py_fwd": "k_fwd_y", "px_product": "k_x_product",
                 "py_inv": "k_inv_y", "energy_inv": "k_inv_energy", "tables": "k_setup", "mu_solve": "k_mu_sect, k_mu_halley"}

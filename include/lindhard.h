@@ -349,7 +349,8 @@ lindhard_status lindhard_kk_rpa(lindhard_plan *plan, int index, const float *imc
  * 4 the default tile with one more CTA per SM, 5 the default tile twice as
  * wide, 6 and 7 the pruned engine on 8 and 4 columns, N = Q = 2P/3);
  * out[3] = the inverse energy
- * pass (0 default, 1 TMA-staged persistent form).
+ * pass (0 default, 1 TMA-staged persistent form, 2 one warp per pair of
+ * output lines, energy FFT lengths 128, 256 and 512).
  * out: host, int[4]. */
 lindhard_status lindhard_plan_variants(const lindhard_plan *plan, int index, int *out);
 

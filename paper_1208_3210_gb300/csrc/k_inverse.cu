@@ -222,10 +222,13 @@ cudaError_t launch_inv_y(const Geom &g, const Work<double> &w, cudaStream_t s, i
 #undef CALL
 }
 cudaError_t launch_inv_energy_tma(const Geom &g, const Work<float> &w, float *out, cudaStream_t s);
-// variant 1: the TMA-staged persistent kernel of k_tma.cu
+cudaError_t launch_inv_energy_warp(const Geom &g, const Work<float> &w, float *out, cudaStream_t s);
+// variant 1: the TMA-staged persistent kernel of k_tma.cu; 2: one warp per
+// pair of output lines (k_energy.cu)
 cudaError_t launch_inv_energy(const Geom &g, const Work<float> &w, float *out, cudaStream_t s, int variant)
 {
     if (variant == 1) return launch_inv_energy_tma(g, w, out, s);
+    if (variant == 2) return launch_inv_energy_warp(g, w, out, s);
 #define CALL(L) launch_inv_energy_t<float, float, L>(g, w, out, s)
     LH_P_SWITCH(g.PE, CALL)
 #undef CALL

@@ -58,6 +58,7 @@ cudaError_t launch_et_twiddles(float2 *out, cudaStream_t s);
 cudaError_t launch_pr_twiddles(float2 *out, cudaStream_t s);
 bool pr_fwd_applies(const Geom &g);
 bool pr_inv_applies(const Geom &g);
+bool et_inv_applies(const Geom &g);
 cudaError_t launch_tc_mats(void *buf, cudaStream_t s);
 cudaError_t launch_inv_y(const Geom &g, const Work<double> &w, cudaStream_t s, int variant);
 cudaError_t launch_inv_energy(const Geom &g, const Work<float> &w, float *out, cudaStream_t s, int variant);
@@ -410,7 +411,9 @@ static cudaError_t autotune(lindhard_plan *p)
         p->xvar[i] = pick(kx, vx, [&](int v) { return launch_x_product(g, w, 0, v); });
         // the inverse energy pass writes the caller's output: time it into the
         // workspace's X buffer (at least as large as the output)
-        p->evar[i] = pick(ke, {0, 1}, [&](int v) { return launch_inv_energy(g, w, (float *)w.X, 0, v); });
+        std::vector<int> ve = {0, 1};
+        if (et_inv_applies(g)) ve.push_back(2);
+        p->evar[i] = pick(ke, ve, [&](int v) { return launch_inv_energy(g, w, (float *)w.X, 0, v); });
         e = cudaGetLastError();
     }
     cudaEventDestroy(a);

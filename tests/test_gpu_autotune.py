@@ -60,7 +60,8 @@ def test_pinned_variants_match_oracle(lh, grid, tmp_path, monkeypatch):
     # with 12 values per thread; 3/4 = TMA-staged forms of 1/2.  Product:
     # 0/1 = default and 12-value tiles, 2/3 = their TMA-staged forms.  The
     # 12-value tiles exist for 3 * 2^k only.
-    combos = [(0, 0), (1, 0), (3, 2), (5, 4)] + ([(2, 1), (1, 1), (4, 3), (3, 3)] if three_pow else [])
+    # 8/9 and 6/7: the pruned engine on 8 and 4 column pairs (N = Q = 2P/3 only)
+    combos = [(0, 0), (1, 0), (3, 2), (5, 4)] + ([(2, 1), (1, 1), (4, 3), (3, 3), (8, 6), (9, 7)] if three_pow else [])
     outs = []
     for j, (vy, vx) in enumerate(combos):
         ve = j % 2   # inverse energy pass: default and TMA-staged forms in turn
@@ -94,7 +95,7 @@ def test_fresh_tune_writes_cache_and_matches_default(lh, tmp_path, monkeypatch):
     kf, ki, kx, ke = _keys(grid, plan.sizes[0])
     plan.close()
     entries = json.loads(path.read_text())
-    assert entries[kf] in range(10) and entries[ki] in range(10) and entries[kx] in range(8) and entries[ke] in (0, 1)
+    assert entries[kf] in range(10) and entries[ki] in range(10) and entries[kx] in range(8) and entries[ke] in (0, 1, 2)
     base = lh.Plan([grid])
     out_d = base.imchi([band])
     base.status()
