@@ -472,6 +472,7 @@ def main():
         dist.barrier()
 
     batched = args.workload.startswith("batched_")
+    persistent = False
     prec = lh.SPLITBF16_TC if args.precision == "tc" else lh.FP32
     if prec != lh.FP32:
         args.no_tc = True   # the timed form is the tensor-core one already
@@ -480,7 +481,10 @@ def main():
         count = int(args.workload.split("_")[1])
         grids, bands = wl.batched_workload(count)
         grids = [dict(g, precision=prec) for g in grids]
-        plan = lh.Plan(grids, graph=True, autotune=not args.no_autotune)
+        # FP32: the persistent batch launch (every instance's passes in one
+        # launch) replayed as a graph; other precisions: graph of stream branches
+        persistent = prec == lh.FP32
+        plan = lh.Plan(grids, graph=True, persistent=persistent, autotune=not args.no_autotune)
         args.no_cpu_baseline = True
     else:
         w = wl.WORKLOADS[args.workload]
@@ -555,7 +559,7 @@ def main():
     dev_outs = [out, torch.empty_like(out)]
     # a caller repeating the call replays it as a CUDA graph (LINDHARD_PLAN_GRAPH):
     # one graph plan per output buffer, so neither records again
-    e2e_plans = ([plan, lh.Plan(grids, graph=True, autotune=not args.no_autotune)] if batched else
+    e2e_plans = ([plan, lh.Plan(grids, graph=True, persistent=persistent, autotune=not args.no_autotune)] if batched else
                  [lh.Plan(grids, graph=True, autotune=not args.no_autotune) for _ in range(2)])
     for b in range(2):
         for _ in range(3):
@@ -597,9 +601,9 @@ def main():
     # kernels launched in the timed region: each step is one forward call; a
     # third multisection pass when gamma < 0.02 eV and the solve spans
     # several CTAs (more than 98 points per zone)
-    launches = sum(int(plan.sizes[i].kernels_forward)
-                   + (1 if bands[i]["gamma"] < 0.02 and grids[i]["npz"] > 98 else 0)
-                   for i in range(len(grids))) * args.steps
+    launches = (sum(int(plan.sizes[i].kernels_forward)
+                    + (1 if bands[i]["gamma"] < 0.02 and grids[i]["npz"] > 98 else 0)
+                    for i in range(len(grids))) + (1 if batched and persistent else 0)) * args.steps
     if batched:
         # concurrent instances: no per-pass split, the batch as one unit
         pipeline_bytes = sum(sum(pass_bytes(plan.sizes[i]).values()) for i in range(len(grids)))
@@ -645,6 +649,26 @@ def main():
         del seq_out
         plain = {"ms_per_step": seq_ms, "value": outputs_per_step / world / (seq_ms * 1e-3),
                  "speedup_batched": seq_ms / step_ms, "max_rel_diff": diff}
+        if persistent:
+            # the earlier batched form: every instance's launches on forked
+            # streams, recorded into one graph (no persistent launch)
+            cg = lh.Plan(grids, graph=True, autotune=not args.no_autotune)
+            cg_out = torch.empty(cg.out_elems(), dtype=torch.float32, device="cuda")
+            for _ in range(3):
+                cg.imchi(bands, out=cg_out, mu_out=mu)
+            cg.status()
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(seq_steps):
+                cg.imchi(bands, out=cg_out, mu_out=mu)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            cg.status()
+            cg_ms = e0.elapsed_time(e1) / seq_steps
+            plain["concurrent_graph"] = {"ms_per_step": cg_ms, "value": outputs_per_step / world / (cg_ms * 1e-3),
+                                         "speedup_persistent": cg_ms / step_ms}
+            cg.close()
+            del cg_out
     dom_kernel = (VARIANT_KERNELS[dom][variants[dom]] if dom in VARIANT_KERNELS else KERNEL_NAMES[dom])
     tc = None
     kk = None

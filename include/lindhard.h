@@ -145,7 +145,9 @@ typedef struct {
                                      solved: with more than 98 points per zone one more when
                                      gamma < 0.02 eV (a third multisection pass); with at most 98
                                      the whole solve runs in the set-up launch (two fewer); with
-                                     a caller-supplied A only the FFT passes                    */
+                                     a caller-supplied A only the FFT passes; in a
+                                     LINDHARD_PLAN_PERSISTENT plan the instance's set-up launches
+                                     only (the batch adds one persistent launch)               */
 } lindhard_sizes;
 
 /* Plan flag: also allocate the buffers of lindhard_imchi_backward (one more
@@ -178,6 +180,23 @@ typedef struct {
  * only (not with LINDHARD_PLAN_BACKWARD); LINDHARD_PLAN_AUTOTUNE tunes
  * nothing in this form.  Otherwise LINDHARD_EUNSUPPORTED. */
 #define LINDHARD_PLAN_ENERGY_DIRECT 16u
+/* Plan flag: run the five transform passes of every instance of the batch as
+ * one persistent launch (a batch scheduler): the CTAs claim (instance, pass,
+ * tile) items from a device queue ordered pass by pass, and an item waits,
+ * with a bounded wait, until its instance's previous pass has completed (a
+ * counter per instance and pass), so the passes of different instances
+ * overlap and no pass ends in a launch tail.  The chemical-potential solves
+ * and tables run first as ordinary launches, on the plan's streams.  Implies
+ * LINDHARD_PLAN_CONCURRENT (one workspace per instance); combines with
+ * LINDHARD_PLAN_GRAPH.  Every grid must be LINDHARD_FP32, LINDHARD_IMCHI,
+ * zones > 1, q_extent = N with N + N/2 in {192, 384, 768, 1536} (the momentum
+ * padding exactly one third) and an energy FFT of 128, 256 or 512 points;
+ * otherwise LINDHARD_EUNSUPPORTED.  Not with LINDHARD_PLAN_BACKWARD or
+ * LINDHARD_PLAN_ENERGY_DIRECT.  A call with a caller-supplied A runs the
+ * instances as ordinary launches instead.  A wait that runs out (the limit
+ * of lindhard_plan_set_wait_limit, 1 s by default) records LINDHARD_ETIMEOUT
+ * for lindhard_plan_status, and every CTA stops. */
+#define LINDHARD_PLAN_PERSISTENT 32u
 
 /* Builds a plan for `batch` instances with the given grids (host array).
  * Validates the grids, picks FFT lengths (the smallest supported length that
@@ -187,7 +206,7 @@ typedef struct {
  * Without LINDHARD_PLAN_CONCURRENT instances are computed one after another
  * and share one workspace sized for the largest.  flags: any of
  * LINDHARD_PLAN_BACKWARD, LINDHARD_PLAN_CONCURRENT, LINDHARD_PLAN_GRAPH,
- * LINDHARD_PLAN_AUTOTUNE, LINDHARD_PLAN_ENERGY_DIRECT.
+ * LINDHARD_PLAN_AUTOTUNE, LINDHARD_PLAN_ENERGY_DIRECT, LINDHARD_PLAN_PERSISTENT.
  * On success *out receives the plan. */
 lindhard_status lindhard_plan_create(const lindhard_grid *grids, int batch,
                                      unsigned flags, lindhard_plan **out);
@@ -335,6 +354,16 @@ lindhard_status lindhard_envelope_k0(lindhard_plan *plan, int index, const float
  * on `stream`; no synchronisation. */
 lindhard_status lindhard_kk_rpa(lindhard_plan *plan, int index, const float *imchi, float *re_out,
                                 float *rpa_out, double v0, int variant, void *stream);
+
+/* Limit of the bounded waits of the persistent batch launch
+ * (LINDHARD_PLAN_PERSISTENT), in nanoseconds of the GPU's global timer
+ * (default 1e9; 0 restores the default).  stall_instance >= 0 makes that
+ * instance's wait for its first pass unsatisfiable (it asks one more tile
+ * than the pass has), so that a test can make a wait run out on purpose: the
+ * call then ends early, its output is not valid, and lindhard_plan_status
+ * returns LINDHARD_ETIMEOUT; -1 for normal operation.  The plan's later
+ * calls use the values set last.  EINVAL for a plan without the flag. */
+lindhard_status lindhard_plan_set_wait_limit(lindhard_plan *plan, unsigned long long wait_ns, int stall_instance);
 
 /* Engine variants the plan runs for instance `index` (set by
  * LINDHARD_PLAN_AUTOTUNE, else the defaults): out[0], out[1] = forward and

@@ -18,36 +18,9 @@
 //     copy of the spectrum); a warp's stores of one line are contiguous.
 // Schedules (forward): 128 = 4.4.8, 256 = 4.8.8, 512 = 8.8.8; 16 values per
 // thread.  Output U1 [N*N lines][SP][2] as k_fwd_energy writes it.
-#include "kernels.cuh"
+#include "et_tiles.cuh"
 
 namespace lh {
-
-__host__ __device__ constexpr bool et_supported(int L) { return L == 128 || L == 256 || L == 512; }
-// Schedules: forward 128 = 4.4.8, 256 = 4.8.8, 512 = 8.8.8 (last radix 8);
-// inverse 128 = 8.4.4, 256 = 8.8.4, 512 = 8.8.8 (first radix 8)
-__host__ __device__ constexpr int et_radix(int L, int s, bool inv = false)
-{
-    return inv ? (s == 0 ? 8 : L == 512 ? 8 : L == 256 ? (s == 1 ? 8 : 4) : 4)
-               : (s == 2 ? 8 : L == 512 ? 8 : L == 256 ? (s == 0 ? 4 : 8) : 4);
-}
-__host__ __device__ constexpr int et_ns(int L, int s, bool inv = false)
-{
-    return s == 0 ? 1 : et_ns(L, s - 1, inv) * et_radix(L, s - 1, inv);
-}
-// per-stage twiddle tables [k][Rs], k < Ns, exp(-2 pi i k r / (Ns Rs)), of
-// stages 1 and 2 of each schedule: forward 128, 256, 512, then inverse
-__host__ __device__ constexpr int et_table_offset(int L, int s, bool inv = false)
-{
-    int o = 0;
-    for (int d = 0; d < 2; ++d)
-        for (int l = 128; l <= 512; l *= 2)
-            for (int st = 1; st <= 2; ++st) {
-                if (l == L && st == s && (d != 0) == inv) return o;
-                o += et_ns(l, st + 1, d != 0);
-            }
-    return o;
-}
-__host__ __device__ constexpr int et_twiddle_entries() { return et_table_offset(0, 0); }
 
 __global__ void k_et_twiddles(float2 *out)
 {
@@ -74,309 +47,25 @@ cudaError_t launch_et_twiddles(float2 *out, cudaStream_t s)
 size_t et_twiddle_bytes() { return (size_t)et_twiddle_entries() * sizeof(float2); }
 bool et_applies(const Geom &g, const Band &band) { return et_supported(g.PE) && !(band.kT > 0); }
 
-// Per warp: ET_LPW lines, LPI = 32 / TPL at a time (TPL = L/16 threads per
-// line); shared memory per warp LPI lines of L + L/16 values.
-constexpr int ET_LPW = 4, ET_WARPS = 8;
-template <int L>
-struct EtGeo {
-    static constexpr int TPL = L / 16, LPI = 32 / TPL, LP = L + L / 16;
-    static constexpr int R0 = et_radix(L, 0), R1 = et_radix(L, 1), R2 = 8;
-    static constexpr int N1 = et_ns(L, 1), N2 = et_ns(L, 2);
-    static constexpr int WARP_ELEMS = LPI * LP;
-    static_assert(R0 * R1 * R2 == L && 16 % R0 == 0 && 16 % R1 == 0, "schedule");
-    static_assert((L / R1) % 16 == 0 && (L / 8) % 16 == 0 && N2 % 16 == 0 && ET_LPW % LPI == 0,
-                  "compile-time padded offsets");
-};
-__host__ __device__ constexpr int et_pad(int n) { return n + n / 16; }
-
-// 1/x as the hardware approximation (relative error about 2^-23; x lies in
-// [gamma^2, 4 e_max^2 + gamma^2], away from zero, subnormals and overflow)
-__device__ __forceinline__ float et_rcp(float x)
-{
-    float r;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
-
-// FULL: n_eps == L (no energy padding; occupied rows n < L/2).  GEN: A is
-// generated (else read from the caller's A_in).
 template <int L, bool FULL, bool GEN>
 __global__ void __launch_bounds__(32 * ET_WARPS)
 k_fwd_energy_warp(Geom g, Band band, const AxisTab *__restrict__ axis, const float2 *__restrict__ eps,
                   const InstState *__restrict__ st, const float *__restrict__ A_in, float2 *__restrict__ U1,
                   const float2 *__restrict__ etw)
 {
-    using G = EtGeo<L>;
-    constexpr int TPL = G::TPL, LPI = G::LPI, LP = G::LP, R0 = G::R0, R1 = G::R1, R2 = G::R2;
-    constexpr int N1 = G::N1, N2 = G::N2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    LH_REQUIRE_SMEM(ET_WARPS * G::WARP_ELEMS, float2)
-    const int lane = (int)threadIdx.x % 32, warp = (int)threadIdx.x / 32;
-    const int sl = lane / TPL, u = lane % TPL;
-    float2 *sm = reinterpret_cast<float2 *>(smem_raw) + warp * G::WARP_ELEMS + sl * LP;
-    const long long nlines = (long long)g.N * g.N;
-    const long long line0 = ((long long)blockIdx.x * ET_WARPS + warp) * ET_LPW;
-    const float g2 = band.gam2;
-    const float2 *tw1 = etw + et_table_offset(L, 1), *tw2 = etw + et_table_offset(L, 2);
-
-    // band energy xi_p = e0(p) - mu (double-float) and |M(p)|^2 gamma / pi of
-    // the warp's lines (Eqs. 4-5), one lane per line; the amplitude carries
-    // the 1/2 of the a^ / b^ separation below (exact), and is 0 for lines
-    // past the end (their values come out 0, no branch per value)
-    float bx = 0.f, bl = 0.f, ba = 0.f;
-    if (GEN && lane < ET_LPW && line0 + lane < nlines) {
-        const long long line = line0 + lane;
-        const int ix = (int)(line / g.N), iy = (int)(line - (long long)ix * g.N);
-        band_point_f32(band, axis[ix], axis[iy], st, bx, bl, ba);
-        ba *= 0.5f;
-    }
-
-    for (int it = 0; it < ET_LPW; it += LPI) {
-        const long long line = line0 + it + sl;
-        const bool live = line < nlines;
-        const float xhi = __shfl_sync(0xffffffffu, bx, it + sl), xlo = __shfl_sync(0xffffffffu, bl, it + sl);
-        const float amp = __shfl_sync(0xffffffffu, ba, it + sl);
-
-        // stage 0: butterflies j = u + b TPL, rows j + r L/R0
-        float2 v[16];
-#pragma unroll
-        for (int b = 0; b < 16 / R0; ++b) {
-            const int j = u + b * TPL;
-#pragma unroll
-            for (int r = 0; r < R0; ++r) {
-                const int n = j + r * (L / R0);
-                float A;
-                if constexpr (GEN) {
-                    const float2 ej = __ldg(&eps[FULL ? n : min(n, g.n_eps - 1)]);
-                    const float e = (ej.x - xhi) + (ej.y - xlo);
-                    A = amp * et_rcp(fmaf(e, e, g2));
-                    if (!FULL && n >= g.n_eps) A = 0.f;
-                } else {
-                    A = (live && (FULL || n < g.n_eps)) ? 0.5f * A_in[line * g.n_eps + n] : 0.f;
-                }
-                // occupied (e_n < 0) -> real part, empty -> imaginary part
-                const bool occ = FULL ? (r < R0 / 2) : (2 * n + 1 < g.n_eps);
-                v[b * R0 + r] = occ ? make_float2(A, 0.f) : make_float2(0.f, A);
-            }
-            Dft<R0, false, float2>::run(v + b * R0);
-        }
-        // exchange 1 (outputs at j R0 + r) and stage 1: butterflies u + b TPL
-        __syncwarp();
-#pragma unroll
-        for (int b = 0; b < 16 / R0; ++b) {
-            const int base = (u + b * TPL) * R0;
-            const int pb = base + base / 16;
-#pragma unroll
-            for (int r = 0; r < R0; ++r) sm[pb + r] = v[b * R0 + r];
-        }
-        __syncwarp();
-#pragma unroll
-        for (int b = 0; b < 16 / R1; ++b) {
-            const int j = u + b * TPL;
-            const int pj = et_pad(j);
-#pragma unroll
-            for (int r = 0; r < R1; ++r) v[b * R1 + r] = sm[pj + et_pad(r * (L / R1))];
-            const float4 *w4 = reinterpret_cast<const float4 *>(tw1 + (j % N1) * R1);
-#pragma unroll
-            for (int h = 0; h < R1 / 2; ++h) {
-                const float4 q = __ldg(w4 + h);
-                if (h > 0) v[b * R1 + 2 * h] = cmul(v[b * R1 + 2 * h], make_float2(q.x, q.y));
-                v[b * R1 + 2 * h + 1] = cmul(v[b * R1 + 2 * h + 1], make_float2(q.z, q.w));
-            }
-            Dft<R1, false, float2>::run(v + b * R1);
-        }
-        // exchange 2 (outputs at (j / N1) N2 + j % N1 + r N1) and stage 2:
-        // butterflies u and L/8 - u (u = 0: 0 and L/16), so that Z(k) and
-        // Z(L - k) end in the same thread
-        __syncwarp();
-#pragma unroll
-        for (int b = 0; b < 16 / R1; ++b) {
-            const int j = u + b * TPL;
-            const int base = (j / N1) * N2 + j % N1;   // base % 16 = j % N1 < N1
-            const int pb = base + base / 16;
-#pragma unroll
-            for (int r = 0; r < R1; ++r) sm[pb + r * N1 + (r * N1) / 16] = v[b * R1 + r];
-        }
-        __syncwarp();
-        const int j2[2] = {u, u == 0 ? TPL : L / 8 - u};
-#pragma unroll
-        for (int b = 0; b < 2; ++b) {
-            const int pj = et_pad(j2[b]);
-#pragma unroll
-            for (int r = 0; r < R2; ++r) v[b * R2 + r] = sm[pj + et_pad(r * (L / 8))];
-            const float4 *w4 = reinterpret_cast<const float4 *>(tw2 + j2[b] * R2);   // j < N2
-#pragma unroll
-            for (int h = 0; h < R2 / 2; ++h) {
-                const float4 q = __ldg(w4 + h);
-                if (h > 0) v[b * R2 + 2 * h] = cmul(v[b * R2 + 2 * h], make_float2(q.x, q.y));
-                v[b * R2 + 2 * h + 1] = cmul(v[b * R2 + 2 * h + 1], make_float2(q.z, q.w));
-            }
-            Dft<R2, false, float2>::run(v + b * R2);
-        }
-
-        // Z(j + r L/8) in v[b 8 + r]; the partner Z(L - k) of (j2[0], r) is
-        // (j2[1], 7 - r) for u > 0; of (0, r) it is (0, 8 - r), of (L/16, r)
-        // it is (L/16, 7 - r)
-        if (live) {
-            float2 *row = U1 + line * (2LL * g.SP);
-            // a^ = (Z(k) + conj Z(-k)) / 2, b^ = (Z(k) - conj Z(-k)) / 2i, the
-            // 1/2 already in Z (the amplitude)
-            auto put = [&](int k, float2 zk, float2 zm) {
-                gst2(row + 2 * k, make_float2(zk.x + zm.x, zk.y - zm.y), make_float2(zk.y + zm.y, zm.x - zk.x));
-            };
-            const bool u0 = u == 0;
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                put(j2[0] + r * (L / 8), v[r], u0 ? v[(8 - r) & 7] : v[8 + 7 - r]);
-                put(j2[1] + r * (L / 8), v[8 + r], u0 ? v[8 + 7 - r] : v[7 - r]);
-            }
-            if (u0) put(L / 2, v[4], v[4]);
-        }
-        __syncwarp();   // the next line's exchange overwrites this one's
-    }
+    LH_REQUIRE_SMEM(ET_WARPS * EtGeo<L>::WARP_ELEMS, float2)
+    energy_fwd_warp_tile<L, FULL, GEN>(g, band, axis, eps, st, A_in, U1, etw, reinterpret_cast<float2 *>(smem_raw),
+                                       blockIdx.x);
 }
 
-// ---------------------------------------------------------------------------
-// Inverse energy pass, one warp per pair of output lines (the transform of
-// k_inv_energy): for the lines (2f, 2f + 1) of U4 [Q^2][SP], W(k) = X1(k) +
-// i X2(k) over k in [0, L), with X(k) = conj X(L - k) above L/2 (the product
-// spectrum of the real correlation is Hermitian in the energy frequency), one
-// complex inverse FFT, Re w -> line 2f, Im w -> line 2f + 1, the transfers
-// m < n_omega, times the Eq. 9 prefactor with the FFT normalisation.  In the
-// first stage a thread owns butterflies j and L/8 - j: it loads X(k) once for
-// k <= L/2 and forms both W(k) and W(L - k) = conj X1(k) + i conj X2(k).
-// HALF: n_omega == L/2 (the outputs of the last stage's first R2/2 rows).
 template <int L, bool HALF>
 __global__ void __launch_bounds__(32 * ET_WARPS)
 k_inv_energy_warp(Geom g, const float2 *__restrict__ U4, float *__restrict__ out, const float2 *__restrict__ etw)
 {
-    constexpr int TPL = L / 16, LPI = 32 / TPL, LP = L + L / 16;
-    constexpr int R0 = et_radix(L, 0, true), R1 = et_radix(L, 1, true), R2 = et_radix(L, 2, true);
-    constexpr int N1 = et_ns(L, 1, true), N2 = et_ns(L, 2, true);
-    constexpr int H = L / 2 + 1, SP = (H + 7) / 8 * 8;
-    static_assert(R0 == 8 && R0 * R1 * R2 == L && 16 % R1 == 0 && 16 % R2 == 0, "schedule");
-    static_assert((L / R1) % 16 == 0 && (L / R2) % 16 == 0 && ET_LPW % LPI == 0, "compile-time padded offsets");
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    LH_REQUIRE_SMEM(ET_WARPS * LPI * LP, float2)
-    const int lane = (int)threadIdx.x % 32, warp = (int)threadIdx.x / 32;
-    const int sl = lane / TPL, u = lane % TPL;
-    float2 *sm = reinterpret_cast<float2 *>(smem_raw) + (warp * LPI + sl) * LP;
-    const long long npairs = (long long)g.Q * g.Q / 2;
-    const long long pair0 = ((long long)blockIdx.x * ET_WARPS + warp) * ET_LPW;
-    const float2 *tw1 = etw + et_table_offset(L, 1, true), *tw2 = etw + et_table_offset(L, 2, true);
-    const float sc = (float)g.scale;
-    const int j0[2] = {u, u == 0 ? TPL : L / 8 - u};
-
-    for (int it = 0; it < ET_LPW; it += LPI) {
-        const long long f = pair0 + it + sl;
-        const bool live = f < npairs;
-        const float2 *row1 = U4 + (live ? 2 * f : 0) * SP, *row2 = row1 + SP;
-        // stage 0: rows j + r L/8 of butterflies j0[0] and j0[1]; the rows
-        // above L/2 of one are the conjugate mirrors of the other's
-        float2 v[16];
-        const float2 zero = make_float2(0.f, 0.f);
-        auto w_of = [](float2 x1, float2 x2) { return make_float2(x1.x - x2.y, x1.y + x2.x); };       // X1 + i X2
-        auto w_conj = [](float2 x1, float2 x2) { return make_float2(x1.x + x2.y, x2.x - x1.y); };     // conj X1 + i conj X2
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const float2 a1 = live ? __ldg(row1 + j0[0] + r * (L / 8)) : zero;
-            const float2 a2 = live ? __ldg(row2 + j0[0] + r * (L / 8)) : zero;
-            const float2 b1 = live ? __ldg(row1 + j0[1] + r * (L / 8)) : zero;
-            const float2 b2 = live ? __ldg(row2 + j0[1] + r * (L / 8)) : zero;
-            v[r] = w_of(a1, a2);
-            v[8 + r] = w_of(b1, b2);
-            // u > 0: L - (j0[0] + r L/8) = j0[1] + (7 - r) L/8 and the other way round
-            v[7 - r] = w_conj(b1, b2);
-            v[8 + 7 - r] = w_conj(a1, a2);
-        }
-        if (u == 0) {
-            // j0[0] = 0: rows r L/8 mirror (8 - r) L/8; row L/2 is its own mirror
-            const float2 c1 = live ? __ldg(row1 + L / 2) : zero, c2 = live ? __ldg(row2 + L / 2) : zero;
-            v[4] = w_of(c1, c2);
-#pragma unroll
-            for (int r = 1; r < 4; ++r) {
-                const float2 x1 = live ? __ldg(row1 + r * (L / 8)) : zero, x2 = live ? __ldg(row2 + r * (L / 8)) : zero;
-                v[8 - r] = w_conj(x1, x2);
-            }
-            // j0[1] = L/16: rows L/16 + r L/8 mirror L/16 + (7 - r) L/8
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const float2 x1 = live ? __ldg(row1 + TPL + r * (L / 8)) : zero;
-                const float2 x2 = live ? __ldg(row2 + TPL + r * (L / 8)) : zero;
-                v[8 + 7 - r] = w_conj(x1, x2);
-            }
-        }
-        Dft<8, true, float2>::run(v);
-        Dft<8, true, float2>::run(v + 8);
-        // exchange 1 (outputs at j 8 + r) and stage 1: butterflies u + b TPL
-        __syncwarp();
-#pragma unroll
-        for (int b = 0; b < 2; ++b) {
-            const int base = j0[b] * 8;
-            const int pb = base + base / 16;
-#pragma unroll
-            for (int r = 0; r < 8; ++r) sm[pb + r] = v[b * 8 + r];
-        }
-        __syncwarp();
-#pragma unroll
-        for (int b = 0; b < 16 / R1; ++b) {
-            const int j = u + b * TPL;
-            const int pj = et_pad(j);
-#pragma unroll
-            for (int r = 0; r < R1; ++r) v[b * R1 + r] = sm[pj + et_pad(r * (L / R1))];
-            const float4 *w4 = reinterpret_cast<const float4 *>(tw1 + (j % N1) * R1);
-#pragma unroll
-            for (int h = 0; h < R1 / 2; ++h) {
-                const float4 q = __ldg(w4 + h);
-                if (h > 0) v[b * R1 + 2 * h] = cmulc(v[b * R1 + 2 * h], make_float2(q.x, q.y));
-                v[b * R1 + 2 * h + 1] = cmulc(v[b * R1 + 2 * h + 1], make_float2(q.z, q.w));
-            }
-            Dft<R1, true, float2>::run(v + b * R1);
-        }
-        // exchange 2 (outputs at (j / N1) N2 + j % N1 + r N1) and stage 2
-        __syncwarp();
-#pragma unroll
-        for (int b = 0; b < 16 / R1; ++b) {
-            const int j = u + b * TPL;
-            const int base = (j / N1) * N2 + j % N1;   // base % 16 = j % 8 < 8
-            const int pb = base + base / 16;
-#pragma unroll
-            for (int r = 0; r < R1; ++r) sm[pb + r * N1 + (r * N1) / 16] = v[b * R1 + r];
-        }
-        __syncwarp();
-#pragma unroll
-        for (int b = 0; b < 16 / R2; ++b) {
-            const int j = u + b * TPL;
-            const int pj = et_pad(j);
-#pragma unroll
-            for (int r = 0; r < R2; ++r) v[b * R2 + r] = sm[pj + et_pad(r * (L / R2))];
-            const float4 *w4 = reinterpret_cast<const float4 *>(tw2 + j * R2);   // j < N2
-#pragma unroll
-            for (int h = 0; h < R2 / 2; ++h) {
-                const float4 q = __ldg(w4 + h);
-                if (h > 0) v[b * R2 + 2 * h] = cmulc(v[b * R2 + 2 * h], make_float2(q.x, q.y));
-                v[b * R2 + 2 * h + 1] = cmulc(v[b * R2 + 2 * h + 1], make_float2(q.z, q.w));
-            }
-            Dft<R2, true, float2>::run(v + b * R2);
-        }
-        // outputs m = j + r L/R2; Re -> line 2f, Im -> line 2f + 1
-        if (live) {
-            float *o1 = out + 2 * f * g.n_omega, *o2 = o1 + g.n_omega;
-#pragma unroll
-            for (int b = 0; b < 16 / R2; ++b) {
-                const int j = u + b * TPL;
-#pragma unroll
-                for (int r = 0; r < (HALF ? R2 / 2 : R2); ++r) {
-                    const int m = j + r * (L / R2);
-                    if (HALF || m < g.n_omega) {
-                        o1[m] = sc * v[b * R2 + r].x;
-                        o2[m] = sc * v[b * R2 + r].y;
-                    }
-                }
-            }
-        }
-        __syncwarp();   // the next pair's exchange overwrites this one's
-    }
+    LH_REQUIRE_SMEM(et_inv_smem_elems<L>(), float2)
+    inv_energy_warp_tile<L, HALF, false>(g, U4, out, etw, reinterpret_cast<float2 *>(smem_raw), blockIdx.x);
 }
 
 template <int L>

@@ -12,18 +12,9 @@
 // The same transforms as k_fwd_y2 / k_x_product / k_inv_y2 (same layouts),
 // with the zero rows neither loaded nor transformed in the first forward
 // stage and the unkept lags not formed in the last inverse stage.
-#include "fft_pruned.cuh"
-#include "kernels.cuh"
+#include "pr_tiles.cuh"
 
 namespace lh {
-
-// Tiles: A = CW 8 (128-byte row segments of the paired layouts), B = CW 4;
-// both 24 values per thread per operand.
-template <int L, int CW>
-struct PrCfg {
-    static constexpr int C = CW, T = CW * L / 24;
-    static constexpr int MINB = 65536 / (T * 128) < 1 ? 1 : 65536 / (T * 128);   // <= 128 registers
-};
 
 __global__ void k_pr_twiddles(float2 *out)
 {
@@ -54,145 +45,34 @@ cudaError_t launch_pr_twiddles(float2 *out, cudaStream_t s)
 }
 size_t pr_twiddle_bytes() { return (size_t)pr_twiddle_entries() * sizeof(float2); }
 
-// ---------------------------------------------------------------------------
 template <int L, typename Cfg>
 __global__ void __launch_bounds__(Cfg::T, Cfg::MINB)
 k_fwd_y_pr(Geom g, const float2 *__restrict__ U1, float2 *__restrict__ U2, const float2 *__restrict__ ptw)
 {
-    constexpr int CP = Cfg::C;
-    using E = PrEng<L, CP, Cfg::T, false, 2, true, false>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2 *sm = reinterpret_cast<float2 *>(smem_raw);
-    LH_REQUIRE_SMEM(E::SMEM_ELEMS, float2)
-
-    const int W = 2 * g.SP;                           // row width (a^ and b^)
-    const int ix = blockIdx.y;
-    const int c = blockIdx.x * (2 * CP) + 2 * E::col();  // (c, c + 1) = (a^, b^) of one frequency
-    const bool valid = c < W && ab_col_valid(c, g.H);
-    const float2 *src = U1 + (long long)ix * g.N * W + c;
-    float2 *dst = U2 + (long long)ix * g.xs2 + c;
-    const float2 zero = make_float2(0.f, 0.f);
-
-    float2 va[E::VPT], vb[E::VPT];
-#pragma unroll
-    for (int b = 0; b < E::VPT / 24; ++b) {
-        const float2 *p = src + (long long)E::jb(b) * W;
-#pragma unroll
-        for (int r = 0; r < 16; ++r) {   // rows jb + r L/24 < N; rows >= N are the padding
-            if (valid) gld2(p + (long long)(r * (L / 24)) * W, va[24 * b + r], vb[24 * b + r]);
-            else { va[24 * b + r] = zero; vb[24 * b + r] = zero; }
-        }
-    }
-    E::run(va, vb, sm, ptw);
-    if (valid) {
-#pragma unroll
-        for (int b = 0; b < E::VPT / E::RL; ++b) {
-            float2 *p = dst + (long long)E::jb(b) * W;
-#pragma unroll
-            for (int r = 0; r < E::RL; ++r) gst2(p + (long long)(r * (L / E::RL)) * W, va[b * E::RL + r], vb[b * E::RL + r]);
-        }
-    }
-}
-
-// Stores of the last inverse stage: outputs r < 8 are lags j + r L/24 + L/3,
-// outputs r >= 16 lags j + (r - 16) L/24 (kept |s| <= L/3 = Q/2).
-template <int L, typename E, typename St>
-__device__ __forceinline__ void pr_store_lags(const float2 *v, St &&store)
-{
-#pragma unroll
-    for (int b = 0; b < E::VPT / 24; ++b) {
-        const int j = E::jb(b);
-#pragma unroll
-        for (int r = 0; r < 8; ++r) {
-            store(j + r * (L / 24) + L / 3, v[24 * b + r]);
-            store(j + r * (L / 24), v[24 * b + 16 + r]);
-        }
-    }
+    LH_REQUIRE_SMEM((PrEng<L, Cfg::C, Cfg::T, false, 2, true, false>::SMEM_ELEMS), float2)
+    fwd_y_pr_tile<L, Cfg::C, Cfg::T, false>(g, U1, U2, ptw, reinterpret_cast<float2 *>(smem_raw), blockIdx.x,
+                                            blockIdx.y);
 }
 
 template <int L, typename Cfg, bool ODD>
 __global__ void __launch_bounds__(Cfg::T, Cfg::MINB)
 k_x_product_pr(Geom g, const float2 *__restrict__ U2, float2 *__restrict__ U3, const float2 *__restrict__ ptw)
 {
-    constexpr int C = Cfg::C;
-    using EF = PrEng<L, C, Cfg::T, false, 2, true, false>;
-    using EI = PrEng<L, C, Cfg::T, true, 1, false, true>;
-    static_assert(EF::RL == EI::R0 && EF::VPT == EI::VPT, "last forward and first inverse stages must coincide");
-    constexpr int SMEM = EF::SMEM_ELEMS > EI::SMEM_ELEMS ? EF::SMEM_ELEMS : EI::SMEM_ELEMS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2 *sm = reinterpret_cast<float2 *>(smem_raw);
-    LH_REQUIRE_SMEM(SMEM, float2)
-
-    const int ky = blockIdx.y;
-    const int c = blockIdx.x * C + EF::col();
-    const bool valid = c < g.H;
-    const long long rs = g.xs2;                        // U2 stride between i_x rows
-    const float2 *src = U2 + (long long)ky * (2 * g.SP) + 2 * c;   // (a^, b^) of frequency c
-    const float2 zero = make_float2(0.f, 0.f);
-
-    float2 va[EF::VPT], vb[EF::VPT];
-#pragma unroll
-    for (int b = 0; b < EF::VPT / 24; ++b) {
-        const float2 *p = src + (long long)EF::jb(b) * rs;
-#pragma unroll
-        for (int r = 0; r < 16; ++r) {
-            if (valid) gld2(p + (long long)(r * (L / 24)) * rs, va[24 * b + r], vb[24 * b + r]);
-            else { va[24 * b + r] = zero; vb[24 * b + r] = zero; }
-        }
-    }
-    EF::run(va, vb, sm, ptw);
-    // conj(a^) b^: transform of C(q) = sum_p a(p) b(p + q); for Im chi_T its
-    // odd part, P - conj(P) = 2 i Im P
-#pragma unroll
-    for (int i = 0; i < EF::VPT; ++i) va[i] = odd_part(cmulc(vb[i], va[i]), ODD);
-    EI::run(va, va, sm, ptw);
-    if (valid) {
-        float2 *dst = U3 + (long long)ky * g.SP + c;
-        const long long os = g.xs3;
-        pr_store_lags<L, EI>(va, [&](int l, float2 x) { dst[(long long)l * os] = x; });
-    }
+    LH_REQUIRE_SMEM((PrProduct<L, Cfg::C, Cfg::T>::SMEM_ELEMS), float2)
+    x_product_pr_tile<L, Cfg::C, Cfg::T, ODD, false>(g, U2, U3, ptw, reinterpret_cast<float2 *>(smem_raw),
+                                                     blockIdx.x, blockIdx.y);
 }
 
 template <int L, typename Cfg>
 __global__ void __launch_bounds__(Cfg::T, Cfg::MINB)
 k_inv_y_pr(Geom g, const float2 *__restrict__ U3, float2 *__restrict__ U4, const float2 *__restrict__ ptw)
 {
-    constexpr int CP = Cfg::C;
-    using E = PrEng<L, CP, Cfg::T, true, 2, false, true>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2 *sm = reinterpret_cast<float2 *>(smem_raw);
-    LH_REQUIRE_SMEM(E::SMEM_ELEMS, float2)
-
-    const int lx = blockIdx.y;
-    const int c = blockIdx.x * (2 * CP) + 2 * E::col();
-    const bool valid = c < g.H;                        // c + 1 < SP: the pair stays in the row
-    const float2 *src = U3 + (long long)lx * g.xs3 + c;
-    float2 *dst = U4 + (long long)lx * g.Q * g.SP + c;
-    const float2 zero = make_float2(0.f, 0.f);
-
-    float2 va[E::VPT], vb[E::VPT];
-#pragma unroll
-    for (int b = 0; b < E::VPT / E::R0; ++b) {
-        const float2 *p = src + (long long)E::jb(b) * g.SP;
-#pragma unroll
-        for (int r = 0; r < E::R0; ++r) {
-            if (valid) gld2(p + (long long)(r * (L / E::R0)) * g.SP, va[b * E::R0 + r], vb[b * E::R0 + r]);
-            else { va[b * E::R0 + r] = zero; vb[b * E::R0 + r] = zero; }
-        }
-    }
-    E::run(va, vb, sm, ptw);
-    if (valid) {
-        const int sp = g.SP;
-#pragma unroll
-        for (int b = 0; b < E::VPT / 24; ++b) {
-            const int j = E::jb(b);
-#pragma unroll
-            for (int r = 0; r < 8; ++r) {
-                gst2(dst + (long long)(j + r * (L / 24) + L / 3) * sp, va[24 * b + r], vb[24 * b + r]);
-                gst2(dst + (long long)(j + r * (L / 24)) * sp, va[24 * b + 16 + r], vb[24 * b + 16 + r]);
-            }
-        }
-    }
+    LH_REQUIRE_SMEM((PrEng<L, Cfg::C, Cfg::T, true, 2, false, true>::SMEM_ELEMS), float2)
+    inv_y_pr_tile<L, Cfg::C, Cfg::T, false>(g, U3, U4, ptw, reinterpret_cast<float2 *>(smem_raw), blockIdx.x,
+                                            blockIdx.y);
 }
 
 // ---------------------------------------------------------------------------

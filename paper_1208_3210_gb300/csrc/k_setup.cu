@@ -433,8 +433,9 @@ __device__ void mu_solve_one_cta(const Geom &g, const Band &band, const MuConst 
 // and the first of them records the given mu.
 __global__ void __launch_bounds__(MU_THREADS, 2)
 k_setup(Geom g, Band band, AxisTab *axis, float2 *eps32, double *eps64, InstState *st, double *acc,
-        unsigned *counter, unsigned *status, double *mu_out, MuConst mc, int G)
+        unsigned *counter, unsigned *status, double *mu_out, MuConst mc, int G, Band *band_out)
 {
+    if (band_out && blockIdx.x == 0 && threadIdx.x == 0) *band_out = band;   // the call's band, for later launches
     if ((int)blockIdx.x >= G) {
         const int tb = blockIdx.x - G;
         if (!band.solve_mu && tb == 0 && threadIdx.x == 0) {
@@ -650,16 +651,23 @@ cudaError_t launch_twiddles(int len, float2 *tw32, double2 *tw64, cudaStream_t s
 
 // Tables plus the first chemical-potential launch (multisection pass 0, or
 // the given mu).
-cudaError_t launch_setup(const Geom &g, const Band &band, AxisTab *axis, float2 *eps32, double *eps64,
-                         InstState *st, double *acc, unsigned *bar, unsigned *status, double *mu_out, int G,
-                         cudaStream_t s)
+// band_out (device, or null): receives the call's band for later launches.
+cudaError_t launch_setup_band(const Geom &g, const Band &band, AxisTab *axis, float2 *eps32, double *eps64,
+                              InstState *st, double *acc, unsigned *bar, unsigned *status, double *mu_out, int G,
+                              Band *band_out, cudaStream_t s)
 {
     const int ntab = g.N > g.n_eps ? g.N : g.n_eps;
     const int GT = (ntab + MU_TAB_THREADS - 1) / MU_TAB_THREADS;
     const int Gs = band.solve_mu ? (mu_single(g) ? 1 : G) : 0;
     k_setup<<<Gs + GT, MU_THREADS, 0, s>>>(g, band, axis, eps32, eps64, st, acc, bar, status, mu_out,
-                                           mu_const(g, band, G), Gs);
+                                           mu_const(g, band, G), Gs, band_out);
     return cudaGetLastError();
+}
+cudaError_t launch_setup(const Geom &g, const Band &band, AxisTab *axis, float2 *eps32, double *eps64,
+                         InstState *st, double *acc, unsigned *bar, unsigned *status, double *mu_out, int G,
+                         cudaStream_t s)
+{
+    return launch_setup_band(g, band, axis, eps32, eps64, st, acc, bar, status, mu_out, G, nullptr, s);
 }
 
 // Whether the chemical potential is solved inside the set-up launch.

@@ -59,6 +59,22 @@ cudaError_t launch_pr_twiddles(float2 *out, cudaStream_t s);
 bool pr_fwd_applies(const Geom &g);
 bool pr_inv_applies(const Geom &g);
 bool et_inv_applies(const Geom &g);
+// persistent batch launch (k_persist.cu)
+bool ps_supported(const Geom &g);
+size_t ps_inst_bytes();
+size_t ps_seg_bytes();
+int ps_grid(int num_sms, int smem_elems);
+int ps_inst_smem_elems(const Geom &g);
+int ps_pass_tiles(const Geom &g, int pass);
+void ps_fill_inst(void *dst, const Geom &g, void *X, void *Y, const AxisTab *axis, const void *eps,
+                  const InstState *st, const Band *band, long long out_off);
+void ps_fill_seg(void *dst, int inst, int pass, int start, int ntiles);
+cudaError_t launch_persistent(const void *insts, const void *segs, int nsegs, int total, unsigned *head,
+                              unsigned *done, unsigned *status, float *out, const float2 *ptw, const float2 *etw,
+                              unsigned long long wait_ns, int stall_inst, int smem_elems, int grid, cudaStream_t s);
+cudaError_t launch_setup_band(const Geom &g, const Band &band, AxisTab *axis, float2 *eps32, double *eps64,
+                              InstState *st, double *acc, unsigned *bar, unsigned *status, double *mu_out, int G,
+                              Band *band_out, cudaStream_t s);
 cudaError_t launch_tc_mats(void *buf, cudaStream_t s);
 cudaError_t launch_inv_y(const Geom &g, const Work<double> &w, cudaStream_t s, int variant);
 cudaError_t launch_inv_energy(const Geom &g, const Work<float> &w, float *out, cudaStream_t s, int variant);
@@ -147,6 +163,14 @@ struct lindhard_plan {
     bool concurrent = false;     // LINDHARD_PLAN_CONCURRENT
     bool graph = false;          // LINDHARD_PLAN_GRAPH
     bool direct = false;         // LINDHARD_PLAN_ENERGY_DIRECT
+    // LINDHARD_PLAN_PERSISTENT: per-instance entries, queue segments,
+    // per-instance per-pass completion counters (+ the queue head) and the
+    // calls' bands, in the workspace; the wait limit and the test stall
+    bool persistent = false;
+    size_t off_ps_inst = 0, off_ps_seg = 0, off_ps_cnt = 0, off_ps_band = 0;
+    int ps_nsegs = 0, ps_total = 0, ps_grid = 0, ps_smem = 0;
+    unsigned long long wait_ns = 1000000000ull;
+    int stall_inst = -1;
     // concurrent execution: instances on plan-owned streams, forked from and
     // joined back into the caller's stream with events
     std::vector<cudaStream_t> streams;
@@ -427,7 +451,7 @@ extern "C" lindhard_status lindhard_plan_create(const lindhard_grid *grids, int 
 {
     if (!grids || !out || batch < 1) return fail(LINDHARD_EINVAL, "grids/out must be non-NULL and batch >= 1");
     const unsigned known = LINDHARD_PLAN_BACKWARD | LINDHARD_PLAN_CONCURRENT | LINDHARD_PLAN_GRAPH |
-                           LINDHARD_PLAN_AUTOTUNE | LINDHARD_PLAN_ENERGY_DIRECT;
+                           LINDHARD_PLAN_AUTOTUNE | LINDHARD_PLAN_ENERGY_DIRECT | LINDHARD_PLAN_PERSISTENT;
     if (flags & ~known) return fail(LINDHARD_EINVAL, "unknown plan flags");
     *out = nullptr;
     lindhard_plan *p = new (std::nothrow) lindhard_plan;
@@ -437,8 +461,14 @@ extern "C" lindhard_status lindhard_plan_create(const lindhard_grid *grids, int 
     p->precision.resize(batch);
     p->backward = (flags & LINDHARD_PLAN_BACKWARD) != 0;
     p->graph = (flags & LINDHARD_PLAN_GRAPH) != 0;
-    p->concurrent = p->graph || (flags & LINDHARD_PLAN_CONCURRENT) != 0;
+    p->persistent = (flags & LINDHARD_PLAN_PERSISTENT) != 0;
+    p->concurrent = p->graph || p->persistent || (flags & LINDHARD_PLAN_CONCURRENT) != 0;
     p->direct = (flags & LINDHARD_PLAN_ENERGY_DIRECT) != 0;
+    if (p->persistent && (p->backward || p->direct)) {
+        delete p;
+        return fail(LINDHARD_EUNSUPPORTED, "the persistent batch launch is forward only, in the 3D form "
+                                           "(not with LINDHARD_PLAN_BACKWARD or LINDHARD_PLAN_ENERGY_DIRECT)");
+    }
     if (p->direct && p->backward) {
         delete p;
         return fail(LINDHARD_EUNSUPPORTED, "the energy-direct form is forward only (no LINDHARD_PLAN_BACKWARD)");
@@ -459,6 +489,12 @@ extern "C" lindhard_status lindhard_plan_create(const lindhard_grid *grids, int 
             delete p;
             return fail(LINDHARD_EUNSUPPORTED, "the energy-direct form takes LINDHARD_FP32, LINDHARD_IMCHI grids "
                                                "with n_eps <= 1024 and n_omega <= 512");
+        }
+        if (p->persistent && (p->precision[i] != LINDHARD_FP32 || !ps_supported(p->geoms[i]))) {
+            delete p;
+            return fail(LINDHARD_EUNSUPPORTED, "the persistent batch launch takes LINDHARD_FP32, LINDHARD_IMCHI "
+                                               "grids with zones > 1, q_extent = N, N + N/2 in {192, 384, 768, "
+                                               "1536} and an energy FFT of 128, 256 or 512 points");
         }
         maxLen = std::max(maxLen, std::max(p->geoms[i].P, p->geoms[i].PE));
         maxNpts = std::max(maxNpts, p->geoms[i].npz * p->geoms[i].npz);
@@ -507,6 +543,12 @@ extern "C" lindhard_status lindhard_plan_create(const lindhard_grid *grids, int 
     // LINDHARD_SPLITBF16_TC grid only)
     if (std::count(p->precision.begin(), p->precision.end(), (int)LINDHARD_SPLITBF16_TC) > 0) {
         p->off_tc = o; o = align_up(o + tc_mats_bytes());
+    }
+    if (p->persistent) {
+        p->off_ps_inst = o; o = align_up(o + ps_inst_bytes() * batch);
+        p->off_ps_seg = o; o = align_up(o + ps_seg_bytes() * 5 * batch);
+        p->off_ps_cnt = o; o = align_up(o + sizeof(unsigned) * (5 * batch + 1));
+        p->off_ps_band = o; o = align_up(o + sizeof(Band) * batch);
     }
     p->off_kk.assign(batch, 0);
     for (int i = 0; i < batch; ++i)
@@ -575,6 +617,31 @@ extern "C" lindhard_status lindhard_plan_create(const lindhard_grid *grids, int 
     p->xvar.assign(batch, 0);
     p->evar.assign(batch, 0);
     if (e == cudaSuccess && (flags & LINDHARD_PLAN_AUTOTUNE) && !p->direct) e = autotune(p);
+    if (e == cudaSuccess && p->persistent) {
+        // the instances' entries and the queue: every tile of pass 0 of every
+        // instance, then pass 1, ... (each dependency lies earlier in the queue)
+        std::vector<unsigned char> hi(ps_inst_bytes() * batch), hs(ps_seg_bytes() * 5 * batch);
+        long long o_off = 0;
+        for (int i = 0; i < batch; ++i) {
+            Work<float> w = work_of<float>(p, i);
+            ps_fill_inst(hi.data() + ps_inst_bytes() * i, p->geoms[i], w.X, w.Y, w.axis, w.eps, w.state,
+                         (const Band *)(p->ws + p->off_ps_band) + i, o_off);
+            o_off += (long long)p->geoms[i].Q * p->geoms[i].Q * p->geoms[i].n_omega;
+        }
+        int start = 0, k = 0;
+        for (int pass = 0; pass < 5; ++pass)
+            for (int i = 0; i < batch; ++i) {
+                const int n = ps_pass_tiles(p->geoms[i], pass);
+                ps_fill_seg(hs.data() + ps_seg_bytes() * k++, i, pass, start, n);
+                start += n;
+            }
+        p->ps_nsegs = k;
+        p->ps_total = start;
+        for (int i = 0; i < batch; ++i) p->ps_smem = std::max(p->ps_smem, ps_inst_smem_elems(p->geoms[i]));
+        p->ps_grid = ps_grid(p->num_sms, p->ps_smem);
+        e = cudaMemcpy(p->ws + p->off_ps_inst, hi.data(), hi.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(p->ws + p->off_ps_seg, hs.data(), hs.size(), cudaMemcpyHostToDevice);
+    }
     if (e != cudaSuccess) {
         lindhard_plan_destroy(p);
         return cuda_fail(e, "plan set-up");
@@ -607,6 +674,9 @@ extern "C" lindhard_status lindhard_plan_sizes(const lindhard_plan *p, int index
     // set-up (tables + multisection pass 0), multisection pass 1, Halley step, 5 FFT passes;
     // zones of at most 98 points solve mu inside the set-up launch
     out->kernels_forward = mu_solve_in_setup(g) ? 6 : 8;
+    // persistent plans: the instance's set-up launches (the batch's passes
+    // are one further launch of the plan)
+    if (p->persistent) out->kernels_forward = mu_solve_in_setup(g) ? 1 : 3;
     if (p->direct) {
         // planes, p_y, p_x, correlation, k_x inverse, k_y inverse, output; the
         // same write-once read-once count over the direct form's intermediates
@@ -765,10 +835,41 @@ static lindhard_status bands_of(lindhard_plan *p, const lindhard_band *bands, bo
 
 // Enqueues the forward sequence of every instance (per-pass timing only in
 // sequential plans).
+// The persistent batch launch: each instance's set-up and chemical-potential
+// launches on the plan's streams (which also store the call's band for the
+// launch), then the completion counters cleared and the one launch of every
+// instance's five passes.
+static cudaError_t enqueue_persistent(lindhard_plan *p, const std::vector<Band> &bs, float *out, double *mu_out,
+                                      cudaStream_t s0)
+{
+    cudaError_t e = fork_begin(p, s0);
+    for (int i = 0; i < p->batch && e == cudaSuccess; ++i) {
+        const Geom &g = p->geoms[i];
+        cudaStream_t s = inst_stream(p, i, s0);
+        Work<float> w = work_of<float>(p, i);
+        e = launch_setup_band(g, bs[i], w.axis, (float2 *)w.eps, nullptr, w.state, w.mu_acc, w.barrier, w.status,
+                              mu_out ? mu_out + i : nullptr, p->mu_G, (Band *)(p->ws + p->off_ps_band) + i, s);
+        if (e == cudaSuccess)
+            e = launch_solve_mu(g, bs[i], w.axis, w.state, w.mu_acc, w.barrier, w.status, mu_out ? mu_out + i : nullptr,
+                                p->mu_G, s);
+    }
+    if (e == cudaSuccess) e = fork_end(p, s0);
+    unsigned *cnt = (unsigned *)(p->ws + p->off_ps_cnt);
+    if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, sizeof(unsigned) * (5 * p->batch + 1), s0);
+    if (e == cudaSuccess)
+        e = launch_persistent(p->ws + p->off_ps_inst, p->ws + p->off_ps_seg, p->ps_nsegs, p->ps_total,
+                              cnt + 5 * p->batch, cnt, (unsigned *)(p->ws + p->off_status), out,
+                              (const float2 *)(p->ws + p->off_prtw), (const float2 *)(p->ws + p->off_etw), p->wait_ns,
+                              p->stall_inst, p->ps_smem, p->ps_grid, s0);
+    return e;
+}
+
 template <typename Real>
 static cudaError_t enqueue_forward(lindhard_plan *p, const std::vector<Band> &bs, const Real *A_in, Real *out,
                                    double *mu_out, cudaStream_t s0)
 {
+    if constexpr (sizeof(Real) == 4)
+        if (p->persistent && A_in == nullptr) return enqueue_persistent(p, bs, out, mu_out, s0);
     cudaError_t e = fork_begin(p, s0);
     size_t a_off = 0, o_off = 0;
     for (int i = 0; i < p->batch && e == cudaSuccess; ++i) {
@@ -1122,6 +1223,18 @@ extern "C" lindhard_status lindhard_plan_pass_times(lindhard_plan *p, double *ms
     if (!p || !ms || !launches) return fail(LINDHARD_EINVAL, "plan/ms/launches must be non-NULL");
     drain_events(p);
     for (int i = 0; i < LINDHARD_NUM_PASSES; ++i) { ms[i] = p->pass_ms[i]; launches[i] = p->pass_n[i]; }
+    return LINDHARD_OK;
+}
+
+extern "C" lindhard_status lindhard_plan_set_wait_limit(lindhard_plan *p, unsigned long long wait_ns,
+                                                        int stall_instance)
+{
+    if (!p) return fail(LINDHARD_EINVAL, "plan must be non-NULL");
+    if (!p->persistent) return fail(LINDHARD_EINVAL, "the wait limit belongs to LINDHARD_PLAN_PERSISTENT plans");
+    if (stall_instance < -1 || stall_instance >= p->batch) return fail(LINDHARD_EINVAL, "stall_instance out of range");
+    p->wait_ns = wait_ns ? wait_ns : 1000000000ull;
+    p->stall_inst = stall_instance;
+    p->key_out = nullptr;   // a graph plan records again with the new values
     return LINDHARD_OK;
 }
 

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "_build", "liblindhard.so")
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOCONV, EUNSUPPORTED = range(7)
 FP32, SPLITBF16_TC, FP64 = 0, 1, 2
 IMCHI, IMCHI_T, SQW = 0, 1, 2          # lindhard_quantity
-PLAN_BACKWARD, PLAN_CONCURRENT, PLAN_GRAPH, PLAN_AUTOTUNE, PLAN_ENERGY_DIRECT = 1, 2, 4, 8, 16
+PLAN_BACKWARD, PLAN_CONCURRENT, PLAN_GRAPH, PLAN_AUTOTUNE, PLAN_ENERGY_DIRECT, PLAN_PERSISTENT = 1, 2, 4, 8, 16, 32
 _STATUS_NAMES = {OK: "OK", EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", ETIMEOUT: "ETIMEOUT",
                  ENOCONV: "ENOCONV", EUNSUPPORTED: "EUNSUPPORTED"}
 
@@ -26,7 +26,8 @@ _STATUS_NAMES = {OK: "OK", EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", E
 SYMBOLS = ("lindhard_plan_create", "lindhard_plan_sizes", "lindhard_plan_workspace_bytes", "lindhard_imchi",
            "lindhard_imchi_f64", "lindhard_imchi_backward", "lindhard_plan_profile", "lindhard_plan_profile_passes",
            "lindhard_plan_pass_times",
-           "lindhard_sum_rule", "lindhard_dmu_dparams", "lindhard_envelope_k0", "lindhard_kk_rpa", "lindhard_plan_variants", "lindhard_plan_status", "lindhard_plan_destroy",
+           "lindhard_sum_rule", "lindhard_dmu_dparams", "lindhard_envelope_k0", "lindhard_kk_rpa",
+           "lindhard_plan_set_wait_limit", "lindhard_plan_variants", "lindhard_plan_status", "lindhard_plan_destroy",
            "lindhard_imchi_noalloc", "lindhard_last_error")
 NOALLOC_SCRATCH_BYTES = 32 << 20
 NUM_PASSES = 7
@@ -99,8 +100,9 @@ def load(path: str = LIB_PATH):
         lib.lindhard_kk_rpa.restype = ctypes.c_int
         for name in ("lindhard_plan_create", "lindhard_plan_sizes", "lindhard_plan_workspace_bytes",
                      "lindhard_imchi", "lindhard_imchi_f64", "lindhard_imchi_backward", "lindhard_plan_profile",
-                     "lindhard_plan_pass_times", "lindhard_plan_status"):
+                     "lindhard_plan_pass_times", "lindhard_plan_status", "lindhard_plan_set_wait_limit"):
             getattr(lib, name).restype = ctypes.c_int
+        lib.lindhard_plan_set_wait_limit.argtypes = [ctypes.c_void_p, ctypes.c_ulonglong, ctypes.c_int]
         _lib = lib
     return _lib
 
@@ -151,7 +153,7 @@ class Plan:
 
     def __init__(self, grids: Sequence[dict], precision: int = FP32, backward: bool = False,
                  concurrent: bool = False, graph: bool = False, autotune: bool = False,
-                 energy_direct: bool = False):
+                 energy_direct: bool = False, persistent: bool = False):
         lib = load()
         self.grids = [make_grid(g["zones"], g["npz"], g["n_eps"], g["e_max"], g.get("n_omega", 0),
                                 g.get("q_extent", 0), g.get("precision", precision), g.get("quantity", IMCHI))
@@ -161,7 +163,7 @@ class Plan:
         h = ctypes.c_void_p()
         flags = (PLAN_BACKWARD if backward else 0) | (PLAN_CONCURRENT if concurrent else 0) | \
             (PLAN_GRAPH if graph else 0) | (PLAN_AUTOTUNE if autotune else 0) | \
-            (PLAN_ENERGY_DIRECT if energy_direct else 0)
+            (PLAN_ENERGY_DIRECT if energy_direct else 0) | (PLAN_PERSISTENT if persistent else 0)
         _check(lib.lindhard_plan_create(arr, self.batch, flags, ctypes.byref(h)))
         self._h = h
         self.sizes = []
@@ -295,6 +297,12 @@ class Plan:
 
     def status(self, stream=None):
         _check(load().lindhard_plan_status(self._h, _stream(stream)))
+
+    def set_wait_limit(self, wait_ns: int = 0, stall_instance: int = -1):
+        """Bounded-wait limit of a persistent plan (ns; 0 = the default 1 s);
+        stall_instance >= 0 makes that instance's first dependency wait run out
+        (a test of the timeout path)."""
+        _check(load().lindhard_plan_set_wait_limit(self._h, int(wait_ns), int(stall_instance)))
 
     def variants(self, index=0):
         """Engine variants of instance `index`: {"py_fwd", "py_inv", "px_product", "energy_inv"}."""

@@ -94,7 +94,27 @@ def test_null_arguments(lib):
     assert lib.lindhard_kk_rpa(None, 0, None, None, None, 0.0, 0, None) == 1
     assert lib.lindhard_envelope_k0(None, 0, None, 0, None, None, None, 0, None, None) == 1
     assert lib.lindhard_dmu_dparams(None, 0, None, 0.0, None, None) == 1
+    assert lib.lindhard_plan_set_wait_limit(None, 0, -1) == 1
     lib.lindhard_plan_destroy(None)
+
+
+@pytest.mark.parametrize("kw,flags,msg", [
+    (dict(), 32 | 1, "forward only"),                                   # persistent + backward
+    (dict(), 32 | 16, "forward only"),                                  # persistent + energy-direct
+    (dict(precision=2), 32, "persistent batch launch takes"),           # FP64
+    (dict(quantity=1), 32, "persistent batch launch takes"),            # finite temperature
+    (dict(zones=1, npz=128), 32, "persistent batch launch takes"),      # reduced zone
+    (dict(q_extent=64), 32, "persistent batch launch takes"),           # Q != N: padding not one third
+    (dict(n_eps=1024), 32, "persistent batch launch takes"),            # energy FFT of 1024
+])
+def test_persistent_plan_rejections_on_host(lib, kw, flags, msg):
+    from paper_1208_3210_gb300 import lindhard as lh
+    g = lh.make_grid(kw.get("zones", 2), kw.get("npz", 64), kw.get("n_eps", 128), 1.0, 0, kw.get("q_extent", 0),
+                     kw.get("precision", 0), kw.get("quantity", 0))
+    h = ctypes.c_void_p()
+    st = lib.lindhard_plan_create(ctypes.byref(g), 1, flags, ctypes.byref(h))
+    assert st == lh.EUNSUPPORTED and not h.value
+    assert msg in lib.lindhard_last_error().decode()
 
 
 @pytest.mark.parametrize("quantity,kT,a_in,band,msg", [
