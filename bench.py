@@ -34,23 +34,24 @@ DEFAULT_WORKLOAD = "large_1024x1024x512"
 FALLBACK_HBM_GBS = 6800.0
 PASS_FILES = {  # kernel sources of each timed pass (for traffic-record staleness)
     "energy_fwd": ("k_forward.cu", "k_energy.cu"),
-    "py_fwd": ("k_forward.cu", "k_tma.cu", "tma.cuh", "async.cuh", "k_pruned.cu", "fft_pruned.cuh"),
-    "px_product": ("k_product.cu", "k_tma.cu", "tma.cuh", "async.cuh", "k_pruned.cu", "fft_pruned.cuh"),
-    "py_inv": ("k_inverse.cu", "k_tma.cu", "tma.cuh", "async.cuh", "k_pruned.cu", "fft_pruned.cuh"),
+    "py_fwd": ("k_forward.cu", "k_tma.cu", "tma.cuh", "async.cuh", "k_pruned.cu", "fft_pruned.cuh", "pr_tiles.cuh", "k_pruned_tma.cu"),
+    "px_product": ("k_product.cu", "k_tma.cu", "tma.cuh", "async.cuh", "k_pruned.cu", "fft_pruned.cuh", "pr_tiles.cuh", "k_pruned_tma.cu"),
+    "py_inv": ("k_inverse.cu", "k_tma.cu", "tma.cuh", "async.cuh", "k_pruned.cu", "fft_pruned.cuh", "pr_tiles.cuh", "k_pruned_tma.cu"),
     "energy_inv": ("k_inverse.cu", "k_tma.cu", "tma.cuh", "async.cuh", "k_energy.cu"),
 }
 # kernel of each pass by engine variant (lindhard_plan_variants)
 VARIANT_KERNELS = {
     "py_fwd": ["k_fwd_y", "k_fwd_y2", "k_fwd_y2 (12-value tiles)", "k_fwd_y_tma", "k_fwd_y_tma (12-value tiles)",
                "k_y_col_tma (forward)", "k_fwd_y2 (double-width tile)", "(unused)", "k_fwd_y_pr (pruned, 8 pairs)",
-               "k_fwd_y_pr (pruned, 4 pairs)"],
+               "k_fwd_y_pr (pruned, 4 pairs)",
+               "k_fwd_y_pr_tma (pruned, TMA-staged)"],
     "py_inv": ["k_inv_y", "k_inv_y2", "k_inv_y2 (12-value tiles)", "k_inv_y_tma", "k_inv_y_tma (12-value tiles)",
                "k_y_col_tma (inverse)", "k_inv_y2 (double-width tile)", "k_inv_y_tc (tensor cores)",
-               "k_inv_y_pr (pruned, 8 pairs)", "k_inv_y_pr (pruned, 4 pairs)"],
+               "k_inv_y_pr (pruned, 8 pairs)", "k_inv_y_pr (pruned, 4 pairs)", "k_inv_y_pr_tma (pruned, TMA-staged)"],
     "px_product": ["k_x_product", "k_x_product (12-value tiles)", "k_x_product_tma",
                    "k_x_product_tma (12-value tiles)", "k_x_product (one more CTA per SM)",
                    "k_x_product (double-width tile)", "k_x_product_pr (pruned, 8 columns)",
-                   "k_x_product_pr (pruned, 4 columns)"],
+                   "k_x_product_pr (pruned, 4 columns)", "k_x_product_pr_tma (pruned, TMA-staged)"],
     "energy_inv": ["k_inv_energy", "k_inv_energy_tma", "k_inv_energy_warp"],
 }
 KERNEL_NAMES = {"batch": "all passes of all instances (graph)", "energy_fwd": "k_fwd_energy", "py_fwd": "k_fwd_y", "px_product": "k_x_product",

@@ -372,11 +372,13 @@ lindhard_status lindhard_plan_set_wait_limit(lindhard_plan *plan, unsigned long 
  * persistent forms of 1, 2 and 0, 6 paired columns on double-width tiles,
  * 7 the tensor-core inverse, 8 and 9 the pruned engine on 8 and 4 column
  * pairs: a radix-24 stage at the padded end, for a padding of exactly one
- * third, N = 2P/3 forward and Q = 2P/3 inverse);
+ * third, N = 2P/3 forward and Q = 2P/3 inverse; 10 its TMA-staged
+ * persistent form, P >= 384);
  * out[2] = the p_x product pass (0 default
  * tile, 1 tile with 12 values per thread, 2 and 3 their TMA-staged forms,
  * 4 the default tile with one more CTA per SM, 5 the default tile twice as
- * wide, 6 and 7 the pruned engine on 8 and 4 columns, N = Q = 2P/3);
+ * wide, 6 and 7 the pruned engine on 8 and 4 columns, N = Q = 2P/3, 8 its
+ * TMA-staged persistent form, P >= 384);
  * out[3] = the inverse energy
  * pass (0 default, 1 TMA-staged persistent form, 2 one warp per pair of
  * output lines, energy FFT lengths 128, 256 and 512).

@@ -22,12 +22,6 @@
 
 namespace lh {
 
-// Shared-memory layout of a pipelined CTA: [staging][FFT exchange][mbarrier].
-// The staging buffer starts at the (128-byte aligned) dynamic base.
-struct TmaSmem {
-    size_t stage_bytes, fft_bytes;
-    __host__ __device__ size_t total() const { return stage_bytes + fft_bytes + 16; }
-};
 
 
 // CTAs per SM the register budget is sized for: the tile config's own count,

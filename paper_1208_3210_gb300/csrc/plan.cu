@@ -410,6 +410,11 @@ static cudaError_t autotune(lindhard_plan *p)
         if (pr_fwd_applies(g)) { vyf.push_back(8); vyf.push_back(9); }
         if (pr_inv_applies(g)) { vyi.push_back(8); vyi.push_back(9); }
         if (pr_fwd_applies(g) && pr_inv_applies(g)) { vx.push_back(6); vx.push_back(7); }
+        if (g.P >= 384) {   // their TMA-staged persistent forms
+            if (pr_fwd_applies(g)) vyf.push_back(10);
+            if (pr_inv_applies(g)) vyi.push_back(10);
+            if (pr_fwd_applies(g) && pr_inv_applies(g)) vx.push_back(8);
+        }
         Work<float> w = work_of<float>(p, i);
         // fastest of the variants of one pass (timed only when not cached)
         auto pick = [&](const std::string &k, const std::vector<int> &vs, auto launch) {

@@ -14,6 +14,13 @@
 
 namespace lh {
 
+// Shared-memory layout of a pipelined CTA: [staging][FFT exchange][mbarrier].
+// The staging buffer starts at the (128-byte aligned) dynamic base.
+struct TmaSmem {
+    size_t stage_bytes, fft_bytes;
+    __host__ __device__ size_t total() const { return stage_bytes + fft_bytes + 16; }
+};
+
 // TMA copy of one 3D box into shared memory, completion counted on bar.
 __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z,
                                             unsigned long long *bar)
