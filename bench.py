@@ -229,33 +229,41 @@ def host_cpu():
     return {"affinity_cores": affinity, "model": model or "unknown"}
 
 
-def cpu_fft_method(A, grid, lx, ly, m, ref, max_points=1.2e8):
+def _host_available_bytes():
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    return int(line.split()[1]) * 1024
+    except Exception:
+        pass
+    return 0
+
+
+def cpu_fft_method(A, grid, lx, ly, m, ref):
     """The paper's own comparison on the host (Sec. 3: the FFT method against
-    the direct sum): the same (p, e) correlation by FP64 FFTs of the occupied
-    and empty parts (scipy, all host cores), timed over the whole output and
-    checked against the direct sums at the sampled outputs.  Workloads whose
-    padded volume exceeds max_points are not timed (host memory)."""
+    the direct sum): every output by the FP64 FFT reference of oracle/
+    (scipy, all host cores), timed, and checked against the direct sums at
+    the sampled outputs.  Skipped when the host lacks the memory (about six
+    complex128 volumes of the padded momentum grid times n_eps/2 + 1)."""
     import numpy as np
-    import scipy.fft as sfft
+
+    from oracle.fft_reference import imchi_fft64
     zones, npz, n_eps, Q, n_omega = grid["zones"], grid["npz"], grid["n_eps"], grid["q_extent"], grid["n_omega"]
     N = zones * npz
-    P = N if zones == 1 else N + Q // 2          # no wrap-around at lags |s| <= Q/2
-    if P * P * n_eps > max_points:
-        return {"unavailable": f"padded volume {P}x{P}x{n_eps} above {max_points:.1e} points (host memory)"}
-    workers = os.cpu_count() or 1
-    j = np.arange(n_eps)
-    occ = (2 * j + 1 < n_eps).astype(np.float64)
-    c = (2.0 * grid["e_max"] / n_eps) / (2.0 * math.pi) / float(npz * npz)
+    P = N if zones == 1 else N + Q // 2
+    need = 6 * P * P * (n_eps // 2 + 1) * 16
+    avail = _host_available_bytes()
+    if avail < 1.3 * need:
+        return {"unavailable": f"needs about {need / 1e9:.0f} GB of host memory, {avail / 1e9:.0f} GB available"}
+    workers = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
     t0 = time.perf_counter()
-    fa = sfft.rfftn(A * occ, s=(P, P, n_eps), workers=workers)
-    fb = sfft.rfftn(A * (1.0 - occ), s=(P, P, n_eps), workers=workers)
-    corr = sfft.irfftn(np.conj(fa) * fb, s=(P, P, n_eps), workers=workers)
-    sl = (np.arange(Q) - Q // 2) % P
-    out = -c * corr[np.ix_(sl, sl, np.arange(n_omega))]
+    out = imchi_fft64(A, grid, workers=workers)
     dt = time.perf_counter() - t0
     diff = float(np.abs(out[lx, ly, m] - ref).max() / max(np.abs(ref).max(), 1e-300))
     return {"value": Q * Q * n_omega / dt, "unit": "outputs/s", "seconds": dt, "cores": workers,
-            "kind": "scipy FP64 FFT correlation (rfftn, conjugate product, irfftn) of the whole output",
+            "kind": "FP64 FFT reference of the whole output (oracle/fft_reference.py: scipy transforms, "
+                    "conjugate product, inverse)",
             "max_rel_diff_vs_direct_sum": diff}
 
 
