@@ -35,7 +35,7 @@ FALLBACK_HBM_GBS = 6800.0
 PASS_FILES = {  # kernel sources of each timed pass (for traffic-record staleness)
     "energy_fwd": ("k_forward.cu", "k_energy.cu"),
     "py_fwd": ("k_forward.cu", "k_tma.cu", "tma.cuh", "async.cuh", "k_pruned.cu", "fft_pruned.cuh", "pr_tiles.cuh", "k_pruned_tma.cu"),
-    "px_product": ("k_product.cu", "k_tma.cu", "tma.cuh", "async.cuh", "k_pruned.cu", "fft_pruned.cuh", "pr_tiles.cuh", "k_pruned_tma.cu"),
+    "px_product": ("k_product.cu", "k_tma.cu", "tma.cuh", "async.cuh", "k_pruned.cu", "fft_pruned.cuh", "pr_tiles.cuh", "k_pruned_tma.cu", "k_product_pipe.cu"),
     "py_inv": ("k_inverse.cu", "k_tma.cu", "tma.cuh", "async.cuh", "k_pruned.cu", "fft_pruned.cuh", "pr_tiles.cuh", "k_pruned_tma.cu"),
     "energy_inv": ("k_inverse.cu", "k_tma.cu", "tma.cuh", "async.cuh", "k_energy.cu"),
 }
@@ -51,7 +51,9 @@ VARIANT_KERNELS = {
     "px_product": ["k_x_product", "k_x_product (12-value tiles)", "k_x_product_tma",
                    "k_x_product_tma (12-value tiles)", "k_x_product (one more CTA per SM)",
                    "k_x_product (double-width tile)", "k_x_product_pr (pruned, 8 columns)",
-                   "k_x_product_pr (pruned, 4 columns)", "k_x_product_pr_tma (pruned, TMA-staged)"],
+                   "k_x_product_pr (pruned, 4 columns)", "k_x_product_pr_tma (pruned, TMA-staged)",
+                   "k_x_product_pr_pipe (pruned, pipelined)",
+                   "k_x_product_pr_pipe (pruned, pipelined, twiddles in shared memory)"],
     "energy_inv": ["k_inv_energy", "k_inv_energy_tma", "k_inv_energy_warp"],
 }
 KERNEL_NAMES = {"batch": "all passes of all instances (graph)", "energy_fwd": "k_fwd_energy", "py_fwd": "k_fwd_y", "px_product": "k_x_product",

@@ -165,9 +165,12 @@ typedef struct {
  * call also runs the sequence once directly. */
 #define LINDHARD_PLAN_GRAPH 4u
 /* Plan flag: at creation, time the available engine variants of the passes
- * along p_y for each FP32 grid of the plan (CUDA events, a few launches each)
- * and use the faster; results are cached per process and, when the
- * environment variable LINDHARD_TUNE_CACHE names a file, in that JSON file. */
+ * along p_y, of the product pass and of the inverse energy pass for each FP32
+ * grid of the plan (CUDA events, a few launches each) and use the fastest;
+ * results are cached per process and, when the environment variable
+ * LINDHARD_TUNE_CACHE names a file, in that JSON file.  With the environment
+ * variable LINDHARD_TUNE_LOG set (and not "0") every timed variant's mean
+ * launch time is printed to stderr. */
 #define LINDHARD_PLAN_AUTOTUNE 8u
 /* Plan flag: compute Im chi in the paper's own arrangement (Sec. 3) instead of
  * the 3D transform: a 2D FFT over momentum for every energy plane (the
@@ -378,7 +381,10 @@ lindhard_status lindhard_plan_set_wait_limit(lindhard_plan *plan, unsigned long 
  * tile, 1 tile with 12 values per thread, 2 and 3 their TMA-staged forms,
  * 4 the default tile with one more CTA per SM, 5 the default tile twice as
  * wide, 6 and 7 the pruned engine on 8 and 4 columns, N = Q = 2P/3, 8 its
- * TMA-staged persistent form, P >= 384);
+ * TMA-staged persistent form, 9 its software-pipelined persistent form
+ * (the next tile's inputs loaded during the inverse transform, half through
+ * registers, half through shared memory), 10 the same with the twiddle
+ * tables in shared memory, P >= 384);
  * out[3] = the inverse energy
  * pass (0 default, 1 TMA-staged persistent form, 2 one warp per pair of
  * output lines, energy FFT lengths 128, 256 and 512).

@@ -39,6 +39,29 @@ template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return mk<C>
 template <typename C> __device__ __forceinline__ C csub(C a, C b) { return mk<C>(a.x - b.x, a.y - b.y); }
 template <typename C> __device__ __forceinline__ C cmul(C a, C b) { return mk<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
 template <typename C> __device__ __forceinline__ C cmulc(C a, C b) { return mk<C>(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y); } // a * conj(b)
+// Complex sums of the butterflies under a policy PK: FP32 complex sums as
+// packed f32x2 instructions (one instruction for both parts; the same IEEE
+// results as two scalar additions) when PK, else scalar.  Packing pays where
+// the kernel has registers to spare (the pair operands must sit in aligned
+// register pairs); kernels at 128 registers per thread run slower with it.
+template <bool PK, typename C> __device__ __forceinline__ C padd(C a, C b)
+{
+    if constexpr (PK && sizeof(C) == 8) return __fadd2_rn(a, b);
+    else return cadd(a, b);
+}
+template <bool PK, typename C> __device__ __forceinline__ C psub(C a, C b)
+{
+    if constexpr (PK && sizeof(C) == 8) {
+        C c;
+        asm("{\n\t.reg .b64 pa, pb, pc;\n\tmov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\t"
+            "sub.rn.f32x2 pc, pa, pb;\n\tmov.b64 {%0, %1}, pc;\n\t}"
+            : "=f"(c.x), "=f"(c.y)
+            : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+        return c;
+    } else {
+        return csub(a, b);
+    }
+}
 template <typename C> __device__ __forceinline__ C cconj(C a) { return mk<C>(a.x, -a.y); }
 // odd ? p - conj(p) = 2 i Im p : p (the transform of the odd part of a real sequence)
 template <typename C> __device__ __forceinline__ C odd_part(C p, bool odd)
@@ -144,91 +167,91 @@ __device__ __forceinline__ C twc(C x)
     }
 }
 
-template <int R, bool INV, typename C> struct Dft;
+template <int R, bool INV, typename C, bool PK = false> struct Dft;
 
-template <bool INV, typename C> struct Dft<1, INV, C> {
+template <bool INV, typename C, bool PK> struct Dft<1, INV, C, PK> {
     __device__ __forceinline__ static void run(C *) {}
 };
-template <bool INV, typename C> struct Dft<2, INV, C> {
+template <bool INV, typename C, bool PK> struct Dft<2, INV, C, PK> {
     __device__ __forceinline__ static void run(C *v)
     {
         C a = v[0], b = v[1];
-        v[0] = cadd(a, b);
-        v[1] = csub(a, b);
+        v[0] = padd<PK>(a, b);
+        v[1] = psub<PK>(a, b);
     }
 };
-template <bool INV, typename C> struct Dft<4, INV, C> {
+template <bool INV, typename C, bool PK> struct Dft<4, INV, C, PK> {
     __device__ __forceinline__ static void run(C *v)
     {
-        C t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
-        C t2 = cadd(v[1], v[3]), t3 = csub(v[1], v[3]);
+        C t0 = padd<PK>(v[0], v[2]), t1 = psub<PK>(v[0], v[2]);
+        C t2 = padd<PK>(v[1], v[3]), t3 = psub<PK>(v[1], v[3]);
         t3 = INV ? mul_i(t3) : mul_mi(t3);
-        v[0] = cadd(t0, t2);
-        v[2] = csub(t0, t2);
-        v[1] = cadd(t1, t3);
-        v[3] = csub(t1, t3);
+        v[0] = padd<PK>(t0, t2);
+        v[2] = psub<PK>(t0, t2);
+        v[1] = padd<PK>(t1, t3);
+        v[3] = psub<PK>(t1, t3);
     }
 };
 // Radix 8 and 16: decimation in time into two halves of radix R/2.
-template <int R, bool INV, typename C, int K>
+template <int R, bool INV, typename C, int K, bool PK = false>
 __device__ __forceinline__ void dit_combine(C *v, const C *e, const C *o)
 {
     if constexpr (K < R / 2) {
         C t = twc<R, K, INV>(o[K]);
-        v[K] = cadd(e[K], t);
-        v[K + R / 2] = csub(e[K], t);
-        dit_combine<R, INV, C, K + 1>(v, e, o);
+        v[K] = padd<PK>(e[K], t);
+        v[K + R / 2] = psub<PK>(e[K], t);
+        dit_combine<R, INV, C, K + 1, PK>(v, e, o);
     }
 }
-template <bool INV, typename C> struct Dft<8, INV, C> {
+template <bool INV, typename C, bool PK> struct Dft<8, INV, C, PK> {
     __device__ __forceinline__ static void run(C *v)
     {
         C e[4] = {v[0], v[2], v[4], v[6]}, o[4] = {v[1], v[3], v[5], v[7]};
-        Dft<4, INV, C>::run(e);
-        Dft<4, INV, C>::run(o);
-        dit_combine<8, INV, C, 0>(v, e, o);
+        Dft<4, INV, C, PK>::run(e);
+        Dft<4, INV, C, PK>::run(o);
+        dit_combine<8, INV, C, 0, PK>(v, e, o);
     }
 };
-template <bool INV, typename C> struct Dft<3, INV, C> {
+template <bool INV, typename C, bool PK> struct Dft<3, INV, C, PK> {
     __device__ __forceinline__ static void run(C *v)
     {
         using T = decltype(C::x);
         constexpr T s3 = (T)0.86602540378443864676;   // sin(2 pi / 3)
-        C t1 = cadd(v[1], v[2]);
+        C t1 = padd<PK>(v[1], v[2]);
         C t2 = mk<C>(v[0].x - (T)0.5 * t1.x, v[0].y - (T)0.5 * t1.y);
-        C d = csub(v[1], v[2]);
+        C d = psub<PK>(v[1], v[2]);
         C t3 = mk<C>(s3 * d.x, s3 * d.y);
-        v[0] = cadd(v[0], t1);
+        v[0] = padd<PK>(v[0], t1);
         // forward: y1 = t2 - i t3, y2 = t2 + i t3 (inverse: the other way round)
-        v[1] = INV ? cadd(t2, mul_i(t3)) : cadd(t2, mul_mi(t3));
-        v[2] = INV ? cadd(t2, mul_mi(t3)) : cadd(t2, mul_i(t3));
+        v[1] = INV ? padd<PK>(t2, mul_i(t3)) : padd<PK>(t2, mul_mi(t3));
+        v[2] = INV ? padd<PK>(t2, mul_mi(t3)) : padd<PK>(t2, mul_i(t3));
     }
 };
 // Radix 6, 12 and 24: decimation in time into two halves.
-template <int R, bool INV, typename C> struct DftDit {
+template <int R, bool INV, typename C, bool PK = false> struct DftDit {
     __device__ __forceinline__ static void run(C *v)
     {
         C e[R / 2], o[R / 2];
 #pragma unroll
         for (int i = 0; i < R / 2; ++i) { e[i] = v[2 * i]; o[i] = v[2 * i + 1]; }
-        Dft<R / 2, INV, C>::run(e);
-        Dft<R / 2, INV, C>::run(o);
-        dit_combine<R, INV, C, 0>(v, e, o);
+        Dft<R / 2, INV, C, PK>::run(e);
+        Dft<R / 2, INV, C, PK>::run(o);
+        dit_combine<R, INV, C, 0, PK>(v, e, o);
     }
 };
-template <bool INV, typename C> struct Dft<6, INV, C> : DftDit<6, INV, C> {};
-template <bool INV, typename C> struct Dft<12, INV, C> : DftDit<12, INV, C> {};
-template <bool INV, typename C> struct Dft<24, INV, C> : DftDit<24, INV, C> {};
+template <bool INV, typename C, bool PK> struct Dft<6, INV, C, PK> : DftDit<6, INV, C, PK> {};
+template <bool INV, typename C, bool PK> struct Dft<12, INV, C, PK> : DftDit<12, INV, C, PK> {};
+template <bool INV, typename C, bool PK> struct Dft<24, INV, C, PK> : DftDit<24, INV, C, PK> {};
 
-template <bool INV, typename C> struct Dft<16, INV, C> {
+template <bool INV, typename C, bool PK> struct Dft<16, INV, C, PK> {
     __device__ __forceinline__ static void run(C *v)
     {
         C e[8], o[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) { e[i] = v[2 * i]; o[i] = v[2 * i + 1]; }
-        Dft<8, INV, C>::run(e);
-        Dft<8, INV, C>::run(o);
-        dit_combine<16, INV, C, 0>(v, e, o);
+        Dft<8, INV, C, PK>::run(e);
+        Dft<8, INV, C, PK>::run(o);
+        dit_combine<16, INV, C, 0, PK>(v, e, o);
     }
 };
 
@@ -342,7 +365,8 @@ namespace lh {
 // two independent dependency chains in flight.  Layout and Stockham ordering
 // as in Fft<..., MAP_COL, ...>: shared memory [L][C].
 // VPT = (C/2) L / T values per thread per column.
-template <typename Real, int L, int C, int T, bool INV>
+// PK: packed f32x2 complex sums in the butterflies (padd/psub).
+template <typename Real, int L, int C, int T, bool INV, bool PK = false>
 struct FftPair {
     using Cx = cx<Real>;
     static constexpr int CP = C / 2;                 // column pairs per tile
@@ -427,8 +451,8 @@ struct FftPair {
                     va[b * Rs + r] = INV ? cmulc(va[b * Rs + r], w) : cmul(va[b * Rs + r], w);
                     vb[b * Rs + r] = INV ? cmulc(vb[b * Rs + r], w) : cmul(vb[b * Rs + r], w);
                 }
-                Dft<Rs, INV, Cx>::run(va + b * Rs);
-                Dft<Rs, INV, Cx>::run(vb + b * Rs);
+                Dft<Rs, INV, Cx, PK>::run(va + b * Rs);
+                Dft<Rs, INV, Cx, PK>::run(vb + b * Rs);
             }
             __syncthreads();
             stage_rest<S + 1>(va, vb, sm, tw);
@@ -441,8 +465,8 @@ struct FftPair {
     {
 #pragma unroll
         for (int b = 0; b < VPT / R0; ++b) {
-            Dft<R0, INV, Cx>::run(va + b * R0);
-            Dft<R0, INV, Cx>::run(vb + b * R0);
+            Dft<R0, INV, Cx, PK>::run(va + b * R0);
+            Dft<R0, INV, Cx, PK>::run(vb + b * R0);
         }
         stage_rest<1>(va, vb, sm, tw);
     }

@@ -71,7 +71,7 @@ __host__ __device__ constexpr int pr_tw_offset(int L, bool inv, int s) { return 
 // 24-point DFTs with a pruned end (sign by INV as in Dft<>).
 // Inputs v[16..23] zero: y[3 k2 + k1] = DFT8_k2( w^(r1 k1) (v[r1] + W3^k1 v[r1 + 8]) ),
 // w = exp(-+2 pi i / 24), W3 = w^8.
-template <bool INV>
+template <bool INV, bool PK = false>
 __device__ __forceinline__ void dft24_in16(float2 *v)
 {
     constexpr float s3 = 0.86602540378443864676f;   // sin(2 pi / 3)
@@ -79,12 +79,12 @@ __device__ __forceinline__ void dft24_in16(float2 *v)
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
         const float2 a = v[r], c = v[r + 8];
-        u0[r] = cadd(a, c);
+        u0[r] = padd<PK>(a, c);
         const float2 t = make_float2(fmaf(-0.5f, c.x, a.x), fmaf(-0.5f, c.y, a.y));
         const float2 q = make_float2(s3 * c.x, s3 * c.y);
         // a + W3 c = t -+ i q, a + W3^2 c = t +- i q (forward: W3 = -1/2 - i s3)
-        u1[r] = INV ? cadd(t, mul_i(q)) : cadd(t, mul_mi(q));
-        u2[r] = INV ? cadd(t, mul_mi(q)) : cadd(t, mul_i(q));
+        u1[r] = INV ? padd<PK>(t, mul_i(q)) : padd<PK>(t, mul_mi(q));
+        u2[r] = INV ? padd<PK>(t, mul_mi(q)) : padd<PK>(t, mul_i(q));
     }
     u1[1] = twc<24, 1, INV>(u1[1]); u1[2] = twc<24, 2, INV>(u1[2]); u1[3] = twc<24, 3, INV>(u1[3]);
     u1[4] = twc<24, 4, INV>(u1[4]); u1[5] = twc<24, 5, INV>(u1[5]); u1[6] = twc<24, 6, INV>(u1[6]);
@@ -92,9 +92,9 @@ __device__ __forceinline__ void dft24_in16(float2 *v)
     u2[1] = twc<24, 2, INV>(u2[1]); u2[2] = twc<24, 4, INV>(u2[2]); u2[3] = twc<24, 6, INV>(u2[3]);
     u2[4] = twc<24, 8, INV>(u2[4]); u2[5] = twc<24, 10, INV>(u2[5]); u2[6] = twc<24, 12, INV>(u2[6]);
     u2[7] = twc<24, 14, INV>(u2[7]);
-    Dft<8, INV, float2>::run(u0);
-    Dft<8, INV, float2>::run(u1);
-    Dft<8, INV, float2>::run(u2);
+    Dft<8, INV, float2, PK>::run(u0);
+    Dft<8, INV, float2, PK>::run(u1);
+    Dft<8, INV, float2, PK>::run(u2);
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
         v[3 * k] = u0[k];
@@ -105,7 +105,7 @@ __device__ __forceinline__ void dft24_in16(float2 *v)
 
 // Outputs y[0..7] and y[16..23] only (v[8..15] are left undefined):
 // y[k1 + 8 k2] = sum_i2 W3^(i2 k2) w^(i2 k1) DFT8_k1(v[3 i1 + i2]).
-template <bool INV>
+template <bool INV, bool PK = false>
 __device__ __forceinline__ void dft24_out16(float2 *v)
 {
     constexpr float s3 = 0.86602540378443864676f;
@@ -116,9 +116,9 @@ __device__ __forceinline__ void dft24_out16(float2 *v)
         y1[i] = v[3 * i + 1];
         y2[i] = v[3 * i + 2];
     }
-    Dft<8, INV, float2>::run(y0);
-    Dft<8, INV, float2>::run(y1);
-    Dft<8, INV, float2>::run(y2);
+    Dft<8, INV, float2, PK>::run(y0);
+    Dft<8, INV, float2, PK>::run(y1);
+    Dft<8, INV, float2, PK>::run(y2);
     y1[1] = twc<24, 1, INV>(y1[1]); y1[2] = twc<24, 2, INV>(y1[2]); y1[3] = twc<24, 3, INV>(y1[3]);
     y1[4] = twc<24, 4, INV>(y1[4]); y1[5] = twc<24, 5, INV>(y1[5]); y1[6] = twc<24, 6, INV>(y1[6]);
     y1[7] = twc<24, 7, INV>(y1[7]);
@@ -127,12 +127,12 @@ __device__ __forceinline__ void dft24_out16(float2 *v)
     y2[7] = twc<24, 14, INV>(y2[7]);
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-        const float2 s = cadd(y1[k], y2[k]), d = csub(y1[k], y2[k]);
-        v[k] = cadd(y0[k], s);
+        const float2 s = padd<PK>(y1[k], y2[k]), d = psub<PK>(y1[k], y2[k]);
+        v[k] = padd<PK>(y0[k], s);
         const float2 t = make_float2(fmaf(-0.5f, s.x, y0[k].x), fmaf(-0.5f, s.y, y0[k].y));
         const float2 q = make_float2(s3 * d.x, s3 * d.y);
         // W3^2 z1 + W3 z2 = -s/2 -+ i s3 d (forward: W3 = -1/2 - i s3)
-        v[k + 16] = INV ? cadd(t, mul_mi(q)) : cadd(t, mul_i(q));
+        v[k + 16] = INV ? padd<PK>(t, mul_mi(q)) : padd<PK>(t, mul_i(q));
     }
 }
 
@@ -141,7 +141,36 @@ __device__ __forceinline__ void dft24_out16(float2 *v)
 // twiddle, stored side by side (16 bytes) in rows of CW pairs; NOPS = 1: one
 // operand, rows of CW values.  PIN: inputs at rows >= 2L/3 are zero (forward
 // first stage); POUT: only the kept lags of the last stage are formed.
-template <int L, int CW, int T, bool INV, int NOPS, bool PIN, bool POUT>
+// TWS (PrEng): the twiddle tables of length L are in shared memory at tw
+// (the padded layout of pr_tws_offset), read with ld.shared, instead of in
+// global memory read through the read-only cache.
+__device__ __forceinline__ float4 lds_f4(const float4 *p)
+{
+    float4 q;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(q.x), "=f"(q.y), "=f"(q.z), "=f"(q.w)
+                 : "r"((unsigned)__cvta_generic_to_shared(p)));
+    return q;
+}
+// The shared-memory copy of one length's tables: forward stages, then inverse
+// stages, each row [k] padded by 16 bytes (Rs + 2 entries) so that the 16-byte
+// twiddle loads of the four consecutive butterflies of a warp fall in
+// different banks.
+__host__ __device__ constexpr int pr_tws_row(int L, bool inv, int s) { return pr_radix(L, s, inv) + 2; }
+__host__ __device__ constexpr int pr_tws_offset(int L, bool inv, int s)
+{
+    int n = 0;
+    for (int d = 0; d < 2; ++d)
+        for (int st = 1; st < pr_nstages(L); ++st) {
+            if (d == (int)inv && st == s) return n;
+            n += pr_ns(L, st, d != 0) * pr_tws_row(L, d != 0, st);
+        }
+    return n;   // past the last table: the total
+}
+__host__ __device__ constexpr int pr_tws_entries(int L) { return pr_tws_offset(L, true, pr_nstages(L)); }
+
+// PK: packed f32x2 complex sums in the butterflies (padd/psub).
+template <int L, int CW, int T, bool INV, int NOPS, bool PIN, bool POUT, bool TWS = false, bool PK = false>
 struct PrEng {
     using Cx = float2;
     static constexpr int S = pr_nstages(L);
@@ -186,9 +215,9 @@ struct PrEng {
     template <int R, bool FIRST, bool LAST>
     __device__ __forceinline__ static void dft(Cx *v)
     {
-        if constexpr (R == 24 && FIRST && PIN) dft24_in16<INV>(v);
-        else if constexpr (R == 24 && LAST && POUT) dft24_out16<INV>(v);
-        else Dft<R, INV, Cx>::run(v);
+        if constexpr (R == 24 && FIRST && PIN) dft24_in16<INV, PK>(v);
+        else if constexpr (R == 24 && LAST && POUT) dft24_out16<INV, PK>(v);
+        else Dft<R, INV, Cx, PK>::run(v);
     }
 
     template <int SS>
@@ -199,7 +228,8 @@ struct PrEng {
             constexpr int Rs = pr_radix(L, SS, INV), Ns = pr_ns(L, SS, INV);
             static_assert(Nsp == 1 || Nsp % R0 == 0, "exchange offsets must stay compile-time");
             static_assert((L / Rs) % R0 == 0, "read offsets must stay compile-time");
-            const Cx *tws = tw + pr_tw_offset(L, INV, SS);
+            const Cx *tws = tw + (TWS ? pr_tws_offset(L, INV, SS) : pr_tw_offset(L, INV, SS));
+            constexpr int TWROW = TWS ? Rs + 2 : Rs;
             // the previous stage's outputs, Stockham order: idxD + r Nsp
 #pragma unroll
             for (int b = 0; b < VPT / Rp; ++b) {
@@ -216,10 +246,10 @@ struct PrEng {
 #pragma unroll
                 for (int r = 0; r < Rs; ++r) ld(sm, base + poff(r * (L / Rs)), va[b * Rs + r], vb[b * Rs + r]);
                 // twiddles exp(-+2 pi i k r / (Ns Rs)), k = j mod Ns, entries [k][0..Rs)
-                const float4 *w4 = reinterpret_cast<const float4 *>(tws + (j % Ns) * Rs);
+                const float4 *w4 = reinterpret_cast<const float4 *>(tws + (j % Ns) * TWROW);
 #pragma unroll
                 for (int h = 0; h < Rs / 2; ++h) {
-                    const float4 q = __ldg(w4 + h);
+                    const float4 q = TWS ? lds_f4(w4 + h) : __ldg(w4 + h);
                     const Cx w0 = make_float2(q.x, q.y), w1 = make_float2(q.z, q.w);
                     if (h > 0) {
                         va[b * Rs + 2 * h] = INV ? cmulc(va[b * Rs + 2 * h], w0) : cmul(va[b * Rs + 2 * h], w0);

@@ -111,12 +111,15 @@ cudaError_t launch_x_product_t(const Geom &g, const Work<Real> &w, cudaStream_t 
 cudaError_t launch_x_product_tma(const Geom &g, const Work<float> &w, cudaStream_t s, int variant);
 cudaError_t launch_x_product_pr(const Geom &g, const Work<float> &w, cudaStream_t s, int variant);
 cudaError_t launch_x_product_pr_tma(const Geom &g, const Work<float> &w, cudaStream_t s);
+cudaError_t launch_x_product_pr_pipe(const Geom &g, const Work<float> &w, cudaStream_t s, int variant);
 // variants 2, 3: the TMA-staged persistent kernels of k_tma.cu; 6, 7: the
 // pruned engine of k_pruned.cu (one-third padding); 8: its TMA-staged
-// persistent form (k_pruned_tma.cu)
+// persistent form (k_pruned_tma.cu); 9, 10: its software-pipelined persistent
+// form (k_product_pipe.cu)
 cudaError_t launch_x_product(const Geom &g, const Work<float> &w, cudaStream_t s, int variant)
 {
     if (variant == 8) return launch_x_product_pr_tma(g, w, s);
+    if (variant == 9 || variant == 10) return launch_x_product_pr_pipe(g, w, s, variant);
     if (variant == 2 || variant == 3) return launch_x_product_tma(g, w, s, variant);
     if (variant == 6 || variant == 7) return launch_x_product_pr(g, w, s, variant);
 #define CALL(L) launch_x_product_t<float, L>(g, w, s, variant)

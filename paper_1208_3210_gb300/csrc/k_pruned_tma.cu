@@ -17,14 +17,14 @@ namespace lh {
 constexpr int PT_CP = 4, PT_C = 2 * PT_CP;
 
 template <int L>
-struct PtFwd {
+struct PtFwd {   // one CTA per SM, registers to spare: packed complex sums
     static constexpr int T = PT_CP * L / 24;
-    using E = PrEng<L, PT_CP, T, false, 2, true, false>;
+    using E = PrEng<L, PT_CP, T, false, 2, true, false, false, true>;
 };
 template <int L>
 struct PtInv {
     static constexpr int T = PT_CP * L / 24;
-    using E = PrEng<L, PT_CP, T, true, 2, false, true>;
+    using E = PrEng<L, PT_CP, T, true, 2, false, true, false, true>;
 };
 template <int L>
 struct PtProd {

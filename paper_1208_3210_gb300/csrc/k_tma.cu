@@ -130,7 +130,9 @@ k_inv_y_tma(Geom g, const __grid_constant__ CUtensorMap map, float2 *__restrict_
             const float2 *__restrict__ tw, unsigned *status, int box_rows)
 {
     constexpr int C = Cfg::C, T = Cfg::T;
-    using E = FftPair<float, L, C, T, true>;
+    // packed complex sums where the launch leaves at least 192 registers a thread
+    constexpr bool PK = 65536 / (T * PairTmaBounds<L, Cfg, true>::MINB) >= 192;
+    using E = FftPair<float, L, C, T, true, PK>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int nbox = (L + box_rows - 1) / box_rows, NR = nbox * box_rows;
     const TmaSmem lay{(size_t)NR * C * sizeof(float2), (size_t)E::SMEM_ELEMS * sizeof(float2)};

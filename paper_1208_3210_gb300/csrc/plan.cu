@@ -157,6 +157,7 @@ struct lindhard_plan {
     // product pass 0 default tile, 1 tile with
     // 12 values per thread, 2 and 3 their TMA-staged persistent forms, 4 the
     // default tile with one more CTA per SM, 5 the default tile twice as wide
+    // (6-10: the pruned engine's forms, as lindhard_plan_variants lists them)
     std::vector<int> yvar_fwd, yvar_inv, xvar;
     // inverse energy pass: 0 default, 1 TMA-staged persistent form
     std::vector<int> evar;
@@ -385,6 +386,8 @@ static cudaError_t autotune(lindhard_plan *p)
     cudaEvent_t a, b;
     cudaEventCreate(&a);
     cudaEventCreate(&b);
+    const char *log_env = getenv("LINDHARD_TUNE_LOG");
+    const bool log = log_env && *log_env && strcmp(log_env, "0") != 0;
     for (int i = 0; i < p->batch && e == cudaSuccess; ++i) {
         const Geom &g = p->geoms[i];
         if (p->precision[i] == LINDHARD_FP64 || g.P < 128) continue;
@@ -413,7 +416,11 @@ static cudaError_t autotune(lindhard_plan *p)
         if (g.P >= 384) {   // their TMA-staged persistent forms
             if (pr_fwd_applies(g)) vyf.push_back(10);
             if (pr_inv_applies(g)) vyi.push_back(10);
-            if (pr_fwd_applies(g) && pr_inv_applies(g)) vx.push_back(8);
+            if (pr_fwd_applies(g) && pr_inv_applies(g)) {
+                vx.push_back(8);
+                vx.push_back(9);    // software-pipelined persistent forms
+                vx.push_back(10);
+            }
         }
         Work<float> w = work_of<float>(p, i);
         // fastest of the variants of one pass (timed only when not cached)
@@ -428,6 +435,7 @@ static cudaError_t autotune(lindhard_plan *p)
                         continue;
                     }
                     float t = time_launches([&] { return launch(vs[j]); }, a, b);
+                    if (log) fprintf(stderr, "lindhard tune %s variant %d: %.4f ms\n", k.c_str(), vs[j], t / 5);
                     if (!any || t < tbest) { best = vs[j]; tbest = t; any = true; }
                 }
                 g_tune[k] = TuneEntry{best, std::string()};
