@@ -76,7 +76,27 @@ def parse_args():
                     help="skip the comparison with the tensor-core form (LINDHARD_SPLITBF16_TC)")
     ap.add_argument("--grid", default=None,
                     help="zones,npz,n_eps,e_max: replace the workload's grid (for profiling smaller cases)")
+    ap.add_argument("--variants", default=None,
+                    help="F,I,X,E: pin the engine variants of the p_y forward, p_y inverse, product and "
+                         "inverse energy passes (through a tune cache file) instead of timing them, e.g. "
+                         "to profile a smaller grid with the variants the full-size workload takes")
     return ap.parse_args()
+
+
+def pin_variants(lh, torch, grids, spec):
+    """Write the pinned variants for the grid's geometry to a fresh tune cache
+    file and point LINDHARD_TUNE_CACHE at it (the autotuner uses cached
+    entries as they are)."""
+    vf, vi, vx, ve = (int(v) for v in spec.split(","))
+    probe = lh.Plan(grids)
+    s = probe.sizes[0]
+    probe.close()
+    key = f"{torch.cuda.get_device_name(0)}|P={s.fft_p}|N={s.N}|PE={s.fft_e}|Q={s.q_extent}"
+    path = os.path.join(tempfile.mkdtemp(prefix="lindhard_pins_"), "tune.json")
+    with open(path, "w") as f:
+        json.dump({key + "|fwd_y": vf, key + "|inv_y": vi, key + "|x_product": vx, key + "|inv_energy": ve},
+                  f, indent=0)
+    os.environ["LINDHARD_TUNE_CACHE"] = path
 
 
 def pass_bytes(s):
@@ -506,6 +526,8 @@ def main():
             args.workload = f"{args.workload} grid {args.grid}"
             args.no_cpu_baseline = True
         grids, bands = [dict(grid, precision=prec)], [band]
+        if args.variants:
+            pin_variants(lh, torch, grids, args.variants)
         plan = lh.Plan(grids, autotune=not args.no_autotune)
     s = plan.sizes[0]
     out = torch.empty(plan.out_elems(), dtype=torch.float32, device="cuda")
