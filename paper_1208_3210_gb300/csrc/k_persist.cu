@@ -27,6 +27,7 @@ __host__ __device__ constexpr int cmax(int a, int b) { return a > b ? a : b; }
 
 constexpr int PS_T = 256;
 constexpr int PS_PASSES = 5;
+constexpr int PS_EG = 4;   // energy-pass tiles per queue item
 
 // Per-instance constants of a persistent plan (device array).
 struct PInst {
@@ -77,14 +78,14 @@ void ps_tiles(const Geom &g, int *ntiles, int *gx)
     const int CW = 6144 / g.P;
     const long long per = (long long)ET_WARPS * ET_LPW;
     gx[0] = gx[4] = 0;
-    ntiles[0] = (int)(((long long)g.N * g.N + per - 1) / per);
+    ntiles[0] = (int)(((long long)g.N * g.N + per * PS_EG - 1) / (per * PS_EG));
     gx[1] = (2 * g.SP + 2 * CW - 1) / (2 * CW);
     ntiles[1] = gx[1] * g.N;
     gx[2] = (g.H + CW - 1) / CW;
     ntiles[2] = gx[2] * g.P;
     gx[3] = (g.H + 2 * CW - 1) / (2 * CW);
     ntiles[3] = gx[3] * g.Q;
-    ntiles[4] = (int)(((long long)g.Q * g.Q / 2 + per - 1) / per);
+    ntiles[4] = (int)(((long long)g.Q * g.Q / 2 + per * PS_EG - 1) / (per * PS_EG));
 }
 
 // Counter value with a bounded wait (thread 0 of the CTA): false when the
@@ -101,7 +102,7 @@ __device__ __forceinline__ bool ps_wait(const unsigned *cnt, unsigned need, unsi
 }
 
 // One tile of each pass, dispatched on the instance's transform lengths.
-__device__ __noinline__ void ps_energy_fwd(const PInst &in, int t, const float2 *etw, float2 *sm)
+__device__ __noinline__ void ps_energy_fwd(const PInst &in, long long t, const float2 *etw, float2 *sm)
 {
     const Geom g = in.g;   // registers (the constant fields the tile reads)
     float2 *U1 = in.X;
@@ -141,7 +142,7 @@ __device__ __noinline__ void ps_inv_y(const PInst &in, int t, const float2 *ptw,
     switch (g.P) { PR_CASE(192) PR_CASE(384) PR_CASE(768) PR_CASE(1536) }
 #undef PR_CASE
 }
-__device__ __noinline__ void ps_energy_inv(const PInst &in, int t, float *out, const float2 *etw, float2 *sm)
+__device__ __noinline__ void ps_energy_inv(const PInst &in, long long t, float *out, const float2 *etw, float2 *sm)
 {
     const Geom g = in.g;
     float *o = out + in.out_off;
@@ -178,6 +179,12 @@ k_persistent(const PInst *__restrict__ insts, const PSeg *__restrict__ segs, int
     // segment changes, before any item of a later pass can wait on them)
     int seg = 0, ok_seg = -1, pend_seg = -1;
     unsigned pend = 0;
+    // thread 0 claims one chunk ahead: the atomic's round trip overlaps the
+    // current chunk's tiles.  Progress still holds: a CTA's claimed-ahead
+    // chunk lies after its current one, so the earliest unfinished item is
+    // either being worked on or next for a CTA whose current items are done.
+    int nxt = 0;
+    if (threadIdx.x == 0) nxt = (int)atomicAdd(head, (unsigned)PS_CHUNK);
     auto flush = [&]() {
         if (pend) {
             __threadfence();   // the CTA's writes (ordered before by the barrier) before the count
@@ -187,7 +194,8 @@ k_persistent(const PInst *__restrict__ insts, const PSeg *__restrict__ segs, int
     };
     for (;;) {
         if (threadIdx.x == 0) {
-            int base = (int)atomicAdd(head, (unsigned)PS_CHUNK);
+            int base = nxt;
+            if (base < total) nxt = (int)atomicAdd(head, (unsigned)PS_CHUNK);
             if (base < total && *(volatile unsigned *)status != DEV_OK) base = total;   // a CTA gave up: stop
             s_base = base;
         }
@@ -229,11 +237,19 @@ k_persistent(const PInst *__restrict__ insts, const PSeg *__restrict__ segs, int
             const PInst &in = s_in;
             const int t = item - sg.start;
             switch (sg.pass) {
-            case 0: ps_energy_fwd(in, t, etw, sm); break;
+            // an item of an energy pass is PS_EG consecutive tiles (short
+            // tiles; the per-item bookkeeping would not pay for itself)
+            case 0:
+#pragma unroll 1
+                for (int u = 0; u < PS_EG; ++u) ps_energy_fwd(in, (long long)t * PS_EG + u, etw, sm);
+                break;
             case 1: ps_fwd_y(in, t, ptw, sm); break;
             case 2: ps_product(in, t, ptw, sm); break;
             case 3: ps_inv_y(in, t, ptw, sm); break;
-            default: ps_energy_inv(in, t, out, etw, sm); break;
+            default:
+#pragma unroll 1
+                for (int u = 0; u < PS_EG; ++u) ps_energy_inv(in, (long long)t * PS_EG + u, out, etw, sm);
+                break;
             }
             __syncthreads();   // every thread's writes of the tile before thread 0 counts it
             if (threadIdx.x == 0) {

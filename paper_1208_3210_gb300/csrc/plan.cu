@@ -175,6 +175,7 @@ struct lindhard_plan {
     // concurrent execution: instances on plan-owned streams, forked from and
     // joined back into the caller's stream with events
     std::vector<cudaStream_t> streams;
+    std::vector<int> stream_of;   // stream index of each instance
     cudaEvent_t fork_ev = nullptr;
     std::vector<cudaEvent_t> join_ev;
     // graph mode: the forward sequence captured once and replayed while the
@@ -622,6 +623,22 @@ extern "C" lindhard_status lindhard_plan_create(const lindhard_grid *grids, int 
             if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->join_ev[k], cudaEventDisableTiming);
         }
         if (e == cudaSuccess && p->graph) e = cudaStreamCreateWithFlags(&p->origin, cudaStreamNonBlocking);
+        // instances to streams longest first, each to the stream with the
+        // least work so far (work ~ transform points P^2 PE), so that the
+        // streams end together instead of one long stream finishing alone
+        std::vector<int> order(batch);
+        std::vector<double> work(batch), load(ns, 0.0);
+        for (int i = 0; i < batch; ++i) {
+            order[i] = i;
+            work[i] = (double)p->geoms[i].P * p->geoms[i].P * p->geoms[i].PE;
+        }
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work[a] > work[b]; });
+        p->stream_of.assign(batch, 0);
+        for (int i : order) {
+            const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+            p->stream_of[i] = k;
+            load[k] += work[i];
+        }
     }
     p->yvar_fwd.assign(batch, 1);
     p->yvar_inv.assign(batch, 1);
@@ -799,7 +816,7 @@ static Work<Real> work_of(lindhard_plan *p, int i)
 // one of the plan's streams (forked from `s` by fork_begin).
 static cudaStream_t inst_stream(lindhard_plan *p, int i, cudaStream_t s)
 {
-    return p->concurrent ? p->streams[i % p->streams.size()] : s;
+    return p->concurrent ? p->streams[p->stream_of[i]] : s;
 }
 static cudaError_t fork_begin(lindhard_plan *p, cudaStream_t s)
 {
