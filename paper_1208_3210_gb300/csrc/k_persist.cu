@@ -27,7 +27,7 @@ __host__ __device__ constexpr int cmax(int a, int b) { return a > b ? a : b; }
 
 constexpr int PS_T = 256;
 constexpr int PS_PASSES = 5;
-constexpr int PS_EG = 4;   // energy-pass tiles per queue item
+constexpr int PS_EG = 8;   // energy-pass tiles per queue item
 
 // Per-instance constants of a persistent plan (device array).
 struct PInst {
