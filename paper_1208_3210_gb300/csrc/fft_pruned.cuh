@@ -212,6 +212,48 @@ struct PrEng {
         }
     }
 
+    __device__ __forceinline__ static float4 tw_ld(const float4 *p) { return TWS ? lds_f4(p) : __ldg(p); }
+    // The twiddles w^r, r < R, of one butterfly (w = exp(-2 pi i k / (Ns R))),
+    // from the table row [k][0..R): for R = 8 and 24 only some entries are
+    // loaded and the rest formed as products of them (at most three
+    // roundings deep, a few ulp): the 16-byte table loads, not the
+    // multiplications, were what the twiddles cost in these passes.
+    template <int R>
+    __device__ __forceinline__ static void twiddle_set(const float4 *w4, Cx *w)
+    {
+        auto lo = [](float4 q) { return make_float2(q.x, q.y); };
+        auto hi = [](float4 q) { return make_float2(q.z, q.w); };
+        if constexpr (R == 8 || R == 24) {
+            const float4 q0 = tw_ld(w4), q1 = tw_ld(w4 + 1);
+            w[1] = hi(q0);
+            w[2] = lo(q1);
+            w[3] = hi(q1);
+            w[4] = cmul(w[2], w[2]);
+            w[5] = cmul(w[2], w[3]);
+            w[6] = cmul(w[3], w[3]);
+            w[7] = cmul(w[3], w[4]);
+            if constexpr (R == 24) {
+                const float4 q4 = tw_ld(w4 + 4), q8 = tw_ld(w4 + 8);
+                w[8] = lo(q4);
+                w[9] = hi(q4);
+                w[16] = lo(q8);
+                w[17] = hi(q8);
+#pragma unroll
+                for (int r = 2; r < 8; ++r) {
+                    w[8 + r] = cmul(w[8], w[r]);
+                    w[16 + r] = cmul(w[16], w[r]);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int h = 0; h < R / 2; ++h) {
+                const float4 q = tw_ld(w4 + h);
+                w[2 * h] = lo(q);
+                w[2 * h + 1] = hi(q);
+            }
+        }
+    }
+
     template <int R, bool FIRST, bool LAST>
     __device__ __forceinline__ static void dft(Cx *v)
     {
@@ -247,18 +289,12 @@ struct PrEng {
                 for (int r = 0; r < Rs; ++r) ld(sm, base + poff(r * (L / Rs)), va[b * Rs + r], vb[b * Rs + r]);
                 // twiddles exp(-+2 pi i k r / (Ns Rs)), k = j mod Ns, entries [k][0..Rs)
                 const float4 *w4 = reinterpret_cast<const float4 *>(tws + (j % Ns) * TWROW);
+                Cx w[Rs];
+                twiddle_set<Rs>(w4, w);
 #pragma unroll
-                for (int h = 0; h < Rs / 2; ++h) {
-                    const float4 q = TWS ? lds_f4(w4 + h) : __ldg(w4 + h);
-                    const Cx w0 = make_float2(q.x, q.y), w1 = make_float2(q.z, q.w);
-                    if (h > 0) {
-                        va[b * Rs + 2 * h] = INV ? cmulc(va[b * Rs + 2 * h], w0) : cmul(va[b * Rs + 2 * h], w0);
-                        if constexpr (NOPS == 2)
-                            vb[b * Rs + 2 * h] = INV ? cmulc(vb[b * Rs + 2 * h], w0) : cmul(vb[b * Rs + 2 * h], w0);
-                    }
-                    va[b * Rs + 2 * h + 1] = INV ? cmulc(va[b * Rs + 2 * h + 1], w1) : cmul(va[b * Rs + 2 * h + 1], w1);
-                    if constexpr (NOPS == 2)
-                        vb[b * Rs + 2 * h + 1] = INV ? cmulc(vb[b * Rs + 2 * h + 1], w1) : cmul(vb[b * Rs + 2 * h + 1], w1);
+                for (int r = 1; r < Rs; ++r) {
+                    va[b * Rs + r] = INV ? cmulc(va[b * Rs + r], w[r]) : cmul(va[b * Rs + r], w[r]);
+                    if constexpr (NOPS == 2) vb[b * Rs + r] = INV ? cmulc(vb[b * Rs + r], w[r]) : cmul(vb[b * Rs + r], w[r]);
                 }
                 dft<Rs, false, SS == S - 1>(va + b * Rs);
                 if constexpr (NOPS == 2) dft<Rs, false, SS == S - 1>(vb + b * Rs);
