@@ -58,6 +58,35 @@ __device__ __forceinline__ float et_rcp(float x)
     return r;
 }
 
+// Twiddles of one radix-R butterfly from its table row [k][0..R) applied to
+// v[1..R) (conjugated with CONJ): for R = 8 two 16-byte loads give w, w^2,
+// w^3 and the rest are products of them (two roundings deep), instead of four
+// loads.
+template <int R, bool CONJ>
+__device__ __forceinline__ void et_twiddle(float2 *v, const float4 *w4)
+{
+    float2 w[R];
+    if constexpr (R == 8) {
+        const float4 q0 = __ldg(w4), q1 = __ldg(w4 + 1);
+        w[1] = make_float2(q0.z, q0.w);
+        w[2] = make_float2(q1.x, q1.y);
+        w[3] = make_float2(q1.z, q1.w);
+        w[4] = cmul(w[2], w[2]);
+        w[5] = cmul(w[2], w[3]);
+        w[6] = cmul(w[3], w[3]);
+        w[7] = cmul(w[3], w[4]);
+    } else {
+#pragma unroll
+        for (int h = 0; h < R / 2; ++h) {
+            const float4 q = __ldg(w4 + h);
+            w[2 * h] = make_float2(q.x, q.y);
+            w[2 * h + 1] = make_float2(q.z, q.w);
+        }
+    }
+#pragma unroll
+    for (int r = 1; r < R; ++r) v[r] = CONJ ? cmulc(v[r], w[r]) : cmul(v[r], w[r]);
+}
+
 // FULL: n_eps == L (no energy padding; occupied rows n < L/2).  GEN: A is
 // generated (else read from the caller's A_in).
 // Tile function: tile `tile` holds lines [32 tile, 32 tile + 32); smem: the
@@ -137,13 +166,7 @@ __device__ __forceinline__ void energy_fwd_warp_tile(const Geom &g, const Band &
             const int pj = et_pad(j);
 #pragma unroll
             for (int r = 0; r < R1; ++r) v[b * R1 + r] = sm[pj + et_pad(r * (L / R1))];
-            const float4 *w4 = reinterpret_cast<const float4 *>(tw1 + (j % N1) * R1);
-#pragma unroll
-            for (int h = 0; h < R1 / 2; ++h) {
-                const float4 q = __ldg(w4 + h);
-                if (h > 0) v[b * R1 + 2 * h] = cmul(v[b * R1 + 2 * h], make_float2(q.x, q.y));
-                v[b * R1 + 2 * h + 1] = cmul(v[b * R1 + 2 * h + 1], make_float2(q.z, q.w));
-            }
+            et_twiddle<R1, false>(v + b * R1, reinterpret_cast<const float4 *>(tw1 + (j % N1) * R1));
             Dft<R1, false, float2>::run(v + b * R1);
         }
         // exchange 2 (outputs at (j / N1) N2 + j % N1 + r N1) and stage 2:
@@ -165,13 +188,7 @@ __device__ __forceinline__ void energy_fwd_warp_tile(const Geom &g, const Band &
             const int pj = et_pad(j2[b]);
 #pragma unroll
             for (int r = 0; r < R2; ++r) v[b * R2 + r] = sm[pj + et_pad(r * (L / 8))];
-            const float4 *w4 = reinterpret_cast<const float4 *>(tw2 + j2[b] * R2);   // j < N2
-#pragma unroll
-            for (int h = 0; h < R2 / 2; ++h) {
-                const float4 q = __ldg(w4 + h);
-                if (h > 0) v[b * R2 + 2 * h] = cmul(v[b * R2 + 2 * h], make_float2(q.x, q.y));
-                v[b * R2 + 2 * h + 1] = cmul(v[b * R2 + 2 * h + 1], make_float2(q.z, q.w));
-            }
+            et_twiddle<R2, false>(v + b * R2, reinterpret_cast<const float4 *>(tw2 + j2[b] * R2));   // j < N2
             Dft<R2, false, float2>::run(v + b * R2);
         }
 

@@ -255,6 +255,31 @@ template <bool INV, typename C, bool PK> struct Dft<16, INV, C, PK> {
     }
 };
 
+// The twiddles w^r = tw[r m], r < R, of one butterfly from the length-L table
+// (m = k L / (Ns R)): for R = 8 and 16 only w, w^2 and w^3 are loaded and the
+// others formed as products of them (at most four roundings deep), instead of
+// R - 1 loads.
+template <int R, typename Cx>
+__device__ __forceinline__ void stage_twiddles(const Cx *__restrict__ tw, int m, Cx *w)
+{
+    if constexpr (R == 8 || R == 16) {
+        w[1] = __ldg(&tw[m]);
+        w[2] = __ldg(&tw[2 * m]);
+        w[3] = __ldg(&tw[3 * m]);
+        w[4] = cmul(w[2], w[2]);
+        w[5] = cmul(w[2], w[3]);
+        w[6] = cmul(w[3], w[3]);
+        w[7] = cmul(w[3], w[4]);
+        if constexpr (R == 16) {
+#pragma unroll
+            for (int r = 8; r < 16; ++r) w[r] = cmul(w[r / 2], w[r - r / 2]);
+        }
+    } else {
+#pragma unroll
+        for (int r = 1; r < R; ++r) w[r] = __ldg(&tw[r * m]);
+    }
+}
+
 enum { MAP_COL = 0, MAP_LINE = 1 };
 
 // ---------------------------------------------------------------------------
@@ -329,11 +354,10 @@ struct Fft {
                 for (int r = 0; r < Rs; ++r) v[b * Rs + r] = sm[saddr(col, j + r * (L / Rs))];
                 int k = j % Ns;
                 // twiddle exp(-+ 2 pi i k r / (Ns Rs)) from the length-L table exp(-2 pi i n / L)
+                Cx w[Rs];
+                stage_twiddles<Rs>(tw, k * (L / (Ns * Rs)), w);
 #pragma unroll
-                for (int r = 1; r < Rs; ++r) {
-                    Cx w = __ldg(&tw[k * r * (L / (Ns * Rs))]);
-                    v[b * Rs + r] = INV ? cmulc(v[b * Rs + r], w) : cmul(v[b * Rs + r], w);
-                }
+                for (int r = 1; r < Rs; ++r) v[b * Rs + r] = INV ? cmulc(v[b * Rs + r], w[r]) : cmul(v[b * Rs + r], w[r]);
                 Dft<Rs, INV, Cx>::run(v + b * Rs);
             }
             __syncthreads();
@@ -445,11 +469,12 @@ struct FftPair {
 #pragma unroll
                 for (int r = 0; r < Rs; ++r) ld2(sm, j + r * (L / Rs), p, va[b * Rs + r], vb[b * Rs + r]);
                 int k = j % Ns;
+                Cx w[Rs];
+                stage_twiddles<Rs>(tw, k * (L / (Ns * Rs)), w);
 #pragma unroll
                 for (int r = 1; r < Rs; ++r) {
-                    Cx w = __ldg(&tw[k * r * (L / (Ns * Rs))]);
-                    va[b * Rs + r] = INV ? cmulc(va[b * Rs + r], w) : cmul(va[b * Rs + r], w);
-                    vb[b * Rs + r] = INV ? cmulc(vb[b * Rs + r], w) : cmul(vb[b * Rs + r], w);
+                    va[b * Rs + r] = INV ? cmulc(va[b * Rs + r], w[r]) : cmul(va[b * Rs + r], w[r]);
+                    vb[b * Rs + r] = INV ? cmulc(vb[b * Rs + r], w[r]) : cmul(vb[b * Rs + r], w[r]);
                 }
                 Dft<Rs, INV, Cx, PK>::run(va + b * Rs);
                 Dft<Rs, INV, Cx, PK>::run(vb + b * Rs);
