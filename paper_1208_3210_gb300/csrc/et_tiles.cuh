@@ -19,8 +19,9 @@ __host__ __device__ constexpr int et_ns(int L, int s, bool inv = false)
 {
     return s == 0 ? 1 : et_ns(L, s - 1, inv) * et_radix(L, s - 1, inv);
 }
-// per-stage twiddle tables [k][Rs], k < Ns, exp(-2 pi i k r / (Ns Rs)), of
-// stages 1 and 2 of each schedule: forward 128, 256, 512, then inverse
+// per-stage twiddle tables, rows [k], k < Ns, of Rs entries w^1, ...,
+// w^(Rs-1), w^0, w = exp(-2 pi i k / (Ns Rs)), of stages 1 and 2 of each
+// schedule: forward 128, 256, 512, then inverse
 __host__ __device__ constexpr int et_table_offset(int L, int s, bool inv = false)
 {
     int o = 0;
@@ -58,30 +59,23 @@ __device__ __forceinline__ float et_rcp(float x)
     return r;
 }
 
-// Twiddles of one radix-R butterfly from its table row [k][0..R) applied to
-// v[1..R) (conjugated with CONJ): for R = 8 two 16-byte loads give w, w^2,
-// w^3 and the rest are products of them (two roundings deep), instead of four
-// loads.
+// Twiddles of one radix-R butterfly from its table row (w^1, ..., w^(R-1),
+// w^0) applied to v[1..R) (conjugated with CONJ): one 16-byte load gives w and
+// w^2, the other powers are products of them (at most two roundings deep).
 template <int R, bool CONJ>
 __device__ __forceinline__ void et_twiddle(float2 *v, const float4 *w4)
 {
+    static_assert(R == 4 || R == 8, "radices of the energy schedules");
     float2 w[R];
+    const float4 q0 = __ldg(w4);
+    w[1] = make_float2(q0.x, q0.y);
+    w[2] = make_float2(q0.z, q0.w);
+    w[3] = cmul(w[1], w[2]);
     if constexpr (R == 8) {
-        const float4 q0 = __ldg(w4), q1 = __ldg(w4 + 1);
-        w[1] = make_float2(q0.z, q0.w);
-        w[2] = make_float2(q1.x, q1.y);
-        w[3] = make_float2(q1.z, q1.w);
         w[4] = cmul(w[2], w[2]);
         w[5] = cmul(w[2], w[3]);
         w[6] = cmul(w[3], w[3]);
         w[7] = cmul(w[3], w[4]);
-    } else {
-#pragma unroll
-        for (int h = 0; h < R / 2; ++h) {
-            const float4 q = __ldg(w4 + h);
-            w[2 * h] = make_float2(q.x, q.y);
-            w[2 * h + 1] = make_float2(q.z, q.w);
-        }
     }
 #pragma unroll
     for (int r = 1; r < R; ++r) v[r] = CONJ ? cmulc(v[r], w[r]) : cmul(v[r], w[r]);
@@ -306,13 +300,7 @@ __device__ __forceinline__ void inv_energy_warp_tile(const Geom &g, const float2
             const int pj = et_pad(j);
 #pragma unroll
             for (int r = 0; r < R1; ++r) v[b * R1 + r] = sm[pj + et_pad(r * (L / R1))];
-            const float4 *w4 = reinterpret_cast<const float4 *>(tw1 + (j % N1) * R1);
-#pragma unroll
-            for (int h = 0; h < R1 / 2; ++h) {
-                const float4 q = __ldg(w4 + h);
-                if (h > 0) v[b * R1 + 2 * h] = cmulc(v[b * R1 + 2 * h], make_float2(q.x, q.y));
-                v[b * R1 + 2 * h + 1] = cmulc(v[b * R1 + 2 * h + 1], make_float2(q.z, q.w));
-            }
+            et_twiddle<R1, true>(v + b * R1, reinterpret_cast<const float4 *>(tw1 + (j % N1) * R1));
             Dft<R1, true, float2>::run(v + b * R1);
         }
         // exchange 2 (outputs at (j / N1) N2 + j % N1 + r N1) and stage 2
@@ -332,13 +320,7 @@ __device__ __forceinline__ void inv_energy_warp_tile(const Geom &g, const float2
             const int pj = et_pad(j);
 #pragma unroll
             for (int r = 0; r < R2; ++r) v[b * R2 + r] = sm[pj + et_pad(r * (L / R2))];
-            const float4 *w4 = reinterpret_cast<const float4 *>(tw2 + j * R2);   // j < N2
-#pragma unroll
-            for (int h = 0; h < R2 / 2; ++h) {
-                const float4 q = __ldg(w4 + h);
-                if (h > 0) v[b * R2 + 2 * h] = cmulc(v[b * R2 + 2 * h], make_float2(q.x, q.y));
-                v[b * R2 + 2 * h + 1] = cmulc(v[b * R2 + 2 * h + 1], make_float2(q.z, q.w));
-            }
+            et_twiddle<R2, true>(v + b * R2, reinterpret_cast<const float4 *>(tw2 + j * R2));   // j < N2
             Dft<R2, true, float2>::run(v + b * R2);
         }
         // outputs m = j + r L/R2; Re -> line 2f, Im -> line 2f + 1

@@ -256,24 +256,15 @@ template <bool INV, typename C, bool PK> struct Dft<16, INV, C, PK> {
 };
 
 // The twiddles w^r = tw[r m], r < R, of one butterfly from the length-L table
-// (m = k L / (Ns R)): for R = 8 and 16 only w, w^2 and w^3 are loaded and the
-// others formed as products of them (at most four roundings deep), instead of
-// R - 1 loads.
+// (m = k L / (Ns R)): for R = 2, 4, 8 and 16 only w is loaded and its powers
+// formed as products (at most four roundings deep), instead of R - 1 loads.
 template <int R, typename Cx>
 __device__ __forceinline__ void stage_twiddles(const Cx *__restrict__ tw, int m, Cx *w)
 {
-    if constexpr (R == 8 || R == 16) {
+    if constexpr (R == 2 || R == 4 || R == 8 || R == 16) {
         w[1] = __ldg(&tw[m]);
-        w[2] = __ldg(&tw[2 * m]);
-        w[3] = __ldg(&tw[3 * m]);
-        w[4] = cmul(w[2], w[2]);
-        w[5] = cmul(w[2], w[3]);
-        w[6] = cmul(w[3], w[3]);
-        w[7] = cmul(w[3], w[4]);
-        if constexpr (R == 16) {
 #pragma unroll
-            for (int r = 8; r < 16; ++r) w[r] = cmul(w[r / 2], w[r - r / 2]);
-        }
+        for (int r = 2; r < R; ++r) w[r] = cmul(w[r / 2], w[r - r / 2]);
     } else {
 #pragma unroll
         for (int r = 1; r < R; ++r) w[r] = __ldg(&tw[r * m]);

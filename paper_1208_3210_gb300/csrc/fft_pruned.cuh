@@ -45,9 +45,10 @@ __host__ __device__ constexpr int pr_ns(int L, int s, bool inv)
     return s == 0 ? 1 : pr_ns(L, s - 1, inv) * pr_radix(L, s - 1, inv);
 }
 
-// Per-stage twiddle tables: for stage s >= 1 of a schedule, entries [k][r],
-// k < Ns, r < Rs, value exp(-2 pi i k r / (Ns Rs)) (forward sign; the inverse
-// engine multiplies by the conjugate).  Tables of L in {192, 384, 768, 1536},
+// Per-stage twiddle tables: for stage s >= 1 of a schedule, rows [k], k < Ns,
+// of Rs entries w^1, w^2, ..., w^(Rs-1), w^0, w = exp(-2 pi i k / (Ns Rs))
+// (forward sign; the inverse engine multiplies by the conjugate): a butterfly's
+// w and w^2 are one 16-byte load.  Tables of L in {192, 384, 768, 1536},
 // forward then inverse schedule, stages in order, back to back.
 __host__ __device__ constexpr int pr_len_index(int L) { return L == 192 ? 0 : L == 384 ? 1 : L == 768 ? 2 : 3; }
 __host__ __device__ constexpr int pr_len_of(int i) { return 192 << i; }
@@ -214,43 +215,37 @@ struct PrEng {
 
     __device__ __forceinline__ static float4 tw_ld(const float4 *p) { return TWS ? lds_f4(p) : __ldg(p); }
     // The twiddles w^r, r < R, of one butterfly (w = exp(-2 pi i k / (Ns R))),
-    // from the table row [k][0..R): for R = 8 and 24 only some entries are
-    // loaded and the rest formed as products of them (at most three
-    // roundings deep, a few ulp): the 16-byte table loads, not the
-    // multiplications, were what the twiddles cost in these passes.
+    // from its table row (w^1, w^2, ..., w^(R-1), w^0): one 16-byte load gives
+    // w and w^2, the other powers are products (for R = 24 also w^7, w^8 and
+    // w^15, w^16 are loaded); at most three roundings deep, a few ulp.  The
+    // 16-byte table loads, not the multiplications, were what the twiddles
+    // cost in these passes.
     template <int R>
     __device__ __forceinline__ static void twiddle_set(const float4 *w4, Cx *w)
     {
         auto lo = [](float4 q) { return make_float2(q.x, q.y); };
         auto hi = [](float4 q) { return make_float2(q.z, q.w); };
-        if constexpr (R == 8 || R == 24) {
-            const float4 q0 = tw_ld(w4), q1 = tw_ld(w4 + 1);
-            w[1] = hi(q0);
-            w[2] = lo(q1);
-            w[3] = hi(q1);
+        static_assert(R == 4 || R == 8 || R == 24, "radices of the pruned schedules");
+        const float4 q0 = tw_ld(w4);
+        w[1] = lo(q0);
+        w[2] = hi(q0);
+        w[3] = cmul(w[1], w[2]);
+        if constexpr (R >= 8) {
             w[4] = cmul(w[2], w[2]);
             w[5] = cmul(w[2], w[3]);
             w[6] = cmul(w[3], w[3]);
-            w[7] = cmul(w[3], w[4]);
-            if constexpr (R == 24) {
-                const float4 q4 = tw_ld(w4 + 4), q8 = tw_ld(w4 + 8);
-                w[8] = lo(q4);
-                w[9] = hi(q4);
-                w[16] = lo(q8);
-                w[17] = hi(q8);
+        }
+        if constexpr (R == 8) w[7] = cmul(w[3], w[4]);
+        if constexpr (R == 24) {
+            const float4 q3 = tw_ld(w4 + 3), q7 = tw_ld(w4 + 7);
+            w[7] = lo(q3);
+            w[8] = hi(q3);
+            w[15] = lo(q7);
+            w[16] = hi(q7);
 #pragma unroll
-                for (int r = 2; r < 8; ++r) {
-                    w[8 + r] = cmul(w[8], w[r]);
-                    w[16 + r] = cmul(w[16], w[r]);
-                }
-            }
-        } else {
+            for (int r = 1; r < 7; ++r) w[8 + r] = cmul(w[8], w[r]);
 #pragma unroll
-            for (int h = 0; h < R / 2; ++h) {
-                const float4 q = tw_ld(w4 + h);
-                w[2 * h] = lo(q);
-                w[2 * h + 1] = hi(q);
-            }
+            for (int r = 1; r < 8; ++r) w[16 + r] = cmul(w[16], w[r]);
         }
     }
 

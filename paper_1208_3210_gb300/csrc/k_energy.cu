@@ -31,7 +31,8 @@ __global__ void k_et_twiddles(float2 *out)
         for (int s = 1; s <= 2; ++s) {
             const int off = et_table_offset(L, s, d != 0), n = et_ns(L, s + 1, d != 0), Rs = et_radix(L, s, d != 0);
             if (e >= off && e < off + n) {
-                const int k = (e - off) / Rs, r = (e - off) % Rs;
+                // row k holds w^1, ..., w^(Rs-1), w^0 (position p: power p + 1)
+                const int k = (e - off) / Rs, r = ((e - off) % Rs + 1) % Rs;
                 double sn, cs;
                 sincospi(-2.0 * (double)((k * r) % n) / (double)n, &sn, &cs);
                 out[e] = make_float2((float)cs, (float)sn);

@@ -95,8 +95,15 @@ k_inv_y2(Geom g, const cx<Real> *__restrict__ U3, cx<Real> *__restrict__ U4,
     }
 }
 
+// FP32, power-of-two lengths: at most 64 registers a thread (four 256-thread
+// CTAs per SM at L = 512): the pass waits on its loads, and resident warps are
+// what hides them (the FP64 and 3 * 2^k forms need more registers)
+template <typename Real, int L>
+struct InvEnergyBounds {
+    static constexpr int MINB = (sizeof(Real) == 4 && fft_len_pow2(L)) ? 65536 / (LineCfg<L>::T * 64) : 1;
+};
 template <typename Real, typename OutT, int L>
-__global__ void __launch_bounds__(LineCfg<L>::T)
+__global__ void __launch_bounds__(LineCfg<L>::T, InvEnergyBounds<Real, L>::MINB)
 k_inv_energy(Geom g, const cx<Real> *__restrict__ U4, OutT *__restrict__ out,
              const cx<Real> *__restrict__ tw)
 {

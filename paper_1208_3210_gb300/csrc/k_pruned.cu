@@ -27,7 +27,8 @@ __global__ void k_pr_twiddles(float2 *out)
                 const int off = pr_tables_before(li, d, s), n = pr_table_entries(L, d != 0, s);
                 if (e >= off && e < off + n) {
                     const int Rs = pr_radix(L, s, d != 0), NR = pr_ns(L, s + 1, d != 0);
-                    const int k = (e - off) / Rs, r = (e - off) % Rs;
+                    // row k holds w^1, w^2, ..., w^(Rs-1), w^0 (position p: power p + 1)
+                    const int k = (e - off) / Rs, r = ((e - off) % Rs + 1) % Rs;
                     double sn, cs;
                     sincospi(-2.0 * (double)((k * r) % NR) / (double)NR, &sn, &cs);
                     out[e] = make_float2((float)cs, (float)sn);
