@@ -37,7 +37,7 @@ __host__ __device__ constexpr int et_twiddle_entries() { return et_table_offset(
 
 // Per warp: ET_LPW lines, LPI = 32 / TPL at a time (TPL = L/16 threads per
 // line); shared memory per warp LPI lines of L + L/16 values.
-constexpr int ET_LPW = 4, ET_WARPS = 8;
+constexpr int ET_LPW = 16, ET_WARPS = 4;
 template <int L>
 struct EtGeo {
     static constexpr int TPL = L / 16, LPI = 32 / TPL, LP = L + L / 16;

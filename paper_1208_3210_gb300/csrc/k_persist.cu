@@ -27,7 +27,12 @@ __host__ __device__ constexpr int cmax(int a, int b) { return a > b ? a : b; }
 
 constexpr int PS_T = 256;
 constexpr int PS_PASSES = 5;
-constexpr int PS_EG = 8;   // energy-pass tiles per queue item
+constexpr int PS_EG = 2;   // energy-pass units per queue item
+// An energy unit is what the CTA's PS_EW warps cover in one call of an energy
+// tile function: PS_EW / ET_WARPS consecutive tiles (the tile functions place
+// warp w at line (tile ET_WARPS + w) ET_LPW, so warps past ET_WARPS take the
+// next tiles' lines).
+constexpr int PS_EW = PS_T / 32;
 
 // Per-instance constants of a persistent plan (device array).
 struct PInst {
@@ -53,17 +58,23 @@ struct PsCfg {
                                           PrEng<P, CW, PS_T, true, 2, false, true>::SMEM_ELEMS),
                                      PrProduct<P, CW, PS_T>::SMEM_ELEMS);
 };
+static_assert(PS_EW % ET_WARPS == 0, "whole energy tiles per unit");
+// shared memory of the energy tiles for all PS_EW warps of the CTA
+__host__ __device__ constexpr int ps_energy_smem_elems()
+{
+    return (PS_EW / ET_WARPS) * cmax(ET_WARPS * EtGeo<512>::WARP_ELEMS, et_inv_smem_elems<512>());
+}
 __host__ __device__ constexpr int ps_smem_elems()
 {
     return cmax(cmax(cmax(PsCfg<192>::SMEM, PsCfg<384>::SMEM), cmax(PsCfg<768>::SMEM, PsCfg<1536>::SMEM)),
-                cmax(ET_WARPS * EtGeo<512>::WARP_ELEMS, et_inv_smem_elems<512>()));
+                ps_energy_smem_elems());
 }
 // shared memory a plan's launch needs: the largest tile of its instances
 int ps_inst_smem_elems(const Geom &g)
 {
     const int pr = g.P == 192 ? PsCfg<192>::SMEM : g.P == 384 ? PsCfg<384>::SMEM
                  : g.P == 768 ? PsCfg<768>::SMEM : PsCfg<1536>::SMEM;
-    return cmax(pr, cmax(ET_WARPS * EtGeo<512>::WARP_ELEMS, et_inv_smem_elems<512>()));
+    return cmax(pr, ps_energy_smem_elems());
 }
 size_t ps_smem_bytes() { return sizeof(float2) * ps_smem_elems(); }
 
@@ -76,7 +87,7 @@ bool ps_supported(const Geom &g)
 void ps_tiles(const Geom &g, int *ntiles, int *gx)
 {
     const int CW = 6144 / g.P;
-    const long long per = (long long)ET_WARPS * ET_LPW;
+    const long long per = (long long)PS_EW * ET_LPW;   // lines (pairs) of one energy unit
     gx[0] = gx[4] = 0;
     ntiles[0] = (int)(((long long)g.N * g.N + per * PS_EG - 1) / (per * PS_EG));
     gx[1] = (2 * g.SP + 2 * CW - 1) / (2 * CW);
@@ -237,18 +248,20 @@ k_persistent(const PInst *__restrict__ insts, const PSeg *__restrict__ segs, int
             const PInst &in = s_in;
             const int t = item - sg.start;
             switch (sg.pass) {
-            // an item of an energy pass is PS_EG consecutive tiles (short
+            // an item of an energy pass is PS_EG consecutive units (short
             // tiles; the per-item bookkeeping would not pay for itself)
             case 0:
 #pragma unroll 1
-                for (int u = 0; u < PS_EG; ++u) ps_energy_fwd(in, (long long)t * PS_EG + u, etw, sm);
+                for (int u = 0; u < PS_EG; ++u)
+                    ps_energy_fwd(in, ((long long)t * PS_EG + u) * (PS_EW / ET_WARPS), etw, sm);
                 break;
             case 1: ps_fwd_y(in, t, ptw, sm); break;
             case 2: ps_product(in, t, ptw, sm); break;
             case 3: ps_inv_y(in, t, ptw, sm); break;
             default:
 #pragma unroll 1
-                for (int u = 0; u < PS_EG; ++u) ps_energy_inv(in, (long long)t * PS_EG + u, out, etw, sm);
+                for (int u = 0; u < PS_EG; ++u)
+                    ps_energy_inv(in, ((long long)t * PS_EG + u) * (PS_EW / ET_WARPS), out, etw, sm);
                 break;
             }
             __syncthreads();   // every thread's writes of the tile before thread 0 counts it
