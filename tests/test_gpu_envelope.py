@@ -6,7 +6,8 @@ take the same zone decisions, so the zone maxima must agree exactly; k0 agrees
 to 1e-6 (the two sum the cost in different orders, and near its flat minimum
 the golden-section comparisons can then go either way, which moves k0 by about
 the square root of the FP64 rounding, 1e-8); against the oracle's direct-sum Im chi the
-zone maxima agree within the FP32 bar.
+zone maxima agree within the FP32 bar.  On a synthetic cut with an exact
+Lorentzian envelope the library recovers its k0.
 """
 import numpy as np
 import pytest
@@ -78,6 +79,36 @@ def test_envelope_against_the_direct_sum(lh):
         assert np.abs(zmax - zmax_ref).max() <= tol
         assert np.all(picked >= zmax_ref - 2 * tol)
     plan.close()
+
+
+@pytest.mark.parametrize("k", [1.3, 4.0, 11.0])
+def test_envelope_recovers_a_lorentzian_envelope_on_the_gpu(lh, k):
+    """The library's fit on a synthetic cut whose zone maxima lie exactly on
+    1 / (1 + (q/k)^2) (the oracle's own pin, Sec. 4 Fig. 5), written straight
+    into an output buffer of a 16-zone, 32-point plan: k comes back to the FP32
+    rounding of the cut values, the zone maxima sit at the zone centres, and
+    the oracle fitting the same FP32 cut agrees."""
+    import math
+    import torch
+    Q, npz, m = 512, 32, 2
+    grid = wl.grid_params(16, npz, 16, 1.5, n_omega=4)
+    plan = lh.Plan([grid])
+    assert plan.sizes[0].q_extent == Q
+    dp = 2 * math.pi / npz
+    q = (np.arange(Q) - Q // 2) * dp
+    env = 1.0 / (1.0 + (q / k) ** 2)
+    centre = ((np.arange(Q) - Q // 2) % npz) == 0
+    im = np.zeros((Q, Q, grid["n_omega"]), dtype=np.float32)
+    im[:, Q // 2, m] = -np.where(centre, env, 0.05 * env)
+    im[:, : Q // 2, :] -= 3.0                                  # off the cut: ignored
+    out = torch.from_numpy(im.reshape(-1)).cuda()
+    k0, qs, ys = plan.envelope_k0(out, m)
+    plan.close()
+    assert abs(k0 - k) <= 1e-5 * k, (k0, k)
+    assert np.allclose(qs, 2 * math.pi * np.arange(len(qs)))
+    k0_ref, qs_ref, ys_ref = oracle.envelope_k0(im, npz, m)
+    assert np.array_equal(qs, qs_ref) and np.allclose(ys, ys_ref, rtol=0, atol=1e-15)
+    assert abs(k0 - k0_ref) <= 1e-6 * k0_ref
 
 
 def test_envelope_argument_checks(lh):
