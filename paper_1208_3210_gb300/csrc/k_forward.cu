@@ -36,6 +36,26 @@ k_fwd_energy(Geom g, Band band, const AxisTab *__restrict__ axis,
     const long long nlines = (long long)g.N * g.N;
     const long long line0 = (long long)blockIdx.x * C;
 
+    if constexpr (THERMAL) {
+        // finite temperature (Appendix A, Eq. A1): the occupied part is A f, the
+        // empty part A (1 - f), f = 1 / (exp(x) + 1), x = e_n / kT; both weights
+        // from u = exp(-|x|) so that neither loses digits to 1 - f.  They depend
+        // on the energy only: tabulated once per CTA in the transform's shared
+        // memory (read before the transform writes it; barrier below) as
+        // (weight of the real part, weight of the imaginary part).
+        for (int n = threadIdx.x; n < L; n += T) {
+            Real x, u;
+            if constexpr (sizeof(Real) == 4) {
+                x = (Real)(2 * n + 1 - g.n_eps) * band.x_step;
+                u = expf(-fabsf(x));
+            } else {
+                x = (Real)(2 * n + 1 - g.n_eps) * (Real)band.x_step64;
+                u = exp(-fabs(x));
+            }
+            const Real big = (Real)1 / ((Real)1 + u), small = u * big;
+            sm[n] = x < 0 ? mk<Cx>(big, small) : mk<Cx>(small, big);
+        }
+    }
     if (A_in == nullptr && threadIdx.x < C) {
         // band energy xi_p = e0(p) - mu and |M(p)|^2 gamma / pi of this line's
         // momentum point (Eqs. 4-5)
@@ -90,19 +110,8 @@ k_fwd_energy(Geom g, Band band, const AxisTab *__restrict__ axis,
                 }
             }
             if constexpr (THERMAL) {
-                // finite temperature (Appendix A, Eq. A1): occupied part A f,
-                // empty part A (1 - f), f = 1 / (exp(x) + 1), x = e_n / kT, both
-                // from u = exp(-|x|) so that neither loses digits to 1 - f
-                Real x, u;
-                if constexpr (sizeof(Real) == 4) {
-                    x = (Real)(2 * n + 1 - g.n_eps) * band.x_step;
-                    u = expf(-fabsf(x));
-                } else {
-                    x = (Real)(2 * n + 1 - g.n_eps) * (Real)band.x_step64;
-                    u = exp(-fabs(x));
-                }
-                const Real big = (Real)1 / ((Real)1 + u), small = u * big;
-                v[b * E::R0 + r] = x < 0 ? mk<Cx>(A * big, A * small) : mk<Cx>(A * small, A * big);
+                const Cx wf = sm[n];   // the Fermi weights of energy n (table above)
+                v[b * E::R0 + r] = mk<Cx>(A * wf.x, A * wf.y);
             } else {
                 // occupied (e_n < 0) -> real part, empty -> imaginary part
                 v[b * E::R0 + r] = (n < g.J0) ? mk<Cx>(A, (Real)0) : mk<Cx>((Real)0, A);
@@ -110,6 +119,7 @@ k_fwd_energy(Geom g, Band band, const AxisTab *__restrict__ axis,
         }
     }
 
+    if constexpr (THERMAL) __syncthreads();   // the weight table is read: the transform may overwrite it
     E::run(v, sm, tw);
 
     // natural-order spectrum to shared memory, then separate a^ and b^
