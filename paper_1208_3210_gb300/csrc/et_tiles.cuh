@@ -7,45 +7,59 @@
 
 namespace lh {
 
+// Lengths of the warp-per-line passes: both directions for 128, 256 and 512
+// (16 values per thread); the forward pass also for 384 and 768 (24 values
+// per thread: the energy axes that finite temperature pads to 3 * 2^k).
 __host__ __device__ constexpr bool et_supported(int L) { return L == 128 || L == 256 || L == 512; }
-// Schedules: forward 128 = 4.4.8, 256 = 4.8.8, 512 = 8.8.8 (last radix 8);
-// inverse 128 = 8.4.4, 256 = 8.8.4, 512 = 8.8.8 (first radix 8)
+__host__ __device__ constexpr bool et_fwd_supported(int L) { return et_supported(L) || L == 384 || L == 768; }
+// Schedules: forward 128 = 4.4.8, 256 = 4.8.8, 512 = 8.8.8, 384 = 8.4.12,
+// 768 = 8.8.12; inverse 128 = 8.4.4, 256 = 8.8.4, 512 = 8.8.8 (first radix 8)
 __host__ __device__ constexpr int et_radix(int L, int s, bool inv = false)
 {
     return inv ? (s == 0 ? 8 : L == 512 ? 8 : L == 256 ? (s == 1 ? 8 : 4) : 4)
-               : (s == 2 ? 8 : L == 512 ? 8 : L == 256 ? (s == 0 ? 4 : 8) : 4);
+         : L == 768 ? (s == 2 ? 12 : 8)
+         : L == 384 ? (s == 0 ? 8 : s == 1 ? 4 : 12)
+                    : (s == 2 ? 8 : L == 512 ? 8 : L == 256 ? (s == 0 ? 4 : 8) : 4);
 }
 __host__ __device__ constexpr int et_ns(int L, int s, bool inv = false)
 {
     return s == 0 ? 1 : et_ns(L, s - 1, inv) * et_radix(L, s - 1, inv);
 }
+// the i-th length with tables in direction d (0 past the last)
+__host__ __device__ constexpr int et_len(int d, int i)
+{
+    return d == 0 ? (i == 0 ? 128 : i == 1 ? 256 : i == 2 ? 512 : i == 3 ? 384 : i == 4 ? 768 : 0)
+                  : (i == 0 ? 128 : i == 1 ? 256 : i == 2 ? 512 : 0);
+}
 // per-stage twiddle tables, rows [k], k < Ns, of Rs entries w^1, ...,
 // w^(Rs-1), w^0, w = exp(-2 pi i k / (Ns Rs)), of stages 1 and 2 of each
-// schedule: forward 128, 256, 512, then inverse
+// schedule: forward 128, 256, 512, 384, 768, then inverse 128, 256, 512
 __host__ __device__ constexpr int et_table_offset(int L, int s, bool inv = false)
 {
     int o = 0;
     for (int d = 0; d < 2; ++d)
-        for (int l = 128; l <= 512; l *= 2)
+        for (int i = 0; et_len(d, i) != 0; ++i)
             for (int st = 1; st <= 2; ++st) {
-                if (l == L && st == s && (d != 0) == inv) return o;
-                o += et_ns(l, st + 1, d != 0);
+                if (et_len(d, i) == L && st == s && (d != 0) == inv) return o;
+                o += et_ns(et_len(d, i), st + 1, d != 0);
             }
     return o;
 }
 __host__ __device__ constexpr int et_twiddle_entries() { return et_table_offset(0, 0); }
 
-// Per warp: ET_LPW lines, LPI = 32 / TPL at a time (TPL = L/16 threads per
-// line); shared memory per warp LPI lines of L + L/16 values.
+// Per warp: ET_LPW lines, LPI = 32 / TPL at a time (TPL = L / VPT threads per
+// line, VPT values per thread); shared memory per warp LPI lines of L + L/16
+// values.
 constexpr int ET_LPW = 16, ET_WARPS = 4;
 template <int L>
 struct EtGeo {
-    static constexpr int TPL = L / 16, LPI = 32 / TPL, LP = L + L / 16;
-    static constexpr int R0 = et_radix(L, 0), R1 = et_radix(L, 1), R2 = 8;
+    static constexpr int VPT = (L & (L - 1)) == 0 ? 16 : 24;
+    static constexpr int TPL = L / VPT, LPI = 32 / TPL, LP = L + L / 16;
+    static constexpr int R0 = et_radix(L, 0), R1 = et_radix(L, 1), R2 = et_radix(L, 2);
     static constexpr int N1 = et_ns(L, 1), N2 = et_ns(L, 2);
     static constexpr int WARP_ELEMS = LPI * LP;
-    static_assert(R0 * R1 * R2 == L && 16 % R0 == 0 && 16 % R1 == 0, "schedule");
-    static_assert((L / R1) % 16 == 0 && (L / 8) % 16 == 0 && N2 % 16 == 0 && ET_LPW % LPI == 0,
+    static_assert(R0 * R1 * R2 == L && VPT % R0 == 0 && VPT % R1 == 0 && VPT == 2 * R2, "schedule");
+    static_assert((L / R1) % 16 == 0 && (L / R2) % 16 == 0 && N2 % 16 == 0 && ET_LPW % LPI == 0,
                   "compile-time padded offsets");
 };
 __host__ __device__ constexpr int et_pad(int n) { return n + n / 16; }
@@ -61,40 +75,41 @@ __device__ __forceinline__ float et_rcp(float x)
 
 // Twiddles of one radix-R butterfly from its table row (w^1, ..., w^(R-1),
 // w^0) applied to v[1..R) (conjugated with CONJ): one 16-byte load gives w and
-// w^2, the other powers are products of them (at most two roundings deep).
+// w^2, the other powers are products of them (at most three roundings deep).
 template <int R, bool CONJ>
 __device__ __forceinline__ void et_twiddle(float2 *v, const float4 *w4)
 {
-    static_assert(R == 4 || R == 8, "radices of the energy schedules");
+    static_assert(R == 4 || R == 8 || R == 12, "radices of the energy schedules");
     float2 w[R];
     const float4 q0 = __ldg(w4);
     w[1] = make_float2(q0.x, q0.y);
     w[2] = make_float2(q0.z, q0.w);
     w[3] = cmul(w[1], w[2]);
-    if constexpr (R == 8) {
-        w[4] = cmul(w[2], w[2]);
-        w[5] = cmul(w[2], w[3]);
-        w[6] = cmul(w[3], w[3]);
-        w[7] = cmul(w[3], w[4]);
-    }
+#pragma unroll
+    for (int r = 4; r < R; ++r) w[r] = cmul(w[r / 2], w[r - r / 2]);   // w^4 = (w^2)^2, w^5 = w^2 w^3, ...
 #pragma unroll
     for (int r = 1; r < R; ++r) v[r] = CONJ ? cmulc(v[r], w[r]) : cmul(v[r], w[r]);
 }
 
 // FULL: n_eps == L (no energy padding; occupied rows n < L/2).  GEN: A is
-// generated (else read from the caller's A_in).
-// Tile function: tile `tile` holds lines [32 tile, 32 tile + 32); smem: the
-// tile's ET_WARPS * WARP_ELEMS values (shared by the kernel below and the
+// generated (else read from the caller's A_in).  THERMAL: the finite-
+// temperature weights (Appendix A, Eq. A1) instead of the T = 0 split: the
+// occupied part A f and the empty part A (1 - f) of energy n, with (weight of
+// the real part, weight of the imaginary part) read from wf[n] (a table the
+// caller fills; et_fermi_weights).
+// Tile function: tile `tile` holds lines [ET_WARPS ET_LPW tile, ...); smem:
+// the tile's ET_WARPS * WARP_ELEMS values (shared by the kernel below and the
 // persistent batch kernel of k_persist.cu).
-template <int L, bool FULL, bool GEN>
+template <int L, bool FULL, bool GEN, bool THERMAL = false>
 __device__ __forceinline__ void energy_fwd_warp_tile(const Geom &g, const Band &band, const AxisTab *__restrict__ axis,
                                                      const float2 *__restrict__ eps, const InstState *__restrict__ st,
                                                      const float *__restrict__ A_in, float2 *__restrict__ U1,
-                                                     const float2 *__restrict__ etw, float2 *smem, long long tile)
+                                                     const float2 *__restrict__ etw, float2 *smem, long long tile,
+                                                     const float2 *wf = nullptr)
 {
     using G = EtGeo<L>;
-    constexpr int TPL = G::TPL, LPI = G::LPI, LP = G::LP, R0 = G::R0, R1 = G::R1, R2 = G::R2;
-    constexpr int N1 = G::N1, N2 = G::N2;
+    constexpr int VPT = G::VPT, TPL = G::TPL, LPI = G::LPI, LP = G::LP, R0 = G::R0, R1 = G::R1, R2 = G::R2;
+    constexpr int N1 = G::N1, N2 = G::N2, NB2 = L / R2;   // butterflies of the last stage
     const int lane = (int)threadIdx.x % 32, warp = (int)threadIdx.x / 32;
     const int sl = lane / TPL, u = lane % TPL;
     float2 *sm = smem + warp * G::WARP_ELEMS + sl * LP;
@@ -122,9 +137,9 @@ __device__ __forceinline__ void energy_fwd_warp_tile(const Geom &g, const Band &
         const float amp = __shfl_sync(0xffffffffu, ba, it + sl);
 
         // stage 0: butterflies j = u + b TPL, rows j + r L/R0
-        float2 v[16];
+        float2 v[VPT];
 #pragma unroll
-        for (int b = 0; b < 16 / R0; ++b) {
+        for (int b = 0; b < VPT / R0; ++b) {
             const int j = u + b * TPL;
 #pragma unroll
             for (int r = 0; r < R0; ++r) {
@@ -138,16 +153,21 @@ __device__ __forceinline__ void energy_fwd_warp_tile(const Geom &g, const Band &
                 } else {
                     A = (live && (FULL || n < g.n_eps)) ? 0.5f * A_in[line * g.n_eps + n] : 0.f;
                 }
-                // occupied (e_n < 0) -> real part, empty -> imaginary part
-                const bool occ = FULL ? (r < R0 / 2) : (2 * n + 1 < g.n_eps);
-                v[b * R0 + r] = occ ? make_float2(A, 0.f) : make_float2(0.f, A);
+                if constexpr (THERMAL) {
+                    const float2 w = wf[n];
+                    v[b * R0 + r] = make_float2(A * w.x, A * w.y);
+                } else {
+                    // occupied (e_n < 0) -> real part, empty -> imaginary part
+                    const bool occ = FULL ? (r < R0 / 2) : (2 * n + 1 < g.n_eps);
+                    v[b * R0 + r] = occ ? make_float2(A, 0.f) : make_float2(0.f, A);
+                }
             }
             Dft<R0, false, float2>::run(v + b * R0);
         }
         // exchange 1 (outputs at j R0 + r) and stage 1: butterflies u + b TPL
         __syncwarp();
 #pragma unroll
-        for (int b = 0; b < 16 / R0; ++b) {
+        for (int b = 0; b < VPT / R0; ++b) {
             const int base = (u + b * TPL) * R0;
             const int pb = base + base / 16;
 #pragma unroll
@@ -155,7 +175,7 @@ __device__ __forceinline__ void energy_fwd_warp_tile(const Geom &g, const Band &
         }
         __syncwarp();
 #pragma unroll
-        for (int b = 0; b < 16 / R1; ++b) {
+        for (int b = 0; b < VPT / R1; ++b) {
             const int j = u + b * TPL;
             const int pj = et_pad(j);
 #pragma unroll
@@ -164,11 +184,11 @@ __device__ __forceinline__ void energy_fwd_warp_tile(const Geom &g, const Band &
             Dft<R1, false, float2>::run(v + b * R1);
         }
         // exchange 2 (outputs at (j / N1) N2 + j % N1 + r N1) and stage 2:
-        // butterflies u and L/8 - u (u = 0: 0 and L/16), so that Z(k) and
-        // Z(L - k) end in the same thread
+        // butterflies u and NB2 - u (u = 0: 0 and NB2/2 = TPL), so that Z(k)
+        // and Z(L - k) end in the same thread
         __syncwarp();
 #pragma unroll
-        for (int b = 0; b < 16 / R1; ++b) {
+        for (int b = 0; b < VPT / R1; ++b) {
             const int j = u + b * TPL;
             const int base = (j / N1) * N2 + j % N1;   // base % 16 = j % N1 < N1
             const int pb = base + base / 16;
@@ -176,19 +196,19 @@ __device__ __forceinline__ void energy_fwd_warp_tile(const Geom &g, const Band &
             for (int r = 0; r < R1; ++r) sm[pb + r * N1 + (r * N1) / 16] = v[b * R1 + r];
         }
         __syncwarp();
-        const int j2[2] = {u, u == 0 ? TPL : L / 8 - u};
+        const int j2[2] = {u, u == 0 ? TPL : NB2 - u};
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
             const int pj = et_pad(j2[b]);
 #pragma unroll
-            for (int r = 0; r < R2; ++r) v[b * R2 + r] = sm[pj + et_pad(r * (L / 8))];
+            for (int r = 0; r < R2; ++r) v[b * R2 + r] = sm[pj + et_pad(r * NB2)];
             et_twiddle<R2, false>(v + b * R2, reinterpret_cast<const float4 *>(tw2 + j2[b] * R2));   // j < N2
             Dft<R2, false, float2>::run(v + b * R2);
         }
 
-        // Z(j + r L/8) in v[b 8 + r]; the partner Z(L - k) of (j2[0], r) is
-        // (j2[1], 7 - r) for u > 0; of (0, r) it is (0, 8 - r), of (L/16, r)
-        // it is (L/16, 7 - r)
+        // Z(j + r NB2) in v[b R2 + r]; the partner Z(L - k) of (j2[0], r) is
+        // (j2[1], R2 - 1 - r) for u > 0; of (0, r) it is (0, R2 - r), of
+        // (NB2/2, r) it is (NB2/2, R2 - 1 - r)
         if (live) {
             float2 *row = U1 + line * (2LL * g.SP);
             // a^ = (Z(k) + conj Z(-k)) / 2, b^ = (Z(k) - conj Z(-k)) / 2i, the
@@ -198,13 +218,29 @@ __device__ __forceinline__ void energy_fwd_warp_tile(const Geom &g, const Band &
             };
             const bool u0 = u == 0;
 #pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                put(j2[0] + r * (L / 8), v[r], u0 ? v[(8 - r) & 7] : v[8 + 7 - r]);
-                put(j2[1] + r * (L / 8), v[8 + r], u0 ? v[8 + 7 - r] : v[7 - r]);
+            for (int r = 0; r < R2 / 2; ++r) {
+                put(j2[0] + r * NB2, v[r], u0 ? v[(R2 - r) % R2] : v[R2 + R2 - 1 - r]);
+                put(j2[1] + r * NB2, v[R2 + r], u0 ? v[R2 + R2 - 1 - r] : v[R2 - 1 - r]);
             }
-            if (u0) put(L / 2, v[4], v[4]);
+            if (u0) put(L / 2, v[R2 / 2], v[R2 / 2]);
         }
         __syncwarp();   // the next line's exchange overwrites this one's
+    }
+}
+
+// The finite-temperature weights of energy n < L (Appendix A, Eq. A1) into
+// wf[n] = (f, 1 - f), f = 1 / (exp(x) + 1), x = e_n / kT =
+// (2 n + 1 - n_eps) x_step (the occupied weight multiplies the real part, the
+// empty one the imaginary part), both from u = exp(-|x|) so that neither loses
+// digits to 1 - f.  Entries t0, t0 + stride, ...
+template <int L>
+__device__ __forceinline__ void et_fermi_weights(const Geom &g, const Band &band, float2 *wf, int t0, int stride)
+{
+    for (int n = t0; n < L; n += stride) {
+        const float x = (float)(2 * n + 1 - g.n_eps) * band.x_step;
+        const float u = expf(-fabsf(x));
+        const float big = 1.f / (1.f + u), small = u * big;
+        wf[n] = x < 0 ? make_float2(big, small) : make_float2(small, big);
     }
 }
 

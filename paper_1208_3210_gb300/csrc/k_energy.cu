@@ -27,8 +27,9 @@ __global__ void k_et_twiddles(float2 *out)
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= et_twiddle_entries()) return;
     for (int d = 0; d < 2; ++d)
-        for (int L = 128; L <= 512; L *= 2)
+        for (int i = 0; et_len(d, i) != 0; ++i)
         for (int s = 1; s <= 2; ++s) {
+            const int L = et_len(d, i);
             const int off = et_table_offset(L, s, d != 0), n = et_ns(L, s + 1, d != 0), Rs = et_radix(L, s, d != 0);
             if (e >= off && e < off + n) {
                 // row k holds w^1, ..., w^(Rs-1), w^0 (position p: power p + 1)
@@ -46,18 +47,30 @@ cudaError_t launch_et_twiddles(float2 *out, cudaStream_t s)
     return cudaGetLastError();
 }
 size_t et_twiddle_bytes() { return (size_t)et_twiddle_entries() * sizeof(float2); }
-bool et_applies(const Geom &g, const Band &band) { return et_supported(g.PE) && !(band.kT > 0); }
+// the warp-per-line forward pass: T = 0 at 128, 256 and 512 energies, finite
+// temperature (whose energy axes are padded to 3 * 2^k) also at 384 and 768
+bool et_applies(const Geom &g, const Band &band)
+{
+    return band.kT > 0 ? et_fwd_supported(g.PE) : et_supported(g.PE);
+}
 
-template <int L, bool FULL, bool GEN>
+// THERMAL: the CTA tabulates the Fermi weights of its energies once, after the
+// warps' exchange areas, before the tile
+template <int L, bool FULL, bool GEN, bool THERMAL>
 __global__ void __launch_bounds__(32 * ET_WARPS)
 k_fwd_energy_warp(Geom g, Band band, const AxisTab *__restrict__ axis, const float2 *__restrict__ eps,
                   const InstState *__restrict__ st, const float *__restrict__ A_in, float2 *__restrict__ U1,
                   const float2 *__restrict__ etw)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    LH_REQUIRE_SMEM(ET_WARPS * EtGeo<L>::WARP_ELEMS, float2)
-    energy_fwd_warp_tile<L, FULL, GEN>(g, band, axis, eps, st, A_in, U1, etw, reinterpret_cast<float2 *>(smem_raw),
-                                       blockIdx.x);
+    LH_REQUIRE_SMEM(ET_WARPS * EtGeo<L>::WARP_ELEMS + (THERMAL ? L : 0), float2)
+    float2 *sm = reinterpret_cast<float2 *>(smem_raw);
+    float2 *wf = sm + ET_WARPS * EtGeo<L>::WARP_ELEMS;
+    if constexpr (THERMAL) {
+        et_fermi_weights<L>(g, band, wf, (int)threadIdx.x, 32 * ET_WARPS);
+        __syncthreads();
+    }
+    energy_fwd_warp_tile<L, FULL, GEN, THERMAL>(g, band, axis, eps, st, A_in, U1, etw, sm, blockIdx.x, wf);
 }
 
 template <int L, bool HALF>
@@ -97,28 +110,37 @@ cudaError_t launch_inv_energy_warp(const Geom &g, const Work<float> &w, float *o
     }
 }
 
-template <int L>
-cudaError_t launch_fwd_energy_col_t(const Geom &g, const Band &band, const Work<float> &w, const float *A_in,
-                                    cudaStream_t s)
+template <int L, bool THERMAL>
+cudaError_t launch_fwd_energy_col_tt(const Geom &g, const Band &band, const Work<float> &w, const float *A_in,
+                                     cudaStream_t s)
 {
     const long long nlines = (long long)g.N * g.N;
     const long long per = (long long)ET_WARPS * ET_LPW;
     const unsigned grid = (unsigned)((nlines + per - 1) / per);
-    const size_t smem = sizeof(float2) * ET_WARPS * EtGeo<L>::WARP_ELEMS;
-    static const cudaError_t e0 = smem_attrs(k_fwd_energy_warp<L, true, true>, smem);
-    static const cudaError_t e1 = smem_attrs(k_fwd_energy_warp<L, false, true>, smem);
-    static const cudaError_t e2 = smem_attrs(k_fwd_energy_warp<L, true, false>, smem);
-    static const cudaError_t e3 = smem_attrs(k_fwd_energy_warp<L, false, false>, smem);
+    const size_t smem = sizeof(float2) * (ET_WARPS * EtGeo<L>::WARP_ELEMS + (THERMAL ? L : 0));
+    static const cudaError_t e0 = smem_attrs(k_fwd_energy_warp<L, true, true, THERMAL>, smem);
+    static const cudaError_t e1 = smem_attrs(k_fwd_energy_warp<L, false, true, THERMAL>, smem);
+    static const cudaError_t e2 = smem_attrs(k_fwd_energy_warp<L, true, false, THERMAL>, smem);
+    static const cudaError_t e3 = smem_attrs(k_fwd_energy_warp<L, false, false, THERMAL>, smem);
     if (e0 != cudaSuccess) return e0;
     if (e1 != cudaSuccess) return e1;
     if (e2 != cudaSuccess) return e2;
     if (e3 != cudaSuccess) return e3;
     const bool full = g.n_eps == L;
-    auto k = A_in ? (full ? k_fwd_energy_warp<L, true, false> : k_fwd_energy_warp<L, false, false>)
-                  : (full ? k_fwd_energy_warp<L, true, true> : k_fwd_energy_warp<L, false, true>);
+    auto k = A_in ? (full ? k_fwd_energy_warp<L, true, false, THERMAL> : k_fwd_energy_warp<L, false, false, THERMAL>)
+                  : (full ? k_fwd_energy_warp<L, true, true, THERMAL> : k_fwd_energy_warp<L, false, true, THERMAL>);
     k<<<grid, 32 * ET_WARPS, smem, s>>>(g, band, w.axis, (const float2 *)w.eps, w.state, A_in, (float2 *)w.X,
                                         (const float2 *)w.etw);
     return cudaGetLastError();
+}
+template <int L>
+cudaError_t launch_fwd_energy_col_t(const Geom &g, const Band &band, const Work<float> &w, const float *A_in,
+                                    cudaStream_t s)
+{
+    if constexpr (et_supported(L)) {
+        if (!(band.kT > 0)) return launch_fwd_energy_col_tt<L, false>(g, band, w, A_in, s);
+    }
+    return launch_fwd_energy_col_tt<L, true>(g, band, w, A_in, s);
 }
 
 cudaError_t launch_fwd_energy_col(const Geom &g, const Band &band, const Work<float> &w, const float *A_in,
@@ -129,6 +151,8 @@ cudaError_t launch_fwd_energy_col(const Geom &g, const Band &band, const Work<fl
     case 128: return launch_fwd_energy_col_t<128>(g, band, w, A_in, s);
     case 256: return launch_fwd_energy_col_t<256>(g, band, w, A_in, s);
     case 512: return launch_fwd_energy_col_t<512>(g, band, w, A_in, s);
+    case 384: return launch_fwd_energy_col_t<384>(g, band, w, A_in, s);
+    case 768: return launch_fwd_energy_col_t<768>(g, band, w, A_in, s);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -77,6 +77,40 @@ def test_thermal_against_oracle(lh, grid, band, kT, quantity):
         assert got.min() >= -TOL32 * np.abs(ref).max()      # S >= 0
 
 
+# energy FFT lengths that take the warp-per-line forward pass with the
+# Fermi-weight table: 128 (a power of two, padded), 384 and 768 (24 values a
+# thread); small momentum grids and few lags keep the oracle's direct sums short
+WARP_CASES = [
+    (wl.grid_params(2, 8, 100, 1.5, n_omega=20), 0.05, 128),
+    (wl.grid_params(2, 8, 256, 1.5, q_extent=12), 0.025, 384),
+    (wl.grid_params(2, 8, 512, 3.0, q_extent=8), 0.025, 768),
+]
+
+
+@pytest.mark.parametrize("quantity", [1, 2], ids=["imchi_T", "S"])
+@pytest.mark.parametrize("grid,kT,pe", WARP_CASES, ids=["PE128", "PE384", "PE768"])
+def test_thermal_warp_energy_lengths(lh, grid, kT, pe, quantity):
+    import torch
+    band = wl.band_params(filling=1.1, gamma=0.06, ff_a=0.8)
+    g = dict(grid, quantity=quantity)
+    got, fft_e = _gpu(lh, g, dict(band, kT=kT))
+    assert fft_e == pe
+    A = oracle.spectral(_solved(band, grid), grid)
+    ref = oracle.thermal_full(A, grid, grid["q_extent"], grid["n_omega"], kT, quantity)
+    err = np.abs(got - ref).max() / np.abs(ref).max()
+    print(f"PE {pe}, quantity {quantity}: {err:.2e} of max")
+    assert err <= TOL32
+    # the same grid with the spectral function supplied by the caller
+    N = grid["zones"] * grid["npz"]
+    Ar = np.random.default_rng(pe).random((N, N, grid["n_eps"]))
+    got_a, _ = _gpu(lh, g, dict(band, kT=kT), A_in=torch.tensor(Ar.ravel(), dtype=torch.float32, device="cuda"))
+    ref_a = oracle.thermal_full(Ar.astype(np.float32).astype(np.float64), grid, grid["q_extent"],
+                                grid["n_omega"], kT, quantity)
+    err_a = np.abs(got_a - ref_a).max() / np.abs(ref_a).max()
+    print(f"PE {pe}, quantity {quantity}, caller A: {err_a:.2e} of max")
+    assert err_a <= TOL32
+
+
 @pytest.mark.parametrize("quantity", [1, 2], ids=["imchi_T", "S"])
 def test_thermal_fp64(lh, quantity):
     grid, band, kT = CASES[0]
