@@ -387,7 +387,7 @@ lindhard_status lindhard_plan_set_wait_limit(lindhard_plan *plan, unsigned long 
  * tables in shared memory, P >= 384);
  * out[3] = the inverse energy
  * pass (0 default, 1 TMA-staged persistent form, 2 one warp per pair of
- * output lines, energy FFT lengths 128, 256 and 512).
+ * output lines, energy FFT lengths 128, 256, 512, 384 and 768).
  * out: host, int[4]. */
 lindhard_status lindhard_plan_variants(const lindhard_plan *plan, int index, int *out);
 

@@ -7,16 +7,19 @@
 
 namespace lh {
 
-// Lengths of the warp-per-line passes: both directions for 128, 256 and 512
-// (16 values per thread); the forward pass also for 384 and 768 (24 values
-// per thread: the energy axes that finite temperature pads to 3 * 2^k).
+// Lengths of the warp-per-line passes: 128, 256 and 512 (16 values per
+// thread; also the lengths of the persistent batch kernel) and 384 and 768
+// (24 values per thread: the energy axes that finite temperature pads to
+// 3 * 2^k).
 __host__ __device__ constexpr bool et_supported(int L) { return L == 128 || L == 256 || L == 512; }
-__host__ __device__ constexpr bool et_fwd_supported(int L) { return et_supported(L) || L == 384 || L == 768; }
+__host__ __device__ constexpr bool et_len_supported(int L) { return et_supported(L) || L == 384 || L == 768; }
 // Schedules: forward 128 = 4.4.8, 256 = 4.8.8, 512 = 8.8.8, 384 = 8.4.12,
-// 768 = 8.8.12; inverse 128 = 8.4.4, 256 = 8.8.4, 512 = 8.8.8 (first radix 8)
+// 768 = 8.8.12; inverse 128 = 8.4.4, 256 = 8.8.4, 512 = 8.8.8, 384 = 12.4.8,
+// 768 = 12.8.8 (the forward ones reversed for 384 and 768)
 __host__ __device__ constexpr int et_radix(int L, int s, bool inv = false)
 {
-    return inv ? (s == 0 ? 8 : L == 512 ? 8 : L == 256 ? (s == 1 ? 8 : 4) : 4)
+    return inv ? (L == 768 ? (s == 0 ? 12 : 8) : L == 384 ? (s == 0 ? 12 : s == 1 ? 4 : 8)
+                           : (s == 0 ? 8 : L == 512 ? 8 : L == 256 ? (s == 1 ? 8 : 4) : 4))
          : L == 768 ? (s == 2 ? 12 : 8)
          : L == 384 ? (s == 0 ? 8 : s == 1 ? 4 : 12)
                     : (s == 2 ? 8 : L == 512 ? 8 : L == 256 ? (s == 0 ? 4 : 8) : 4);
@@ -28,12 +31,11 @@ __host__ __device__ constexpr int et_ns(int L, int s, bool inv = false)
 // the i-th length with tables in direction d (0 past the last)
 __host__ __device__ constexpr int et_len(int d, int i)
 {
-    return d == 0 ? (i == 0 ? 128 : i == 1 ? 256 : i == 2 ? 512 : i == 3 ? 384 : i == 4 ? 768 : 0)
-                  : (i == 0 ? 128 : i == 1 ? 256 : i == 2 ? 512 : 0);
+    return i == 0 ? 128 : i == 1 ? 256 : i == 2 ? 512 : i == 3 ? 384 : i == 4 ? 768 : 0;
 }
 // per-stage twiddle tables, rows [k], k < Ns, of Rs entries w^1, ...,
 // w^(Rs-1), w^0, w = exp(-2 pi i k / (Ns Rs)), of stages 1 and 2 of each
-// schedule: forward 128, 256, 512, 384, 768, then inverse 128, 256, 512
+// schedule: forward 128, 256, 512, 384, 768, then inverse the same
 __host__ __device__ constexpr int et_table_offset(int L, int s, bool inv = false)
 {
     int o = 0;
@@ -255,20 +257,23 @@ __device__ __forceinline__ void et_fermi_weights(const Geom &g, const Band &band
 // k <= L/2 and forms both W(k) and W(L - k) = conj X1(k) + i conj X2(k).
 // HALF: n_omega == L/2 (the outputs of the last stage's first R2/2 rows).
 template <int L>
-constexpr int et_inv_smem_elems() { return ET_WARPS * (32 / (L / 16)) * (L + L / 16); }
-// Tile function (pairs [32 tile, 32 tile + 32)); COH: read U4 through L2 only
-// (written earlier in the same launch by other CTAs).
+__host__ __device__ constexpr int et_inv_smem_elems() { return ET_WARPS * EtGeo<L>::LPI * EtGeo<L>::LP; }
+// Tile function (pairs [ET_WARPS ET_LPW tile, ...)); COH: read U4 through L2
+// only (written earlier in the same launch by other CTAs).
 template <int L, bool HALF, bool COH>
 __device__ __forceinline__ void inv_energy_warp_tile(const Geom &g, const float2 *__restrict__ U4,
                                                      float *__restrict__ out, const float2 *__restrict__ etw,
                                                      float2 *smem, long long tile)
 {
-    constexpr int TPL = L / 16, LPI = 32 / TPL, LP = L + L / 16;
+    using G = EtGeo<L>;
+    constexpr int VPT = G::VPT, TPL = G::TPL, LPI = G::LPI, LP = G::LP;
     constexpr int R0 = et_radix(L, 0, true), R1 = et_radix(L, 1, true), R2 = et_radix(L, 2, true);
-    constexpr int N1 = et_ns(L, 1, true), N2 = et_ns(L, 2, true);
+    constexpr int N1 = et_ns(L, 1, true), N2 = et_ns(L, 2, true), NB0 = L / R0;   // first-stage butterflies
     constexpr int H = L / 2 + 1, SP = (H + 7) / 8 * 8;
-    static_assert(R0 == 8 && R0 * R1 * R2 == L && 16 % R1 == 0 && 16 % R2 == 0, "schedule");
-    static_assert((L / R1) % 16 == 0 && (L / R2) % 16 == 0 && ET_LPW % LPI == 0, "compile-time padded offsets");
+    static_assert(VPT == 2 * R0 && R0 * R1 * R2 == L && VPT % R1 == 0 && VPT % R2 == 0 && NB0 == 2 * TPL,
+                  "schedule");
+    static_assert((L / R1) % 16 == 0 && (L / R2) % 16 == 0 && N1 % 4 == 0 && ET_LPW % LPI == 0,
+                  "compile-time padded offsets");
     const int lane = (int)threadIdx.x % 32, warp = (int)threadIdx.x / 32;
     const int sl = lane / TPL, u = lane % TPL;
     float2 *sm = smem + (warp * LPI + sl) * LP;
@@ -276,62 +281,61 @@ __device__ __forceinline__ void inv_energy_warp_tile(const Geom &g, const float2
     const long long pair0 = (tile * ET_WARPS + warp) * ET_LPW;
     const float2 *tw1 = etw + et_table_offset(L, 1, true), *tw2 = etw + et_table_offset(L, 2, true);
     const float sc = (float)g.scale;
-    const int j0[2] = {u, u == 0 ? TPL : L / 8 - u};
+    const int j0[2] = {u, u == 0 ? TPL : NB0 - u};
 
     for (int it = 0; it < ET_LPW; it += LPI) {
         const long long f = pair0 + it + sl;
         const bool live = f < npairs;
         const float2 *row1 = U4 + (live ? 2 * f : 0) * SP, *row2 = row1 + SP;
-        // stage 0: rows j + r L/8 of butterflies j0[0] and j0[1]; the rows
+        // stage 0: rows j + r NB0 of butterflies j0[0] and j0[1]; the rows
         // above L/2 of one are the conjugate mirrors of the other's
-        float2 v[16];
+        float2 v[VPT];
         const float2 zero = make_float2(0.f, 0.f);
         auto ldx = [](const float2 *p) { return COH ? __ldcg(p) : __ldg(p); };
         auto w_of = [](float2 x1, float2 x2) { return make_float2(x1.x - x2.y, x1.y + x2.x); };       // X1 + i X2
         auto w_conj = [](float2 x1, float2 x2) { return make_float2(x1.x + x2.y, x2.x - x1.y); };     // conj X1 + i conj X2
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const float2 a1 = live ? ldx(row1 + j0[0] + r * (L / 8)) : zero;
-            const float2 a2 = live ? ldx(row2 + j0[0] + r * (L / 8)) : zero;
-            const float2 b1 = live ? ldx(row1 + j0[1] + r * (L / 8)) : zero;
-            const float2 b2 = live ? ldx(row2 + j0[1] + r * (L / 8)) : zero;
+        for (int r = 0; r < R0 / 2; ++r) {
+            const float2 a1 = live ? ldx(row1 + j0[0] + r * NB0) : zero;
+            const float2 a2 = live ? ldx(row2 + j0[0] + r * NB0) : zero;
+            const float2 b1 = live ? ldx(row1 + j0[1] + r * NB0) : zero;
+            const float2 b2 = live ? ldx(row2 + j0[1] + r * NB0) : zero;
             v[r] = w_of(a1, a2);
-            v[8 + r] = w_of(b1, b2);
-            // u > 0: L - (j0[0] + r L/8) = j0[1] + (7 - r) L/8 and the other way round
-            v[7 - r] = w_conj(b1, b2);
-            v[8 + 7 - r] = w_conj(a1, a2);
+            v[R0 + r] = w_of(b1, b2);
+            // u > 0: L - (j0[0] + r NB0) = j0[1] + (R0 - 1 - r) NB0 and the other way round
+            v[R0 - 1 - r] = w_conj(b1, b2);
+            v[R0 + R0 - 1 - r] = w_conj(a1, a2);
         }
         if (u == 0) {
-            // j0[0] = 0: rows r L/8 mirror (8 - r) L/8; row L/2 is its own mirror
+            // j0[0] = 0: rows r NB0 mirror (R0 - r) NB0; row L/2 is its own mirror
             const float2 c1 = live ? ldx(row1 + L / 2) : zero, c2 = live ? ldx(row2 + L / 2) : zero;
-            v[4] = w_of(c1, c2);
+            v[R0 / 2] = w_of(c1, c2);
 #pragma unroll
-            for (int r = 1; r < 4; ++r) {
-                const float2 x1 = live ? ldx(row1 + r * (L / 8)) : zero, x2 = live ? ldx(row2 + r * (L / 8)) : zero;
-                v[8 - r] = w_conj(x1, x2);
+            for (int r = 1; r < R0 / 2; ++r) {
+                const float2 x1 = live ? ldx(row1 + r * NB0) : zero, x2 = live ? ldx(row2 + r * NB0) : zero;
+                v[R0 - r] = w_conj(x1, x2);
             }
-            // j0[1] = L/16: rows L/16 + r L/8 mirror L/16 + (7 - r) L/8
+            // j0[1] = NB0/2: rows NB0/2 + r NB0 mirror NB0/2 + (R0 - 1 - r) NB0
 #pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const float2 x1 = live ? ldx(row1 + TPL + r * (L / 8)) : zero;
-                const float2 x2 = live ? ldx(row2 + TPL + r * (L / 8)) : zero;
-                v[8 + 7 - r] = w_conj(x1, x2);
+            for (int r = 0; r < R0 / 2; ++r) {
+                const float2 x1 = live ? ldx(row1 + TPL + r * NB0) : zero;
+                const float2 x2 = live ? ldx(row2 + TPL + r * NB0) : zero;
+                v[R0 + R0 - 1 - r] = w_conj(x1, x2);
             }
         }
-        Dft<8, true, float2>::run(v);
-        Dft<8, true, float2>::run(v + 8);
-        // exchange 1 (outputs at j 8 + r) and stage 1: butterflies u + b TPL
+        Dft<R0, true, float2>::run(v);
+        Dft<R0, true, float2>::run(v + R0);
+        // exchange 1 (outputs at j R0 + r) and stage 1: butterflies u + b TPL
         __syncwarp();
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
-            const int base = j0[b] * 8;
-            const int pb = base + base / 16;
+            const int base = j0[b] * R0;
 #pragma unroll
-            for (int r = 0; r < 8; ++r) sm[pb + r] = v[b * 8 + r];
+            for (int r = 0; r < R0; ++r) sm[et_pad(base + r)] = v[b * R0 + r];
         }
         __syncwarp();
 #pragma unroll
-        for (int b = 0; b < 16 / R1; ++b) {
+        for (int b = 0; b < VPT / R1; ++b) {
             const int j = u + b * TPL;
             const int pj = et_pad(j);
 #pragma unroll
@@ -342,16 +346,15 @@ __device__ __forceinline__ void inv_energy_warp_tile(const Geom &g, const float2
         // exchange 2 (outputs at (j / N1) N2 + j % N1 + r N1) and stage 2
         __syncwarp();
 #pragma unroll
-        for (int b = 0; b < 16 / R1; ++b) {
+        for (int b = 0; b < VPT / R1; ++b) {
             const int j = u + b * TPL;
-            const int base = (j / N1) * N2 + j % N1;   // base % 16 = j % 8 < 8
-            const int pb = base + base / 16;
+            const int base = (j / N1) * N2 + j % N1;
 #pragma unroll
-            for (int r = 0; r < R1; ++r) sm[pb + r * N1 + (r * N1) / 16] = v[b * R1 + r];
+            for (int r = 0; r < R1; ++r) sm[et_pad(base + r * N1)] = v[b * R1 + r];
         }
         __syncwarp();
 #pragma unroll
-        for (int b = 0; b < 16 / R2; ++b) {
+        for (int b = 0; b < VPT / R2; ++b) {
             const int j = u + b * TPL;
             const int pj = et_pad(j);
 #pragma unroll
@@ -363,7 +366,7 @@ __device__ __forceinline__ void inv_energy_warp_tile(const Geom &g, const float2
         if (live) {
             float *o1 = out + 2 * f * g.n_omega, *o2 = o1 + g.n_omega;
 #pragma unroll
-            for (int b = 0; b < 16 / R2; ++b) {
+            for (int b = 0; b < VPT / R2; ++b) {
                 const int j = u + b * TPL;
 #pragma unroll
                 for (int r = 0; r < (HALF ? R2 / 2 : R2); ++r) {

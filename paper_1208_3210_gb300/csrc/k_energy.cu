@@ -1,23 +1,27 @@
-// Energy pass with one warp per momentum point (FP32, T = 0 split).
+// Energy passes with one warp per momentum point (FP32).
 //
-// The same transform as k_fwd_energy (Eqs. 4-5 generated on chip, the T = 0
-// split of Sec. 3 / Appendix A Eq. A3, z = a + i b transformed along energy,
-// a^ and b^ separated for the non-redundant frequencies k <= L/2), arranged
-// so that
-//   * the L/16 threads of one line (momentum point) sit in one warp (a warp
-//     holds 32 / (L/16) lines at a time): every exchange of a line stays in
+// Forward: the same transform as k_fwd_energy (Eqs. 4-5 generated on chip,
+// split into the occupied and the empty part (Sec. 3 / Appendix A: Eq. A3 at
+// T = 0, the Fermi weights of Eq. A1 at T > 0), z = a + i b transformed along
+// energy, a^ and b^ separated for the non-redundant frequencies k <= L/2),
+// arranged so that
+//   * the TPL = L/VPT threads of one line (momentum point) sit in one warp (a
+//     warp holds 32 / TPL lines at a time): every exchange of a line stays in
 //     its warp (__syncwarp, no CTA barrier), the warp's lines' band energies
 //     are computed by one lane each and broadcast by shuffles, and every
 //     thread keeps its line's band energy and amplitude in registers;
 //   * every shared-memory address is a per-butterfly base plus compile-time
 //     offsets (one pad value every 16 spreads the Stockham writes over the
 //     banks), the twiddles 16-byte loads from per-stage tables;
-//   * in the last stage a thread owns butterflies j and L/8 - j, so it holds
+//   * in the last stage a thread owns butterflies j and L/R2 - j, so it holds
 //     Z(k) and Z(L - k) together and separates a^(k) = (Z(k) + conj Z(L - k))/2
 //     and b^(k) = (Z(k) - conj Z(L - k))/2i in registers (no natural-order
 //     copy of the spectrum); a warp's stores of one line are contiguous.
-// Schedules (forward): 128 = 4.4.8, 256 = 4.8.8, 512 = 8.8.8; 16 values per
-// thread.  Output U1 [N*N lines][SP][2] as k_fwd_energy writes it.
+// Inverse: one warp per pair of (q_x, q_y) lines, the mirror image (a thread's
+// first-stage butterflies j and L/R0 - j form W(k) and W(L - k) from the
+// stored half spectra).
+// Schedules (et_tiles.cuh): VPT = 16 values per thread at 128, 256 and 512,
+// 24 at 384 and 768.  Output U1 [N*N lines][SP][2] as k_fwd_energy writes it.
 #include "et_tiles.cuh"
 
 namespace lh {
@@ -51,7 +55,7 @@ size_t et_twiddle_bytes() { return (size_t)et_twiddle_entries() * sizeof(float2)
 // temperature (whose energy axes are padded to 3 * 2^k) also at 384 and 768
 bool et_applies(const Geom &g, const Band &band)
 {
-    return band.kT > 0 ? et_fwd_supported(g.PE) : et_supported(g.PE);
+    return band.kT > 0 ? et_len_supported(g.PE) : et_supported(g.PE);
 }
 
 // THERMAL: the CTA tabulates the Fermi weights of its energies once, after the
@@ -88,7 +92,7 @@ cudaError_t launch_inv_energy_warp_t(const Geom &g, const Work<float> &w, float 
     const long long npairs = (long long)g.Q * g.Q / 2;
     const long long per = (long long)ET_WARPS * ET_LPW;
     const unsigned grid = (unsigned)((npairs + per - 1) / per);
-    const size_t smem = sizeof(float2) * ET_WARPS * (32 / (L / 16)) * (L + L / 16);
+    const size_t smem = sizeof(float2) * et_inv_smem_elems<L>();
     static const cudaError_t e0 = smem_attrs(k_inv_energy_warp<L, true>, smem);
     static const cudaError_t e1 = smem_attrs(k_inv_energy_warp<L, false>, smem);
     if (e0 != cudaSuccess) return e0;
@@ -98,7 +102,8 @@ cudaError_t launch_inv_energy_warp_t(const Geom &g, const Work<float> &w, float 
     return cudaGetLastError();
 }
 
-bool et_inv_applies(const Geom &g) { return et_supported(g.PE) && g.Q % 2 == 0; }
+// the warp-per-pair inverse pass: every length of the warp-per-line passes
+bool et_inv_applies(const Geom &g) { return et_len_supported(g.PE) && g.Q % 2 == 0; }
 cudaError_t launch_inv_energy_warp(const Geom &g, const Work<float> &w, float *out, cudaStream_t s)
 {
     if (!w.etw || !et_inv_applies(g)) return cudaErrorInvalidValue;
@@ -106,6 +111,8 @@ cudaError_t launch_inv_energy_warp(const Geom &g, const Work<float> &w, float *o
     case 128: return launch_inv_energy_warp_t<128>(g, w, out, s);
     case 256: return launch_inv_energy_warp_t<256>(g, w, out, s);
     case 512: return launch_inv_energy_warp_t<512>(g, w, out, s);
+    case 384: return launch_inv_energy_warp_t<384>(g, w, out, s);
+    case 768: return launch_inv_energy_warp_t<768>(g, w, out, s);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -111,6 +111,44 @@ def test_thermal_warp_energy_lengths(lh, grid, kT, pe, quantity):
     assert err_a <= TOL32
 
 
+# the warp-per-pair inverse energy pass (inverse variant 2) at the 3 * 2^k
+# energy lengths, pinned through the tune cache (momentum FFTs of at least 128
+# points take the tuned passes), on sampled outputs against the oracle
+@pytest.mark.parametrize("quantity", [1, 2], ids=["imchi_T", "S"])
+@pytest.mark.parametrize("n_eps,e_max,kT,pe", [(256, 1.5, 0.025, 384), (512, 3.0, 0.025, 768)],
+                         ids=["PE384", "PE768"])
+def test_thermal_warp_inverse_lengths(lh, tmp_path, monkeypatch, n_eps, e_max, kT, pe, quantity):
+    import torch
+    grid = wl.grid_params(2, 64, n_eps, e_max, q_extent=96, quantity=quantity)
+    band = dict(wl.band_params(filling=1.1, gamma=0.06, ff_a=0.8), kT=kT)
+    probe = lh.Plan([grid])
+    s = probe.sizes[0]
+    assert s.fft_e == pe and s.fft_p >= 128
+    base = f"{torch.cuda.get_device_name(0)}|P={s.fft_p}|N={s.N}|PE={s.fft_e}|Q={s.q_extent}"
+    probe.close()
+    lx, ly, m = wl.output_samples(grid, 120, seed=pe + quantity)
+    A = oracle.spectral(_solved(band, grid), grid)
+    ref = oracle.thermal_samples(A, grid, grid["q_extent"], kT, quantity, lx, ly, m)
+    outs = {}
+    for ve in (0, 2):
+        path = tmp_path / f"tune_{ve}.json"
+        path.write_text(json.dumps({base + "|fwd_y": 1, base + "|inv_y": 1, base + "|x_product": 0,
+                                    base + "|inv_energy": ve}, indent=0))
+        monkeypatch.setenv("LINDHARD_TUNE_CACHE", str(path))
+        plan = lh.Plan([grid], autotune=True)
+        out = plan.imchi([band])
+        plan.status()
+        assert plan.variants()["energy_inv"] == ve
+        outs[ve] = out.reshape(s.q_extent, s.q_extent, s.n_omega).cpu().numpy().astype(np.float64)
+        plan.close()
+        err = np.abs(outs[ve][lx, ly, m] - ref).max() / np.abs(ref).max()
+        print(f"PE {pe}, quantity {quantity}, inverse energy variant {ve}: {err:.2e} of max")
+        assert err <= TOL32
+    # every output: the two inverse passes differ only in rounding order
+    scale = np.abs(outs[0]).max()
+    assert np.abs(outs[2] - outs[0]).max() <= TOL32 * scale
+
+
 @pytest.mark.parametrize("quantity", [1, 2], ids=["imchi_T", "S"])
 def test_thermal_fp64(lh, quantity):
     grid, band, kT = CASES[0]
