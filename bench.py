@@ -44,10 +44,11 @@ VARIANT_KERNELS = {
     "py_fwd": ["k_fwd_y", "k_fwd_y2", "k_fwd_y2 (12-value tiles)", "k_fwd_y_tma", "k_fwd_y_tma (12-value tiles)",
                "k_y_col_tma (forward)", "k_fwd_y2 (double-width tile)", "(unused)", "k_fwd_y_pr (pruned, 8 pairs)",
                "k_fwd_y_pr (pruned, 4 pairs)",
-               "k_fwd_y_pr_tma (pruned, TMA-staged)"],
+               "k_fwd_y_pr_tma (pruned, TMA-staged)", "k_fwd_y_pr_tma2 (pruned, TMA-staged, two CTAs per SM)"],
     "py_inv": ["k_inv_y", "k_inv_y2", "k_inv_y2 (12-value tiles)", "k_inv_y_tma", "k_inv_y_tma (12-value tiles)",
                "k_y_col_tma (inverse)", "k_inv_y2 (double-width tile)", "k_inv_y_tc (tensor cores)",
-               "k_inv_y_pr (pruned, 8 pairs)", "k_inv_y_pr (pruned, 4 pairs)", "k_inv_y_pr_tma (pruned, TMA-staged)"],
+               "k_inv_y_pr (pruned, 8 pairs)", "k_inv_y_pr (pruned, 4 pairs)", "k_inv_y_pr_tma (pruned, TMA-staged)",
+               "k_inv_y_pr_tma2 (pruned, TMA-staged, two CTAs per SM)"],
     "px_product": ["k_x_product", "k_x_product (12-value tiles)", "k_x_product_tma",
                    "k_x_product_tma (12-value tiles)", "k_x_product (one more CTA per SM)",
                    "k_x_product (double-width tile)", "k_x_product_pr (pruned, 8 columns)",

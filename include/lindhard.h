@@ -376,7 +376,7 @@ lindhard_status lindhard_plan_set_wait_limit(lindhard_plan *plan, unsigned long 
  * 7 the tensor-core inverse, 8 and 9 the pruned engine on 8 and 4 column
  * pairs: a radix-24 stage at the padded end, for a padding of exactly one
  * third, N = 2P/3 forward and Q = 2P/3 inverse; 10 its TMA-staged
- * persistent form, P >= 384);
+ * persistent form, 11 the same with two CTAs per SM, P >= 384);
  * out[2] = the p_x product pass (0 default
  * tile, 1 tile with 12 values per thread, 2 and 3 their TMA-staged forms,
  * 4 the default tile with one more CTA per SM, 5 the default tile twice as

@@ -320,13 +320,13 @@ cudaError_t launch_fwd_energy(const Geom &g, const Band &band, const Work<double
 }
 cudaError_t launch_fwd_y_tma(const Geom &g, const Work<float> &w, cudaStream_t s, int variant);
 cudaError_t launch_fwd_y_pr(const Geom &g, const Work<float> &w, cudaStream_t s, int variant);
-cudaError_t launch_fwd_y_pr_tma(const Geom &g, const Work<float> &w, cudaStream_t s);
+cudaError_t launch_fwd_y_pr_tma(const Geom &g, const Work<float> &w, cudaStream_t s, int variant);
 // variants 3, 4, 5: the TMA-staged persistent kernels of k_tma.cu; 8, 9: the
 // pruned engine of k_pruned.cu (one-third padding); 10: its TMA-staged
-// persistent form (k_pruned_tma.cu)
+// persistent form, 11 the same with two CTAs per SM (k_pruned_tma.cu)
 cudaError_t launch_fwd_y(const Geom &g, const Work<float> &w, cudaStream_t s, int variant)
 {
-    if (variant == 10) return launch_fwd_y_pr_tma(g, w, s);
+    if (variant == 10 || variant == 11) return launch_fwd_y_pr_tma(g, w, s, variant);
     if (variant >= 3 && variant <= 5) return launch_fwd_y_tma(g, w, s, variant);
     if (variant == 8 || variant == 9) return launch_fwd_y_pr(g, w, s, variant);
 #define CALL(L) launch_fwd_y_t<float, L>(g, w, s, variant)

@@ -212,12 +212,13 @@ cudaError_t launch_inv_y_tma(const Geom &g, const Work<float> &w, cudaStream_t s
 cudaError_t launch_inv_y_tc(const Geom &g, const Work<float> &w, cudaStream_t s);
 // variants 3, 4: the TMA-staged persistent kernels of k_tma.cu
 cudaError_t launch_inv_y_pr(const Geom &g, const Work<float> &w, cudaStream_t s, int variant);
-cudaError_t launch_inv_y_pr_tma(const Geom &g, const Work<float> &w, cudaStream_t s);
+cudaError_t launch_inv_y_pr_tma(const Geom &g, const Work<float> &w, cudaStream_t s, int variant);
 // 8, 9: the pruned engine of k_pruned.cu (one-third padding); 10: its
-// TMA-staged persistent form (k_pruned_tma.cu)
+// TMA-staged persistent form, 11 the same with two CTAs per SM
+// (k_pruned_tma.cu)
 cudaError_t launch_inv_y(const Geom &g, const Work<float> &w, cudaStream_t s, int variant)
 {
-    if (variant == 10) return launch_inv_y_pr_tma(g, w, s);
+    if (variant == 10 || variant == 11) return launch_inv_y_pr_tma(g, w, s, variant);
     if (variant >= 3 && variant <= 5) return launch_inv_y_tma(g, w, s, variant);
     if (variant == 8 || variant == 9) return launch_inv_y_pr(g, w, s, variant);
     if (variant == 7) return launch_inv_y_tc(g, w, s);   // tensor-core stages (k_tc.cu)

@@ -414,9 +414,9 @@ static cudaError_t autotune(lindhard_plan *p)
         if (pr_fwd_applies(g)) { vyf.push_back(8); vyf.push_back(9); }
         if (pr_inv_applies(g)) { vyi.push_back(8); vyi.push_back(9); }
         if (pr_fwd_applies(g) && pr_inv_applies(g)) { vx.push_back(6); vx.push_back(7); }
-        if (g.P >= 384) {   // their TMA-staged persistent forms
-            if (pr_fwd_applies(g)) vyf.push_back(10);
-            if (pr_inv_applies(g)) vyi.push_back(10);
+        if (g.P >= 384) {   // their TMA-staged persistent forms (11: two CTAs per SM)
+            if (pr_fwd_applies(g)) { vyf.push_back(10); vyf.push_back(11); }
+            if (pr_inv_applies(g)) { vyi.push_back(10); vyi.push_back(11); }
             if (pr_fwd_applies(g) && pr_inv_applies(g)) {
                 vx.push_back(8);
                 vx.push_back(9);    // software-pipelined persistent forms

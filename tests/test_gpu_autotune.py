@@ -95,7 +95,7 @@ def test_fresh_tune_writes_cache_and_matches_default(lh, tmp_path, monkeypatch):
     kf, ki, kx, ke = _keys(grid, plan.sizes[0])
     plan.close()
     entries = json.loads(path.read_text())
-    assert entries[kf] in range(11) and entries[ki] in range(11) and entries[kx] in range(11) and entries[ke] in (0, 1, 2)
+    assert entries[kf] in range(12) and entries[ki] in range(12) and entries[kx] in range(11) and entries[ke] in (0, 1, 2)
     base = lh.Plan([grid])
     out_d = base.imchi([band])
     base.status()
@@ -119,8 +119,9 @@ def test_tma_variants_full_size_match_default(lh, tmp_path, monkeypatch):
     kf, ki, kx, ke = _keys(grid, base.sizes[0])
     base.close()
     mx = float(out_d.abs().max())
-    # 10 / 8: the TMA-staged pruned passes; 9 / 10: the pipelined product pass
-    for vy, vx, ve in [(3, 2, 1), (4, 3, 0), (5, 2, 1), (6, 5, 0), (10, 8, 2), (8, 9, 2), (10, 10, 0)]:
+    # 10 / 8: the TMA-staged pruned passes (11: two CTAs per SM); 9 / 10: the
+    # pipelined product pass
+    for vy, vx, ve in [(3, 2, 1), (4, 3, 0), (5, 2, 1), (6, 5, 0), (10, 8, 2), (8, 9, 2), (10, 10, 0), (11, 10, 2)]:
         path = tmp_path / f"tma_{vy}{vx}.json"
         path.write_text(json.dumps({kf: vy, ki: vy, kx: vx, ke: ve}, indent=0))
         monkeypatch.setenv("LINDHARD_TUNE_CACHE", str(path))

@@ -24,7 +24,7 @@ pytestmark = pytest.mark.gpu
 TOL32 = 2e-5
 NAME = "large_1024x1024x512"
 # variants the autotuner tries at P = 1536 (a 3 * 2^k length >= 384), per pass
-CANDIDATES = {"fwd_y": [0, 1, 2, 3, 4, 5, 6, 8, 9, 10], "inv_y": [0, 1, 2, 3, 4, 5, 6, 8, 9, 10],
+CANDIDATES = {"fwd_y": [0, 1, 2, 3, 4, 5, 6, 8, 9, 10, 11], "inv_y": [0, 1, 2, 3, 4, 5, 6, 8, 9, 10, 11],
               "x_product": [0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10], "inv_energy": [0, 1, 2]}
 # the passes not under test run the variants the tuner chose on GB300
 TUNED = {"fwd_y": 3, "inv_y": 3, "x_product": 5, "inv_energy": 0}
