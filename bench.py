@@ -32,13 +32,15 @@ sys.path.insert(0, ROOT)
 
 DEFAULT_WORKLOAD = "large_1024x1024x512"
 FALLBACK_HBM_GBS = 6800.0
+COMMON_FILES = ("fft_engine.cuh", "kernels.cuh", "lindhard_internal.h")
 PASS_FILES = {  # kernel sources of each timed pass (for traffic-record staleness)
-    "energy_fwd": ("k_forward.cu", "k_energy.cu"),
+    "energy_fwd": ("k_forward.cu", "k_energy.cu", "et_tiles.cuh"),
     "py_fwd": ("k_forward.cu", "k_tma.cu", "tma.cuh", "async.cuh", "k_pruned.cu", "fft_pruned.cuh", "pr_tiles.cuh", "k_pruned_tma.cu"),
     "px_product": ("k_product.cu", "k_tma.cu", "tma.cuh", "async.cuh", "k_pruned.cu", "fft_pruned.cuh", "pr_tiles.cuh", "k_pruned_tma.cu", "k_product_pipe.cu"),
     "py_inv": ("k_inverse.cu", "k_tma.cu", "tma.cuh", "async.cuh", "k_pruned.cu", "fft_pruned.cuh", "pr_tiles.cuh", "k_pruned_tma.cu"),
-    "energy_inv": ("k_inverse.cu", "k_tma.cu", "tma.cuh", "async.cuh", "k_energy.cu"),
+    "energy_inv": ("k_inverse.cu", "k_tma.cu", "tma.cuh", "async.cuh", "k_energy.cu", "et_tiles.cuh"),
 }
+PASS_FILES = {k: v + COMMON_FILES for k, v in PASS_FILES.items()}
 # kernel of each pass by engine variant (lindhard_plan_variants)
 VARIANT_KERNELS = {
     "py_fwd": ["k_fwd_y", "k_fwd_y2", "k_fwd_y2 (12-value tiles)", "k_fwd_y_tma", "k_fwd_y_tma (12-value tiles)",
