@@ -445,6 +445,54 @@ def thermal_form(lh, grids, bands, steps, autotune, stream, kT=0.025):
     return res
 
 
+def batched_form(lh, steps, autotune, stream, count=64):
+    """The batched workload (`count` independent instances of mixed filling,
+    broadening and size, one call per batch) in the plan's three batch forms:
+    the persistent batch launch replayed as a graph, the same instances one
+    after another on one stream, and every instance's launches on forked
+    streams recorded into one graph; device time per batch, outside the timed
+    region of the single-instance call."""
+    import torch
+    from paper_1208_3210_gb300 import workloads as wl
+    grids, bands = wl.batched_workload(count)
+    res = {"instances": count}
+    n = max(3, min(steps, 10))
+    ref = None
+    for name, kw in (("plain_sequential", {}), ("persistent_graph", dict(graph=True, persistent=True)),
+                     ("concurrent_graph", dict(graph=True))):
+        try:
+            p = lh.Plan(grids, autotune=autotune, **kw)
+        except Exception as exc:
+            res[name] = {"unavailable": str(exc)}
+            continue
+        o = torch.empty(p.out_elems(), dtype=torch.float32, device="cuda")
+        for _ in range(3):
+            p.imchi(bands, out=o)
+        p.status()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(n):
+            p.imchi(bands, out=o)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        p.status()
+        ms = e0.elapsed_time(e1) / n
+        res[name] = {"ms_per_batch": ms, "value": p.out_elems() / (ms * 1e-3), "steps": n}
+        if ref is None:
+            ref = o
+        else:
+            res[name]["max_rel_diff_vs_plain"] = float((o - ref).abs().max() / ref.abs().max().clamp_min(1e-30))
+            del o
+        p.close()
+    if "ms_per_batch" in res.get("plain_sequential", {}):
+        for name in ("persistent_graph", "concurrent_graph"):
+            if "ms_per_batch" in res.get(name, {}):
+                res[name]["speedup_vs_plain"] = res["plain_sequential"]["ms_per_batch"] / res[name]["ms_per_batch"]
+    del ref
+    return res
+
+
 def energy_direct_form(lh, grids, bands, out_3d, steps, mu, stream):
     """The paper's own arrangement (LINDHARD_PLAN_ENERGY_DIRECT: 2D momentum
     FFTs per energy plane, the energy sum done directly per momentum
@@ -710,12 +758,17 @@ def main():
     kk = None
     thermal = None
     direct = None
+    batch = None
     if not batched and not args.no_tc:
         plan.imchi(bands, out=out, mu_out=mu)
         kk = kk_rpa_form(plan, out, args.steps, stream, peak)
         thermal = thermal_form(lh, grids, bands, args.steps, not args.no_autotune, stream)
         plan.imchi(bands, out=out, mu_out=mu)
         direct = energy_direct_form(lh, grids, bands, out, args.steps, mu, stream)
+        try:
+            batch = batched_form(lh, args.steps, not args.no_autotune, stream)
+        except Exception as exc:   # an extra object: never the main line's failure
+            batch = {"unavailable": str(exc)}
         tc = tensor_core_form(lh, grids, bands, out, args.steps, not args.no_autotune, mu, stream)
         if "py_inv_ms" in tc:
             tc["py_inv_ms_fp32"] = round(ptimes["py_inv"][0] / max(ptimes["py_inv"][1], 1), 5)
@@ -762,6 +815,8 @@ def main():
             line["finite_temperature"] = thermal
         if direct is not None:
             line["energy_direct"] = direct
+        if batch is not None:
+            line["batched_64"] = batch
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.workload)
         print(json.dumps(line), flush=True)

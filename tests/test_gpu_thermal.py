@@ -115,11 +115,13 @@ def test_thermal_warp_energy_lengths(lh, grid, kT, pe, quantity):
 # energy lengths, pinned through the tune cache (momentum FFTs of at least 128
 # points take the tuned passes), on sampled outputs against the oracle
 @pytest.mark.parametrize("quantity", [1, 2], ids=["imchi_T", "S"])
-@pytest.mark.parametrize("n_eps,e_max,kT,pe", [(256, 1.5, 0.025, 384), (512, 3.0, 0.025, 768)],
-                         ids=["PE384", "PE768"])
-def test_thermal_warp_inverse_lengths(lh, tmp_path, monkeypatch, n_eps, e_max, kT, pe, quantity):
+# (n_omega = PE/2 takes the kernel's half-output form)
+@pytest.mark.parametrize("n_eps,n_omega,e_max,kT,pe", [(256, 128, 1.5, 0.025, 384), (512, 256, 3.0, 0.025, 768),
+                                                       (193, 192, 1.5, 0.025, 384)],
+                         ids=["PE384", "PE768", "PE384_half"])
+def test_thermal_warp_inverse_lengths(lh, tmp_path, monkeypatch, n_eps, n_omega, e_max, kT, pe, quantity):
     import torch
-    grid = wl.grid_params(2, 64, n_eps, e_max, q_extent=96, quantity=quantity)
+    grid = wl.grid_params(2, 64, n_eps, e_max, n_omega=n_omega, q_extent=96, quantity=quantity)
     band = dict(wl.band_params(filling=1.1, gamma=0.06, ff_a=0.8), kT=kT)
     probe = lh.Plan([grid])
     s = probe.sizes[0]
