@@ -257,68 +257,45 @@ struct PrEng {
         else Dft<R, INV, Cx, PK>::run(v);
     }
 
-    // The exchange before stage SS: the previous stage's outputs, Stockham
-    // order (idxD + r Nsp), into sm.
-    template <int SS>
-    __device__ __forceinline__ static void wr(const Cx *va, const Cx *vb, Cx *sm)
-    {
-        constexpr int Rp = pr_radix(L, SS - 1, INV), Nsp = pr_ns(L, SS - 1, INV);
-        static_assert(Nsp == 1 || Nsp % R0 == 0, "exchange offsets must stay compile-time");
-#pragma unroll
-        for (int b = 0; b < VPT / Rp; ++b) {
-            const int j = jb(b);
-            const int base = pbase((j / Nsp) * Nsp * Rp + j % Nsp);
-#pragma unroll
-            for (int r = 0; r < Rp; ++r) st(sm, base + poff(r * Nsp), va[b * Rp + r], vb[b * Rp + r]);
-        }
-    }
-    // Stage SS from sm: the butterfly inputs, their twiddles, the DFTs.
-    template <int SS>
-    __device__ __forceinline__ static void rd(Cx *va, Cx *vb, const Cx *sm, const Cx *__restrict__ tw)
-    {
-        constexpr int Rs = pr_radix(L, SS, INV), Ns = pr_ns(L, SS, INV);
-        static_assert((L / Rs) % R0 == 0, "read offsets must stay compile-time");
-        const Cx *tws = tw + (TWS ? pr_tws_offset(L, INV, SS) : pr_tw_offset(L, INV, SS));
-        constexpr int TWROW = TWS ? Rs + 2 : Rs;
-#pragma unroll
-        for (int b = 0; b < VPT / Rs; ++b) {
-            const int j = jb(b);
-            const int base = pbase(j);
-#pragma unroll
-            for (int r = 0; r < Rs; ++r) ld(sm, base + poff(r * (L / Rs)), va[b * Rs + r], vb[b * Rs + r]);
-            // twiddles exp(-+2 pi i k r / (Ns Rs)), k = j mod Ns, entries [k][0..Rs)
-            const float4 *w4 = reinterpret_cast<const float4 *>(tws + (j % Ns) * TWROW);
-            Cx w[Rs];
-            twiddle_set<Rs>(w4, w);
-#pragma unroll
-            for (int r = 1; r < Rs; ++r) {
-                va[b * Rs + r] = INV ? cmulc(va[b * Rs + r], w[r]) : cmul(va[b * Rs + r], w[r]);
-                if constexpr (NOPS == 2) vb[b * Rs + r] = INV ? cmulc(vb[b * Rs + r], w[r]) : cmul(vb[b * Rs + r], w[r]);
-            }
-            dft<Rs, false, SS == S - 1>(va + b * Rs);
-            if constexpr (NOPS == 2) dft<Rs, false, SS == S - 1>(vb + b * Rs);
-        }
-    }
-
     template <int SS>
     __device__ __forceinline__ static void stage_rest(Cx *va, Cx *vb, Cx *sm, const Cx *__restrict__ tw)
     {
         if constexpr (SS < S) {
-            wr<SS>(va, vb, sm);
+            constexpr int Rp = pr_radix(L, SS - 1, INV), Nsp = pr_ns(L, SS - 1, INV);
+            constexpr int Rs = pr_radix(L, SS, INV), Ns = pr_ns(L, SS, INV);
+            static_assert(Nsp == 1 || Nsp % R0 == 0, "exchange offsets must stay compile-time");
+            static_assert((L / Rs) % R0 == 0, "read offsets must stay compile-time");
+            const Cx *tws = tw + (TWS ? pr_tws_offset(L, INV, SS) : pr_tw_offset(L, INV, SS));
+            constexpr int TWROW = TWS ? Rs + 2 : Rs;
+            // the previous stage's outputs, Stockham order: idxD + r Nsp
+#pragma unroll
+            for (int b = 0; b < VPT / Rp; ++b) {
+                const int j = jb(b);
+                const int base = pbase((j / Nsp) * Nsp * Rp + j % Nsp);
+#pragma unroll
+                for (int r = 0; r < Rp; ++r) st(sm, base + poff(r * Nsp), va[b * Rp + r], vb[b * Rp + r]);
+            }
             __syncthreads();
-            rd<SS>(va, vb, sm, tw);
+#pragma unroll
+            for (int b = 0; b < VPT / Rs; ++b) {
+                const int j = jb(b);
+                const int base = pbase(j);
+#pragma unroll
+                for (int r = 0; r < Rs; ++r) ld(sm, base + poff(r * (L / Rs)), va[b * Rs + r], vb[b * Rs + r]);
+                // twiddles exp(-+2 pi i k r / (Ns Rs)), k = j mod Ns, entries [k][0..Rs)
+                const float4 *w4 = reinterpret_cast<const float4 *>(tws + (j % Ns) * TWROW);
+                Cx w[Rs];
+                twiddle_set<Rs>(w4, w);
+#pragma unroll
+                for (int r = 1; r < Rs; ++r) {
+                    va[b * Rs + r] = INV ? cmulc(va[b * Rs + r], w[r]) : cmul(va[b * Rs + r], w[r]);
+                    if constexpr (NOPS == 2) vb[b * Rs + r] = INV ? cmulc(vb[b * Rs + r], w[r]) : cmul(vb[b * Rs + r], w[r]);
+                }
+                dft<Rs, false, SS == S - 1>(va + b * Rs);
+                if constexpr (NOPS == 2) dft<Rs, false, SS == S - 1>(vb + b * Rs);
+            }
             __syncthreads();
             stage_rest<SS + 1>(va, vb, sm, tw);
-        }
-    }
-
-    // the first stage, in registers
-    __device__ __forceinline__ static void first(Cx *va, Cx *vb)
-    {
-#pragma unroll
-        for (int b = 0; b < VPT / R0; ++b) {
-            dft<R0, true, S == 1>(va + b * R0);
-            if constexpr (NOPS == 2) dft<R0, true, S == 1>(vb + b * R0);
         }
     }
 
@@ -328,7 +305,11 @@ struct PrEng {
     // tables (pr_tw_offset).  Ends with a __syncthreads().
     __device__ __forceinline__ static void run(Cx *va, Cx *vb, Cx *sm, const Cx *__restrict__ tw)
     {
-        first(va, vb);
+#pragma unroll
+        for (int b = 0; b < VPT / R0; ++b) {
+            dft<R0, true, S == 1>(va + b * R0);
+            if constexpr (NOPS == 2) dft<R0, true, S == 1>(vb + b * R0);
+        }
         stage_rest<1>(va, vb, sm, tw);
     }
 };
