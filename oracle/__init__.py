@@ -72,6 +72,10 @@ def _load():
             lib.lo_grad_A_samples.restype = None
             lib.lo_grad_A_samples.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, _dp,
                                               ctypes.c_int, ctypes.c_int, _dp, ctypes.c_long, _ip, _ip, _ip, _dp]
+            lib.lo_thermal_grad_A_samples.restype = None
+            lib.lo_thermal_grad_A_samples.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, _dp,
+                                                      ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, _dp,
+                                                      ctypes.c_long, _ip, _ip, _ip, _dp]
             lib.lo_spectral_dtheta.restype = None
             lib.lo_spectral_dtheta.argtypes = ([ctypes.c_double] * 6
                                                + [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, _dp])
@@ -239,6 +243,35 @@ def grad_A_full(A: np.ndarray, grid: dict, q_extent: int, w: np.ndarray) -> np.n
     N = grid["zones"] * grid["npz"]
     ix, iy, j = np.meshgrid(np.arange(N), np.arange(N), np.arange(grid["n_eps"]), indexing="ij")
     return grad_A_samples(A, grid, q_extent, w, ix.ravel(), iy.ravel(), j.ravel()).reshape(N, N, grid["n_eps"])
+
+
+def thermal_grad_A_samples(A: np.ndarray, grid: dict, q_extent: int, w: np.ndarray, kT: float, quantity: int,
+                           ix, iy, j) -> np.ndarray:
+    """dL/dA at sample points for L = sum w * X, X = Im chi_T (IMCHI_T) or
+    S(q, w) (SQW) at temperature kT (adjoint of Eq. A1 / Eq. 1 as
+    thermal_samples sums them)."""
+    assert kT > 0 and quantity in (IMCHI_T, SQW)
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    Q = q_extent
+    assert w.shape[0] == Q and w.shape[1] == Q
+    n_omega = w.shape[2]
+    ix = np.ascontiguousarray(ix, dtype=np.int32)
+    iy = np.ascontiguousarray(iy, dtype=np.int32)
+    j = np.ascontiguousarray(j, dtype=np.int32)
+    out = np.empty(ix.size, dtype=np.float64)
+    _load().lo_thermal_grad_A_samples(grid["zones"], grid["npz"], grid["n_eps"], grid["e_max"], _d(A), Q, n_omega,
+                                      float(kT), int(quantity), _d(w), ix.size, _i(ix), _i(iy), _i(j), _d(out))
+    return out
+
+
+def thermal_grad_A_full(A: np.ndarray, grid: dict, q_extent: int, w: np.ndarray, kT: float,
+                        quantity: int) -> np.ndarray:
+    """thermal_grad_A_samples at every grid point, shape [N, N, n_eps] (small grids only)."""
+    N = grid["zones"] * grid["npz"]
+    ix, iy, j = np.meshgrid(np.arange(N), np.arange(N), np.arange(grid["n_eps"]), indexing="ij")
+    return thermal_grad_A_samples(A, grid, q_extent, w, kT, quantity, ix.ravel(), iy.ravel(),
+                                  j.ravel()).reshape(N, N, grid["n_eps"])
 
 
 def spectral_dtheta(band_p: dict, grid: dict) -> np.ndarray:

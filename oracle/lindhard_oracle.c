@@ -297,6 +297,67 @@ void lo_grad_A_samples(int zones, int npz, int n_eps, double e_max,
     }
 }
 
+/* Gradient of L = sum_{l,m} w[l_x][l_y][m] X(q_l, w_m) with respect to
+ * A(p_i, e_j) at finite temperature, X = Im chi_T (quantity 1) or S(q, w)
+ * (quantity 2) as lo_thermal_samples sums them (Eq. 1, Appendix A Eq. A1):
+ *   X(q, m) = kappa sum_{p, j} A(p, e_j) A(p + q, e_{j+m}) W(j, m),
+ *   W(j, m) = f_j - f_{j+m} (kappa = -c)  or  f_j (1 - f_{j+m}) (kappa = c/pi).
+ * A(p0, e_j0) enters as the first factor (p = p0, j = j0) and as the second
+ * (p = p0 - q, j = j0 - m), so
+ *   dL/dA(p0, e_j0) = kappa sum_{l,m} w(l,m) [W(j0, m) A(p0 + q_l, e_{j0+m})
+ *                                            + W(j0 - m, m) A(p0 - q_l, e_{j0-m})],
+ * every partner on the grid (the same shifts and edges as the forward sum). */
+void lo_thermal_grad_A_samples(int zones, int npz, int n_eps, double e_max,
+                               const double *A, int q_extent, int n_omega,
+                               double kT, int quantity, const double *w,
+                               long n, const int *ix, const int *iy,
+                               const int *jj, double *out)
+{
+    long N = (long)zones * npz;
+    int periodic = (zones == 1), Q = q_extent;
+    double de = 2.0 * e_max / n_eps;
+    double c = de / (2.0 * LO_PI) / ((double)npz * (double)npz);
+    double kappa = quantity == 1 ? -c : c / LO_PI;
+    double *f = (double *)malloc(sizeof(double) * 2 * (size_t)n_eps);
+    double *fe = f + n_eps;            /* 1 - f */
+    for (int j = 0; j < n_eps; ++j) {
+        double e = -e_max + (j + 0.5) * de;
+        f[j] = 1.0 / (exp(e / kT) + 1.0);
+        fe[j] = 1.0 / (exp(-e / kT) + 1.0);
+    }
+#pragma omp parallel for schedule(dynamic, 1)
+    for (long k = 0; k < n; ++k) {
+        int j0 = jj[k];
+        double sum = 0.0;
+        for (int lx = 0; lx < Q; ++lx) {
+            long sx = lx - Q / 2;
+            long ax = lo_shift(ix[k], sx, N, periodic), bx = lo_shift(ix[k], -sx, N, periodic);
+            for (int ly = 0; ly < Q; ++ly) {
+                long sy = ly - Q / 2;
+                long ay = lo_shift(iy[k], sy, N, periodic), by = lo_shift(iy[k], -sy, N, periodic);
+                const double *wr = w + ((size_t)lx * Q + ly) * n_omega;
+                if (ax >= 0 && ay >= 0) {           /* A(p0, e_j0) first: partner at p0 + q, e_{j0+m} */
+                    const double *row = A + ((size_t)ax * N + ay) * n_eps;
+                    for (int mm = 0; mm < n_omega && j0 + mm < n_eps; ++mm) {
+                        double wgt = quantity == 1 ? f[j0] - f[j0 + mm] : f[j0] * fe[j0 + mm];
+                        sum += wr[mm] * wgt * row[j0 + mm];
+                    }
+                }
+                if (bx >= 0 && by >= 0) {           /* A(p0, e_j0) second: partner at p0 - q, e_{j0-m} */
+                    const double *row = A + ((size_t)bx * N + by) * n_eps;
+                    for (int mm = 0; mm < n_omega && j0 - mm >= 0; ++mm) {
+                        int jq = j0 - mm;
+                        double wgt = quantity == 1 ? f[jq] - f[j0] : f[jq] * fe[j0];
+                        sum += wr[mm] * wgt * row[jq];
+                    }
+                }
+            }
+        }
+        out[k] = kappa * sum;
+    }
+    free(f);
+}
+
 /* Derivatives of A(p, e) (Eqs. 4-5 with the band above) with respect to the
  * five band parameters theta = (t, t', t'', mu, gamma), written into
  * dA[5][N][N][n_eps].  With D = (e - xi)^2 + gamma^2:

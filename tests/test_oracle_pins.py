@@ -552,3 +552,48 @@ def test_thermal_sum_rule():
     for mm in range(nw):
         ref = -c * sum(D[j] * D[j + mm] * (f[j] - f[j + mm]) for j in range(20 - mm))
         assert abs(im[..., mm].sum() - ref) <= 1e-12 * max(abs(ref), np.abs(im).max())
+
+
+# --- the finite-temperature adjoint (thermal_grad_A_samples) ---------------------
+
+def _thermal_loss(A, grid, Q, w, kT, quantity):
+    return float(np.sum(w * oracle.thermal_full(A, grid, Q, w.shape[2], kT, quantity)))
+
+
+@pytest.mark.parametrize("zones", [1, 2])
+@pytest.mark.parametrize("quantity", [1, 2], ids=["imchi_T", "S"])
+def test_thermal_grad_A_central_difference_is_exact(zones, quantity):
+    # Eq. A1 and Eq. 1 are quadratic forms in A, so a central difference in A
+    # is exact up to rounding: (L(A + hE) - L(A - hE)) / 2h = dL/dA . E
+    grid, band, A, Q, w = _small_case(zones=zones, npz=6 if zones == 1 else 4)
+    kT = 0.15
+    g = oracle.thermal_grad_A_full(A, grid, Q, w, kT, quantity)
+    rng = np.random.default_rng(11)
+    h = 0.05
+    for _ in range(6):
+        ix, iy, j = (int(rng.integers(0, A.shape[0])), int(rng.integers(0, A.shape[1])),
+                     int(rng.integers(0, A.shape[2])))
+        Ap, Am = A.copy(), A.copy()
+        Ap[ix, iy, j] += h
+        Am[ix, iy, j] -= h
+        fd = (_thermal_loss(Ap, grid, Q, w, kT, quantity) - _thermal_loss(Am, grid, Q, w, kT, quantity)) / (2 * h)
+        assert g[ix, iy, j] == pytest.approx(fd, rel=1e-9, abs=1e-13)
+
+
+@pytest.mark.parametrize("quantity", [1, 2], ids=["imchi_T", "S"])
+def test_thermal_grad_A_homogeneity(quantity):
+    # L is homogeneous of degree 2 in A: <dL/dA, A> = 2 L (Euler)
+    grid, band, A, Q, w = _small_case()
+    g = oracle.thermal_grad_A_full(A, grid, Q, w, 0.08, quantity)
+    L = _thermal_loss(A, grid, Q, w, 0.08, quantity)
+    assert float(np.sum(g * A)) == pytest.approx(2 * L, rel=1e-12)
+
+
+def test_thermal_grad_A_zero_temperature_limit():
+    # kT far below the half cell: occupations exactly 0 or 1, Im chi_T = Im chi
+    # term by term, so the adjoints agree with the T = 0 one
+    grid, band, A, Q, w = _small_case()
+    kT = (2 * 1.0 / grid["n_eps"]) / 4000
+    g = oracle.thermal_grad_A_full(A, grid, Q, w, kT, oracle.IMCHI_T)
+    ref = oracle.grad_A_full(A, grid, Q, w)
+    assert np.abs(g - ref).max() <= 1e-13 * np.abs(ref).max()
