@@ -259,8 +259,15 @@ lindhard_status lindhard_imchi_f64(lindhard_plan *plan, const lindhard_band *ban
  *             dL/d(t, t', t'', mu, gamma) by the chain rule through Eqs. 4-5
  *             (A_in must be NULL), mu held fixed (a partial derivative even
  *             when mu was solved from the filling).
- * At least one of dA and dparams must be non-NULL.  LINDHARD_IMCHI grids only
- * (others: LINDHARD_EUNSUPPORTED). */
+ * At least one of dA and dparams must be non-NULL.
+ * Finite-temperature grids (Appendix A, Eq. A1; Eq. 1): L sums w times the
+ * grid's quantity (Im chi_T or S(q, w)); with a = A f, b = A (1 - f) on every
+ * cell and C(q, w) = sum a(p, e) b(p + q, e + w), Im chi_T = -c [C(q, w) -
+ * C(-q, -w)] and S = (c/pi) C(q, w), so
+ *   dL/dA(p, e_j) = kappa [f_j sum_{s,m} w'(s, m) b(p + s, e_{j+m})
+ *                          + (1 - f_j) sum_{s,m} w'(s, m) a(p - s, e_{j-m})]
+ * with kappa = -c, w'(s, m) = w(s, m) - w(-s, -m) (Im chi_T) or kappa = c/pi,
+ * w' = w (S); bands must then be given (their kT) also with A_in. */
 lindhard_status lindhard_imchi_backward(lindhard_plan *plan,
                                         const lindhard_band *bands,
                                         const float *A_in, const float *w,

@@ -10,6 +10,14 @@
 // products along p_x, and invert.  The wrap-around argument of the forward
 // call (P >= N + Q/2, PE >= n_eps) also covers these lags.
 //
+// Finite temperature (Appendix A, Eq. A1): a = A f and b = A (1 - f) on every
+// cell, and the correlation C(q, w) = sum a(p, e) b(p + q, e + w) enters
+// Im chi_T as C(q, w) - C(-q, -w) and S(q, w) as C(q, w).  For Im chi_T the
+// adjoint of C therefore sees w(q, w) - w(-q, -w), whose transform is the odd
+// part W^ - conj(W^) = 2i Im W^ (the forward's odd_part, applied to W^); for
+// S it sees w.  dL/dA = scale (f g + (1 - f) h) with the same Fermi weights as
+// the forward energy pass.
+//
 //   k_w_energy      : w [Q][Q][n_omega] (real) -> half spectra along energy,
 //                     two lines per complex FFT.                WU1 [Q][Q][SP]
 //   k_w_y           : FFT along q_y, lags placed at their circular index.
@@ -73,7 +81,7 @@ k_w_energy(Geom g, const Real *__restrict__ w, cx<Real> *__restrict__ WU1, const
         long long f = f0 + col;
         if (f >= npairs) continue;
         Cx zk = sm[E::saddr(col, k)];
-        Cx zm = sm[E::saddr(col, (L - k) & (L - 1))];
+        Cx zm = sm[E::saddr(col, k == 0 ? 0 : L - k)];   // Z(L - k), any length
         Cx w1 = mk<Cx>(half * (zk.x + zm.x), half * (zk.y - zm.y));
         Cx dd = mk<Cx>(zk.x - zm.x, zk.y + zm.y);
         Cx w2 = mk<Cx>(half * dd.y, -half * dd.x);
@@ -157,6 +165,10 @@ k_bw_product(Geom g, cx<Real> *__restrict__ U2, const cx<Real> *__restrict__ WU2
             v[b * EF::R0 + r] = (valid && n < g.N) ? colA[(long long)n * rstride] : zero;
         }
     EF::run(vw, sm, tw);
+    if (g.quantity == LINDHARD_IMCHI_T) {   // w(q, w) - w(-q, -w): W^ - conj(W^)
+#pragma unroll
+        for (int i = 0; i < EF::VPT; ++i) vw[i] = mk<Cx>((Real)0, (Real)2 * vw[i].y);
+    }
     EF::run(v, sm, tw);
 #pragma unroll
     for (int i = 0; i < EF::VPT; ++i) v[i] = cmul(vw[i], v[i]);          // h^ = W^ a^
@@ -311,7 +323,22 @@ k_bw_inv_energy(Geom g, Band band, const AxisTab *__restrict__ axis,
             long long line = line0 + col;
             if (line < nlines && n < g.n_eps) {
                 Cx x = v[b * E::RL + r];
-                Real d = sc * ((n < g.J0) ? x.x : x.y);     // dL/dA(p, e_n)
+                Real d;                                       // dL/dA(p, e_n)
+                if (band.kT > 0) {
+                    // Fermi weights of e_n as the forward energy pass forms them
+                    Real xe, u;
+                    if constexpr (sizeof(Real) == 4) {
+                        xe = (Real)(2 * n + 1 - g.n_eps) * band.x_step;
+                        u = expf(-fabsf(xe));
+                    } else {
+                        xe = (Real)(2 * n + 1 - g.n_eps) * (Real)band.x_step64;
+                        u = exp(-fabs(xe));
+                    }
+                    const Real big = (Real)1 / ((Real)1 + u), small = u * big;
+                    d = xe < 0 ? sc * (big * x.x + small * x.y) : sc * (small * x.x + big * x.y);
+                } else {
+                    d = sc * ((n < g.J0) ? x.x : x.y);
+                }
                 if (dA) dA[line * g.n_eps + n] = d;
                 if (want_params) {
                     Real e;
@@ -444,11 +471,12 @@ cudaError_t launch_bw_inv_energy_t(const Geom &g, const Band &band, const AxisTa
     return cudaGetLastError();
 }
 
+// energy lengths: powers of two and, at finite temperature, 3 * 2^k
 cudaError_t launch_w_energy(const Geom &g, const float *w, float2 *WU1, const float2 *tw, int tw_len,
                             cudaStream_t s)
 {
 #define CALL(L) launch_w_energy_t<L>(g, w, WU1, tw, tw_len, s)
-    LH_LEN_SWITCH(g.PE, CALL)
+    LH_P_SWITCH(g.PE, CALL)
 #undef CALL
 }
 cudaError_t launch_w_y(const Geom &g, const float2 *WU1, float2 *WU2, const float2 *tw, int tw_len, cudaStream_t s)
@@ -476,7 +504,7 @@ cudaError_t launch_bw_inv_energy(const Geom &g, const Band &band, const AxisTab 
                                  const float2 *tw, int tw_len, cudaStream_t s)
 {
 #define CALL(L) launch_bw_inv_energy_t<L>(g, band, axis, eps, st, G4, dA, partial, tw, tw_len, s)
-    LH_LEN_SWITCH(g.PE, CALL)
+    LH_P_SWITCH(g.PE, CALL)
 #undef CALL
 }
 int bw_energy_blocks(const Geom &g)
@@ -485,11 +513,17 @@ int bw_energy_blocks(const Geom &g)
     switch (g.PE) {
     case 16: C = LineCfg<16>::C; break;
     case 32: C = LineCfg<32>::C; break;
+    case 48: C = LineCfg<48>::C; break;
     case 64: C = LineCfg<64>::C; break;
+    case 96: C = LineCfg<96>::C; break;
     case 128: C = LineCfg<128>::C; break;
+    case 192: C = LineCfg<192>::C; break;
     case 256: C = LineCfg<256>::C; break;
+    case 384: C = LineCfg<384>::C; break;
     case 512: C = LineCfg<512>::C; break;
+    case 768: C = LineCfg<768>::C; break;
     case 1024: C = LineCfg<1024>::C; break;
+    case 1536: C = LineCfg<1536>::C; break;
     case 2048: C = LineCfg<2048>::C; break;
     default: C = LineCfg<4096>::C; break;
     }

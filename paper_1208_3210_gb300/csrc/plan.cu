@@ -1033,9 +1033,6 @@ extern "C" lindhard_status lindhard_imchi_backward(lindhard_plan *p, const lindh
     if (!p->backward) return fail(LINDHARD_EINVAL, "create the plan with LINDHARD_PLAN_BACKWARD");
     if (!dA && !dparams) return fail(LINDHARD_EINVAL, "nothing to compute: dA and dparams are both NULL");
     if (dparams && A_in) return fail(LINDHARD_EINVAL, "dparams needs the generated A (A_in must be NULL)");
-    for (int i = 0; i < p->batch; ++i)
-        if (p->geoms[i].quantity != LINDHARD_IMCHI)
-            return fail(LINDHARD_EUNSUPPORTED, "the adjoint is built for LINDHARD_IMCHI grids only");
     std::vector<Band> bs(p->batch);
     {
         lindhard_status st = bands_of(p, bands, A_in == nullptr, bs);

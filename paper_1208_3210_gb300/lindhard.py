@@ -214,8 +214,9 @@ class Plan:
         return out
 
     def backward(self, w, bands=None, A_in=None, dA=None, dparams=None, stream=None):
-        """Adjoint for L = sum w * Im chi: fills dA (float32, A layout) and/or
-        dparams (float64, [batch][5] = dL/d(t, t', t'', mu, gamma))."""
+        """Adjoint for L = sum w * X (X the grids' quantity: Im chi, Im chi_T or
+        S(q, w)): fills dA (float32, A layout) and/or dparams (float64,
+        [batch][5] = dL/d(t, t', t'', mu, gamma))."""
         assert w.dtype.is_floating_point and w.is_cuda and w.is_contiguous() and w.numel() == self.out_elems()
         if dA is not None:
             assert dA.is_cuda and dA.is_contiguous() and dA.numel() == self.a_elems()

@@ -220,3 +220,64 @@ def test_gradient_at_fixed_filling(lh, kind):
         scale = abs(fd) + abs(dp[r if r < 3 else 4]) + abs(dp[3] * dmu[r])
         print(f"kind {kind} d/d{name}: total {total[r]:.6e}, central difference {fd:.6e}")
         assert abs(total[r] - fd) <= 2e-4 * scale, (name, total[r], fd)
+
+
+# --- finite temperature (Appendix A, Eq. A1; Eq. 1) ------------------------------
+
+def _gpu_backward_thermal(lh, grid, band, w, A=None):
+    import torch
+    plan = lh.Plan([grid], backward=True)
+    s = plan.sizes[0]
+    w_t = torch.from_numpy(np.ascontiguousarray(w, dtype=np.float32)).cuda().reshape(-1)
+    dA = torch.empty(s.a_elems, dtype=torch.float32, device="cuda")
+    dp = None if A is not None else torch.zeros(5, dtype=torch.float64, device="cuda")
+    A_t = None if A is None else torch.from_numpy(np.ascontiguousarray(A, dtype=np.float32)).cuda().reshape(-1)
+    plan.backward(w_t, bands=[band], A_in=A_t, dA=dA, dparams=dp)
+    plan.status()
+    out = dA.cpu().numpy().astype(np.float64).reshape(s.N, s.N, s.n_eps)
+    dpn = None if dp is None else dp.cpu().numpy()
+    fft_e = s.fft_e
+    plan.close()
+    return out, dpn, fft_e
+
+
+# energy FFTs of 48 (3 * 2^4) and 32 points (n_eps + n_omega - 1 = 35 and 29)
+THERMAL_CFGS = [(dict(zones=2, npz=8, n_eps=24, e_max=1.5), 48), (dict(zones=1, npz=16, n_eps=20), 32)]
+
+
+@pytest.mark.parametrize("quantity", [1, 2], ids=["imchi_T", "S"])
+@pytest.mark.parametrize("cfg,pe", THERMAL_CFGS, ids=["PE48", "PE32"])
+def test_thermal_dA_matches_oracle_random_A(lh, cfg, pe, quantity):
+    grid = dict(_grid(**cfg), quantity=quantity)
+    kT = 0.05
+    band = dict(wl.band_params(filling=1.12, gamma=0.08, ff_a=0.8), kT=kT)
+    A = wl.random_spectral(grid, seed=3)
+    w = wl.loss_weights(grid, seed=6, dtype=np.float64).astype(np.float32).astype(np.float64)
+    got, _, fft_e = _gpu_backward_thermal(lh, grid, band, w, A=A)
+    assert fft_e == pe
+    ref = oracle.thermal_grad_A_full(A.astype(np.float32).astype(np.float64), grid, grid["q_extent"], w, kT, quantity)
+    err = np.abs(got - ref).max() / np.abs(ref).max()
+    print(f"PE {pe}, quantity {quantity}, caller A: dL/dA {err:.2e} of max")
+    assert err <= TOL32, err
+
+
+@pytest.mark.parametrize("quantity", [1, 2], ids=["imchi_T", "S"])
+@pytest.mark.parametrize("cfg,pe", THERMAL_CFGS, ids=["PE48", "PE32"])
+def test_thermal_dA_and_dparams_match_oracle_generated_A(lh, cfg, pe, quantity):
+    grid = dict(_grid(**cfg), quantity=quantity)
+    kT = 0.04
+    band = dict(wl.band_params(filling=1.1, gamma=0.07, ff_a=0.8), kT=kT)
+    w = wl.loss_weights(grid, seed=8, dtype=np.float64).astype(np.float32).astype(np.float64)
+    got, dp, fft_e = _gpu_backward_thermal(lh, grid, band, w)
+    assert fft_e == pe
+    b = _oracle_band(band, grid)
+    A = oracle.spectral(b, grid)
+    gref = oracle.thermal_grad_A_full(A, grid, grid["q_extent"], w, kT, quantity)
+    err = np.abs(got - gref).max() / np.abs(gref).max()
+    print(f"PE {pe}, quantity {quantity}: dL/dA {err:.2e} of max")
+    assert err <= TOL32, err
+    d = oracle.spectral_dtheta(b, grid)
+    for r in range(5):
+        terms = gref * d[r]
+        ref = terms.sum()
+        assert abs(dp[r] - ref) <= 1e-4 * np.abs(terms).sum(), (r, dp[r], ref)
