@@ -445,6 +445,56 @@ def thermal_form(lh, grids, bands, steps, autotune, stream, kT=0.025):
     return res
 
 
+def backward_bytes(s):
+    """Algorithmic HBM bytes of one adjoint call (lindhard_imchi_backward with
+    dL/dA and dL/dtheta) on one instance, counted like pass_bytes: the
+    forward energy and p_y passes again (a^, b^), w along energy and q_y, the
+    two products along p_x (a^, b^ and W^ read, h^ and g^ written), the
+    inverse along p_y and the inverse along energy writing dL/dA."""
+    N, P, PE, Q, n_omega, n_eps = s.N, s.fft_p, s.fft_e, s.q_extent, s.n_omega, s.n_eps
+    H = PE // 2 + 1
+    W1, W2 = N * N * 2 * H, N * P * 2 * H
+    WQ1, WQ2 = Q * Q * H, Q * P * H
+    return 8 * (W1 + (W1 + W2) + WQ1 + (WQ1 + WQ2) + (W2 + WQ2 + W2) + (W2 + W1) + W1) + 4 * (Q * Q * n_omega
+                                                                                          + N * N * n_eps)
+
+
+def backward_form(lh, grids, bands, steps, stream, peak, autotune):
+    """The adjoint (row a8): one lindhard_imchi_backward call for
+    L = sum w Im chi with seeded weights, dL/dA and dL/d(t, t', t'', mu, gamma)
+    both requested; device time per call, outside the timed region of the
+    forward call."""
+    import torch
+    try:
+        bp = lh.Plan(grids, backward=True, autotune=autotune)   # the forward p_y pass it repeats, tuned
+    except Exception as exc:
+        return {"unavailable": str(exc)}
+    gen = torch.Generator(device="cuda").manual_seed(7)
+    w = torch.rand(bp.out_elems(), generator=gen, device="cuda", dtype=torch.float32)
+    dA = torch.empty(bp.a_elems(), dtype=torch.float32, device="cuda")
+    dp = torch.zeros(5 * len(grids), dtype=torch.float64, device="cuda")
+    for _ in range(3):
+        bp.backward(w, bands=bands, dA=dA, dparams=dp)
+    bp.status()
+    n = max(3, min(steps, 20))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(n):
+        bp.backward(w, bands=bands, dA=dA, dparams=dp)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    bp.status()
+    ms = e0.elapsed_time(e1) / n
+    byts = sum(backward_bytes(bp.sizes[i]) for i in range(len(grids)))
+    res = {"ms_per_call": ms, "dA_elems_per_s": bp.a_elems() / (ms * 1e-3), "calls": n,
+           "algorithmic_bytes": byts, "gbs": byts / (ms * 1e-3) / 1e9,
+           "frac_of_hbm_peak": byts / (ms * 1e-3) / 1e9 / peak}
+    bp.close()
+    del w, dA, dp
+    return res
+
+
 def batched_form(lh, steps, autotune, stream, count=64):
     """The batched workload (`count` independent instances of mixed filling,
     broadening and size, one call per batch) in the plan's three batch forms:
@@ -759,12 +809,14 @@ def main():
     thermal = None
     direct = None
     batch = None
+    bwd = None
     if not batched and not args.no_tc:
         plan.imchi(bands, out=out, mu_out=mu)
         kk = kk_rpa_form(plan, out, args.steps, stream, peak)
         thermal = thermal_form(lh, grids, bands, args.steps, not args.no_autotune, stream)
         plan.imchi(bands, out=out, mu_out=mu)
         direct = energy_direct_form(lh, grids, bands, out, args.steps, mu, stream)
+        bwd = backward_form(lh, grids, bands, args.steps, stream, peak, not args.no_autotune)
         try:
             batch = batched_form(lh, args.steps, not args.no_autotune, stream)
         except Exception as exc:   # an extra object: never the main line's failure
@@ -815,6 +867,8 @@ def main():
             line["finite_temperature"] = thermal
         if direct is not None:
             line["energy_direct"] = direct
+        if bwd is not None:
+            line["backward"] = bwd
         if batch is not None:
             line["batched_64"] = batch
         if world == 1 and not args.no_cpu_baseline:
