@@ -485,9 +485,14 @@ cudaError_t launch_w_y(const Geom &g, const float2 *WU1, float2 *WU2, const floa
     LH_P_SWITCH(g.P, CALL)
 #undef CALL
 }
+bool pr_fwd_applies(const Geom &g);
+bool pr_inv_applies(const Geom &g);
+cudaError_t launch_bw_product_pr(const Geom &g, float2 *U2, const float2 *WU2, const float2 *ptw, cudaStream_t s);
+// the pruned engine (k_pruned.cu) where the padding is exactly one third
 cudaError_t launch_bw_product(const Geom &g, float2 *U2, const float2 *WU2, const float2 *tw, int tw_len,
-                              cudaStream_t s)
+                              const float2 *ptw, cudaStream_t s)
 {
+    if (ptw && pr_fwd_applies(g) && pr_inv_applies(g)) return launch_bw_product_pr(g, U2, WU2, ptw, s);
 #define CALL(L) launch_bw_product_t<L>(g, U2, WU2, tw, tw_len, s)
     LH_P_SWITCH(g.P, CALL)
 #undef CALL

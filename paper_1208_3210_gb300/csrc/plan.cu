@@ -83,7 +83,7 @@ cudaError_t launch_w_energy(const Geom &g, const float *w, float2 *WU1, const fl
                             cudaStream_t s);
 cudaError_t launch_w_y(const Geom &g, const float2 *WU1, float2 *WU2, const float2 *tw, int tw_len, cudaStream_t s);
 cudaError_t launch_bw_product(const Geom &g, float2 *U2, const float2 *WU2, const float2 *tw, int tw_len,
-                              cudaStream_t s);
+                              const float2 *ptw, cudaStream_t s);
 cudaError_t launch_bw_inv_y(const Geom &g, const float2 *G3, float2 *G4, const float2 *tw, int tw_len,
                             cudaStream_t s);
 cudaError_t launch_bw_inv_energy(const Geom &g, const Band &band, const AxisTab *axis, const float2 *eps,
@@ -1062,7 +1062,7 @@ extern "C" lindhard_status lindhard_imchi_backward(lindhard_plan *p, const lindh
         if (e == cudaSuccess) e = launch_fwd_y(g, wk, s, p->yvar_fwd[i]);                           // Y = U2
         if (e == cudaSuccess) e = launch_w_energy(g, w + o_off, X, tw, p->tw_len, s);                // X = WU1
         if (e == cudaSuccess) e = launch_w_y(g, X, Z, tw, p->tw_len, s);                             // Z = WU2
-        if (e == cudaSuccess) e = launch_bw_product(g, Y, Z, tw, p->tw_len, s);                      // Y = G3
+        if (e == cudaSuccess) e = launch_bw_product(g, Y, Z, tw, p->tw_len, (const float2 *)wk.ptw, s);              // Y = G3
         if (e == cudaSuccess) e = launch_bw_inv_y(g, Y, X, tw, p->tw_len, s);                        // X = G4
         if (e == cudaSuccess)
             e = launch_bw_inv_energy(g, b, wk.axis, (const float2 *)wk.eps, wk.state, X, dA ? dA + a_off : nullptr,

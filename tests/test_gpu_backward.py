@@ -281,3 +281,38 @@ def test_thermal_dA_and_dparams_match_oracle_generated_A(lh, cfg, pe, quantity):
         terms = gref * d[r]
         ref = terms.sum()
         assert abs(dp[r] - ref) <= 1e-4 * np.abs(terms).sum(), (r, dp[r], ref)
+
+
+@pytest.mark.parametrize("quantity", [0, 1, 2], ids=["imchi", "imchi_T", "S"])
+def test_pruned_product_geometry_against_oracle_samples(lh, quantity):
+    # N = Q = 2P/3 (P = 192): the adjoint's p_x products run on the pruned
+    # engine (weights loaded as rows [0, Q) and phase-shifted, the inverse
+    # keeping p_x < N); seeded cells against the oracle's adjoint sums
+    import torch
+    grid = dict(_grid(2, 64, 24, 1.5), quantity=quantity)
+    band = wl.band_params(filling=1.1, gamma=0.07, ff_a=0.8)
+    kT = 0.05 if quantity else 0.0
+    if quantity:
+        band = dict(band, kT=kT)
+    w = wl.loss_weights(grid, seed=9, dtype=np.float64).astype(np.float32).astype(np.float64)
+    plan = lh.Plan([grid], backward=True)
+    s = plan.sizes[0]
+    assert s.fft_p == 192 and s.N == 128 and s.q_extent == 128
+    w_t = torch.from_numpy(np.ascontiguousarray(w, dtype=np.float32)).cuda().reshape(-1)
+    dA = torch.empty(s.a_elems, dtype=torch.float32, device="cuda")
+    plan.backward(w_t, bands=[band], dA=dA)
+    plan.status()
+    got = dA.cpu().numpy().astype(np.float64).reshape(s.N, s.N, s.n_eps)
+    plan.close()
+    b = _oracle_band(band, grid)
+    A = oracle.spectral(b, grid)
+    rng = np.random.default_rng(12)
+    ix, iy, jj = rng.integers(0, 128, 300), rng.integers(0, 128, 300), rng.integers(0, 24, 300)
+    if quantity:
+        ref = oracle.thermal_grad_A_samples(A, grid, 128, w, kT, quantity, ix, iy, jj)
+    else:
+        ref = oracle.grad_A_samples(A, grid, 128, w, ix, iy, jj)
+    scale = np.abs(ref).max()
+    err = np.abs(got[ix, iy, jj] - ref).max() / scale
+    print(f"quantity {quantity}: dL/dA {err:.2e} of the samples' max")
+    assert err <= TOL32, err
