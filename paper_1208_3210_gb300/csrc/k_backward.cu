@@ -249,7 +249,7 @@ k_bw_inv_y(Geom g, const cx<Real> *__restrict__ G3, cx<Real> *__restrict__ G4, c
 // --- inverse along energy, dL/dA and dL/dtheta -----------------------------------
 // partial[blockIdx.x][5] receives this CTA's FP64 sums of dL/dA * dA/dtheta.
 template <typename Real, int L>
-__global__ void __launch_bounds__(LineCfg<L>::T)
+__global__ void __launch_bounds__(LineCfg<L>::T, (L & (L - 1)) == 0 ? 3 : 1)   // 16-value tiles: three CTAs per SM
 k_bw_inv_energy(Geom g, Band band, const AxisTab *__restrict__ axis,
                 const typename EpsEntry<Real>::type *__restrict__ eps, const InstState *__restrict__ st,
                 const cx<Real> *__restrict__ G4, Real *__restrict__ dA, double *__restrict__ partial,
@@ -312,7 +312,7 @@ k_bw_inv_energy(Geom g, Band band, const AxisTab *__restrict__ axis,
     E::run(v, sm, tw);   // ends with __syncthreads: s_* visible
 
     const Real sc = (Real)g.scale;
-    const Real gam = (Real)band.gamma, g2 = gam * gam;
+    const Real gam = (Real)band.gamma, g2 = gam * gam, igam = (Real)1 / gam;
     Real acc_xi[4] = {0, 0, 0, 0}, acc_g = 0;
 #pragma unroll
     for (int b = 0; b < E::VPT / E::RL; ++b)
@@ -349,10 +349,17 @@ k_bw_inv_energy(Geom g, Band band, const AxisTab *__restrict__ axis,
                         e = eps[n] - s_xhi[col];
                     }
                     Real D = e * e + g2;
-                    Real iD = (Real)1 / D;
+                    Real iD;
+                    if constexpr (sizeof(Real) == 4) {
+                        // the hardware reciprocal (relative error about 2^-23;
+                        // D lies in [gamma^2, 4 e_max^2 + gamma^2])
+                        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(iD) : "f"(D));
+                    } else {
+                        iD = (Real)1 / D;
+                    }
                     Real A = s_amp[col] * iD;
                     Real dxi = d * (2 * e * A * iD);                  // dL/dA * dA/dxi
-                    Real dg = d * (s_amp[col] / gam) * (e * e - g2) * iD * iD;   // dL/dA * dA/dgamma
+                    Real dg = d * (s_amp[col] * igam) * (e * e - g2) * iD * iD;   // dL/dA * dA/dgamma
 #pragma unroll
                     for (int q = 0; q < 4; ++q) acc_xi[q] += dxi * s_f[col][q];
                     acc_g += dg;
@@ -375,22 +382,44 @@ k_bw_inv_energy(Geom g, Band band, const AxisTab *__restrict__ axis,
     }
 }
 
-// Final sum of the per-CTA partials, in a fixed order (deterministic).
-__global__ void k_reduce_params(const double *__restrict__ partial, int nblocks, double *__restrict__ out)
+// Final sum of the per-CTA partials [nblocks][5] in a fixed order
+// (deterministic), in two levels: KRP_G CTAs each sum one fixed contiguous
+// range into level[g][5], then one CTA sums the KRP_G rows.  In a CTA, 1020
+// threads sweep the range coalesced, thread t always on component t % 5 (the
+// stride 1020 keeps it), eight independent chains each; then each
+// component's 204 thread sums are added in thread order.
+constexpr int KRP_T = 1020, KRP_G = 64;
+__device__ __forceinline__ void krp_sum(const double *__restrict__ src, long long n, double *s, double *dst)
 {
-    __shared__ double s[256];
-    for (int q = 0; q < 5; ++q) {
-        double t = 0;
-        for (int i = threadIdx.x; i < nblocks; i += 256) t += partial[(size_t)i * 5 + q];
-        s[threadIdx.x] = t;
-        __syncthreads();
-        for (int w = 128; w > 0; w >>= 1) {
-            if (threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) out[q] = s[0];
-        __syncthreads();
+    const int t = threadIdx.x;
+    if (t < KRP_T) {
+        double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        long long i = t;
+        for (; i + 7 * KRP_T < n; i += 8 * KRP_T)
+#pragma unroll
+            for (int u = 0; u < 8; ++u) acc[u] += src[i + u * KRP_T];
+        for (; i < n; i += KRP_T) acc[0] += src[i];
+        s[t] = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
     }
+    __syncthreads();
+    if (t < 5) {
+        double acc = 0;
+        for (int k = t; k < KRP_T; k += 5) acc += s[k];
+        dst[t] = acc;
+    }
+}
+__global__ void __launch_bounds__(1024) k_reduce_params1(const double *__restrict__ partial, int nblocks,
+                                                         double *__restrict__ level)
+{
+    __shared__ double s[KRP_T];
+    const long long per = (nblocks + KRP_G - 1) / KRP_G;
+    const long long b0 = min((long long)nblocks, per * blockIdx.x), b1 = min((long long)nblocks, b0 + per);
+    krp_sum(partial + 5 * b0, 5 * (b1 - b0), s, level + 5 * blockIdx.x);
+}
+__global__ void __launch_bounds__(1024) k_reduce_params2(const double *__restrict__ level, double *__restrict__ out)
+{
+    __shared__ double s[KRP_T];
+    krp_sum(level, 5LL * KRP_G, s, out);
 }
 
 // --- launchers ------------------------------------------------------------------
@@ -535,9 +564,12 @@ int bw_energy_blocks(const Geom &g)
     long long nlines = (long long)g.N * g.N;
     return (int)((nlines + C - 1) / C);
 }
+// partial holds nblocks x 5 sums followed by room for KRP_G x 5
 cudaError_t launch_reduce_params(const double *partial, int nblocks, double *out, cudaStream_t s)
 {
-    k_reduce_params<<<1, 256, 0, s>>>(partial, nblocks, out);
+    double *level = const_cast<double *>(partial) + 5LL * nblocks;
+    k_reduce_params1<<<KRP_G, 1024, 0, s>>>(partial, nblocks, level);
+    k_reduce_params2<<<1, 1024, 0, s>>>(level, out);
     return cudaGetLastError();
 }
 

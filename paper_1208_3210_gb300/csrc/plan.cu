@@ -540,7 +540,8 @@ extern "C" lindhard_status lindhard_plan_create(const lindhard_grid *grids, int 
                             (size_t)g.Q * g.Q * d.o.SP}) * cb;
         }
         n.Z = p->backward ? (size_t)g.Q * (size_t)g.xs3 * cb : 0;
-        n.partial = p->backward ? (size_t)bw_energy_blocks(g) * 5 * sizeof(double) : 0;
+        // the last pass's per-CTA sums, then the first reduction level's (KRP_G x 5)
+        n.partial = p->backward ? (size_t)(bw_energy_blocks(g) + 64) * 5 * sizeof(double) : 0;
         n.axis = (size_t)g.N * sizeof(AxisTab);
         n.eps32 = (size_t)g.n_eps * sizeof(float2);
         n.eps64 = (size_t)g.n_eps * sizeof(double);
