@@ -50,3 +50,22 @@ def _with_root(digest, root, fnames):
     finally:
         bench.ROOT = saved
 
+
+
+def test_backward_bytes_of_the_large_workload():
+    # the adjoint call at 1024^2 x 512 (P = 1536, H = 257, Q = 1024, 256
+    # transfers): each pass's reads and writes counted by hand
+    s = types.SimpleNamespace(N=1024, fft_p=1536, fft_e=512, q_extent=1024, n_omega=256, n_eps=512)
+    H = 257
+    W1, W2 = 1024 * 1024 * 2 * H, 1024 * 1536 * 2 * H          # a^ b^ along energy, along p_y
+    WQ1, WQ2 = 1024 * 1024 * H, 1024 * 1536 * H                # W^ along energy, along q_y
+    passes = [
+        8 * W1,                                                # energy forward (write)
+        8 * (W1 + W2),                                         # p_y forward
+        4 * 1024 * 1024 * 256 + 8 * WQ1,                       # w along energy
+        8 * (WQ1 + WQ2),                                       # w along q_y
+        8 * (W2 + WQ2 + W2),                                   # products along p_x (h^, g^ over a^, b^)
+        8 * (W2 + W1),                                         # p_y inverse
+        8 * W1 + 4 * 1024 * 1024 * 512,                        # energy inverse, dL/dA written
+    ]
+    assert bench.backward_bytes(s) == sum(passes) == 57118031872
