@@ -173,11 +173,14 @@ k_bw_product_pr(Geom g, float2 *__restrict__ U2, const float2 *__restrict__ WU2,
     };
 
     float2 vw[24], v[24];
+    {
+        const float2 *pw = colW + (long long)j * ws, *pa = colA + (long long)j * rs;
+        const long long dw = (long long)(L / 24) * ws, da = (long long)(L / 24) * rs;
 #pragma unroll
-    for (int r = 0; r < 16; ++r) {
-        const long long n = j + r * (L / 24);
-        vw[r] = valid ? __ldg(colW + n * ws) : zero;
-        v[r] = valid ? __ldg(colA + n * rs) : zero;
+        for (int r = 0; r < 16; ++r) {
+            vw[r] = valid ? __ldg(pw + r * dw) : zero;
+            v[r] = valid ? __ldg(pa + r * da) : zero;
+        }
     }
     EF2::run(vw, v, sm, ptw);
 #pragma unroll
@@ -194,8 +197,12 @@ k_bw_product_pr(Geom g, float2 *__restrict__ U2, const float2 *__restrict__ WU2,
     }
     EI::run(v, v, sm, ptw);
     if (valid) pr_store_lags<L, EI>(v, [&](int l, float2 x) { colA[(long long)l * rs] = x; });
+    {
+        const float2 *pb = colB + (long long)j * rs;
+        const long long db = (long long)(L / 24) * rs;
 #pragma unroll
-    for (int r = 0; r < 16; ++r) v[r] = valid ? __ldg(colB + (long long)(j + r * (L / 24)) * rs) : zero;
+        for (int r = 0; r < 16; ++r) v[r] = valid ? __ldg(pb + r * db) : zero;
+    }
     EF1::run(v, v, sm, ptw);
 #pragma unroll
     for (int b = 0; b < 24 / EF2::RL; ++b) {
