@@ -263,17 +263,22 @@ def _small_case(zones=2, npz=4, n_eps=10, seed=1):
     return grid, band, A, Q, w
 
 
+@pytest.mark.parametrize("n_eps", [10, 11])
 @pytest.mark.parametrize("zones", [1, 2])
-def test_grad_A_central_difference_is_exact(zones):
+def test_grad_A_central_difference_is_exact(zones, n_eps):
     # L is a quadratic form in A, so a central difference in A is exact up to
-    # rounding: (L(A + hE) - L(A - hE)) / 2h = dL/dA . E.
-    grid, band, A, Q, w = _small_case(zones=zones, npz=6 if zones == 1 else 4)
+    # rounding: (L(A + hE) - L(A - hE)) / 2h = dL/dA . E.  An odd energy count
+    # puts a cell at e = 0 (empty by the split): every cell is probed there.
+    grid, band, A, Q, w = _small_case(zones=zones, npz=6 if zones == 1 else 4, n_eps=n_eps)
     g = oracle.grad_A_full(A, grid, Q, w)
     rng = np.random.default_rng(7)
     h = 0.05
-    for _ in range(6):
-        ix, iy, j = (int(rng.integers(0, A.shape[0])), int(rng.integers(0, A.shape[1])),
-                     int(rng.integers(0, A.shape[2])))
+    cells = [(int(rng.integers(0, A.shape[0])), int(rng.integers(0, A.shape[1])), int(rng.integers(0, A.shape[2])))
+             for _ in range(6)]
+    if n_eps % 2:
+        cells += [(int(rng.integers(0, A.shape[0])), int(rng.integers(0, A.shape[1])), j)
+                  for j in (n_eps // 2 - 1, n_eps // 2, n_eps // 2 + 1)]
+    for ix, iy, j in cells:
         Ap, Am = A.copy(), A.copy()
         Ap[ix, iy, j] += h
         Am[ix, iy, j] -= h
