@@ -426,6 +426,25 @@ def test_envelope_recovers_a_lorentzian_envelope(k):
     assert abs(oracle.envelope_k0(im, npz, 2)[0] - k) <= 1e-6 * k
 
 
+def test_envelope_takes_each_zone_whole():
+    # a zone is the lag window [G_n - npz/2, G_n + npz/2) around its
+    # reciprocal lattice vector: with each zone's spike a quarter zone left of
+    # G_n, the maxima sit there (a window shifted by half a zone would take
+    # the next zone's spike instead)
+    Q, npz, k = 256, 16, 5.0
+    dp = 2 * math.pi / npz
+    lag = np.arange(Q) - Q // 2
+    q = lag * dp
+    spike = (lag + npz // 4) % npz == 0
+    im = np.zeros((Q, Q, 2))
+    im[:, Q // 2, 1] = -np.where(spike, 1.0 / (1.0 + (q / k) ** 2), 0.01)
+    k0, qs, ys = oracle.envelope_k0(im, npz, 1)
+    assert np.allclose(qs, 2 * math.pi * (np.arange(len(qs)) - 0.25))
+    env = 1.0 / (1.0 + (qs / k) ** 2)
+    assert np.allclose(ys, env / env.max(), rtol=1e-14)          # the spikes, normalised by the largest
+    assert 0 < k0 < Q * dp
+
+
 def test_envelope_of_the_lindhard_response_decays():
     # on an extended grid the zone maxima of -Im chi fall off with q (the form
     # factor |M(p)|^2 and the band) and the fitted k0 is finite and positive
