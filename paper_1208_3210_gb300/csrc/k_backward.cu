@@ -564,6 +564,8 @@ int bw_energy_blocks(const Geom &g)
     long long nlines = (long long)g.N * g.N;
     return (int)((nlines + C - 1) / C);
 }
+// rows the reduction's first level adds after the nblocks x 5 sums
+int bw_partial_extra_rows() { return KRP_G; }
 // partial holds nblocks x 5 sums followed by room for KRP_G x 5
 cudaError_t launch_reduce_params(const double *partial, int nblocks, double *out, cudaStream_t s)
 {

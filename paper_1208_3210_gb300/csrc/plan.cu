@@ -94,6 +94,7 @@ cudaError_t launch_sum_rule(const Geom &g, const Band &band, const AxisTab *axis
                             const InstState *st, const float *A_in, const float *out, double *D, double *sum_q,
                             double *dos_corr, cudaStream_t s);
 cudaError_t launch_reduce_params(const double *partial, int nblocks, double *out, cudaStream_t s);
+int bw_partial_extra_rows();
 }  // namespace lh
 
 using namespace lh;
@@ -540,8 +541,8 @@ extern "C" lindhard_status lindhard_plan_create(const lindhard_grid *grids, int 
                             (size_t)g.Q * g.Q * d.o.SP}) * cb;
         }
         n.Z = p->backward ? (size_t)g.Q * (size_t)g.xs3 * cb : 0;
-        // the last pass's per-CTA sums, then the first reduction level's (KRP_G x 5)
-        n.partial = p->backward ? (size_t)(bw_energy_blocks(g) + 64) * 5 * sizeof(double) : 0;
+        // the last pass's per-CTA sums, then the first reduction level's
+        n.partial = p->backward ? (size_t)(bw_energy_blocks(g) + bw_partial_extra_rows()) * 5 * sizeof(double) : 0;
         n.axis = (size_t)g.N * sizeof(AxisTab);
         n.eps32 = (size_t)g.n_eps * sizeof(float2);
         n.eps64 = (size_t)g.n_eps * sizeof(double);
